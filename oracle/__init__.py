@@ -1,0 +1,235 @@
+"""FP64 CPU oracle for the HJ-Gauss frozen-coefficient Picard sweep.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package; the library under
+``paper_2605_18566_gb300/`` never does, and shares no code with it.
+
+The arithmetic lives in ``hjg_oracle.c`` (plain C, double precision, OpenMP over
+evaluation states) and in ``mlp.py`` (surrogate network, numpy FP64).  This module
+compiles the C file with gcc on first use and exposes thin ctypes wrappers.
+
+Paper sections restated here: Algorithm 1 (Picard loop), Eq. coeff_frozen and
+Lemma 2.7 (coefficient map), Remark 2.8 (sign and clip), Corollaries B.4-B.6 (value,
+gradient and tilted estimators), Section 2.4 (ESS), Appendix D.2 and Section 3.2 (games).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hjg_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GAMES = {"dubins3": 1, "rockets6": 2, "rockets45": 3, "flock4": 4,
+         "quadratic": 100, "zero_h": 101}
+
+
+class Problem(C.Structure):
+    """Mirror of ``orc_problem`` in hjg_oracle.c."""
+    _fields_ = [
+        ("game", C.c_int32), ("n", C.c_int32),
+        ("delta", C.c_double), ("T", C.c_double), ("eta", C.c_double),
+        ("c_min", C.c_double), ("c_max", C.c_double), ("radius", C.c_double),
+        ("speed", C.c_double * 16), ("h_sign", C.c_double),
+        ("A", C.c_double * 64), ("x0", C.c_double * 8), ("d", C.c_double),
+        ("seed", C.c_uint64), ("instance", C.c_uint32), ("tilt", C.c_int32),
+        ("flock_k", C.c_int32), ("pad_", C.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile hjg_oracle.c into liboracle.so (gcc, -O2, OpenMP)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB_PATH)
+        P = C.POINTER
+        d, i64, u32, i32 = C.c_double, C.c_int64, C.c_uint32, C.c_int
+        pd = P(C.c_double)
+        L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+        L.orc_philox_batch.argtypes = [i64, P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+        L.orc_u01.argtypes = [u32]; L.orc_u01.restype = d
+        L.orc_normals.argtypes = [i32, C.c_uint64, u32, u32, u32, u32, pd]
+        L.orc_ell.argtypes = [P(Problem), pd, pd]; L.orc_ell.restype = d
+        L.orc_grad_ell.argtypes = [P(Problem), pd, pd, pd]
+        L.orc_hamiltonian.argtypes = [P(Problem), pd, pd, d]; L.orc_hamiltonian.restype = d
+        L.orc_coef.argtypes = [P(Problem), pd, pd, d]; L.orc_coef.restype = d
+        L.orc_sweep.argtypes = [P(Problem), i64, pd, pd, pd, pd, i64, u32, pd, pd, pd]
+        L.orc_sweep.restype = i32
+        L.orc_init.argtypes = [P(Problem), i64, pd, pd, pd, pd, pd, pd]
+        L.orc_residual.argtypes = [i64, pd, pd, pd, pd]
+        L.orc_picard.argtypes = [P(Problem), i64, pd, pd, pd, i64, i32, u32,
+                                 pd, pd, pd, pd, pd, pd]
+        L.orc_picard.restype = i32
+        L.orc_num_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=None,
+                 c_max=None, radius=0.5, speed=None, h_sign=1.0, A=None, x0=None,
+                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7) -> Problem:
+    """Build an oracle problem.  Defaults follow the readings used throughout:
+    eta = 1e-6, c_min = 1e-2/delta, c_max = 1e2/delta."""
+    P = Problem()
+    P.game = GAMES[game]
+    P.n = n
+    P.delta = delta
+    P.T = T
+    P.eta = eta
+    P.c_min = (1e-2 / delta) if c_min is None else c_min
+    P.c_max = (1e2 / delta) if c_max is None else c_max
+    P.radius = radius
+    sp = [1.0] * 16 if speed is None else list(speed) + [1.0] * (16 - len(speed))
+    for k in range(16):
+        P.speed[k] = sp[k]
+    P.h_sign = h_sign
+    if A is not None:
+        A = np.asarray(A, dtype=np.float64).reshape(n, n)
+        for k, val in enumerate(A.ravel()):
+            P.A[k] = val
+    if x0 is not None:
+        for k, val in enumerate(np.asarray(x0, dtype=np.float64).ravel()):
+            P.x0[k] = val
+    P.d = d
+    P.seed = seed
+    P.instance = instance
+    P.tilt = 1 if tilt else 0
+    P.flock_k = flock_k
+    return P
+
+
+# ---------------------------------------------------------------- primitives
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 blocks: ctr uint32 [K,4], key uint32 [K,2] -> uint32 [K,4]."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    P = C.POINTER(C.c_uint32)
+    lib().orc_philox_batch(ctr.shape[0], ctr.ctypes.data_as(P), key.ctypes.data_as(P),
+                           out.ctypes.data_as(P))
+    return out
+
+
+def u01(x: int) -> float:
+    return lib().orc_u01(int(x))
+
+
+def normals(n, seed, instance, sample, point, sweep):
+    z = np.zeros(n, dtype=np.float64)
+    lib().orc_normals(n, seed, instance, sample, point, sweep, _dp(z))
+    return z
+
+
+def ell(P, y, nbr=None):
+    y = _f64(y)
+    nb = _f64(nbr) if nbr is not None else None
+    return lib().orc_ell(C.byref(P), _dp(y), _dp(nb))
+
+
+def grad_ell(P, x, nbr=None):
+    x = _f64(x)
+    g = np.zeros(P.n)
+    nb = _f64(nbr) if nbr is not None else None
+    lib().orc_grad_ell(C.byref(P), _dp(x), _dp(nb), _dp(g))
+    return g
+
+
+def hamiltonian(P, x, p, psibar=0.0):
+    return lib().orc_hamiltonian(C.byref(P), _dp(_f64(x)), _dp(_f64(p)), float(psibar))
+
+
+def coef(P, x, p, psibar=0.0):
+    return lib().orc_coef(C.byref(P), _dp(_f64(x)), _dp(_f64(p)), float(psibar))
+
+
+# ---------------------------------------------------------------- method
+def init(P, x, nbr=None, psibar=None):
+    """Algorithm 1 initial iterate: (v0, p0, c0) at states x [M,n]."""
+    x = _f64(x).reshape(-1, P.n)
+    M = x.shape[0]
+    v0 = np.zeros(M); p0 = np.zeros((M, P.n)); c0 = np.zeros(M)
+    nb = _f64(nbr) if nbr is not None else None
+    pb = _f64(psibar) if psibar is not None else None
+    lib().orc_init(C.byref(P), M, _dp(x), _dp(nb), _dp(pb), _dp(v0), _dp(p0), _dp(c0))
+    return v0, p0, c0
+
+
+def sweep(P, x, c, N, sweep_index, theta=None, nbr=None):
+    """One frozen-coefficient heat-kernel solve Phi(c) at states x: (v, p, ess)."""
+    x = _f64(x).reshape(-1, P.n)
+    M = x.shape[0]
+    c = _f64(c).reshape(M)
+    th = _f64(theta).reshape(M, P.n) if theta is not None else None
+    nb = _f64(nbr) if nbr is not None else None
+    v = np.zeros(M); p = np.zeros((M, P.n)); ess = np.zeros(M)
+    rc = lib().orc_sweep(C.byref(P), M, _dp(x), _dp(c), _dp(th), _dp(nb), int(N),
+                         int(sweep_index), _dp(v), _dp(p), _dp(ess))
+    if rc:
+        raise RuntimeError("orc_sweep failed (%d)" % rc)
+    return v, p, ess
+
+
+def picard(P, x, N, K, k0=0, state=None, nbr=None, psibar=None):
+    """Algorithm 1 for K sweeps.  Returns dict with v_hist [K+1,M], p, c, resid, sup, ess.
+    ``state`` = (v, p, c) to resume from; default is the initial iterate."""
+    x = _f64(x).reshape(-1, P.n)
+    M = x.shape[0]
+    if state is None:
+        v0, p, c = init(P, x, nbr, psibar)
+    else:
+        v0, p, c = (_f64(s).copy() for s in state)
+        p = p.reshape(M, P.n)
+    v_hist = np.zeros((K + 1, M)); v_hist[0] = v0
+    resid = np.zeros(K); sup = np.zeros(K); ess = np.zeros(M)
+    p = np.ascontiguousarray(p); c = np.ascontiguousarray(c)
+    nb = _f64(nbr) if nbr is not None else None
+    pb = _f64(psibar) if psibar is not None else None
+    rc = lib().orc_picard(C.byref(P), M, _dp(x), _dp(nb), _dp(pb), int(N), int(K), int(k0),
+                          _dp(v_hist), _dp(p), _dp(c), _dp(resid), _dp(sup), _dp(ess))
+    if rc:
+        raise RuntimeError("orc_picard failed (%d)" % rc)
+    return {"v_hist": v_hist, "v": v_hist[-1].copy(), "p": p, "c": c,
+            "resid": resid, "sup": sup, "ess": ess}
+
+
+def residual(v_old, v_new):
+    v_old = _f64(v_old); v_new = _f64(v_new)
+    rel = C.c_double(); sup = C.c_double()
+    lib().orc_residual(v_old.size, _dp(v_old), _dp(v_new), C.byref(rel), C.byref(sup))
+    return rel.value, sup.value
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())

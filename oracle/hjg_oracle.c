@@ -1,0 +1,449 @@
+/*
+ * hjg_oracle.c -- plain, slow FP64 CPU oracle for the HJ-Gauss frozen-coefficient
+ * Picard sweep (arXiv 2605.18566).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link or call
+ * this file; it exists so that the tests, the smoke check and the CPU baseline of the
+ * benchmark can compare the CUDA path against an independent restatement of the paper.
+ * It shares no source with the CUDA library.
+ *
+ * What it computes, and where the paper defines it:
+ *   - Algorithm 1 (quasi-linearisation Picard loop): v^(0)=g, c^(0)=Gamma(Dg); per
+ *     sweep freeze c, solve the heat equation through its Gaussian expectation,
+ *     recover v = -(1/c) log phi, update Dv and c, report the relative change.
+ *   - Eq. (coeff_frozen) / Lemma 2.7 (coeff_regularized): c = (2/delta) H / (|p|^2+eta),
+ *     Remark 2.8 (coeff_sign): sign kept, |c| clipped to [c_min, c_max].
+ *   - Proposition 2.1 / Lemma 2.2 (heat-kernel expectation, sample covariance delta*t*I),
+ *     Corollary B.4 (log-sum-exp value estimator), Corollary B.5 (MC gradient estimator
+ *     (x - sum s_i w_i / sum w_i) / (t delta c)), Corollary B.6 (tilted proposal with
+ *     density-ratio weight w_theta), Section 2.4 (ESS).
+ *   - Games: Appendix D.2 Dubins relative game (Hamiltonian of Eq. dubins_ham_unit
+ *     with the sign of the p2 term taken from the dynamics of Eq. dubins_dyna),
+ *     Section 3.2 multi-rocket game (Eq. multiagent_dynamics), a two-rocket planar game
+ *     built from the same per-agent dynamics, and quadratic test problems
+ *     (H = +-|p|^2/2, the exact Cole-Hopf case of Corollary B.2).
+ *   - Counter-based sampler: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), uniforms
+ *     u = ((x>>9)+0.5) 2^-23, Box-Muller normals.
+ *
+ * Everything is double precision except the Philox integer stream itself.
+ * Pinned by tests/test_oracle_*.py (closed forms, quadrature, brute force, an
+ * independent Philox implementation); see each function for its pin.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAXN 64
+
+enum {
+    ORC_DUBINS3 = 1,
+    ORC_ROCKETS6 = 2,
+    ORC_ROCKETS45 = 3,
+    ORC_FLOCK4 = 4,
+    ORC_TEST_QUADRATIC = 100,
+    ORC_TEST_ZERO_H = 101
+};
+
+/* Problem description.  Field order is mirrored by the ctypes Structure in
+ * oracle/__init__.py. */
+typedef struct {
+    int32_t game;
+    int32_t n;          /* state dimension */
+    double delta;       /* viscosity delta (= 2 nu) */
+    double T;           /* horizon t at which v(t;x) is evaluated */
+    double eta;         /* denominator regulariser of Lemma 2.7 */
+    double c_min;       /* |c| clip bounds of Remark 2.8 */
+    double c_max;
+    double radius;      /* capture radius of the signed-distance target */
+    double speed[16];   /* per-agent forward speeds */
+    double h_sign;      /* quadratic test: H = h_sign * |p|^2 / 2 */
+    double A[64];       /* quadratic test target l(y) = (y-x0)^T A (y-x0)/2 + d, A row-major n x n */
+    double x0[8];
+    double d;
+    uint64_t seed;
+    uint32_t instance;
+    int32_t tilt;       /* 1: tilted proposal theta = -sigma^2 c p (Eq. tilt_shift) */
+    int32_t flock_k;    /* flock: neighbours per agent */
+    int32_t pad_;
+} orc_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10.  Each round multiplies two counter words by fixed odd
+ * constants (full 64-bit products), swaps and mixes the halves with the key,
+ * and the key is advanced by the Weyl increments between rounds. */
+
+static const uint32_t PHILOX_MUL0 = 0xD2511F53u;
+static const uint32_t PHILOX_MUL1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_WEYL0 = 0x9E3779B9u;
+static const uint32_t PHILOX_WEYL1 = 0xBB67AE85u;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)PHILOX_MUL0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)PHILOX_MUL1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += PHILOX_WEYL0;
+        k1 += PHILOX_WEYL1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox_batch(int64_t count, const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    for (int64_t i = 0; i < count; ++i)
+        orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* 23-bit uniform strictly inside (0,1): every value is exact in FP32 and FP64. */
+double orc_u01(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* Standard normals for one (sample, point, sweep): dims 4j..4j+3 come from the
+ * Philox block with counter (sample, j, point, sweep) and key
+ * (seed_lo, seed_hi ^ instance).  Box-Muller on (u0,u1) gives dims 4j, 4j+1
+ * (radius from u0, angle from u1); (u2,u3) give dims 4j+2, 4j+3. */
+void orc_normals(int n, uint64_t seed, uint32_t instance, uint32_t sample,
+                 uint32_t point, uint32_t sweep, double *z)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance};
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int j = 0; 4 * j < n; ++j) {
+        uint32_t ctr[4] = {sample, (uint32_t)j, point, sweep};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        double u[4];
+        for (int q = 0; q < 4; ++q) u[q] = orc_u01(r[q]);
+        double ra = sqrt(-2.0 * log(u[0]));
+        double rb = sqrt(-2.0 * log(u[2]));
+        double zz[4] = {ra * cos(two_pi * u[1]), ra * sin(two_pi * u[1]),
+                        rb * cos(two_pi * u[3]), rb * sin(two_pi * u[3])};
+        for (int q = 0; q < 4 && 4 * j + q < n; ++q) z[4 * j + q] = zz[q];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Games: target l (signed distance), its gradient, and the closed-form
+ * Hamiltonian H(x,p) = max_u min_d <p, f(x,u,d)>. */
+
+/* Flock auxiliary data: per agent, k neighbour positions (3 each) followed by
+ * the neighbours' circular-mean heading.  Unused by the other games. */
+typedef struct {
+    const double *nbr;  /* [M][k*3] */
+    const double *psibar; /* [M] */
+} orc_aux;
+
+static double quad_form(const orc_problem *P, const double *y)
+{
+    int n = P->n;
+    double r = P->d;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            r += 0.5 * (y[a] - P->x0[a]) * P->A[a * n + b] * (y[b] - P->x0[b]);
+    return r;
+}
+
+double orc_ell(const orc_problem *P, const double *y, const double *nbr)
+{
+    switch (P->game) {
+    case ORC_DUBINS3:
+        return sqrt(y[0] * y[0] + y[1] * y[1]) - P->radius;
+    case ORC_ROCKETS6: {
+        double dx = y[0] - y[2], dz = y[1] - y[3];
+        return sqrt(dx * dx + dz * dz) - P->radius;
+    }
+    case ORC_ROCKETS45: {
+        /* agents i = 0..14 with state (x_i, z_i, theta_i); agent 14 evades */
+        double best = INFINITY;
+        for (int i = 0; i < 14; ++i) {
+            double dx = y[3 * i] - y[42], dz = y[3 * i + 1] - y[43];
+            double dist = sqrt(dx * dx + dz * dz);
+            if (dist < best) best = dist;
+        }
+        return best - P->radius;
+    }
+    case ORC_FLOCK4: {
+        double best = INFINITY;
+        for (int j = 0; j < P->flock_k; ++j) {
+            double dx = y[0] - nbr[3 * j], dy = y[1] - nbr[3 * j + 1], dz = y[2] - nbr[3 * j + 2];
+            double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            if (dist < best) best = dist;
+        }
+        return best - P->radius;
+    }
+    case ORC_TEST_QUADRATIC:
+    case ORC_TEST_ZERO_H:
+        return quad_form(P, y);
+    }
+    return NAN;
+}
+
+/* Analytic gradient of l, 0 where it is undefined (the ridge of a distance). */
+void orc_grad_ell(const orc_problem *P, const double *x, const double *nbr, double *g)
+{
+    int n = P->n;
+    for (int a = 0; a < n; ++a) g[a] = 0.0;
+    switch (P->game) {
+    case ORC_DUBINS3: {
+        double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        if (rho > 0) { g[0] = x[0] / rho; g[1] = x[1] / rho; }
+        break;
+    }
+    case ORC_ROCKETS6: {
+        double dx = x[0] - x[2], dz = x[1] - x[3];
+        double rho = sqrt(dx * dx + dz * dz);
+        if (rho > 0) { g[0] = dx / rho; g[1] = dz / rho; g[2] = -dx / rho; g[3] = -dz / rho; }
+        break;
+    }
+    case ORC_ROCKETS45: {
+        int arg = -1; double best = INFINITY;
+        for (int i = 0; i < 14; ++i) {
+            double dx = x[3 * i] - x[42], dz = x[3 * i + 1] - x[43];
+            double dist = sqrt(dx * dx + dz * dz);
+            if (dist < best) { best = dist; arg = i; }
+        }
+        if (arg >= 0 && best > 0) {
+            double dx = x[3 * arg] - x[42], dz = x[3 * arg + 1] - x[43];
+            g[3 * arg] = dx / best; g[3 * arg + 1] = dz / best;
+            g[42] = -dx / best; g[43] = -dz / best;
+        }
+        break;
+    }
+    case ORC_FLOCK4: {
+        int arg = -1; double best = INFINITY;
+        for (int j = 0; j < P->flock_k; ++j) {
+            double dx = x[0] - nbr[3 * j], dy = x[1] - nbr[3 * j + 1], dz = x[2] - nbr[3 * j + 2];
+            double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            if (dist < best) { best = dist; arg = j; }
+        }
+        if (arg >= 0 && best > 0)
+            for (int a = 0; a < 3; ++a) g[a] = (x[a] - nbr[3 * arg + a]) / best;
+        break;
+    }
+    case ORC_TEST_QUADRATIC:
+    case ORC_TEST_ZERO_H:
+        for (int a = 0; a < n; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < n; ++b) s += P->A[a * n + b] * (x[b] - P->x0[b]);
+            g[a] = s;
+        }
+        break;
+    }
+}
+
+/* wrap an angle difference into (-pi, pi] */
+static double wrap_angle(double a)
+{
+    const double pi = 3.14159265358979323846;
+    double r = fmod(a + pi, 2.0 * pi);
+    if (r <= 0) r += 2.0 * pi;
+    return r - pi;
+}
+
+double orc_hamiltonian(const orc_problem *P, const double *x, const double *p, double psibar)
+{
+    switch (P->game) {
+    case ORC_DUBINS3:
+        /* x1' = -1 + cos x3 + u x2, x2' = sin x3 - u x1, x3' = d - u; u evader (max), d pursuer (min) */
+        return p[0] * (cos(x[2]) - 1.0) + p[1] * sin(x[2])
+             + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
+    case ORC_ROCKETS6:
+        /* (xA,zA,xB,zB,thA,thB); A evader turn rate u (max), B pursuer turn rate d (min) */
+        return P->speed[0] * (p[0] * cos(x[4]) + p[1] * sin(x[4]))
+             + P->speed[1] * (p[2] * cos(x[5]) + p[3] * sin(x[5]))
+             + fabs(p[4]) - fabs(p[5]);
+    case ORC_ROCKETS45: {
+        double h = 0.0;
+        for (int i = 0; i < 15; ++i)
+            h += P->speed[i] * (p[3 * i] * cos(x[3 * i + 2]) + p[3 * i + 1] * sin(x[3 * i + 2]));
+        h += fabs(p[44]);
+        for (int i = 0; i < 14; ++i) h -= fabs(p[3 * i + 2]);
+        return h;
+    }
+    case ORC_FLOCK4:
+        /* (px,py,pz,psi): p' = (v cos psi, v sin psi, u_z), psi' = wrap(psibar - psi) + d;
+           the bird controls u_z (max), the attack disturbance d (min) */
+        return P->speed[0] * (p[0] * cos(x[3]) + p[1] * sin(x[3])) + fabs(p[2])
+             + p[3] * wrap_angle(psibar - x[3]) - fabs(p[3]);
+    case ORC_TEST_QUADRATIC: {
+        double s = 0.0;
+        for (int a = 0; a < P->n; ++a) s += p[a] * p[a];
+        return P->h_sign * 0.5 * s;
+    }
+    case ORC_TEST_ZERO_H:
+        return 0.0;
+    }
+    return NAN;
+}
+
+/* Coefficient-update map Gamma of Theorem 2.8 with the regularised denominator
+ * of Lemma 2.7 and the sign-keeping clip of Remark 2.8 (sign(0) taken as +). */
+double orc_coef(const orc_problem *P, const double *x, const double *p, double psibar)
+{
+    double h = orc_hamiltonian(P, x, p, psibar);
+    double pp = 0.0;
+    for (int a = 0; a < P->n; ++a) pp += p[a] * p[a];
+    double c = (2.0 / P->delta) * h / (pp + P->eta);
+    double mag = fabs(c);
+    if (!(mag >= P->c_min)) mag = P->c_min; /* also maps NaN to c_min */
+    if (mag > P->c_max) mag = P->c_max;
+    return (c < 0.0) ? -mag : mag;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One frozen-coefficient heat-kernel solve at one evaluation state.
+ *   samples  y_i = x + theta + sqrt(delta t) z_i,  z_i ~ N(0,I)  (theta = 0 untilted)
+ *   log-weights  lw_i = -c l(y_i) + (|theta|^2 - 2<y_i - x, theta>)/(2 sigma^2)
+ *   v  = -(1/c) log( (1/N) sum_i exp(lw_i) )              (Cor. B.4 / B.6)
+ *   Dv = (x - sum_i y_i w_i / sum_i w_i) / (t delta c)     (Cor. B.5 / B.6)
+ *   ESS = (sum w)^2 / sum w^2                              (Section 2.4)
+ * Two passes: the first finds max lw (log-sum-exp shift), the second regenerates
+ * the same samples and accumulates. */
+static void solve_point(const orc_problem *P, const double *x, double c, const double *theta,
+                        const double *nbr, int64_t N, uint32_t point, uint32_t sweep,
+                        double *lw, double *v_out, double *p_out, double *ess_out)
+{
+    int n = P->n;
+    double sigma2 = P->delta * P->T;
+    double sigma = sqrt(sigma2);
+    double z[ORC_MAXN], y[ORC_MAXN];
+    double th2 = 0.0;
+    for (int a = 0; a < n; ++a) th2 += theta[a] * theta[a];
+
+    double mx = -INFINITY;
+    for (int64_t i = 0; i < N; ++i) {
+        orc_normals(n, P->seed, P->instance, (uint32_t)i, point, sweep, z);
+        double dot = 0.0;
+        for (int a = 0; a < n; ++a) {
+            y[a] = x[a] + theta[a] + sigma * z[a];
+            dot += (y[a] - x[a]) * theta[a];
+        }
+        lw[i] = -c * orc_ell(P, y, nbr) + (th2 - 2.0 * dot) / (2.0 * sigma2);
+        if (lw[i] > mx) mx = lw[i];
+    }
+    double sw = 0.0, sw2 = 0.0, swy[ORC_MAXN];
+    for (int a = 0; a < n; ++a) swy[a] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        orc_normals(n, P->seed, P->instance, (uint32_t)i, point, sweep, z);
+        double w = exp(lw[i] - mx);
+        sw += w;
+        sw2 += w * w;
+        for (int a = 0; a < n; ++a) swy[a] += w * (x[a] + theta[a] + sigma * z[a]);
+    }
+    *v_out = -(mx + log(sw / (double)N)) / c;
+    for (int a = 0; a < n; ++a) p_out[a] = (x[a] - swy[a] / sw) / (P->T * P->delta * c);
+    *ess_out = sw * sw / sw2;
+}
+
+/* One sweep of the heat-kernel map Phi at M states for given frozen c (and tilt theta,
+ * NULL for none).  x, theta, p are [M][n] row-major; nbr/psibar only for the flock. */
+int orc_sweep(const orc_problem *P, int64_t M, const double *x, const double *c,
+              const double *theta, const double *nbr, int64_t N, uint32_t sweep,
+              double *v, double *p, double *ess)
+{
+    int n = P->n;
+    if (n < 1 || n > ORC_MAXN || N < 1) return 1;
+    int failed = 0;
+#pragma omp parallel
+    {
+        double *lw = (double *)malloc(sizeof(double) * (size_t)N);
+        double zero[ORC_MAXN];
+        for (int a = 0; a < ORC_MAXN; ++a) zero[a] = 0.0;
+        if (!lw) {
+#pragma omp atomic write
+            failed = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t m = 0; m < M; ++m) {
+                const double *th = theta ? theta + m * n : zero;
+                const double *nb = nbr ? nbr + m * 3 * P->flock_k : NULL;
+                solve_point(P, x + m * n, c[m], th, nb, N, (uint32_t)m, sweep, lw,
+                            v + m, p + m * n, ess + m);
+            }
+        }
+        free(lw);
+    }
+    return failed ? 2 : 0;
+}
+
+/* Initial iterate (Algorithm 1, "Fix"): v0 = g(x), p0 = Dg(x), c0 = Gamma(p0). */
+void orc_init(const orc_problem *P, int64_t M, const double *x, const double *nbr,
+              const double *psibar, double *v0, double *p0, double *c0)
+{
+    int n = P->n;
+    for (int64_t m = 0; m < M; ++m) {
+        const double *nb = nbr ? nbr + m * 3 * P->flock_k : NULL;
+        double pb = psibar ? psibar[m] : 0.0;
+        v0[m] = orc_ell(P, x + m * n, nb);
+        orc_grad_ell(P, x + m * n, nb, p0 + m * n);
+        c0[m] = orc_coef(P, x + m * n, p0 + m * n, pb);
+    }
+}
+
+/* Relative L2 change ||v1 - v0|| / ||v0|| and sup-norm change (Algorithm 1, last step). */
+void orc_residual(int64_t M, const double *v_old, const double *v_new, double *rel, double *sup)
+{
+    double num = 0.0, den = 0.0, mx = 0.0;
+    for (int64_t m = 0; m < M; ++m) {
+        double dv = v_new[m] - v_old[m];
+        num += dv * dv;
+        den += v_old[m] * v_old[m];
+        if (fabs(dv) > mx) mx = fabs(dv);
+    }
+    *rel = sqrt(num) / sqrt(den);
+    *sup = mx;
+}
+
+/* Algorithm 1 for K sweeps starting at sweep index k0 from the state (v, p, c).
+ * With tilt, sweep k uses theta = -sigma^2 c^(k) p^(k) (Eq. tilt_shift).
+ * v_hist is [K+1][M] (row 0 = incoming v); p and c are updated in place;
+ * resid/sup get K entries; ess gets the last sweep's ESS. */
+int orc_picard(const orc_problem *P, int64_t M, const double *x, const double *nbr,
+               const double *psibar, int64_t N, int K, uint32_t k0,
+               double *v_hist, double *p, double *c, double *resid, double *sup, double *ess)
+{
+    int n = P->n;
+    double sigma2 = P->delta * P->T;
+    double *theta = NULL;
+    if (P->tilt) {
+        theta = (double *)malloc(sizeof(double) * (size_t)(M * n));
+        if (!theta) return 2;
+    }
+    for (int k = 0; k < K; ++k) {
+        double *v_old = v_hist + (int64_t)k * M;
+        double *v_new = v_hist + (int64_t)(k + 1) * M;
+        if (theta)
+            for (int64_t m = 0; m < M; ++m)
+                for (int a = 0; a < n; ++a) theta[m * n + a] = -sigma2 * c[m] * p[m * n + a];
+        int rc = orc_sweep(P, M, x, c, theta, nbr, N, k0 + (uint32_t)k, v_new, p, ess);
+        if (rc) { free(theta); return rc; }
+        for (int64_t m = 0; m < M; ++m)
+            c[m] = orc_coef(P, x + m * n, p + m * n, psibar ? psibar[m] : 0.0);
+        orc_residual(M, v_old, v_new, resid + k, sup + k);
+    }
+    free(theta);
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,146 @@
+"""Pins for the oracle's counter-based sampler (Philox4x32-10, uniforms, Box-Muller).
+
+The Philox stream is checked against an independent implementation (Triton's Philox in
+its CPU interpreter, run in a subprocess); the uniform map and the normals are checked
+against exact invariants and distribution tests.
+"""
+import json
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _random_ctr_key(k, seed=7):
+    r = np.random.default_rng(seed)
+    ctr = r.integers(0, 2**32, size=(k, 4), dtype=np.uint64).astype(np.uint32)
+    key = r.integers(0, 2**32, size=(k, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0; key[0] = 0
+    ctr[1] = 0xFFFFFFFF; key[1] = 0xFFFFFFFF
+    return ctr, key
+
+
+_TRITON_SCRIPT = textwrap.dedent("""
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def blocks(c_ptr, out_ptr, seed, B: tl.constexpr):
+        i = tl.arange(0, B)
+        c0 = tl.load(c_ptr + 4 * i + 0)
+        c1 = tl.load(c_ptr + 4 * i + 1)
+        c2 = tl.load(c_ptr + 4 * i + 2)
+        c3 = tl.load(c_ptr + 4 * i + 3)
+        a, b, c, d = tl.random.philox(seed, c0, c1, c2, c3, 10)
+        tl.store(out_ptr + 4 * i + 0, a)
+        tl.store(out_ptr + 4 * i + 1, b)
+        tl.store(out_ptr + 4 * i + 2, c)
+        tl.store(out_ptr + 4 * i + 3, d)
+
+    req = json.loads(sys.stdin.read())
+    res = []
+    for ctr, key in zip(req["ctr"], req["key"]):
+        seed = (key[1] << 32) | key[0]
+        c = torch.tensor(np.array([ctr], dtype=np.uint32).view(np.int32))
+        out = torch.zeros(4, dtype=torch.int32)
+        blocks[(1,)](c, out, seed, B=1)
+        res.append(out.numpy().view(np.uint32).tolist())
+    print(json.dumps(res))
+""")
+
+
+def test_philox_matches_independent_implementation():
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    ctr, key = _random_ctr_key(24)
+    req = json.dumps({"ctr": ctr.tolist(), "key": key.tolist()})
+    env = dict(os.environ, TRITON_INTERPRET="1", CUDA_VISIBLE_DEVICES="")
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=req,
+                          capture_output=True, text=True, timeout=600, env=env)
+    if proc.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + proc.stderr[-300:])
+    ref = np.array(json.loads(proc.stdout.strip().splitlines()[-1]), dtype=np.uint32)
+    got = oracle.philox4x32_10(ctr, key)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_philox_counter_sensitivity():
+    """Every counter word and key word changes the block (avalanche sanity)."""
+    base_c = np.array([[1, 2, 3, 4]], dtype=np.uint32)
+    base_k = np.array([[5, 6]], dtype=np.uint32)
+    ref = oracle.philox4x32_10(base_c, base_k)[0]
+    for w in range(4):
+        c = base_c.copy(); c[0, w] ^= 1
+        out = oracle.philox4x32_10(c, base_k)[0]
+        bits = sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(out, ref))
+        assert 40 < bits < 88
+    for w in range(2):
+        k = base_k.copy(); k[0, w] ^= 1
+        out = oracle.philox4x32_10(base_c, k)[0]
+        bits = sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(out, ref))
+        assert 40 < bits < 88
+
+
+def test_uniform_map_exact_and_symmetric():
+    xs = [0, 1, 511, 512, 2**31, 2**32 - 1, 0x12345678]
+    for x in xs:
+        u = oracle.u01(x)
+        assert 0.0 < u < 1.0
+        # 23-bit level plus half a step, exact in binary32
+        assert np.float32(u) == u
+        assert u * 2**23 == (x >> 9) + 0.5
+        # reflection x -> ~x maps u -> 1 - u exactly
+        assert oracle.u01(x) + oracle.u01((~x) & 0xFFFFFFFF) == 1.0
+    assert oracle.u01(0) == 2.0**-24
+    assert oracle.u01(2**32 - 1) == 1.0 - 2.0**-24
+
+
+def test_box_muller_pair_structure():
+    """Radius of pair (z_4j, z_4j+1) comes from u0, its angle from u1 (likewise u2, u3)."""
+    seed, inst, sample, point, sweep = 0x1234_5678_9ABC, 3, 17, 5, 2
+    n = 8
+    z = oracle.normals(n, seed, inst, sample, point, sweep)
+    key = np.array([[seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ inst]], dtype=np.uint32)
+    for j in range(2):
+        blk = oracle.philox4x32_10(np.array([[sample, j, point, sweep]], dtype=np.uint32), key)[0]
+        u = [oracle.u01(int(b)) for b in blk]
+        for q in (0, 2):
+            za, zb = z[4 * j + q], z[4 * j + q + 1]
+            np.testing.assert_allclose(za * za + zb * zb, -2.0 * np.log(u[q]), rtol=1e-12)
+            ang = np.arctan2(zb, za) % (2 * np.pi)
+            np.testing.assert_allclose(ang, (2 * np.pi * u[q + 1]) % (2 * np.pi), atol=1e-9)
+
+
+def test_normals_distribution():
+    n = 6
+    Z = np.array([oracle.normals(n, 0, 0, i, 3, 1) for i in range(40000)])
+    # mean, variance, no cross-correlation, Gaussian shape
+    assert np.all(np.abs(Z.mean(0)) < 5 / np.sqrt(len(Z)))
+    np.testing.assert_allclose(Z.var(0), 1.0, atol=0.03)
+    C = np.corrcoef(Z.T)
+    assert np.max(np.abs(C - np.eye(n))) < 0.03
+    for d in range(n):
+        assert stats.kstest(Z[:, d], "norm").pvalue > 1e-3
+    # different points / sweeps draw different samples
+    a = oracle.normals(n, 0, 0, 0, 0, 0)
+    assert not np.allclose(a, oracle.normals(n, 0, 0, 0, 1, 0))
+    assert not np.allclose(a, oracle.normals(n, 0, 0, 0, 0, 1))
+    assert not np.allclose(a, oracle.normals(n, 0, 1, 0, 0, 0))
+    # truncation: |z| <= sqrt(-2 ln 2^-24)
+    assert np.abs(Z).max() <= np.sqrt(-2 * np.log(2.0**-24)) + 1e-12
+
+
+def test_normals_prefix_consistency():
+    """The first dims do not depend on how many dims are requested."""
+    a = oracle.normals(45, 9, 0, 11, 22, 3)
+    b = oracle.normals(6, 9, 0, 11, 22, 3)
+    np.testing.assert_array_equal(a[:6], b)
