@@ -1,0 +1,291 @@
+"""Benchmark: point-samples per second of the frozen-coefficient Picard sweep on GB300.
+
+One step = one full Picard solve (Algorithm 1: initial iterate + K sweeps + residuals) of
+the two-rocket 6-D workload: 65,536 states uniform in [-3,3]^4 x [-pi,pi]^2, N = 65,536
+samples per state and sweep, K = 20 sweeps, nu = 0.05 (delta = 0.1), T = 2.
+metric value = M * N * K / (device time of the step); the inputs are resident in HBM
+before the step starts.  e2e repeats the measurement through hjg_value_grad with pinned
+host buffers (state upload and value/gradient download inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on a bounded
+sample of the same workload on the host cores.  Multi-GPU (torchrun): every rank solves
+its own independent instance of the workload (weak scaling, no collective on the data
+path); rank 0 prints the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hjg_inputs  # noqa: E402
+
+METRIC = "point-samples/s per Picard sweep (v+grad v)"
+UNIT = "point-samples/s"
+W = hjg_inputs.ROCKETS6
+
+# Algorithmic MUFU operations per point-sample of the 6-D sweep: three Box-Muller pairs
+# (log2, sqrt, sin, cos each), one sqrt in the target distance, one exp2 weight.
+MUFU_PER_SAMPLE = {"rockets6": 3 * 4 + 1 + 1, "dubins3": 2 + 2 + 2 + 1 + 1 + 1,
+                   "rockets45": 23 * 4 - 1 + 1 + 1}
+# MUFU (XU pipe) issue rate per SM per clock, and the GB300 unit counts and clock.
+MUFU_PER_SM_CLK = 16
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def flush_l2(buf):
+    buf.fill_(1.0)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2605_18566_gb300 import Solver
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    x_np = hjg_inputs.points(W, seed=W.seed + rank)
+    x = torch.from_numpy(x_np).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    solver = Solver(W.game, W.nu, W.T, W.N, W.K, radius=W.radius, seed=0, instance=rank,
+                    stream=stream)
+    l2 = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step():
+        solver.set_points(x)
+        solver.picard_sweep(W.K, residuals=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush_l2(l2)
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # sweep-kernel duration alone: the library brackets the sweep launch with its own CUDA
+    # events on the launching stream and reports it when residuals are read back
+    kern_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(max(3, min(args.steps, 5))):
+            solver.set_points(x)
+            solver.picard_sweep(W.K, residuals=True)
+            kern_ms.append(solver.diagnostics()["last_ms"])
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- end to end through the public API with pinned host buffers
+    x_host = torch.from_numpy(x_np).pin_memory()
+    v_host = torch.empty(W.M, dtype=torch.float64).pin_memory()
+    g_host = torch.empty(W.M, W.n, dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        solver.value_grad(x_host, v_out=v_host, grad_out=g_host)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            solver.value_grad(x_host, v_out=v_host, grad_out=g_host)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    solver.close()
+
+    samples_per_step = W.M * W.N * W.K
+    value = world * samples_per_step * args.steps / (total_ms / 1e3)
+    e2e_value = world * samples_per_step / e2e_s
+    clocks = clk.summary()
+    peaks = load_peaks()
+    mufu = MUFU_PER_SAMPLE[W.game]
+    kern_s = statistics.median(kern_ms) / 1e3
+    achieved = samples_per_step * mufu / kern_s / 1e9          # G MUFU-op/s
+    peak = MUFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e9        # G MUFU-op/s at max clock
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 combine/log/residual)",
+        "data": "synthetic (seeded uniform states)",
+        "config": {"workload": "rockets6_uniform: 6-D two-rocket game, M=65536 states in "
+                               "[-3,3]^4x[-pi,pi]^2, N=65536 samples/state/sweep, K=20 sweeps, "
+                               "nu=0.05, T=2",
+                   "M": W.M, "N": W.N, "K": W.K, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(x_np.nbytes),
+                "d2h_bytes_per_step": int(W.M * 8 + W.M * W.n * 4 + W.K * 8)},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "pipe": "MUFU (XU)", "achieved": achieved, "peak": peak,
+                     "unit": "GMUFU-op/s", "frac": achieved / peak, "traffic": None,
+                     "ops_per_point_sample": mufu,
+                     "kernel_ms_per_step": statistics.median(kern_ms),
+                     "peak_basis": "16 MUFU ops/clk/SM x 152 SMs x 2070 MHz"},
+        "clocks": clocks,
+        "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
+    }
+    return out
+
+
+def run_cpu_baseline(seconds_target=12.0, rank=0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload's states."""
+    import oracle
+    x = hjg_inputs.points(W)
+    P = oracle.make_problem(W.game, W.n, W.delta, W.T, radius=W.radius, seed=0)
+    # calibrate on a tiny sample, then size the timed sample to about seconds_target
+    t0 = time.perf_counter()
+    probe = 8
+    oracle.picard(P, x[:probe].astype(np.float64), W.N, 1)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_state_sweep = dt / probe
+    threads = oracle.num_threads()
+    m = int(max(threads, min(W.M, seconds_target / (per_state_sweep * W.K) * threads)))
+    m = max(threads, (m // threads) * threads)
+    idx = hjg_inputs.subset_indices(W.M, m, seed=5)
+    t0 = time.perf_counter()
+    oracle.picard(P, x[idx].astype(np.float64), W.N, W.K, idx=idx)
+    el = time.perf_counter() - t0
+    return {"value": m * W.N * W.K / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d states (seeded subset), full N=%d and K=%d, %.1f s"
+                      % (m, W.M, W.N, W.K, el)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        runs = []
+        for i in range(args.warmup + args.steps):
+            r = run_cpu_baseline(seconds_target=6.0)
+            if i >= args.warmup:
+                runs.append(r)
+        val = statistics.median(r["value"] for r in runs)
+        out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic (seeded uniform states)",
+               "config": {"workload": "rockets6_uniform (bounded CPU sample per step)",
+                          "M": W.M, "N": W.N, "K": W.K},
+               "cpu_baseline": {"value": val, "unit": UNIT, "cores": runs[0]["cores"],
+                                "kind": "oracle", "sample": runs[0]["sample"]},
+               "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = run_cpu_baseline()
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * hjg.h -- C ABI of libhjg.so, a GB300 (sm_103a) implementation of the HJ-Gauss
+ * frozen-coefficient Picard sweep (arXiv 2605.18566).
+ *
+ * The library solves the viscous Hamilton-Jacobi initial-value problem
+ *     v_t + H(x, Dv) = (delta/2) Lap v,   v(0, x) = l(x)            (Eq. HJ-Visc)
+ * at M independent evaluation states x_m by Algorithm 1 of the paper:
+ *     v^(0) = l,  c^(0) = Gamma(Dl);  for k = 0, 1, ...:
+ *         freeze c^(k); phi = E_{y ~ N(x, delta t I)}[exp(-c^(k) l(y))]       (Prop. 2.1)
+ *         v^(k+1) = -(1/c^(k)) log phi                                        (Lemma 2.2)
+ *         Dv^(k+1) = (x - E[y e^{-c l}] / E[e^{-c l}]) / (t delta c^(k))       (Cor. 2.3)
+ *         c^(k+1) = (2/delta) H(x, Dv^(k+1)) / (|Dv^(k+1)|^2 + eta)          (Eq. coeff_frozen,
+ *                   |c| clipped to [c_min, c_max], sign kept                   Lemma 2.7, Rem. 2.8)
+ *         residual_k = ||v^(k+1) - v^(k)||_2 / ||v^(k)||_2                     (Algorithm 1)
+ * with N Monte-Carlo samples per state and sweep, estimated by the log-sum-exp form
+ * (Cor. B.4), optionally under the tilted proposal theta = -delta t c^(k) Dv^(k)
+ * (Eq. tilt_shift, Cor. B.6).  Viscosity is given as nu with delta = 2 nu, so samples
+ * are y = x + sqrt(2 nu t) z.
+ *
+ * Samples are never stored: sample i of state m in sweep k, dims 4j..4j+3, come from
+ * Philox4x32-10 with counter (i, j, m, k) and key (seed_lo, seed_hi ^ instance),
+ * mapped to uniforms u = ((r >> 9) + 0.5) 2^-23 and Box-Muller normals (radius from
+ * u0 / u2, angle from u1 / u3).
+ *
+ * Conventions for every entry point:
+ *   - Return an hjg_status; no call aborts or exits.  hjg_last_error() gives a message.
+ *   - "on_device" = 1: the pointer is CUDA device memory of the current device;
+ *     0: ordinary (pageable or pinned) host memory.  The caller owns all buffers it
+ *     passes; the context owns its internal state.
+ *   - "stream" is a cudaStream_t (NULL = the context's stream, default the legacy
+ *     stream).  Calls that return host results synchronise that stream.
+ *   - Arrays of states are row-major [M][ld] FP32 with ld >= n.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef HJG_H
+#define HJG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HJG_OK = 0,
+    HJG_EINVAL = 1,        /* bad argument (size, pointer, option) */
+    HJG_ENOMEM = 2,        /* device or host allocation failed */
+    HJG_ECUDA = 3,         /* a CUDA call or kernel launch failed */
+    HJG_ENONFINITE = 4,    /* results contain non-finite values (results still written) */
+    HJG_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    HJG_ENOTCONVERGED = 6, /* tolerance not reached within the sweep budget (results written) */
+    HJG_EUNSUPPORTED = 7   /* game / dimension / option not available */
+} hjg_status;
+
+/* Games (dynamics f, closed-form Hamiltonian H(x,p) = max_u min_d <p, f>, target l). */
+typedef enum {
+    HJG_DUBINS3 = 1,    /* Appendix D.2 relative Dubins game, unit speeds and turn rates:
+                           x1' = -1 + cos x3 + u x2, x2' = sin x3 - u x1, x3' = d - u;
+                           l = |(x1,x2)| - radius.  n = 3. */
+    HJG_ROCKETS6 = 2,   /* two planar rockets (xA,zA,xB,zB,thA,thB), per-agent dynamics of
+                           Eq. multiagent_dynamics, A evades (turn rate u), B pursues (d);
+                           l = |(xA,zA) - (xB,zB)| - radius.  n = 6. */
+    HJG_ROCKETS45 = 3,  /* Section 3.2: 15 agents (x_i, z_i, th_i), agent 15 evades;
+                           l = min_{i<=14} |pos_i - pos_15| - radius.  n = 45. */
+    HJG_FLOCK4 = 4,     /* reserved: murmuration agent game (Appendix D.5) */
+    HJG_TEST_QUADRATIC = 100, /* H = h_sign |p|^2 / 2, l = (y-x0)^T A (y-x0)/2 + d; n <= 8 */
+    HJG_TEST_ZERO_H = 101     /* H = 0 (pure heat equation), same quadratic l; n <= 8 */
+} hjg_game;
+
+typedef struct {
+    int32_t game;        /* hjg_game */
+    int32_t n;           /* state dimension; must equal the game's (3, 6, 45) or 1..8 for tests */
+    double speed[16];    /* forward speeds per agent (ROCKETS6: [0]=A, [1]=B; ROCKETS45: a_1..a_15);
+                            0 entries are read as 1 */
+    double h_sign;       /* TEST_QUADRATIC only: +1 or -1 */
+} hjg_dynamics;
+
+typedef struct {
+    double radius;       /* capture radius of the signed-distance target */
+    double A[64];        /* quadratic test target, row-major n x n, symmetric */
+    double x0[8];
+    double d;
+} hjg_target;
+
+typedef struct {
+    int64_t N;           /* samples per state and sweep (>= 1) */
+    int32_t K;           /* sweeps run by hjg_value_grad */
+    int32_t tilt;        /* 1: tilted proposal theta = -delta t c Dv (Eq. tilt_shift) */
+    double eps;          /* hjg_value_grad stops after the sweep whose residual < eps (0: never) */
+    double eta;          /* Lemma 2.7 regulariser; < 0 selects 1e-6 */
+    double c_min, c_max; /* |c| clip; <= 0 selects 1e-2/delta and 1e2/delta */
+    uint64_t seed;       /* Philox key (low word, high word ^ instance) */
+    uint32_t instance;
+    int32_t block_threads; /* 0: tuned default; else 128, 256 or 512 */
+    int32_t grid_blocks;   /* 0: tuned default (persistent grid over the SMs) */
+    int32_t reserved[7];
+} hjg_options;
+
+typedef struct {
+    int64_t M;                /* states currently loaded */
+    uint32_t next_sweep;      /* global index of the next sweep (Philox counter word 3) */
+    int64_t nonfinite;        /* states with non-finite v or Dv in the last call */
+    int64_t clipped;          /* states whose |c| hit a clip bound in the last sweep */
+    double ess_min, ess_median; /* effective sample size of the last sweep (Section 2.4) */
+    double last_ms;           /* device time of the last hjg_picard_sweep / hjg_value_grad */
+    int32_t block_threads, grid_blocks;
+} hjg_diag;
+
+typedef struct hjg_ctx hjg_ctx;
+
+/* Create a solver for one game instance (Eq. HJ-Visc with delta = 2 nu, evaluated at
+ * t = T).  Allocates nothing on the device until points are set.  *out receives the
+ * context; free it with hjg_destroy.  EINVAL on inconsistent game/n/options,
+ * EUNSUPPORTED for a reserved game. */
+hjg_status hjg_create(const hjg_dynamics *dyn, const hjg_target *target, double nu, double T,
+                      const hjg_options *opt, hjg_ctx **out);
+
+/* Load M evaluation states (row-major [M][ld] FP32, host or device) and form the initial
+ * iterate of Algorithm 1: v^(0) = l(x), p^(0) = Dl(x) (0 where undefined), c^(0) =
+ * Gamma(p^(0)).  Resets the sweep counter to 0.  Device buffers grow as needed. */
+hjg_status hjg_set_points(hjg_ctx *ctx, const float *pts, int64_t M, int64_t ld, int on_device,
+                          void *stream);
+
+/* Run n_sweeps Picard sweeps (Algorithm 1 loop body) on the loaded states, continuing the
+ * global sweep counter.  residual_out / supnorm_out: host arrays of n_sweeps doubles
+ * (relative L2 change and sup-norm change per sweep) or NULL (then the call does not
+ * synchronise).  ENONFINITE if any state produced a non-finite v or Dv. */
+hjg_status hjg_picard_sweep(hjg_ctx *ctx, int n_sweeps, double *residual_out, double *supnorm_out);
+
+/* Copy the current iterate out: v [M] FP64, p = Dv [M][ldp] FP32, c [M] FP32 (the frozen
+ * coefficient for the next sweep), ess [M] FP32 (last sweep).  Any pointer may be NULL. */
+hjg_status hjg_get_state(hjg_ctx *ctx, double *v, float *p, int64_t ldp, float *c, float *ess,
+                         int on_device);
+
+/* Overwrite the iterate (checkpoint resume, or a warm start): any of v, p, c may be NULL
+ * (kept); next_sweep sets the global sweep counter.  Resuming with the state and counter
+ * of an earlier run reproduces it bit for bit. */
+hjg_status hjg_set_state(hjg_ctx *ctx, const double *v, const float *p, int64_t ldp,
+                         const float *c, uint32_t next_sweep, int on_device);
+
+/* v^(k) history of the last hjg_picard_sweep call: rows 0..n_sweeps, row 0 = the
+ * incoming v.  out is [(n_sweeps+1)][M] FP64. */
+hjg_status hjg_get_history(hjg_ctx *ctx, double *out, int on_device);
+
+/* hjg_set_points + up to opt.K sweeps (stopping early once residual < opt.eps > 0) +
+ * copy-out: v_out [M] FP64, grad_out [M][ldg] FP32, residual_out [K] FP64 (host; entries
+ * after an early stop are set to NaN).  Host or device buffers per on_device. */
+hjg_status hjg_value_grad(hjg_ctx *ctx, const float *pts, int64_t M, int64_t ld, int on_device,
+                          double *v_out, float *grad_out, int64_t ldg, double *residual_out,
+                          void *stream);
+
+hjg_status hjg_get_diagnostics(hjg_ctx *ctx, hjg_diag *out);
+hjg_status hjg_set_stream(hjg_ctx *ctx, void *stream);
+void hjg_destroy(hjg_ctx *ctx);
+const char *hjg_last_error(const hjg_ctx *ctx);
+const char *hjg_status_string(hjg_status s);
+
+/* ---- building blocks, exposed for bit-level tests ------------------------------ */
+
+/* Philox4x32-10 blocks on the device: ctr [count][4], key [count][2], out [count][4]
+ * uint32, all device pointers. */
+hjg_status hjg_philox_blocks(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                             int64_t count, void *stream);
+
+/* The FP32 standard normals the sweep consumes for state `point`, sweep `sweep`, samples
+ * 0..n_samples-1: out is device [n_samples][n] FP32. */
+hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point,
+                              uint32_t sweep, int64_t n_samples, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HJG_H */

@@ -74,11 +74,12 @@ def lib():
         L.orc_grad_ell.argtypes = [P(Problem), pd, pd, pd]
         L.orc_hamiltonian.argtypes = [P(Problem), pd, pd, d]; L.orc_hamiltonian.restype = d
         L.orc_coef.argtypes = [P(Problem), pd, pd, d]; L.orc_coef.restype = d
-        L.orc_sweep.argtypes = [P(Problem), i64, pd, pd, pd, pd, i64, u32, pd, pd, pd]
+        pi64 = P(C.c_int64)
+        L.orc_sweep.argtypes = [P(Problem), i64, pd, pd, pd, pd, pi64, i64, u32, pd, pd, pd]
         L.orc_sweep.restype = i32
         L.orc_init.argtypes = [P(Problem), i64, pd, pd, pd, pd, pd, pd]
         L.orc_residual.argtypes = [i64, pd, pd, pd, pd]
-        L.orc_picard.argtypes = [P(Problem), i64, pd, pd, pd, i64, i32, u32,
+        L.orc_picard.argtypes = [P(Problem), i64, pd, pd, pd, pi64, i64, i32, u32,
                                  pd, pd, pd, pd, pd, pd]
         L.orc_picard.restype = i32
         L.orc_num_threads.restype = i32
@@ -88,6 +89,13 @@ def lib():
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _idx(a):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int64))
 
 
 def _f64(a, shape=None):
@@ -186,22 +194,24 @@ def init(P, x, nbr=None, psibar=None):
     return v0, p0, c0
 
 
-def sweep(P, x, c, N, sweep_index, theta=None, nbr=None):
-    """One frozen-coefficient heat-kernel solve Phi(c) at states x: (v, p, ess)."""
+def sweep(P, x, c, N, sweep_index, theta=None, nbr=None, idx=None):
+    """One frozen-coefficient heat-kernel solve Phi(c) at states x: (v, p, ess).
+    idx: global state indices of the rows (default 0..M-1)."""
     x = _f64(x).reshape(-1, P.n)
     M = x.shape[0]
     c = _f64(c).reshape(M)
     th = _f64(theta).reshape(M, P.n) if theta is not None else None
     nb = _f64(nbr) if nbr is not None else None
     v = np.zeros(M); p = np.zeros((M, P.n)); ess = np.zeros(M)
-    rc = lib().orc_sweep(C.byref(P), M, _dp(x), _dp(c), _dp(th), _dp(nb), int(N),
+    ia, ip = _idx(idx)
+    rc = lib().orc_sweep(C.byref(P), M, _dp(x), _dp(c), _dp(th), _dp(nb), ip, int(N),
                          int(sweep_index), _dp(v), _dp(p), _dp(ess))
     if rc:
         raise RuntimeError("orc_sweep failed (%d)" % rc)
     return v, p, ess
 
 
-def picard(P, x, N, K, k0=0, state=None, nbr=None, psibar=None):
+def picard(P, x, N, K, k0=0, state=None, nbr=None, psibar=None, idx=None):
     """Algorithm 1 for K sweeps.  Returns dict with v_hist [K+1,M], p, c, resid, sup, ess.
     ``state`` = (v, p, c) to resume from; default is the initial iterate."""
     x = _f64(x).reshape(-1, P.n)
@@ -216,7 +226,8 @@ def picard(P, x, N, K, k0=0, state=None, nbr=None, psibar=None):
     p = np.ascontiguousarray(p); c = np.ascontiguousarray(c)
     nb = _f64(nbr) if nbr is not None else None
     pb = _f64(psibar) if psibar is not None else None
-    rc = lib().orc_picard(C.byref(P), M, _dp(x), _dp(nb), _dp(pb), int(N), int(K), int(k0),
+    ia, ip = _idx(idx)
+    rc = lib().orc_picard(C.byref(P), M, _dp(x), _dp(nb), _dp(pb), ip, int(N), int(K), int(k0),
                           _dp(v_hist), _dp(p), _dp(c), _dp(resid), _dp(sup), _dp(ess))
     if rc:
         raise RuntimeError("orc_picard failed (%d)" % rc)

@@ -350,10 +350,12 @@ static void solve_point(const orc_problem *P, const double *x, double c, const d
 }
 
 /* One sweep of the heat-kernel map Phi at M states for given frozen c (and tilt theta,
- * NULL for none).  x, theta, p are [M][n] row-major; nbr/psibar only for the flock. */
+ * NULL for none).  x, theta, p are [M][n] row-major; nbr/psibar only for the flock.
+ * idx (NULL: 0..M-1) gives each row's global state index, which keys its samples, so a
+ * subset of a large workload draws exactly the samples it draws in the full run. */
 int orc_sweep(const orc_problem *P, int64_t M, const double *x, const double *c,
-              const double *theta, const double *nbr, int64_t N, uint32_t sweep,
-              double *v, double *p, double *ess)
+              const double *theta, const double *nbr, const int64_t *idx, int64_t N,
+              uint32_t sweep, double *v, double *p, double *ess)
 {
     int n = P->n;
     if (n < 1 || n > ORC_MAXN || N < 1) return 1;
@@ -371,7 +373,8 @@ int orc_sweep(const orc_problem *P, int64_t M, const double *x, const double *c,
             for (int64_t m = 0; m < M; ++m) {
                 const double *th = theta ? theta + m * n : zero;
                 const double *nb = nbr ? nbr + m * 3 * P->flock_k : NULL;
-                solve_point(P, x + m * n, c[m], th, nb, N, (uint32_t)m, sweep, lw,
+                uint32_t point = (uint32_t)(idx ? idx[m] : m);
+                solve_point(P, x + m * n, c[m], th, nb, N, point, sweep, lw,
                             v + m, p + m * n, ess + m);
             }
         }
@@ -413,7 +416,7 @@ void orc_residual(int64_t M, const double *v_old, const double *v_new, double *r
  * v_hist is [K+1][M] (row 0 = incoming v); p and c are updated in place;
  * resid/sup get K entries; ess gets the last sweep's ESS. */
 int orc_picard(const orc_problem *P, int64_t M, const double *x, const double *nbr,
-               const double *psibar, int64_t N, int K, uint32_t k0,
+               const double *psibar, const int64_t *idx, int64_t N, int K, uint32_t k0,
                double *v_hist, double *p, double *c, double *resid, double *sup, double *ess)
 {
     int n = P->n;
@@ -429,7 +432,7 @@ int orc_picard(const orc_problem *P, int64_t M, const double *x, const double *n
         if (theta)
             for (int64_t m = 0; m < M; ++m)
                 for (int a = 0; a < n; ++a) theta[m * n + a] = -sigma2 * c[m] * p[m * n + a];
-        int rc = orc_sweep(P, M, x, c, theta, nbr, N, k0 + (uint32_t)k, v_new, p, ess);
+        int rc = orc_sweep(P, M, x, c, theta, nbr, idx, N, k0 + (uint32_t)k, v_new, p, ess);
         if (rc) { free(theta); return rc; }
         for (int64_t m = 0; m < M; ++m)
             c[m] = orc_coef(P, x + m * n, p + m * n, psibar ? psibar[m] : 0.0);

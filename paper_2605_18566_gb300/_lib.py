@@ -1,0 +1,96 @@
+"""ctypes binding of libhjg.so (the C ABI in include/hjg.h): structures, status codes and
+symbol signatures.  Argument marshalling only; every step of the sweep runs in the CUDA
+library.  Loading fails loudly when the library has not been built."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhjg.so")
+
+HJG_OK, HJG_EINVAL, HJG_ENOMEM, HJG_ECUDA, HJG_ENONFINITE, HJG_ETIMEOUT, \
+    HJG_ENOTCONVERGED, HJG_EUNSUPPORTED = range(8)
+
+GAMES = {"dubins3": 1, "rockets6": 2, "rockets45": 3, "flock4": 4,
+         "quadratic": 100, "zero_h": 101}
+GAME_DIMS = {"dubins3": 3, "rockets6": 6, "rockets45": 45, "flock4": 4}
+
+
+class Dynamics(C.Structure):
+    _fields_ = [("game", C.c_int32), ("n", C.c_int32), ("speed", C.c_double * 16),
+                ("h_sign", C.c_double)]
+
+
+class Target(C.Structure):
+    _fields_ = [("radius", C.c_double), ("A", C.c_double * 64), ("x0", C.c_double * 8),
+                ("d", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("tilt", C.c_int32), ("eps", C.c_double),
+                ("eta", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double),
+                ("seed", C.c_uint64), ("instance", C.c_uint32), ("block_threads", C.c_int32),
+                ("grid_blocks", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("M", C.c_int64), ("next_sweep", C.c_uint32), ("nonfinite", C.c_int64),
+                ("clipped", C.c_int64), ("ess_min", C.c_double), ("ess_median", C.c_double),
+                ("last_ms", C.c_double), ("block_threads", C.c_int32), ("grid_blocks", C.c_int32)]
+
+
+# name -> (restype, argtypes)
+_vp = C.c_void_p
+_SIGS = {
+    "hjg_create": (C.c_int, [C.POINTER(Dynamics), C.POINTER(Target), C.c_double, C.c_double,
+                             C.POINTER(Options), C.POINTER(_vp)]),
+    "hjg_set_points": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, C.c_int, _vp]),
+    "hjg_picard_sweep": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "hjg_get_state": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_int]),
+    "hjg_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, C.c_uint32, C.c_int]),
+    "hjg_get_history": (C.c_int, [_vp, _vp, C.c_int]),
+    "hjg_value_grad": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, C.c_int, _vp, _vp, C.c_int64,
+                                 _vp, _vp]),
+    "hjg_get_diagnostics": (C.c_int, [_vp, C.POINTER(Diag)]),
+    "hjg_set_stream": (C.c_int, [_vp, _vp]),
+    "hjg_destroy": (None, [_vp]),
+    "hjg_last_error": (C.c_char_p, [_vp]),
+    "hjg_status_string": (C.c_char_p, [C.c_int]),
+    "hjg_philox_blocks": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
+    "hjg_sample_normals": (C.c_int, [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                     C.c_int64, _vp, _vp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhjg.so and bind every exported symbol; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libhjg.so not found at %s: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def symbols():
+    return list(_SIGS)
+
+
+class HJGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (status %d): %s" % (status_string(status), status, msg))
+        self.status = status
+
+
+def status_string(st: int) -> str:
+    return load().hjg_status_string(st).decode()

@@ -1,0 +1,183 @@
+// games.cuh -- targets l, their gradients and closed-form Hamiltonians
+// H(x, p) = max_u min_d <p, f(x, u, d)> (Eq. sign_convention) for the games the
+// sweep supports.  Sample-level targets run in FP32 on registers; the per-state
+// quantities of the coefficient update (Eq. coeff_frozen) run in FP64.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+namespace hjg {
+
+struct GameParams {
+    int32_t game;
+    int32_t n;
+    float radius;
+    float h_sign;
+    float speed[16];
+    float A[64];      // quadratic test target (row-major n x n)
+    float x0[8];
+    float d;
+    double radius_d;
+    double h_sign_d;
+    double speed_d[16];
+    double A_d[64];
+    double x0_d[8];
+    double d_d;
+};
+
+enum GameId : int32_t {
+    kDubins3 = 1, kRockets6 = 2, kRockets45 = 3, kFlock4 = 4,
+    kTestQuadratic = 100, kTestZeroH = 101
+};
+
+// ---------------------------------------------------------------- Dubins (App. D.2)
+// x1' = -1 + cos x3 + u x2,  x2' = sin x3 - u x1,  x3' = d - u;  u evader (max), d pursuer (min)
+struct Dubins3 {
+    static constexpr int kN = 3;
+    __device__ static __forceinline__ float ell(const float* y, const GameParams& g) {
+        return sqrtf_fast(y[0] * y[0] + y[1] * y[1]) - g.radius;
+    }
+    __device__ static __forceinline__ float sqrtf_fast(float a) {
+        float r; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a)); return r;
+    }
+    __device__ static double ell_d(const double* x, const GameParams& g) {
+        return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&) {
+        const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        gr[0] = rho > 0 ? x[0] / rho : 0.0;
+        gr[1] = rho > 0 ? x[1] / rho : 0.0;
+        gr[2] = 0.0;
+    }
+    __device__ static double ham_d(const double* x, const double* p, const GameParams&) {
+        double s, c;
+        sincos(x[2], &s, &c);
+        return p[0] * (c - 1.0) + p[1] * s + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
+    }
+};
+
+// ---------------------------------------------------------------- two rockets
+// state (xA, zA, xB, zB, thA, thB); A: x' = a cos th, z' = a sin th, th' = u (max);
+// B likewise with turn rate d (min).
+struct Rockets6 {
+    static constexpr int kN = 6;
+    __device__ static __forceinline__ float ell(const float* y, const GameParams& g) {
+        const float dx = y[0] - y[2], dz = y[1] - y[3];
+        return Dubins3::sqrtf_fast(dx * dx + dz * dz) - g.radius;
+    }
+    __device__ static double ell_d(const double* x, const GameParams& g) {
+        const double dx = x[0] - x[2], dz = x[1] - x[3];
+        return sqrt(dx * dx + dz * dz) - g.radius_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&) {
+        const double dx = x[0] - x[2], dz = x[1] - x[3];
+        const double rho = sqrt(dx * dx + dz * dz);
+        const double a = rho > 0 ? dx / rho : 0.0, b = rho > 0 ? dz / rho : 0.0;
+        gr[0] = a; gr[1] = b; gr[2] = -a; gr[3] = -b; gr[4] = 0.0; gr[5] = 0.0;
+    }
+    __device__ static double ham_d(const double* x, const double* p, const GameParams& g) {
+        double sA, cA, sB, cB;
+        sincos(x[4], &sA, &cA);
+        sincos(x[5], &sB, &cB);
+        return g.speed_d[0] * (p[0] * cA + p[1] * sA) + g.speed_d[1] * (p[2] * cB + p[3] * sB)
+             + fabs(p[4]) - fabs(p[5]);
+    }
+};
+
+// ---------------------------------------------------------------- 15 rockets (Sec. 3.2)
+// agents i = 0..14 with (x_i, z_i, th_i) at dims 3i..3i+2; agent 14 evades.
+// l = min_{i < 14} |pos_i - pos_14| - r.  The per-sample target is evaluated cooperatively
+// by 4 lanes (see sweep.cu); only the per-state FP64 parts live here.
+struct Rockets45 {
+    static constexpr int kN = 45;
+    __device__ static double ell_d(const double* x, const GameParams& g) {
+        double best = INFINITY;
+        for (int i = 0; i < 14; ++i) {
+            const double dx = x[3 * i] - x[42], dz = x[3 * i + 1] - x[43];
+            best = fmin(best, sqrt(dx * dx + dz * dz));
+        }
+        return best - g.radius_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&) {
+        int arg = -1;
+        double best = INFINITY;
+        for (int i = 0; i < 14; ++i) {
+            const double dx = x[3 * i] - x[42], dz = x[3 * i + 1] - x[43];
+            const double dd = sqrt(dx * dx + dz * dz);
+            if (dd < best) { best = dd; arg = i; }
+        }
+        for (int a = 0; a < 45; ++a) gr[a] = 0.0;
+        if (arg >= 0 && best > 0) {
+            const double dx = x[3 * arg] - x[42], dz = x[3 * arg + 1] - x[43];
+            gr[3 * arg] = dx / best; gr[3 * arg + 1] = dz / best;
+            gr[42] = -dx / best; gr[43] = -dz / best;
+        }
+    }
+    __device__ static double ham_d(const double* x, const double* p, const GameParams& g) {
+        double h = 0.0;
+        for (int i = 0; i < 15; ++i) {
+            double s, c;
+            sincos(x[3 * i + 2], &s, &c);
+            h += g.speed_d[i] * (p[3 * i] * c + p[3 * i + 1] * s);
+        }
+        h += fabs(p[44]);
+        for (int i = 0; i < 14; ++i) h -= fabs(p[3 * i + 2]);
+        return h;
+    }
+};
+
+// ---------------------------------------------------------------- quadratic tests
+// H = h_sign |p|^2 / 2 (ZERO_H: H = 0), l = (y - x0)^T A (y - x0) / 2 + d.  NDIM <= 8.
+template <int NDIM, bool kZeroH>
+struct Quadratic {
+    static constexpr int kN = NDIM;
+    __device__ static __forceinline__ float ell(const float* y, const GameParams& g) {
+        float e[NDIM];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) e[a] = y[a] - g.x0[a];
+        float r = 0.0f;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            float row = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NDIM; ++b) row = fmaf(g.A[a * NDIM + b], e[b], row);
+            r = fmaf(e[a], row, r);
+        }
+        return fmaf(0.5f, r, g.d);
+    }
+    __device__ static double ell_d(const double* x, const GameParams& g) {
+        double r = 0.0;
+        for (int a = 0; a < NDIM; ++a)
+            for (int b = 0; b < NDIM; ++b)
+                r += (x[a] - g.x0_d[a]) * g.A_d[a * NDIM + b] * (x[b] - g.x0_d[b]);
+        return 0.5 * r + g.d_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams& g) {
+        for (int a = 0; a < NDIM; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < NDIM; ++b) s += g.A_d[a * NDIM + b] * (x[b] - g.x0_d[b]);
+            gr[a] = s;
+        }
+    }
+    __device__ static double ham_d(const double*, const double* p, const GameParams& g) {
+        if (kZeroH) return 0.0;
+        double s = 0.0;
+        for (int a = 0; a < NDIM; ++a) s += p[a] * p[a];
+        return g.h_sign_d * 0.5 * s;
+    }
+};
+
+// Coefficient-update map Gamma (Eq. coeff_frozen with the regulariser of Lemma 2.7 and
+// the sign-keeping clip of Remark 2.8; sign(0) = +, NaN -> c_min).
+__device__ __forceinline__ double coef_update(double h, double pp, double delta, double eta,
+                                              double c_min, double c_max, int* clipped) {
+    const double c = (2.0 / delta) * h / (pp + eta);
+    double mag = fabs(c);
+    int cl = 0;
+    if (!(mag >= c_min)) { mag = c_min; cl = 1; }
+    if (mag > c_max) { mag = c_max; cl = 1; }
+    *clipped = cl;
+    return (c < 0.0) ? -mag : mag;
+}
+
+}  // namespace hjg

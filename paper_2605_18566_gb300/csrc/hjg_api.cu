@@ -1,0 +1,519 @@
+// hjg_api.cu -- the C ABI of libhjg.so (declared in include/hjg.h): context management,
+// argument checking, host<->device staging, and the launches of the sweep, init and
+// residual kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hjg.h"
+#include "dispatch.h"
+
+using namespace hjg;
+
+struct hjg_ctx {
+    hjg_dynamics dyn;
+    hjg_target target;
+    hjg_options opt;
+    double nu = 0, T = 0, delta = 0, sigma2 = 0, eta = 0, c_min = 0, c_max = 0;
+    int n = 0, ldx = 0;
+    GameParams gp{};
+    GameKernels kern{};
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+
+    int64_t M = 0, cap = 0;
+    float* d_x = nullptr;
+    double* d_v = nullptr;
+    float* d_p = nullptr;
+    float* d_c = nullptr;
+    float* d_ess = nullptr;
+    unsigned long long* d_counters = nullptr;
+    double* d_vhist = nullptr;
+    int64_t vhist_rows = 0;   // allocated rows
+    int last_sweeps = 0;      // rows used by the last call = last_sweeps + 1
+    double* d_resid = nullptr;  // [K][2]
+    int resid_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the sweep kernel alone
+
+    uint32_t next_sweep = 0;
+    int64_t nonfinite = 0, clipped = 0;
+    double last_ms = 0;
+    int threads = 0, grid = 0;
+    std::string err;
+};
+
+namespace {
+
+hjg_status fail(hjg_ctx* ctx, hjg_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+#define HJG_CUDA(ctx, call)                                                               \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? HJG_ENOMEM : HJG_ECUDA,  \
+                        "%s: %s", #call, cudaGetErrorString(e_));                         \
+    } while (0)
+
+cudaStream_t pick_stream(hjg_ctx* ctx, void* s) {
+    return s ? (cudaStream_t)s : ctx->stream;
+}
+
+template <class T>
+hjg_status grow(hjg_ctx* ctx, T** ptr, size_t count) {
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    cudaError_t e = cudaMalloc((void**)ptr, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail(ctx, HJG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    return HJG_OK;
+}
+
+// Residual of Algorithm 1 from the value history: block k reduces rows k, k+1 over all
+// states in a fixed order (deterministic) and writes (||v_{k+1}-v_k|| / ||v_k||, max |dv|).
+__global__ void residual_kernel(const double* __restrict__ vhist, int64_t M, double* out) {
+    constexpr int T = 256;
+    __shared__ double s_num[T], s_den[T], s_sup[T];
+    const int k = blockIdx.x, tid = threadIdx.x;
+    const double* a = vhist + (int64_t)k * M;
+    const double* b = a + M;
+    double num = 0.0, den = 0.0, sup = 0.0;
+    for (int64_t m = tid; m < M; m += T) {
+        const double d = b[m] - a[m];
+        num = fma(d, d, num);
+        den = fma(a[m], a[m], den);
+        sup = fmax(sup, fabs(d));
+    }
+    s_num[tid] = num; s_den[tid] = den; s_sup[tid] = sup;
+    __syncthreads();
+    for (int w = T / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+            s_num[tid] += s_num[tid + w];
+            s_den[tid] += s_den[tid + w];
+            s_sup[tid] = fmax(s_sup[tid], s_sup[tid + w]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        out[2 * k] = sqrt(s_num[0]) / sqrt(s_den[0]);
+        out[2 * k + 1] = s_sup[0];
+    }
+}
+
+__global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
+                                     uint32_t* __restrict__ out, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint4 r = philox4x32_10(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]),
+                                  key[2 * i], key[2 * i + 1]);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+// The same normals the sweep draws (draw_normals with all four kept), sample i per thread.
+__global__ void normals_kernel(int n, uint32_t k0, uint32_t k1, uint32_t point, uint32_t sweep,
+                               int64_t ns, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    for (int q = 0; 4 * q < n; ++q) {
+        float z[4];
+        draw_normals<1, 4>((uint32_t)i, (uint32_t)q, point, sweep, k0, k1, z);
+        for (int j = 0; j < 4 && 4 * q + j < n; ++j) out[i * n + 4 * q + j] = z[j];
+    }
+}
+
+void fill_game_params(hjg_ctx* ctx) {
+    GameParams& g = ctx->gp;
+    memset(&g, 0, sizeof g);
+    g.game = ctx->dyn.game;
+    g.n = ctx->n;
+    g.radius = (float)ctx->target.radius;
+    g.radius_d = ctx->target.radius;
+    g.h_sign = (float)ctx->dyn.h_sign;
+    g.h_sign_d = ctx->dyn.h_sign;
+    for (int i = 0; i < 16; ++i) {
+        const double s = ctx->dyn.speed[i] == 0.0 ? 1.0 : ctx->dyn.speed[i];
+        g.speed[i] = (float)s;
+        g.speed_d[i] = s;
+    }
+    for (int i = 0; i < 64; ++i) { g.A[i] = (float)ctx->target.A[i]; g.A_d[i] = ctx->target.A[i]; }
+    for (int i = 0; i < 8; ++i) { g.x0[i] = (float)ctx->target.x0[i]; g.x0_d[i] = ctx->target.x0[i]; }
+    g.d = (float)ctx->target.d;
+    g.d_d = ctx->target.d;
+}
+
+hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
+    if (M <= ctx->cap) return HJG_OK;
+    hjg_status st;
+    if ((st = grow(ctx, &ctx->d_x, (size_t)M * ctx->ldx))) return st;
+    if ((st = grow(ctx, &ctx->d_v, (size_t)M))) return st;
+    if ((st = grow(ctx, &ctx->d_p, (size_t)M * ctx->ldx))) return st;
+    if ((st = grow(ctx, &ctx->d_c, (size_t)M))) return st;
+    if ((st = grow(ctx, &ctx->d_ess, (size_t)M))) return st;
+    if (ctx->d_vhist) { cudaFree(ctx->d_vhist); ctx->d_vhist = nullptr; ctx->vhist_rows = 0; }
+    ctx->cap = M;
+    return HJG_OK;
+}
+
+hjg_status ensure_history(hjg_ctx* ctx, int K) {
+    hjg_status st;
+    if (K + 1 > ctx->vhist_rows) {
+        if ((st = grow(ctx, &ctx->d_vhist, (size_t)(K + 1) * ctx->cap))) return st;
+        ctx->vhist_rows = K + 1;
+    }
+    if (K > ctx->resid_cap) {
+        if ((st = grow(ctx, &ctx->d_resid, (size_t)2 * K))) return st;
+        ctx->resid_cap = K;
+    }
+    return HJG_OK;
+}
+
+// Copy states [M][ld] (host or device) into the context's padded [M][ldx] buffer.
+hjg_status stage_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld, int on_device,
+                        cudaStream_t st) {
+    const size_t row = (size_t)ctx->n * sizeof(float);
+    if (ld == ctx->ldx) {
+        HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_x, pts, (size_t)M * ld * sizeof(float),
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+        HJG_CUDA(ctx, cudaMemcpy2DAsync(ctx->d_x, ctx->ldx * sizeof(float), pts, ld * sizeof(float), row,
+                                        (size_t)M, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        st));
+    }
+    return HJG_OK;
+}
+
+SweepArgs make_args(hjg_ctx* ctx, int K) {
+    SweepArgs A;
+    memset(&A, 0, sizeof A);
+    A.x = ctx->d_x;
+    A.p = ctx->d_p;
+    A.c = ctx->d_c;
+    A.v = ctx->d_v;
+    A.vhist = ctx->d_vhist;
+    A.ess = ctx->d_ess;
+    A.counters = ctx->d_counters;
+    A.ldx = ctx->ldx;
+    A.ldp = ctx->ldx;
+    A.M = ctx->M;
+    A.N = ctx->opt.N;
+    A.key0 = (uint32_t)ctx->opt.seed;
+    A.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.instance;
+    A.k0 = ctx->next_sweep;
+    A.K = K;
+    A.sigma_d = std::sqrt(ctx->sigma2);
+    A.sigma = (float)A.sigma_d;
+    A.sigma2_d = ctx->sigma2;
+    A.delta = ctx->delta;
+    A.eta = ctx->eta;
+    A.c_min = ctx->c_min;
+    A.c_max = ctx->c_max;
+    A.g = ctx->gp;
+    return A;
+}
+
+hjg_status choose_launch(hjg_ctx* ctx) {
+    const bool tilt = ctx->opt.tilt != 0;
+    int threads = ctx->opt.block_threads > 0 ? ctx->opt.block_threads : ctx->kern.default_threads;
+    int occ = ctx->kern.occupancy(tilt, threads);
+    if (occ <= 0)
+        return fail(ctx, HJG_EINVAL, "block_threads=%d is not available for this game", threads);
+    int64_t grid = ctx->opt.grid_blocks > 0 ? ctx->opt.grid_blocks : (int64_t)occ * ctx->num_sms;
+    grid = std::min<int64_t>(grid, std::max<int64_t>(ctx->M, 1));
+    ctx->threads = threads;
+    ctx->grid = (int)grid;
+    return HJG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hjg_status_string(hjg_status s) {
+    switch (s) {
+    case HJG_OK: return "ok";
+    case HJG_EINVAL: return "invalid argument";
+    case HJG_ENOMEM: return "out of memory";
+    case HJG_ECUDA: return "CUDA error";
+    case HJG_ENONFINITE: return "non-finite result";
+    case HJG_ETIMEOUT: return "device wait timed out";
+    case HJG_ENOTCONVERGED: return "not converged";
+    case HJG_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* hjg_last_error(const hjg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double nu, double T,
+                      const hjg_options* opt, hjg_ctx** out) {
+    if (!out) return HJG_EINVAL;
+    *out = nullptr;
+    if (!dyn || !target || !opt) return HJG_EINVAL;
+    if (!(nu > 0) || !(T > 0) || !std::isfinite(nu) || !std::isfinite(T)) return HJG_EINVAL;
+    if (opt->N < 1 || opt->N > 0xFFFFFFFFll || opt->K < 0) return HJG_EINVAL;
+    hjg_ctx* ctx = new (std::nothrow) hjg_ctx();
+    if (!ctx) return HJG_ENOMEM;
+    ctx->dyn = *dyn;
+    ctx->target = *target;
+    ctx->opt = *opt;
+    ctx->nu = nu;
+    ctx->T = T;
+    ctx->delta = 2.0 * nu;
+    ctx->sigma2 = ctx->delta * T;
+    ctx->eta = opt->eta < 0 ? 1e-6 : opt->eta;
+    ctx->c_min = opt->c_min > 0 ? opt->c_min : 1e-2 / ctx->delta;
+    ctx->c_max = opt->c_max > 0 ? opt->c_max : 1e2 / ctx->delta;
+    ctx->n = dyn->n;
+    hjg_status st = HJG_OK;
+    switch (dyn->game) {
+    case HJG_DUBINS3: ctx->kern = kernels_dubins3(); break;
+    case HJG_ROCKETS6: ctx->kern = kernels_rockets6(); break;
+    case HJG_ROCKETS45: ctx->kern = kernels_rockets45(); break;
+    case HJG_TEST_QUADRATIC:
+    case HJG_TEST_ZERO_H:
+        if (!kernels_quadratic(dyn->n, dyn->game == HJG_TEST_ZERO_H, &ctx->kern)) st = HJG_EUNSUPPORTED;
+        break;
+    case HJG_FLOCK4: st = HJG_EUNSUPPORTED; break;
+    default: st = HJG_EINVAL;
+    }
+    if (st == HJG_OK && ctx->kern.n != dyn->n) st = HJG_EINVAL;
+    if (st == HJG_OK && !(ctx->c_min <= ctx->c_max)) st = HJG_EINVAL;
+    if (st != HJG_OK) { delete ctx; return st; }
+    ctx->ldx = (ctx->n + 3) / 4 * 4;
+    fill_game_params(ctx);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        delete ctx;
+        return HJG_ECUDA;
+    }
+    if (cudaMalloc((void**)&ctx->d_counters, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        delete ctx;
+        return HJG_ENOMEM;
+    }
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    *out = ctx;
+    return HJG_OK;
+}
+
+void hjg_destroy(hjg_ctx* ctx) {
+    if (!ctx) return;
+    cudaFree(ctx->d_x); cudaFree(ctx->d_v); cudaFree(ctx->d_p); cudaFree(ctx->d_c);
+    cudaFree(ctx->d_ess); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+hjg_status hjg_set_stream(hjg_ctx* ctx, void* stream) {
+    if (!ctx) return HJG_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return HJG_OK;
+}
+
+hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld, int on_device,
+                          void* stream) {
+    if (!ctx) return HJG_EINVAL;
+    if (M < 0 || M > 0xFFFFFFFFll || (M > 0 && !pts) || ld < ctx->n)
+        return fail(ctx, HJG_EINVAL, "set_points: bad M=%lld or ld=%lld (n=%d)", (long long)M,
+                    (long long)ld, ctx->n);
+    cudaStream_t st = pick_stream(ctx, stream);
+    hjg_status s;
+    if ((s = ensure_capacity(ctx, M))) return s;
+    ctx->M = M;
+    ctx->next_sweep = 0;
+    ctx->last_sweeps = 0;
+    if (M == 0) return HJG_OK;
+    if ((s = stage_points(ctx, pts, M, ld, on_device, st))) return s;
+    if (ctx->ldx > ctx->n) {
+        // zero the padding columns of x and p so every row is a clean float4 multiple
+        HJG_CUDA(ctx, cudaMemset2DAsync(ctx->d_x + ctx->n, ctx->ldx * sizeof(float), 0,
+                                        (ctx->ldx - ctx->n) * sizeof(float), (size_t)M, st));
+        HJG_CUDA(ctx, cudaMemset2DAsync(ctx->d_p + ctx->n, ctx->ldx * sizeof(float), 0,
+                                        (ctx->ldx - ctx->n) * sizeof(float), (size_t)M, st));
+    }
+    HJG_CUDA(ctx, ctx->kern.init(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min,
+                                 ctx->c_max, ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, ctx->d_ess, st));
+    return HJG_OK;
+}
+
+hjg_status hjg_picard_sweep(hjg_ctx* ctx, int n_sweeps, double* residual_out, double* supnorm_out) {
+    if (!ctx) return HJG_EINVAL;
+    if (n_sweeps < 0) return fail(ctx, HJG_EINVAL, "n_sweeps < 0");
+    if ((uint64_t)ctx->next_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull)
+        return fail(ctx, HJG_EINVAL, "sweep counter would overflow");
+    if (n_sweeps == 0 || ctx->M == 0) { ctx->last_sweeps = 0; return HJG_OK; }
+    hjg_status s;
+    if ((s = ensure_history(ctx, n_sweeps))) return s;
+    if ((s = choose_launch(ctx))) return s;
+    cudaStream_t st = ctx->stream;
+    HJG_CUDA(ctx, cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
+    SweepArgs A = make_args(ctx, n_sweeps);
+    HJG_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
+    HJG_CUDA(ctx, ctx->kern.sweep(A, ctx->opt.tilt != 0, ctx->threads, ctx->grid, st));
+    residual_kernel<<<n_sweeps, 256, 0, st>>>(ctx->d_vhist, ctx->M, ctx->d_resid);
+    HJG_CUDA(ctx, cudaGetLastError());
+    HJG_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
+    ctx->next_sweep += (uint32_t)n_sweeps;
+    ctx->last_sweeps = n_sweeps;
+    if (residual_out || supnorm_out) {
+        std::vector<double> r(2 * (size_t)n_sweeps);
+        unsigned long long cnt[4];
+        HJG_CUDA(ctx, cudaMemcpyAsync(r.data(), ctx->d_resid, r.size() * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st));
+        HJG_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
+        HJG_CUDA(ctx, cudaStreamSynchronize(st));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        ctx->last_ms = ms;
+        for (int k = 0; k < n_sweeps; ++k) {
+            if (residual_out) residual_out[k] = r[2 * k];
+            if (supnorm_out) supnorm_out[k] = r[2 * k + 1];
+        }
+        ctx->nonfinite = (int64_t)cnt[0];
+        ctx->clipped = (int64_t)cnt[1];
+        if (cnt[0]) return fail(ctx, HJG_ENONFINITE, "%llu states gave a non-finite v or Dv", cnt[0]);
+    }
+    return HJG_OK;
+}
+
+hjg_status hjg_get_state(hjg_ctx* ctx, double* v, float* p, int64_t ldp, float* c, float* ess,
+                         int on_device) {
+    if (!ctx) return HJG_EINVAL;
+    if (p && ldp < ctx->n) return fail(ctx, HJG_EINVAL, "ldp < n");
+    cudaStream_t st = ctx->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    if (v) HJG_CUDA(ctx, cudaMemcpyAsync(v, ctx->d_v, M * sizeof(double), kind, st));
+    if (c) HJG_CUDA(ctx, cudaMemcpyAsync(c, ctx->d_c, M * sizeof(float), kind, st));
+    if (ess) HJG_CUDA(ctx, cudaMemcpyAsync(ess, ctx->d_ess, M * sizeof(float), kind, st));
+    if (p) HJG_CUDA(ctx, cudaMemcpy2DAsync(p, ldp * sizeof(float), ctx->d_p, ctx->ldx * sizeof(float),
+                                           ctx->n * sizeof(float), (size_t)M, kind, st));
+    HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
+hjg_status hjg_set_state(hjg_ctx* ctx, const double* v, const float* p, int64_t ldp, const float* c,
+                         uint32_t next_sweep, int on_device) {
+    if (!ctx) return HJG_EINVAL;
+    if (p && ldp < ctx->n) return fail(ctx, HJG_EINVAL, "ldp < n");
+    cudaStream_t st = ctx->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const int64_t M = ctx->M;
+    if (M > 0) {
+        if (v) HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_v, v, M * sizeof(double), kind, st));
+        if (c) HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_c, c, M * sizeof(float), kind, st));
+        if (p) HJG_CUDA(ctx, cudaMemcpy2DAsync(ctx->d_p, ctx->ldx * sizeof(float), p, ldp * sizeof(float),
+                                               ctx->n * sizeof(float), (size_t)M, kind, st));
+        HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    ctx->next_sweep = next_sweep;
+    return HJG_OK;
+}
+
+hjg_status hjg_get_history(hjg_ctx* ctx, double* out, int on_device) {
+    if (!ctx || !out) return HJG_EINVAL;
+    if (ctx->last_sweeps == 0 || ctx->M == 0) return HJG_OK;
+    cudaStream_t st = ctx->stream;
+    HJG_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_vhist, (size_t)(ctx->last_sweeps + 1) * ctx->M * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
+hjg_status hjg_value_grad(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld, int on_device,
+                          double* v_out, float* grad_out, int64_t ldg, double* residual_out,
+                          void* stream) {
+    if (!ctx) return HJG_EINVAL;
+    if (grad_out && ldg < ctx->n) return fail(ctx, HJG_EINVAL, "ldg < n");
+    cudaStream_t saved = ctx->stream;
+    if (stream) ctx->stream = (cudaStream_t)stream;
+    hjg_status s = hjg_set_points(ctx, pts, M, ld, on_device, nullptr);
+    const int K = ctx->opt.K;
+    std::vector<double> r(std::max(K, 1), NAN);
+    hjg_status sweep_status = HJG_OK;
+    if (s == HJG_OK && K > 0) {
+        if (ctx->opt.eps > 0) {
+            // Algorithm 1's stopping rule: stop after the sweep whose relative change < eps
+            for (int k = 0; k < K; ++k) {
+                s = hjg_picard_sweep(ctx, 1, &r[k], nullptr);
+                if (s != HJG_OK && s != HJG_ENONFINITE) break;
+                if (s == HJG_ENONFINITE) sweep_status = s;
+                if (r[k] < ctx->opt.eps) break;
+            }
+        } else {
+            s = hjg_picard_sweep(ctx, K, r.data(), nullptr);
+            if (s == HJG_ENONFINITE) { sweep_status = s; s = HJG_OK; }
+        }
+        if (s == HJG_ENONFINITE) s = HJG_OK;
+    }
+    if (s == HJG_OK) s = hjg_get_state(ctx, v_out, grad_out, ldg, nullptr, nullptr, on_device);
+    if (s == HJG_OK && residual_out)
+        for (int k = 0; k < K; ++k) residual_out[k] = r[k];
+    ctx->stream = saved;
+    return s != HJG_OK ? s : sweep_status;
+}
+
+hjg_status hjg_get_diagnostics(hjg_ctx* ctx, hjg_diag* out) {
+    if (!ctx || !out) return HJG_EINVAL;
+    memset(out, 0, sizeof *out);
+    out->M = ctx->M;
+    out->next_sweep = ctx->next_sweep;
+    out->nonfinite = ctx->nonfinite;
+    out->clipped = ctx->clipped;
+    out->last_ms = ctx->last_ms;
+    out->block_threads = ctx->threads;
+    out->grid_blocks = ctx->grid;
+    if (ctx->M > 0) {
+        std::vector<float> e((size_t)ctx->M);
+        HJG_CUDA(ctx, cudaMemcpyAsync(e.data(), ctx->d_ess, e.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::vector<float> sorted = e;
+        std::nth_element(sorted.begin(), sorted.begin() + sorted.size() / 2, sorted.end());
+        out->ess_median = sorted[sorted.size() / 2];
+        out->ess_min = *std::min_element(e.begin(), e.end());
+    }
+    return HJG_OK;
+}
+
+hjg_status hjg_philox_blocks(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count,
+                             void* stream) {
+    if (count < 0 || (count > 0 && (!ctr || !key || !out))) return HJG_EINVAL;
+    if (count == 0) return HJG_OK;
+    const int T = 256;
+    philox_blocks_kernel<<<(unsigned)((count + T - 1) / T), T, 0, (cudaStream_t)stream>>>(ctr, key, out, count);
+    return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
+}
+
+hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point, uint32_t sweep,
+                              int64_t n_samples, float* out, void* stream) {
+    if (n < 1 || n > 64 || n_samples < 0 || n_samples > 0xFFFFFFFFll || (n_samples > 0 && !out))
+        return HJG_EINVAL;
+    if (n_samples == 0) return HJG_OK;
+    const int T = 256;
+    normals_kernel<<<(unsigned)((n_samples + T - 1) / T), T, 0, (cudaStream_t)stream>>>(
+        n, (uint32_t)seed, (uint32_t)(seed >> 32) ^ instance, point, sweep, n_samples, out);
+    return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// Sweep kernels for the quadratic test problems (H = +-|p|^2/2 or H = 0, quadratic
+// target), n in {1, 2, 3, 4, 6, 8}: the exact Cole-Hopf case of Corollary B.2 and the
+// pure heat equation, used to check the estimator against closed forms.
+#include "dispatch.h"
+
+namespace hjg {
+namespace {
+template <class G>
+cudaError_t sweep(const SweepArgs& A, bool tilt, int threads, int grid, cudaStream_t st) {
+    if (threads != 128) return cudaErrorInvalidValue;
+    return launch_sweep_generic<G, 128>(A, tilt, grid, st);
+}
+template <class G>
+int occ(bool tilt, int threads) {
+    return threads == 128 ? occupancy_generic<G, 128>(tilt) : 0;
+}
+template <int N, bool Z>
+GameKernels make() {
+    using G = Quadratic<N, Z>;
+    return {N, sweep<G>, occ<G>, launch_init<G>, 128};
+}
+}  // namespace
+
+bool kernels_quadratic(int n, bool zero_h, GameKernels* out) {
+#define HJG_Q(N) case N: *out = zero_h ? make<N, true>() : make<N, false>(); return true;
+    switch (n) { HJG_Q(1) HJG_Q(2) HJG_Q(3) HJG_Q(4) HJG_Q(6) HJG_Q(8) }
+#undef HJG_Q
+    return false;
+}
+}  // namespace hjg

@@ -1,0 +1,404 @@
+// sweep_impl.cuh -- the fused frozen-coefficient Picard sweep (Algorithm 1) on sm_103a.
+//
+// One CTA owns one evaluation state at a time and runs all requested sweeps for it:
+// states are independent (c_m depends only on Dv at x_m, Theorem 2.8's map Gamma acts
+// pointwise), so no grid-wide synchronisation is ever needed.  Per sweep:
+//   a2  sampler    Philox4x32-10 -> uniforms -> Box-Muller, in registers
+//   a3  payoff     y = x + theta + sigma z, a = -c l(y) - <z, theta>/sigma   (base 2)
+//   a4  LSE        running shift m, s = sum 2^(a-m), S_j = sum 2^(a-m) z_j, Q = sum 2^(2(a-m))
+//   a5  merge      warp shuffle (FP32) -> shared-memory block combine in FP64
+//   a6  recover    v = -(m ln2 - |theta|^2/2sigma^2 + ln(s/N)) / c        (Cor. B.4 / B.6)
+//                  Dv = -(theta + sigma S/s) / (c sigma^2)                  (Cor. B.5 / B.6)
+//                  ESS = s^2 / Q                                           (Section 2.4)
+//   a7  Gamma      c = clip((2/delta) H(x, Dv) / (|Dv|^2 + eta))           (Eq. coeff_frozen)
+// The incoming and outgoing v of every sweep go to a history buffer from which the
+// residual kernel forms the relative L2 change of Algorithm 1.
+#pragma once
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+
+#include "games.cuh"
+#include "sampler.cuh"
+
+namespace hjg {
+
+struct SweepArgs {
+    const float* x;           // [M][ldx] evaluation states
+    float* p;                 // [M][ldp] Dv iterate (in: p^(k), out: p^(k+K))
+    float* c;                 // [M] frozen coefficient (in: c^(k), out: c^(k+K))
+    double* v;                // [M] value iterate (in: v^(k), out: v^(k+K))
+    double* vhist;            // [K+1][M] value history (row 0 = incoming v); may be null
+    float* ess;               // [M] ESS of the last sweep
+    unsigned long long* counters;  // [0] non-finite states, [1] clipped coefficients (last sweep)
+    int64_t ldx, ldp, M, N;
+    uint32_t key0, key1;      // Philox key
+    uint32_t k0;              // global index of the first sweep
+    int32_t K;                // sweeps to run
+    float sigma;              // sqrt(delta t)
+    double sigma_d, sigma2_d, delta, eta, c_min, c_max;
+    GameParams g;
+};
+
+// Threshold (base-2 units) above the running shift at which the sums are rescaled.
+// Weights stay below 2^32 and Q below N 2^64, far inside FP32 range, while the rescale
+// branch is taken only a handful of times per thread.
+constexpr float kRescaleTau = 32.0f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr double kLn2 = 0.69314718055994530942;
+
+__device__ __forceinline__ float merge_factor(float m, float M) {
+    return (m == -INFINITY) ? 0.0f : ex2_approx(m - M);
+}
+
+// Online accumulation of one sample with log2-weight a.
+template <int NS>
+__device__ __forceinline__ void lse_accumulate(float a, const float* z, float& m, float& s,
+                                               float& q, float* S) {
+    float d = a - m;
+    if (d > kRescaleTau) {
+        const float f = ex2_approx(-d);   // 2^(m_old - a); 0 on the first sample
+        s *= f;
+        q *= f * f;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) S[j] *= f;
+        m = a;
+        d = 0.0f;
+    }
+    const float w = ex2_approx(d);
+    s += w;
+    q = fmaf(w, w, q);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) S[j] = fmaf(w, z[j], S[j]);
+}
+
+// Butterfly merge of (m, s, q, S) across the lanes selected by the xor offsets [lo, 16].
+template <int NS>
+__device__ __forceinline__ void warp_merge(int lo, float& m, float& s, float& q, float* S) {
+    for (int off = 16; off >= lo; off >>= 1) {
+        const float mo = __shfl_xor_sync(0xffffffffu, m, off);
+        const float so = __shfl_xor_sync(0xffffffffu, s, off);
+        const float qo = __shfl_xor_sync(0xffffffffu, q, off);
+        const float Mx = fmaxf(m, mo);
+        const float f1 = merge_factor(m, Mx), f2 = merge_factor(mo, Mx);
+        s = s * f1 + so * f2;
+        q = q * (f1 * f1) + qo * (f2 * f2);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const float So = __shfl_xor_sync(0xffffffffu, S[j], off);
+            S[j] = S[j] * f1 + So * f2;
+        }
+        m = Mx;
+    }
+}
+
+// Shared-memory state of one CTA.
+template <int NPAD, int W>
+struct SweepShared {
+    double x[NPAD];       // state in FP64
+    double S[NPAD];       // combined weighted normal sums (FP64)
+    double s, q, mx;      // combined sums and shift
+    float xf[NPAD];       // state in FP32
+    float yoff[NPAD];     // x + theta (FP32), the sample mean
+    float tq[NPAD];       // -theta_j log2e / sigma (tilt log-weight slope)
+    float theta[NPAD];
+    float cneg2;          // -c log2e
+    float c;
+    double thconst;       // -|theta|^2 / (2 sigma^2)
+    float red_m[W], red_s[W], red_q[W];
+    float red_S[W][NPAD];
+};
+
+// FP64 combine of the per-warp partials; threads tid < n each own one S_j.
+template <int NPAD, int W>
+__device__ __forceinline__ void block_combine(SweepShared<NPAD, W>& sh, int n, int tid) {
+    double Mx = -INFINITY;
+#pragma unroll
+    for (int w = 0; w < W; ++w) Mx = fmax(Mx, (double)sh.red_m[w]);
+    if (tid < n || tid == n) {
+        double acc = 0.0, acc_q = 0.0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const double f = (sh.red_m[w] == -INFINITY) ? 0.0 : exp2((double)sh.red_m[w] - Mx);
+            if (tid < n) {
+                acc += f * (double)sh.red_S[w][tid];
+            } else {
+                acc += f * (double)sh.red_s[w];
+                acc_q += f * f * (double)sh.red_q[w];
+            }
+        }
+        if (tid < n) {
+            sh.S[tid] = acc;
+        } else {
+            sh.s = acc;
+            sh.q = acc_q;
+            sh.mx = Mx;
+        }
+    }
+}
+
+// Per-state set-up for a sweep: theta from the current (c, p) when tilting, and the
+// FP32 constants the sample loop needs.  Thread 0 only.
+template <int NPAD, int W, bool TILT>
+__device__ __forceinline__ void prepare_sweep(SweepShared<NPAD, W>& sh, const SweepArgs& A,
+                                              int n, float c, const float* p_cur) {
+    sh.c = c;
+    sh.cneg2 = -c * kLog2e;
+    double th2 = 0.0;
+    for (int j = 0; j < NPAD; ++j) {
+        float th = 0.0f;
+        if (TILT && j < n) th = (float)(-A.sigma2_d * (double)c * (double)p_cur[j]);
+        sh.theta[j] = th;
+        sh.yoff[j] = sh.xf[j] + th;
+        sh.tq[j] = -th * kLog2e / A.sigma;
+        th2 += (double)th * (double)th;
+    }
+    sh.thconst = -th2 / (2.0 * A.sigma2_d);
+}
+
+// Recover v, Dv, ESS from the combined sums, update c (thread 0).  Writes outputs and
+// returns the new (c, p) through shared memory for the next sweep.
+template <class G, int NPAD, int W>
+__device__ __forceinline__ void recover_and_update(SweepShared<NPAD, W>& sh, const SweepArgs& A,
+                                                   int64_t pt, int k, bool last, float* p_cur) {
+    constexpr int n = G::kN;
+    const double c = (double)sh.c;
+    const double s = sh.s;
+    const double logmean = sh.mx * kLn2 + sh.thconst + log(s / (double)A.N);
+    const double v = -logmean / c;
+    double pd[n];
+    double pp = 0.0;
+    bool finite = isfinite(v);
+    for (int j = 0; j < n; ++j) {
+        pd[j] = -((double)sh.theta[j] + A.sigma_d * sh.S[j] / s) / (c * A.sigma2_d);
+        pp += pd[j] * pd[j];
+        finite = finite && isfinite(pd[j]);
+    }
+    const double h = G::ham_d(sh.x, pd, A.g);
+    int clipped = 0;
+    const double c_new = coef_update(h, pp, A.delta, A.eta, A.c_min, A.c_max, &clipped);
+    const float c_new_f = (float)c_new;
+    for (int j = 0; j < n; ++j) p_cur[j] = (float)pd[j];
+    if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
+    if (last) {
+        A.v[pt] = v;
+        A.c[pt] = c_new_f;
+        A.ess[pt] = (float)(s * s / sh.q);
+        for (int j = 0; j < n; ++j) A.p[pt * A.ldp + j] = p_cur[j];
+        if (!finite) atomicAdd(&A.counters[0], 1ull);
+        if (clipped) atomicAdd(&A.counters[1], 1ull);
+    }
+    sh.c = c_new_f;
+}
+
+// ------------------------------------------------------------------------------------
+// One lane per sample stream (games with n <= 8).
+template <class G, int THREADS, bool TILT>
+__global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
+    constexpr int n = G::kN;
+    constexpr int NQ = (n + 3) / 4;
+    constexpr int NPAD = 4 * NQ;
+    constexpr int W = THREADS / 32;
+    __shared__ SweepShared<NPAD, W> sh;
+    __shared__ float p_cur[NPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
+        if (tid < NPAD) {
+            const float xv = tid < n ? A.x[pt * A.ldx + tid] : 0.0f;
+            sh.xf[tid] = xv;
+            sh.x[tid] = (double)xv;
+            p_cur[tid] = tid < n ? A.p[pt * A.ldp + tid] : 0.0f;
+        }
+        if (tid == 0 && A.vhist) A.vhist[pt] = A.v[pt];
+        __syncthreads();
+        if (tid == 0) prepare_sweep<NPAD, W, TILT>(sh, A, n, A.c[pt], p_cur);
+        __syncthreads();
+
+        for (int k = 0; k < A.K; ++k) {
+            const uint32_t sweep = A.k0 + (uint32_t)k;
+            const float cneg2 = sh.cneg2;
+            float yoff[n], tq[n];
+#pragma unroll
+            for (int j = 0; j < n; ++j) { yoff[j] = sh.yoff[j]; tq[j] = sh.tq[j]; }
+            float m = -INFINITY, s = 0.0f, q = 0.0f, S[n];
+#pragma unroll
+            for (int j = 0; j < n; ++j) S[j] = 0.0f;
+
+            const uint32_t N32 = (uint32_t)A.N;
+            for (uint32_t i = tid; i < N32; i += THREADS) {
+                float z[NPAD];
+                draw_normals<NQ, n>(i, 0u, (uint32_t)pt, sweep, A.key0, A.key1, z);
+                float y[n];
+#pragma unroll
+                for (int j = 0; j < n; ++j) y[j] = fmaf(A.sigma, z[j], yoff[j]);
+                float a = cneg2 * G::ell(y, A.g);
+                if (TILT) {
+#pragma unroll
+                    for (int j = 0; j < n; ++j) a = fmaf(z[j], tq[j], a);
+                }
+                lse_accumulate<n>(a, z, m, s, q, S);
+            }
+
+            warp_merge<n>(1, m, s, q, S);
+            if (lane == 0) {
+                sh.red_m[warp] = m; sh.red_s[warp] = s; sh.red_q[warp] = q;
+#pragma unroll
+                for (int j = 0; j < n; ++j) sh.red_S[warp][j] = S[j];
+            }
+            __syncthreads();
+            block_combine<NPAD, W>(sh, n, tid);
+            __syncthreads();
+            if (tid == 0) {
+                recover_and_update<G, NPAD, W>(sh, A, pt, k, k + 1 == A.K, p_cur);
+                prepare_sweep<NPAD, W, TILT>(sh, A, n, sh.c, p_cur);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// 45-D multi-rocket game: four lanes per sample stream.  Lane q of a group owns dims
+// 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. Philox blocks 3q..3q+2.
+// The evader (agent 14, dims 42..44) sits on lane 3; its position is broadcast, each lane
+// takes the minimum squared distance over its own pursuers, and two shuffles finish the
+// group minimum.  All four lanes then hold the same log-weight and accumulate their own
+// twelve S_j.
+template <int THREADS, bool TILT>
+__global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
+    using G = Rockets45;
+    constexpr int n = 45;
+    constexpr int NPAD = 48;
+    constexpr int W = THREADS / 32;
+    constexpr int GROUPS = THREADS / 4;
+    __shared__ SweepShared<NPAD, W> sh;
+    __shared__ float p_cur[NPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q4 = lane & 3;
+    const int grp = tid >> 2;
+    const int src3 = (lane & ~3) | 3;
+    const int nag = (q4 == 3) ? 2 : 4;   // pursuers owned by this lane
+
+    for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
+        if (tid < NPAD) {
+            const float xv = tid < n ? A.x[pt * A.ldx + tid] : 0.0f;
+            sh.xf[tid] = xv;
+            sh.x[tid] = (double)xv;
+            p_cur[tid] = tid < n ? A.p[pt * A.ldp + tid] : 0.0f;
+        }
+        if (tid == 0 && A.vhist) A.vhist[pt] = A.v[pt];
+        __syncthreads();
+        if (tid == 0) prepare_sweep<NPAD, W, TILT>(sh, A, n, A.c[pt], p_cur);
+        __syncthreads();
+
+        for (int k = 0; k < A.K; ++k) {
+            const uint32_t sweep = A.k0 + (uint32_t)k;
+            const float cneg2 = sh.cneg2;
+            float yoff[12], tq[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) { yoff[j] = sh.yoff[12 * q4 + j]; tq[j] = sh.tq[12 * q4 + j]; }
+            float m = -INFINITY, s = 0.0f, q = 0.0f, S[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) S[j] = 0.0f;
+
+            const uint32_t N32 = (uint32_t)A.N;
+            for (uint32_t i = grp; i < N32; i += GROUPS) {
+                float z[12];
+                draw_normals<3, 12>(i, 3u * q4, (uint32_t)pt, sweep, A.key0, A.key1, z);
+                float yx[4], yz[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    yx[a] = fmaf(A.sigma, z[3 * a], yoff[3 * a]);
+                    yz[a] = fmaf(A.sigma, z[3 * a + 1], yoff[3 * a + 1]);
+                }
+                const float ex = __shfl_sync(0xffffffffu, yx[2], src3);
+                const float ez = __shfl_sync(0xffffffffu, yz[2], src3);
+                float d2 = INFINITY;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float dx = yx[a] - ex, dz = yz[a] - ez;
+                    const float dd = fmaf(dx, dx, dz * dz);
+                    d2 = (a < nag) ? fminf(d2, dd) : d2;
+                }
+                d2 = fminf(d2, __shfl_xor_sync(0xffffffffu, d2, 1));
+                d2 = fminf(d2, __shfl_xor_sync(0xffffffffu, d2, 2));
+                float a2 = cneg2 * (sqrt_approx(d2) - A.g.radius);
+                if (TILT) {
+                    float part = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) part = fmaf(z[j], tq[j], part);
+                    part += __shfl_xor_sync(0xffffffffu, part, 1);
+                    part += __shfl_xor_sync(0xffffffffu, part, 2);
+                    a2 += part;
+                }
+                lse_accumulate<12>(a2, z, m, s, q, S);
+            }
+
+            warp_merge<12>(4, m, s, q, S);
+            if (lane < 4) {
+                if (lane == 0) { sh.red_m[warp] = m; sh.red_s[warp] = s; sh.red_q[warp] = q; }
+#pragma unroll
+                for (int j = 0; j < 12; ++j) sh.red_S[warp][12 * lane + j] = S[j];
+            }
+            __syncthreads();
+            block_combine<NPAD, W>(sh, n, tid);
+            __syncthreads();
+            if (tid == 0) {
+                recover_and_update<G, NPAD, W>(sh, A, pt, k, k + 1 == A.K, p_cur);
+                prepare_sweep<NPAD, W, TILT>(sh, A, n, sh.c, p_cur);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Initial iterate of Algorithm 1: v0 = l(x), p0 = Dl(x), c0 = Gamma(p0) (FP64 per state).
+template <class G>
+__global__ void init_kernel(const float* __restrict__ x, int64_t ldx, int64_t M, GameParams g,
+                            double delta, double eta, double c_min, double c_max,
+                            double* __restrict__ v, float* __restrict__ p, int64_t ldp,
+                            float* __restrict__ c, float* __restrict__ ess) {
+    constexpr int n = G::kN;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double xd[n], gr[n];
+    for (int j = 0; j < n; ++j) xd[j] = (double)x[m * ldx + j];
+    v[m] = G::ell_d(xd, g);
+    G::grad_ell_d(xd, gr, g);
+    double pp = 0.0;
+    for (int j = 0; j < n; ++j) { p[m * ldp + j] = (float)gr[j]; pp += gr[j] * gr[j]; }
+    int clipped;
+    c[m] = (float)coef_update(G::ham_d(xd, gr, g), pp, delta, eta, c_min, c_max, &clipped);
+    ess[m] = 0.0f;
+}
+
+// Launch helpers instantiated once per game in its own translation unit.
+template <class G, int THREADS>
+cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
+    if (tilt) sweep_kernel<G, THREADS, true><<<grid, THREADS, 0, st>>>(A);
+    else sweep_kernel<G, THREADS, false><<<grid, THREADS, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <class G, int THREADS>
+int occupancy_generic(bool tilt) {
+    int nb = 0;
+    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, true>, THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, false>, THREADS, 0);
+    return nb;
+}
+
+template <class G>
+cudaError_t launch_init(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta,
+                        double eta, double c_min, double c_max, double* v, float* p, int64_t ldp,
+                        float* c, float* ess, cudaStream_t st) {
+    const int T = 128;
+    const int64_t blocks = (M + T - 1) / T;
+    init_kernel<G><<<(unsigned)blocks, T, 0, st>>>(x, ldx, M, g, delta, eta, c_min, c_max, v, p,
+                                                  ldp, c, ess);
+    return cudaGetLastError();
+}
+
+}  // namespace hjg

@@ -1,0 +1,191 @@
+"""Python binding of the C ABI: a thin wrapper that marshals torch tensors (device memory,
+streams) into libhjg.so calls.  No arithmetic of the method happens here."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import HJGError
+
+
+def _check(lib, ctx, st):
+    if st != _lib.HJG_OK:
+        msg = lib.hjg_last_error(ctx).decode() if ctx else ""
+        raise HJGError(st, msg)
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """One game instance of the frozen-coefficient Picard sweep (Algorithm 1).
+
+    game: 'dubins3' | 'rockets6' | 'rockets45' | 'quadratic' | 'zero_h';
+    nu: viscosity with delta = 2 nu; T: horizon; N: samples per state and sweep;
+    K: sweeps run by value_grad.
+    """
+
+    def __init__(self, game: str, nu: float, T: float, N: int, K: int = 10, *,
+                 n: Optional[int] = None, radius: float = 0.5,
+                 speed: Optional[Sequence[float]] = None, h_sign: float = 1.0,
+                 A=None, x0=None, d: float = 0.0, seed: int = 0, instance: int = 0,
+                 tilt: bool = False, eps: float = 0.0, eta: float = -1.0,
+                 c_min: float = 0.0, c_max: float = 0.0, block_threads: int = 0,
+                 grid_blocks: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _lib.load()
+        if n is None:
+            n = _lib.GAME_DIMS[game]
+        self.n = n
+        self.game = game
+        dyn = _lib.Dynamics()
+        dyn.game = _lib.GAMES[game]
+        dyn.n = n
+        for i, s in enumerate(speed or []):
+            dyn.speed[i] = s
+        dyn.h_sign = h_sign
+        tgt = _lib.Target()
+        tgt.radius = radius
+        if A is not None:
+            for i, a in enumerate(np.asarray(A, dtype=np.float64).ravel()):
+                tgt.A[i] = a
+        if x0 is not None:
+            for i, a in enumerate(np.asarray(x0, dtype=np.float64).ravel()):
+                tgt.x0[i] = a
+        tgt.d = d
+        opt = _lib.Options()
+        opt.N = N; opt.K = K; opt.tilt = 1 if tilt else 0; opt.eps = eps; opt.eta = eta
+        opt.c_min = c_min; opt.c_max = c_max; opt.seed = seed; opt.instance = instance
+        opt.block_threads = block_threads; opt.grid_blocks = grid_blocks
+        self.opt = opt
+        ctx = C.c_void_p()
+        torch.cuda.init()
+        st = self.lib.hjg_create(C.byref(dyn), C.byref(tgt), nu, T, C.byref(opt), C.byref(ctx))
+        if st != _lib.HJG_OK:
+            raise HJGError(st, "hjg_create")
+        self.ctx = ctx
+        self.M = 0
+        self.set_stream(stream)
+
+    # ------------------------------------------------------------------ plumbing
+    def set_stream(self, stream: Optional[torch.cuda.Stream]):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _check(self.lib, self.ctx, self.lib.hjg_set_stream(self.ctx, _stream_handle(self.stream)))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.hjg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptr(self, t: Optional[torch.Tensor]):
+        return C.c_void_p(t.data_ptr()) if t is not None else None
+
+    # ------------------------------------------------------------------ API
+    def set_points(self, x: torch.Tensor):
+        """x: [M, ld] float32 (ld >= n), on the GPU or in host memory."""
+        assert x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1
+        on_dev = 1 if x.is_cuda else 0
+        self.M = x.shape[0]
+        _check(self.lib, self.ctx, self.lib.hjg_set_points(
+            self.ctx, self._ptr(x), x.shape[0], x.stride(0), on_dev, None))
+
+    def picard_sweep(self, n_sweeps: int, residuals: bool = True):
+        """Run n_sweeps sweeps; returns (relative L2 residual, sup-norm) per sweep as numpy,
+        or None when residuals=False (asynchronous)."""
+        if not residuals:
+            _check(self.lib, self.ctx, self.lib.hjg_picard_sweep(self.ctx, n_sweeps, None, None))
+            return None
+        r = np.zeros(max(n_sweeps, 1)); s = np.zeros(max(n_sweeps, 1))
+        st = self.lib.hjg_picard_sweep(self.ctx, n_sweeps, r.ctypes.data_as(C.c_void_p),
+                                       s.ctypes.data_as(C.c_void_p))
+        if st not in (_lib.HJG_OK, _lib.HJG_ENONFINITE):
+            _check(self.lib, self.ctx, st)
+        self.last_status = st
+        return r[:n_sweeps], s[:n_sweeps]
+
+    def get_state(self, device: bool = True):
+        M, n = self.M, self.n
+        kw = dict(device="cuda") if device else {}
+        v = torch.empty(M, dtype=torch.float64, **kw)
+        p = torch.empty(M, n, dtype=torch.float32, **kw)
+        c = torch.empty(M, dtype=torch.float32, **kw)
+        ess = torch.empty(M, dtype=torch.float32, **kw)
+        _check(self.lib, self.ctx, self.lib.hjg_get_state(
+            self.ctx, self._ptr(v), self._ptr(p), n, self._ptr(c), self._ptr(ess),
+            1 if device else 0))
+        return {"v": v, "p": p, "c": c, "ess": ess}
+
+    def set_state(self, v=None, p=None, c=None, next_sweep: int = 0):
+        ts = [t for t in (v, p, c) if t is not None]
+        dev = ts[0].is_cuda if ts else True
+        if p is not None:
+            assert p.dtype == torch.float32 and p.stride(1) == 1
+        _check(self.lib, self.ctx, self.lib.hjg_set_state(
+            self.ctx, self._ptr(v), self._ptr(p), p.stride(0) if p is not None else self.n,
+            self._ptr(c), next_sweep, 1 if dev else 0))
+
+    def history(self, n_sweeps: int) -> torch.Tensor:
+        out = torch.empty(n_sweeps + 1, self.M, dtype=torch.float64, device="cuda")
+        _check(self.lib, self.ctx, self.lib.hjg_get_history(self.ctx, self._ptr(out), 1))
+        return out
+
+    def value_grad(self, x: torch.Tensor, v_out=None, grad_out=None):
+        """Algorithm 1 end to end: set points, run K sweeps (or stop at eps), copy out.
+        Host tensors in -> host tensors out (copies inside the call); device -> device."""
+        assert x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1
+        M = x.shape[0]
+        dev = x.is_cuda
+        kw = dict(device=x.device) if dev else dict(pin_memory=False)
+        if v_out is None:
+            v_out = torch.empty(M, dtype=torch.float64, **kw)
+        if grad_out is None:
+            grad_out = torch.empty(M, self.n, dtype=torch.float32, **kw)
+        K = self.opt.K
+        r = np.full(max(K, 1), np.nan)
+        self.M = M
+        st = self.lib.hjg_value_grad(self.ctx, self._ptr(x), M, x.stride(0), 1 if dev else 0,
+                                     self._ptr(v_out), self._ptr(grad_out), grad_out.stride(0),
+                                     r.ctypes.data_as(C.c_void_p), None)
+        if st not in (_lib.HJG_OK, _lib.HJG_ENONFINITE):
+            _check(self.lib, self.ctx, st)
+        self.last_status = st
+        return v_out, grad_out, r[:K]
+
+    def diagnostics(self) -> dict:
+        d = _lib.Diag()
+        _check(self.lib, self.ctx, self.lib.hjg_get_diagnostics(self.ctx, C.byref(d)))
+        return {f: getattr(d, f) for f, _ in _lib.Diag._fields_}
+
+
+def philox_blocks(ctr: torch.Tensor, key: torch.Tensor) -> torch.Tensor:
+    """Device Philox4x32-10: ctr int32/uint32 [K,4], key [K,2] (CUDA tensors)."""
+    lib = _lib.load()
+    out = torch.empty_like(ctr)
+    st = lib.hjg_philox_blocks(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()),
+                               C.c_void_p(out.data_ptr()), ctr.shape[0],
+                               _stream_handle(None))
+    if st:
+        raise HJGError(st, "hjg_philox_blocks")
+    return out
+
+
+def sample_normals(n: int, seed: int, instance: int, point: int, sweep: int,
+                   n_samples: int) -> torch.Tensor:
+    lib = _lib.load()
+    out = torch.empty(n_samples, n, dtype=torch.float32, device="cuda")
+    st = lib.hjg_sample_normals(n, seed, instance, point, sweep, n_samples,
+                                C.c_void_p(out.data_ptr()), _stream_handle(None))
+    if st:
+        raise HJGError(st, "hjg_sample_normals")
+    return out

@@ -1,0 +1,192 @@
+"""GPU sweep vs the FP64 oracle on the same Philox draws.
+
+P1 (one-sweep parity): the oracle is handed the GPU's frozen coefficient c^(k) (and tilt)
+for one sweep and must agree on every state.
+P2 (trajectory parity): after K sweeps from the same initial iterate, v, Dv and the
+residuals must agree.  Tolerance per state: |dv| <= 1e-4 (1+|v|), ||dDv|| <= 1e-3 (1+||Dv||).
+Full-size workloads are checked on a seeded subset of states, which the oracle computes
+with their global indices (and so the same samples).
+"""
+import numpy as np
+import pytest
+
+import hjg_inputs
+import oracle
+from helpers import assert_parity, problem_for, rel_errors, solver_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W1, W2, W3 = hjg_inputs.DUBINS3, hjg_inputs.ROCKETS6, hjg_inputs.ROCKETS45
+
+
+def run_gpu(w, x, N, K, **kw):
+    s = solver_for(w, N=N, K=K, **kw)
+    s.set_points(torch.from_numpy(x).cuda())
+    st0 = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    r, sup = s.picard_sweep(K)
+    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    hist = s.history(K).cpu().numpy()
+    s.close()
+    return st0, st, r, sup, hist
+
+
+# ------------------------------------------------------------------------------ P1
+@pytest.mark.parametrize("w,M,N", [(W1, 4096, 4096), (W2, 333, 65536), (W3, 37, 8192)],
+                         ids=["dubins3", "rockets6", "rockets45"])
+@pytest.mark.parametrize("tilt", [False, True])
+def test_one_sweep_parity(w, M, N, tilt):
+    x = hjg_inputs.points(w, M=M)
+    st0, st, r, sup, hist = run_gpu(w, x, N, 1, tilt=tilt)
+    P = problem_for(w)
+    xd = x.astype(np.float64)
+    c0 = st0["c"].astype(np.float64)
+    theta = None
+    if tilt:
+        theta = -w.sigma2 * c0[:, None] * st0["p"].astype(np.float64)
+    v, p, ess = oracle.sweep(P, xd, c0, N, 0, theta=theta)
+    assert_parity(st["v"], st["p"], v, p, what="P1 %s" % w.game)
+    # the initial iterate itself: v0 = l(x) and c0 = Gamma(Dl)
+    v0, p0, c0_ref = oracle.init(P, xd)
+    np.testing.assert_allclose(hist[0], v0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(st0["p"], p0, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(st0["c"], c0_ref, rtol=1e-6)
+    np.testing.assert_allclose(st["ess"], ess, rtol=1e-3)
+
+
+# ------------------------------------------------------------------------------ P2
+@pytest.mark.parametrize("w,M,N,K", [(W1, 4096, 4096, 10), (W2, 257, 65536, 20),
+                                     (W3, 24, 16384, 6)],
+                         ids=["dubins3-full", "rockets6-M257", "rockets45-M24"])
+def test_trajectory_parity(w, M, N, K):
+    x = hjg_inputs.points(w, M=M)
+    st0, st, r, sup, hist = run_gpu(w, x, N, K)
+    ref = oracle.picard(problem_for(w), x.astype(np.float64), N, K)
+    dv, dp = assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="P2 %s" % w.game)
+    for k in range(K + 1):
+        dvk = np.abs(hist[k] - ref["v_hist"][k]) / (1 + np.abs(ref["v_hist"][k]))
+        assert dvk.max() <= 1e-4, (k, dvk.max())
+    np.testing.assert_allclose(r, ref["resid"], rtol=2e-3, atol=1e-7)
+    np.testing.assert_allclose(sup, ref["sup"], rtol=2e-2, atol=1e-5)
+
+
+@pytest.mark.parametrize("w,n_sub", [(W2, 48), (W3, 8)], ids=["rockets6-full", "rockets45-full"])
+def test_full_size_sampled_parity(w, n_sub):
+    """The benchmark's launch configuration at the workload's full size; a seeded subset of
+    states is recomputed by the oracle (same global indices, same draws)."""
+    x = hjg_inputs.points(w)
+    K = w.K if w.game != "rockets45" else 3
+    st0, st, r, sup, hist = run_gpu(w, x, w.N, K)
+    idx = hjg_inputs.subset_indices(w.M, n_sub, seed=11)
+    ref = oracle.picard(problem_for(w), x[idx].astype(np.float64), w.N, K, idx=idx)
+    assert_parity(st["v"][idx], st["p"][idx], ref["v"], ref["p"], what="full %s" % w.game)
+    assert np.all(np.isfinite(st["v"])) and np.all(np.isfinite(st["p"]))
+    assert np.all(np.isfinite(r)) and np.all(r >= 0)
+
+
+# ------------------------------------------------------------------------------ tests games
+def test_quadratic_exact_case_and_negative_c():
+    n = 3
+    A = hjg_inputs.spd_matrix(n, 0.3, 0.9, seed=3)
+    x0 = np.array([0.2, -0.1, 0.4]); d = 0.25
+    from paper_2605_18566_gb300 import Solver
+    x = hjg_inputs.random_states(301, n, 1.0, seed=5)
+    for h_sign in (1.0, -1.0):
+        s = Solver("quadratic", 0.1, 1.0, 3000, 3, n=n, A=A, x0=x0, d=d, h_sign=h_sign, eta=0.0)
+        s.set_points(torch.from_numpy(x).cuda())
+        r, _ = s.picard_sweep(3)
+        st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+        s.close()
+        P = oracle.make_problem("quadratic", n, 0.2, 1.0, A=A, x0=x0, d=d, h_sign=h_sign, eta=0.0)
+        ref = oracle.picard(P, x.astype(np.float64), 3000, 3)
+        assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="quadratic %+g" % h_sign)
+        np.testing.assert_allclose(st["c"], h_sign / 0.2, rtol=1e-6)
+
+
+def test_zero_hamiltonian_parity():
+    n = 2
+    A = np.array([[0.8, 0.1], [0.1, 0.5]])
+    from paper_2605_18566_gb300 import Solver
+    x = hjg_inputs.random_states(100, n, 1.0, seed=6)
+    s = Solver("zero_h", 0.1, 1.0, 5000, 2, n=n, A=A, d=0.1)
+    s.set_points(torch.from_numpy(x).cuda())
+    s.picard_sweep(2)
+    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    s.close()
+    P = oracle.make_problem("zero_h", n, 0.2, 1.0, A=A, d=0.1)
+    ref = oracle.picard(P, x.astype(np.float64), 5000, 2)
+    assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="zero_h")
+    np.testing.assert_allclose(st["c"], P.c_min, rtol=1e-6)
+
+
+# ------------------------------------------------------------------------------ edges
+@pytest.mark.parametrize("M,N,threads", [(1, 1, 0), (5, 31, 0), (17, 1000, 128),
+                                         (130, 777, 512), (3, 257, 256)])
+def test_ragged_sizes(M, N, threads):
+    w = W1
+    x = hjg_inputs.points(w)[7:7 + M].copy()
+    st0, st, r, sup, hist = run_gpu(w, x, N, 2, block_threads=threads)
+    ref = oracle.picard(problem_for(w), x.astype(np.float64), N, 2)
+    assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="M=%d N=%d" % (M, N))
+
+
+def test_strided_and_host_inputs():
+    w = W2
+    x = hjg_inputs.points(w, M=50)
+    wide = np.zeros((50, 11), np.float32); wide[:, :6] = x
+    s = solver_for(w, N=4096, K=2)
+    v1, g1, r1 = s.value_grad(torch.from_numpy(wide).cuda())          # ld = 11 on device
+    v2, g2, r2 = s.value_grad(torch.from_numpy(x))                      # host in, host out
+    s.close()
+    assert not v2.is_cuda
+    np.testing.assert_array_equal(v1.cpu().numpy(), v2.numpy())
+    np.testing.assert_array_equal(g1.cpu().numpy(), g2.numpy())
+    np.testing.assert_array_equal(r1, r2)
+    ref = oracle.picard(problem_for(w), x.astype(np.float64), 4096, 2)
+    assert_parity(v2.numpy(), g2.numpy(), ref["v"], ref["p"], what="host")
+
+
+def test_empty_and_zero_sweeps():
+    s = solver_for(W1, N=128, K=3)
+    s.set_points(torch.zeros(0, 3, device="cuda"))
+    r, sup = s.picard_sweep(3)
+    assert s.get_state()["v"].numel() == 0
+    x = torch.from_numpy(hjg_inputs.points(W1, M=9)).cuda()
+    s.set_points(x)
+    r0 = s.picard_sweep(0)
+    assert len(r0[0]) == 0
+    s.close()
+
+
+def test_resume_is_bit_exact_and_deterministic():
+    w = W2
+    x = torch.from_numpy(hjg_inputs.points(w, M=200)).cuda()
+    s = solver_for(w, N=8192, K=4)
+    s.set_points(x)
+    r_full, _ = s.picard_sweep(4)
+    full = s.get_state()
+    s.set_points(x)
+    r_a, _ = s.picard_sweep(2)
+    mid = s.get_state()
+    s.set_points(x)
+    s.set_state(v=mid["v"], p=mid["p"], c=mid["c"], next_sweep=2)
+    r_b, _ = s.picard_sweep(2)
+    res = s.get_state()
+    s.set_points(x)
+    r_again, _ = s.picard_sweep(4)
+    again = s.get_state()
+    s.close()
+    for key in ("v", "p", "c"):
+        assert torch.equal(full[key], res[key]), key
+        assert torch.equal(full[key], again[key]), key
+    np.testing.assert_array_equal(r_full[2:], r_b)
+    np.testing.assert_array_equal(r_full[:2], r_a)
+
+
+def test_value_grad_early_stop():
+    w = W1
+    x = torch.from_numpy(hjg_inputs.points(w, M=512)).cuda()
+    s = solver_for(w, N=2048, K=30, eps=1e30)    # any finite residual stops at once
+    v, g, r = s.value_grad(x)
+    s.close()
+    assert np.isfinite(r[0]) and np.all(np.isnan(r[1:]))
