@@ -229,15 +229,15 @@ def run_cpu_baseline(seconds_target=12.0, rank=0):
     import oracle
     x = hjg_inputs.points(W)
     P = oracle.make_problem(W.game, W.n, W.delta, W.T, radius=W.radius, seed=0)
-    # calibrate on a tiny sample, then size the timed sample to about seconds_target
-    t0 = time.perf_counter()
-    probe = 8
-    oracle.picard(P, x[:probe].astype(np.float64), W.N, 1)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    per_state_sweep = dt / probe
+    # calibrate: one sweep of one state per thread, then size the timed sample so that the
+    # full K-sweep solve takes about seconds_target of wall time on all host threads
     threads = oracle.num_threads()
-    m = int(max(threads, min(W.M, seconds_target / (per_state_sweep * W.K) * threads)))
-    m = max(threads, (m // threads) * threads)
+    probe = hjg_inputs.subset_indices(W.M, threads, seed=4)
+    t0 = time.perf_counter()
+    oracle.picard(P, x[probe].astype(np.float64), W.N, 1, idx=probe)
+    wall_per_state_sweep = max(time.perf_counter() - t0, 1e-4)   # per thread
+    m = int(seconds_target / (wall_per_state_sweep * W.K)) * threads
+    m = int(min(W.M, max(threads, m)))
     idx = hjg_inputs.subset_indices(W.M, m, seed=5)
     t0 = time.perf_counter()
     oracle.picard(P, x[idx].astype(np.float64), W.N, W.K, idx=idx)
@@ -247,6 +247,23 @@ def run_cpu_baseline(seconds_target=12.0, rank=0):
                       % (m, W.M, W.N, W.K, el)}
 
 
+def ncu_case(w):
+    """A small case of one workload for ncu: M = 4 x 152 states (a few MB on the device),
+    the workload's N, two sweeps per launch; one warm-up launch, then one profiled launch."""
+    import torch
+    from paper_2605_18566_gb300 import Solver
+    M = 4 * SMS
+    x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
+    s = Solver(w.game, w.nu, w.T, w.N, 2, radius=w.radius)
+    for _ in range(2):
+        s.set_points(x)
+        r, _ = s.picard_sweep(2)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": w.name, "M": M, "N": w.N, "K": 2,
+                      "sweep_ms": s.diagnostics()["last_ms"], "resid": list(r)}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,8 +271,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS),
+                    help="run one small launch of the named workload's sweep (profiling)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
+    if args.ncu_case:
+        ncu_case(hjg_inputs.WORKLOADS[args.ncu_case])
+        return
 
     if args.impl == "reference":
         if rank != 0:

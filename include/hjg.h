@@ -168,6 +168,22 @@ hjg_status hjg_philox_blocks(const uint32_t *ctr, const uint32_t *key, uint32_t 
 hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point,
                               uint32_t sweep, int64_t n_samples, float *out, void *stream);
 
+/* ---- pipe micro-benchmarks (roofline denominators) ------------------------------ */
+
+/* Instruction classes timed by hjg_microbench: FP32 FMA, the MUFU transcendental
+ * approximations (ex2, lg2, sin, cos, sqrt), whole Philox4x32-10 blocks, and whole
+ * Box-Muller normals as the sweep draws them. */
+enum {
+    HJG_MB_FFMA = 1, HJG_MB_EX2 = 2, HJG_MB_LG2 = 3, HJG_MB_SIN = 4, HJG_MB_COS = 5,
+    HJG_MB_SQRT = 6, HJG_MB_PHILOX = 7, HJG_MB_NORMALS = 8
+};
+
+/* Run one saturating launch (8 CTAs of 256 threads per SM, 8 independent chains per
+ * thread, `iters` steps per chain) of instruction class `op` on the current device and
+ * return its throughput in operations (or blocks, or normals) per second, and the launch
+ * time in ms.  Synchronises the device; EINVAL for an unknown op. */
+hjg_status hjg_microbench(int op, int64_t iters, double *ops_per_s, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

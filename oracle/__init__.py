@@ -69,11 +69,13 @@ def lib():
         L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
         L.orc_philox_batch.argtypes = [i64, P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
         L.orc_u01.argtypes = [u32]; L.orc_u01.restype = d
+        L.orc_slot_stride.argtypes = [i32]; L.orc_slot_stride.restype = i32
         L.orc_normals.argtypes = [i32, C.c_uint64, u32, u32, u32, u32, pd]
         L.orc_ell.argtypes = [P(Problem), pd, pd]; L.orc_ell.restype = d
         L.orc_grad_ell.argtypes = [P(Problem), pd, pd, pd]
         L.orc_hamiltonian.argtypes = [P(Problem), pd, pd, d]; L.orc_hamiltonian.restype = d
         L.orc_coef.argtypes = [P(Problem), pd, pd, d]; L.orc_coef.restype = d
+        L.orc_coef_batch.argtypes = [P(Problem), i64, pd, pd, pd, pd]
         pi64 = P(C.c_int64)
         L.orc_sweep.argtypes = [P(Problem), i64, pd, pd, pd, pd, pi64, i64, u32, pd, pd, pd]
         L.orc_sweep.restype = i32
@@ -154,6 +156,10 @@ def u01(x: int) -> float:
     return lib().orc_u01(int(x))
 
 
+def slot_stride(n: int) -> int:
+    return int(lib().orc_slot_stride(n))
+
+
 def normals(n, seed, instance, sample, point, sweep):
     z = np.zeros(n, dtype=np.float64)
     lib().orc_normals(n, seed, instance, sample, point, sweep, _dp(z))
@@ -180,6 +186,16 @@ def hamiltonian(P, x, p, psibar=0.0):
 
 def coef(P, x, p, psibar=0.0):
     return lib().orc_coef(C.byref(P), _dp(_f64(x)), _dp(_f64(p)), float(psibar))
+
+
+def coef_batch(P, x, p, psibar=None):
+    """Gamma at M states: x, p [M, n] -> c [M]."""
+    x = _f64(x).reshape(-1, P.n)
+    p = _f64(p).reshape(-1, P.n)
+    c = np.zeros(x.shape[0])
+    pb = _f64(psibar) if psibar is not None else None
+    lib().orc_coef_batch(C.byref(P), x.shape[0], _dp(x), _dp(p), _dp(pb), _dp(c))
+    return c
 
 
 # ---------------------------------------------------------------- method

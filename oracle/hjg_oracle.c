@@ -23,7 +23,7 @@
  *     built from the same per-agent dynamics, and quadratic test problems
  *     (H = +-|p|^2/2, the exact Cole-Hopf case of Corollary B.2).
  *   - Counter-based sampler: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), uniforms
- *     u = ((x>>9)+0.5) 2^-23, Box-Muller normals.
+ *     u = ((x & (2^23-1))+0.5) 2^-23, Box-Muller normals, packed per-sample slots.
  *
  * Everything is double precision except the Philox integer stream itself.
  * Pinned by tests/test_oracle_*.py (closed forms, quadrature, brute force, an
@@ -107,32 +107,57 @@ void orc_philox_batch(int64_t count, const uint32_t *ctr, const uint32_t *key, u
         orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
 }
 
-/* 23-bit uniform strictly inside (0,1): every value is exact in FP32 and FP64. */
+/* 23-bit uniform strictly inside (0,1) from the low 23 bits of a Philox word:
+ * u = ((x & (2^23-1)) + 0.5) 2^-23; every value is exact in FP32 and FP64. */
 double orc_u01(uint32_t x)
 {
-    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
+    return ((double)(x & 0x7FFFFFu) + 0.5) * (1.0 / 8388608.0);
 }
 
-/* Standard normals for one (sample, point, sweep): dims 4j..4j+3 come from the
- * Philox block with counter (sample, j, point, sweep) and key
- * (seed_lo, seed_hi ^ instance).  Box-Muller on (u0,u1) gives dims 4j, 4j+1
- * (radius from u0, angle from u1); (u2,u3) give dims 4j+2, 4j+3. */
+/* Slots per sample in the normal stream of one (state, sweep): n for n <= 8 (the normals
+ * of consecutive samples are packed back to back), n rounded up to a multiple of 4 above
+ * (each sample starts on a fresh Philox block). */
+int orc_slot_stride(int n)
+{
+    return n <= 8 ? n : (n + 3) / 4 * 4;
+}
+
+/* The four normals of Philox block b of the stream of (point, sweep): counter
+ * (b_lo, b_hi, point, sweep), key (seed_lo, seed_hi ^ instance).  Box-Muller on (u0,u1)
+ * gives slots 4b, 4b+1 (radius from u0, angle from u1); (u2,u3) give 4b+2, 4b+3. */
+static void block_normals(uint64_t seed, uint32_t instance, uint64_t b, uint32_t point,
+                          uint32_t sweep, double zz[4])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance};
+    uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), point, sweep};
+    uint32_t r[4];
+    const double two_pi = 6.283185307179586476925286766559;
+    orc_philox4x32_10(ctr, key, r);
+    double u[4];
+    for (int q = 0; q < 4; ++q) u[q] = orc_u01(r[q]);
+    double ra = sqrt(-2.0 * log(u[0]));
+    double rb = sqrt(-2.0 * log(u[2]));
+    zz[0] = ra * cos(two_pi * u[1]);
+    zz[1] = ra * sin(two_pi * u[1]);
+    zz[2] = rb * cos(two_pi * u[3]);
+    zz[3] = rb * sin(two_pi * u[3]);
+}
+
+/* Standard normals z[0..n) of sample `sample` of state `point` in sweep `sweep`: slot
+ * q = sample * orc_slot_stride(n) + d of the stream, i.e. lane q % 4 of block q / 4. */
 void orc_normals(int n, uint64_t seed, uint32_t instance, uint32_t sample,
                  uint32_t point, uint32_t sweep, double *z)
 {
-    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance};
-    const double two_pi = 6.283185307179586476925286766559;
-    for (int j = 0; 4 * j < n; ++j) {
-        uint32_t ctr[4] = {sample, (uint32_t)j, point, sweep};
-        uint32_t r[4];
-        orc_philox4x32_10(ctr, key, r);
-        double u[4];
-        for (int q = 0; q < 4; ++q) u[q] = orc_u01(r[q]);
-        double ra = sqrt(-2.0 * log(u[0]));
-        double rb = sqrt(-2.0 * log(u[2]));
-        double zz[4] = {ra * cos(two_pi * u[1]), ra * sin(two_pi * u[1]),
-                        rb * cos(two_pi * u[3]), rb * sin(two_pi * u[3])};
-        for (int q = 0; q < 4 && 4 * j + q < n; ++q) z[4 * j + q] = zz[q];
+    uint64_t q0 = (uint64_t)sample * (uint64_t)orc_slot_stride(n);
+    uint64_t cached = UINT64_MAX;
+    double zz[4] = {0, 0, 0, 0};
+    for (int d = 0; d < n; ++d) {
+        uint64_t q = q0 + (uint64_t)d;
+        if ((q >> 2) != cached) {
+            cached = q >> 2;
+            block_normals(seed, instance, cached, point, sweep, zz);
+        }
+        z[d] = zz[q & 3];
     }
 }
 
@@ -395,6 +420,14 @@ void orc_init(const orc_problem *P, int64_t M, const double *x, const double *nb
         orc_grad_ell(P, x + m * n, nb, p0 + m * n);
         c0[m] = orc_coef(P, x + m * n, p0 + m * n, pb);
     }
+}
+
+/* Gamma applied to M states (p rows of n), for checking a coefficient update. */
+void orc_coef_batch(const orc_problem *P, int64_t M, const double *x, const double *p,
+                    const double *psibar, double *c)
+{
+    for (int64_t m = 0; m < M; ++m)
+        c[m] = orc_coef(P, x + m * P->n, p + m * P->n, psibar ? psibar[m] : 0.0);
 }
 
 /* Relative L2 change ||v1 - v0|| / ||v0|| and sup-norm change (Algorithm 1, last step). */

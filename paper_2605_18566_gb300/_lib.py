@@ -60,7 +60,12 @@ _SIGS = {
     "hjg_philox_blocks": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
     "hjg_sample_normals": (C.c_int, [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                      C.c_int64, _vp, _vp]),
+    "hjg_microbench": (C.c_int, [C.c_int, C.c_int64, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
 }
+
+MICROBENCH = {"ffma": 1, "ex2": 2, "lg2": 3, "sin": 4, "cos": 5, "sqrt": 6, "philox": 7,
+              "normals": 8}
 
 _lib = None
 

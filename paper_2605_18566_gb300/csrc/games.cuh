@@ -54,6 +54,12 @@ struct Dubins3 {
         sincos(x[2], &s, &c);
         return p[0] * (c - 1.0) + p[1] * s + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
     }
+    // Per-state trigonometric cache of H (computed once per state, one value per thread).
+    static constexpr int kCache = 2;
+    __device__ static double cache(const double* x, int j) { return j == 0 ? cos(x[2]) : sin(x[2]); }
+    __device__ static double ham_c(const double* x, const double* hc, const double* p, const GameParams&) {
+        return p[0] * (hc[0] - 1.0) + p[1] * hc[1] + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
+    }
 };
 
 // ---------------------------------------------------------------- two rockets
@@ -80,6 +86,15 @@ struct Rockets6 {
         sincos(x[4], &sA, &cA);
         sincos(x[5], &sB, &cB);
         return g.speed_d[0] * (p[0] * cA + p[1] * sA) + g.speed_d[1] * (p[2] * cB + p[3] * sB)
+             + fabs(p[4]) - fabs(p[5]);
+    }
+    static constexpr int kCache = 4;   // cos thA, sin thA, cos thB, sin thB
+    __device__ static double cache(const double* x, int j) {
+        const double a = x[4 + (j >> 1)];
+        return (j & 1) ? sin(a) : cos(a);
+    }
+    __device__ static double ham_c(const double*, const double* hc, const double* p, const GameParams& g) {
+        return g.speed_d[0] * (p[0] * hc[0] + p[1] * hc[1]) + g.speed_d[1] * (p[2] * hc[2] + p[3] * hc[3])
              + fabs(p[4]) - fabs(p[5]);
     }
 };
@@ -124,6 +139,17 @@ struct Rockets45 {
         for (int i = 0; i < 14; ++i) h -= fabs(p[3 * i + 2]);
         return h;
     }
+    static constexpr int kCache = 30;  // cos th_i, sin th_i for the 15 agents
+    __device__ static double cache(const double* x, int j) {
+        const double a = x[3 * (j >> 1) + 2];
+        return (j & 1) ? sin(a) : cos(a);
+    }
+    __device__ static double ham_c(const double*, const double* hc, const double* p, const GameParams& g) {
+        double h = fabs(p[44]);
+        for (int i = 0; i < 15; ++i) h += g.speed_d[i] * (p[3 * i] * hc[2 * i] + p[3 * i + 1] * hc[2 * i + 1]);
+        for (int i = 0; i < 14; ++i) h -= fabs(p[3 * i + 2]);
+        return h;
+    }
 };
 
 // ---------------------------------------------------------------- quadratic tests
@@ -164,6 +190,11 @@ struct Quadratic {
         double s = 0.0;
         for (int a = 0; a < NDIM; ++a) s += p[a] * p[a];
         return g.h_sign_d * 0.5 * s;
+    }
+    static constexpr int kCache = 0;
+    __device__ static double cache(const double*, int) { return 0.0; }
+    __device__ static double ham_c(const double* x, const double*, const double* p, const GameParams& g) {
+        return ham_d(x, p, g);
     }
 };
 

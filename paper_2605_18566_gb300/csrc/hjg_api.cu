@@ -127,15 +127,22 @@ __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, const uin
     out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
 }
 
-// The same normals the sweep draws (draw_normals with all four kept), sample i per thread.
+// The normals the sweep draws for samples 0..ns-1 of (point, sweep): sample i, dim d is
+// slot i * slot_stride(n) + d of the stream, i.e. lane (slot % 4) of block slot / 4.
 __global__ void normals_kernel(int n, uint32_t k0, uint32_t k1, uint32_t point, uint32_t sweep,
                                int64_t ns, float* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
-    for (int q = 0; 4 * q < n; ++q) {
-        float z[4];
-        draw_normals<1, 4>((uint32_t)i, (uint32_t)q, point, sweep, k0, k1, z);
-        for (int j = 0; j < 4 && 4 * q + j < n; ++j) out[i * n + 4 * q + j] = z[j];
+    const uint64_t q0 = (uint64_t)i * (uint64_t)slot_stride(n);
+    uint64_t cached = ~0ull;
+    float z[4];
+    for (int d = 0; d < n; ++d) {
+        const uint64_t q = q0 + (uint64_t)d;
+        if ((q >> 2) != cached) {
+            cached = q >> 2;
+            block_normals<4>((uint32_t)cached, point, sweep, k0, k1, z);
+        }
+        out[i * n + d] = z[q & 3];
     }
 }
 
@@ -507,7 +514,7 @@ hjg_status hjg_philox_blocks(const uint32_t* ctr, const uint32_t* key, uint32_t*
 
 hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point, uint32_t sweep,
                               int64_t n_samples, float* out, void* stream) {
-    if (n < 1 || n > 64 || n_samples < 0 || n_samples > 0xFFFFFFFFll || (n_samples > 0 && !out))
+    if (n < 1 || n > 64 || n_samples < 0 || n_samples > 0x3FFFFFFll || (n_samples > 0 && !out))
         return HJG_EINVAL;
     if (n_samples == 0) return HJG_OK;
     const int T = 256;

@@ -1,0 +1,110 @@
+// microbench.cu -- pipe-throughput micro-benchmarks used to put the sweep kernel on an
+// ALU roofline: the sweep moves almost no bytes per sample, so its ceiling is the issue
+// rate of the FP32 (FMA), integer and MUFU (transcendental) pipes.  Each kernel runs
+// ILP independent dependency chains per thread of one instruction class.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/hjg.h"
+#include "sampler.cuh"
+
+namespace {
+
+constexpr int kIlp = 8;
+constexpr int kThreads = 256;
+
+template <int OP>
+__device__ __forceinline__ float step(float x) {
+    if (OP == HJG_MB_FFMA) return fmaf(x, 0.9999f, 0.0001f);
+    if (OP == HJG_MB_EX2) return hjg::ex2_approx(-x);
+    if (OP == HJG_MB_LG2) return hjg::lg2_approx(fabsf(x) + 1.0f);
+    if (OP == HJG_MB_SIN) return hjg::sin_approx(x);
+    if (OP == HJG_MB_COS) return hjg::cos_approx(x);
+    if (OP == HJG_MB_SQRT) return hjg::sqrt_approx(x);
+    return x;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) float_pipe(int64_t iters, float* sink) {
+    float x[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) x[j] = 0.25f + 0.01f * (threadIdx.x + j);
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) x[j] = step<OP>(x[j]);
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) acc += x[j];
+    if (acc == 1234.5f) sink[threadIdx.x] = acc;   // keeps the chains live
+}
+
+// Philox4x32-10 blocks (the sampler's integer work: IMAD.WIDE and LOP3).
+__global__ void __launch_bounds__(kThreads) philox_pipe(int64_t iters, float* sink) {
+    uint32_t acc = 0;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = 0; i < iters; ++i) {
+        const uint4 r = hjg::philox4x32_10(make_uint4((uint32_t)i, t, 7u, 9u), 0x1234u, 0x5678u);
+        acc ^= r.x ^ r.y ^ r.z ^ r.w;
+    }
+    if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
+}
+
+// Full Box-Muller normals from Philox blocks, as the sweep draws them (4 per block).
+__global__ void __launch_bounds__(kThreads) normals_pipe(int64_t iters, float* sink) {
+    float acc = 0.0f;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = 0; i < iters; ++i) {
+        float z[4];
+        hjg::block_normals<4>((uint32_t)i, t, 3u, 0x1234u, 0x5678u, z);
+        acc += z[0] + z[1] + z[2] + z[3];
+    }
+    if (acc == 1234.5f) sink[threadIdx.x] = acc;
+}
+
+}  // namespace
+
+extern "C" hjg_status hjg_microbench(int op, int64_t iters, double* ops_per_s, double* ms) {
+    if (!ops_per_s || iters < 1) return HJG_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HJG_ECUDA;
+    float* sink = nullptr;
+    if (cudaMalloc(&sink, kThreads * sizeof(float)) != cudaSuccess) return HJG_ENOMEM;
+    const int grid = sms * 8;
+    double per_thread_iter = kIlp;
+    auto launch = [&]() {
+        switch (op) {
+        case HJG_MB_FFMA: float_pipe<HJG_MB_FFMA><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_EX2: float_pipe<HJG_MB_EX2><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_LG2: float_pipe<HJG_MB_LG2><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_SIN: float_pipe<HJG_MB_SIN><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_COS: float_pipe<HJG_MB_COS><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_SQRT: float_pipe<HJG_MB_SQRT><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_PHILOX: philox_pipe<<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_NORMALS: normals_pipe<<<grid, kThreads>>>(iters, sink); break;
+        }
+    };
+    if (op == HJG_MB_PHILOX) per_thread_iter = 1.0;   // Philox blocks
+    if (op == HJG_MB_NORMALS) per_thread_iter = 4.0;  // normals
+    if (op < HJG_MB_FFMA || op > HJG_MB_NORMALS) { cudaFree(sink); return HJG_EINVAL; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch();   // warm-up
+    cudaEventRecord(e0);
+    launch();
+    cudaEventRecord(e1);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (err != cudaSuccess || cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+    *ops_per_s = (double)grid * kThreads * (double)iters * per_thread_iter / (t * 1e-3);
+    if (ms) *ms = t;
+    return HJG_OK;
+}

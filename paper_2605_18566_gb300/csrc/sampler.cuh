@@ -1,9 +1,14 @@
 // sampler.cuh -- in-register counter-based Gaussian sampler for the Picard sweep.
 //
-// Sample i of evaluation state m in sweep k, dims 4j..4j+3, is drawn from one
-// Philox4x32-10 block (Salmon et al., SC'11) with counter (i, j, m, k) and key
-// (seed_lo, seed_hi ^ instance).  Nothing is written to memory: the heat-kernel
-// expectation of Prop. 2.1 / Cor. B.4 consumes each draw where it is made.
+// For each (state m, sweep k) the sampler defines one stream of standard normals: slot q
+// is lane q % 4 of Philox4x32-10 block b = q / 4, drawn with counter (b_lo, b_hi, m, k)
+// and key (seed_lo, seed_hi ^ instance) (Philox: Salmon et al., SC'11).  Within a block,
+// Box-Muller on (u0, u1) gives slots 4b, 4b+1 (radius from u0, angle from u1) and (u2, u3)
+// gives 4b+2, 4b+3, with u = ((r & (2^23-1)) + 0.5) 2^-23.  Sample i of a game with n
+// state dimensions reads slots i*S .. i*S + n - 1, S = n for n <= 8 (consecutive samples
+// packed back to back, so every Philox output is used) and S = n rounded up to a multiple
+// of 4 above.  Nothing is written to memory: the heat-kernel expectation of Prop. 2.1 /
+// Cor. B.4 consumes each draw where it is made.
 #pragma once
 #include <cstdint>
 
@@ -46,55 +51,54 @@ __device__ __forceinline__ float cos_approx(float x) {
     float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y;
 }
 
-// The 23 high bits of r as a float in [1, 2): 1 + (r >> 9) 2^-23 (exact).
+// The low 23 bits of r as a float in [1, 2): 1 + (r & (2^23-1)) 2^-23 (exact, one LOP3).
 __device__ __forceinline__ float mant_one_two(uint32_t r) {
-    return __uint_as_float((r >> 9) | 0x3F800000u);
+    return __uint_as_float((r & 0x007FFFFFu) | 0x3F800000u);
 }
 
-// u = ((r >> 9) + 0.5) 2^-23, exactly (the sum below is exact in binary32).
+// u = ((r & (2^23-1)) + 0.5) 2^-23, exactly (the sum below is exact in binary32).
 __device__ __forceinline__ float u01(uint32_t r) {
     return mant_one_two(r) + (-1.0f + 0x1.0p-24f);
 }
 
-// Box-Muller radius sqrt(-2 ln u) from the radius word.
+// Box-Muller radius sqrt(-2 ln u) from the radius word.  Near u = 1 the approximate log2
+// may come out as a tiny positive number; the magnitude is taken (the radius is ~0 there).
 __device__ __forceinline__ float bm_radius(uint32_t r) {
-    const float u = u01(r);
-    // -2 ln u = -2 ln2 * log2 u; clamp: near u = 1 the approximate log2 may cross 0.
-    const float t = fmaxf(-1.3862943611198906f * lg2_approx(u), 0.0f);
-    return sqrt_approx(t);
+    const float t = -1.3862943611198906f * lg2_approx(u01(r));
+    return sqrt_approx(fabsf(t));
 }
 
-// Box-Muller angle: returns phi = 2 pi (u - 1/2) in (-pi, pi); the pair is
-// (r cos 2 pi u, r sin 2 pi u) = (-r cos phi, -r sin phi).
+// Box-Muller phase phi = 2 pi u - pi in (-pi, pi), one FMA from the mantissa float f = u + 1
+// - 2^-24; the pair is (r cos 2 pi u, r sin 2 pi u) = (-r cos phi, -r sin phi).
 __device__ __forceinline__ float bm_phase(uint32_t r) {
-    const float t = (mant_one_two(r) - 1.5f) + 0x1.0p-24f;   // u - 1/2, exact
-    return t * 6.283185307179586f;
+    return fmaf(mant_one_two(r), 6.283185307179586f, -9.42477798461914f);
 }
 
-// Standard normals of dims [4*q0, 4*q0 + 4*NQ) for one sample, keeping only the first
-// NUSE of them (the rest are never computed).
-template <int NQ, int NUSE>
-__device__ __forceinline__ void draw_normals(uint32_t sample, uint32_t q0, uint32_t point,
-                                             uint32_t sweep, uint32_t k0, uint32_t k1,
-                                             float* z) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int b = 4 * q;
-        if (b >= NUSE) break;
-        const uint4 r = philox4x32_10(make_uint4(sample, q0 + q, point, sweep), k0, k1);
-        {
-            const float ra = bm_radius(r.x);
-            const float ph = bm_phase(r.y);
-            z[b] = -ra * cos_approx(ph);
-            if (b + 1 < NUSE) z[b + 1] = -ra * sin_approx(ph);
-        }
-        if (b + 2 < NUSE) {
-            const float rb = bm_radius(r.z);
-            const float ph = bm_phase(r.w);
-            z[b + 2] = -rb * cos_approx(ph);
-            if (b + 3 < NUSE) z[b + 3] = -rb * sin_approx(ph);
-        }
+// The first NUSE (1..4) normals of block b of the (point, sweep) stream.
+template <int NUSE>
+__device__ __forceinline__ void block_normals(uint32_t b, uint32_t point, uint32_t sweep,
+                                              uint32_t k0, uint32_t k1, float* z) {
+    const uint4 r = philox4x32_10(make_uint4(b, 0u, point, sweep), k0, k1);
+    {
+        const float ra = bm_radius(r.x);
+        const float ph = bm_phase(r.y);
+        z[0] = -ra * cos_approx(ph);
+        if (NUSE > 1) z[1] = -ra * sin_approx(ph);
     }
+    if (NUSE > 2) {
+        const float rb = bm_radius(r.z);
+        const float ph = bm_phase(r.w);
+        z[2] = -rb * cos_approx(ph);
+        if (NUSE > 3) z[3] = -rb * sin_approx(ph);
+    }
+}
+
+// Slots per sample and the sample grouping that makes a group end on a block boundary.
+__host__ __device__ constexpr int slot_stride(int n) { return n <= 8 ? n : (n + 3) / 4 * 4; }
+__host__ __device__ constexpr int gcd4(int a) { return (a % 4 == 0) ? 4 : (a % 2 == 0 ? 2 : 1); }
+__host__ __device__ constexpr int group_samples(int n) { return 4 / gcd4(slot_stride(n)); }
+__host__ __device__ constexpr int group_blocks(int n) {
+    return group_samples(n) * slot_stride(n) / 4;
 }
 
 }  // namespace hjg

@@ -1,9 +1,9 @@
 // sweep_impl.cuh -- the fused frozen-coefficient Picard sweep (Algorithm 1) on sm_103a.
 //
 // One CTA owns one evaluation state at a time and runs all requested sweeps for it:
-// states are independent (c_m depends only on Dv at x_m, Theorem 2.8's map Gamma acts
+// states are independent (c_m depends only on Dv at x_m; the map Gamma of Theorem 2.8 acts
 // pointwise), so no grid-wide synchronisation is ever needed.  Per sweep:
-//   a2  sampler    Philox4x32-10 -> uniforms -> Box-Muller, in registers
+//   a2  sampler    Philox4x32-10 -> uniforms -> Box-Muller, in registers (sampler.cuh)
 //   a3  payoff     y = x + theta + sigma z, a = -c l(y) - <z, theta>/sigma   (base 2)
 //   a4  LSE        running shift m, s = sum 2^(a-m), S_j = sum 2^(a-m) z_j, Q = sum 2^(2(a-m))
 //   a5  merge      warp shuffle (FP32) -> shared-memory block combine in FP64
@@ -93,126 +93,147 @@ __device__ __forceinline__ void warp_merge(int lo, float& m, float& s, float& q,
 }
 
 // Shared-memory state of one CTA.
-template <int NPAD, int W>
+template <int NPAD, int W, int NC>
 struct SweepShared {
     double x[NPAD];       // state in FP64
-    double S[NPAD];       // combined weighted normal sums (FP64)
+    double pd[NPAD];      // Dv of the sweep just finished (FP64)
+    double hc[NC > 0 ? NC : 1];  // per-state trigonometric cache of H
+    double fw[W];         // block-combine factors 2^(m_w - max)
     double s, q, mx;      // combined sums and shift
     float xf[NPAD];       // state in FP32
+    float p_cur[NPAD];    // Dv iterate in FP32 (the stored precision)
     float yoff[NPAD];     // x + theta (FP32), the sample mean
     float tq[NPAD];       // -theta_j log2e / sigma (tilt log-weight slope)
     float theta[NPAD];
     float cneg2;          // -c log2e
     float c;
-    double thconst;       // -|theta|^2 / (2 sigma^2)
     float red_m[W], red_s[W], red_q[W];
     float red_S[W][NPAD];
 };
 
-// FP64 combine of the per-warp partials; threads tid < n each own one S_j.
-template <int NPAD, int W>
-__device__ __forceinline__ void block_combine(SweepShared<NPAD, W>& sh, int n, int tid) {
-    double Mx = -INFINITY;
+// Load state pt into shared memory (threads < NPAD) and its trigonometric cache.
+template <class G, int NPAD, int W, int NC>
+__device__ __forceinline__ void load_state(SweepShared<NPAD, W, NC>& sh, const SweepArgs& A,
+                                           int64_t pt, int tid) {
+    constexpr int n = G::kN;
+    if (tid < NPAD) {
+        const float xv = tid < n ? A.x[pt * A.ldx + tid] : 0.0f;
+        sh.xf[tid] = xv;
+        sh.x[tid] = (double)xv;
+        sh.p_cur[tid] = tid < n ? A.p[pt * A.ldp + tid] : 0.0f;
+    }
+    if (tid == 0) {
+        if (A.vhist) A.vhist[pt] = A.v[pt];
+        sh.c = A.c[pt];
+        sh.cneg2 = -sh.c * kLog2e;
+    }
+    __syncthreads();
+    if (NC > 0 && tid < NC) sh.hc[tid] = G::cache(sh.x, tid);
+}
+
+// theta = -sigma^2 c p (Eq. tilt_shift) for the coming sweep and the FP32 constants the
+// sample loop needs (threads < NPAD).
+template <int NPAD, int W, int NC, bool TILT>
+__device__ __forceinline__ void prepare_sweep(SweepShared<NPAD, W, NC>& sh, const SweepArgs& A,
+                                              int n, int tid) {
+    if (tid < NPAD) {
+        float th = 0.0f;
+        if (TILT && tid < n) th = (float)(-A.sigma2_d * (double)sh.c * (double)sh.p_cur[tid]);
+        sh.theta[tid] = th;
+        sh.yoff[tid] = sh.xf[tid] + th;
+        sh.tq[tid] = -th * kLog2e / A.sigma;
+    }
+}
+
+// Block combine of the per-warp partials in FP64, recovery of v, Dv, ESS and the
+// coefficient update.  Must be entered by all threads right after the partials are
+// written; ends synchronised.
+template <class G, int NPAD, int W, int NC, bool TILT>
+__device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const SweepArgs& A,
+                                             int64_t pt, int k, int tid) {
+    constexpr int n = G::kN;
+    const bool last = (k + 1 == A.K);
+    __syncthreads();
+    if (tid < W) {
+        double Mx = -INFINITY;
 #pragma unroll
-    for (int w = 0; w < W; ++w) Mx = fmax(Mx, (double)sh.red_m[w]);
-    if (tid < n || tid == n) {
-        double acc = 0.0, acc_q = 0.0;
+        for (int w = 0; w < W; ++w) Mx = fmax(Mx, (double)sh.red_m[w]);
+        sh.fw[tid] = (sh.red_m[tid] == -INFINITY) ? 0.0 : exp2((double)sh.red_m[tid] - Mx);
+        if (tid == 0) sh.mx = Mx;
+    }
+    __syncthreads();
+    const double c = (double)sh.c;
+    if (tid < n) {
+        double s = 0.0, Sj = 0.0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const double f = (sh.red_m[w] == -INFINITY) ? 0.0 : exp2((double)sh.red_m[w] - Mx);
-            if (tid < n) {
-                acc += f * (double)sh.red_S[w][tid];
-            } else {
-                acc += f * (double)sh.red_s[w];
-                acc_q += f * f * (double)sh.red_q[w];
-            }
+            s = fma(sh.fw[w], (double)sh.red_s[w], s);
+            Sj = fma(sh.fw[w], (double)sh.red_S[w][tid], Sj);
         }
-        if (tid < n) {
-            sh.S[tid] = acc;
-        } else {
-            sh.s = acc;
-            sh.q = acc_q;
-            sh.mx = Mx;
+        const double pj = -((double)sh.theta[tid] + A.sigma_d * Sj / s) / (c * A.sigma2_d);
+        sh.pd[tid] = pj;
+        sh.p_cur[tid] = (float)pj;
+        if (last) A.p[pt * A.ldp + tid] = (float)pj;
+        if (tid == 0) {
+            double q = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) q = fma(sh.fw[w] * sh.fw[w], (double)sh.red_q[w], q);
+            sh.s = s;
+            sh.q = q;
         }
     }
-}
-
-// Per-state set-up for a sweep: theta from the current (c, p) when tilting, and the
-// FP32 constants the sample loop needs.  Thread 0 only.
-template <int NPAD, int W, bool TILT>
-__device__ __forceinline__ void prepare_sweep(SweepShared<NPAD, W>& sh, const SweepArgs& A,
-                                              int n, float c, const float* p_cur) {
-    sh.c = c;
-    sh.cneg2 = -c * kLog2e;
-    double th2 = 0.0;
-    for (int j = 0; j < NPAD; ++j) {
-        float th = 0.0f;
-        if (TILT && j < n) th = (float)(-A.sigma2_d * (double)c * (double)p_cur[j]);
-        sh.theta[j] = th;
-        sh.yoff[j] = sh.xf[j] + th;
-        sh.tq[j] = -th * kLog2e / A.sigma;
-        th2 += (double)th * (double)th;
+    __syncthreads();
+    if (tid == 0) {
+        double th2 = 0.0, pp = 0.0;
+        bool finite = true;
+        for (int j = 0; j < n; ++j) {
+            th2 += (double)sh.theta[j] * (double)sh.theta[j];
+            pp += sh.pd[j] * sh.pd[j];
+            finite = finite && isfinite(sh.pd[j]);
+        }
+        const double s = sh.s;
+        const double logmean = sh.mx * kLn2 - th2 / (2.0 * A.sigma2_d) + log(s / (double)A.N);
+        const double v = -logmean / c;
+        finite = finite && isfinite(v);
+        const double h = G::ham_c(sh.x, sh.hc, sh.pd, A.g);
+        int clipped = 0;
+        const float c_new = (float)coef_update(h, pp, A.delta, A.eta, A.c_min, A.c_max, &clipped);
+        if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
+        if (last) {
+            A.v[pt] = v;
+            A.c[pt] = c_new;
+            A.ess[pt] = (float)(s * s / sh.q);
+            if (!finite) atomicAdd(&A.counters[0], 1ull);
+            if (clipped) atomicAdd(&A.counters[1], 1ull);
+        }
+        sh.c = c_new;
+        sh.cneg2 = -c_new * kLog2e;
     }
-    sh.thconst = -th2 / (2.0 * A.sigma2_d);
-}
-
-// Recover v, Dv, ESS from the combined sums, update c (thread 0).  Writes outputs and
-// returns the new (c, p) through shared memory for the next sweep.
-template <class G, int NPAD, int W>
-__device__ __forceinline__ void recover_and_update(SweepShared<NPAD, W>& sh, const SweepArgs& A,
-                                                   int64_t pt, int k, bool last, float* p_cur) {
-    constexpr int n = G::kN;
-    const double c = (double)sh.c;
-    const double s = sh.s;
-    const double logmean = sh.mx * kLn2 + sh.thconst + log(s / (double)A.N);
-    const double v = -logmean / c;
-    double pd[n];
-    double pp = 0.0;
-    bool finite = isfinite(v);
-    for (int j = 0; j < n; ++j) {
-        pd[j] = -((double)sh.theta[j] + A.sigma_d * sh.S[j] / s) / (c * A.sigma2_d);
-        pp += pd[j] * pd[j];
-        finite = finite && isfinite(pd[j]);
-    }
-    const double h = G::ham_d(sh.x, pd, A.g);
-    int clipped = 0;
-    const double c_new = coef_update(h, pp, A.delta, A.eta, A.c_min, A.c_max, &clipped);
-    const float c_new_f = (float)c_new;
-    for (int j = 0; j < n; ++j) p_cur[j] = (float)pd[j];
-    if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
-    if (last) {
-        A.v[pt] = v;
-        A.c[pt] = c_new_f;
-        A.ess[pt] = (float)(s * s / sh.q);
-        for (int j = 0; j < n; ++j) A.p[pt * A.ldp + j] = p_cur[j];
-        if (!finite) atomicAdd(&A.counters[0], 1ull);
-        if (clipped) atomicAdd(&A.counters[1], 1ull);
-    }
-    sh.c = c_new_f;
+    __syncthreads();
+    if (!last) prepare_sweep<NPAD, W, NC, TILT>(sh, A, n, tid);
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------------------------
-// One lane per sample stream (games with n <= 8).
+// One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
+// g = group_samples(n) that end on a Philox block boundary (n = 3: 4 samples from 3 blocks;
+// n = 6: 2 samples from 3 blocks), so every normal drawn is used.
 template <class G, int THREADS, bool TILT>
 __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
-    constexpr int NQ = (n + 3) / 4;
-    constexpr int NPAD = 4 * NQ;
+    constexpr int NPAD = (n + 3) / 4 * 4;
     constexpr int W = THREADS / 32;
-    __shared__ SweepShared<NPAD, W> sh;
-    __shared__ float p_cur[NPAD];
+    constexpr int GS = group_samples(n);
+    constexpr int GB = group_blocks(n);
+    __shared__ SweepShared<NPAD, W, G::kCache> sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t N32 = (uint32_t)A.N;
+    const uint32_t groups = (N32 + GS - 1) / GS;
 
     for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
-        if (tid < NPAD) {
-            const float xv = tid < n ? A.x[pt * A.ldx + tid] : 0.0f;
-            sh.xf[tid] = xv;
-            sh.x[tid] = (double)xv;
-            p_cur[tid] = tid < n ? A.p[pt * A.ldp + tid] : 0.0f;
-        }
-        if (tid == 0 && A.vhist) A.vhist[pt] = A.v[pt];
+        load_state<G, NPAD, W, G::kCache>(sh, A, pt, tid);
         __syncthreads();
-        if (tid == 0) prepare_sweep<NPAD, W, TILT>(sh, A, n, A.c[pt], p_cur);
+        prepare_sweep<NPAD, W, G::kCache, TILT>(sh, A, n, tid);
         __syncthreads();
 
         for (int k = 0; k < A.K; ++k) {
@@ -225,19 +246,26 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
 #pragma unroll
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
 
-            const uint32_t N32 = (uint32_t)A.N;
-            for (uint32_t i = tid; i < N32; i += THREADS) {
-                float z[NPAD];
-                draw_normals<NQ, n>(i, 0u, (uint32_t)pt, sweep, A.key0, A.key1, z);
-                float y[n];
+            for (uint32_t grp = tid; grp < groups; grp += THREADS) {
+                float z[4 * GB];
 #pragma unroll
-                for (int j = 0; j < n; ++j) y[j] = fmaf(A.sigma, z[j], yoff[j]);
-                float a = cneg2 * G::ell(y, A.g);
-                if (TILT) {
+                for (int b = 0; b < GB; ++b)
+                    block_normals<4>(grp * GB + b, (uint32_t)pt, sweep, A.key0, A.key1, z + 4 * b);
+                const uint32_t left = N32 - grp * GS;   // samples of this group inside N
 #pragma unroll
-                    for (int j = 0; j < n; ++j) a = fmaf(z[j], tq[j], a);
+                for (int t = 0; t < GS; ++t) {
+                    if (GS > 1 && (uint32_t)t >= left) break;
+                    const float* zt = z + t * n;
+                    float y[n];
+#pragma unroll
+                    for (int j = 0; j < n; ++j) y[j] = fmaf(A.sigma, zt[j], yoff[j]);
+                    float a = cneg2 * G::ell(y, A.g);
+                    if (TILT) {
+#pragma unroll
+                        for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
+                    }
+                    lse_accumulate<n>(a, zt, m, s, q, S);
                 }
-                lse_accumulate<n>(a, z, m, s, q, S);
             }
 
             warp_merge<n>(1, m, s, q, S);
@@ -246,25 +274,18 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
 #pragma unroll
                 for (int j = 0; j < n; ++j) sh.red_S[warp][j] = S[j];
             }
-            __syncthreads();
-            block_combine<NPAD, W>(sh, n, tid);
-            __syncthreads();
-            if (tid == 0) {
-                recover_and_update<G, NPAD, W>(sh, A, pt, k, k + 1 == A.K, p_cur);
-                prepare_sweep<NPAD, W, TILT>(sh, A, n, sh.c, p_cur);
-            }
-            __syncthreads();
+            finish_sweep<G, NPAD, W, G::kCache, TILT>(sh, A, pt, k, tid);
         }
     }
 }
 
 // ------------------------------------------------------------------------------------
 // 45-D multi-rocket game: four lanes per sample stream.  Lane q of a group owns dims
-// 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. Philox blocks 3q..3q+2.
-// The evader (agent 14, dims 42..44) sits on lane 3; its position is broadcast, each lane
-// takes the minimum squared distance over its own pursuers, and two shuffles finish the
-// group minimum.  All four lanes then hold the same log-weight and accumulate their own
-// twelve S_j.
+// 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. blocks 12 i + 3q + j of the
+// stream.  The evader (agent 14, dims 42..44) sits on lane 3; its position is broadcast,
+// each lane takes the minimum squared distance over its own pursuers, and two shuffles
+// finish the group minimum.  All four lanes then hold the same log-weight and accumulate
+// their own twelve S_j.
 template <int THREADS, bool TILT>
 __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
     using G = Rockets45;
@@ -272,24 +293,18 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
     constexpr int NPAD = 48;
     constexpr int W = THREADS / 32;
     constexpr int GROUPS = THREADS / 4;
-    __shared__ SweepShared<NPAD, W> sh;
-    __shared__ float p_cur[NPAD];
+    __shared__ SweepShared<NPAD, W, G::kCache> sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q4 = lane & 3;
     const int grp = tid >> 2;
     const int src3 = (lane & ~3) | 3;
     const int nag = (q4 == 3) ? 2 : 4;   // pursuers owned by this lane
+    const uint32_t N32 = (uint32_t)A.N;
 
     for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
-        if (tid < NPAD) {
-            const float xv = tid < n ? A.x[pt * A.ldx + tid] : 0.0f;
-            sh.xf[tid] = xv;
-            sh.x[tid] = (double)xv;
-            p_cur[tid] = tid < n ? A.p[pt * A.ldp + tid] : 0.0f;
-        }
-        if (tid == 0 && A.vhist) A.vhist[pt] = A.v[pt];
+        load_state<G, NPAD, W, G::kCache>(sh, A, pt, tid);
         __syncthreads();
-        if (tid == 0) prepare_sweep<NPAD, W, TILT>(sh, A, n, A.c[pt], p_cur);
+        prepare_sweep<NPAD, W, G::kCache, TILT>(sh, A, n, tid);
         __syncthreads();
 
         for (int k = 0; k < A.K; ++k) {
@@ -302,10 +317,11 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
 #pragma unroll
             for (int j = 0; j < 12; ++j) S[j] = 0.0f;
 
-            const uint32_t N32 = (uint32_t)A.N;
             for (uint32_t i = grp; i < N32; i += GROUPS) {
                 float z[12];
-                draw_normals<3, 12>(i, 3u * q4, (uint32_t)pt, sweep, A.key0, A.key1, z);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    block_normals<4>(12u * i + 3u * q4 + j, (uint32_t)pt, sweep, A.key0, A.key1, z + 4 * j);
                 float yx[4], yz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -341,14 +357,7 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
 #pragma unroll
                 for (int j = 0; j < 12; ++j) sh.red_S[warp][12 * lane + j] = S[j];
             }
-            __syncthreads();
-            block_combine<NPAD, W>(sh, n, tid);
-            __syncthreads();
-            if (tid == 0) {
-                recover_and_update<G, NPAD, W>(sh, A, pt, k, k + 1 == A.K, p_cur);
-                prepare_sweep<NPAD, W, TILT>(sh, A, n, sh.c, p_cur);
-            }
-            __syncthreads();
+            finish_sweep<G, NPAD, W, G::kCache, TILT>(sh, A, pt, k, tid);
         }
     }
 }

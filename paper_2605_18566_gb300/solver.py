@@ -189,3 +189,13 @@ def sample_normals(n: int, seed: int, instance: int, point: int, sweep: int,
     if st:
         raise HJGError(st, "hjg_sample_normals")
     return out
+
+
+def microbench(op: str, iters: int = 4096):
+    """Throughput of one instruction class (ops/s) and the launch time (ms)."""
+    lib = _lib.load()
+    r = C.c_double(); ms = C.c_double()
+    st = lib.hjg_microbench(_lib.MICROBENCH[op], iters, C.byref(r), C.byref(ms))
+    if st:
+        raise HJGError(st, "hjg_microbench")
+    return r.value, ms.value

@@ -76,19 +76,23 @@ def test_fixed_c_quadratic_closed_form(c):
 
 def test_exact_cole_hopf_case_one_sweep():
     """H = |p|^2/2 with eta = 0: c = 1/delta, one sweep is the exact viscous solution,
-    and the Picard loop stays there."""
+    and the Picard loop stays there (every sweep, every replica seed)."""
     n = 2
     A = np.array([[1.0, 0.3], [0.3, 0.6]]); x0 = np.array([0.5, -0.5]); d = 0.1
     delta, T = 0.2, 1.5
     P = oracle.make_problem("quadratic", n, delta, T, A=A, x0=x0, d=d, eta=0.0)
     x = hjg_inputs.random_states(5, n, 1.0, seed=11).astype(np.float64)
-    out = oracle.picard(P, x, 1 << 15, 3)
-    np.testing.assert_allclose(out["c"], 1.0 / delta, rtol=1e-12)
+    outs = []
+    for r in range(8):
+        P.seed = 500 + r
+        outs.append(oracle.picard(P, x, 1 << 14, 3))
+        np.testing.assert_allclose(outs[-1]["c"], 1.0 / delta, rtol=1e-12)
     for m in range(len(x)):
         v_ref, p_ref = quad_closed_form(A, x0, d, x[m], 1.0 / delta, delta * T)
         for k in (1, 2, 3):
-            assert abs(out["v_hist"][k, m] - v_ref) < 2e-3 * (1 + abs(v_ref))
-        assert np.linalg.norm(out["p"][m] - p_ref) < 5e-3 * (1 + np.linalg.norm(p_ref))
+            vs = np.array([o["v_hist"][k, m] for o in outs])
+            ps = np.array([o["p"][m] for o in outs])
+            check_against(vs, ps, v_ref, p_ref)
     # initial iterate: v0 = g, c0 = 1/delta
     v0, p0, c0 = oracle.init(P, x)
     np.testing.assert_allclose(c0, 1.0 / delta, rtol=1e-12)

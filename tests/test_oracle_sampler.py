@@ -97,7 +97,7 @@ def test_uniform_map_exact_and_symmetric():
         assert 0.0 < u < 1.0
         # 23-bit level plus half a step, exact in binary32
         assert np.float32(u) == u
-        assert u * 2**23 == (x >> 9) + 0.5
+        assert u * 2**23 == (x & 0x7FFFFF) + 0.5
         # reflection x -> ~x maps u -> 1 - u exactly
         assert oracle.u01(x) + oracle.u01((~x) & 0xFFFFFFFF) == 1.0
     assert oracle.u01(0) == 2.0**-24
@@ -107,17 +107,31 @@ def test_uniform_map_exact_and_symmetric():
 def test_box_muller_pair_structure():
     """Radius of pair (z_4j, z_4j+1) comes from u0, its angle from u1 (likewise u2, u3)."""
     seed, inst, sample, point, sweep = 0x1234_5678_9ABC, 3, 17, 5, 2
-    n = 8
+    n = 8                                   # 8 slots per sample: blocks 2*sample, 2*sample+1
     z = oracle.normals(n, seed, inst, sample, point, sweep)
     key = np.array([[seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ inst]], dtype=np.uint32)
     for j in range(2):
-        blk = oracle.philox4x32_10(np.array([[sample, j, point, sweep]], dtype=np.uint32), key)[0]
-        u = [oracle.u01(int(b)) for b in blk]
+        b = 2 * sample + j
+        blk = oracle.philox4x32_10(np.array([[b, 0, point, sweep]], dtype=np.uint32), key)[0]
+        u = [oracle.u01(int(v)) for v in blk]
         for q in (0, 2):
             za, zb = z[4 * j + q], z[4 * j + q + 1]
             np.testing.assert_allclose(za * za + zb * zb, -2.0 * np.log(u[q]), rtol=1e-12)
             ang = np.arctan2(zb, za) % (2 * np.pi)
             np.testing.assert_allclose(ang, (2 * np.pi * u[q + 1]) % (2 * np.pi), atol=1e-9)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6, 7, 45])
+def test_slot_packing(n):
+    """Sample s, dim d reads slot s*stride + d of one stream per (state, sweep); the stream
+    is the same whatever n is (compare with the n = 4 layout, one block per sample)."""
+    stride = oracle.slot_stride(n)
+    assert stride == (n if n <= 8 else 4 * ((n + 3) // 4))
+    for s in (0, 1, 2, 3, 11):
+        z = oracle.normals(n, 5, 1, s, 9, 4)
+        for d in range(n):
+            q = s * stride + d
+            assert z[d] == oracle.normals(4, 5, 1, q // 4, 9, 4)[q % 4]
 
 
 def test_normals_distribution():
@@ -139,8 +153,3 @@ def test_normals_distribution():
     assert np.abs(Z).max() <= np.sqrt(-2 * np.log(2.0**-24)) + 1e-12
 
 
-def test_normals_prefix_consistency():
-    """The first dims do not depend on how many dims are requested."""
-    a = oracle.normals(45, 9, 0, 11, 22, 3)
-    b = oracle.normals(6, 9, 0, 11, 22, 3)
-    np.testing.assert_array_equal(a[:6], b)
