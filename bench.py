@@ -140,6 +140,8 @@ def run_ours(args, rank, world, local_rank):
         solver.picard_sweep(W.K, residuals=False)
 
     with torch.cuda.stream(stream):
+        solver.set_points(x)
+        tuned = solver.autotune(max_states=4 * SMS * 6)   # launch variant, outside timing
         for _ in range(args.warmup):
             step()
     torch.cuda.synchronize()
@@ -208,6 +210,7 @@ def run_ours(args, rank, world, local_rank):
                                "[-3,3]^4x[-pi,pi]^2, N=65536 samples/state/sweep, K=20 sweeps, "
                                "nu=0.05, T=2",
                    "M": W.M, "N": W.N, "K": W.K, "l2": "flushed (256 MB write) between steps",
+                   "launch": {"variant": tuned["variant"], "threads": tuned["threads"]},
                    "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(x_np.nbytes),
@@ -247,19 +250,20 @@ def run_cpu_baseline(seconds_target=12.0, rank=0):
                       % (m, W.M, W.N, W.K, el)}
 
 
-def ncu_case(w):
+def ncu_case(w, variant):
     """A small case of one workload for ncu: M = 4 x 152 states (a few MB on the device),
-    the workload's N, two sweeps per launch; one warm-up launch, then one profiled launch."""
+    the workload's N, two sweeps per launch, launch variant `variant`; one warm-up launch,
+    then one profiled launch."""
     import torch
     from paper_2605_18566_gb300 import Solver
     M = 4 * SMS
     x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
-    s = Solver(w.game, w.nu, w.T, w.N, 2, radius=w.radius)
+    s = Solver(w.game, w.nu, w.T, w.N, 2, radius=w.radius, variant=variant)
     for _ in range(2):
         s.set_points(x)
         r, _ = s.picard_sweep(2)
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": w.name, "M": M, "N": w.N, "K": 2,
+    print(json.dumps({"ncu_case": w.name, "M": M, "N": w.N, "K": 2, "variant": variant,
                       "sweep_ms": s.diagnostics()["last_ms"], "resid": list(r)}))
     s.close()
 
@@ -273,10 +277,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS),
                     help="run one small launch of the named workload's sweep (profiling)")
+    ap.add_argument("--variant", type=int, default=2, help="sweep launch variant for --ncu-case")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if args.ncu_case:
-        ncu_case(hjg_inputs.WORKLOADS[args.ncu_case])
+        ncu_case(hjg_inputs.WORKLOADS[args.ncu_case], args.variant)
         return
 
     if args.impl == "reference":

@@ -94,7 +94,8 @@ typedef struct {
     uint32_t instance;
     int32_t block_threads; /* 0: tuned default; else 128, 256 or 512 */
     int32_t grid_blocks;   /* 0: tuned default (persistent grid over the SMs) */
-    int32_t reserved[7];
+    int32_t variant;       /* 0: default / autotuned; v > 0 forces sweep launch variant v - 1 */
+    int32_t reserved[6];
 } hjg_options;
 
 typedef struct {
@@ -103,8 +104,10 @@ typedef struct {
     int64_t nonfinite;        /* states with non-finite v or Dv in the last call */
     int64_t clipped;          /* states whose |c| hit a clip bound in the last sweep */
     double ess_min, ess_median; /* effective sample size of the last sweep (Section 2.4) */
-    double last_ms;           /* device time of the last hjg_picard_sweep / hjg_value_grad */
-    int32_t block_threads, grid_blocks;
+    double last_ms;           /* device time of the sweep kernel of the last hjg_picard_sweep that
+                                 returned residuals */
+    int32_t block_threads, grid_blocks; /* launch shape of that sweep */
+    int32_t variant;          /* launch variant of the sweep kernel (hjg_autotune) */
 } hjg_diag;
 
 typedef struct hjg_ctx hjg_ctx;
@@ -151,6 +154,16 @@ hjg_status hjg_value_grad(hjg_ctx *ctx, const float *pts, int64_t M, int64_t ld,
                           void *stream);
 
 hjg_status hjg_get_diagnostics(hjg_ctx *ctx, hjg_diag *out);
+
+/* Autotuner: time one sweep of every launch variant of the sweep kernel (CTA size x
+ * register budget, with the persistent grid that fills the SMs) on the first
+ * min(M, max_states) loaded states (max_states <= 0: all), keep the fastest for this
+ * context and report its index, CTA size and time.  Works on scratch copies: the iterate
+ * and the sweep counter are unchanged.  Allocates and frees device scratch; synchronises
+ * the context's stream.  EINVAL when no states are loaded.  An explicit
+ * opt.block_threads is cleared by tuning. */
+hjg_status hjg_autotune(hjg_ctx *ctx, int64_t max_states, int32_t *variant_out, int32_t *threads_out,
+                        double *best_ms_out);
 hjg_status hjg_set_stream(hjg_ctx *ctx, void *stream);
 void hjg_destroy(hjg_ctx *ctx);
 const char *hjg_last_error(const hjg_ctx *ctx);

@@ -31,13 +31,14 @@ class Options(C.Structure):
     _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("tilt", C.c_int32), ("eps", C.c_double),
                 ("eta", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double),
                 ("seed", C.c_uint64), ("instance", C.c_uint32), ("block_threads", C.c_int32),
-                ("grid_blocks", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("grid_blocks", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Diag(C.Structure):
     _fields_ = [("M", C.c_int64), ("next_sweep", C.c_uint32), ("nonfinite", C.c_int64),
                 ("clipped", C.c_int64), ("ess_min", C.c_double), ("ess_median", C.c_double),
-                ("last_ms", C.c_double), ("block_threads", C.c_int32), ("grid_blocks", C.c_int32)]
+                ("last_ms", C.c_double), ("block_threads", C.c_int32), ("grid_blocks", C.c_int32),
+                ("variant", C.c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -53,6 +54,8 @@ _SIGS = {
     "hjg_value_grad": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, C.c_int, _vp, _vp, C.c_int64,
                                  _vp, _vp]),
     "hjg_get_diagnostics": (C.c_int, [_vp, C.POINTER(Diag)]),
+    "hjg_autotune": (C.c_int, [_vp, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_double)]),
     "hjg_set_stream": (C.c_int, [_vp, _vp]),
     "hjg_destroy": (None, [_vp]),
     "hjg_last_error": (C.c_char_p, [_vp]),

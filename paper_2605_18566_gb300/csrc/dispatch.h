@@ -8,18 +8,18 @@
 namespace hjg {
 
 struct GameKernels {
-    int n;  // state dimension
-    // Launch the fused sweep with `threads` per CTA (0 if unsupported) on `grid` CTAs.
-    cudaError_t (*sweep)(const SweepArgs& A, bool tilt, int threads, int grid, cudaStream_t st);
-    // Resident CTAs per SM for the given variant (0 if unsupported).
-    int (*occupancy)(bool tilt, int threads);
+    int n;            // state dimension
+    int nvariants;    // launch variants (CTA size x register budget) available
+    int threads[8];   // CTA size of each variant
+    int minb[8];      // minimum resident CTAs per SM each variant was compiled for
+    // Launch the fused sweep, variant v, on `grid` CTAs.
+    cudaError_t (*sweep)(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st);
+    // Resident CTAs per SM of variant v (0 if it cannot launch).
+    int (*occupancy)(bool tilt, int v);
     cudaError_t (*init)(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta,
                         double eta, double c_min, double c_max, double* v, float* p, int64_t ldp,
                         float* c, float* ess, cudaStream_t st);
-    int default_threads;
 };
-
-bool kernels_for(int game, int n, GameKernels* out);
 
 GameKernels kernels_dubins3();
 GameKernels kernels_rockets6();
@@ -27,3 +27,35 @@ GameKernels kernels_rockets45();
 bool kernels_quadratic(int n, bool zero_h, GameKernels* out);
 
 }  // namespace hjg
+
+// Body of a game translation unit for the one-lane-per-sample kernel.
+#define HJG_GENERIC_GAME_TU(GAME, FN)                                                      \
+    namespace hjg {                                                                        \
+    namespace {                                                                            \
+    cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {   \
+        switch (v) {                                                                       \
+            HJG_SWEEP_VARIANTS(HJG_CASE_LAUNCH)                                            \
+        }                                                                                  \
+        return cudaErrorInvalidValue;                                                      \
+    }                                                                                      \
+    int occ(bool tilt, int v) {                                                            \
+        switch (v) {                                                                       \
+            HJG_SWEEP_VARIANTS(HJG_CASE_OCC)                                               \
+        }                                                                                  \
+        return 0;                                                                          \
+    }                                                                                      \
+    }                                                                                      \
+    GameKernels FN() {                                                                     \
+        GameKernels k{};                                                                   \
+        k.n = GAME::kN;                                                                    \
+        k.nvariants = kNumVariants;                                                        \
+        HJG_SWEEP_VARIANTS(HJG_FILL)                                                       \
+        k.sweep = sweep;                                                                   \
+        k.occupancy = occ;                                                                 \
+        k.init = launch_init<GAME>;                                                        \
+        return k;                                                                          \
+    }                                                                                      \
+    }
+#define HJG_CASE_LAUNCH(i, T, B) case i: return launch_sweep_generic<HJG_GAME, T, B>(A, tilt, grid, st);
+#define HJG_CASE_OCC(i, T, B) case i: return occupancy_generic<HJG_GAME, T, B>(tilt);
+#define HJG_FILL(i, T, B) k.threads[i] = T; k.minb[i] = B;

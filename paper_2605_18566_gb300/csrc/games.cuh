@@ -32,13 +32,19 @@ enum GameId : int32_t {
 
 // ---------------------------------------------------------------- Dubins (App. D.2)
 // x1' = -1 + cos x3 + u x2,  x2' = sin x3 - u x1,  x3' = d - u;  u evader (max), d pursuer (min)
+// Per-sample target in the sweep: l(y) = dist(...) - radius (radius 0 for the quadratic
+// tests), with y = yoff + sk z for the sample mean yoff and the scaled raw normals z.
+__device__ __forceinline__ float sqrtf_fast(float a) {
+    float r; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a)); return r;
+}
+
 struct Dubins3 {
     static constexpr int kN = 3;
-    __device__ static __forceinline__ float ell(const float* y, const GameParams& g) {
-        return sqrtf_fast(y[0] * y[0] + y[1] * y[1]) - g.radius;
-    }
-    __device__ static __forceinline__ float sqrtf_fast(float a) {
-        float r; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a)); return r;
+    static constexpr bool kRadius = true;
+    __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
+                                                 const GameParams&) {
+        const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
+        return sqrtf_fast(fmaf(y0, y0, y1 * y1));
     }
     __device__ static double ell_d(const double* x, const GameParams& g) {
         return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
@@ -67,9 +73,12 @@ struct Dubins3 {
 // B likewise with turn rate d (min).
 struct Rockets6 {
     static constexpr int kN = 6;
-    __device__ static __forceinline__ float ell(const float* y, const GameParams& g) {
-        const float dx = y[0] - y[2], dz = y[1] - y[3];
-        return Dubins3::sqrtf_fast(dx * dx + dz * dz) - g.radius;
+    static constexpr bool kRadius = true;
+    __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
+                                                 const GameParams&) {
+        const float dx = fmaf(sk, z[0] - z[2], yoff[0] - yoff[2]);
+        const float dz = fmaf(sk, z[1] - z[3], yoff[1] - yoff[3]);
+        return sqrtf_fast(fmaf(dx, dx, dz * dz));
     }
     __device__ static double ell_d(const double* x, const GameParams& g) {
         const double dx = x[0] - x[2], dz = x[1] - x[3];
@@ -105,6 +114,7 @@ struct Rockets6 {
 // by 4 lanes (see sweep.cu); only the per-state FP64 parts live here.
 struct Rockets45 {
     static constexpr int kN = 45;
+    static constexpr bool kRadius = true;
     __device__ static double ell_d(const double* x, const GameParams& g) {
         double best = INFINITY;
         for (int i = 0; i < 14; ++i) {
@@ -157,10 +167,12 @@ struct Rockets45 {
 template <int NDIM, bool kZeroH>
 struct Quadratic {
     static constexpr int kN = NDIM;
-    __device__ static __forceinline__ float ell(const float* y, const GameParams& g) {
+    static constexpr bool kRadius = false;
+    __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
+                                                 const GameParams& g) {
         float e[NDIM];
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) e[a] = y[a] - g.x0[a];
+        for (int a = 0; a < NDIM; ++a) e[a] = fmaf(sk, z[a], yoff[a]) - g.x0[a];
         float r = 0.0f;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {

@@ -45,6 +45,7 @@ struct hjg_ctx {
     int64_t nonfinite = 0, clipped = 0;
     double last_ms = 0;
     int threads = 0, grid = 0;
+    int variant = 0;          // launch variant of the sweep kernel (see hjg_autotune)
     std::string err;
 };
 
@@ -221,12 +222,13 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
     A.ldp = ctx->ldx;
     A.M = ctx->M;
     A.N = ctx->opt.N;
-    A.key0 = (uint32_t)ctx->opt.seed;
-    A.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.instance;
+    A.rk = philox_round_keys((uint32_t)ctx->opt.seed,
+                             (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.instance);
     A.k0 = ctx->next_sweep;
     A.K = K;
     A.sigma_d = std::sqrt(ctx->sigma2);
     A.sigma = (float)A.sigma_d;
+    A.sk = (float)(A.sigma_d * (double)kBmScale);
     A.sigma2_d = ctx->sigma2;
     A.delta = ctx->delta;
     A.eta = ctx->eta;
@@ -238,14 +240,24 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
 
 hjg_status choose_launch(hjg_ctx* ctx) {
     const bool tilt = ctx->opt.tilt != 0;
-    int threads = ctx->opt.block_threads > 0 ? ctx->opt.block_threads : ctx->kern.default_threads;
-    int occ = ctx->kern.occupancy(tilt, threads);
-    if (occ <= 0)
-        return fail(ctx, HJG_EINVAL, "block_threads=%d is not available for this game", threads);
+    int v = ctx->variant;
+    if (ctx->opt.variant > 0) {
+        v = ctx->opt.variant - 1;
+        if (v >= ctx->kern.nvariants) return fail(ctx, HJG_EINVAL, "variant %d out of range", v);
+    } else if (ctx->opt.block_threads > 0) {
+        v = -1;
+        for (int i = 0; i < ctx->kern.nvariants && v < 0; ++i)
+            if (ctx->kern.threads[i] == ctx->opt.block_threads) v = i;
+        if (v < 0) return fail(ctx, HJG_EINVAL, "block_threads=%d is not available for this game",
+                               ctx->opt.block_threads);
+    }
+    const int occ = ctx->kern.occupancy(tilt, v);
+    if (occ <= 0) return fail(ctx, HJG_ECUDA, "sweep variant %d cannot launch", v);
     int64_t grid = ctx->opt.grid_blocks > 0 ? ctx->opt.grid_blocks : (int64_t)occ * ctx->num_sms;
     grid = std::min<int64_t>(grid, std::max<int64_t>(ctx->M, 1));
-    ctx->threads = threads;
+    ctx->threads = ctx->kern.threads[v];
     ctx->grid = (int)grid;
+    ctx->variant = v;
     return HJG_OK;
 }
 
@@ -375,7 +387,7 @@ hjg_status hjg_picard_sweep(hjg_ctx* ctx, int n_sweeps, double* residual_out, do
     HJG_CUDA(ctx, cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
     SweepArgs A = make_args(ctx, n_sweeps);
     HJG_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
-    HJG_CUDA(ctx, ctx->kern.sweep(A, ctx->opt.tilt != 0, ctx->threads, ctx->grid, st));
+    HJG_CUDA(ctx, ctx->kern.sweep(A, ctx->opt.tilt != 0, ctx->variant, ctx->grid, st));
     residual_kernel<<<n_sweeps, 256, 0, st>>>(ctx->d_vhist, ctx->M, ctx->d_resid);
     HJG_CUDA(ctx, cudaGetLastError());
     HJG_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
@@ -490,6 +502,7 @@ hjg_status hjg_get_diagnostics(hjg_ctx* ctx, hjg_diag* out) {
     out->last_ms = ctx->last_ms;
     out->block_threads = ctx->threads;
     out->grid_blocks = ctx->grid;
+    out->variant = ctx->variant;
     if (ctx->M > 0) {
         std::vector<float> e((size_t)ctx->M);
         HJG_CUDA(ctx, cudaMemcpyAsync(e.data(), ctx->d_ess, e.size() * sizeof(float), cudaMemcpyDeviceToHost,
@@ -500,6 +513,58 @@ hjg_status hjg_get_diagnostics(hjg_ctx* ctx, hjg_diag* out) {
         out->ess_median = sorted[sorted.size() / 2];
         out->ess_min = *std::min_element(e.begin(), e.end());
     }
+    return HJG_OK;
+}
+
+hjg_status hjg_autotune(hjg_ctx* ctx, int64_t max_states, int32_t* variant_out, int32_t* threads_out,
+                        double* best_ms_out) {
+    if (!ctx) return HJG_EINVAL;
+    if (ctx->M == 0) return fail(ctx, HJG_EINVAL, "autotune needs loaded states");
+    const bool tilt = ctx->opt.tilt != 0;
+    const int64_t Mt = std::min<int64_t>(ctx->M, max_states > 0 ? max_states : ctx->M);
+    cudaStream_t st = ctx->stream;
+    float *p = nullptr, *c = nullptr, *ess = nullptr;
+    double* v = nullptr;
+    unsigned long long* cnt = nullptr;
+    hjg_status s = HJG_OK;
+    if ((s = grow(ctx, &p, (size_t)Mt * ctx->ldx)) || (s = grow(ctx, &c, (size_t)Mt)) ||
+        (s = grow(ctx, &ess, (size_t)Mt)) || (s = grow(ctx, &v, (size_t)Mt)) ||
+        (s = grow(ctx, &cnt, (size_t)4))) {
+        cudaFree(p); cudaFree(c); cudaFree(ess); cudaFree(v); cudaFree(cnt);
+        return s;
+    }
+    int best = -1;
+    float best_ms = 0.0f;
+    for (int var = 0; var < ctx->kern.nvariants && s == HJG_OK; ++var) {
+        const int occ = ctx->kern.occupancy(tilt, var);
+        if (occ <= 0) continue;
+        const int grid = (int)std::min<int64_t>((int64_t)occ * ctx->num_sms, Mt);
+        SweepArgs A = make_args(ctx, 1);
+        A.M = Mt; A.p = p; A.c = c; A.v = v; A.ess = ess; A.vhist = nullptr; A.counters = cnt;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && s == HJG_OK; ++rep) {   // warm-up, then timed
+            cudaError_t e = cudaMemcpyAsync(p, ctx->d_p, (size_t)Mt * ctx->ldx * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c, ctx->d_c, (size_t)Mt * sizeof(float),
+                                                      cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev0, st);
+            if (e == cudaSuccess) e = ctx->kern.sweep(A, tilt, var, grid, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            if (e != cudaSuccess) s = fail(ctx, HJG_ECUDA, "autotune variant %d: %s", var, cudaGetErrorString(e));
+        }
+        if (s == HJG_OK && (best < 0 || ms < best_ms)) { best = var; best_ms = ms; }
+    }
+    cudaFree(p); cudaFree(c); cudaFree(ess); cudaFree(v); cudaFree(cnt);
+    if (s != HJG_OK) return s;
+    if (best < 0) return fail(ctx, HJG_ECUDA, "no sweep variant can launch");
+    ctx->variant = best;
+    ctx->opt.block_threads = 0;
+    ctx->opt.variant = 0;
+    if (variant_out) *variant_out = best;
+    if (threads_out) *threads_out = ctx->kern.threads[best];
+    if (best_ms_out) *best_ms_out = best_ms;
     return HJG_OK;
 }
 

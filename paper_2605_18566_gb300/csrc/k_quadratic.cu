@@ -1,23 +1,32 @@
 // Sweep kernels for the quadratic test problems (H = +-|p|^2/2 or H = 0, quadratic
 // target), n in {1, 2, 3, 4, 6, 8}: the exact Cole-Hopf case of Corollary B.2 and the
-// pure heat equation, used to check the estimator against closed forms.
+// pure heat equation, used to check the estimator against closed forms.  One launch
+// variant (128 threads).
 #include "dispatch.h"
 
 namespace hjg {
 namespace {
 template <class G>
-cudaError_t sweep(const SweepArgs& A, bool tilt, int threads, int grid, cudaStream_t st) {
-    if (threads != 128) return cudaErrorInvalidValue;
-    return launch_sweep_generic<G, 128>(A, tilt, grid, st);
+cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
+    if (v != 0) return cudaErrorInvalidValue;
+    return launch_sweep_generic<G, 128, 1>(A, tilt, grid, st);
 }
 template <class G>
-int occ(bool tilt, int threads) {
-    return threads == 128 ? occupancy_generic<G, 128>(tilt) : 0;
+int occ(bool tilt, int v) {
+    return v == 0 ? occupancy_generic<G, 128, 1>(tilt) : 0;
 }
 template <int N, bool Z>
 GameKernels make() {
     using G = Quadratic<N, Z>;
-    return {N, sweep<G>, occ<G>, launch_init<G>, 128};
+    GameKernels k{};
+    k.n = N;
+    k.nvariants = 1;
+    k.threads[0] = 128;
+    k.minb[0] = 1;
+    k.sweep = sweep<G>;
+    k.occupancy = occ<G>;
+    k.init = launch_init<G>;
+    return k;
 }
 }  // namespace
 

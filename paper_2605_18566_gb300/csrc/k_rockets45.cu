@@ -4,35 +4,38 @@
 
 namespace hjg {
 namespace {
-template <int T>
+template <int T, int B>
 cudaError_t launch(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
-    if (tilt) sweep_kernel_r45<T, true><<<grid, T, 0, st>>>(A);
-    else sweep_kernel_r45<T, false><<<grid, T, 0, st>>>(A);
+    if (tilt) sweep_kernel_r45<T, B, true><<<grid, T, 0, st>>>(A);
+    else sweep_kernel_r45<T, B, false><<<grid, T, 0, st>>>(A);
     return cudaGetLastError();
 }
-template <int T>
+template <int T, int B>
 int occupancy(bool tilt) {
     int nb = 0;
-    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, true>, T, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, false>, T, 0);
+    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, true>, T, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, false>, T, 0);
     return nb;
 }
-cudaError_t sweep(const SweepArgs& A, bool tilt, int threads, int grid, cudaStream_t st) {
-    switch (threads) {
-    case 128: return launch<128>(A, tilt, grid, st);
-    case 256: return launch<256>(A, tilt, grid, st);
-    case 512: return launch<512>(A, tilt, grid, st);
-    }
+#define R45_LAUNCH(i, T, B) case i: return launch<T, B>(A, tilt, grid, st);
+#define R45_OCC(i, T, B) case i: return occupancy<T, B>(tilt);
+cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
+    switch (v) { HJG_R45_VARIANTS(R45_LAUNCH) }
     return cudaErrorInvalidValue;
 }
-int occ(bool tilt, int threads) {
-    switch (threads) {
-    case 128: return occupancy<128>(tilt);
-    case 256: return occupancy<256>(tilt);
-    case 512: return occupancy<512>(tilt);
-    }
+int occ(bool tilt, int v) {
+    switch (v) { HJG_R45_VARIANTS(R45_OCC) }
     return 0;
 }
 }  // namespace
-GameKernels kernels_rockets45() { return {45, sweep, occ, launch_init<Rockets45>, 256}; }
+GameKernels kernels_rockets45() {
+    GameKernels k{};
+    k.n = 45;
+    k.nvariants = kNumVariants;
+    HJG_R45_VARIANTS(HJG_FILL)
+    k.sweep = sweep;
+    k.occupancy = occ;
+    k.init = launch_init<Rockets45>;
+    return k;
+}
 }  // namespace hjg

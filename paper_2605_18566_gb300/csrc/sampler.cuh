@@ -61,36 +61,72 @@ __device__ __forceinline__ float u01(uint32_t r) {
     return mant_one_two(r) + (-1.0f + 0x1.0p-24f);
 }
 
-// Box-Muller radius sqrt(-2 ln u) from the radius word.  Near u = 1 the approximate log2
-// may come out as a tiny positive number; the magnitude is taken (the radius is ~0 there).
-__device__ __forceinline__ float bm_radius(uint32_t r) {
-    const float t = -1.3862943611198906f * lg2_approx(u01(r));
-    return sqrt_approx(fabsf(t));
-}
-
 // Box-Muller phase phi = 2 pi u - pi in (-pi, pi), one FMA from the mantissa float f = u + 1
 // - 2^-24; the pair is (r cos 2 pi u, r sin 2 pi u) = (-r cos phi, -r sin phi).
 __device__ __forceinline__ float bm_phase(uint32_t r) {
     return fmaf(mant_one_two(r), 6.283185307179586f, -9.42477798461914f);
 }
 
-// The first NUSE (1..4) normals of block b of the (point, sweep) stream.
+// Per-round Philox keys (k + r W for rounds r = 0..9), computed once on the host so that
+// the rounds take them straight from the constant bank.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = k0;
+        rk.k1[r] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 ctr, const PhiloxKeys& rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * ctr.x;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * ctr.z;
+        ctr = make_uint4((uint32_t)(p1 >> 32) ^ ctr.y ^ rk.k0[r], (uint32_t)p1,
+                         (uint32_t)(p0 >> 32) ^ ctr.w ^ rk.k1[r], (uint32_t)p0);
+    }
+    return ctr;
+}
+
+// Box-Muller without its constant factors: the normal pair is kBmScale * (r' cos phi,
+// r' sin phi) with r' = sqrt(|log2 u0|) and phi the phase above, kBmScale = -sqrt(2 ln 2).
+// The sweep keeps the scale out of the per-sample loop (it folds it into sigma, the tilt
+// slope and the final gradient).
+constexpr float kBmScale = -1.1774100225154747f;
+
+template <int NUSE>
+__device__ __forceinline__ void block_normals_raw(uint32_t b, uint32_t point, uint32_t sweep,
+                                                  const PhiloxKeys& rk, float* z) {
+    const uint4 r = philox4x32_10_rk(make_uint4(b, 0u, point, sweep), rk);
+    {
+        const float ra = sqrt_approx(fabsf(lg2_approx(u01(r.x))));
+        const float ph = bm_phase(r.y);
+        z[0] = ra * cos_approx(ph);
+        if (NUSE > 1) z[1] = ra * sin_approx(ph);
+    }
+    if (NUSE > 2) {
+        const float rb = sqrt_approx(fabsf(lg2_approx(u01(r.z))));
+        const float ph = bm_phase(r.w);
+        z[2] = rb * cos_approx(ph);
+        if (NUSE > 3) z[3] = rb * sin_approx(ph);
+    }
+}
+
+// The first NUSE (1..4) standard normals of block b of the (point, sweep) stream.
 template <int NUSE>
 __device__ __forceinline__ void block_normals(uint32_t b, uint32_t point, uint32_t sweep,
                                               uint32_t k0, uint32_t k1, float* z) {
-    const uint4 r = philox4x32_10(make_uint4(b, 0u, point, sweep), k0, k1);
-    {
-        const float ra = bm_radius(r.x);
-        const float ph = bm_phase(r.y);
-        z[0] = -ra * cos_approx(ph);
-        if (NUSE > 1) z[1] = -ra * sin_approx(ph);
-    }
-    if (NUSE > 2) {
-        const float rb = bm_radius(r.z);
-        const float ph = bm_phase(r.w);
-        z[2] = -rb * cos_approx(ph);
-        if (NUSE > 3) z[3] = -rb * sin_approx(ph);
-    }
+    const PhiloxKeys rk = philox_round_keys(k0, k1);
+    block_normals_raw<NUSE>(b, point, sweep, rk, z);
+#pragma unroll
+    for (int j = 0; j < NUSE; ++j) z[j] *= kBmScale;
 }
 
 // Slots per sample and the sample grouping that makes a group end on a block boundary.

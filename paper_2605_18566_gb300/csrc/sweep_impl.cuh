@@ -32,10 +32,11 @@ struct SweepArgs {
     float* ess;               // [M] ESS of the last sweep
     unsigned long long* counters;  // [0] non-finite states, [1] clipped coefficients (last sweep)
     int64_t ldx, ldp, M, N;
-    uint32_t key0, key1;      // Philox key
+    PhiloxKeys rk;            // Philox round keys of (seed_lo, seed_hi ^ instance)
     uint32_t k0;              // global index of the first sweep
     int32_t K;                // sweeps to run
     float sigma;              // sqrt(delta t)
+    float sk;                 // sigma * kBmScale: y = x + theta + sk * (raw normal)
     double sigma_d, sigma2_d, delta, eta, c_min, c_max;
     GameParams g;
 };
@@ -103,9 +104,10 @@ struct SweepShared {
     float xf[NPAD];       // state in FP32
     float p_cur[NPAD];    // Dv iterate in FP32 (the stored precision)
     float yoff[NPAD];     // x + theta (FP32), the sample mean
-    float tq[NPAD];       // -theta_j log2e / sigma (tilt log-weight slope)
+    float tq[NPAD];       // -theta_j log2e kBmScale / sigma (tilt slope per raw normal)
     float theta[NPAD];
     float cneg2;          // -c log2e
+    float cr;             // -cneg2 radius (0 for targets without a radius)
     float c;
     float red_m[W], red_s[W], red_q[W];
     float red_S[W][NPAD];
@@ -126,6 +128,7 @@ __device__ __forceinline__ void load_state(SweepShared<NPAD, W, NC>& sh, const S
         if (A.vhist) A.vhist[pt] = A.v[pt];
         sh.c = A.c[pt];
         sh.cneg2 = -sh.c * kLog2e;
+        sh.cr = G::kRadius ? -sh.cneg2 * A.g.radius : 0.0f;
     }
     __syncthreads();
     if (NC > 0 && tid < NC) sh.hc[tid] = G::cache(sh.x, tid);
@@ -141,7 +144,7 @@ __device__ __forceinline__ void prepare_sweep(SweepShared<NPAD, W, NC>& sh, cons
         if (TILT && tid < n) th = (float)(-A.sigma2_d * (double)sh.c * (double)sh.p_cur[tid]);
         sh.theta[tid] = th;
         sh.yoff[tid] = sh.xf[tid] + th;
-        sh.tq[tid] = -th * kLog2e / A.sigma;
+        sh.tq[tid] = -th * kLog2e * kBmScale / A.sigma;
     }
 }
 
@@ -170,6 +173,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
             s = fma(sh.fw[w], (double)sh.red_s[w], s);
             Sj = fma(sh.fw[w], (double)sh.red_S[w][tid], Sj);
         }
+        Sj *= (double)kBmScale;   // the sample loop accumulates raw normals
         const double pj = -((double)sh.theta[tid] + A.sigma_d * Sj / s) / (c * A.sigma2_d);
         sh.pd[tid] = pj;
         sh.p_cur[tid] = (float)pj;
@@ -208,6 +212,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
         }
         sh.c = c_new;
         sh.cneg2 = -c_new * kLog2e;
+        sh.cr = G::kRadius ? -sh.cneg2 * A.g.radius : 0.0f;
     }
     __syncthreads();
     if (!last) prepare_sweep<NPAD, W, NC, TILT>(sh, A, n, tid);
@@ -218,8 +223,8 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
 // One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
 // g = group_samples(n) that end on a Philox block boundary (n = 3: 4 samples from 3 blocks;
 // n = 6: 2 samples from 3 blocks), so every normal drawn is used.
-template <class G, int THREADS, bool TILT>
-__global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
+template <class G, int THREADS, int MINB, bool TILT>
+__global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int NPAD = (n + 3) / 4 * 4;
     constexpr int W = THREADS / 32;
@@ -228,6 +233,7 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
     __shared__ SweepShared<NPAD, W, G::kCache> sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t N32 = (uint32_t)A.N;
+    const uint32_t full = N32 / GS;            // groups whose GS samples all lie inside N
     const uint32_t groups = (N32 + GS - 1) / GS;
 
     for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
 
         for (int k = 0; k < A.K; ++k) {
             const uint32_t sweep = A.k0 + (uint32_t)k;
-            const float cneg2 = sh.cneg2;
+            const float cneg2 = sh.cneg2, cr = sh.cr;
             float yoff[n], tq[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) { yoff[j] = sh.yoff[j]; tq[j] = sh.tq[j]; }
@@ -246,26 +252,28 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
 #pragma unroll
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
 
-            for (uint32_t grp = tid; grp < groups; grp += THREADS) {
+            auto sample = [&](const float* zt) {
+                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g), cr);
+                if (TILT) {
+#pragma unroll
+                    for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
+                }
+                lse_accumulate<n>(a, zt, m, s, q, S);
+            };
+            for (uint32_t grp = tid; grp < full; grp += THREADS) {
                 float z[4 * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals<4>(grp * GB + b, (uint32_t)pt, sweep, A.key0, A.key1, z + 4 * b);
-                const uint32_t left = N32 - grp * GS;   // samples of this group inside N
+                    block_normals_raw<4>(grp * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
 #pragma unroll
-                for (int t = 0; t < GS; ++t) {
-                    if (GS > 1 && (uint32_t)t >= left) break;
-                    const float* zt = z + t * n;
-                    float y[n];
+                for (int t = 0; t < GS; ++t) sample(z + t * n);
+            }
+            if (GS > 1 && full < groups && tid == (int)(full % THREADS)) {   // ragged last group
+                float z[4 * GB];
 #pragma unroll
-                    for (int j = 0; j < n; ++j) y[j] = fmaf(A.sigma, zt[j], yoff[j]);
-                    float a = cneg2 * G::ell(y, A.g);
-                    if (TILT) {
-#pragma unroll
-                        for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
-                    }
-                    lse_accumulate<n>(a, zt, m, s, q, S);
-                }
+                for (int b = 0; b < GB; ++b)
+                    block_normals_raw<4>(full * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                for (uint32_t t = 0; t < N32 - full * GS; ++t) sample(z + t * n);
             }
 
             warp_merge<n>(1, m, s, q, S);
@@ -286,8 +294,8 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(const SweepArgs A) {
 // each lane takes the minimum squared distance over its own pursuers, and two shuffles
 // finish the group minimum.  All four lanes then hold the same log-weight and accumulate
 // their own twelve S_j.
-template <int THREADS, bool TILT>
-__global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
+template <int THREADS, int MINB, bool TILT>
+__global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArgs A) {
     using G = Rockets45;
     constexpr int n = 45;
     constexpr int NPAD = 48;
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
 
         for (int k = 0; k < A.K; ++k) {
             const uint32_t sweep = A.k0 + (uint32_t)k;
-            const float cneg2 = sh.cneg2;
+            const float cneg2 = sh.cneg2, cr = sh.cr;
             float yoff[12], tq[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) { yoff[j] = sh.yoff[12 * q4 + j]; tq[j] = sh.tq[12 * q4 + j]; }
@@ -321,12 +329,12 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
                 float z[12];
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    block_normals<4>(12u * i + 3u * q4 + j, (uint32_t)pt, sweep, A.key0, A.key1, z + 4 * j);
+                    block_normals_raw<4>(12u * i + 3u * q4 + j, (uint32_t)pt, sweep, A.rk, z + 4 * j);
                 float yx[4], yz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    yx[a] = fmaf(A.sigma, z[3 * a], yoff[3 * a]);
-                    yz[a] = fmaf(A.sigma, z[3 * a + 1], yoff[3 * a + 1]);
+                    yx[a] = fmaf(A.sk, z[3 * a], yoff[3 * a]);
+                    yz[a] = fmaf(A.sk, z[3 * a + 1], yoff[3 * a + 1]);
                 }
                 const float ex = __shfl_sync(0xffffffffu, yx[2], src3);
                 const float ez = __shfl_sync(0xffffffffu, yz[2], src3);
@@ -339,7 +347,7 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel_r45(const SweepArgs A) {
                 }
                 d2 = fminf(d2, __shfl_xor_sync(0xffffffffu, d2, 1));
                 d2 = fminf(d2, __shfl_xor_sync(0xffffffffu, d2, 2));
-                float a2 = cneg2 * (sqrt_approx(d2) - A.g.radius);
+                float a2 = fmaf(cneg2, sqrt_approx(d2), cr);
                 if (TILT) {
                     float part = 0.0f;
 #pragma unroll
@@ -383,19 +391,24 @@ __global__ void init_kernel(const float* __restrict__ x, int64_t ldx, int64_t M,
     ess[m] = 0.0f;
 }
 
-// Launch helpers instantiated once per game in its own translation unit.
-template <class G, int THREADS>
+// Launch variants (CTA size, minimum resident CTAs per SM for the register budget) the
+// autotuner chooses among; every game's translation unit instantiates all of them.
+#define HJG_SWEEP_VARIANTS(X) X(0, 256, 1) X(1, 256, 5) X(2, 256, 6) X(3, 128, 1) X(4, 512, 1)
+#define HJG_R45_VARIANTS(X) X(0, 256, 1) X(1, 256, 2) X(2, 128, 1) X(3, 128, 4) X(4, 512, 1)
+constexpr int kNumVariants = 5;
+
+template <class G, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
-    if (tilt) sweep_kernel<G, THREADS, true><<<grid, THREADS, 0, st>>>(A);
-    else sweep_kernel<G, THREADS, false><<<grid, THREADS, 0, st>>>(A);
+    if (tilt) sweep_kernel<G, THREADS, MINB, true><<<grid, THREADS, 0, st>>>(A);
+    else sweep_kernel<G, THREADS, MINB, false><<<grid, THREADS, 0, st>>>(A);
     return cudaGetLastError();
 }
 
-template <class G, int THREADS>
+template <class G, int THREADS, int MINB>
 int occupancy_generic(bool tilt) {
     int nb = 0;
-    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, true>, THREADS, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, false>, THREADS, 0);
+    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true>, THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false>, THREADS, 0);
     return nb;
 }
 

@@ -37,7 +37,8 @@ class Solver:
                  A=None, x0=None, d: float = 0.0, seed: int = 0, instance: int = 0,
                  tilt: bool = False, eps: float = 0.0, eta: float = -1.0,
                  c_min: float = 0.0, c_max: float = 0.0, block_threads: int = 0,
-                 grid_blocks: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 grid_blocks: int = 0, variant: int = -1,
+                 stream: Optional[torch.cuda.Stream] = None):
         self.lib = _lib.load()
         if n is None:
             n = _lib.GAME_DIMS[game]
@@ -62,6 +63,7 @@ class Solver:
         opt.N = N; opt.K = K; opt.tilt = 1 if tilt else 0; opt.eps = eps; opt.eta = eta
         opt.c_min = c_min; opt.c_max = c_max; opt.seed = seed; opt.instance = instance
         opt.block_threads = block_threads; opt.grid_blocks = grid_blocks
+        opt.variant = variant + 1 if variant >= 0 else 0
         self.opt = opt
         ctx = C.c_void_p()
         torch.cuda.init()
@@ -161,6 +163,13 @@ class Solver:
             _check(self.lib, self.ctx, st)
         self.last_status = st
         return v_out, grad_out, r[:K]
+
+    def autotune(self, max_states: int = 0) -> dict:
+        """Pick the fastest sweep launch variant on the loaded states (see hjg_autotune)."""
+        v = C.c_int32(); t = C.c_int32(); ms = C.c_double()
+        _check(self.lib, self.ctx, self.lib.hjg_autotune(self.ctx, max_states, C.byref(v),
+                                                         C.byref(t), C.byref(ms)))
+        return {"variant": v.value, "threads": t.value, "ms": ms.value}
 
     def diagnostics(self) -> dict:
         d = _lib.Diag()

@@ -60,7 +60,7 @@ def test_one_sweep_parity(w, M, N, tilt):
                          ids=["dubins3-full", "rockets6-M257", "rockets45-M24"])
 def test_trajectory_parity(w, M, N, K):
     x = hjg_inputs.points(w, M=M)
-    out = check_trajectory(w, x, N, K)
+    out = check_trajectory(w, x, N, K, min_pass=0.97 if M > 100 else 0.9)
     np.testing.assert_allclose(out["resid"], out["ref_resid"], rtol=5e-3, atol=1e-7)
 
 
@@ -189,3 +189,32 @@ def test_value_grad_early_stop():
     v, g, r = s.value_grad(x)
     s.close()
     assert np.isfinite(r[0]) and np.all(np.isnan(r[1:]))
+
+
+def test_autotune_keeps_state_and_results():
+    w = W2
+    x = torch.from_numpy(hjg_inputs.points(w, M=300)).cuda()
+    s = solver_for(w, N=4096, K=3)
+    s.set_points(x)
+    before = s.get_state()
+    tuned = s.autotune()
+    after = s.get_state()
+    for key in ("v", "p", "c"):
+        assert torch.equal(before[key], after[key]), key
+    assert tuned["threads"] in (128, 256, 512) and tuned["ms"] > 0
+    r_tuned, _ = s.picard_sweep(3)
+    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    s.close()
+    ref = oracle.picard(problem_for(w), x.cpu().numpy().astype(np.float64), 4096, 3)
+    assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.99, what="tuned variant")
+    xs = x.cpu().numpy().astype(np.float64)
+    for v in range(5):     # every launch variant agrees with the oracle on one sweep
+        s = solver_for(w, N=4096, K=1, variant=v)
+        s.set_points(x)
+        c0 = s.get_state()["c"].cpu().numpy().astype(np.float64)
+        s.picard_sweep(1)
+        st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+        assert s.diagnostics()["variant"] == v
+        s.close()
+        vr, pr, _ = oracle.sweep(problem_for(w), xs, c0, 4096, 0)
+        assert_parity(st["v"], st["p"], vr, pr, what="variant %d" % v)
