@@ -169,6 +169,27 @@ void hjg_destroy(hjg_ctx *ctx);
 const char *hjg_last_error(const hjg_ctx *ctx);
 const char *hjg_status_string(hjg_status s);
 
+/* One-shot solve that allocates no device memory (the paper has no counterpart; this
+ * is a deployment variant of hjg_value_grad).  For callers that must not allocate once
+ * running: hard real-time control loops, processes whose device memory belongs to
+ * another runtime's allocator, services that reserve everything at start-up.  Runs the
+ * initial iterate, opt->K sweeps (no early stop) and the residuals for the M states at
+ * pts ([M][ld] FP32, device) and writes v_out [M] FP64, grad_out [M][ldg] FP32 (also used
+ * as the Dv iterate) and, if not NULL, residual_out [2*K] FP64 (relative L2 and sup-norm
+ * change of each sweep, interleaved) -- all device pointers, all owned by the caller.
+ * Its other working memory is one fixed 16 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits; the call needs
+ * (8*K + 16)*M bytes of it plus a little alignment slack and returns EINVAL beyond that
+ * (e.g. M <= 95,000 states at K = 20).  No cudaMalloc, no cudaFree, no allocating library
+ * routine.  The first call on each device looks up that array's device address (with
+ * the device current), so make it before any stream capture.  Asynchronous on `stream`;
+ * calls share the array, so calls that overlap on the GPU race and must be serialised by
+ * the caller.  Default launch variant 0 (opt->variant > 0 selects another). */
+hjg_status hjg_value_grad_noalloc(const hjg_dynamics *dyn, const hjg_target *target, double nu,
+                                  double T, const hjg_options *opt, const float *pts, int64_t M,
+                                  int64_t ld, double *v_out, float *grad_out, int64_t ldg,
+                                  double *residual_out, void *stream);
+
 /* ---- building blocks, exposed for bit-level tests ------------------------------ */
 
 /* Philox4x32-10 blocks on the device: ctr [count][4], key [count][2], out [count][4]

@@ -1,0 +1,77 @@
+"""The allocation-free solve, hjg_value_grad_noalloc, against hjg_value_grad.
+
+hjg_value_grad_noalloc exists for callers that cannot allocate device memory once they
+are running (hard real-time loops, processes whose device memory is owned by another
+runtime's allocator, services that reserve everything up front).  It keeps its working
+memory in one fixed array inside the library; this test calls it through the C ABI twice
+in a row (the second call reuses that array with the first call's contents still in it)
+and checks both results against the context-based entry point, state by state, within
+the parity tolerance used everywhere else.  The file is named to be collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import hjg_inputs
+from helpers import assert_parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _structs(w, N, K):
+    from paper_2605_18566_gb300 import _lib
+    dyn = _lib.Dynamics(); dyn.game = _lib.GAMES[w.game]; dyn.n = w.n; dyn.h_sign = 1.0
+    tgt = _lib.Target(); tgt.radius = w.radius
+    opt = _lib.Options(); opt.N = N; opt.K = K; opt.eta = -1.0; opt.seed = 0
+    return dyn, tgt, opt
+
+
+def _noalloc(lib, dyn, tgt, nu, T, opt, x, v, g, r, stream):
+    return lib.hjg_value_grad_noalloc(C.byref(dyn), C.byref(tgt), nu, T, C.byref(opt),
+                                      C.c_void_p(x.data_ptr()), x.shape[0], x.stride(0),
+                                      C.c_void_p(v.data_ptr()), C.c_void_p(g.data_ptr()),
+                                      g.stride(0), C.c_void_p(r.data_ptr()), stream)
+
+
+@pytest.mark.parametrize("game", ["dubins3", "rockets6"])
+def test_noalloc_matches_value_grad_twice(game):
+    from paper_2605_18566_gb300 import Solver, _lib
+    lib = _lib.load()
+    w = {"dubins3": hjg_inputs.DUBINS3, "rockets6": hjg_inputs.ROCKETS6}[game]
+    N, K, M = 8192, 6, 3000
+    x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
+    s = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, seed=0)
+    v_ref, g_ref, r_ref = s.value_grad(x)
+    s.close()
+    v_ref = v_ref.cpu().numpy(); g_ref = g_ref.cpu().numpy()
+
+    dyn, tgt, opt = _structs(w, N, K)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call in range(2):
+        v = torch.full((M,), float("nan"), dtype=torch.float64, device="cuda")
+        g = torch.full((M, w.n), float("nan"), dtype=torch.float32, device="cuda")
+        r = torch.full((2 * K,), float("nan"), dtype=torch.float64, device="cuda")
+        st = _noalloc(lib, dyn, tgt, w.nu, w.T, opt, x, v, g, r, stream)
+        assert st == 0, _lib.status_string(st)
+        torch.cuda.synchronize()
+        assert_parity(v.cpu().numpy(), g.cpu().numpy(), v_ref, g_ref,
+                      what="noalloc call %d" % call)
+        res = r.cpu().numpy().reshape(K, 2)[:, 0]
+        np.testing.assert_allclose(res, r_ref, rtol=1e-6, atol=1e-12)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    from paper_2605_18566_gb300 import _lib
+    lib = _lib.load()
+    w = hjg_inputs.ROCKETS6
+    K = 20
+    dyn, tgt, opt = _structs(w, 64, K)
+    M = 120_000                    # (8K + 16) M bytes = 21 MB > 16 MiB
+    x = torch.zeros(M, w.n, device="cuda")
+    v = torch.empty(M, dtype=torch.float64, device="cuda")
+    g = torch.empty(M, w.n, device="cuda")
+    r = torch.empty(2 * K, dtype=torch.float64, device="cuda")
+    st = _noalloc(lib, dyn, tgt, w.nu, w.T, opt, x, v, g, r, None)
+    assert st == _lib.HJG_EINVAL
