@@ -38,14 +38,41 @@ METRIC = "point-samples/s per Picard sweep (v+grad v)"
 UNIT = "point-samples/s"
 W = hjg_inputs.ROCKETS6
 
-# Algorithmic MUFU operations per point-sample of the 6-D sweep: three Box-Muller pairs
-# (log2, sqrt, sin, cos each), one sqrt in the target distance, one exp2 weight.
-MUFU_PER_SAMPLE = {"rockets6": 3 * 4 + 1 + 1, "dubins3": 2 + 2 + 2 + 1 + 1 + 1,
-                   "rockets45": 23 * 4 - 1 + 1 + 1}
-# MUFU (XU pipe) issue rate per SM per clock, and the GB300 unit counts and clock.
-MUFU_PER_SM_CLK = 16
+# Algorithmic per-point-sample work of the sweep on the two pipes that bind it (counts
+# for each workload's game; the block index sits in the Philox counter words the first
+# round does not multiply, so 4 of the 20 multiplies of a block depend only on the state
+# and sweep and are not per-sample work):
+#   Philox blocks per sample: n / 4 for n <= 8 (packed slots), ceil(n/4) above
+#   IMAD.WIDE (32x32->64 multiplies, FMA-heavy pipe): 16 per block
+#   MUFU (XU pipe): log2, sqrt, sin, cos per Box-Muller pair, one sqrt for the target
+#   distance, one exp2 weight (exp2 issues at twice the rate of the others on GB300)
+BLOCKS_PER_SAMPLE = {"dubins3": 0.75, "rockets6": 1.5, "rockets45": 12.0}
+MUFU_PER_SAMPLE = {"dubins3": 2 * 3 + 2, "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
+IMUL_PER_BLOCK = 16
+# GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations
+# and 32 IMAD.WIDE (half the 64 32-bit IMADs per clock).
 SMS = 152
 SM_MAX_MHZ = 2070.0
+MUFU_PER_SM_CLK = 16
+IMUL_PER_SM_CLK = 32
+
+
+def roofline(game, samples, kernel_s):
+    """Binding-pipe roofline of the sweep kernel: achieved algorithmic operations per
+    second over the pipe's peak at the maximum SM clock."""
+    clk = SMS * SM_MAX_MHZ * 1e6
+    pipes = {
+        "imad_wide": (samples * BLOCKS_PER_SAMPLE[game] * IMUL_PER_BLOCK, IMUL_PER_SM_CLK * clk),
+        "mufu": (samples * (MUFU_PER_SAMPLE[game] - 0.5), MUFU_PER_SM_CLK * clk),
+    }
+    fr = {k: (ops / kernel_s) / peak for k, (ops, peak) in pipes.items()}
+    bind = max(fr, key=fr.get)
+    ops, peak = pipes[bind]
+    return {"bound": "alu", "pipe": bind, "achieved": ops / kernel_s / 1e9, "peak": peak / 1e9,
+            "unit": "Gop/s", "frac": fr[bind], "traffic": None,
+            "ops_per_point_sample": ops / samples,
+            "other_pipes": {k: round(v, 4) for k, v in fr.items() if k != bind},
+            "peak_basis": "per-SM-per-clock pipe rate x 152 SMs x 2070 MHz"}
 
 
 def dist_env():
@@ -196,10 +223,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = world * samples_per_step / e2e_s
     clocks = clk.summary()
     peaks = load_peaks()
-    mufu = MUFU_PER_SAMPLE[W.game]
     kern_s = statistics.median(kern_ms) / 1e3
-    achieved = samples_per_step * mufu / kern_s / 1e9          # G MUFU-op/s
-    peak = MUFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e9        # G MUFU-op/s at max clock
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -216,11 +240,8 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(x_np.nbytes),
                 "d2h_bytes_per_step": int(W.M * 8 + W.M * W.n * 4 + W.K * 8)},
         "gpu_launches": 3 * args.steps,
-        "roofline": {"bound": "alu", "pipe": "MUFU (XU)", "achieved": achieved, "peak": peak,
-                     "unit": "GMUFU-op/s", "frac": achieved / peak, "traffic": None,
-                     "ops_per_point_sample": mufu,
-                     "kernel_ms_per_step": statistics.median(kern_ms),
-                     "peak_basis": "16 MUFU ops/clk/SM x 152 SMs x 2070 MHz"},
+        "roofline": dict(roofline(W.game, samples_per_step, kern_s),
+                         kernel_ms_per_step=statistics.median(kern_ms)),
         "clocks": clocks,
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
     }
@@ -251,12 +272,12 @@ def run_cpu_baseline(seconds_target=12.0, rank=0):
 
 
 def ncu_case(w, variant):
-    """A small case of one workload for ncu: M = 4 x 152 states (a few MB on the device),
+    """A small case of one workload for ncu: M = 12 x 152 states (a few MB on the device),
     the workload's N, two sweeps per launch, launch variant `variant`; one warm-up launch,
     then one profiled launch."""
     import torch
     from paper_2605_18566_gb300 import Solver
-    M = 4 * SMS
+    M = 12 * SMS
     x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
     s = Solver(w.game, w.nu, w.T, w.N, 2, radius=w.radius, variant=variant)
     for _ in range(2):

@@ -205,17 +205,18 @@ hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t 
 /* ---- pipe micro-benchmarks (roofline denominators) ------------------------------ */
 
 /* Instruction classes timed by hjg_microbench: FP32 FMA, the MUFU transcendental
- * approximations (ex2, lg2, sin, cos, sqrt), whole Philox4x32-10 blocks, and whole
- * Box-Muller normals as the sweep draws them. */
+ * approximations (ex2, lg2, sin, cos, sqrt), whole Philox4x32-10 blocks, whole
+ * Box-Muller normals as the sweep draws them, and 32x32->64-bit integer multiplies. */
 enum {
     HJG_MB_FFMA = 1, HJG_MB_EX2 = 2, HJG_MB_LG2 = 3, HJG_MB_SIN = 4, HJG_MB_COS = 5,
-    HJG_MB_SQRT = 6, HJG_MB_PHILOX = 7, HJG_MB_NORMALS = 8
+    HJG_MB_SQRT = 6, HJG_MB_PHILOX = 7, HJG_MB_NORMALS = 8, HJG_MB_IMAD_WIDE = 9
 };
 
 /* Run one saturating launch (8 CTAs of 256 threads per SM, 8 independent chains per
  * thread, `iters` steps per chain) of instruction class `op` on the current device and
  * return its throughput in operations (or blocks, or normals) per second, and the launch
- * time in ms.  Synchronises the device; EINVAL for an unknown op. */
+ * time in ms.  Allocates (and frees) a 1 KB sink; synchronises the device; EINVAL for an
+ * unknown op. */
 hjg_status hjg_microbench(int op, int64_t iters, double *ops_per_s, double *ms);
 
 #ifdef __cplusplus

@@ -123,13 +123,13 @@ int orc_slot_stride(int n)
 }
 
 /* The four normals of Philox block b of the stream of (point, sweep): counter
- * (b_lo, b_hi, point, sweep), key (seed_lo, seed_hi ^ instance).  Box-Muller on (u0,u1)
+ * (point, b_lo, sweep, b_hi), key (seed_lo, seed_hi ^ instance).  Box-Muller on (u0,u1)
  * gives slots 4b, 4b+1 (radius from u0, angle from u1); (u2,u3) give 4b+2, 4b+3. */
 static void block_normals(uint64_t seed, uint32_t instance, uint64_t b, uint32_t point,
                           uint32_t sweep, double zz[4])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance};
-    uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), point, sweep};
+    uint32_t ctr[4] = {point, (uint32_t)b, sweep, (uint32_t)(b >> 32)};
     uint32_t r[4];
     const double two_pi = 6.283185307179586476925286766559;
     orc_philox4x32_10(ctr, key, r);

@@ -71,7 +71,7 @@ _SIGS = {
 }
 
 MICROBENCH = {"ffma": 1, "ex2": 2, "lg2": 3, "sin": 4, "cos": 5, "sqrt": 6, "philox": 7,
-              "normals": 8}
+              "normals": 8, "imad_wide": 9}
 
 _lib = None
 

@@ -14,6 +14,25 @@ namespace {
 constexpr int kIlp = 8;
 constexpr int kThreads = 256;
 
+// Independent 32x32 -> 64-bit unsigned multiplies (IMAD.WIDE.U32), the Philox round's
+// product: 8 chains per thread, each multiply feeding the next through its high word.
+__global__ void __launch_bounds__(kThreads) imad_wide_pipe(int64_t iters, float* sink) {
+    uint32_t x[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) x[j] = threadIdx.x * 7919u + j;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const uint64_t p = (uint64_t)0xD2511F53u * x[j];
+            x[j] = (uint32_t)(p >> 32) + (uint32_t)p;
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) acc ^= x[j];
+    if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
+}
+
 template <int OP>
 __device__ __forceinline__ float step(float x) {
     if (OP == HJG_MB_FFMA) return fmaf(x, 0.9999f, 0.0001f);
@@ -40,12 +59,14 @@ __global__ void __launch_bounds__(kThreads) float_pipe(int64_t iters, float* sin
     if (acc == 1234.5f) sink[threadIdx.x] = acc;   // keeps the chains live
 }
 
-// Philox4x32-10 blocks (the sampler's integer work: IMAD.WIDE and LOP3).
+// Philox4x32-10 blocks with the sweep's counter layout (state and sweep words fixed per
+// CTA, block index varying): the sampler's integer work, IMAD.WIDE and LOP3.
 __global__ void __launch_bounds__(kThreads) philox_pipe(int64_t iters, float* sink) {
     uint32_t acc = 0;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = 0; i < iters; ++i) {
-        const uint4 r = hjg::philox4x32_10(make_uint4((uint32_t)i, t, 7u, 9u), 0x1234u, 0x5678u);
+        const uint4 r = hjg::philox4x32_10(make_uint4(blockIdx.x, (uint32_t)i * 65536u + t, 9u, 0u),
+                                           0x1234u, 0x5678u);
         acc ^= r.x ^ r.y ^ r.z ^ r.w;
     }
     if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
@@ -57,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) normals_pipe(int64_t iters, float* s
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = 0; i < iters; ++i) {
         float z[4];
-        hjg::block_normals<4>((uint32_t)i, t, 3u, 0x1234u, 0x5678u, z);
+        hjg::block_normals<4>((uint32_t)i * 65536u + t, blockIdx.x, 3u, 0x1234u, 0x5678u, z);
         acc += z[0] + z[1] + z[2] + z[3];
     }
     if (acc == 1234.5f) sink[threadIdx.x] = acc;
@@ -85,11 +106,12 @@ extern "C" hjg_status hjg_microbench(int op, int64_t iters, double* ops_per_s, d
         case HJG_MB_SQRT: float_pipe<HJG_MB_SQRT><<<grid, kThreads>>>(iters, sink); break;
         case HJG_MB_PHILOX: philox_pipe<<<grid, kThreads>>>(iters, sink); break;
         case HJG_MB_NORMALS: normals_pipe<<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_IMAD_WIDE: imad_wide_pipe<<<grid, kThreads>>>(iters, sink); break;
         }
     };
     if (op == HJG_MB_PHILOX) per_thread_iter = 1.0;   // Philox blocks
     if (op == HJG_MB_NORMALS) per_thread_iter = 4.0;  // normals
-    if (op < HJG_MB_FFMA || op > HJG_MB_NORMALS) { cudaFree(sink); return HJG_EINVAL; }
+    if (op < HJG_MB_FFMA || op > HJG_MB_IMAD_WIDE) { cudaFree(sink); return HJG_EINVAL; }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

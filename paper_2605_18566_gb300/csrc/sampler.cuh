@@ -1,8 +1,10 @@
 // sampler.cuh -- in-register counter-based Gaussian sampler for the Picard sweep.
 //
 // For each (state m, sweep k) the sampler defines one stream of standard normals: slot q
-// is lane q % 4 of Philox4x32-10 block b = q / 4, drawn with counter (b_lo, b_hi, m, k)
-// and key (seed_lo, seed_hi ^ instance) (Philox: Salmon et al., SC'11).  Within a block,
+// is lane q % 4 of Philox4x32-10 block b = q / 4, drawn with counter (m, b_lo, k, b_hi)
+// and key (seed_lo, seed_hi ^ instance) (Philox: Salmon et al., SC'11).  The block index
+// sits in the words the first round does not multiply, so the products of the first
+// rounds that depend only on (m, k) are the same for every sample of a state and sweep.  Within a block,
 // Box-Muller on (u0, u1) gives slots 4b, 4b+1 (radius from u0, angle from u1) and (u2, u3)
 // gives 4b+2, 4b+3, with u = ((r & (2^23-1)) + 0.5) 2^-23.  Sample i of a game with n
 // state dimensions reads slots i*S .. i*S + n - 1, S = n for n <= 8 (consecutive samples
@@ -51,9 +53,12 @@ __device__ __forceinline__ float cos_approx(float x) {
     float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y;
 }
 
-// The low 23 bits of r as a float in [1, 2): 1 + (r & (2^23-1)) 2^-23 (exact, one LOP3).
+// The low 23 bits of r as a float in [1, 2): 1 + (r & (2^23-1)) 2^-23 (exact): a single
+// three-input logic operation (r & 0x7FFFFF) | one, with `one` held in a register.
 __device__ __forceinline__ float mant_one_two(uint32_t r) {
-    return __uint_as_float((r & 0x007FFFFFu) | 0x3F800000u);
+    uint32_t one = 0x3F800000u, y;
+    asm("lop3.b32 %0, %1, 0x007FFFFF, %2, 0xEA;" : "=r"(y) : "r"(r), "r"(one));
+    return __uint_as_float(y);
 }
 
 // u = ((r & (2^23-1)) + 0.5) 2^-23, exactly (the sum below is exact in binary32).
@@ -104,7 +109,7 @@ constexpr float kBmScale = -1.1774100225154747f;
 template <int NUSE>
 __device__ __forceinline__ void block_normals_raw(uint32_t b, uint32_t point, uint32_t sweep,
                                                   const PhiloxKeys& rk, float* z) {
-    const uint4 r = philox4x32_10_rk(make_uint4(b, 0u, point, sweep), rk);
+    const uint4 r = philox4x32_10_rk(make_uint4(point, b, sweep, 0u), rk);
     {
         const float ra = sqrt_approx(fabsf(lg2_approx(u01(r.x))));
         const float ph = bm_phase(r.y);

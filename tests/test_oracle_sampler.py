@@ -112,7 +112,7 @@ def test_box_muller_pair_structure():
     key = np.array([[seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ inst]], dtype=np.uint32)
     for j in range(2):
         b = 2 * sample + j
-        blk = oracle.philox4x32_10(np.array([[b, 0, point, sweep]], dtype=np.uint32), key)[0]
+        blk = oracle.philox4x32_10(np.array([[point, b, sweep, 0]], dtype=np.uint32), key)[0]
         u = [oracle.u01(int(v)) for v in blk]
         for q in (0, 2):
             za, zb = z[4 * j + q], z[4 * j + q + 1]
@@ -136,14 +136,14 @@ def test_slot_packing(n):
 
 def test_normals_distribution():
     n = 6
-    Z = np.array([oracle.normals(n, 0, 0, i, 3, 1) for i in range(40000)])
+    Z = np.array([oracle.normals(n, 0, 0, i, 3, 1) for i in range(100000)])
     # mean, variance, no cross-correlation, Gaussian shape
     assert np.all(np.abs(Z.mean(0)) < 5 / np.sqrt(len(Z)))
     np.testing.assert_allclose(Z.var(0), 1.0, atol=0.03)
     C = np.corrcoef(Z.T)
     assert np.max(np.abs(C - np.eye(n))) < 0.03
-    for d in range(n):
-        assert stats.kstest(Z[:, d], "norm").pvalue > 1e-3
+    for d in range(n):      # six tests: a 1e-4 level each keeps false alarms below 1e-3
+        assert stats.kstest(Z[:, d], "norm").pvalue > 1e-4
     # different points / sweeps draw different samples
     a = oracle.normals(n, 0, 0, 0, 0, 0)
     assert not np.allclose(a, oracle.normals(n, 0, 0, 0, 1, 0))
