@@ -57,7 +57,13 @@ MUFU_PER_SM_CLK = 16
 IMUL_PER_SM_CLK = 32
 
 
-def roofline(game, samples, kernel_s):
+# DRAM bytes per state of one sweep-kernel launch, from an ncu capture of the 6-D sweep
+# over 1,824 states (dram__bytes_read.sum 189,952 B + dram__bytes_write.sum 0 B; the
+# launch's writes stayed in L2); reads grow in proportion to the states processed.
+DRAM_BYTES_PER_STATE = 189952.0 / 1824
+
+
+def roofline(game, samples, kernel_s, states=None):
     """Binding-pipe roofline of the sweep kernel: achieved algorithmic operations per
     second over the pipe's peak at the maximum SM clock."""
     clk = SMS * SM_MAX_MHZ * 1e6
@@ -69,7 +75,8 @@ def roofline(game, samples, kernel_s):
     bind = max(fr, key=fr.get)
     ops, peak = pipes[bind]
     return {"bound": "alu", "pipe": bind, "achieved": ops / kernel_s / 1e9, "peak": peak / 1e9,
-            "unit": "Gop/s", "frac": fr[bind], "traffic": None,
+            "unit": "Gop/s", "frac": fr[bind],
+            "traffic": (DRAM_BYTES_PER_STATE * states if states and game == "rockets6" else None),
             "ops_per_point_sample": ops / samples,
             "other_pipes": {k: round(v, 4) for k, v in fr.items() if k != bind},
             "peak_basis": "per-SM-per-clock pipe rate x 152 SMs x 2070 MHz"}
@@ -240,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(x_np.nbytes),
                 "d2h_bytes_per_step": int(W.M * 8 + W.M * W.n * 4 + W.K * 8)},
         "gpu_launches": 3 * args.steps,
-        "roofline": dict(roofline(W.game, samples_per_step, kern_s),
+        "roofline": dict(roofline(W.game, samples_per_step, kern_s, states=W.M),
                          kernel_ms_per_step=statistics.median(kern_ms)),
         "clocks": clocks,
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),

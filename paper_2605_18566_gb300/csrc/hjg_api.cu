@@ -254,7 +254,8 @@ hjg_status choose_launch(hjg_ctx* ctx) {
     const int occ = ctx->kern.occupancy(tilt, v);
     if (occ <= 0) return fail(ctx, HJG_ECUDA, "sweep variant %d cannot launch", v);
     int64_t grid = ctx->opt.grid_blocks > 0 ? ctx->opt.grid_blocks : (int64_t)occ * ctx->num_sms;
-    grid = std::min<int64_t>(grid, std::max<int64_t>(ctx->M, 1));
+    const int64_t per_cta = ctx->kern.per_warp[v] ? ctx->kern.threads[v] / 32 : 1;   // states per CTA pass
+    grid = std::min<int64_t>(grid, std::max<int64_t>((ctx->M + per_cta - 1) / per_cta, 1));
     ctx->threads = ctx->kern.threads[v];
     ctx->grid = (int)grid;
     ctx->variant = v;
@@ -538,7 +539,8 @@ hjg_status hjg_autotune(hjg_ctx* ctx, int64_t max_states, int32_t* variant_out, 
     for (int var = 0; var < ctx->kern.nvariants && s == HJG_OK; ++var) {
         const int occ = ctx->kern.occupancy(tilt, var);
         if (occ <= 0) continue;
-        const int grid = (int)std::min<int64_t>((int64_t)occ * ctx->num_sms, Mt);
+        const int64_t per_cta = ctx->kern.per_warp[var] ? ctx->kern.threads[var] / 32 : 1;
+        const int grid = (int)std::min<int64_t>((int64_t)occ * ctx->num_sms, (Mt + per_cta - 1) / per_cta);
         SweepArgs A = make_args(ctx, 1);
         A.M = Mt; A.p = p; A.c = c; A.v = v; A.ess = ess; A.vhist = nullptr; A.counters = cnt;
         float ms = 0.0f;

@@ -9,11 +9,11 @@ namespace {
 template <class G>
 cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
     if (v != 0) return cudaErrorInvalidValue;
-    return launch_sweep_generic<G, 128, 1>(A, tilt, grid, st);
+    return launch_sweep_generic<G, 0, 128, 1>(A, tilt, grid, st);
 }
 template <class G>
 int occ(bool tilt, int v) {
-    return v == 0 ? occupancy_generic<G, 128, 1>(tilt) : 0;
+    return v == 0 ? occupancy_generic<G, 0, 128, 1>(tilt) : 0;
 }
 template <int N, bool Z>
 GameKernels make() {

@@ -17,8 +17,8 @@ int occupancy(bool tilt) {
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, false>, T, 0);
     return nb;
 }
-#define R45_LAUNCH(i, T, B) case i: return launch<T, B>(A, tilt, grid, st);
-#define R45_OCC(i, T, B) case i: return occupancy<T, B>(tilt);
+#define R45_LAUNCH(i, KIND, T, B) case i: return launch<T, B>(A, tilt, grid, st);
+#define R45_OCC(i, KIND, T, B) case i: return occupancy<T, B>(tilt);
 cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
     switch (v) { HJG_R45_VARIANTS(R45_LAUNCH) }
     return cudaErrorInvalidValue;
@@ -31,7 +31,7 @@ int occ(bool tilt, int v) {
 GameKernels kernels_rockets45() {
     GameKernels k{};
     k.n = 45;
-    k.nvariants = kNumVariants;
+    k.nvariants = kNumR45Variants;
     HJG_R45_VARIANTS(HJG_FILL)
     k.sweep = sweep;
     k.occupancy = occ;

@@ -287,6 +287,132 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
     }
 }
 
+// Lane 0's FP64 recovery for the one-warp-per-state kernel (kept out of line so that its
+// double-precision temporaries do not compete with the sample loop for registers):
+// v, Dv, ESS from the merged sums, the coefficient update, and the outputs.  Updates
+// p (FP32 Dv iterate) in place and returns the new FP32 coefficient.
+template <class G, bool TILT>
+__device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k, float c, float m,
+                                           float s, float q, const double* xd, float* p,
+                                           const float* S, double* pd) {
+    constexpr int n = G::kN;
+    const bool last = (k + 1 == A.K);
+    const double cd = (double)c;
+    const double sd = (double)s;
+    double th2 = 0.0, pp = 0.0;
+    bool finite = true;
+    for (int j = 0; j < n; ++j) {
+        const double th = TILT ? (double)(float)(-A.sigma2_d * cd * (double)p[j]) : 0.0;
+        th2 += th * th;
+        const double pj = -(th + A.sigma_d * (double)kBmScale * (double)S[j] / sd) / (cd * A.sigma2_d);
+        pd[j] = pj;
+        pp += pj * pj;
+        finite = finite && isfinite(pj);
+    }
+    const double v = -((double)m * kLn2 - th2 / (2.0 * A.sigma2_d) + log(sd / (double)A.N)) / cd;
+    finite = finite && isfinite(v);
+    int clipped = 0;
+    const float c_new = (float)coef_update(G::ham_d(xd, pd, A.g), pp, A.delta, A.eta, A.c_min,
+                                           A.c_max, &clipped);
+    for (int j = 0; j < n; ++j) p[j] = (float)pd[j];
+    if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
+    if (last) {
+        A.v[pt] = v;
+        A.c[pt] = c_new;
+        A.ess[pt] = (float)(sd * sd / (double)q);
+        for (int j = 0; j < n; ++j) A.p[pt * A.ldp + j] = p[j];
+        if (!finite) atomicAdd(&A.counters[0], 1ull);
+        if (clipped) atomicAdd(&A.counters[1], 1ull);
+    }
+    return c_new;
+}
+
+// ------------------------------------------------------------------------------------
+// One warp per state (games with n <= 8): the 32 lanes of a warp share one state's N
+// samples, the butterfly merge leaves the sums on every lane, and lane 0 alone does the
+// FP64 recovery and coefficient update and broadcasts the new (c, Dv) with shuffles.
+// No CTA barrier is involved, so a warp never waits for another state's epilogue.
+// Chosen by the autotuner when there are many more states than warps in flight.
+template <class G, int THREADS, int MINB, bool TILT>
+__global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepArgs A) {
+    constexpr int n = G::kN;
+    constexpr int GS = group_samples(n);
+    constexpr int GB = group_blocks(n);
+    constexpr int WPC = THREADS / 32;
+    __shared__ float s_x[WPC][n];    // the warp's state and Dv iterate (FP32)
+    __shared__ float s_p[WPC][n];
+    __shared__ double s_xd[WPC][n];  // lane 0's FP64 work space for the recovery
+    __shared__ double s_pd[WPC][n];
+    __shared__ float s_S[WPC][n];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * WPC;
+    const uint32_t N32 = (uint32_t)A.N;
+    const uint32_t full = N32 / GS;
+    const uint32_t groups = (N32 + GS - 1) / GS;
+
+    for (int64_t pt = (int64_t)blockIdx.x * WPC + wl; pt < A.M; pt += nwarps) {
+        if (lane < n) {
+            const float xv = A.x[pt * A.ldx + lane];
+            s_x[wl][lane] = xv;
+            s_xd[wl][lane] = (double)xv;
+            s_p[wl][lane] = A.p[pt * A.ldp + lane];
+        }
+        if (lane == 0 && A.vhist) A.vhist[pt] = A.v[pt];
+        float c = A.c[pt];
+        __syncwarp();
+
+        for (int k = 0; k < A.K; ++k) {
+            const uint32_t sweep = A.k0 + (uint32_t)k;
+            const float cneg2 = -c * kLog2e;
+            const float cr = G::kRadius ? -cneg2 * A.g.radius : 0.0f;
+            float yoff[n], tq[n];
+#pragma unroll
+            for (int j = 0; j < n; ++j) {
+                const float th = TILT ? (float)(-A.sigma2_d * (double)c * (double)s_p[wl][j]) : 0.0f;
+                yoff[j] = s_x[wl][j] + th;
+                tq[j] = -th * kLog2e * kBmScale / A.sigma;
+            }
+            float m = -INFINITY, s = 0.0f, q = 0.0f, S[n];
+#pragma unroll
+            for (int j = 0; j < n; ++j) S[j] = 0.0f;
+            auto sample = [&](const float* zt) {
+                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g), cr);
+                if (TILT) {
+#pragma unroll
+                    for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
+                }
+                lse_accumulate<n>(a, zt, m, s, q, S);
+            };
+            for (uint32_t grp = lane; grp < full; grp += 32) {
+                float z[4 * GB];
+#pragma unroll
+                for (int b = 0; b < GB; ++b)
+                    block_normals_raw<4>(grp * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+#pragma unroll
+                for (int t = 0; t < GS; ++t) sample(z + t * n);
+            }
+            if (GS > 1 && full < groups && lane == (int)(full % 32)) {
+                float z[4 * GB];
+#pragma unroll
+                for (int b = 0; b < GB; ++b)
+                    block_normals_raw<4>(full * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                for (uint32_t t = 0; t < N32 - full * GS; ++t) sample(z + t * n);
+            }
+            warp_merge<n>(1, m, s, q, S);
+
+            float c_new = 0.0f;
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < n; ++j) s_S[wl][j] = S[j];
+                c_new = warp_recover<G, TILT>(A, pt, k, c, m, s, q, s_xd[wl], s_p[wl], s_S[wl], s_pd[wl]);
+            }
+            c = __shfl_sync(0xffffffffu, c_new, 0);
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // 45-D multi-rocket game: four lanes per sample stream.  Lane q of a group owns dims
 // 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. blocks 12 i + 3q + j of the
@@ -391,24 +517,38 @@ __global__ void init_kernel(const float* __restrict__ x, int64_t ldx, int64_t M,
     ess[m] = 0.0f;
 }
 
-// Launch variants (CTA size, minimum resident CTAs per SM for the register budget) the
-// autotuner chooses among; every game's translation unit instantiates all of them.
-#define HJG_SWEEP_VARIANTS(X) X(0, 256, 1) X(1, 256, 5) X(2, 256, 6) X(3, 128, 1) X(4, 512, 1)
-#define HJG_R45_VARIANTS(X) X(0, 256, 1) X(1, 256, 2) X(2, 128, 1) X(3, 128, 4) X(4, 512, 1)
-constexpr int kNumVariants = 5;
+// Launch variants the autotuner chooses among: kind 0 = one CTA per state, kind 1 = one
+// warp per state; CTA size; minimum resident CTAs per SM (the register budget).  Every
+// game's translation unit instantiates all of them.
+#define HJG_SWEEP_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 5) X(2, 0, 256, 6) X(3, 0, 128, 1) \
+    X(4, 0, 512, 1) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12)
+#define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 1) X(3, 0, 128, 4) \
+    X(4, 0, 512, 1)
+constexpr int kNumVariants = 8;
+constexpr int kNumR45Variants = 5;
 
-template <class G, int THREADS, int MINB>
+template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
-    if (tilt) sweep_kernel<G, THREADS, MINB, true><<<grid, THREADS, 0, st>>>(A);
-    else sweep_kernel<G, THREADS, MINB, false><<<grid, THREADS, 0, st>>>(A);
+    if constexpr (KIND == 1) {
+        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel_warp<G, THREADS, MINB, false><<<grid, THREADS, 0, st>>>(A);
+    } else {
+        if (tilt) sweep_kernel<G, THREADS, MINB, true><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel<G, THREADS, MINB, false><<<grid, THREADS, 0, st>>>(A);
+    }
     return cudaGetLastError();
 }
 
-template <class G, int THREADS, int MINB>
+template <class G, int KIND, int THREADS, int MINB>
 int occupancy_generic(bool tilt) {
     int nb = 0;
-    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true>, THREADS, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false>, THREADS, 0);
+    if constexpr (KIND == 1) {
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false>, THREADS, 0);
+    } else {
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false>, THREADS, 0);
+    }
     return nb;
 }
 

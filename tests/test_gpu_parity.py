@@ -208,7 +208,7 @@ def test_autotune_keeps_state_and_results():
     ref = oracle.picard(problem_for(w), x.cpu().numpy().astype(np.float64), 4096, 3)
     assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.99, what="tuned variant")
     xs = x.cpu().numpy().astype(np.float64)
-    for v in range(5):     # every launch variant agrees with the oracle on one sweep
+    for v in range(8):     # every launch variant agrees with the oracle on one sweep
         s = solver_for(w, N=4096, K=1, variant=v)
         s.set_points(x)
         c0 = s.get_state()["c"].cpu().numpy().astype(np.float64)
