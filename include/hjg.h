@@ -202,6 +202,30 @@ hjg_status hjg_philox_blocks(const uint32_t *ctr, const uint32_t *key, uint32_t 
 hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point,
                               uint32_t sweep, int64_t n_samples, float *out, void *stream);
 
+/* ---- batches: many instances, one CUDA-graph launch ------------------------------- */
+
+/* A batch advances several instances (contexts, possibly of different games, dimensions
+ * and state counts) by the same number of Picard sweeps in one CUDA-graph launch: each
+ * instance's fused sweep kernel and residual kernel run on their own branch of the graph,
+ * concurrently on the SMs.  This is Algorithm 1 applied to each instance independently
+ * (instances share nothing).  The contexts stay owned by the caller and must outlive the
+ * batch; their points must be loaded (hjg_set_points) before each run. */
+typedef struct hjg_batch hjg_batch;
+
+hjg_status hjg_batch_create(hjg_batch **out);
+/* Add an instance; EINVAL if it is already in the batch. */
+hjg_status hjg_batch_add(hjg_batch *b, hjg_ctx *ctx);
+/* Run n_sweeps sweeps of every instance in one graph launch on `stream` (NULL: a private
+ * stream, and the call synchronises).  The graph is captured on each call and the
+ * instantiated graph updated in place (the sweep counters advance between calls).
+ * residual_out: host [instances][n_sweeps] relative L2 residuals, or NULL (then, with a
+ * caller stream, the call is asynchronous).  device_ms: device time of the graph launch,
+ * or NULL.  ENONFINITE if an instance produced non-finite values. */
+hjg_status hjg_batch_run(hjg_batch *b, int n_sweeps, double *residual_out, void *stream,
+                         double *device_ms);
+void hjg_batch_destroy(hjg_batch *b);
+const char *hjg_batch_last_error(const hjg_batch *b);
+
 /* ---- pipe micro-benchmarks (roofline denominators) ------------------------------ */
 
 /* Instruction classes timed by hjg_microbench: FP32 FMA, the MUFU transcendental

@@ -4,7 +4,7 @@ The compute path is libhjg.so (hand-written CUDA, C ABI in include/hjg.h); this 
 is its Python binding.  Import fails loudly if the library has not been built.
 """
 from ._lib import HJGError, load, symbols  # noqa: F401
-from .solver import Solver, microbench, philox_blocks, sample_normals  # noqa: F401
+from .solver import Batch, Solver, microbench, philox_blocks, sample_normals  # noqa: F401
 
-__all__ = ["Solver", "HJGError", "microbench", "philox_blocks", "sample_normals", "load",
+__all__ = ["Batch", "Solver", "HJGError", "microbench", "philox_blocks", "sample_normals", "load",
            "symbols"]

@@ -63,6 +63,11 @@ _SIGS = {
     "hjg_value_grad_noalloc": (C.c_int, [C.POINTER(Dynamics), C.POINTER(Target), C.c_double,
                                          C.c_double, C.POINTER(Options), _vp, C.c_int64,
                                          C.c_int64, _vp, _vp, C.c_int64, _vp, _vp]),
+    "hjg_batch_create": (C.c_int, [C.POINTER(_vp)]),
+    "hjg_batch_add": (C.c_int, [_vp, _vp]),
+    "hjg_batch_run": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),
+    "hjg_batch_destroy": (None, [_vp]),
+    "hjg_batch_last_error": (C.c_char_p, [_vp]),
     "hjg_philox_blocks": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
     "hjg_sample_normals": (C.c_int, [C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                      C.c_int64, _vp, _vp]),

@@ -590,4 +590,160 @@ hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t 
     return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Batches: several game instances (contexts) advanced together by one CUDA-graph launch.
+// Each instance's sweep and residual kernels sit on their own branch of the graph, so
+// instances of different games and sizes run concurrently on the SMs.
+
+struct hjg_batch {
+    std::vector<hjg_ctx*> ctxs;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double last_ms = 0;
+    std::string err;
+};
+
+hjg_status hjg_batch_create(hjg_batch** out) {
+    if (!out) return HJG_EINVAL;
+    hjg_batch* b = new (std::nothrow) hjg_batch();
+    if (!b) return HJG_ENOMEM;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
+        delete b;
+        return HJG_ECUDA;
+    }
+    *out = b;
+    return HJG_OK;
+}
+
+hjg_status hjg_batch_add(hjg_batch* b, hjg_ctx* ctx) {
+    if (!b || !ctx) return HJG_EINVAL;
+    for (hjg_ctx* c : b->ctxs)
+        if (c == ctx) return HJG_EINVAL;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return HJG_ECUDA;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return HJG_ECUDA;
+    }
+    b->ctxs.push_back(ctx);
+    b->side.push_back(s);
+    b->join.push_back(e);
+    return HJG_OK;
+}
+
+void hjg_batch_destroy(hjg_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    delete b;
+}
+
+const char* hjg_batch_last_error(const hjg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+hjg_status hjg_batch_run(hjg_batch* b, int n_sweeps, double* residual_out, void* stream, double* device_ms) {
+    if (!b) return HJG_EINVAL;
+    if (n_sweeps < 1) return HJG_EINVAL;
+    const size_t I = b->ctxs.size();
+    for (hjg_ctx* c : b->ctxs) {
+        if (c->M == 0) { b->err = "a batch instance has no states loaded"; return HJG_EINVAL; }
+        if ((uint64_t)c->next_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull) return HJG_EINVAL;
+        hjg_status s;
+        if ((s = ensure_history(c, n_sweeps)) || (s = choose_launch(c))) {
+            b->err = c->err;
+            return s;
+        }
+    }
+    cudaStream_t origin = (cudaStream_t)stream;
+    bool own_origin = false;
+    if (!origin) {   // capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess) return HJG_ECUDA;
+        own_origin = true;
+    }
+    auto bail = [&](const char* what, cudaError_t e) {
+        cudaGraph_t g = nullptr;
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(origin, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(origin, &g);
+        if (g) cudaGraphDestroy(g);
+        if (own_origin) cudaStreamDestroy(origin);
+        b->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? HJG_ENOMEM : HJG_ECUDA;
+    };
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail("begin capture", e);
+    if ((e = cudaEventRecord(b->fork, origin)) != cudaSuccess) return bail("fork", e);
+    for (size_t i = 0; i < I; ++i) {
+        hjg_ctx* c = b->ctxs[i];
+        cudaStream_t s = b->side[i];
+        if ((e = cudaStreamWaitEvent(s, b->fork, 0)) != cudaSuccess) return bail("wait fork", e);
+        if ((e = cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+            return bail("counters", e);
+        SweepArgs A = make_args(c, n_sweeps);
+        if ((e = c->kern.sweep(A, c->opt.tilt != 0, c->variant, c->grid, s)) != cudaSuccess)
+            return bail("sweep", e);
+        residual_kernel<<<n_sweeps, 256, 0, s>>>(c->d_vhist, c->M, c->d_resid);
+        if ((e = cudaGetLastError()) != cudaSuccess) return bail("residual", e);
+        if ((e = cudaEventRecord(b->join[i], s)) != cudaSuccess) return bail("join", e);
+        if ((e = cudaStreamWaitEvent(origin, b->join[i], 0)) != cudaSuccess) return bail("wait join", e);
+    }
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamEndCapture(origin, &g)) != cudaSuccess) return bail("end capture", e);
+    bool updated = false;
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(b->exec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (!updated && (e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return bail("instantiate", e);
+    }
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph = g;
+    if ((e = cudaEventRecord(b->t0, origin)) != cudaSuccess) return bail("timing", e);
+    if ((e = cudaGraphLaunch(b->exec, origin)) != cudaSuccess) return bail("graph launch", e);
+    if ((e = cudaEventRecord(b->t1, origin)) != cudaSuccess) return bail("timing", e);
+    for (hjg_ctx* c : b->ctxs) {
+        c->next_sweep += (uint32_t)n_sweeps;
+        c->last_sweeps = n_sweeps;
+    }
+    hjg_status result = HJG_OK;
+    if (residual_out || device_ms || own_origin) {
+        if ((e = cudaStreamSynchronize(origin)) != cudaSuccess) return bail("synchronize", e);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, b->t0, b->t1);
+        b->last_ms = ms;
+        if (device_ms) *device_ms = ms;
+        for (size_t i = 0; i < I && residual_out; ++i) {
+            hjg_ctx* c = b->ctxs[i];
+            std::vector<double> r(2 * (size_t)n_sweeps);
+            unsigned long long cnt[4];
+            if ((e = cudaMemcpy(r.data(), c->d_resid, r.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+                (e = cudaMemcpy(cnt, c->d_counters, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return bail("copy residuals", e);
+            for (int k = 0; k < n_sweeps; ++k) residual_out[i * n_sweeps + k] = r[2 * k];
+            c->nonfinite = (int64_t)cnt[0];
+            c->clipped = (int64_t)cnt[1];
+            if (cnt[0]) result = HJG_ENONFINITE;
+        }
+    }
+    if (own_origin) cudaStreamDestroy(origin);
+    return result;
+}
+
 }  // extern "C"

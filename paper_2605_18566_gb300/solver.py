@@ -177,6 +177,44 @@ class Solver:
         return {f: getattr(d, f) for f, _ in _lib.Diag._fields_}
 
 
+class Batch:
+    """Several Solver instances advanced by one CUDA-graph launch (hjg_batch_*)."""
+
+    def __init__(self, solvers):
+        self.lib = _lib.load()
+        self.solvers = list(solvers)
+        b = C.c_void_p()
+        st = self.lib.hjg_batch_create(C.byref(b))
+        if st:
+            raise HJGError(st, "hjg_batch_create")
+        self.b = b
+        for s in self.solvers:
+            st = self.lib.hjg_batch_add(self.b, s.ctx)
+            if st:
+                raise HJGError(st, "hjg_batch_add")
+
+    def run(self, n_sweeps: int, stream: Optional[torch.cuda.Stream] = None):
+        """Returns (residuals [instances, n_sweeps] numpy, device ms)."""
+        r = np.zeros((len(self.solvers), n_sweeps))
+        ms = C.c_double()
+        st = self.lib.hjg_batch_run(self.b, n_sweeps, r.ctypes.data_as(C.c_void_p),
+                                    _stream_handle(stream), C.byref(ms))
+        if st not in (_lib.HJG_OK, _lib.HJG_ENONFINITE):
+            raise HJGError(st, self.lib.hjg_batch_last_error(self.b).decode())
+        return r, ms.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.hjg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def philox_blocks(ctr: torch.Tensor, key: torch.Tensor) -> torch.Tensor:
     """Device Philox4x32-10: ctr int32/uint32 [K,4], key [K,2] (CUDA tensors)."""
     lib = _lib.load()
