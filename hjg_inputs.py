@@ -52,7 +52,13 @@ class Workload:
 DUBINS3 = Workload("dubins3_grid16", "dubins3", 3, 0.1, 1.0, 4096, 4096, 10, 0.5)
 ROCKETS6 = Workload("rockets6_uniform", "rockets6", 6, 0.05, 2.0, 65536, 65536, 20, 0.3)
 ROCKETS45 = Workload("rockets45_gauss", "rockets45", 45, 0.05, 2.0, 262144, 131072, 30, 0.3)
-WORKLOADS = {w.name: w for w in (DUBINS3, ROCKETS6, ROCKETS45)}
+FLOCK = Workload("flock_murmuration", "flock4", 4, 0.02, 1.0, 100000, 16384, 15, 0.2)
+WORKLOADS = {w.name: w for w in (DUBINS3, ROCKETS6, ROCKETS45, FLOCK)}
+
+# The mixed batch that runs alongside the flock: (workload, states) per instance, all at
+# nu = 0.02, T = 1, N = 16,384, 15 sweeps.
+MIXED = [(DUBINS3, 1024), (DUBINS3, 65536), (ROCKETS6, 4096), (ROCKETS6, 131072),
+         (ROCKETS45, 16384), (ROCKETS45, 262144)]
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -85,6 +91,22 @@ def rockets45_points(M: int, seed: int = 0) -> np.ndarray:
     return np.concatenate([pos, ang], axis=2).reshape(M, 45).astype(np.float32)
 
 
+def flock_states(M: int, seed: int = 0, clusters: int = 6, ring: float = 40.0,
+                 std: float = 2.4, heading_std: float = 0.3) -> np.ndarray:
+    """M starlings (p_x, p_y, p_z, psi) in `clusters` Gaussian flocks spaced on a ring of
+    radius `ring` in the horizontal plane; per-axis spread `std` (2.4 puts the median
+    nearest-neighbour distance at about 0.2); each flock's mean heading is the ring's
+    tangent there, each bird's heading that plus N(0, heading_std^2), wrapped to [-pi, pi)."""
+    r = _rng(seed)
+    k = np.arange(M) % clusters
+    ang = 2.0 * math.pi * k / clusters
+    centers = np.stack([ring * np.cos(ang), ring * np.sin(ang), np.zeros(M)], axis=1)
+    pos = centers + r.normal(0.0, std, size=(M, 3))
+    psi = ang + 0.5 * math.pi + r.normal(0.0, heading_std, size=M)
+    psi = (psi + math.pi) % (2.0 * math.pi) - math.pi
+    return np.concatenate([pos, psi[:, None]], axis=1).astype(np.float32)
+
+
 def points(w: Workload, M: int | None = None, seed: int | None = None) -> np.ndarray:
     """Evaluation states of workload ``w`` (first M of them when M is given)."""
     seed = w.seed if seed is None else seed
@@ -96,6 +118,8 @@ def points(w: Workload, M: int | None = None, seed: int | None = None) -> np.nda
         return rockets6_points(M, seed)
     if w.game == "rockets45":
         return rockets45_points(M, seed)
+    if w.game == "flock4":
+        return flock_states(M, seed)
     raise KeyError(w.game)
 
 

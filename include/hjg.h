@@ -63,7 +63,13 @@ typedef enum {
                            l = |(xA,zA) - (xB,zB)| - radius.  n = 6. */
     HJG_ROCKETS45 = 3,  /* Section 3.2: 15 agents (x_i, z_i, th_i), agent 15 evades;
                            l = min_{i<=14} |pos_i - pos_15| - radius.  n = 45. */
-    HJG_FLOCK4 = 4,     /* reserved: murmuration agent game (Appendix D.5) */
+    HJG_FLOCK4 = 4,     /* one agent of a murmuration (Appendix D.5, per-agent reading): state
+                           (p_x, p_y, p_z, psi); p' = (a cos psi, a sin psi, u_z), psi' =
+                           wrap(psibar - psi) + d, |u_z|, |d| <= 1, u_z maximises, d minimises;
+                           l = distance to the nearest of the agent's 7 nearest neighbours minus
+                           radius.  The loaded states are the agents themselves: hjg_set_points
+                           finds each one's neighbours and their circular mean heading psibar
+                           and holds them frozen for the solve.  n = 4, M >= 8. */
     HJG_TEST_QUADRATIC = 100, /* H = h_sign |p|^2 / 2, l = (y-x0)^T A (y-x0)/2 + d; n <= 8 */
     HJG_TEST_ZERO_H = 101     /* H = 0 (pure heat equation), same quadratic l; n <= 8 */
 } hjg_game;
@@ -201,6 +207,14 @@ hjg_status hjg_philox_blocks(const uint32_t *ctr, const uint32_t *key, uint32_t 
  * 0..n_samples-1: out is device [n_samples][n] FP32. */
 hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point,
                               uint32_t sweep, int64_t n_samples, float *out, void *stream);
+
+/* Neighbour structure of a flock (the HJG_FLOCK4 game): for agent states [M][ld] FP32
+ * (ld >= 4; components 0..2 position, 3 heading), idx_out [M][k] int32 receives the k
+ * nearest other agents (exact, squared FP32 distance, ties by index) and psibar_out [M]
+ * FP32 (or NULL) the circular mean atan2(sum sin psi_j, sum cos psi_j) of their headings.
+ * k must be 7; device pointers; asynchronous on stream. */
+hjg_status hjg_flock_neighbours(const float *states, int64_t M, int64_t ld, int k, int32_t *idx_out,
+                                float *psibar_out, void *stream);
 
 /* ---- batches: many instances, one CUDA-graph launch ------------------------------- */
 

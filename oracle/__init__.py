@@ -258,5 +258,25 @@ def residual(v_old, v_new):
     return rel.value, sup.value
 
 
+def flock_neighbours(states, k=7):
+    """Each agent's k nearest other agents (positions = state components 0..2, FP64
+    distances, library k-d tree), their positions [M, 3k] and the circular mean of their
+    headings psibar = atan2(sum sin psi_j, sum cos psi_j) (Appendix D.5, per-agent
+    reading of the heading average)."""
+    from scipy.spatial import cKDTree
+    st = np.asarray(states, dtype=np.float64)
+    pos = st[:, :3]
+    M = len(st)
+    d, idx = cKDTree(pos).query(pos, k=k + 1)
+    out = np.empty((M, k), dtype=np.int64)
+    for i in range(M):
+        row = [j for j in idx[i] if j != i][:k]
+        out[i] = row
+    nbr = pos[out].reshape(M, 3 * k)
+    psi = st[:, 3]
+    psibar = np.arctan2(np.sin(psi[out]).sum(1), np.cos(psi[out]).sum(1))
+    return out, nbr, psibar
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())

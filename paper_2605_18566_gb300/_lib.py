@@ -63,6 +63,7 @@ _SIGS = {
     "hjg_value_grad_noalloc": (C.c_int, [C.POINTER(Dynamics), C.POINTER(Target), C.c_double,
                                          C.c_double, C.POINTER(Options), _vp, C.c_int64,
                                          C.c_int64, _vp, _vp, C.c_int64, _vp, _vp]),
+    "hjg_flock_neighbours": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int, _vp, _vp, _vp]),
     "hjg_batch_create": (C.c_int, [C.POINTER(_vp)]),
     "hjg_batch_add": (C.c_int, [_vp, _vp]),
     "hjg_batch_run": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),

@@ -19,13 +19,20 @@ struct GameKernels {
     int (*occupancy)(bool tilt, int v);
     cudaError_t (*init)(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta,
                         double eta, double c_min, double c_max, double* v, float* p, int64_t ldp,
-                        float* c, float* ess, cudaStream_t st);
+                        float* c, float* ess, cudaStream_t st, const float* aux, int64_t ldaux);
 };
 
 GameKernels kernels_dubins3();
 GameKernels kernels_rockets6();
 GameKernels kernels_rockets45();
+GameKernels kernels_flock4();
 bool kernels_quadratic(int n, bool zero_h, GameKernels* out);
+
+// Flock neighbour structure (flock.cu): 7 nearest agents, their mean heading, and the
+// per-agent game data [M][kFlockAux] (neighbour positions, then the mean heading).
+constexpr int kFlockAux = 22;
+cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* idx, float* psibar,
+                             float* aux, int64_t ldaux, cudaStream_t st);
 
 }  // namespace hjg
 

@@ -41,28 +41,29 @@ __device__ __forceinline__ float sqrtf_fast(float a) {
 struct Dubins3 {
     static constexpr int kN = 3;
     static constexpr bool kRadius = true;
+    static constexpr int kAux = 0;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
-                                                 const GameParams&) {
+                                                 const GameParams&, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
         return sqrtf_fast(fmaf(y0, y0, y1 * y1));
     }
-    __device__ static double ell_d(const double* x, const GameParams& g) {
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
         return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
         const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
         gr[0] = rho > 0 ? x[0] / rho : 0.0;
         gr[1] = rho > 0 ? x[1] / rho : 0.0;
         gr[2] = 0.0;
     }
-    __device__ static double ham_d(const double* x, const double* p, const GameParams&) {
+    __device__ static double ham_d(const double* x, const double* p, const GameParams&, const float* = nullptr) {
         double s, c;
         sincos(x[2], &s, &c);
         return p[0] * (c - 1.0) + p[1] * s + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
     }
     // Per-state trigonometric cache of H (computed once per state, one value per thread).
     static constexpr int kCache = 2;
-    __device__ static double cache(const double* x, int j) { return j == 0 ? cos(x[2]) : sin(x[2]); }
+    __device__ static double cache(const double* x, int j, const float* = nullptr) { return j == 0 ? cos(x[2]) : sin(x[2]); }
     __device__ static double ham_c(const double* x, const double* hc, const double* p, const GameParams&) {
         return p[0] * (hc[0] - 1.0) + p[1] * hc[1] + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
     }
@@ -74,23 +75,24 @@ struct Dubins3 {
 struct Rockets6 {
     static constexpr int kN = 6;
     static constexpr bool kRadius = true;
+    static constexpr int kAux = 0;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
-                                                 const GameParams&) {
+                                                 const GameParams&, const float* = nullptr) {
         const float dx = fmaf(sk, z[0] - z[2], yoff[0] - yoff[2]);
         const float dz = fmaf(sk, z[1] - z[3], yoff[1] - yoff[3]);
         return sqrtf_fast(fmaf(dx, dx, dz * dz));
     }
-    __device__ static double ell_d(const double* x, const GameParams& g) {
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
         const double dx = x[0] - x[2], dz = x[1] - x[3];
         return sqrt(dx * dx + dz * dz) - g.radius_d;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
         const double dx = x[0] - x[2], dz = x[1] - x[3];
         const double rho = sqrt(dx * dx + dz * dz);
         const double a = rho > 0 ? dx / rho : 0.0, b = rho > 0 ? dz / rho : 0.0;
         gr[0] = a; gr[1] = b; gr[2] = -a; gr[3] = -b; gr[4] = 0.0; gr[5] = 0.0;
     }
-    __device__ static double ham_d(const double* x, const double* p, const GameParams& g) {
+    __device__ static double ham_d(const double* x, const double* p, const GameParams& g, const float* = nullptr) {
         double sA, cA, sB, cB;
         sincos(x[4], &sA, &cA);
         sincos(x[5], &sB, &cB);
@@ -98,7 +100,7 @@ struct Rockets6 {
              + fabs(p[4]) - fabs(p[5]);
     }
     static constexpr int kCache = 4;   // cos thA, sin thA, cos thB, sin thB
-    __device__ static double cache(const double* x, int j) {
+    __device__ static double cache(const double* x, int j, const float* = nullptr) {
         const double a = x[4 + (j >> 1)];
         return (j & 1) ? sin(a) : cos(a);
     }
@@ -115,7 +117,8 @@ struct Rockets6 {
 struct Rockets45 {
     static constexpr int kN = 45;
     static constexpr bool kRadius = true;
-    __device__ static double ell_d(const double* x, const GameParams& g) {
+    static constexpr int kAux = 0;
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
         double best = INFINITY;
         for (int i = 0; i < 14; ++i) {
             const double dx = x[3 * i] - x[42], dz = x[3 * i + 1] - x[43];
@@ -123,7 +126,7 @@ struct Rockets45 {
         }
         return best - g.radius_d;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
         int arg = -1;
         double best = INFINITY;
         for (int i = 0; i < 14; ++i) {
@@ -138,7 +141,7 @@ struct Rockets45 {
             gr[42] = -dx / best; gr[43] = -dz / best;
         }
     }
-    __device__ static double ham_d(const double* x, const double* p, const GameParams& g) {
+    __device__ static double ham_d(const double* x, const double* p, const GameParams& g, const float* = nullptr) {
         double h = 0.0;
         for (int i = 0; i < 15; ++i) {
             double s, c;
@@ -150,7 +153,7 @@ struct Rockets45 {
         return h;
     }
     static constexpr int kCache = 30;  // cos th_i, sin th_i for the 15 agents
-    __device__ static double cache(const double* x, int j) {
+    __device__ static double cache(const double* x, int j, const float* = nullptr) {
         const double a = x[3 * (j >> 1) + 2];
         return (j & 1) ? sin(a) : cos(a);
     }
@@ -162,14 +165,82 @@ struct Rockets45 {
     }
 };
 
+// ---------------------------------------------------------------- murmuration agent
+// One starling of the flock game (Appendix D.5, in the per-agent reading): state
+// (p_x, p_y, p_z, psi).  The agent flies at speed a in its heading, sets its climb rate
+// u_z (|u_z| <= 1, maximises), and its heading relaxes toward the circular mean heading
+// psibar of its 7 nearest neighbours under a bounded attack disturbance d (|d| <= 1,
+// minimises): p' = (a cos psi, a sin psi, u_z), psi' = wrap(psibar - psi) + d.  Target:
+// distance to the nearest of those (frozen) neighbours minus the radius (union of the
+// per-neighbour signed distances, Eq. sdf_union).  Per-state data aux = the 7 neighbour
+// positions (21 floats) followed by psibar.
+__device__ __forceinline__ double wrap_angle_d(double a) {
+    const double two_pi = 6.283185307179586476925286766559;
+    double r = fmod(a + 3.14159265358979323846, two_pi);
+    if (r <= 0.0) r += two_pi;
+    return r - 3.14159265358979323846;
+}
+
+struct Flock4 {
+    static constexpr int kN = 4;
+    static constexpr bool kRadius = true;
+    static constexpr int kAux = 22;
+    static constexpr int kNbr = 7;
+    __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
+                                                 const GameParams&, const float* aux) {
+        const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]), y2 = fmaf(sk, z[2], yoff[2]);
+        float best = INFINITY;
+#pragma unroll
+        for (int j = 0; j < kNbr; ++j) {
+            const float dx = y0 - aux[3 * j], dy = y1 - aux[3 * j + 1], dz = y2 - aux[3 * j + 2];
+            best = fminf(best, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+        return sqrtf_fast(best);
+    }
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* aux) {
+        double best = INFINITY;
+        for (int j = 0; j < kNbr; ++j) {
+            const double dx = x[0] - aux[3 * j], dy = x[1] - aux[3 * j + 1], dz = x[2] - aux[3 * j + 2];
+            best = fmin(best, sqrt(dx * dx + dy * dy + dz * dz));
+        }
+        return best - g.radius_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* aux) {
+        int arg = -1;
+        double best = INFINITY;
+        for (int j = 0; j < kNbr; ++j) {
+            const double dx = x[0] - aux[3 * j], dy = x[1] - aux[3 * j + 1], dz = x[2] - aux[3 * j + 2];
+            const double dd = sqrt(dx * dx + dy * dy + dz * dz);
+            if (dd < best) { best = dd; arg = j; }
+        }
+        for (int a = 0; a < 4; ++a) gr[a] = 0.0;
+        if (arg >= 0 && best > 0)
+            for (int a = 0; a < 3; ++a) gr[a] = (x[a] - aux[3 * arg + a]) / best;
+    }
+    __device__ static double ham_d(const double* x, const double* p, const GameParams& g, const float* aux) {
+        double s, c;
+        sincos(x[3], &s, &c);
+        return g.speed_d[0] * (p[0] * c + p[1] * s) + fabs(p[2]) + p[3] * wrap_angle_d((double)aux[21] - x[3])
+             - fabs(p[3]);
+    }
+    static constexpr int kCache = 3;   // cos psi, sin psi, wrap(psibar - psi)
+    __device__ static double cache(const double* x, int j, const float* aux) {
+        return j == 0 ? cos(x[3]) : (j == 1 ? sin(x[3]) : wrap_angle_d((double)aux[21] - x[3]));
+    }
+    __device__ static double ham_c(const double*, const double* hc, const double* p, const GameParams& g) {
+        return g.speed_d[0] * (p[0] * hc[0] + p[1] * hc[1]) + fabs(p[2]) + p[3] * hc[2] - fabs(p[3]);
+    }
+};
+
 // ---------------------------------------------------------------- quadratic tests
 // H = h_sign |p|^2 / 2 (ZERO_H: H = 0), l = (y - x0)^T A (y - x0) / 2 + d.  NDIM <= 8.
 template <int NDIM, bool kZeroH>
 struct Quadratic {
     static constexpr int kN = NDIM;
     static constexpr bool kRadius = false;
+    static constexpr int kAux = 0;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
-                                                 const GameParams& g) {
+                                                 const GameParams& g, const float* = nullptr) {
         float e[NDIM];
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) e[a] = fmaf(sk, z[a], yoff[a]) - g.x0[a];
@@ -183,28 +254,28 @@ struct Quadratic {
         }
         return fmaf(0.5f, r, g.d);
     }
-    __device__ static double ell_d(const double* x, const GameParams& g) {
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
         double r = 0.0;
         for (int a = 0; a < NDIM; ++a)
             for (int b = 0; b < NDIM; ++b)
                 r += (x[a] - g.x0_d[a]) * g.A_d[a * NDIM + b] * (x[b] - g.x0_d[b]);
         return 0.5 * r + g.d_d;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams& g) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams& g, const float* = nullptr) {
         for (int a = 0; a < NDIM; ++a) {
             double s = 0.0;
             for (int b = 0; b < NDIM; ++b) s += g.A_d[a * NDIM + b] * (x[b] - g.x0_d[b]);
             gr[a] = s;
         }
     }
-    __device__ static double ham_d(const double*, const double* p, const GameParams& g) {
+    __device__ static double ham_d(const double*, const double* p, const GameParams& g, const float* = nullptr) {
         if (kZeroH) return 0.0;
         double s = 0.0;
         for (int a = 0; a < NDIM; ++a) s += p[a] * p[a];
         return g.h_sign_d * 0.5 * s;
     }
     static constexpr int kCache = 0;
-    __device__ static double cache(const double*, int) { return 0.0; }
+    __device__ static double cache(const double*, int, const float* = nullptr) { return 0.0; }
     __device__ static double ham_c(const double* x, const double*, const double* p, const GameParams& g) {
         return ham_d(x, p, g);
     }

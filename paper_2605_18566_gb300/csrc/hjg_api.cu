@@ -33,6 +33,8 @@ struct hjg_ctx {
     float* d_p = nullptr;
     float* d_c = nullptr;
     float* d_ess = nullptr;
+    float* d_aux = nullptr;       // [M][22] flock: neighbour positions and their mean heading
+    int32_t* d_idx = nullptr;     // [M][7] flock: neighbour indices
     unsigned long long* d_counters = nullptr;
     double* d_vhist = nullptr;
     int64_t vhist_rows = 0;   // allocated rows
@@ -175,6 +177,10 @@ hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
     if ((st = grow(ctx, &ctx->d_p, (size_t)M * ctx->ldx))) return st;
     if ((st = grow(ctx, &ctx->d_c, (size_t)M))) return st;
     if ((st = grow(ctx, &ctx->d_ess, (size_t)M))) return st;
+    if (ctx->dyn.game == HJG_FLOCK4) {
+        if ((st = grow(ctx, &ctx->d_aux, (size_t)M * kFlockAux))) return st;
+        if ((st = grow(ctx, &ctx->d_idx, (size_t)M * 7))) return st;
+    }
     if (ctx->d_vhist) { cudaFree(ctx->d_vhist); ctx->d_vhist = nullptr; ctx->vhist_rows = 0; }
     ctx->cap = M;
     return HJG_OK;
@@ -235,6 +241,8 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
     A.c_min = ctx->c_min;
     A.c_max = ctx->c_max;
     A.g = ctx->gp;
+    A.aux = ctx->d_aux;
+    A.ldaux = kFlockAux;
     return A;
 }
 
@@ -311,7 +319,7 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
     case HJG_TEST_ZERO_H:
         if (!kernels_quadratic(dyn->n, dyn->game == HJG_TEST_ZERO_H, &ctx->kern)) st = HJG_EUNSUPPORTED;
         break;
-    case HJG_FLOCK4: st = HJG_EUNSUPPORTED; break;
+    case HJG_FLOCK4: ctx->kern = kernels_flock4(); break;
     default: st = HJG_EINVAL;
     }
     if (st == HJG_OK && ctx->kern.n != dyn->n) st = HJG_EINVAL;
@@ -338,6 +346,7 @@ void hjg_destroy(hjg_ctx* ctx) {
     if (!ctx) return;
     cudaFree(ctx->d_x); cudaFree(ctx->d_v); cudaFree(ctx->d_p); cudaFree(ctx->d_c);
     cudaFree(ctx->d_ess); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
+    cudaFree(ctx->d_aux); cudaFree(ctx->d_idx);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -352,6 +361,8 @@ hjg_status hjg_set_stream(hjg_ctx* ctx, void* stream) {
 hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld, int on_device,
                           void* stream) {
     if (!ctx) return HJG_EINVAL;
+    if (ctx->dyn.game == HJG_FLOCK4 && M > 0 && M < 8)
+        return fail(ctx, HJG_EINVAL, "a flock needs at least 8 agents (7 neighbours each)");
     if (M < 0 || M > 0xFFFFFFFFll || (M > 0 && !pts) || ld < ctx->n)
         return fail(ctx, HJG_EINVAL, "set_points: bad M=%lld or ld=%lld (n=%d)", (long long)M,
                     (long long)ld, ctx->n);
@@ -370,8 +381,11 @@ hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld,
         HJG_CUDA(ctx, cudaMemset2DAsync(ctx->d_p + ctx->n, ctx->ldx * sizeof(float), 0,
                                         (ctx->ldx - ctx->n) * sizeof(float), (size_t)M, st));
     }
+    if (ctx->dyn.game == HJG_FLOCK4)   // neighbours among the loaded agents, frozen for the solve
+        HJG_CUDA(ctx, flock_neighbours(ctx->d_x, ctx->ldx, M, ctx->d_idx, nullptr, ctx->d_aux, kFlockAux, st));
     HJG_CUDA(ctx, ctx->kern.init(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min,
-                                 ctx->c_max, ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, ctx->d_ess, st));
+                                 ctx->c_max, ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, ctx->d_ess, st,
+                                 ctx->d_aux, kFlockAux));
     return HJG_OK;
 }
 

@@ -169,7 +169,8 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     const GameParams g = game_params(dyn, target);
 
     if (cudaMemsetAsync(cnt, 0, 256, s) != cudaSuccess) return HJG_ECUDA;
-    if (kern.init(pts, ld, M, g, delta, eta, c_min, c_max, v_out, grad_out, ldg, c, ess, s) != cudaSuccess)
+    if (kern.init(pts, ld, M, g, delta, eta, c_min, c_max, v_out, grad_out, ldg, c, ess, s, nullptr, 0) !=
+        cudaSuccess)
         return HJG_ECUDA;
     SweepArgs A;
     memset(&A, 0, sizeof A);

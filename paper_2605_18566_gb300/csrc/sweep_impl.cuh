@@ -38,6 +38,8 @@ struct SweepArgs {
     float sigma;              // sqrt(delta t)
     float sk;                 // sigma * kBmScale: y = x + theta + sk * (raw normal)
     double sigma_d, sigma2_d, delta, eta, c_min, c_max;
+    const float* aux;         // [M][ldaux] per-state game data (flock neighbours), or null
+    int64_t ldaux;
     GameParams g;
 };
 
@@ -116,8 +118,9 @@ struct SweepShared {
 // Load state pt into shared memory (threads < NPAD) and its trigonometric cache.
 template <class G, int NPAD, int W, int NC>
 __device__ __forceinline__ void load_state(SweepShared<NPAD, W, NC>& sh, const SweepArgs& A,
-                                           int64_t pt, int tid) {
+                                           int64_t pt, int tid, float* s_aux) {
     constexpr int n = G::kN;
+    if (G::kAux > 0 && tid < G::kAux) s_aux[tid] = A.aux[pt * A.ldaux + tid];
     if (tid < NPAD) {
         const float xv = tid < n ? A.x[pt * A.ldx + tid] : 0.0f;
         sh.xf[tid] = xv;
@@ -131,7 +134,7 @@ __device__ __forceinline__ void load_state(SweepShared<NPAD, W, NC>& sh, const S
         sh.cr = G::kRadius ? -sh.cneg2 * A.g.radius : 0.0f;
     }
     __syncthreads();
-    if (NC > 0 && tid < NC) sh.hc[tid] = G::cache(sh.x, tid);
+    if (NC > 0 && tid < NC) sh.hc[tid] = G::cache(sh.x, tid, s_aux);
 }
 
 // theta = -sigma^2 c p (Eq. tilt_shift) for the coming sweep and the FP32 constants the
@@ -230,14 +233,16 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
     constexpr int W = THREADS / 32;
     constexpr int GS = group_samples(n);
     constexpr int GB = group_blocks(n);
+    constexpr int KA = G::kAux > 0 ? G::kAux : 1;
     __shared__ SweepShared<NPAD, W, G::kCache> sh;
+    __shared__ float s_aux[KA];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t N32 = (uint32_t)A.N;
     const uint32_t full = N32 / GS;            // groups whose GS samples all lie inside N
     const uint32_t groups = (N32 + GS - 1) / GS;
 
     for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
-        load_state<G, NPAD, W, G::kCache>(sh, A, pt, tid);
+        load_state<G, NPAD, W, G::kCache>(sh, A, pt, tid, s_aux);
         __syncthreads();
         prepare_sweep<NPAD, W, G::kCache, TILT>(sh, A, n, tid);
         __syncthreads();
@@ -248,12 +253,15 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
             float yoff[n], tq[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) { yoff[j] = sh.yoff[j]; tq[j] = sh.tq[j]; }
+            float auxr[KA];
+#pragma unroll
+            for (int j = 0; j < KA; ++j) auxr[j] = G::kAux > 0 ? s_aux[j] : 0.0f;
             float m = -INFINITY, s = 0.0f, q = 0.0f, S[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
 
             auto sample = [&](const float* zt) {
-                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g), cr);
+                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g, auxr), cr);
                 if (TILT) {
 #pragma unroll
                     for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
 template <class G, bool TILT>
 __device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k, float c, float m,
                                            float s, float q, const double* xd, float* p,
-                                           const float* S, double* pd) {
+                                           const float* S, double* pd, const float* aux) {
     constexpr int n = G::kN;
     const bool last = (k + 1 == A.K);
     const double cd = (double)c;
@@ -312,7 +320,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k
     const double v = -((double)m * kLn2 - th2 / (2.0 * A.sigma2_d) + log(sd / (double)A.N)) / cd;
     finite = finite && isfinite(v);
     int clipped = 0;
-    const float c_new = (float)coef_update(G::ham_d(xd, pd, A.g), pp, A.delta, A.eta, A.c_min,
+    const float c_new = (float)coef_update(G::ham_d(xd, pd, A.g, aux), pp, A.delta, A.eta, A.c_min,
                                            A.c_max, &clipped);
     for (int j = 0; j < n; ++j) p[j] = (float)pd[j];
     if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
@@ -344,6 +352,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
     __shared__ double s_xd[WPC][n];  // lane 0's FP64 work space for the recovery
     __shared__ double s_pd[WPC][n];
     __shared__ float s_S[WPC][n];
+    constexpr int KA = G::kAux > 0 ? G::kAux : 1;
+    __shared__ float s_aux[WPC][KA];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * WPC;
     const uint32_t N32 = (uint32_t)A.N;
@@ -357,6 +367,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
             s_xd[wl][lane] = (double)xv;
             s_p[wl][lane] = A.p[pt * A.ldp + lane];
         }
+        if (G::kAux > 0 && lane < G::kAux) s_aux[wl][lane] = A.aux[pt * A.ldaux + lane];
         if (lane == 0 && A.vhist) A.vhist[pt] = A.v[pt];
         float c = A.c[pt];
         __syncwarp();
@@ -372,11 +383,14 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 yoff[j] = s_x[wl][j] + th;
                 tq[j] = -th * kLog2e * kBmScale / A.sigma;
             }
+            float auxr[KA];
+#pragma unroll
+            for (int j = 0; j < KA; ++j) auxr[j] = G::kAux > 0 ? s_aux[wl][j] : 0.0f;
             float m = -INFINITY, s = 0.0f, q = 0.0f, S[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
             auto sample = [&](const float* zt) {
-                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g), cr);
+                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g, auxr), cr);
                 if (TILT) {
 #pragma unroll
                     for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
@@ -404,7 +418,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
             if (lane == 0) {
 #pragma unroll
                 for (int j = 0; j < n; ++j) s_S[wl][j] = S[j];
-                c_new = warp_recover<G, TILT>(A, pt, k, c, m, s, q, s_xd[wl], s_p[wl], s_S[wl], s_pd[wl]);
+                c_new = warp_recover<G, TILT>(A, pt, k, c, m, s, q, s_xd[wl], s_p[wl], s_S[wl], s_pd[wl],
+                                              s_aux[wl]);
             }
             c = __shfl_sync(0xffffffffu, c_new, 0);
             __syncwarp();
@@ -428,6 +443,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
     constexpr int W = THREADS / 32;
     constexpr int GROUPS = THREADS / 4;
     __shared__ SweepShared<NPAD, W, G::kCache> sh;
+    __shared__ float s_aux[1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q4 = lane & 3;
     const int grp = tid >> 2;
@@ -436,7 +452,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
     const uint32_t N32 = (uint32_t)A.N;
 
     for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
-        load_state<G, NPAD, W, G::kCache>(sh, A, pt, tid);
+        load_state<G, NPAD, W, G::kCache>(sh, A, pt, tid, s_aux);
         __syncthreads();
         prepare_sweep<NPAD, W, G::kCache, TILT>(sh, A, n, tid);
         __syncthreads();
@@ -502,18 +518,20 @@ template <class G>
 __global__ void init_kernel(const float* __restrict__ x, int64_t ldx, int64_t M, GameParams g,
                             double delta, double eta, double c_min, double c_max,
                             double* __restrict__ v, float* __restrict__ p, int64_t ldp,
-                            float* __restrict__ c, float* __restrict__ ess) {
+                            float* __restrict__ c, float* __restrict__ ess,
+                            const float* __restrict__ aux, int64_t ldaux) {
     constexpr int n = G::kN;
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     double xd[n], gr[n];
     for (int j = 0; j < n; ++j) xd[j] = (double)x[m * ldx + j];
-    v[m] = G::ell_d(xd, g);
-    G::grad_ell_d(xd, gr, g);
+    const float* am = G::kAux > 0 ? aux + m * ldaux : nullptr;
+    v[m] = G::ell_d(xd, g, am);
+    G::grad_ell_d(xd, gr, g, am);
     double pp = 0.0;
     for (int j = 0; j < n; ++j) { p[m * ldp + j] = (float)gr[j]; pp += gr[j] * gr[j]; }
     int clipped;
-    c[m] = (float)coef_update(G::ham_d(xd, gr, g), pp, delta, eta, c_min, c_max, &clipped);
+    c[m] = (float)coef_update(G::ham_d(xd, gr, g, am), pp, delta, eta, c_min, c_max, &clipped);
     ess[m] = 0.0f;
 }
 
@@ -555,11 +573,11 @@ int occupancy_generic(bool tilt) {
 template <class G>
 cudaError_t launch_init(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta,
                         double eta, double c_min, double c_max, double* v, float* p, int64_t ldp,
-                        float* c, float* ess, cudaStream_t st) {
+                        float* c, float* ess, cudaStream_t st, const float* aux, int64_t ldaux) {
     const int T = 128;
     const int64_t blocks = (M + T - 1) / T;
     init_kernel<G><<<(unsigned)blocks, T, 0, st>>>(x, ldx, M, g, delta, eta, c_min, c_max, v, p,
-                                                  ldp, c, ess);
+                                                  ldp, c, ess, aux, ldaux);
     return cudaGetLastError();
 }
 

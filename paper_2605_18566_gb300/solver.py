@@ -215,6 +215,20 @@ class Batch:
             pass
 
 
+def flock_neighbours(states: torch.Tensor, k: int = 7):
+    """7 nearest neighbours of each agent and their circular mean heading (device)."""
+    lib = _lib.load()
+    M = states.shape[0]
+    idx = torch.empty(M, k, dtype=torch.int32, device=states.device)
+    psibar = torch.empty(M, dtype=torch.float32, device=states.device)
+    st = lib.hjg_flock_neighbours(C.c_void_p(states.data_ptr()), M, states.stride(0), k,
+                                  C.c_void_p(idx.data_ptr()), C.c_void_p(psibar.data_ptr()),
+                                  _stream_handle(None))
+    if st:
+        raise HJGError(st, "hjg_flock_neighbours")
+    return idx, psibar
+
+
 def philox_blocks(ctr: torch.Tensor, key: torch.Tensor) -> torch.Tensor:
     """Device Philox4x32-10: ctr int32/uint32 [K,4], key [K,2] (CUDA tensors)."""
     lib = _lib.load()

@@ -69,12 +69,17 @@ def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97):
     largest local coefficient error at that state (three random perturbations).  At least
     ``min_pass`` of the states must pass P2 outright."""
     states, resid, one, r_all = gpu_trajectory(w, x, N, K, tilt=tilt)
+    nb_all = pb_all = None
+    if w.game == "flock4":   # neighbours among all loaded agents, as the GPU found them
+        _, nb_all, pb_all = oracle.flock_neighbours(x)
     # one K-sweep launch == K one-sweep launches
     for key in ("v", "p", "c"):
         np.testing.assert_array_equal(one[key], states[-1][key])
     np.testing.assert_array_equal(r_all, resid)
     sel = np.arange(len(x)) if idx is None else np.asarray(idx)
     xs = x[sel].astype(np.float64)
+    nb = nb_all[sel] if nb_all is not None else None
+    pb = pb_all[sel] if pb_all is not None else None
     P = problem_for(w, tilt=tilt)
     P1 = problem_for(w)
     local_c = np.zeros(len(sel))
@@ -83,12 +88,12 @@ def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97):
         theta = None
         if tilt:
             theta = -w.sigma2 * c_k[:, None] * states[k]["p"][sel].astype(np.float64)
-        v, p, _ = oracle.sweep(P1, xs, c_k, N, k, theta=theta, idx=sel)
+        v, p, _ = oracle.sweep(P1, xs, c_k, N, k, theta=theta, nbr=nb, idx=sel)
         g_v, g_p = states[k + 1]["v"][sel], states[k + 1]["p"][sel]
         assert_parity(g_v, g_p, v, p, what="P1 %s sweep %d" % (w.game, k))
         g_c = states[k + 1]["c"][sel].astype(np.float64)
         gp64 = g_p.astype(np.float64)
-        c_ref = oracle.coef_batch(P, xs, gp64)
+        c_ref = oracle.coef_batch(P, xs, gp64, pb)
         # the GPU applied Gamma to its FP64 Dv, which the stored FP32 Dv rounds by half an
         # ulp: bound the effect with one-sided difference quotients of the oracle's Gamma
         slack = 1e-6 * np.abs(c_ref)
@@ -96,25 +101,26 @@ def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97):
             h = np.maximum(np.abs(gp64[:, j]), 1e-30) * 2.0**-24
             up = gp64.copy(); up[:, j] += h
             dn = gp64.copy(); dn[:, j] -= h
-            slack += 2.0 * np.maximum(np.abs(oracle.coef_batch(P, xs, up) - c_ref),
-                                      np.abs(oracle.coef_batch(P, xs, dn) - c_ref))
+            slack += 2.0 * np.maximum(np.abs(oracle.coef_batch(P, xs, up, pb) - c_ref),
+                                      np.abs(oracle.coef_batch(P, xs, dn, pb) - c_ref))
         err = np.abs(g_c - c_ref)
         assert np.all(err <= slack + 2.0**-23 * np.abs(c_ref)), ("Gamma", k, (err - slack).max())
-        c_from_p1 = oracle.coef_batch(P, xs, p)
+        c_from_p1 = oracle.coef_batch(P, xs, p, pb)
         local_c = np.maximum(local_c, np.abs(g_c - c_from_p1) / np.abs(c_from_p1))
-    ref = oracle.picard(P, xs, N, K, idx=sel)
+    ref = oracle.picard(P, xs, N, K, idx=sel, nbr=nb, psibar=pb)
     dv, dp = rel_errors(states[-1]["v"][sel], states[-1]["p"][sel], ref["v"], ref["p"])
     fail = (dv > TOL_V) | (dp > TOL_P)
     ill = np.zeros(len(sel), bool)
     if fail.any():
         amp = np.maximum(2.0 * local_c, 3e-6)
-        v0, p0, c0 = oracle.init(P, xs)
+        v0, p0, c0 = oracle.init(P, xs, nb, pb)
         for rep in range(3):
             rng = np.random.default_rng(100 + rep)
             st = (v0, p0, c0)
             for k in range(K):
                 c_pert = st[2] * (1.0 + amp * rng.standard_normal(len(xs)))
-                out = oracle.picard(P, xs, N, 1, k0=k, state=(st[0], st[1], c_pert), idx=sel)
+                out = oracle.picard(P, xs, N, 1, k0=k, state=(st[0], st[1], c_pert), idx=sel,
+                                    nbr=nb, psibar=pb)
                 st = (out["v"], out["p"], out["c"])
             sv, sp = rel_errors(st[0], st[1], ref["v"], ref["p"])
             ill |= (sv > 0.1 * TOL_V) | (sp > 0.1 * TOL_P)

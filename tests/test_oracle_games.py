@@ -190,3 +190,33 @@ def test_picard_resume_is_bit_exact_and_residual_settles():
     # the residual of the first sweep (leaving the target data) dominates later ones
     assert full["resid"][0] > full["resid"][-1]
     assert np.all(np.isfinite(full["v"])) and np.all(full["ess"] >= 1.0)
+
+
+def test_flock_neighbours_brute_force_and_target():
+    """k-d-tree neighbours equal a brute-force search; the flock target is the distance to
+    the nearest neighbour minus the radius; psibar is the circular mean."""
+    x = hjg_inputs.flock_states(600, seed=2).astype(np.float64)
+    idx, nbr, psibar = oracle.flock_neighbours(x)
+    pos = x[:, :3]
+    d2 = ((pos[:, None, :] - pos[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    brute = np.argsort(d2, axis=1, kind="stable")[:, :7]
+    np.testing.assert_array_equal(np.sort(idx, 1), np.sort(brute, 1))
+    P = oracle.make_problem("flock4", 4, 0.04, 1.0, radius=0.2)
+    for i in (0, 17, 333):
+        expect = np.sqrt(d2[i][brute[i]].min()) - 0.2
+        assert abs(oracle.ell(P, x[i], nbr[i]) - expect) < 1e-12
+        ang = x[idx[i], 3]
+        assert abs(np.angle(np.exp(1j * (psibar[i] - np.angle(np.exp(1j * ang).sum()))))) < 1e-12
+    # identical headings average to themselves; opposite pairs around a direction to it
+    y = x[:40].copy(); y[:, 3] = 0.7
+    _, _, pb = oracle.flock_neighbours(y)
+    np.testing.assert_allclose(pb, 0.7, atol=1e-12)
+
+
+def test_flock_workload_shape():
+    x = hjg_inputs.flock_states(20000, seed=0)
+    idx, nbr, _ = oracle.flock_neighbours(x[:, :4])
+    dnn = np.linalg.norm(x[:, :3] - x[idx[:, 0], :3], axis=1)
+    assert 0.1 < np.median(dnn) < 0.6        # 20k of the 100k birds: sparser than full size
+    assert np.all(np.abs(x[:, 3]) <= np.pi)
