@@ -296,6 +296,53 @@ def ncu_case(w, variant):
     s.close()
 
 
+def run_mixed(args):
+    """The mixed batch plus the 100,000-agent flock, all at nu = 0.02, T = 1, N = 16,384,
+    K = 15 (the instances of hjg_inputs.MIXED and the flock), advanced by one CUDA-graph
+    launch per step; value = total point-samples of all instances / device time."""
+    import torch
+    from paper_2605_18566_gb300 import Batch, Solver
+    N, K, nu, T = 16384, 15, 0.02, 1.0
+    inst = list(hjg_inputs.MIXED) + [(hjg_inputs.FLOCK, hjg_inputs.FLOCK.M)]
+    solvers, xs = [], []
+    for i, (w, M) in enumerate(inst):
+        x = hjg_inputs.points(w, M=M) if w.game != "dubins3" else \
+            np.tile(hjg_inputs.points(w), (max(1, M // 4096), 1))[:M]
+        xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        s = Solver(w.game, nu, T, N, K, radius=w.radius, instance=i)
+        s.set_points(xt)
+        s.autotune(max_states=4 * SMS * 6)
+        solvers.append(s); xs.append(xt)
+    b = Batch(solvers)
+    samples = sum(M for _, M in inst) * N * K
+    for _ in range(args.warmup):
+        for s, x in zip(solvers, xs):
+            s.set_points(x)
+        b.run(K)
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            for s, x in zip(solvers, xs):
+                s.set_points(x)
+            _, t = b.run(K)
+            ms.append(t)
+    out = {"metric": METRIC, "value": samples / (sum(ms) / len(ms) / 1e3), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sum(ms) / len(ms), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (FP64 combine/log/residual)",
+           "data": "synthetic (seeded states; flock of 6 Gaussian clusters on a ring)",
+           "config": {"workload": "mixed batch (Dubins 1,024 + 65,536; rockets6 4,096 + "
+                                  "131,072; rockets45 16,384 + 262,144 states) + 100,000-agent "
+                                  "flock, nu=0.02, T=1, N=16384, K=15, one CUDA-graph launch",
+                      "instances": len(inst), "states": sum(M for _, M in inst),
+                      "launch": "graph of per-instance sweep + residual kernels (batch)"},
+           "clocks": clk.summary()}
+    b.close()
+    for s in solvers:
+        s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +350,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rockets6", choices=["rockets6", "mixed"],
+                    help="rockets6 (default, the benchmark line) or the mixed batch + flock")
     ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS),
                     help="run one small launch of the named workload's sweep (profiling)")
     ap.add_argument("--variant", type=int, default=2, help="sweep launch variant for --ncu-case")
@@ -335,6 +384,10 @@ def main():
         print(json.dumps(out))
         return
 
+    if args.workload == "mixed":
+        if rank == 0:
+            print(json.dumps(run_mixed(args)))
+        return
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:

@@ -148,6 +148,13 @@ hjg_status hjg_get_state(hjg_ctx *ctx, double *v, float *p, int64_t ldp, float *
 hjg_status hjg_set_state(hjg_ctx *ctx, const double *v, const float *p, int64_t ldp,
                          const float *c, uint32_t next_sweep, int on_device);
 
+/* Warm start (a surrogate's prediction in place of Algorithm 1's initial iterate): set
+ * p^(0) = p0 [M][ldp] FP32 and, if v0 is not NULL, v^(0) = v0 [M] FP64, then recompute the
+ * frozen coefficient c^(0) = Gamma(p0) (Eq. coeff_frozen with Lemma 2.7 and Remark 2.8) on
+ * the device.  With opt.tilt the first sweep is then drawn from the tilted proposal around
+ * theta = -delta t c^(0) p0 (Eq. tilt_shift).  Synchronises the context's stream. */
+hjg_status hjg_warm_start(hjg_ctx *ctx, const double *v0, const float *p0, int64_t ldp, int on_device);
+
 /* v^(k) history of the last hjg_picard_sweep call: rows 0..n_sweeps, row 0 = the
  * incoming v.  out is [(n_sweeps+1)][M] FP64. */
 hjg_status hjg_get_history(hjg_ctx *ctx, double *out, int on_device);
@@ -215,6 +222,38 @@ hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t 
  * k must be 7; device pointers; asynchronous on stream. */
 hjg_status hjg_flock_neighbours(const float *states, int64_t M, int64_t ld, int k, int32_t *idx_out,
                                 float *psibar_out, void *stream);
+
+/* ---- surrogate network (BF16 tensor cores, trained on the sweep's own tuples) ---- */
+
+/* An MLP n_in -> width -> width -> width -> n_out with SiLU activations (the surrogate of
+ * the learned warm start; the paper has no counterpart): BF16 weights and activations,
+ * FP32 accumulation on the tensor cores, FP32 master weights, Adam.  For the value
+ * surrogate n_out = n + 1: output 0 predicts v, outputs 1..n predict Dv.  Training loss:
+ * (o_0 - v)^2 + mean_j (o_j - Dv_j)^2, averaged over the batch.  Weights start uniform in
+ * +-sqrt(6/(fan_in + fan_out)) from a hash of `seed`, biases at zero.  width must be a
+ * multiple of 16 and at least n_in and n_out rounded up to 16.  Device pointers
+ * throughout; the context's stream (hjg_mlp_set_stream) orders every call. */
+typedef struct hjg_mlp hjg_mlp;
+
+hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp **out);
+void hjg_mlp_destroy(hjg_mlp *m);
+hjg_status hjg_mlp_set_stream(hjg_mlp *m, void *stream);
+/* Number of FP32 parameters: [W1 b1 W2 b2 W3 b3 W4 b4], W_l [out_pad][in_pad] row-major
+ * (inputs and outputs padded to multiples of 16 with zero weights). */
+int64_t hjg_mlp_num_params(const hjg_mlp *m);
+hjg_status hjg_mlp_get_params(hjg_mlp *m, float *out, int on_device);
+/* Load parameters (resets Adam's moments and step count). */
+hjg_status hjg_mlp_set_params(hjg_mlp *m, const float *in, int on_device);
+/* out [B][ldout] (n_out used) = MLP(x [B][ldx] (n_in used)). */
+hjg_status hjg_mlp_forward(hjg_mlp *m, const float *x, int64_t ldx, int64_t B, float *out, int64_t ldout);
+/* Loss (host, FP64, may be NULL) and gradients w.r.t. all parameters (host grad_out of
+ * hjg_mlp_num_params floats, may be NULL) on one batch; parameters unchanged. */
+hjg_status hjg_mlp_gradients(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,
+                             int64_t B, double *loss_out, float *grad_out);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on one batch;
+ * loss_out (host) may be NULL (then the call does not synchronise). */
+hjg_status hjg_mlp_train_step(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,
+                              int64_t B, float lr, double *loss_out);
 
 /* ---- batches: many instances, one CUDA-graph launch ------------------------------- */
 

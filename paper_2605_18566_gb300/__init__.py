@@ -4,8 +4,8 @@ The compute path is libhjg.so (hand-written CUDA, C ABI in include/hjg.h); this 
 is its Python binding.  Import fails loudly if the library has not been built.
 """
 from ._lib import HJGError, load, symbols  # noqa: F401
-from .solver import (Batch, Solver, flock_neighbours, microbench, philox_blocks,  # noqa: F401
-                     sample_normals)
+from .solver import (Batch, Solver, Surrogate, flock_neighbours, microbench,  # noqa: F401
+                     philox_blocks, sample_normals)
 
-__all__ = ["Batch", "Solver", "HJGError", "microbench", "philox_blocks", "sample_normals", "load",
+__all__ = ["Batch", "Solver", "Surrogate", "HJGError", "microbench", "philox_blocks", "sample_normals", "load",
            "symbols"]

@@ -64,6 +64,18 @@ _SIGS = {
                                          C.c_double, C.POINTER(Options), _vp, C.c_int64,
                                          C.c_int64, _vp, _vp, C.c_int64, _vp, _vp]),
     "hjg_flock_neighbours": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int, _vp, _vp, _vp]),
+    "hjg_warm_start": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int]),
+    "hjg_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_vp)]),
+    "hjg_mlp_destroy": (None, [_vp]),
+    "hjg_mlp_set_stream": (C.c_int, [_vp, _vp]),
+    "hjg_mlp_num_params": (C.c_int64, [_vp]),
+    "hjg_mlp_get_params": (C.c_int, [_vp, _vp, C.c_int]),
+    "hjg_mlp_set_params": (C.c_int, [_vp, _vp, C.c_int]),
+    "hjg_mlp_forward": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, _vp, C.c_int64]),
+    "hjg_mlp_gradients": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64,
+                                    C.POINTER(C.c_double), _vp]),
+    "hjg_mlp_train_step": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_float,
+                                     C.POINTER(C.c_double)]),
     "hjg_batch_create": (C.c_int, [C.POINTER(_vp)]),
     "hjg_batch_add": (C.c_int, [_vp, _vp]),
     "hjg_batch_run": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),

@@ -20,6 +20,9 @@ struct GameKernels {
     cudaError_t (*init)(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta,
                         double eta, double c_min, double c_max, double* v, float* p, int64_t ldp,
                         float* c, float* ess, cudaStream_t st, const float* aux, int64_t ldaux);
+    cudaError_t (*coef)(const float* x, int64_t ldx, int64_t M, const float* p, int64_t ldp,
+                        const GameParams& g, double delta, double eta, double c_min, double c_max, float* c,
+                        const float* aux, int64_t ldaux, cudaStream_t st);
 };
 
 GameKernels kernels_dubins3();
@@ -61,6 +64,7 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
         k.sweep = sweep;                                                                   \
         k.occupancy = occ;                                                                 \
         k.init = launch_init<GAME>;                                                        \
+        k.coef = launch_coef<GAME>;                                                        \
         return k;                                                                          \
     }                                                                                      \
     }

@@ -464,6 +464,22 @@ hjg_status hjg_set_state(hjg_ctx* ctx, const double* v, const float* p, int64_t 
     return HJG_OK;
 }
 
+hjg_status hjg_warm_start(hjg_ctx* ctx, const double* v0, const float* p0, int64_t ldp, int on_device) {
+    if (!ctx || !p0) return HJG_EINVAL;
+    if (ldp < ctx->n) return fail(ctx, HJG_EINVAL, "ldp < n");
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    cudaStream_t st = ctx->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (v0) HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_v, v0, M * sizeof(double), kind, st));
+    HJG_CUDA(ctx, cudaMemcpy2DAsync(ctx->d_p, ctx->ldx * sizeof(float), p0, ldp * sizeof(float),
+                                    ctx->n * sizeof(float), (size_t)M, kind, st));
+    HJG_CUDA(ctx, ctx->kern.coef(ctx->d_x, ctx->ldx, M, ctx->d_p, ctx->ldx, ctx->gp, ctx->delta, ctx->eta,
+                                 ctx->c_min, ctx->c_max, ctx->d_c, ctx->d_aux, kFlockAux, st));
+    HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
 hjg_status hjg_get_history(hjg_ctx* ctx, double* out, int on_device) {
     if (!ctx || !out) return HJG_EINVAL;
     if (ctx->last_sweeps == 0 || ctx->M == 0) return HJG_OK;

@@ -26,6 +26,7 @@ GameKernels make() {
     k.sweep = sweep<G>;
     k.occupancy = occ<G>;
     k.init = launch_init<G>;
+    k.coef = launch_coef<G>;
     return k;
 }
 }  // namespace

@@ -36,6 +36,7 @@ GameKernels kernels_rockets45() {
     k.sweep = sweep;
     k.occupancy = occ;
     k.init = launch_init<Rockets45>;
+    k.coef = launch_coef<Rockets45>;
     return k;
 }
 }  // namespace hjg

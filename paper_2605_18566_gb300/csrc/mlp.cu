@@ -1,0 +1,516 @@
+// mlp.cu -- the surrogate network: an MLP n_in -> W -> W -> W -> n_out with SiLU
+// activations, BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
+// master weights and Adam.  It is trained on the (x, v, Dv) tuples the Picard sweeps
+// produce (loss: mean squared error of v plus the mean squared error of Dv averaged over
+// its n components) and supplies a warm start (v, Dv, hence c = Gamma(Dv) and the tilt
+// theta = -sigma^2 c Dv) for the sweep, which stays the judge of its accuracy.
+//
+// Layout: parameters are one FP32 array [W1 | b1 | W2 | b2 | W3 | b3 | W4 | b4] with each
+// W_l stored [out][in] row-major; a BF16 copy of the W_l feeds the tensor cores.  Inputs
+// and outputs are padded to multiples of 16 (45 -> 48, 46 -> 48).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hjg.h"
+
+namespace {
+
+constexpr int kLayers = 4;
+
+__host__ __device__ inline int pad16(int n) { return (n + 15) / 16 * 16; }
+
+// ------------------------------------------------------------------------------------
+// Strided BF16 GEMM on the tensor cores: C(m, n) = sum_k A(m, k) B(k, n), with
+// A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn] (BF16), FP32 accumulation, and
+// an epilogue.  CTA tile 64 x 64, four warps of 32 x 32, K step 32, mma.sync m16n8k16.
+// gridDim.z splits K (each split writes its own partial for a later reduction).
+enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    const __nv_bfloat16* B;
+    int64_t sam, sak, sbk, sbn;
+    int M, N, K;
+    float* C;          // FP32 output (z or partial), [M][ldc] (+ split * M * ldc)
+    int64_t ldc;
+    __nv_bfloat16* H;  // BF16 activation output (kEpiBiasSilu), [M][ldh]
+    int64_t ldh;
+    const float* bias; // [N]
+};
+
+__device__ __forceinline__ void mma_bf16_16x8x16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+
+template <int EPI>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
+    constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];   // As[m][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];   // Bs[n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int kper = (g.K + gridDim.z - 1) / gridDim.z;
+    const int kbeg = blockIdx.z * kper, kend = min(g.K, kbeg + kper);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 128) {
+            const int mm = e / BK, kk = e % BK;
+            const int m = m0 + mm, k = k0 + kk;
+            As[mm][kk] = (m < g.M && k < kend) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
+        }
+        for (int e = tid; e < BN * BK; e += 128) {
+            const int nn = e / BK, kk = e % BK;
+            const int n = n0 + nn, k = k0 + kk;
+            Bs[nn][kk] = (n < g.N && k < kend) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            const int gid = lane >> 2, tig = lane & 3;
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + gid;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + gid;
+                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16x8x16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue: acc[i][j] = rows (wm + 16i + gid, +8), cols (wn + 8j + 2 tig, +1)
+    const int gid = lane >> 2, tig = lane & 3;
+    float* C = g.C ? g.C + (int64_t)blockIdx.z * g.M * g.ldc : nullptr;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
+                if (m >= g.M || n >= g.N) continue;
+                float v = acc[i][j][r];
+                if (EPI != kEpiStore) v += g.bias[n];
+                if (C) C[(int64_t)m * g.ldc + n] = v;
+                if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + n] = __float2bfloat16(silu(v));
+            }
+}
+
+cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st) {
+    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, splits);
+    switch (epi) {
+    case kEpiStore: gemm_bf16_kernel<kEpiStore><<<grid, 128, 0, st>>>(g); break;
+    case kEpiBiasSilu: gemm_bf16_kernel<kEpiBiasSilu><<<grid, 128, 0, st>>>(g); break;
+    case kEpiBias: gemm_bf16_kernel<kEpiBias><<<grid, 128, 0, st>>>(g); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Element-wise kernels.
+
+// x [B][ldx] FP32 (n_in used) -> X [B][in_pad] BF16 (zero padding).
+__global__ void pack_input_kernel(const float* __restrict__ x, int64_t ldx, int64_t B, int n_in,
+                                  int in_pad, __nv_bfloat16* __restrict__ X) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * in_pad) return;
+    const int64_t b = e / in_pad;
+    const int j = (int)(e % in_pad);
+    X[e] = __float2bfloat16(j < n_in ? x[b * ldx + j] : 0.0f);
+}
+
+// Loss and its gradient w.r.t. the outputs: L = mean_b[(o_0 - y_0)^2 + mean_j (o_j - y_j)^2]
+// over j = 1..n_out-1.  dO (BF16) is written for the backward GEMMs; the per-block partial
+// sums of L go to partial[blockIdx.x] (reduced in a fixed order on the host side).
+__global__ void loss_grad_kernel(const float* __restrict__ out, int64_t ldo, const float* __restrict__ y,
+                                 int64_t ldy, int64_t B, int n_out, int out_pad,
+                                 __nv_bfloat16* __restrict__ dO, float* __restrict__ dOf,
+                                 double* __restrict__ partial) {
+    __shared__ double red[256];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (e < B * out_pad) {
+        const int64_t b = e / out_pad;
+        const int j = (int)(e % out_pad);
+        float g = 0.0f;
+        if (j < n_out) {
+            const float d = out[b * ldo + j] - y[b * ldy + j];
+            const float w = j == 0 ? 1.0f : 1.0f / (float)(n_out - 1);
+            l = (double)w * (double)d * (double)d / (double)B;
+            g = 2.0f * w * d / (float)B;
+        }
+        dO[e] = __float2bfloat16(g);
+        if (dOf) dOf[e] = g;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// dZ = dH * SiLU'(Z), SiLU'(z) = s (1 + z (1 - s)), s = sigmoid(z); BF16 out.
+__global__ void silu_backward_kernel(const float* __restrict__ dH, const float* __restrict__ Z, int64_t n,
+                                     __nv_bfloat16* __restrict__ dZ) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float z = Z[e];
+    const float s = 1.0f / (1.0f + __expf(-z));
+    dZ[e] = __float2bfloat16(dH[e] * s * (1.0f + z * (1.0f - s)));
+}
+
+// Sum of `splits` partial weight gradients [splits][rows][cols] into grad (FP32), and the
+// bias gradient (column sums of dZ over the batch) for this layer.
+__global__ void reduce_wgrad_kernel(const float* __restrict__ part, int splits, int64_t n,
+                                    float* __restrict__ grad) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k) s += part[(int64_t)k * n + e];
+    grad[e] = s;
+}
+
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dZ, int64_t B, int cols,
+                                 float* __restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int64_t b = 0; b < B; ++b) s += __bfloat162float(dZ[b * cols + c]);
+    db[c] = s;
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters; refresh the BF16 weight copy.
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
+                            float* __restrict__ m2, __nv_bfloat16* __restrict__ wb, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float gg = g[e];
+    const float a = b1 * m1[e] + (1.0f - b1) * gg;
+    const float b = b2 * m2[e] + (1.0f - b2) * gg * gg;
+    m1[e] = a;
+    m2[e] = b;
+    const float upd = lr * (a / c1) / (sqrtf(b / c2) + eps);
+    const float nw = w[e] - upd;
+    w[e] = nw;
+    wb[e] = __float2bfloat16(nw);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) wb[e] = __float2bfloat16(w[e]);
+}
+
+// Deterministic initialisation: W_l uniform in +-sqrt(6 / (fan_in + fan_out)) (rows beyond
+// n_out and columns beyond n_in zero), biases zero; uniforms from a 64-bit mix of
+// (seed, index).
+__device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)((z >> 40) * (1.0 / 16777216.0)) * 2.0f - 1.0f;
+}
+
+__global__ void init_weight_kernel(float* __restrict__ W, int rows, int cols, int rows_used,
+                                   int cols_used, float scale, uint64_t seed) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * cols) return;
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    W[e] = (r < rows_used && c < cols_used) ? scale * hash_uniform(seed, (uint64_t)e) : 0.0f;
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+struct hjg_mlp {
+    int n_in, n_out, width, in_pad, out_pad;
+    int rows[kLayers], cols[kLayers];     // W_l is [rows][cols] = [out_pad_l][in_pad_l]
+    int64_t w_off[kLayers], b_off[kLayers], n_params;
+    float* p = nullptr;                   // FP32 master parameters
+    float* g = nullptr;                   // gradients
+    float* m1 = nullptr;                  // Adam moments
+    float* m2 = nullptr;
+    __nv_bfloat16* pb = nullptr;          // BF16 copy (weights used by the GEMMs)
+    int64_t cap = 0;                      // batch capacity of the work buffers
+    __nv_bfloat16* X = nullptr;           // [cap][in_pad]
+    float* Z[kLayers] = {};               // pre-activations [cap][width] (layer 4: outputs)
+    __nv_bfloat16* H[kLayers] = {};       // activations [cap][width] BF16
+    __nv_bfloat16* dZ = nullptr;          // [cap][width] BF16
+    float* dH = nullptr;                  // [cap][width] FP32
+    float* wpart = nullptr;               // split-K partial weight gradients
+    double* lpart = nullptr;              // loss partial sums
+    int64_t lpart_cap = 0;
+    int64_t step = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+constexpr int kSplits = 16;
+
+hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
+    if (B <= m->cap) return HJG_OK;
+    auto fre = [](void* p) { if (p) cudaFree(p); };
+    fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart);
+    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); m->Z[l] = nullptr; m->H[l] = nullptr; }
+    const int W = m->width;
+    bool ok = cudaMalloc(&m->X, (size_t)B * m->in_pad * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&m->dZ, (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&m->dH, (size_t)B * W * sizeof(float)) == cudaSuccess;
+    for (int l = 0; l < kLayers && ok; ++l) {
+        ok = cudaMalloc(&m->Z[l], (size_t)B * W * sizeof(float)) == cudaSuccess &&
+             cudaMalloc(&m->H[l], (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess;
+    }
+    m->lpart_cap = (B * m->out_pad + 255) / 256;
+    ok = ok && cudaMalloc(&m->lpart, (size_t)m->lpart_cap * sizeof(double)) == cudaSuccess;
+    if (!ok) { m->cap = 0; m->err = "MLP work buffers: out of memory"; return HJG_ENOMEM; }
+    m->cap = B;
+    return HJG_OK;
+}
+
+// Forward pass on X (already packed); outputs FP32 in Z[3] [B][out_pad].
+cudaError_t mlp_forward(hjg_mlp* m, int64_t B) {
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        GemmArgs g{};
+        const __nv_bfloat16* in = l == 0 ? m->X : m->H[l - 1];
+        const int in_ld = l == 0 ? m->in_pad : m->width;
+        g.A = in; g.sam = in_ld; g.sak = 1;
+        g.B = m->pb + m->w_off[l]; g.sbk = 1; g.sbn = m->cols[l];
+        g.M = (int)B; g.N = m->rows[l]; g.K = m->cols[l];
+        g.C = m->Z[l]; g.ldc = m->rows[l];
+        g.bias = m->p + m->b_off[l];
+        if (l + 1 < kLayers) {
+            g.H = m->H[l]; g.ldh = m->rows[l];
+            e = gemm(g, kEpiBiasSilu, 1, m->stream);
+        } else {
+            e = gemm(g, kEpiBias, 1, m->stream);
+        }
+    }
+    return e;
+}
+
+// Backward pass from dO (BF16 in m->dZ, [B][out_pad]); gradients into m->g.
+cudaError_t mlp_backward(hjg_mlp* m, int64_t B) {
+    cudaError_t e = cudaSuccess;
+    for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int rows = m->rows[l], cols = m->cols[l];
+        // dW_l = dZ_l^T . H_{l-1}  ([rows][cols], reduction over the batch, split-K)
+        GemmArgs gw{};
+        gw.A = m->dZ; gw.sam = 1; gw.sak = rows;
+        const __nv_bfloat16* hin = l == 0 ? m->X : m->H[l - 1];
+        gw.B = hin; gw.sbk = cols; gw.sbn = 1;
+        gw.M = rows; gw.N = cols; gw.K = (int)B;
+        gw.C = m->wpart; gw.ldc = cols;
+        e = gemm(gw, kEpiStore, kSplits, m->stream);
+        if (e != cudaSuccess) break;
+        const int64_t nw = (int64_t)rows * cols;
+        reduce_wgrad_kernel<<<nblk(nw), 256, 0, m->stream>>>(m->wpart, kSplits, nw, m->g + m->w_off[l]);
+        bias_grad_kernel<<<nblk(rows, 128), 128, 0, m->stream>>>(m->dZ, B, rows, m->g + m->b_off[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess || l == 0) break;
+        // dH_{l-1} = dZ_l . W_l  ([B][cols])
+        GemmArgs gd{};
+        gd.A = m->dZ; gd.sam = rows; gd.sak = 1;
+        gd.B = m->pb + m->w_off[l]; gd.sbk = cols; gd.sbn = 1;
+        gd.M = (int)B; gd.N = cols; gd.K = rows;
+        gd.C = m->dH; gd.ldc = cols;
+        e = gemm(gd, kEpiStore, 1, m->stream);
+        if (e != cudaSuccess) break;
+        const int64_t nh = B * (int64_t)cols;
+        silu_backward_kernel<<<nblk(nh), 256, 0, m->stream>>>(m->dH, m->Z[l - 1], nh, m->dZ);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
+                              int64_t B, double* loss_out) {
+    hjg_status s = mlp_ensure(m, B);
+    if (s) return s;
+    cudaStream_t st = m->stream;
+    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
+    if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B) != cudaSuccess) return HJG_ECUDA;
+    const int64_t nb = (B * m->out_pad + 255) / 256;
+    loss_grad_kernel<<<(unsigned)nb, 256, 0, st>>>(m->Z[kLayers - 1], m->out_pad, y, ldy, B, m->n_out,
+                                                   m->out_pad, m->dZ, nullptr, m->lpart);
+    if (cudaGetLastError() != cudaSuccess || mlp_backward(m, B) != cudaSuccess) return HJG_ECUDA;
+    if (loss_out) {
+        std::vector<double> part((size_t)nb);
+        if (cudaMemcpyAsync(part.data(), m->lpart, nb * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return HJG_ECUDA;
+        double l = 0.0;
+        for (double v : part) l += v;
+        *loss_out = l;
+    }
+    return HJG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp** out) {
+    if (!out || n_in < 1 || n_in > 256 || n_out < 1 || n_out > 256 || width < 16 || width > 1024 ||
+        width % 16 || pad16(n_out) > width || pad16(n_in) > width)
+        return HJG_EINVAL;
+    hjg_mlp* m = new (std::nothrow) hjg_mlp();
+    if (!m) return HJG_ENOMEM;
+    m->n_in = n_in; m->n_out = n_out; m->width = width;
+    m->in_pad = pad16(n_in); m->out_pad = pad16(n_out);
+    const int ins[kLayers] = {m->in_pad, width, width, width};
+    const int outs[kLayers] = {width, width, width, m->out_pad};
+    int64_t off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        m->rows[l] = outs[l]; m->cols[l] = ins[l];
+        m->w_off[l] = off; off += (int64_t)outs[l] * ins[l];
+        m->b_off[l] = off; off += outs[l];
+    }
+    m->n_params = off;
+    const size_t nb = (size_t)off * sizeof(float);
+    int64_t wpart = 0;
+    for (int l = 0; l < kLayers; ++l) wpart = std::max<int64_t>(wpart, (int64_t)m->rows[l] * m->cols[l]);
+    if (cudaMalloc(&m->p, nb) != cudaSuccess || cudaMalloc(&m->g, nb) != cudaSuccess ||
+        cudaMalloc(&m->m1, nb) != cudaSuccess || cudaMalloc(&m->m2, nb) != cudaSuccess ||
+        cudaMalloc(&m->pb, (size_t)off * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc(&m->wpart, (size_t)kSplits * wpart * sizeof(float)) != cudaSuccess) {
+        hjg_mlp_destroy(m);
+        return HJG_ENOMEM;
+    }
+    cudaMemset(m->p, 0, nb);
+    cudaMemset(m->m1, 0, nb);
+    cudaMemset(m->m2, 0, nb);
+    cudaMemset(m->g, 0, nb);
+    const int used_in[kLayers] = {n_in, width, width, width};
+    const int used_out[kLayers] = {width, width, width, n_out};
+    for (int l = 0; l < kLayers; ++l) {
+        const float scale = sqrtf(6.0f / (float)(used_in[l] + used_out[l]));
+        const int64_t n = (int64_t)m->rows[l] * m->cols[l];
+        init_weight_kernel<<<nblk(n), 256>>>(m->p + m->w_off[l], m->rows[l], m->cols[l], used_out[l],
+                                             used_in[l], scale, seed * 31 + l);
+    }
+    to_bf16_kernel<<<nblk(off), 256>>>(m->p, m->pb, off);
+    if (cudaDeviceSynchronize() != cudaSuccess) { hjg_mlp_destroy(m); return HJG_ECUDA; }
+    *out = m;
+    return HJG_OK;
+}
+
+void hjg_mlp_destroy(hjg_mlp* m) {
+    if (!m) return;
+    auto fre = [](void* p) { if (p) cudaFree(p); };
+    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->wpart);
+    fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart);
+    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); }
+    delete m;
+}
+
+hjg_status hjg_mlp_set_stream(hjg_mlp* m, void* stream) {
+    if (!m) return HJG_EINVAL;
+    m->stream = (cudaStream_t)stream;
+    return HJG_OK;
+}
+
+int64_t hjg_mlp_num_params(const hjg_mlp* m) { return m ? m->n_params : -1; }
+
+hjg_status hjg_mlp_get_params(hjg_mlp* m, float* out, int on_device) {
+    if (!m || !out) return HJG_EINVAL;
+    if (cudaMemcpyAsync(out, m->p, m->n_params * sizeof(float),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_set_params(hjg_mlp* m, const float* in, int on_device) {
+    if (!m || !in) return HJG_EINVAL;
+    if (cudaMemcpyAsync(m->p, in, m->n_params * sizeof(float),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
+        return HJG_ECUDA;
+    to_bf16_kernel<<<nblk(m->n_params), 256, 0, m->stream>>>(m->p, m->pb, m->n_params);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess) return HJG_ECUDA;
+    m->step = 0;
+    cudaMemsetAsync(m->m1, 0, m->n_params * sizeof(float), m->stream);
+    cudaMemsetAsync(m->m2, 0, m->n_params * sizeof(float), m->stream);
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_forward(hjg_mlp* m, const float* x, int64_t ldx, int64_t B, float* out, int64_t ldout) {
+    if (!m || B < 0 || ldx < m->n_in || ldout < m->n_out || (B > 0 && (!x || !out))) return HJG_EINVAL;
+    if (B == 0) return HJG_OK;
+    hjg_status s = mlp_ensure(m, B);
+    if (s) return s;
+    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, m->stream>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
+    if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B) != cudaSuccess) return HJG_ECUDA;
+    if (cudaMemcpy2DAsync(out, ldout * sizeof(float), m->Z[kLayers - 1], m->out_pad * sizeof(float),
+                          m->n_out * sizeof(float), (size_t)B, cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess)
+        return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_gradients(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
+                             int64_t B, double* loss_out, float* grad_out) {
+    if (!m || B < 1 || !x || !y || ldx < m->n_in || ldy < m->n_out) return HJG_EINVAL;
+    hjg_status s = mlp_loss_and_grads(m, x, ldx, y, ldy, B, loss_out);
+    if (s) return s;
+    if (grad_out &&
+        (cudaMemcpyAsync(grad_out, m->g, m->n_params * sizeof(float), cudaMemcpyDeviceToHost, m->stream) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(m->stream) != cudaSuccess))
+        return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_train_step(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
+                              int64_t B, float lr, double* loss_out) {
+    if (!m || B < 1 || !x || !y || ldx < m->n_in || ldy < m->n_out || !(lr > 0)) return HJG_EINVAL;
+    hjg_status s = mlp_loss_and_grads(m, x, ldx, y, ldy, B, loss_out);
+    if (s) return s;
+    m->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
+    adam_kernel<<<nblk(m->n_params), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb, m->n_params, lr,
+                                                           b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
+}
+
+}  // extern "C"

@@ -535,6 +535,37 @@ __global__ void init_kernel(const float* __restrict__ x, int64_t ldx, int64_t M,
     ess[m] = 0.0f;
 }
 
+// Coefficient map Gamma at given (x, p) per state (FP64): used for warm starts, where Dv
+// comes from outside the sweep (a surrogate) rather than from a sweep.
+template <class G>
+__global__ void coef_kernel(const float* __restrict__ x, int64_t ldx, int64_t M, const float* __restrict__ p,
+                            int64_t ldp, GameParams g, double delta, double eta, double c_min, double c_max,
+                            float* __restrict__ c, const float* __restrict__ aux, int64_t ldaux) {
+    constexpr int n = G::kN;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double xd[n], pd[n];
+    double pp = 0.0;
+    for (int j = 0; j < n; ++j) {
+        xd[j] = (double)x[m * ldx + j];
+        pd[j] = (double)p[m * ldp + j];
+        pp += pd[j] * pd[j];
+    }
+    int clipped;
+    c[m] = (float)coef_update(G::ham_d(xd, pd, g, G::kAux > 0 ? aux + m * ldaux : nullptr), pp, delta, eta,
+                              c_min, c_max, &clipped);
+}
+
+template <class G>
+cudaError_t launch_coef(const float* x, int64_t ldx, int64_t M, const float* p, int64_t ldp,
+                        const GameParams& g, double delta, double eta, double c_min, double c_max, float* c,
+                        const float* aux, int64_t ldaux, cudaStream_t st) {
+    const int T = 128;
+    coef_kernel<G><<<(unsigned)((M + T - 1) / T), T, 0, st>>>(x, ldx, M, p, ldp, g, delta, eta, c_min, c_max,
+                                                              c, aux, ldaux);
+    return cudaGetLastError();
+}
+
 // Launch variants the autotuner chooses among: kind 0 = one CTA per state, kind 1 = one
 // warp per state; CTA size; minimum resident CTAs per SM (the register budget).  Every
 // game's translation unit instantiates all of them.

@@ -164,6 +164,14 @@ class Solver:
         self.last_status = st
         return v_out, grad_out, r[:K]
 
+    def warm_start(self, p0: torch.Tensor, v0: Optional[torch.Tensor] = None):
+        """Replace the initial iterate by (v0, p0) and set c = Gamma(p0) (hjg_warm_start)."""
+        assert p0.dtype == torch.float32 and p0.stride(1) == 1 and p0.is_cuda
+        if v0 is not None:
+            assert v0.dtype == torch.float64 and v0.is_cuda
+        _check(self.lib, self.ctx, self.lib.hjg_warm_start(
+            self.ctx, self._ptr(v0), self._ptr(p0), p0.stride(0), 1))
+
     def autotune(self, max_states: int = 0) -> dict:
         """Pick the fastest sweep launch variant on the loaded states (see hjg_autotune)."""
         v = C.c_int32(); t = C.c_int32(); ms = C.c_double()
@@ -175,6 +183,97 @@ class Solver:
         d = _lib.Diag()
         _check(self.lib, self.ctx, self.lib.hjg_get_diagnostics(self.ctx, C.byref(d)))
         return {f: getattr(d, f) for f, _ in _lib.Diag._fields_}
+
+
+class Surrogate:
+    """The BF16 tensor-core MLP of hjg_mlp_*: n_in -> width x3 -> n_out, SiLU."""
+
+    def __init__(self, n_in: int, n_out: int, width: int = 256, seed: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _lib.load()
+        self.n_in, self.n_out, self.width = n_in, n_out, width
+        m = C.c_void_p()
+        torch.cuda.init()
+        st = self.lib.hjg_mlp_create(n_in, n_out, width, seed, C.byref(m))
+        if st:
+            raise HJGError(st, "hjg_mlp_create")
+        self.m = m
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.lib.hjg_mlp_set_stream(self.m, _stream_handle(self.stream))
+        self.n_params = int(self.lib.hjg_mlp_num_params(self.m))
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.lib.hjg_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        st = self.lib.hjg_mlp_get_params(self.m, out.ctypes.data_as(C.c_void_p), 0)
+        if st:
+            raise HJGError(st, "hjg_mlp_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        st = self.lib.hjg_mlp_set_params(self.m, p.ctypes.data_as(C.c_void_p), 0)
+        if st:
+            raise HJGError(st, "hjg_mlp_set_params")
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        assert x.is_cuda and x.dtype == torch.float32 and x.stride(1) == 1
+        out = torch.empty(x.shape[0], self.n_out, dtype=torch.float32, device=x.device)
+        st = self.lib.hjg_mlp_forward(self.m, C.c_void_p(x.data_ptr()), x.stride(0), x.shape[0],
+                                      C.c_void_p(out.data_ptr()), self.n_out)
+        if st:
+            raise HJGError(st, "hjg_mlp_forward")
+        return out
+
+    def gradients(self, x: torch.Tensor, y: torch.Tensor):
+        loss = C.c_double()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        st = self.lib.hjg_mlp_gradients(self.m, C.c_void_p(x.data_ptr()), x.stride(0),
+                                        C.c_void_p(y.data_ptr()), y.stride(0), x.shape[0],
+                                        C.byref(loss), g.ctypes.data_as(C.c_void_p))
+        if st:
+            raise HJGError(st, "hjg_mlp_gradients")
+        return loss.value, g
+
+    def train_step(self, x: torch.Tensor, y: torch.Tensor, lr: float, want_loss: bool = True):
+        loss = C.c_double()
+        st = self.lib.hjg_mlp_train_step(self.m, C.c_void_p(x.data_ptr()), x.stride(0),
+                                         C.c_void_p(y.data_ptr()), y.stride(0), x.shape[0],
+                                         lr, C.byref(loss) if want_loss else None)
+        if st:
+            raise HJGError(st, "hjg_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def fit(self, x: torch.Tensor, y: torch.Tensor, epochs: int, batch: int = 4096,
+            lr: float = 1e-3, lr_final: float = 1e-5):
+        """Adam over contiguous minibatches of (x, y) (shuffle the rows beforehand), with
+        the learning rate decayed geometrically from lr to lr_final; returns the mean loss
+        of each epoch."""
+        n = x.shape[0]
+        steps = epochs * max(1, n // batch)
+        hist, t = [], 0
+        for ep in range(epochs):
+            tot, cnt = 0.0, 0
+            for b0 in range(0, n - batch + 1 if n >= batch else 1, batch):
+                b1 = min(n, b0 + batch)
+                rate = lr * (lr_final / lr) ** (t / max(1, steps - 1))
+                last = b0 + batch > n - batch
+                l = self.train_step(x[b0:b1], y[b0:b1], rate, want_loss=last)
+                t += 1
+                if last:
+                    tot += l; cnt += 1
+            hist.append(tot / max(cnt, 1))
+        return hist
 
 
 class Batch:

@@ -1,0 +1,83 @@
+"""The surrogate network's tensor-core kernels against the FP64 reference (oracle/mlp.py):
+forward outputs and every parameter gradient, at a ragged batch size; training lowers the
+loss; the warm start sets c = Gamma(Dv) like the oracle's coefficient map."""
+import numpy as np
+import pytest
+
+import hjg_inputs
+import oracle
+from oracle import mlp as omlp
+from helpers import problem_for, solver_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N_IN, N_OUT, WIDTH = 45, 46, 256
+
+
+def _sur(seed=1):
+    from paper_2605_18566_gb300 import Surrogate
+    return Surrogate(N_IN, N_OUT, WIDTH, seed=seed)
+
+
+def test_forward_matches_reference():
+    s = _sur()
+    x = hjg_inputs.random_states(300, N_IN, 1.5, seed=3)
+    out = s.forward(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    p = s.params()
+    ref_bf, _ = omlp.forward(p, x.astype(np.float64), N_IN, N_OUT, WIDTH, bf16=True)
+    ref64, _ = omlp.forward(p, x.astype(np.float64), N_IN, N_OUT, WIDTH, bf16=False)
+    scale = np.abs(ref64).max()
+    assert np.abs(out - ref_bf).max() <= 1e-2 * scale
+    assert np.median(np.abs(out - ref_bf)) <= 1e-3 * scale
+    assert np.abs(out - ref64).max() <= 5e-2 * scale
+    s.close()
+
+
+def test_gradients_match_reference():
+    s = _sur(seed=2)
+    rng = np.random.default_rng(4)
+    x = hjg_inputs.random_states(300, N_IN, 1.5, seed=5)
+    y = rng.normal(size=(300, N_OUT)).astype(np.float32)
+    loss, g = s.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    p = s.params()
+    rloss, rg = omlp.loss_and_grads(p, x.astype(np.float64), y.astype(np.float64), N_IN, N_OUT,
+                                    WIDTH, bf16=True)
+    assert abs(loss - rloss) <= 1e-3 * rloss
+    lay, _ = omlp.layout(N_IN, N_OUT, WIDTH)
+    for (w, o, i, b) in lay:
+        for a, z in ((w, w + o * i), (b, b + o)):
+            gg, rr = g[a:z].astype(np.float64), rg[a:z]
+            assert np.linalg.norm(gg - rr) <= 2e-2 * np.linalg.norm(rr) + 1e-12, (a, z)
+    # padded outputs/inputs receive no gradient
+    w4, o4, i4, b4 = lay[3]
+    assert np.all(g[w4:w4 + o4 * i4].reshape(o4, i4)[N_OUT:] == 0)
+    s.close()
+
+
+def test_training_lowers_loss():
+    s = _sur(seed=3)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-2, 2, size=(16384, N_IN)).astype(np.float32)
+    y = np.concatenate([np.sin(x).sum(1, keepdims=True) / 10, np.cos(x) / 10], 1).astype(np.float32)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    hist = s.fit(xt, yt, epochs=40, batch=2048, lr=2e-3, lr_final=1e-4)
+    assert hist[-1] < 0.05 * hist[0], hist
+    s.close()
+
+
+def test_warm_start_sets_gamma():
+    w = hjg_inputs.ROCKETS45
+    x = hjg_inputs.points(w, M=200)
+    rng = np.random.default_rng(6)
+    p0 = (0.3 * rng.normal(size=(200, 45))).astype(np.float32)
+    v0 = rng.normal(size=200)
+    s = solver_for(w, N=1024, K=1)
+    s.set_points(torch.from_numpy(x).cuda())
+    s.warm_start(torch.from_numpy(p0).cuda(), torch.from_numpy(v0).cuda())
+    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    s.close()
+    np.testing.assert_array_equal(st["p"], p0)
+    np.testing.assert_array_equal(st["v"], v0)
+    c_ref = oracle.coef_batch(problem_for(w), x.astype(np.float64), p0.astype(np.float64))
+    np.testing.assert_allclose(st["c"], c_ref, rtol=1e-6)
