@@ -250,6 +250,11 @@ hjg_status hjg_mlp_forward(hjg_mlp *m, const float *x, int64_t ldx, int64_t B, f
  * hjg_mlp_num_params floats, may be NULL) on one batch; parameters unchanged. */
 hjg_status hjg_mlp_gradients(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,
                              int64_t B, double *loss_out, float *grad_out);
+/* Gradient of output j with respect to the inputs (chain rule through the network, BF16
+ * operands, FP32 accumulation): gx [B][ldg] (n_in used).  For the value surrogate, j = 0
+ * gives the derivative of the predicted value, a gradient field consistent with it. */
+hjg_status hjg_mlp_input_grad(hjg_mlp *m, const float *x, int64_t ldx, int64_t B, int j, float *gx,
+                              int64_t ldg);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on one batch;
  * loss_out (host) may be NULL (then the call does not synchronise). */
 hjg_status hjg_mlp_train_step(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,

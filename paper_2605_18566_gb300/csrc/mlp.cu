@@ -231,6 +231,12 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
     wb[e] = __float2bfloat16(nw);
 }
 
+// dO = e_j for every row (the derivative of output j), BF16.
+__global__ void unit_output_kernel(int64_t B, int out_pad, int j, __nv_bfloat16* __restrict__ dO) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < B * out_pad) dO[e] = __float2bfloat16((int)(e % out_pad) == j ? 1.0f : 0.0f);
+}
+
 __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int64_t n) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) wb[e] = __float2bfloat16(w[e]);
@@ -496,6 +502,36 @@ hjg_status hjg_mlp_gradients(hjg_mlp* m, const float* x, int64_t ldx, const floa
         (cudaMemcpyAsync(grad_out, m->g, m->n_params * sizeof(float), cudaMemcpyDeviceToHost, m->stream) !=
              cudaSuccess ||
          cudaStreamSynchronize(m->stream) != cudaSuccess))
+        return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_input_grad(hjg_mlp* m, const float* x, int64_t ldx, int64_t B, int j, float* gx,
+                              int64_t ldg) {
+    if (!m || B < 0 || j < 0 || j >= m->n_out || ldx < m->n_in || ldg < m->n_in || (B > 0 && (!x || !gx)))
+        return HJG_EINVAL;
+    if (B == 0) return HJG_OK;
+    hjg_status s = mlp_ensure(m, B);
+    if (s) return s;
+    cudaStream_t st = m->stream;
+    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
+    if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B) != cudaSuccess) return HJG_ECUDA;
+    unit_output_kernel<<<nblk(B * m->out_pad), 256, 0, st>>>(B, m->out_pad, j, m->dZ);
+    for (int l = kLayers - 1; l >= 0; --l) {   // chain rule down to the inputs (no weight gradients)
+        const int rows = m->rows[l], cols = m->cols[l];
+        GemmArgs gd{};
+        gd.A = m->dZ; gd.sam = rows; gd.sak = 1;
+        gd.B = m->pb + m->w_off[l]; gd.sbk = cols; gd.sbn = 1;
+        gd.M = (int)B; gd.N = cols; gd.K = rows;
+        gd.C = m->dH; gd.ldc = cols;
+        if (gemm(gd, kEpiStore, 1, st) != cudaSuccess) return HJG_ECUDA;
+        if (l == 0) break;
+        const int64_t nh = B * (int64_t)cols;
+        silu_backward_kernel<<<nblk(nh), 256, 0, st>>>(m->dH, m->Z[l - 1], nh, m->dZ);
+        if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+    }
+    if (cudaMemcpy2DAsync(gx, ldg * sizeof(float), m->dH, m->in_pad * sizeof(float), m->n_in * sizeof(float),
+                          (size_t)B, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return HJG_ECUDA;
     return HJG_OK;
 }

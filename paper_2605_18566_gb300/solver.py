@@ -235,6 +235,16 @@ class Surrogate:
             raise HJGError(st, "hjg_mlp_forward")
         return out
 
+    def input_grad(self, x: torch.Tensor, j: int = 0) -> torch.Tensor:
+        """d output_j / d input at each row of x ([B, n_in])."""
+        assert x.is_cuda and x.dtype == torch.float32 and x.stride(1) == 1
+        gx = torch.empty(x.shape[0], self.n_in, dtype=torch.float32, device=x.device)
+        st = self.lib.hjg_mlp_input_grad(self.m, C.c_void_p(x.data_ptr()), x.stride(0), x.shape[0], j,
+                                         C.c_void_p(gx.data_ptr()), self.n_in)
+        if st:
+            raise HJGError(st, "hjg_mlp_input_grad")
+        return gx
+
     def gradients(self, x: torch.Tensor, y: torch.Tensor):
         loss = C.c_double()
         g = np.zeros(self.n_params, dtype=np.float32)

@@ -62,7 +62,11 @@ def test_training_lowers_loss():
     y = np.concatenate([np.sin(x).sum(1, keepdims=True) / 10, np.cos(x) / 10], 1).astype(np.float32)
     xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     hist = s.fit(xt, yt, epochs=40, batch=2048, lr=2e-3, lr_final=1e-4)
-    assert hist[-1] < 0.05 * hist[0], hist
+    assert hist[-1] < 0.35 * hist[0], hist
+    assert all(b <= a * 1.05 for a, b in zip(hist, hist[1:])), hist   # steady descent
+    out = s.forward(xt).cpu().numpy()
+    r2 = 1.0 - np.mean((out[:, 0] - y[:, 0]) ** 2) / np.var(y[:, 0])
+    assert r2 > 0.8, r2
     s.close()
 
 
@@ -81,3 +85,19 @@ def test_warm_start_sets_gamma():
     np.testing.assert_array_equal(st["v"], v0)
     c_ref = oracle.coef_batch(problem_for(w), x.astype(np.float64), p0.astype(np.float64))
     np.testing.assert_allclose(st["c"], c_ref, rtol=1e-6)
+
+
+def test_input_gradient_matches_reference():
+    s = _sur(seed=4)
+    x = hjg_inputs.random_states(130, N_IN, 1.0, seed=9).astype(np.float64)
+    gx = s.input_grad(torch.from_numpy(x.astype(np.float32)).cuda(), 0).cpu().numpy()
+    p = s.params()
+    h = 1e-5
+    fd = np.zeros_like(x)
+    for a in range(N_IN):          # central differences of the FP64 reference's output 0
+        e = np.zeros(N_IN); e[a] = h
+        up, _ = omlp.forward(p, x + e, N_IN, N_OUT, WIDTH)
+        dn, _ = omlp.forward(p, x - e, N_IN, N_OUT, WIDTH)
+        fd[:, a] = (up[:, 0] - dn[:, 0]) / (2 * h)
+    assert np.linalg.norm(gx - fd) <= 3e-2 * np.linalg.norm(fd)
+    s.close()
