@@ -260,6 +260,14 @@ hjg_status hjg_mlp_input_grad(hjg_mlp *m, const float *x, int64_t ldx, int64_t B
 hjg_status hjg_mlp_train_step(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,
                               int64_t B, float lr, double *loss_out);
 
+/* The surrogate's GEMM on its own (the tensor-core kernel behind hjg_mlp_*):
+ * C(m, n) = sum_k A(m, k) B(k, n) with A(m, k) = A[m*sam + k*sak] and B(k, n) =
+ * B[k*sbk + n*sbn] in BF16, C [M][ldc] FP32, device pointers.  timed_out (host, may be
+ * NULL) receives 1 if a bounded wait of the kernel gave up (then ETIMEOUT); passing it
+ * synchronises the stream. */
+hjg_status hjg_gemm_bf16(const void *A, int64_t sam, int64_t sak, const void *B, int64_t sbk, int64_t sbn,
+                         int M, int N, int K, float *C, int64_t ldc, int *timed_out, void *stream);
+
 /* ---- batches: many instances, one CUDA-graph launch ------------------------------- */
 
 /* A batch advances several instances (contexts, possibly of different games, dimensions

@@ -74,6 +74,8 @@ _SIGS = {
     "hjg_mlp_forward": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, _vp, C.c_int64]),
     "hjg_mlp_gradients": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64,
                                     C.POINTER(C.c_double), _vp]),
+    "hjg_gemm_bf16": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_int,
+                                C.c_int, C.c_int, _vp, C.c_int64, C.POINTER(C.c_int), _vp]),
     "hjg_mlp_input_grad": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, C.c_int, _vp, C.c_int64]),
     "hjg_mlp_train_step": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_float,
                                      C.POINTER(C.c_double)]),

@@ -27,10 +27,10 @@ constexpr int kLayers = 4;
 __host__ __device__ inline int pad16(int n) { return (n + 15) / 16 * 16; }
 
 // ------------------------------------------------------------------------------------
-// Strided BF16 GEMM on the tensor cores: C(m, n) = sum_k A(m, k) B(k, n), with
-// A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn] (BF16), FP32 accumulation, and
-// an epilogue.  CTA tile 64 x 64, four warps of 32 x 32, K step 32, mma.sync m16n8k16.
-// gridDim.z splits K (each split writes its own partial for a later reduction).
+// Strided BF16 GEMM: C(m, n) = sum_k A(m, k) B(k, n), with A(m, k) = A[m*sam + k*sak],
+// B(k, n) = B[k*sbk + n*sbn] (BF16), FP32 accumulation, and an epilogue (bias, SiLU,
+// BF16 activation copy).  gridDim.z splits K (each split writes its own partial for a
+// later reduction).
 enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2 };
 
 struct GemmArgs {
@@ -45,99 +45,178 @@ struct GemmArgs {
     const float* bias; // [N]
 };
 
-__device__ __forceinline__ void mma_bf16_16x8x16(float* d, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 
-template <int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
-    constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];   // As[m][k]
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];   // Bs[n][k]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int kper = (g.K + gridDim.z - 1) / gridDim.z;
-    const int kbeg = blockIdx.z * kper, kend = min(g.K, kbeg + kper);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += 128) {
-            const int mm = e / BK, kk = e % BK;
-            const int m = m0 + mm, k = k0 + kk;
-            As[mm][kk] = (m < g.M && k < kend) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
-        }
-        for (int e = tid; e < BN * BK; e += 128) {
-            const int nn = e / BK, kk = e % BK;
-            const int n = n0 + nn, k = k0 + kk;
-            Bs[nn][kk] = (n < g.N && k < kend) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            const int gid = lane >> 2, tig = lane & 3;
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gid;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8 + gid;
-                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2 + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16_16x8x16(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
-    }
-    // epilogue: acc[i][j] = rows (wm + 16i + gid, +8), cols (wn + 8j + 2 tig, +1)
-    const int gid = lane >> 2, tig = lane & 3;
-    float* C = g.C ? g.C + (int64_t)blockIdx.z * g.M * g.ldc : nullptr;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[i][j][r];
-                if (EPI != kEpiStore) v += g.bias[n];
-                if (C) C[(int64_t)m * g.ldc + n] = v;
-                if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + n] = __float2bfloat16(silu(v));
-            }
+// ------------------------------------------------------------------------------------
+// The GEMM runs on the 5th-generation tensor cores (tcgen05, sm_100 family):
+// a CTA of 4 warps owns a 128 x 128 tile of C, accumulated in tensor memory (TMEM, 128
+// lanes x 128 FP32 columns).  Per K chunk of 64 the operands are staged by all threads into
+// shared memory in the canonical K-major no-swizzle layout (8-row x 16-byte core matrices,
+// 128 B apart along K, 256 B apart along rows), made visible to the tensor core's async
+// proxy, and thread 0 issues four tcgen05.mma (M = 128, N = 128, K = 16) and commits them to
+// an mbarrier; every wait on that barrier is bounded and records a time-out in *err.
+// The epilogue reads TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31 = rows).
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st) {
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, splits);
+// Shared-memory matrix descriptor: start address, leading (K-direction) and stride
+// (row-direction) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) of a [R][64] operand chunk in the canonical layout.
+__device__ __forceinline__ uint32_t canon_off(int r, int k, int R) {
+    return (uint32_t)((k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err) {
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+        if (done) return true;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err) {
+    __shared__ __align__(1024) uint8_t sA[kTcM * kTcK * 2];
+    __shared__ __align__(1024) uint8_t sB[kTcN * kTcK * 2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
+    const int kper = (g.K + gridDim.z - 1) / gridDim.z;
+    const int kbeg = blockIdx.z * kper, kend = min(g.K, kbeg + kper);
+    const uint32_t bar = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(kTcN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = umma_idesc_bf16(kTcM, kTcN);
+    uint32_t phase = 0;
+    bool ok = true;
+    int nchunk = 0;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int k0 = kbeg; k0 < kend && ok; k0 += kTcK, ++nchunk) {
+        for (int e = tid; e < kTcM * kTcK; e += 128) {
+            const int r = e / kTcK, k = e % kTcK;
+            const int m = m0 + r, kk = k0 + k;
+            const __nv_bfloat16 a = (m < g.M && kk < kend) ? g.A[(int64_t)m * g.sam + (int64_t)kk * g.sak] : zero;
+            *reinterpret_cast<__nv_bfloat16*>(sA + canon_off(r, k, kTcM)) = a;
+        }
+        for (int e = tid; e < kTcN * kTcK; e += 128) {
+            const int r = e / kTcK, k = e % kTcK;
+            const int n = n0 + r, kk = k0 + k;
+            const __nv_bfloat16 b = (n < g.N && kk < kend) ? g.B[(int64_t)kk * g.sbk + (int64_t)n * g.sbn] : zero;
+            *reinterpret_cast<__nv_bfloat16*>(sB + canon_off(r, k, kTcN)) = b;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 16; ++ks) {
+                const uint64_t da = umma_desc(smem_u32(sA) + ks * (kTcM * 32), 128, 256);
+                const uint64_t db = umma_desc(smem_u32(sB) + ks * (kTcN * 32), 128, 256);
+                const uint32_t acc = (nchunk > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                    :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar) : "memory");
+        }
+        ok = mbar_wait(bar, phase, err);   // operands may be overwritten only after the MMAs read them
+        phase ^= 1;
+        ok = __syncthreads_and(ok) != 0;   // one verdict for the whole CTA (.sync.aligned epilogue)
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // epilogue: row r = 32 warp + lane, 8 columns per tcgen05.ld
+    const int r = warp * 32 + lane;
+    const int m = m0 + r;
+    float* C = g.C ? g.C + (int64_t)blockIdx.z * g.M * g.ldc : nullptr;
+    if (ok && nchunk > 0) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTcN; c0 += 8) {
+            uint32_t v[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < g.M) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= g.N) continue;
+                    float x = __uint_as_float(v[j]);
+                    if (EPI != kEpiStore) x += g.bias[n];
+                    if (C) C[(int64_t)m * g.ldc + n] = x;
+                    if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + n] = __float2bfloat16(silu(x));
+                }
+            }
+        }
+    } else if (m < g.M && C) {   // empty K range (or a timed-out wait): C = 0 (+ bias)
+        for (int n = n0; n < min(g.N, n0 + kTcN); ++n) {
+            const float x = (EPI != kEpiStore) ? g.bias[n] : 0.0f;
+            C[(int64_t)m * g.ldc + n] = x;
+            if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + n] = __float2bfloat16(silu(x));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN));
+}
+
+int* g_tc_err = nullptr;   // device word set by a timed-out barrier wait
+
+cudaError_t gemm_tc(const GemmArgs& g, int epi, int splits, cudaStream_t st) {
+    if (!g_tc_err) {
+        if (cudaMalloc(&g_tc_err, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
+        cudaMemset(g_tc_err, 0, sizeof(int));
+    }
+    dim3 grid((g.N + kTcN - 1) / kTcN, (g.M + kTcM - 1) / kTcM, splits);
     switch (epi) {
-    case kEpiStore: gemm_bf16_kernel<kEpiStore><<<grid, 128, 0, st>>>(g); break;
-    case kEpiBiasSilu: gemm_bf16_kernel<kEpiBiasSilu><<<grid, 128, 0, st>>>(g); break;
-    case kEpiBias: gemm_bf16_kernel<kEpiBias><<<grid, 128, 0, st>>>(g); break;
+    case kEpiStore: gemm_tc_kernel<kEpiStore><<<grid, 128, 0, st>>>(g, g_tc_err); break;
+    case kEpiBiasSilu: gemm_tc_kernel<kEpiBiasSilu><<<grid, 128, 0, st>>>(g, g_tc_err); break;
+    case kEpiBias: gemm_tc_kernel<kEpiBias><<<grid, 128, 0, st>>>(g, g_tc_err); break;
     }
     return cudaGetLastError();
 }
+
+cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st) { return gemm_tc(g, epi, splits, st); }
 
 // ------------------------------------------------------------------------------------
 // Element-wise kernels.
@@ -533,6 +612,28 @@ hjg_status hjg_mlp_input_grad(hjg_mlp* m, const float* x, int64_t ldx, int64_t B
     if (cudaMemcpy2DAsync(gx, ldg * sizeof(float), m->dH, m->in_pad * sizeof(float), m->n_in * sizeof(float),
                           (size_t)B, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_gemm_bf16(const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbk, int64_t sbn,
+                         int M, int N, int K, float* C, int64_t ldc, int* timed_out, void* stream) {
+    if (M < 0 || N < 0 || K < 0 || (M > 0 && N > 0 && (!C || (K > 0 && (!A || !B)))) || ldc < N)
+        return HJG_EINVAL;
+    if (M == 0 || N == 0) return HJG_OK;
+    GemmArgs g{};
+    g.A = (const __nv_bfloat16*)A; g.sam = sam; g.sak = sak;
+    g.B = (const __nv_bfloat16*)B; g.sbk = sbk; g.sbn = sbn;
+    g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (gemm_tc(g, kEpiStore, 1, st) != cudaSuccess) return HJG_ECUDA;
+    if (timed_out) {
+        int e = 0;
+        if (cudaMemcpyAsync(&e, g_tc_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return HJG_ECUDA;
+        *timed_out = e;
+        if (e) return HJG_ETIMEOUT;
+    }
     return HJG_OK;
 }
 
