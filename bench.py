@@ -343,6 +343,86 @@ def run_mixed(args):
     return out
 
 
+def run_surrogate(args):
+    """The learned part on the 45-D game: tuples (x, v, Dv) from the plain sweeps of the
+    262,144-state workload (sweeps 23-30 of 30 at N = 131,072: 2,097,152 tuples), GPU
+    training of the 45 -> 256^3 -> 46 BF16 network on them, and, on 1,024 held-out states,
+    the value error against a high-sample tilted reference for the plain form and the
+    surrogate-assisted form over N = 4,096 ... 131,072."""
+    import torch
+    from paper_2605_18566_gb300 import Solver, Surrogate
+    w = hjg_inputs.ROCKETS45
+    t0 = time.perf_counter()
+    x = torch.from_numpy(hjg_inputs.points(w)).cuda()
+    s = Solver(w.game, w.nu, w.T, w.N, w.K, radius=w.radius)
+    s.set_points(x)
+    s.autotune(max_states=4 * SMS * 2)
+    s.picard_sweep(w.K - 8, residuals=False)
+    X, Y = [], []
+    resid = []
+    for _ in range(8):
+        r, _ = s.picard_sweep(1)
+        resid.append(float(r[0]))
+        st = s.get_state()
+        X.append(x)
+        Y.append(torch.cat([st["v"][:, None].float(), st["p"]], 1))
+    s.close()
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    X = torch.cat(X); Y = torch.cat(Y)
+    perm = torch.from_numpy(np.random.default_rng(0).permutation(X.shape[0])).cuda()
+    X = X[perm].contiguous(); Y = Y[perm].contiguous()
+    sur = Surrogate(45, 46, 256, seed=0)
+    epochs, batch = 8, 8192
+    torch.cuda.synchronize(); t1 = time.perf_counter()
+    hist = sur.fit(X, Y, epochs=epochs, batch=batch, lr=2e-3, lr_final=1e-4)
+    torch.cuda.synchronize(); t_train = time.perf_counter() - t1
+    tuples = X.shape[0] * epochs
+    flops_per_tuple = 6 * (48 * 256 + 256 * 256 * 2 + 256 * 48)   # forward + backward GEMMs
+    peaks = load_peaks()
+    tensor_peak = peaks.get("bf16_tflops", 1906.5)
+    xte = torch.from_numpy(hjg_inputs.rockets45_points(1024, seed=1)).cuda()
+
+    def solve(N, K, tilt=False, warm=None, seed=11):
+        so = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, tilt=tilt, seed=seed)
+        so.set_points(xte)
+        if warm is not None:
+            so.warm_start(warm[1], warm[0])
+        r, _ = so.picard_sweep(K)
+        st = so.get_state()
+        so.close()
+        return st["v"].cpu().numpy(), float(r[-1])
+
+    vref, rref = solve(1 << 20, 12, tilt=True, seed=7)
+    pred = sur.forward(xte)
+    vs, ps = pred[:, 0].double().contiguous(), pred[:, 1:].contiguous()
+    rows = []
+    for N in (4096, 16384, 65536, 131072):
+        for mode in ("plain", "surrogate+tilt"):
+            K = 12
+            v, r = solve(N, K, tilt=mode != "plain", warm=(vs, ps) if mode != "plain" else None)
+            rows.append({"mode": mode, "N": N, "K": K, "point_samples_per_state": N * K,
+                         "rms_value_error": float(np.sqrt(np.mean((v - vref) ** 2))),
+                         "final_residual": r})
+    sur.close()
+    out = {"metric": "surrogate training tuples/s and error vs point-samples (45-D game)",
+           "value": tuples / t_train, "unit": "tuples/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (tuples from the plain sweeps)",
+           "config": {"workload": "rockets45_gauss sweeps 23-30 -> 2,097,152 tuples; MLP 45-256-256-256-46",
+                      "epochs": epochs, "batch": batch},
+           "tuple_generation_s": t_data, "train_s": t_train, "loss": [hist[0], hist[-1]],
+           "data_residuals": resid,
+           "mlp_tflops": tuples * flops_per_tuple / t_train / 1e12,
+           "roofline": {"bound": "tensor", "achieved": tuples * flops_per_tuple / t_train / 1e12,
+                        "peak": tensor_peak, "unit": "TFLOP/s",
+                        "frac": tuples * flops_per_tuple / t_train / 1e12 / tensor_peak,
+                        "note": "whole training step (GEMMs + element-wise + Adam) at batch 8192"},
+           "reference": {"N": 1 << 20, "K": 12, "tilt": True, "final_residual": rref},
+           "surrogate_alone_rms_value_error": float(np.sqrt(np.mean((vs.cpu().numpy() - vref) ** 2))),
+           "study": rows}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,8 +430,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rockets6", choices=["rockets6", "mixed"],
-                    help="rockets6 (default, the benchmark line) or the mixed batch + flock")
+    ap.add_argument("--workload", default="rockets6", choices=["rockets6", "mixed", "surrogate"],
+                    help="rockets6 (default, the benchmark line), the mixed batch + flock, or "
+                         "the learned part on the 45-D game")
     ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS),
                     help="run one small launch of the named workload's sweep (profiling)")
     ap.add_argument("--variant", type=int, default=2, help="sweep launch variant for --ncu-case")
@@ -384,9 +465,9 @@ def main():
         print(json.dumps(out))
         return
 
-    if args.workload == "mixed":
+    if args.workload in ("mixed", "surrogate"):
         if rank == 0:
-            print(json.dumps(run_mixed(args)))
+            print(json.dumps(run_mixed(args) if args.workload == "mixed" else run_surrogate(args)))
         return
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:

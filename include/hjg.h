@@ -101,7 +101,10 @@ typedef struct {
     int32_t block_threads; /* 0: tuned default; else 128, 256 or 512 */
     int32_t grid_blocks;   /* 0: tuned default (persistent grid over the SMs) */
     int32_t variant;       /* 0: default / autotuned; v > 0 forces sweep launch variant v - 1 */
-    int32_t reserved[6];
+    uint32_t point_offset; /* global index of the first loaded state (Philox counter word 0):
+                              a shard of a larger state set draws the samples it would draw
+                              in the whole set */
+    int32_t reserved[5];
 } hjg_options;
 
 typedef struct {
@@ -154,6 +157,12 @@ hjg_status hjg_set_state(hjg_ctx *ctx, const double *v, const float *p, int64_t 
  * the device.  With opt.tilt the first sweep is then drawn from the tilted proposal around
  * theta = -delta t c^(0) p0 (Eq. tilt_shift).  Synchronises the context's stream. */
 hjg_status hjg_warm_start(hjg_ctx *ctx, const double *v0, const float *p0, int64_t ldp, int on_device);
+
+/* Per-sweep parts of the residual of the last hjg_picard_sweep call over the loaded
+ * states: out [n_sweeps][3] = (sum (v^(k+1)-v^(k))^2, sum (v^(k))^2, max |v^(k+1)-v^(k)|),
+ * FP64, host.  Shards of one state set combine these (sum, sum, max) to the global
+ * relative residual sqrt(sum0)/sqrt(sum1) of Algorithm 1. */
+hjg_status hjg_get_residual_parts(hjg_ctx *ctx, double *out);
 
 /* v^(k) history of the last hjg_picard_sweep call: rows 0..n_sweeps, row 0 = the
  * incoming v.  out is [(n_sweeps+1)][M] FP64. */

@@ -31,7 +31,8 @@ class Options(C.Structure):
     _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("tilt", C.c_int32), ("eps", C.c_double),
                 ("eta", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double),
                 ("seed", C.c_uint64), ("instance", C.c_uint32), ("block_threads", C.c_int32),
-                ("grid_blocks", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("grid_blocks", C.c_int32), ("variant", C.c_int32), ("point_offset", C.c_uint32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class Diag(C.Structure):
@@ -65,6 +66,7 @@ _SIGS = {
                                          C.c_int64, _vp, _vp, C.c_int64, _vp, _vp]),
     "hjg_flock_neighbours": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int, _vp, _vp, _vp]),
     "hjg_warm_start": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int]),
+    "hjg_get_residual_parts": (C.c_int, [_vp, _vp]),
     "hjg_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_vp)]),
     "hjg_mlp_destroy": (None, [_vp]),
     "hjg_mlp_set_stream": (C.c_int, [_vp, _vp]),

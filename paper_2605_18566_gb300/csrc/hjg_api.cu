@@ -40,6 +40,7 @@ struct hjg_ctx {
     int64_t vhist_rows = 0;   // allocated rows
     int last_sweeps = 0;      // rows used by the last call = last_sweeps + 1
     double* d_resid = nullptr;  // [K][2]
+    double* d_parts = nullptr;  // [K][3] sums behind the residual
     int resid_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the sweep kernel alone
 
@@ -92,7 +93,7 @@ hjg_status grow(hjg_ctx* ctx, T** ptr, size_t count) {
 
 // Residual of Algorithm 1 from the value history: block k reduces rows k, k+1 over all
 // states in a fixed order (deterministic) and writes (||v_{k+1}-v_k|| / ||v_k||, max |dv|).
-__global__ void residual_kernel(const double* __restrict__ vhist, int64_t M, double* out) {
+__global__ void residual_kernel(const double* __restrict__ vhist, int64_t M, double* out, double* parts) {
     constexpr int T = 256;
     __shared__ double s_num[T], s_den[T], s_sup[T];
     const int k = blockIdx.x, tid = threadIdx.x;
@@ -118,6 +119,11 @@ __global__ void residual_kernel(const double* __restrict__ vhist, int64_t M, dou
     if (tid == 0) {
         out[2 * k] = sqrt(s_num[0]) / sqrt(s_den[0]);
         out[2 * k + 1] = s_sup[0];
+        if (parts) {
+            parts[3 * k] = s_num[0];
+            parts[3 * k + 1] = s_den[0];
+            parts[3 * k + 2] = s_sup[0];
+        }
     }
 }
 
@@ -194,6 +200,7 @@ hjg_status ensure_history(hjg_ctx* ctx, int K) {
     }
     if (K > ctx->resid_cap) {
         if ((st = grow(ctx, &ctx->d_resid, (size_t)2 * K))) return st;
+        if ((st = grow(ctx, &ctx->d_parts, (size_t)3 * K))) return st;
         ctx->resid_cap = K;
     }
     return HJG_OK;
@@ -231,6 +238,7 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
     A.rk = philox_round_keys((uint32_t)ctx->opt.seed,
                              (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.instance);
     A.k0 = ctx->next_sweep;
+    A.pt0 = ctx->opt.point_offset;
     A.K = K;
     A.sigma_d = std::sqrt(ctx->sigma2);
     A.sigma = (float)A.sigma_d;
@@ -346,7 +354,7 @@ void hjg_destroy(hjg_ctx* ctx) {
     if (!ctx) return;
     cudaFree(ctx->d_x); cudaFree(ctx->d_v); cudaFree(ctx->d_p); cudaFree(ctx->d_c);
     cudaFree(ctx->d_ess); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
-    cudaFree(ctx->d_aux); cudaFree(ctx->d_idx);
+    cudaFree(ctx->d_aux); cudaFree(ctx->d_idx); cudaFree(ctx->d_parts);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -403,9 +411,9 @@ hjg_status hjg_picard_sweep(hjg_ctx* ctx, int n_sweeps, double* residual_out, do
     SweepArgs A = make_args(ctx, n_sweeps);
     HJG_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
     HJG_CUDA(ctx, ctx->kern.sweep(A, ctx->opt.tilt != 0, ctx->variant, ctx->grid, st));
-    residual_kernel<<<n_sweeps, 256, 0, st>>>(ctx->d_vhist, ctx->M, ctx->d_resid);
-    HJG_CUDA(ctx, cudaGetLastError());
     HJG_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
+    residual_kernel<<<n_sweeps, 256, 0, st>>>(ctx->d_vhist, ctx->M, ctx->d_resid, ctx->d_parts);
+    HJG_CUDA(ctx, cudaGetLastError());
     ctx->next_sweep += (uint32_t)n_sweeps;
     ctx->last_sweeps = n_sweeps;
     if (residual_out || supnorm_out) {
@@ -477,6 +485,15 @@ hjg_status hjg_warm_start(hjg_ctx* ctx, const double* v0, const float* p0, int64
     HJG_CUDA(ctx, ctx->kern.coef(ctx->d_x, ctx->ldx, M, ctx->d_p, ctx->ldx, ctx->gp, ctx->delta, ctx->eta,
                                  ctx->c_min, ctx->c_max, ctx->d_c, ctx->d_aux, kFlockAux, st));
     HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
+hjg_status hjg_get_residual_parts(hjg_ctx* ctx, double* out) {
+    if (!ctx || !out) return HJG_EINVAL;
+    if (ctx->last_sweeps == 0 || ctx->M == 0) return HJG_OK;
+    HJG_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_parts, (size_t)3 * ctx->last_sweeps * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HJG_OK;
 }
 
@@ -722,7 +739,7 @@ hjg_status hjg_batch_run(hjg_batch* b, int n_sweeps, double* residual_out, void*
         SweepArgs A = make_args(c, n_sweeps);
         if ((e = c->kern.sweep(A, c->opt.tilt != 0, c->variant, c->grid, s)) != cudaSuccess)
             return bail("sweep", e);
-        residual_kernel<<<n_sweeps, 256, 0, s>>>(c->d_vhist, c->M, c->d_resid);
+        residual_kernel<<<n_sweeps, 256, 0, s>>>(c->d_vhist, c->M, c->d_resid, c->d_parts);
         if ((e = cudaGetLastError()) != cudaSuccess) return bail("residual", e);
         if ((e = cudaEventRecord(b->join[i], s)) != cudaSuccess) return bail("join", e);
         if ((e = cudaStreamWaitEvent(origin, b->join[i], 0)) != cudaSuccess) return bail("wait join", e);

@@ -34,6 +34,7 @@ struct SweepArgs {
     int64_t ldx, ldp, M, N;
     PhiloxKeys rk;            // Philox round keys of (seed_lo, seed_hi ^ instance)
     uint32_t k0;              // global index of the first sweep
+    uint32_t pt0;             // global index of state 0 (Philox counter word 0 = pt0 + state)
     int32_t K;                // sweeps to run
     float sigma;              // sqrt(delta t)
     float sk;                 // sigma * kBmScale: y = x + theta + sk * (raw normal)
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                 float z[4 * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(grp * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                    block_normals_raw<4>(grp * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
 #pragma unroll
                 for (int t = 0; t < GS; ++t) sample(z + t * n);
             }
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                 float z[4 * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(full * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                    block_normals_raw<4>(full * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
                 for (uint32_t t = 0; t < N32 - full * GS; ++t) sample(z + t * n);
             }
 
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 float z[4 * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(grp * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                    block_normals_raw<4>(grp * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
 #pragma unroll
                 for (int t = 0; t < GS; ++t) sample(z + t * n);
             }
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 float z[4 * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(full * GB + b, (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                    block_normals_raw<4>(full * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
                 for (uint32_t t = 0; t < N32 - full * GS; ++t) sample(z + t * n);
             }
             warp_merge<n>(1, m, s, q, S);
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
                 float z[12];
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    block_normals_raw<4>(12u * i + 3u * q4 + j, (uint32_t)pt, sweep, A.rk, z + 4 * j);
+                    block_normals_raw<4>(12u * i + 3u * q4 + j, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * j);
                 float yx[4], yz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {

@@ -37,7 +37,7 @@ class Solver:
                  A=None, x0=None, d: float = 0.0, seed: int = 0, instance: int = 0,
                  tilt: bool = False, eps: float = 0.0, eta: float = -1.0,
                  c_min: float = 0.0, c_max: float = 0.0, block_threads: int = 0,
-                 grid_blocks: int = 0, variant: int = -1,
+                 grid_blocks: int = 0, variant: int = -1, point_offset: int = 0,
                  stream: Optional[torch.cuda.Stream] = None):
         self.lib = _lib.load()
         if n is None:
@@ -64,6 +64,7 @@ class Solver:
         opt.c_min = c_min; opt.c_max = c_max; opt.seed = seed; opt.instance = instance
         opt.block_threads = block_threads; opt.grid_blocks = grid_blocks
         opt.variant = variant + 1 if variant >= 0 else 0
+        opt.point_offset = point_offset
         self.opt = opt
         ctx = C.c_void_p()
         torch.cuda.init()
@@ -115,6 +116,12 @@ class Solver:
             _check(self.lib, self.ctx, st)
         self.last_status = st
         return r[:n_sweeps], s[:n_sweeps]
+
+    def residual_parts(self, n_sweeps: int) -> np.ndarray:
+        """[n_sweeps, 3] (sum dv^2, sum v^2, max |dv|) of the last picard_sweep call."""
+        out = np.zeros((max(n_sweeps, 1), 3))
+        _check(self.lib, self.ctx, self.lib.hjg_get_residual_parts(self.ctx, out.ctypes.data_as(C.c_void_p)))
+        return out[:n_sweeps]
 
     def get_state(self, device: bool = True):
         M, n = self.M, self.n
