@@ -90,7 +90,9 @@ typedef struct {
 } hjg_target;
 
 typedef struct {
-    int64_t N;           /* samples per state and sweep (>= 1) */
+    int64_t N;           /* samples per state and sweep (>= 1; at most 2^34 / S, S = n for
+                            n <= 8 and n rounded up to a multiple of 4 above, so that one
+                            state's stream needs at most 2^32 Philox blocks) */
     int32_t K;           /* sweeps run by hjg_value_grad */
     int32_t tilt;        /* 1: tilted proposal theta = -delta t c Dv (Eq. tilt_shift) */
     double eps;          /* hjg_value_grad stops after the sweep whose residual < eps (0: never) */

@@ -10,9 +10,9 @@ namespace hjg {
 struct GameKernels {
     int n;            // state dimension
     int nvariants;    // launch variants (CTA size x register budget) available
-    int threads[8];   // CTA size of each variant
-    int minb[8];      // minimum resident CTAs per SM each variant was compiled for
-    int per_warp[8];  // 1: one warp per state (the grid is counted in CTAs of threads/32 warps)
+    int threads[16];   // CTA size of each variant
+    int minb[16];      // minimum resident CTAs per SM each variant was compiled for
+    int per_warp[16];  // 1: one warp per state (the grid is counted in CTAs of threads/32 warps)
     // Launch the fused sweep, variant v, on `grid` CTAs.
     cudaError_t (*sweep)(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st);
     // Resident CTAs per SM of variant v (0 if it cannot launch).
@@ -70,4 +70,4 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
     }
 #define HJG_CASE_LAUNCH(i, KIND, T, B) case i: return launch_sweep_generic<HJG_GAME, KIND, T, B>(A, tilt, grid, st);
 #define HJG_CASE_OCC(i, KIND, T, B) case i: return occupancy_generic<HJG_GAME, KIND, T, B>(tilt);
-#define HJG_FILL(i, KIND, T, B) k.threads[i] = T; k.minb[i] = B; k.per_warp[i] = KIND;
+#define HJG_FILL(i, KIND, T, B) k.threads[i] = T; k.minb[i] = B; k.per_warp[i] = (KIND) & 1;

@@ -305,6 +305,7 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
     if (!dyn || !target || !opt) return HJG_EINVAL;
     if (!(nu > 0) || !(T > 0) || !std::isfinite(nu) || !std::isfinite(T)) return HJG_EINVAL;
     if (opt->N < 1 || opt->N > 0xFFFFFFFFll || opt->K < 0) return HJG_EINVAL;
+    if (!stream_blocks_fit(dyn->n, opt->N)) return HJG_EINVAL;
     hjg_ctx* ctx = new (std::nothrow) hjg_ctx();
     if (!ctx) return HJG_ENOMEM;
     ctx->dyn = *dyn;

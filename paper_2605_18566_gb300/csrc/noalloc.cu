@@ -123,6 +123,7 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     if (!dyn || !target || !opt) return HJG_EINVAL;
     if (!(nu > 0) || !(T > 0) || !std::isfinite(nu) || !std::isfinite(T)) return HJG_EINVAL;
     if (opt->N < 1 || opt->N > 0xFFFFFFFFll || opt->K < 1 || M < 0 || M > 0xFFFFFFFFll) return HJG_EINVAL;
+    if (!stream_blocks_fit(dyn->n, opt->N)) return HJG_EINVAL;
     GameKernels kern{};
     if (!pick_kernels(dyn, &kern)) return HJG_EINVAL;
     const int n = dyn->n;

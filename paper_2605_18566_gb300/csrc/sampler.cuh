@@ -106,10 +106,9 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 ctr, const PhiloxKeys& r
 // slope and the final gradient).
 constexpr float kBmScale = -1.1774100225154747f;
 
+// Box-Muller on the four words of one Philox block (constant factors left out, see above).
 template <int NUSE>
-__device__ __forceinline__ void block_normals_raw(uint32_t b, uint32_t point, uint32_t sweep,
-                                                  const PhiloxKeys& rk, float* z) {
-    const uint4 r = philox4x32_10_rk(make_uint4(point, b, sweep, 0u), rk);
+__device__ __forceinline__ void bm_normals_raw(const uint4& r, float* z) {
     {
         const float ra = sqrt_approx(fabsf(lg2_approx(u01(r.x))));
         const float ph = bm_phase(r.y);
@@ -124,7 +123,17 @@ __device__ __forceinline__ void block_normals_raw(uint32_t b, uint32_t point, ui
     }
 }
 
-// The first NUSE (1..4) standard normals of block b of the (point, sweep) stream.
+// Philox block b of the stream of (point, sweep).
+__device__ __forceinline__ uint4 stream_block(uint32_t b, uint32_t point, uint32_t sweep,
+                                              const PhiloxKeys& rk) {
+    return philox4x32_10_rk(make_uint4(point, b, sweep, 0u), rk);
+}
+
+template <int NUSE>
+__device__ __forceinline__ void block_normals_raw(uint32_t b, uint32_t point, uint32_t sweep,
+                                                  const PhiloxKeys& rk, float* z) {
+    bm_normals_raw<NUSE>(stream_block(b, point, sweep, rk), z);
+}
 template <int NUSE>
 __device__ __forceinline__ void block_normals(uint32_t b, uint32_t point, uint32_t sweep,
                                               uint32_t k0, uint32_t k1, float* z) {
@@ -138,8 +147,17 @@ __device__ __forceinline__ void block_normals(uint32_t b, uint32_t point, uint32
 __host__ __device__ constexpr int slot_stride(int n) { return n <= 8 ? n : (n + 3) / 4 * 4; }
 __host__ __device__ constexpr int gcd4(int a) { return (a % 4 == 0) ? 4 : (a % 2 == 0 ? 2 : 1); }
 __host__ __device__ constexpr int group_samples(int n) { return 4 / gcd4(slot_stride(n)); }
+
 __host__ __device__ constexpr int group_blocks(int n) {
     return group_samples(n) * slot_stride(n) / 4;
+}
+
+// The kernels carry a stream's block index in one 32-bit counter word (the high word is
+// 0), so the groups that hold N samples of an n-dimensional state may span at most 2^32
+// blocks.
+__host__ __device__ constexpr bool stream_blocks_fit(int n, int64_t N) {
+    return n >= 1 && N >= 0 &&
+           ((uint64_t)N + group_samples(n) - 1) / group_samples(n) * (uint64_t)group_blocks(n) <= 0x100000000ull;
 }
 
 }  // namespace hjg

@@ -223,11 +223,46 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
     __syncthreads();
 }
 
+// The full groups g = start, start + STRIDE, ... < full of one (state, sweep) stream, each
+// turned into GB Philox blocks, 4 GB normals and GS samples handed to `sample`.  With PIPE
+// the Philox blocks of the next group are drawn while the current group's Box-Muller and
+// samples run (software pipelining), so that each warp's instruction stream interleaves the
+// integer multiplies of the generator with the transcendental and FP32 work of the samples;
+// the one group drawn past the end is discarded.  Both forms consume identical draws.
+template <int GS, int GB, int STRIDE, bool PIPE, class F>
+__device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32_t point, uint32_t sweep,
+                                           const PhiloxKeys& rk, F&& sample_group) {
+    if constexpr (PIPE) {
+        uint4 r[GB];
+#pragma unroll
+        for (int b = 0; b < GB; ++b) r[b] = stream_block(start * GB + b, point, sweep, rk);
+        for (uint32_t grp = start; grp < full; grp += STRIDE) {
+            uint4 rn[GB];
+            const uint32_t nxt = grp + STRIDE;
+#pragma unroll
+            for (int b = 0; b < GB; ++b) rn[b] = stream_block(nxt * GB + b, point, sweep, rk);
+            float z[4 * GB];
+#pragma unroll
+            for (int b = 0; b < GB; ++b) bm_normals_raw<4>(r[b], z + 4 * b);
+            sample_group(z);
+#pragma unroll
+            for (int b = 0; b < GB; ++b) r[b] = rn[b];
+        }
+    } else {
+        for (uint32_t grp = start; grp < full; grp += STRIDE) {
+            float z[4 * GB];
+#pragma unroll
+            for (int b = 0; b < GB; ++b) block_normals_raw<4>(grp * GB + b, point, sweep, rk, z + 4 * b);
+            sample_group(z);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
 // g = group_samples(n) that end on a Philox block boundary (n = 3: 4 samples from 3 blocks;
 // n = 6: 2 samples from 3 blocks), so every normal drawn is used.
-template <class G, int THREADS, int MINB, bool TILT>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int NPAD = (n + 3) / 4 * 4;
@@ -269,14 +304,11 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                 }
                 lse_accumulate<n>(a, zt, m, s, q, S);
             };
-            for (uint32_t grp = tid; grp < full; grp += THREADS) {
-                float z[4 * GB];
+            run_groups<GS, GB, THREADS, PIPE>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                              [&](const float* z) {
 #pragma unroll
-                for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(grp * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
-#pragma unroll
-                for (int t = 0; t < GS; ++t) sample(z + t * n);
-            }
+                                                  for (int t = 0; t < GS; ++t) sample(z + t * n);
+                                              });
             if (GS > 1 && full < groups && tid == (int)(full % THREADS)) {   // ragged last group
                 float z[4 * GB];
 #pragma unroll
@@ -342,7 +374,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k
 // FP64 recovery and coefficient update and broadcasts the new (c, Dv) with shuffles.
 // No CTA barrier is involved, so a warp never waits for another state's epilogue.
 // Chosen by the autotuner when there are many more states than warps in flight.
-template <class G, int THREADS, int MINB, bool TILT>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int GS = group_samples(n);
@@ -398,14 +430,11 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 }
                 lse_accumulate<n>(a, zt, m, s, q, S);
             };
-            for (uint32_t grp = lane; grp < full; grp += 32) {
-                float z[4 * GB];
+            run_groups<GS, GB, 32, PIPE>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                         [&](const float* z) {
 #pragma unroll
-                for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(grp * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
-#pragma unroll
-                for (int t = 0; t < GS; ++t) sample(z + t * n);
-            }
+                                             for (int t = 0; t < GS; ++t) sample(z + t * n);
+                                         });
             if (GS > 1 && full < groups && lane == (int)(full % 32)) {
                 float z[4 * GB];
 #pragma unroll
@@ -567,24 +596,26 @@ cudaError_t launch_coef(const float* x, int64_t ldx, int64_t M, const float* p, 
     return cudaGetLastError();
 }
 
-// Launch variants the autotuner chooses among: kind 0 = one CTA per state, kind 1 = one
-// warp per state; CTA size; minimum resident CTAs per SM (the register budget).  Every
-// game's translation unit instantiates all of them.
+// Launch variants the autotuner chooses among: kind bit 0 = one warp per state (else one
+// CTA per state), kind bit 1 = software-pipelined sampler; CTA size; minimum resident CTAs
+// per SM (the register budget).  Every game's translation unit instantiates all of them.
 #define HJG_SWEEP_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 5) X(2, 0, 256, 6) X(3, 0, 128, 1) \
-    X(4, 0, 512, 1) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12)
+    X(4, 0, 512, 1) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12) X(8, 2, 256, 4)      \
+    X(9, 2, 128, 8) X(10, 3, 256, 4) X(11, 3, 128, 8)
 #define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 1) X(3, 0, 128, 4) \
     X(4, 0, 512, 1)
-constexpr int kNumVariants = 8;
+constexpr int kNumVariants = 12;
 constexpr int kNumR45Variants = 5;
 
 template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
-    if constexpr (KIND == 1) {
-        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true><<<grid, THREADS, 0, st>>>(A);
-        else sweep_kernel_warp<G, THREADS, MINB, false><<<grid, THREADS, 0, st>>>(A);
+    constexpr bool PIPE = (KIND & 2) != 0;
+    if constexpr ((KIND & 1) != 0) {
+        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true, PIPE><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel_warp<G, THREADS, MINB, false, PIPE><<<grid, THREADS, 0, st>>>(A);
     } else {
-        if (tilt) sweep_kernel<G, THREADS, MINB, true><<<grid, THREADS, 0, st>>>(A);
-        else sweep_kernel<G, THREADS, MINB, false><<<grid, THREADS, 0, st>>>(A);
+        if (tilt) sweep_kernel<G, THREADS, MINB, true, PIPE><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel<G, THREADS, MINB, false, PIPE><<<grid, THREADS, 0, st>>>(A);
     }
     return cudaGetLastError();
 }
@@ -592,12 +623,13 @@ cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaSt
 template <class G, int KIND, int THREADS, int MINB>
 int occupancy_generic(bool tilt) {
     int nb = 0;
-    if constexpr (KIND == 1) {
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true>, THREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false>, THREADS, 0);
+    constexpr bool PIPE = (KIND & 2) != 0;
+    if constexpr ((KIND & 1) != 0) {
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true, PIPE>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false, PIPE>, THREADS, 0);
     } else {
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true>, THREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false>, THREADS, 0);
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true, PIPE>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false, PIPE>, THREADS, 0);
     }
     return nb;
 }

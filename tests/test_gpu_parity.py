@@ -157,6 +157,16 @@ def test_empty_and_zero_sweeps():
     s.close()
 
 
+def test_sample_count_limit():
+    """One state's stream may span at most 2^32 Philox blocks: the largest N of the 45-D
+    game (12 blocks per sample) is accepted, the next one is refused."""
+    from paper_2605_18566_gb300 import HJGError
+    nmax = (1 << 32) // 12
+    solver_for(W3, N=nmax, K=1).close()
+    with pytest.raises(HJGError):
+        solver_for(W3, N=nmax + 1, K=1)
+
+
 def test_resume_is_bit_exact_and_deterministic():
     w = W2
     x = torch.from_numpy(hjg_inputs.points(w, M=200)).cuda()
@@ -208,7 +218,7 @@ def test_autotune_keeps_state_and_results():
     ref = oracle.picard(problem_for(w), x.cpu().numpy().astype(np.float64), 4096, 3)
     assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.99, what="tuned variant")
     xs = x.cpu().numpy().astype(np.float64)
-    for v in range(8):     # every launch variant agrees with the oracle on one sweep
+    for v in range(12):    # every launch variant agrees with the oracle on one sweep
         s = solver_for(w, N=4096, K=1, variant=v)
         s.set_points(x)
         c0 = s.get_state()["c"].cpu().numpy().astype(np.float64)
