@@ -296,6 +296,21 @@ def ncu_case(w, variant):
     s.close()
 
 
+def ncu_case_surrogate():
+    """A small case of the surrogate's training for ncu: one epoch of 8 Adam steps at batch
+    8,192 on 65,536 seeded Gaussian tuples of the 45-D network (45 -> 256^3 -> 46)."""
+    import torch
+    from paper_2605_18566_gb300 import Surrogate
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(65536, 45, device="cuda", generator=g)
+    Y = torch.randn(65536, 46, device="cuda", generator=g)
+    sur = Surrogate(45, 46, 256, seed=0)
+    hist = sur.fit(X, Y, epochs=1, batch=8192, lr=1e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "surrogate_mlp", "batch": 8192, "steps": 8, "loss": hist[-1]}))
+    sur.close()
+
+
 def run_mixed(args):
     """The mixed batch plus the 100,000-agent flock, all at nu = 0.02, T = 1, N = 16,384,
     K = 15 (the instances of hjg_inputs.MIXED and the flock), advanced by one CUDA-graph
@@ -433,11 +448,14 @@ def main():
     ap.add_argument("--workload", default="rockets6", choices=["rockets6", "mixed", "surrogate"],
                     help="rockets6 (default, the benchmark line), the mixed batch + flock, or "
                          "the learned part on the 45-D game")
-    ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS),
+    ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS) + ["surrogate_mlp"],
                     help="run one small launch of the named workload's sweep (profiling)")
     ap.add_argument("--variant", type=int, default=2, help="sweep launch variant for --ncu-case")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
+    if args.ncu_case == "surrogate_mlp":
+        ncu_case_surrogate()
+        return
     if args.ncu_case:
         ncu_case(hjg_inputs.WORKLOADS[args.ncu_case], args.variant)
         return

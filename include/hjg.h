@@ -106,7 +106,10 @@ typedef struct {
     uint32_t point_offset; /* global index of the first loaded state (Philox counter word 0):
                               a shard of a larger state set draws the samples it would draw
                               in the whole set */
-    int32_t reserved[5];
+    int32_t tube;          /* 1: tube form v_t + min{0, H} = (delta/2) Lap v (Eq. HJ-RCBRT-Visc):
+                              Gamma is built from min{0, H}, so a state that has entered the
+                              target keeps a non-positive value */
+    int32_t reserved[4];
 } hjg_options;
 
 typedef struct {

@@ -40,7 +40,7 @@ class Problem(C.Structure):
         ("speed", C.c_double * 16), ("h_sign", C.c_double),
         ("A", C.c_double * 64), ("x0", C.c_double * 8), ("d", C.c_double),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("tilt", C.c_int32),
-        ("flock_k", C.c_int32), ("pad_", C.c_int32),
+        ("flock_k", C.c_int32), ("tube", C.c_int32),
     ]
 
 
@@ -109,9 +109,10 @@ def _f64(a, shape=None):
 
 def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=None,
                  c_max=None, radius=0.5, speed=None, h_sign=1.0, A=None, x0=None,
-                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7) -> Problem:
+                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7, tube=False) -> Problem:
     """Build an oracle problem.  Defaults follow the readings used throughout:
-    eta = 1e-6, c_min = 1e-2/delta, c_max = 1e2/delta."""
+    eta = 1e-6, c_min = 1e-2/delta, c_max = 1e2/delta.  tube=True selects the tube form
+    (Eq. HJ-RCBRT-Visc): the coefficient map uses min{0, H}."""
     P = Problem()
     P.game = GAMES[game]
     P.n = n
@@ -137,6 +138,7 @@ def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=N
     P.instance = instance
     P.tilt = 1 if tilt else 0
     P.flock_k = flock_k
+    P.tube = 1 if tube else 0
     return P
 
 

@@ -68,7 +68,7 @@ typedef struct {
     uint32_t instance;
     int32_t tilt;       /* 1: tilted proposal theta = -sigma^2 c p (Eq. tilt_shift) */
     int32_t flock_k;    /* flock: neighbours per agent */
-    int32_t pad_;
+    int32_t tube;       /* 1: tube form, Gamma built from min{0, H} (Eq. HJ-RCBRT-Visc) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -316,10 +316,12 @@ double orc_hamiltonian(const orc_problem *P, const double *x, const double *p, d
 }
 
 /* Coefficient-update map Gamma of Theorem 2.8 with the regularised denominator
- * of Lemma 2.7 and the sign-keeping clip of Remark 2.8 (sign(0) taken as +). */
+ * of Lemma 2.7 and the sign-keeping clip of Remark 2.8 (sign(0) taken as +).  The
+ * tube form (Eq. HJ-RCBRT-Visc) replaces H by min{0, H}. */
 double orc_coef(const orc_problem *P, const double *x, const double *p, double psibar)
 {
     double h = orc_hamiltonian(P, x, p, psibar);
+    if (P->tube && !(h <= 0.0)) h = 0.0;   /* min{0, H}; a NaN H counts as 0 */
     double pp = 0.0;
     for (int a = 0; a < P->n; ++a) pp += p[a] * p[a];
     double c = (2.0 / P->delta) * h / (pp + P->eta);

@@ -11,6 +11,7 @@ namespace hjg {
 struct GameParams {
     int32_t game;
     int32_t n;
+    int32_t tube;     // 1: the tube form, Gamma built from min{0, H} (Eq. HJ-RCBRT-Visc)
     float radius;
     float h_sign;
     float speed[16];
@@ -284,7 +285,8 @@ struct Quadratic {
 // Coefficient-update map Gamma (Eq. coeff_frozen with the regulariser of Lemma 2.7 and
 // the sign-keeping clip of Remark 2.8; sign(0) = +, NaN -> c_min).
 __device__ __forceinline__ double coef_update(double h, double pp, double delta, double eta,
-                                              double c_min, double c_max, int* clipped) {
+                                              double c_min, double c_max, int tube, int* clipped) {
+    if (tube) h = fmin(h, 0.0);   // the freezing operator min{0, H} of the tube form
     const double c = (2.0 / delta) * h / (pp + eta);
     double mag = fabs(c);
     int cl = 0;

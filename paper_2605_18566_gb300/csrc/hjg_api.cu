@@ -160,6 +160,7 @@ void fill_game_params(hjg_ctx* ctx) {
     memset(&g, 0, sizeof g);
     g.game = ctx->dyn.game;
     g.n = ctx->n;
+    g.tube = ctx->opt.tube != 0;
     g.radius = (float)ctx->target.radius;
     g.radius_d = ctx->target.radius;
     g.h_sign = (float)ctx->dyn.h_sign;

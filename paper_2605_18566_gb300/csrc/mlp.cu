@@ -43,6 +43,7 @@ struct GemmArgs {
     __nv_bfloat16* H;  // BF16 activation output (kEpiBiasSilu), [M][ldh]
     int64_t ldh;
     const float* bias; // [N]
+    int kper;          // K values per split (a multiple of 64 when split)
 };
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
@@ -50,12 +51,12 @@ __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z));
 // ------------------------------------------------------------------------------------
 // The GEMM runs on the 5th-generation tensor cores (tcgen05, sm_100 family):
 // a CTA of 4 warps owns a 128 x 128 tile of C, accumulated in tensor memory (TMEM, 128
-// lanes x 128 FP32 columns).  Per K chunk of 64 the operands are staged by all threads into
-// shared memory in the canonical K-major no-swizzle layout (8-row x 16-byte core matrices,
-// 128 B apart along K, 256 B apart along rows), made visible to the tensor core's async
-// proxy, and thread 0 issues four tcgen05.mma (M = 128, N = 128, K = 16) and commits them to
-// an mbarrier; every wait on that barrier is bounded and records a time-out in *err.
-// The epilogue reads TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31 = rows).
+// lanes x 128 FP32 columns).  Per K chunk of 64 the operands are staged in shared memory
+// in the canonical K-major no-swizzle layout (8-row x 16-byte core matrices, 128 B apart
+// along K, 256 B apart along rows), made visible to the tensor core's async proxy, and
+// thread 0 issues four tcgen05.mma (M = 128, N = 128, K = 16) and commits them to an
+// mbarrier; every wait on a barrier is bounded and records a time-out in *err.  The
+// epilogue reads TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31 = rows).
 constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -98,24 +99,57 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err
     return false;
 }
 
+// Two-stage pipeline: while the tensor core multiplies chunk c from one shared-memory
+// stage, the CTA's threads copy chunk c + 1 into the other with 16-byte cp.async (global
+// -> shared, bypassing L1); a stage is overwritten only after the commit of the MMAs that
+// read it has arrived on that stage's mbarrier.  Both operands are K-major in global memory
+// (A(m, k) = A[m lda + k], B(k, n) = Bt[n ldb + k], lda and ldb multiples of 8, rows
+// 16-byte aligned); gemm() packs other layouts first.
+constexpr int kTcStage = (kTcM + kTcN) * kTcK * 2;   // bytes of one stage (A then B)
+constexpr int kTcSmem = 2 * kTcStage;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+// Copy the 64-wide K chunk starting at k0 of rows [r0, r0 + R) of a K-major operand into
+// the canonical layout at `dst`; rows >= rmax and columns >= kend read as zero.  Lanes pair
+// up on 32 contiguous bytes of one row (one sector); eight rows fill 256 contiguous bytes of
+// shared memory, so the 16-byte writes are conflict-free.
+template <int R>
+__device__ __forceinline__ void load_chunk(uint32_t dst, const __nv_bfloat16* src, int64_t ld, int r0, int rmax,
+                                           int k0, int kend, int tid) {
+#pragma unroll
+    for (int i = 0; i < R * 8 / 128; ++i) {
+        const int e = tid + 128 * i;
+        const int lo = e & 1, r = (e >> 1) % R, kq = (e >> 1) / R;
+        const int k8 = 2 * kq + lo;
+        const int row = r0 + r, kk = k0 + 8 * k8;
+        const bool in = row < rmax && kk < kend;
+        const __nv_bfloat16* p = in ? src + (int64_t)row * ld + kk : src;
+        cp_async16(dst + canon_off(r, 8 * k8, R), p, in ? 16u : 0u);
+    }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err) {
-    __shared__ __align__(1024) uint8_t sA[kTcM * kTcK * 2];
-    __shared__ __align__(1024) uint8_t sB[kTcN * kTcK * 2];
-    __shared__ __align__(8) uint64_t mbar;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
-    const int kper = (g.K + gridDim.z - 1) / gridDim.z;
-    const int kbeg = blockIdx.z * kper, kend = min(g.K, kbeg + kper);
-    const uint32_t bar = smem_u32(&mbar);
+    const int kbeg = blockIdx.z * g.kper, kend = min(g.K, kbeg + g.kper);
+    const int nch = kend > kbeg ? (kend - kbeg + kTcK - 1) / kTcK : 0;
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&tmem_base)), "r"(kTcN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -123,32 +157,41 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = umma_idesc_bf16(kTcM, kTcN);
-    uint32_t phase = 0;
+    uint32_t phase[2] = {0u, 0u};
     bool ok = true;
-    int nchunk = 0;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = kbeg; k0 < kend && ok; k0 += kTcK, ++nchunk) {
-        for (int e = tid; e < kTcM * kTcK; e += 128) {
-            const int r = e / kTcK, k = e % kTcK;
-            const int m = m0 + r, kk = k0 + k;
-            const __nv_bfloat16 a = (m < g.M && kk < kend) ? g.A[(int64_t)m * g.sam + (int64_t)kk * g.sak] : zero;
-            *reinterpret_cast<__nv_bfloat16*>(sA + canon_off(r, k, kTcM)) = a;
-        }
-        for (int e = tid; e < kTcN * kTcK; e += 128) {
-            const int r = e / kTcK, k = e % kTcK;
-            const int n = n0 + r, kk = k0 + k;
-            const __nv_bfloat16 b = (n < g.N && kk < kend) ? g.B[(int64_t)kk * g.sbk + (int64_t)n * g.sbn] : zero;
-            *reinterpret_cast<__nv_bfloat16*>(sB + canon_off(r, k, kTcN)) = b;
+    if (nch > 0) {
+        load_chunk<kTcM>(s0, g.A, g.sam, m0, g.M, kbeg, kend, tid);
+        load_chunk<kTcN>(s0 + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, kbeg, kend, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int c = 0; c < nch && ok; ++c) {
+        const int s = c & 1;
+        if (c + 1 < nch) {
+            if (c >= 1) {   // the MMAs of chunk c - 1 read stage s ^ 1: wait for them
+                ok = mbar_wait(s ? bar0 : bar1, phase[s ^ 1], err);
+                phase[s ^ 1] ^= 1u;
+                ok = __syncthreads_and(ok) != 0;
+                if (!ok) break;
+            }
+            const uint32_t st = s0 + (uint32_t)((s ^ 1) * kTcStage);
+            const int k0 = kbeg + (c + 1) * kTcK;
+            load_chunk<kTcM>(st, g.A, g.sam, m0, g.M, k0, kend, tid);
+            load_chunk<kTcN>(st + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, k0, kend, tid);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = s0 + (uint32_t)(s * kTcStage), sb = sa + kTcM * kTcK * 2;
 #pragma unroll
             for (int ks = 0; ks < kTcK / 16; ++ks) {
-                const uint64_t da = umma_desc(smem_u32(sA) + ks * (kTcM * 32), 128, 256);
-                const uint64_t db = umma_desc(smem_u32(sB) + ks * (kTcN * 32), 128, 256);
-                const uint32_t acc = (nchunk > 0 || ks > 0) ? 1u : 0u;
+                const uint64_t da = umma_desc(sa + ks * (kTcM * 32), 128, 256);
+                const uint64_t db = umma_desc(sb + ks * (kTcN * 32), 128, 256);
+                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
@@ -156,18 +199,25 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(bar) : "memory");
+                         :: "r"(s ? bar1 : bar0) : "memory");
         }
-        ok = mbar_wait(bar, phase, err);   // operands may be overwritten only after the MMAs read them
-        phase ^= 1;
-        ok = __syncthreads_and(ok) != 0;   // one verdict for the whole CTA (.sync.aligned epilogue)
+    }
+    if (nch > 0) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // nothing left in flight on any path
+        if (ok) {   // the last commit covers every earlier MMA of this thread
+            const int s = (nch - 1) & 1;
+            ok = mbar_wait(s ? bar1 : bar0, phase[s], err);
+        }
+        ok = __syncthreads_and(ok) != 0;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: row r = 32 warp + lane, 8 columns per tcgen05.ld
     const int r = warp * 32 + lane;
     const int m = m0 + r;
     float* C = g.C ? g.C + (int64_t)blockIdx.z * g.M * g.ldc : nullptr;
-    if (ok && nchunk > 0) {
+    const bool vecC = C && (g.ldc % 4) == 0 && ((uintptr_t)C & 15) == 0;
+    const bool vecH = (g.ldh % 8) == 0 && ((uintptr_t)g.H & 15) == 0;
+    if (ok && nch > 0) {
 #pragma unroll 1
         for (int c0 = 0; c0 < kTcN; c0 += 8) {
             uint32_t v[8];
@@ -176,15 +226,38 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                 : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m < g.M) {
+            if (m >= g.M) continue;
+            const int nb = n0 + c0;
+            float x[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (n >= g.N) continue;
-                    float x = __uint_as_float(v[j]);
-                    if (EPI != kEpiStore) x += g.bias[n];
-                    if (C) C[(int64_t)m * g.ldc + n] = x;
-                    if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + n] = __float2bfloat16(silu(x));
+            for (int j = 0; j < 8; ++j) {
+                x[j] = __uint_as_float(v[j]);
+                if (EPI != kEpiStore && nb + j < g.N) x[j] += g.bias[nb + j];
+            }
+            if (nb + 8 <= g.N) {
+                if (C && vecC) {
+                    float4* d = reinterpret_cast<float4*>(C + (int64_t)m * g.ldc + nb);
+                    d[0] = make_float4(x[0], x[1], x[2], x[3]);
+                    d[1] = make_float4(x[4], x[5], x[6], x[7]);
+                } else if (C) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) C[(int64_t)m * g.ldc + nb + j] = x[j];
+                }
+                if (EPI == kEpiBiasSilu) {
+                    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(silu(x[j]));
+                    if (vecH) {
+                        *reinterpret_cast<uint4*>(g.H + (int64_t)m * g.ldh + nb) = *reinterpret_cast<const uint4*>(h);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
+                    }
+                }
+            } else {
+                for (int j = 0; j < 8 && nb + j < g.N; ++j) {
+                    if (C) C[(int64_t)m * g.ldc + nb + j] = x[j];
+                    if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + nb + j] = __float2bfloat16(silu(x[j]));
                 }
             }
         }
@@ -200,23 +273,91 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN));
 }
 
+// Pack an operand into K-major form: dst[r][k] = src[r * s_r + k * s_k] for k < K, zero
+// for K <= k < ldd (ldd a multiple of 8).  32 x 32 tiles through shared memory, so that
+// both the reads (along whichever index of src is contiguous) and the writes (along k)
+// are coalesced.
+__global__ void pack_kmajor_kernel(const __nv_bfloat16* __restrict__ src, int64_t s_r, int64_t s_k, int R, int K,
+                                   __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const bool r_fast = s_r == 1;   // src contiguous along r: let threadIdx.x run along r
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int a = r_fast ? k0 + i : r0 + i;                  // slow index
+        const int b = r_fast ? r0 + threadIdx.x : k0 + threadIdx.x;   // fast index
+        const int r = r_fast ? b : a, k = r_fast ? a : b;
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (r < R && k < K) v = src[(int64_t)r * s_r + (int64_t)k * s_k];
+        if (r_fast) tile[threadIdx.x][i] = v; else tile[i][threadIdx.x] = v;   // tile[r - r0][k - k0]
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, k = k0 + threadIdx.x;
+        if (r < R && k < ldd) dst[(int64_t)r * ldd + k] = tile[i][threadIdx.x];
+    }
+}
+
 int* g_tc_err = nullptr;   // device word set by a timed-out barrier wait
 
-cudaError_t gemm_tc(const GemmArgs& g, int epi, int splits, cudaStream_t st) {
-    if (!g_tc_err) {
-        if (cudaMalloc(&g_tc_err, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
-        cudaMemset(g_tc_err, 0, sizeof(int));
+inline int64_t pad8(int64_t k) { return (k + 7) / 8 * 8; }
+
+// Scratch (elements) gemm() needs to pack the operands of g into K-major form.
+inline int64_t gemm_scratch_a(const GemmArgs& g) {
+    const bool ok = g.sak == 1 && g.sam % 8 == 0 && g.K % 8 == 0 && ((uintptr_t)g.A & 15) == 0;
+    return ok ? 0 : (int64_t)g.M * pad8(g.K);
+}
+inline int64_t gemm_scratch_b(const GemmArgs& g) {
+    const bool ok = g.sbk == 1 && g.sbn % 8 == 0 && g.K % 8 == 0 && ((uintptr_t)g.B & 15) == 0;
+    return ok ? 0 : (int64_t)g.N * pad8(g.K);
+}
+
+template <int EPI>
+cudaError_t launch_tc(const GemmArgs& k, int splits, cudaStream_t st) {
+    static bool attr = false;   // opt in to 64 KB of dynamic shared memory once per process
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kTcSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
-    dim3 grid((g.N + kTcN - 1) / kTcN, (g.M + kTcM - 1) / kTcM, splits);
-    switch (epi) {
-    case kEpiStore: gemm_tc_kernel<kEpiStore><<<grid, 128, 0, st>>>(g, g_tc_err); break;
-    case kEpiBiasSilu: gemm_tc_kernel<kEpiBiasSilu><<<grid, 128, 0, st>>>(g, g_tc_err); break;
-    case kEpiBias: gemm_tc_kernel<kEpiBias><<<grid, 128, 0, st>>>(g, g_tc_err); break;
-    }
+    dim3 grid((k.N + kTcN - 1) / kTcN, (k.M + kTcM - 1) / kTcM, splits);
+    gemm_tc_kernel<EPI><<<grid, 128, kTcSmem, st>>>(k, g_tc_err);
     return cudaGetLastError();
 }
 
-cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st) { return gemm_tc(g, epi, splits, st); }
+// C = A B (+ epilogue) on the tensor cores.  Operands that are not K-major with aligned
+// rows are packed into the caller's scratch (sizes gemm_scratch_a / _b) first.  With
+// splits > 1 each split covers a multiple of 64 values of K and writes its own partial.
+cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st, __nv_bfloat16* scratch_a = nullptr,
+                 __nv_bfloat16* scratch_b = nullptr) {
+    if (!g_tc_err) {
+        if (cudaMalloc(&g_tc_err, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (cudaMemset(g_tc_err, 0, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    }
+    GemmArgs k = g;
+    const int64_t Kp = pad8(g.K);
+    if (gemm_scratch_a(g)) {
+        if (!scratch_a) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((g.M + 31) / 32));
+        pack_kmajor_kernel<<<grid, dim3(32, 8), 0, st>>>(g.A, g.sam, g.sak, g.M, g.K, scratch_a, Kp);
+        k.A = scratch_a; k.sam = Kp; k.sak = 1;
+    }
+    if (gemm_scratch_b(g)) {
+        if (!scratch_b) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((g.N + 31) / 32));
+        pack_kmajor_kernel<<<grid, dim3(32, 8), 0, st>>>(g.B, g.sbn, g.sbk, g.N, g.K, scratch_b, Kp);
+        k.B = scratch_b; k.sbn = Kp; k.sbk = 1;
+    }
+    k.K = (int)Kp;   // the padded columns hold zeros
+    // split boundaries on chunk boundaries; a split left without K values writes zeros
+    k.kper = splits > 1 ? ((int)((Kp + splits - 1) / splits) + kTcK - 1) / kTcK * kTcK : (int)Kp;
+    switch (epi) {
+    case kEpiStore: return launch_tc<kEpiStore>(k, splits, st);
+    case kEpiBiasSilu: return launch_tc<kEpiBiasSilu>(k, splits, st);
+    case kEpiBias: return launch_tc<kEpiBias>(k, splits, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 // ------------------------------------------------------------------------------------
 // Element-wise kernels.
@@ -284,13 +425,28 @@ __global__ void reduce_wgrad_kernel(const float* __restrict__ part, int splits, 
     grad[e] = s;
 }
 
-__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dZ, int64_t B, int cols,
-                                 float* __restrict__ db) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+// Bias gradient = column sums of dZ [B][cols], first stage: CTA (x, y) sums 32 columns
+// over the y-th of gridDim.y row chunks (8 row lanes, then a shared-memory sum); the
+// chunk partials [gridDim.y][cols] are added by reduce_wgrad_kernel (fixed order).
+constexpr int kBiasChunks = 64;
+__global__ void __launch_bounds__(256) bias_partial_kernel(const __nv_bfloat16* __restrict__ dZ, int64_t B,
+                                                           int cols, float* __restrict__ part) {
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int64_t per = (B + gridDim.y - 1) / gridDim.y;
+    const int64_t b0 = (int64_t)blockIdx.y * per;
+    const int64_t b1 = b0 + per < B ? b0 + per : B;
     float s = 0.0f;
-    for (int64_t b = 0; b < B; ++b) s += __bfloat162float(dZ[b * cols + c]);
-    db[c] = s;
+    if (c < cols)
+        for (int64_t b = b0 + threadIdx.y; b < b1; b += 8) s += __bfloat162float(dZ[b * cols + c]);
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+        part[(int64_t)blockIdx.y * cols + c] = t;
+    }
 }
 
 // Adam (Kingma & Ba) on the FP32 master parameters; refresh the BF16 weight copy.
@@ -361,6 +517,8 @@ struct hjg_mlp {
     __nv_bfloat16* dZ = nullptr;          // [cap][width] BF16
     float* dH = nullptr;                  // [cap][width] FP32
     float* wpart = nullptr;               // split-K partial weight gradients
+    __nv_bfloat16* packA = nullptr;       // K-major copies of transposed GEMM operands
+    __nv_bfloat16* packB = nullptr;       //   (dZ^T, H^T, W^T) for the backward GEMMs
     double* lpart = nullptr;              // loss partial sums
     int64_t lpart_cap = 0;
     int64_t step = 0;
@@ -375,12 +533,17 @@ constexpr int kSplits = 16;
 hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
     if (B <= m->cap) return HJG_OK;
     auto fre = [](void* p) { if (p) cudaFree(p); };
-    fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart);
+    fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart); fre(m->packA); fre(m->packB);
+    m->packA = m->packB = nullptr;
     for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); m->Z[l] = nullptr; m->H[l] = nullptr; }
     const int W = m->width;
+    const int64_t D = std::max<int64_t>(W, std::max(m->in_pad, m->out_pad));
+    const int64_t pa = D * pad8(B), pbk = D * std::max(pad8(B), pad8(D));
     bool ok = cudaMalloc(&m->X, (size_t)B * m->in_pad * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&m->dZ, (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess &&
-              cudaMalloc(&m->dH, (size_t)B * W * sizeof(float)) == cudaSuccess;
+              cudaMalloc(&m->dH, (size_t)B * W * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->packA, (size_t)pa * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&m->packB, (size_t)pbk * sizeof(__nv_bfloat16)) == cudaSuccess;
     for (int l = 0; l < kLayers && ok; ++l) {
         ok = cudaMalloc(&m->Z[l], (size_t)B * W * sizeof(float)) == cudaSuccess &&
              cudaMalloc(&m->H[l], (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess;
@@ -426,11 +589,14 @@ cudaError_t mlp_backward(hjg_mlp* m, int64_t B) {
         gw.B = hin; gw.sbk = cols; gw.sbn = 1;
         gw.M = rows; gw.N = cols; gw.K = (int)B;
         gw.C = m->wpart; gw.ldc = cols;
-        e = gemm(gw, kEpiStore, kSplits, m->stream);
+        e = gemm(gw, kEpiStore, kSplits, m->stream, m->packA, m->packB);
         if (e != cudaSuccess) break;
         const int64_t nw = (int64_t)rows * cols;
         reduce_wgrad_kernel<<<nblk(nw), 256, 0, m->stream>>>(m->wpart, kSplits, nw, m->g + m->w_off[l]);
-        bias_grad_kernel<<<nblk(rows, 128), 128, 0, m->stream>>>(m->dZ, B, rows, m->g + m->b_off[l]);
+        // the split-K partials are consumed: the bias partials reuse their buffer
+        bias_partial_kernel<<<dim3((rows + 31) / 32, kBiasChunks), dim3(32, 8), 0, m->stream>>>(m->dZ, B, rows,
+                                                                                            m->wpart);
+        reduce_wgrad_kernel<<<nblk(rows), 256, 0, m->stream>>>(m->wpart, kBiasChunks, rows, m->g + m->b_off[l]);
         if ((e = cudaGetLastError()) != cudaSuccess || l == 0) break;
         // dH_{l-1} = dZ_l . W_l  ([B][cols])
         GemmArgs gd{};
@@ -438,7 +604,7 @@ cudaError_t mlp_backward(hjg_mlp* m, int64_t B) {
         gd.B = m->pb + m->w_off[l]; gd.sbk = cols; gd.sbn = 1;
         gd.M = (int)B; gd.N = cols; gd.K = rows;
         gd.C = m->dH; gd.ldc = cols;
-        e = gemm(gd, kEpiStore, 1, m->stream);
+        e = gemm(gd, kEpiStore, 1, m->stream, m->packA, m->packB);
         if (e != cudaSuccess) break;
         const int64_t nh = B * (int64_t)cols;
         silu_backward_kernel<<<nblk(nh), 256, 0, m->stream>>>(m->dH, m->Z[l - 1], nh, m->dZ);
@@ -495,10 +661,12 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
     const size_t nb = (size_t)off * sizeof(float);
     int64_t wpart = 0;
     for (int l = 0; l < kLayers; ++l) wpart = std::max<int64_t>(wpart, (int64_t)m->rows[l] * m->cols[l]);
+    wpart *= kSplits;
+    for (int l = 0; l < kLayers; ++l) wpart = std::max<int64_t>(wpart, (int64_t)kBiasChunks * m->rows[l]);
     if (cudaMalloc(&m->p, nb) != cudaSuccess || cudaMalloc(&m->g, nb) != cudaSuccess ||
         cudaMalloc(&m->m1, nb) != cudaSuccess || cudaMalloc(&m->m2, nb) != cudaSuccess ||
         cudaMalloc(&m->pb, (size_t)off * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc(&m->wpart, (size_t)kSplits * wpart * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&m->wpart, (size_t)wpart * sizeof(float)) != cudaSuccess) {
         hjg_mlp_destroy(m);
         return HJG_ENOMEM;
     }
@@ -523,7 +691,7 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
 void hjg_mlp_destroy(hjg_mlp* m) {
     if (!m) return;
     auto fre = [](void* p) { if (p) cudaFree(p); };
-    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->wpart);
+    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->wpart); fre(m->packA); fre(m->packB);
     fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart);
     for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); }
     delete m;
@@ -603,7 +771,7 @@ hjg_status hjg_mlp_input_grad(hjg_mlp* m, const float* x, int64_t ldx, int64_t B
         gd.B = m->pb + m->w_off[l]; gd.sbk = cols; gd.sbn = 1;
         gd.M = (int)B; gd.N = cols; gd.K = rows;
         gd.C = m->dH; gd.ldc = cols;
-        if (gemm(gd, kEpiStore, 1, st) != cudaSuccess) return HJG_ECUDA;
+        if (gemm(gd, kEpiStore, 1, st, m->packA, m->packB) != cudaSuccess) return HJG_ECUDA;
         if (l == 0) break;
         const int64_t nh = B * (int64_t)cols;
         silu_backward_kernel<<<nblk(nh), 256, 0, st>>>(m->dH, m->Z[l - 1], nh, m->dZ);
@@ -625,7 +793,18 @@ hjg_status hjg_gemm_bf16(const void* A, int64_t sam, int64_t sak, const void* B,
     g.B = (const __nv_bfloat16*)B; g.sbk = sbk; g.sbn = sbn;
     g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc;
     cudaStream_t st = (cudaStream_t)stream;
-    if (gemm_tc(g, kEpiStore, 1, st) != cudaSuccess) return HJG_ECUDA;
+    // operands in other layouts are packed into stream-ordered temporaries
+    const int64_t na = gemm_scratch_a(g), nb = gemm_scratch_b(g);
+    __nv_bfloat16 *sa = nullptr, *sb = nullptr;
+    if ((na && cudaMallocAsync((void**)&sa, (size_t)na * sizeof(__nv_bfloat16), st) != cudaSuccess) ||
+        (nb && cudaMallocAsync((void**)&sb, (size_t)nb * sizeof(__nv_bfloat16), st) != cudaSuccess)) {
+        if (sa) cudaFreeAsync(sa, st);
+        return HJG_ENOMEM;
+    }
+    const cudaError_t ge = gemm(g, kEpiStore, 1, st, sa, sb);
+    if (sa) cudaFreeAsync(sa, st);
+    if (sb) cudaFreeAsync(sb, st);
+    if (ge != cudaSuccess) return HJG_ECUDA;
     if (timed_out) {
         int e = 0;
         if (cudaMemcpyAsync(&e, g_tc_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -92,11 +92,12 @@ bool pick_kernels(const hjg_dynamics* dyn, GameKernels* k) {
     return k->n == dyn->n;
 }
 
-GameParams game_params(const hjg_dynamics* dyn, const hjg_target* t) {
+GameParams game_params(const hjg_dynamics* dyn, const hjg_target* t, int tube) {
     GameParams g;
     memset(&g, 0, sizeof g);
     g.game = dyn->game;
     g.n = dyn->n;
+    g.tube = tube != 0;
     g.radius = (float)t->radius;
     g.radius_d = t->radius;
     g.h_sign = (float)dyn->h_sign;
@@ -167,7 +168,7 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     int64_t grid = opt->grid_blocks > 0 ? opt->grid_blocks : (int64_t)occ * sms;
     if (grid > M) grid = M;
     cudaStream_t s = (cudaStream_t)stream;
-    const GameParams g = game_params(dyn, target);
+    const GameParams g = game_params(dyn, target, opt->tube);
 
     if (cudaMemsetAsync(cnt, 0, 256, s) != cudaSuccess) return HJG_ECUDA;
     if (kern.init(pts, ld, M, g, delta, eta, c_min, c_max, v_out, grad_out, ldg, c, ess, s, nullptr, 0) !=

@@ -205,7 +205,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
         finite = finite && isfinite(v);
         const double h = G::ham_c(sh.x, sh.hc, sh.pd, A.g);
         int clipped = 0;
-        const float c_new = (float)coef_update(h, pp, A.delta, A.eta, A.c_min, A.c_max, &clipped);
+        const float c_new = (float)coef_update(h, pp, A.delta, A.eta, A.c_min, A.c_max, A.g.tube, &clipped);
         if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
         if (last) {
             A.v[pt] = v;
@@ -354,7 +354,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k
     finite = finite && isfinite(v);
     int clipped = 0;
     const float c_new = (float)coef_update(G::ham_d(xd, pd, A.g, aux), pp, A.delta, A.eta, A.c_min,
-                                           A.c_max, &clipped);
+                                           A.c_max, A.g.tube, &clipped);
     for (int j = 0; j < n; ++j) p[j] = (float)pd[j];
     if (A.vhist) A.vhist[(int64_t)(k + 1) * A.M + pt] = v;
     if (last) {
@@ -561,7 +561,7 @@ __global__ void init_kernel(const float* __restrict__ x, int64_t ldx, int64_t M,
     double pp = 0.0;
     for (int j = 0; j < n; ++j) { p[m * ldp + j] = (float)gr[j]; pp += gr[j] * gr[j]; }
     int clipped;
-    c[m] = (float)coef_update(G::ham_d(xd, gr, g, am), pp, delta, eta, c_min, c_max, &clipped);
+    c[m] = (float)coef_update(G::ham_d(xd, gr, g, am), pp, delta, eta, c_min, c_max, g.tube, &clipped);
     ess[m] = 0.0f;
 }
 
@@ -583,7 +583,7 @@ __global__ void coef_kernel(const float* __restrict__ x, int64_t ldx, int64_t M,
     }
     int clipped;
     c[m] = (float)coef_update(G::ham_d(xd, pd, g, G::kAux > 0 ? aux + m * ldaux : nullptr), pp, delta, eta,
-                              c_min, c_max, &clipped);
+                              c_min, c_max, g.tube, &clipped);
 }
 
 template <class G>

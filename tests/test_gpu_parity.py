@@ -64,6 +64,20 @@ def test_trajectory_parity(w, M, N, K):
     np.testing.assert_allclose(out["resid"], out["ref_resid"], rtol=5e-3, atol=1e-7)
 
 
+@pytest.mark.parametrize("w,M,N,K", [(W1, 1024, 4096, 6), (W2, 129, 16384, 5)],
+                         ids=["dubins3", "rockets6"])
+def test_tube_trajectory_parity(w, M, N, K):
+    """Tube form (Eq. HJ-RCBRT-Visc): same P1 / Gamma / P2 protocol with min{0, H} in the
+    coefficient map; every coefficient is negative or +c_min."""
+    x = hjg_inputs.points(w, M=M)
+    out = check_trajectory(w, x, N, K, tube=True, min_pass=0.97 if M > 200 else 0.9)
+    c_min = 1e-2 / w.delta
+    for st in out["states"]:
+        c = st["c"].astype(np.float64)
+        assert np.all((c < 0) | np.isclose(c, c_min, rtol=1e-6))
+    assert any(np.any(st["c"] < 0) for st in out["states"])
+
+
 def test_trajectory_parity_tilted():
     w = W1
     x = hjg_inputs.points(w, M=1024)
