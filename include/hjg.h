@@ -169,6 +169,24 @@ hjg_status hjg_warm_start(hjg_ctx *ctx, const double *v0, const float *p0, int64
  * relative residual sqrt(sum0)/sqrt(sum1) of Algorithm 1. */
 hjg_status hjg_get_residual_parts(hjg_ctx *ctx, double *out);
 
+/* Conservative safety certificate (Cor. 2.9) of the current iterate, after at least one
+ * sweep: per state the band half-width
+ *     E_m = e0 + q/(1-q) ||v^(K) - v^(K-1)||_inf + sqrt(2 log(2/delta_p)) se_m
+ * (e0 >= 0: the caller's bound on the quasi-linearisation defect and the viscosity error;
+ * the second term is the a-posteriori iteration bound of Theorem 2.8 with contraction factor
+ * 0 <= q < 1 and the last sweep's sup-norm change; se_m = sqrt(1/ESS_m - 1/N) / |c_m| is the
+ * delta-method Monte-Carlo standard error of v_m in the last sweep, c_m the coefficient that
+ * sweep used, and the factor a sub-Gaussian two-sided quantile for failure probability
+ * 0 < delta_p < 1).  label_out [M] int8: +1 SAFE (v > E_m), -1 UNSAFE (v < -E_m), 0
+ * UNDETERMINED, also wherever the last sweep's ESS is below ess_min >= 0 (collapsed
+ * weights, Section 2.4: the standard error is then not trustworthy); band_out [M] FP32 = E_m; se_out [M] FP32 = se_m; counts_out [3] (host) =
+ * (SAFE, UNSAFE, UNDETERMINED) counts.  Every output may be NULL; on_device selects
+ * device or host pointers for the arrays.  EINVAL for parameters outside their ranges or
+ * when no sweep has run since the iterate was loaded or replaced.  Synchronises the
+ * context's stream. */
+hjg_status hjg_certify(hjg_ctx *ctx, double e0, double q, double delta_p, double ess_min, int8_t *label_out,
+                       float *band_out, float *se_out, int64_t *counts_out, int on_device);
+
 /* v^(k) history of the last hjg_picard_sweep call: rows 0..n_sweeps, row 0 = the
  * incoming v.  out is [(n_sweeps+1)][M] FP64. */
 hjg_status hjg_get_history(hjg_ctx *ctx, double *out, int on_device);

@@ -15,6 +15,7 @@ gradient and tilted estimators), Section 2.4 (ESS), Appendix D.2 and Section 3.2
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -258,6 +259,32 @@ def residual(v_old, v_new):
     rel = C.c_double(); sup = C.c_double()
     lib().orc_residual(v_old.size, _dp(v_old), _dp(v_new), C.byref(rel), C.byref(sup))
     return rel.value, sup.value
+
+
+def mc_std_error(ess, c, N):
+    """Delta-method Monte-Carlo standard error of v = -(1/c) log((1/N) sum w_i) from one
+    sweep: sd(w) / (sqrt(N) mean(w) |c|) = sqrt(1/ESS - 1/N) / |c| with ESS = (sum w)^2 /
+    sum w^2 (Section 2.4) and c the coefficient that sweep used (Theorem 2.4 gives the
+    O(N^-1/2) rate this estimates per state)."""
+    ess = np.asarray(ess, dtype=np.float64)
+    return np.sqrt(np.maximum(0.0, 1.0 / ess - 1.0 / N)) / np.abs(np.asarray(c, dtype=np.float64))
+
+
+def certify(v, se, sup_last, e0, q, delta_p, ess=None, ess_min=0.0):
+    """Conservative certificate of Cor. 2.9: band E = e0 + q/(1-q) sup_last + z se with
+    z = sqrt(2 log(2/delta_p)) (the Monte-Carlo term at failure probability delta_p; the
+    iteration term is the a-posteriori bound of Theorem 2.8 from the last sweep's
+    sup-norm change; e0 bounds the remaining defect and viscosity terms).  Returns labels
+    (+1 SAFE where v > E, -1 UNSAFE where v < -E, 0 UNDETERMINED) and E.  States whose
+    ESS is below ess_min are UNDETERMINED: with collapsed weights (Section 2.4) the
+    standard error itself is not trustworthy."""
+    v = np.asarray(v, dtype=np.float64)
+    z = math.sqrt(2.0 * math.log(2.0 / delta_p))
+    band = e0 + (q / (1.0 - q)) * sup_last + z * np.asarray(se, dtype=np.float64)
+    labels = np.where(v > band, 1, np.where(v < -band, -1, 0)).astype(np.int8)
+    if ess is not None:
+        labels[np.asarray(ess, dtype=np.float64) < ess_min] = 0
+    return labels, band
 
 
 def flock_neighbours(states, k=7):

@@ -33,6 +33,11 @@ struct hjg_ctx {
     float* d_p = nullptr;
     float* d_c = nullptr;
     float* d_ess = nullptr;
+    float* d_se = nullptr;        // [M] Monte-Carlo standard error of v (last sweep)
+    bool se_valid = false;        // a sweep has run since the iterate was last replaced
+    int8_t* d_label = nullptr;    // [M] certificate labels
+    float* d_band = nullptr;      // [M] certificate band half-widths
+    unsigned long long* d_cert = nullptr;  // [3] label counts
     float* d_aux = nullptr;       // [M][22] flock: neighbour positions and their mean heading
     int32_t* d_idx = nullptr;     // [M][7] flock: neighbour indices
     unsigned long long* d_counters = nullptr;
@@ -184,6 +189,9 @@ hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
     if ((st = grow(ctx, &ctx->d_p, (size_t)M * ctx->ldx))) return st;
     if ((st = grow(ctx, &ctx->d_c, (size_t)M))) return st;
     if ((st = grow(ctx, &ctx->d_ess, (size_t)M))) return st;
+    if ((st = grow(ctx, &ctx->d_se, (size_t)M))) return st;
+    if ((st = grow(ctx, &ctx->d_label, (size_t)M))) return st;
+    if ((st = grow(ctx, &ctx->d_band, (size_t)M))) return st;
     if (ctx->dyn.game == HJG_FLOCK4) {
         if ((st = grow(ctx, &ctx->d_aux, (size_t)M * kFlockAux))) return st;
         if ((st = grow(ctx, &ctx->d_idx, (size_t)M * 7))) return st;
@@ -231,6 +239,7 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
     A.v = ctx->d_v;
     A.vhist = ctx->d_vhist;
     A.ess = ctx->d_ess;
+    A.se = ctx->d_se;
     A.counters = ctx->d_counters;
     A.ldx = ctx->ldx;
     A.ldp = ctx->ldx;
@@ -280,6 +289,27 @@ hjg_status choose_launch(hjg_ctx* ctx) {
 }
 
 }  // namespace
+
+// Conservative certificate of Cor. 2.9 per state: band E_m = e0 + q/(1-q) ||v^(K) - v^(K-1)||_inf
+// + z se_m (the a-posteriori iteration bound of Theorem 2.8 from the last sweep's sup-norm
+// change, and the Monte-Carlo term from the state's standard error); label +1 (SAFE) if
+// v > E_m, -1 (UNSAFE) if v < -E_m, else 0 (UNDETERMINED); a state whose ESS is below
+// ess_min is UNDETERMINED.
+__global__ void certify_kernel(const double* __restrict__ v, const float* __restrict__ se,
+                               const float* __restrict__ ess, int64_t M, double e0, double qf,
+                               const double* __restrict__ sup_last, double z, double ess_min,
+                               int8_t* __restrict__ label, float* __restrict__ band,
+                               unsigned long long* __restrict__ counts) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double b = e0 + (qf > 0.0 ? qf * sup_last[0] : 0.0) + z * (double)se[m];
+    const double vm = v[m];
+    int8_t l = vm > b ? 1 : (vm < -b ? -1 : 0);
+    if ((double)ess[m] < ess_min) l = 0;   // collapsed weights: the error estimate is not trusted
+    label[m] = l;
+    band[m] = (float)b;
+    atomicAdd(&counts[l + 1], 1ull);
+}
 
 extern "C" {
 
@@ -355,7 +385,8 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
 void hjg_destroy(hjg_ctx* ctx) {
     if (!ctx) return;
     cudaFree(ctx->d_x); cudaFree(ctx->d_v); cudaFree(ctx->d_p); cudaFree(ctx->d_c);
-    cudaFree(ctx->d_ess); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
+    cudaFree(ctx->d_ess); cudaFree(ctx->d_se); cudaFree(ctx->d_label); cudaFree(ctx->d_band);
+    cudaFree(ctx->d_cert); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
     cudaFree(ctx->d_aux); cudaFree(ctx->d_idx); cudaFree(ctx->d_parts);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -382,6 +413,7 @@ hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld,
     ctx->M = M;
     ctx->next_sweep = 0;
     ctx->last_sweeps = 0;
+    ctx->se_valid = false;
     if (M == 0) return HJG_OK;
     if ((s = stage_points(ctx, pts, M, ld, on_device, st))) return s;
     if (ctx->ldx > ctx->n) {
@@ -418,6 +450,7 @@ hjg_status hjg_picard_sweep(hjg_ctx* ctx, int n_sweeps, double* residual_out, do
     HJG_CUDA(ctx, cudaGetLastError());
     ctx->next_sweep += (uint32_t)n_sweeps;
     ctx->last_sweeps = n_sweeps;
+    ctx->se_valid = true;
     if (residual_out || supnorm_out) {
         std::vector<double> r(2 * (size_t)n_sweeps);
         unsigned long long cnt[4];
@@ -471,6 +504,7 @@ hjg_status hjg_set_state(hjg_ctx* ctx, const double* v, const float* p, int64_t 
         HJG_CUDA(ctx, cudaStreamSynchronize(st));
     }
     ctx->next_sweep = next_sweep;
+    ctx->se_valid = false;
     return HJG_OK;
 }
 
@@ -481,6 +515,7 @@ hjg_status hjg_warm_start(hjg_ctx* ctx, const double* v0, const float* p0, int64
     if (M == 0) return HJG_OK;
     cudaStream_t st = ctx->stream;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ctx->se_valid = false;
     if (v0) HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_v, v0, M * sizeof(double), kind, st));
     HJG_CUDA(ctx, cudaMemcpy2DAsync(ctx->d_p, ctx->ldx * sizeof(float), p0, ldp * sizeof(float),
                                     ctx->n * sizeof(float), (size_t)M, kind, st));
@@ -496,6 +531,44 @@ hjg_status hjg_get_residual_parts(hjg_ctx* ctx, double* out) {
     HJG_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_parts, (size_t)3 * ctx->last_sweeps * sizeof(double),
                                   cudaMemcpyDeviceToHost, ctx->stream));
     HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HJG_OK;
+}
+
+hjg_status hjg_certify(hjg_ctx* ctx, double e0, double q, double delta_p, double ess_min, int8_t* label_out,
+                       float* band_out, float* se_out, int64_t* counts_out, int on_device) {
+    if (!ctx) return HJG_EINVAL;
+    if (!(e0 >= 0.0) || !(q >= 0.0 && q < 1.0) || !(delta_p > 0.0 && delta_p < 1.0) || !(ess_min >= 0.0))
+        return fail(ctx, HJG_EINVAL, "certify: need e0 >= 0, 0 <= q < 1, 0 < delta_p < 1, ess_min >= 0");
+    const int64_t M = ctx->M;
+    if (M == 0) {
+        if (counts_out) counts_out[0] = counts_out[1] = counts_out[2] = 0;
+        return HJG_OK;
+    }
+    if (!ctx->se_valid || ctx->last_sweeps == 0)
+        return fail(ctx, HJG_EINVAL, "certify: run at least one sweep on the current iterate first");
+    cudaStream_t st = ctx->stream;
+    if (!ctx->d_cert && cudaMalloc((void**)&ctx->d_cert, 3 * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(ctx, HJG_ENOMEM, "certify: counters");
+    HJG_CUDA(ctx, cudaMemsetAsync(ctx->d_cert, 0, 3 * sizeof(unsigned long long), st));
+    const double z = std::sqrt(2.0 * std::log(2.0 / delta_p));
+    const double qf = q / (1.0 - q);
+    const double* sup_last = ctx->d_resid + 2 * (ctx->last_sweeps - 1) + 1;
+    certify_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(ctx->d_v, ctx->d_se, ctx->d_ess, M, e0, qf,
+                                                                 sup_last, z, ess_min, ctx->d_label, ctx->d_band,
+                                                                 ctx->d_cert);
+    HJG_CUDA(ctx, cudaGetLastError());
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (label_out) HJG_CUDA(ctx, cudaMemcpyAsync(label_out, ctx->d_label, M * sizeof(int8_t), kind, st));
+    if (band_out) HJG_CUDA(ctx, cudaMemcpyAsync(band_out, ctx->d_band, M * sizeof(float), kind, st));
+    if (se_out) HJG_CUDA(ctx, cudaMemcpyAsync(se_out, ctx->d_se, M * sizeof(float), kind, st));
+    unsigned long long cnt[3] = {0, 0, 0};
+    HJG_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->d_cert, sizeof cnt, cudaMemcpyDeviceToHost, st));
+    HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    if (counts_out) {   // SAFE, UNSAFE, UNDETERMINED
+        counts_out[0] = (int64_t)cnt[2];
+        counts_out[1] = (int64_t)cnt[0];
+        counts_out[2] = (int64_t)cnt[1];
+    }
     return HJG_OK;
 }
 
@@ -591,7 +664,7 @@ hjg_status hjg_autotune(hjg_ctx* ctx, int64_t max_states, int32_t* variant_out, 
         const int64_t per_cta = ctx->kern.per_warp[var] ? ctx->kern.threads[var] / 32 : 1;
         const int grid = (int)std::min<int64_t>((int64_t)occ * ctx->num_sms, (Mt + per_cta - 1) / per_cta);
         SweepArgs A = make_args(ctx, 1);
-        A.M = Mt; A.p = p; A.c = c; A.v = v; A.ess = ess; A.vhist = nullptr; A.counters = cnt;
+        A.M = Mt; A.p = p; A.c = c; A.v = v; A.ess = ess; A.se = nullptr; A.vhist = nullptr; A.counters = cnt;
         float ms = 0.0f;
         for (int rep = 0; rep < 2 && s == HJG_OK; ++rep) {   // warm-up, then timed
             cudaError_t e = cudaMemcpyAsync(p, ctx->d_p, (size_t)Mt * ctx->ldx * sizeof(float),
@@ -770,6 +843,7 @@ hjg_status hjg_batch_run(hjg_batch* b, int n_sweeps, double* residual_out, void*
     for (hjg_ctx* c : b->ctxs) {
         c->next_sweep += (uint32_t)n_sweeps;
         c->last_sweeps = n_sweeps;
+        c->se_valid = true;
     }
     hjg_status result = HJG_OK;
     if (residual_out || device_ms || own_origin) {

@@ -30,6 +30,7 @@ struct SweepArgs {
     double* v;                // [M] value iterate (in: v^(k), out: v^(k+K))
     double* vhist;            // [K+1][M] value history (row 0 = incoming v); may be null
     float* ess;               // [M] ESS of the last sweep
+    float* se;                // [M] Monte-Carlo standard error of v in the last sweep, or null
     unsigned long long* counters;  // [0] non-finite states, [1] clipped coefficients (last sweep)
     int64_t ldx, ldp, M, N;
     PhiloxKeys rk;            // Philox round keys of (seed_lo, seed_hi ^ instance)
@@ -211,6 +212,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
             A.v[pt] = v;
             A.c[pt] = c_new;
             A.ess[pt] = (float)(s * s / sh.q);
+            if (A.se) A.se[pt] = (float)(sqrt(fmax(0.0, sh.q / (s * s) - 1.0 / (double)A.N)) / fabs(c));
             if (!finite) atomicAdd(&A.counters[0], 1ull);
             if (clipped) atomicAdd(&A.counters[1], 1ull);
         }
@@ -361,6 +363,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k
         A.v[pt] = v;
         A.c[pt] = c_new;
         A.ess[pt] = (float)(sd * sd / (double)q);
+        if (A.se) A.se[pt] = (float)(sqrt(fmax(0.0, (double)q / (sd * sd) - 1.0 / (double)A.N)) / fabs(cd));
         for (int j = 0; j < n; ++j) A.p[pt * A.ldp + j] = p[j];
         if (!finite) atomicAdd(&A.counters[0], 1ull);
         if (clipped) atomicAdd(&A.counters[1], 1ull);

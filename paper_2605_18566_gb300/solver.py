@@ -124,6 +124,20 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.hjg_get_residual_parts(self.ctx, out.ctypes.data_as(C.c_void_p)))
         return out[:n_sweeps]
 
+    def certify(self, e0: float = 0.0, q: float = 0.0, delta_p: float = 0.05, ess_min: float = 0.0):
+        """Conservative certificate of the current iterate (Cor. 2.9): returns (labels int8
+        [M] with +1 SAFE / -1 UNSAFE / 0 UNDETERMINED, band half-widths [M], Monte-Carlo
+        standard errors [M], counts (safe, unsafe, undetermined)), tensors on the GPU."""
+        M = self.M
+        lab = torch.empty(M, dtype=torch.int8, device="cuda")
+        band = torch.empty(M, dtype=torch.float32, device="cuda")
+        se = torch.empty(M, dtype=torch.float32, device="cuda")
+        cnt = np.zeros(3, dtype=np.int64)
+        _check(self.lib, self.ctx, self.lib.hjg_certify(
+            self.ctx, e0, q, delta_p, ess_min, self._ptr(lab), self._ptr(band), self._ptr(se),
+            cnt.ctypes.data_as(C.c_void_p), 1))
+        return lab, band, se, tuple(int(x) for x in cnt)
+
     def get_state(self, device: bool = True):
         M, n = self.M, self.n
         kw = dict(device="cuda") if device else {}
