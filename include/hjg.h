@@ -135,7 +135,9 @@ hjg_status hjg_create(const hjg_dynamics *dyn, const hjg_target *target, double 
 
 /* Load M evaluation states (row-major [M][ld] FP32, host or device) and form the initial
  * iterate of Algorithm 1: v^(0) = l(x), p^(0) = Dl(x) (0 where undefined), c^(0) =
- * Gamma(p^(0)).  Resets the sweep counter to 0.  Device buffers grow as needed. */
+ * Gamma(p^(0)).  Resets the sweep counter to 0.  Device buffers grow as needed.  With H
+ * horizons set (hjg_set_horizons) the context holds M H items, item h M + m being state m
+ * at horizon t_h, and every per-state array of the other calls has M H rows in that order. */
 hjg_status hjg_set_points(hjg_ctx *ctx, const float *pts, int64_t M, int64_t ld, int on_device,
                           void *stream);
 
@@ -155,6 +157,15 @@ hjg_status hjg_get_state(hjg_ctx *ctx, double *v, float *p, int64_t ldp, float *
  * of an earlier run reproduces it bit for bit. */
 hjg_status hjg_set_state(hjg_ctx *ctx, const double *v, const float *p, int64_t ldp,
                          const float *c, uint32_t next_sweep, int on_device);
+
+/* Several horizons in one solve: the value v(t_h; x) at each of the n_horizons times
+ * t_h > 0 (host array, copied) is computed for every loaded state in the same launches,
+ * item h M + m using the heat kernel of width sqrt(delta t_h) (Lemma 2.2 at t = t_h) and
+ * its own Philox stream (counter word 0 = point_offset + h M + m).  The items are
+ * independent solves; the residual runs over all of them.  Drops the loaded states (load
+ * them again); n_horizons = 0 returns to the single horizon T of hjg_create.  EINVAL for a
+ * non-positive or non-finite time. */
+hjg_status hjg_set_horizons(hjg_ctx *ctx, const double *t, int n_horizons);
 
 /* Warm start (a surrogate's prediction in place of Algorithm 1's initial iterate): set
  * p^(0) = p0 [M][ldp] FP32 and, if v0 is not NULL, v^(0) = v0 [M] FP64, then recompute the

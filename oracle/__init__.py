@@ -254,6 +254,30 @@ def picard(P, x, N, K, k0=0, state=None, nbr=None, psibar=None, idx=None):
             "resid": resid, "sup": sup, "ess": ess}
 
 
+def picard_horizons(P, x, N, K, times, nbr=None, psibar=None):
+    """The value at several horizons t_h: for each h an independent run of Algorithm 1 at
+    T = t_h (kernel width sqrt(delta t_h), Lemma 2.2) whose state m carries the global
+    index h M + m; the residual of each sweep is the relative L2 change over all items.
+    Returns v [H*M], p [H*M, n], c, resid [K], sup [K], ess (horizon-major)."""
+    x = _f64(x).reshape(-1, P.n)
+    M = x.shape[0]
+    T0 = P.T
+    outs = []
+    try:
+        for h, t in enumerate(times):
+            P.T = float(t)
+            outs.append(picard(P, x, N, K, nbr=nbr, psibar=psibar, idx=h * M + np.arange(M)))
+    finally:
+        P.T = T0
+    vh = np.concatenate([o["v_hist"] for o in outs], axis=1)
+    dv = np.diff(vh, axis=0)
+    resid = np.sqrt((dv ** 2).sum(1)) / np.sqrt((vh[:-1] ** 2).sum(1))
+    sup = np.abs(dv).max(1) if K > 0 else np.zeros(0)
+    return {"v": vh[-1].copy(), "v_hist": vh, "p": np.concatenate([o["p"] for o in outs]),
+            "c": np.concatenate([o["c"] for o in outs]), "ess": np.concatenate([o["ess"] for o in outs]),
+            "resid": resid, "sup": sup}
+
+
 def residual(v_old, v_new):
     v_old = _f64(v_old); v_new = _f64(v_new)
     rel = C.c_double(); sup = C.c_double()

@@ -38,6 +38,9 @@ struct hjg_ctx {
     int8_t* d_label = nullptr;    // [M] certificate labels
     float* d_band = nullptr;      // [M] certificate band half-widths
     unsigned long long* d_cert = nullptr;  // [3] label counts
+    std::vector<double> horizons;  // several horizons t per solve (empty: the single T)
+    Sig* d_tsig = nullptr;         // [horizons] kernel widths
+    int64_t m_base = 0;            // states per horizon
     float* d_aux = nullptr;       // [M][22] flock: neighbour positions and their mean heading
     int32_t* d_idx = nullptr;     // [M][7] flock: neighbour indices
     unsigned long long* d_counters = nullptr;
@@ -245,6 +248,10 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
     A.ldp = ctx->ldx;
     A.M = ctx->M;
     A.N = ctx->opt.N;
+    if (!ctx->horizons.empty()) {
+        A.tsig = ctx->d_tsig;
+        A.m_base = ctx->m_base;
+    }
     A.rk = philox_round_keys((uint32_t)ctx->opt.seed,
                              (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.instance);
     A.k0 = ctx->next_sweep;
@@ -386,7 +393,7 @@ void hjg_destroy(hjg_ctx* ctx) {
     if (!ctx) return;
     cudaFree(ctx->d_x); cudaFree(ctx->d_v); cudaFree(ctx->d_p); cudaFree(ctx->d_c);
     cudaFree(ctx->d_ess); cudaFree(ctx->d_se); cudaFree(ctx->d_label); cudaFree(ctx->d_band);
-    cudaFree(ctx->d_cert); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
+    cudaFree(ctx->d_cert); cudaFree(ctx->d_tsig); cudaFree(ctx->d_counters); cudaFree(ctx->d_vhist); cudaFree(ctx->d_resid);
     cudaFree(ctx->d_aux); cudaFree(ctx->d_idx); cudaFree(ctx->d_parts);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -404,13 +411,16 @@ hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld,
     if (!ctx) return HJG_EINVAL;
     if (ctx->dyn.game == HJG_FLOCK4 && M > 0 && M < 8)
         return fail(ctx, HJG_EINVAL, "a flock needs at least 8 agents (7 neighbours each)");
-    if (M < 0 || M > 0xFFFFFFFFll || (M > 0 && !pts) || ld < ctx->n)
+    const int64_t H = ctx->horizons.empty() ? 1 : (int64_t)ctx->horizons.size();
+    if (M < 0 || M * H > 0xFFFFFFFFll || (M > 0 && !pts) || ld < ctx->n)
         return fail(ctx, HJG_EINVAL, "set_points: bad M=%lld or ld=%lld (n=%d)", (long long)M,
                     (long long)ld, ctx->n);
     cudaStream_t st = pick_stream(ctx, stream);
     hjg_status s;
-    if ((s = ensure_capacity(ctx, M))) return s;
-    ctx->M = M;
+    const int64_t items = M * H;   // item j M + m: state m at horizon j
+    if ((s = ensure_capacity(ctx, items))) return s;
+    ctx->M = items;
+    ctx->m_base = M;
     ctx->next_sweep = 0;
     ctx->last_sweeps = 0;
     ctx->se_valid = false;
@@ -419,15 +429,49 @@ hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld,
     if (ctx->ldx > ctx->n) {
         // zero the padding columns of x and p so every row is a clean float4 multiple
         HJG_CUDA(ctx, cudaMemset2DAsync(ctx->d_x + ctx->n, ctx->ldx * sizeof(float), 0,
-                                        (ctx->ldx - ctx->n) * sizeof(float), (size_t)M, st));
+                                        (ctx->ldx - ctx->n) * sizeof(float), (size_t)items, st));
         HJG_CUDA(ctx, cudaMemset2DAsync(ctx->d_p + ctx->n, ctx->ldx * sizeof(float), 0,
-                                        (ctx->ldx - ctx->n) * sizeof(float), (size_t)M, st));
+                                        (ctx->ldx - ctx->n) * sizeof(float), (size_t)items, st));
     }
     if (ctx->dyn.game == HJG_FLOCK4)   // neighbours among the loaded agents, frozen for the solve
         HJG_CUDA(ctx, flock_neighbours(ctx->d_x, ctx->ldx, M, ctx->d_idx, nullptr, ctx->d_aux, kFlockAux, st));
-    HJG_CUDA(ctx, ctx->kern.init(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min,
+    for (int64_t h = 1; h < H; ++h) {   // the same states (and neighbour data) at every horizon
+        HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_x + h * M * ctx->ldx, ctx->d_x, (size_t)M * ctx->ldx * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st));
+        if (ctx->dyn.game == HJG_FLOCK4)
+            HJG_CUDA(ctx, cudaMemcpyAsync(ctx->d_aux + h * M * kFlockAux, ctx->d_aux,
+                                          (size_t)M * kFlockAux * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    HJG_CUDA(ctx, ctx->kern.init(ctx->d_x, ctx->ldx, items, ctx->gp, ctx->delta, ctx->eta, ctx->c_min,
                                  ctx->c_max, ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, ctx->d_ess, st,
                                  ctx->d_aux, kFlockAux));
+    return HJG_OK;
+}
+
+hjg_status hjg_set_horizons(hjg_ctx* ctx, const double* t, int n_horizons) {
+    if (!ctx || n_horizons < 0 || (n_horizons > 0 && !t)) return HJG_EINVAL;
+    for (int h = 0; h < n_horizons; ++h)
+        if (!(t[h] > 0.0) || !std::isfinite(t[h])) return fail(ctx, HJG_EINVAL, "horizon %d is not > 0", h);
+    ctx->M = 0;   // the loaded states are dropped: load them again for the new horizons
+    ctx->m_base = 0;
+    ctx->last_sweeps = 0;
+    ctx->se_valid = false;
+    ctx->horizons.assign(t, t + n_horizons);
+    if (ctx->d_tsig) { cudaFree(ctx->d_tsig); ctx->d_tsig = nullptr; }
+    if (n_horizons == 0) return HJG_OK;
+    std::vector<Sig> tab((size_t)n_horizons);
+    for (int h = 0; h < n_horizons; ++h) {
+        tab[h].sigma2_d = ctx->delta * t[h];
+        tab[h].sigma_d = std::sqrt(tab[h].sigma2_d);
+        tab[h].sigma = (float)tab[h].sigma_d;
+        tab[h].sk = (float)(tab[h].sigma_d * (double)kBmScale);
+    }
+    if (cudaMalloc((void**)&ctx->d_tsig, tab.size() * sizeof(Sig)) != cudaSuccess) {
+        ctx->d_tsig = nullptr;
+        ctx->horizons.clear();
+        return fail(ctx, HJG_ENOMEM, "horizon table");
+    }
+    HJG_CUDA(ctx, cudaMemcpy(ctx->d_tsig, tab.data(), tab.size() * sizeof(Sig), cudaMemcpyHostToDevice));
     return HJG_OK;
 }
 

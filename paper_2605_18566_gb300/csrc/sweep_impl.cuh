@@ -23,6 +23,12 @@
 
 namespace hjg {
 
+// Kernel width of one item: sigma = sqrt(delta t) for its horizon t.
+struct Sig {
+    double sigma_d, sigma2_d;
+    float sigma, sk;          // sk = sigma kBmScale
+};
+
 struct SweepArgs {
     const float* x;           // [M][ldx] evaluation states
     float* p;                 // [M][ldp] Dv iterate (in: p^(k), out: p^(k+K))
@@ -42,8 +48,21 @@ struct SweepArgs {
     double sigma_d, sigma2_d, delta, eta, c_min, c_max;
     const float* aux;         // [M][ldaux] per-state game data (flock neighbours), or null
     int64_t ldaux;
+    const struct Sig* tsig;   // per-horizon kernel widths (item pt uses tsig[pt / m_base]), or null
+    int64_t m_base;           //   states per horizon
     GameParams g;
 };
+
+// The kernel width of item pt: its horizon's entry of the table, else the solve's own.
+__device__ __forceinline__ Sig item_sig(const SweepArgs& A, int64_t pt) {
+    if (A.tsig) return A.tsig[pt / A.m_base];
+    Sig g;
+    g.sigma_d = A.sigma_d;
+    g.sigma2_d = A.sigma2_d;
+    g.sigma = A.sigma;
+    g.sk = A.sk;
+    return g;
+}
 
 // Threshold (base-2 units) above the running shift at which the sums are rescaled.
 // Weights stay below 2^32 and Q below N 2^64, far inside FP32 range, while the rescale
@@ -110,6 +129,7 @@ struct SweepShared {
     float yoff[NPAD];     // x + theta (FP32), the sample mean
     float tq[NPAD];       // -theta_j log2e kBmScale / sigma (tilt slope per raw normal)
     float theta[NPAD];
+    Sig sig;              // kernel width of the state's horizon
     float cneg2;          // -c log2e
     float cr;             // -cneg2 radius (0 for targets without a radius)
     float c;
@@ -131,6 +151,7 @@ __device__ __forceinline__ void load_state(SweepShared<NPAD, W, NC>& sh, const S
     }
     if (tid == 0) {
         if (A.vhist) A.vhist[pt] = A.v[pt];
+        sh.sig = item_sig(A, pt);
         sh.c = A.c[pt];
         sh.cneg2 = -sh.c * kLog2e;
         sh.cr = G::kRadius ? -sh.cneg2 * A.g.radius : 0.0f;
@@ -146,10 +167,10 @@ __device__ __forceinline__ void prepare_sweep(SweepShared<NPAD, W, NC>& sh, cons
                                               int n, int tid) {
     if (tid < NPAD) {
         float th = 0.0f;
-        if (TILT && tid < n) th = (float)(-A.sigma2_d * (double)sh.c * (double)sh.p_cur[tid]);
+        if (TILT && tid < n) th = (float)(-sh.sig.sigma2_d * (double)sh.c * (double)sh.p_cur[tid]);
         sh.theta[tid] = th;
         sh.yoff[tid] = sh.xf[tid] + th;
-        sh.tq[tid] = -th * kLog2e * kBmScale / A.sigma;
+        sh.tq[tid] = -th * kLog2e * kBmScale / sh.sig.sigma;
     }
 }
 
@@ -179,7 +200,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
             Sj = fma(sh.fw[w], (double)sh.red_S[w][tid], Sj);
         }
         Sj *= (double)kBmScale;   // the sample loop accumulates raw normals
-        const double pj = -((double)sh.theta[tid] + A.sigma_d * Sj / s) / (c * A.sigma2_d);
+        const double pj = -((double)sh.theta[tid] + sh.sig.sigma_d * Sj / s) / (c * sh.sig.sigma2_d);
         sh.pd[tid] = pj;
         sh.p_cur[tid] = (float)pj;
         if (last) A.p[pt * A.ldp + tid] = (float)pj;
@@ -201,7 +222,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
             finite = finite && isfinite(sh.pd[j]);
         }
         const double s = sh.s;
-        const double logmean = sh.mx * kLn2 - th2 / (2.0 * A.sigma2_d) + log(s / (double)A.N);
+        const double logmean = sh.mx * kLn2 - th2 / (2.0 * sh.sig.sigma2_d) + log(s / (double)A.N);
         const double v = -logmean / c;
         finite = finite && isfinite(v);
         const double h = G::ham_c(sh.x, sh.hc, sh.pd, A.g);
@@ -287,7 +308,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
 
         for (int k = 0; k < A.K; ++k) {
             const uint32_t sweep = A.k0 + (uint32_t)k;
-            const float cneg2 = sh.cneg2, cr = sh.cr;
+            const float cneg2 = sh.cneg2, cr = sh.cr, sk = sh.sig.sk;
             float yoff[n], tq[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) { yoff[j] = sh.yoff[j]; tq[j] = sh.tq[j]; }
@@ -299,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
 
             auto sample = [&](const float* zt) {
-                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g, auxr), cr);
+                float a = fmaf(cneg2, G::dist(zt, yoff, sk, A.g, auxr), cr);
                 if (TILT) {
 #pragma unroll
                     for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
@@ -335,8 +356,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
 // v, Dv, ESS from the merged sums, the coefficient update, and the outputs.  Updates
 // p (FP32 Dv iterate) in place and returns the new FP32 coefficient.
 template <class G, bool TILT>
-__device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k, float c, float m,
-                                           float s, float q, const double* xd, float* p,
+__device__ __noinline__ float warp_recover(const SweepArgs& A, const Sig& sig, int64_t pt, int k, float c,
+                                           float m, float s, float q, const double* xd, float* p,
                                            const float* S, double* pd, const float* aux) {
     constexpr int n = G::kN;
     const bool last = (k + 1 == A.K);
@@ -345,14 +366,14 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, int64_t pt, int k
     double th2 = 0.0, pp = 0.0;
     bool finite = true;
     for (int j = 0; j < n; ++j) {
-        const double th = TILT ? (double)(float)(-A.sigma2_d * cd * (double)p[j]) : 0.0;
+        const double th = TILT ? (double)(float)(-sig.sigma2_d * cd * (double)p[j]) : 0.0;
         th2 += th * th;
-        const double pj = -(th + A.sigma_d * (double)kBmScale * (double)S[j] / sd) / (cd * A.sigma2_d);
+        const double pj = -(th + sig.sigma_d * (double)kBmScale * (double)S[j] / sd) / (cd * sig.sigma2_d);
         pd[j] = pj;
         pp += pj * pj;
         finite = finite && isfinite(pj);
     }
-    const double v = -((double)m * kLn2 - th2 / (2.0 * A.sigma2_d) + log(sd / (double)A.N)) / cd;
+    const double v = -((double)m * kLn2 - th2 / (2.0 * sig.sigma2_d) + log(sd / (double)A.N)) / cd;
     finite = finite && isfinite(v);
     int clipped = 0;
     const float c_new = (float)coef_update(G::ham_d(xd, pd, A.g, aux), pp, A.delta, A.eta, A.c_min,
@@ -406,6 +427,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
         if (G::kAux > 0 && lane < G::kAux) s_aux[wl][lane] = A.aux[pt * A.ldaux + lane];
         if (lane == 0 && A.vhist) A.vhist[pt] = A.v[pt];
         float c = A.c[pt];
+        const Sig sig = item_sig(A, pt);
+        const float sk = sig.sk;
         __syncwarp();
 
         for (int k = 0; k < A.K; ++k) {
@@ -415,9 +438,9 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
             float yoff[n], tq[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) {
-                const float th = TILT ? (float)(-A.sigma2_d * (double)c * (double)s_p[wl][j]) : 0.0f;
+                const float th = TILT ? (float)(-sig.sigma2_d * (double)c * (double)s_p[wl][j]) : 0.0f;
                 yoff[j] = s_x[wl][j] + th;
-                tq[j] = -th * kLog2e * kBmScale / A.sigma;
+                tq[j] = -th * kLog2e * kBmScale / sig.sigma;
             }
             float auxr[KA];
 #pragma unroll
@@ -426,7 +449,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
 #pragma unroll
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
             auto sample = [&](const float* zt) {
-                float a = fmaf(cneg2, G::dist(zt, yoff, A.sk, A.g, auxr), cr);
+                float a = fmaf(cneg2, G::dist(zt, yoff, sk, A.g, auxr), cr);
                 if (TILT) {
 #pragma unroll
                     for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
@@ -451,8 +474,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
             if (lane == 0) {
 #pragma unroll
                 for (int j = 0; j < n; ++j) s_S[wl][j] = S[j];
-                c_new = warp_recover<G, TILT>(A, pt, k, c, m, s, q, s_xd[wl], s_p[wl], s_S[wl], s_pd[wl],
-                                              s_aux[wl]);
+                c_new = warp_recover<G, TILT>(A, sig, pt, k, c, m, s, q, s_xd[wl], s_p[wl], s_S[wl],
+                                              s_pd[wl], s_aux[wl]);
             }
             c = __shfl_sync(0xffffffffu, c_new, 0);
             __syncwarp();
@@ -492,7 +515,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
 
         for (int k = 0; k < A.K; ++k) {
             const uint32_t sweep = A.k0 + (uint32_t)k;
-            const float cneg2 = sh.cneg2, cr = sh.cr;
+            const float cneg2 = sh.cneg2, cr = sh.cr, sk = sh.sig.sk;
             float yoff[12], tq[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) { yoff[j] = sh.yoff[12 * q4 + j]; tq[j] = sh.tq[12 * q4 + j]; }
@@ -508,8 +531,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
                 float yx[4], yz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    yx[a] = fmaf(A.sk, z[3 * a], yoff[3 * a]);
-                    yz[a] = fmaf(A.sk, z[3 * a + 1], yoff[3 * a + 1]);
+                    yx[a] = fmaf(sk, z[3 * a], yoff[3 * a]);
+                    yz[a] = fmaf(sk, z[3 * a + 1], yoff[3 * a + 1]);
                 }
                 const float ex = __shfl_sync(0xffffffffu, yx[2], src3);
                 const float ez = __shfl_sync(0xffffffffu, yz[2], src3);

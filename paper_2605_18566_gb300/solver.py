@@ -96,11 +96,20 @@ class Solver:
         return C.c_void_p(t.data_ptr()) if t is not None else None
 
     # ------------------------------------------------------------------ API
+    def set_horizons(self, times):
+        """Solve at several horizons t_h at once; afterwards every per-state array has
+        len(times) * M rows (horizon-major).  An empty list returns to the single T."""
+        t = np.ascontiguousarray(np.asarray(times, dtype=np.float64).ravel())
+        _check(self.lib, self.ctx, self.lib.hjg_set_horizons(
+            self.ctx, t.ctypes.data_as(C.c_void_p) if t.size else None, int(t.size)))
+        self.n_horizons = max(1, int(t.size))
+        self.M = 0
+
     def set_points(self, x: torch.Tensor):
         """x: [M, ld] float32 (ld >= n), on the GPU or in host memory."""
         assert x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1
         on_dev = 1 if x.is_cuda else 0
-        self.M = x.shape[0]
+        self.M = x.shape[0] * getattr(self, "n_horizons", 1)
         _check(self.lib, self.ctx, self.lib.hjg_set_points(
             self.ctx, self._ptr(x), x.shape[0], x.stride(0), on_dev, None))
 
@@ -168,7 +177,7 @@ class Solver:
         """Algorithm 1 end to end: set points, run K sweeps (or stop at eps), copy out.
         Host tensors in -> host tensors out (copies inside the call); device -> device."""
         assert x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1
-        M = x.shape[0]
+        M = x.shape[0] * getattr(self, "n_horizons", 1)   # rows of the outputs
         dev = x.is_cuda
         kw = dict(device=x.device) if dev else dict(pin_memory=False)
         if v_out is None:
@@ -178,7 +187,7 @@ class Solver:
         K = self.opt.K
         r = np.full(max(K, 1), np.nan)
         self.M = M
-        st = self.lib.hjg_value_grad(self.ctx, self._ptr(x), M, x.stride(0), 1 if dev else 0,
+        st = self.lib.hjg_value_grad(self.ctx, self._ptr(x), x.shape[0], x.stride(0), 1 if dev else 0,
                                      self._ptr(v_out), self._ptr(grad_out), grad_out.stride(0),
                                      r.ctypes.data_as(C.c_void_p), None)
         if st not in (_lib.HJG_OK, _lib.HJG_ENONFINITE):
