@@ -266,6 +266,29 @@ hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t 
 hjg_status hjg_flock_neighbours(const float *states, int64_t M, int64_t ld, int k, int32_t *idx_out,
                                 float *psibar_out, void *stream);
 
+/* Event flags of hjg_topology (the threshold rules of the murmuration study's phase-
+ * transition markers, recorded at the later of two consecutive slices). */
+enum {
+    HJG_EVENT_VACUOLE = 1,        /* chi dropped: chi_h - chi_{h-1} < -0.5 */
+    HJG_EVENT_CORDON = 2,         /* beta_1 >= 1 and beta_1 was 0 at the previous slice */
+    HJG_EVENT_FRAGMENTATION = 4   /* n_comp grew */
+};
+
+/* Topology of the zero sublevel set {v <= 0} on H 2-D value slices (Appendix D, phase-
+ * transition markers): v [H][m][m] FP64 on the device (e.g. a grid of states solved at H
+ * horizons).  Each slice is first smoothed by a separable Gaussian of smooth_cells grid
+ * cells (weights exp(-k^2/(2 s^2)), |k| <= int(4 s + 0.5), normalised, half-sample-symmetric
+ * reflection at the border; 0 skips it; the radius must stay below m), then its set cells
+ * (4-connected) and complement cells (8-connected) are labelled.  markers_out [H][3] int32
+ * (host) = (n_comp, beta_1 = complement components not touching the border, chi = n_comp -
+ * beta_1); events_out [H] int32 (host, or NULL) = HJG_EVENT_* flags against the previous
+ * slice (0 for the first); smoothed_out [H][m][m] FP64 and labels_out [H][m][m] int32 (root
+ * cell index of each cell's component; host or device, or NULL).  Temporaries are stream-
+ * ordered allocations; synchronises the stream.  EINVAL for bad sizes, ETIMEOUT if a
+ * union-find walk hit its iteration bound. */
+hjg_status hjg_topology(const double *v, int H, int m, double smooth_cells, double *smoothed_out,
+                        int32_t *markers_out, int32_t *events_out, int32_t *labels_out, void *stream);
+
 /* ---- surrogate network (BF16 tensor cores, trained on the sweep's own tuples) ---- */
 
 /* An MLP n_in -> width -> width -> width -> n_out with SiLU activations (the surrogate of

@@ -369,6 +369,26 @@ def flock_neighbours(states: torch.Tensor, k: int = 7):
     return idx, psibar
 
 
+def topology(v: torch.Tensor, smooth_cells: float = 1.5):
+    """Topology markers of {v <= 0} on slices v [H, m, m] (FP64, device): returns
+    (markers int32 [H, 3] = (n_comp, beta_1, chi), events int32 [H] (HJG_EVENT_* bits),
+    smoothed field [H, m, m], component labels [H, m, m]) -- hjg_topology."""
+    lib = _lib.load()
+    assert v.dtype == torch.float64 and v.dim() == 3 and v.shape[1] == v.shape[2] and v.is_cuda
+    v = v.contiguous()
+    H, m = v.shape[0], v.shape[1]
+    markers = np.zeros((H, 3), dtype=np.int32)
+    events = np.zeros(H, dtype=np.int32)
+    sm = torch.empty_like(v)
+    lab = torch.empty(H, m, m, dtype=torch.int32, device=v.device)
+    st = lib.hjg_topology(C.c_void_p(v.data_ptr()), H, m, smooth_cells, C.c_void_p(sm.data_ptr()),
+                          markers.ctypes.data_as(C.c_void_p), events.ctypes.data_as(C.c_void_p),
+                          C.c_void_p(lab.data_ptr()), _stream_handle(None))
+    if st:
+        raise HJGError(st, "hjg_topology")
+    return markers, events, sm, lab
+
+
 def philox_blocks(ctr: torch.Tensor, key: torch.Tensor) -> torch.Tensor:
     """Device Philox4x32-10: ctr int32/uint32 [K,4], key [K,2] (CUDA tensors)."""
     lib = _lib.load()
