@@ -53,7 +53,16 @@ DUBINS3 = Workload("dubins3_grid16", "dubins3", 3, 0.1, 1.0, 4096, 4096, 10, 0.5
 ROCKETS6 = Workload("rockets6_uniform", "rockets6", 6, 0.05, 2.0, 65536, 65536, 20, 0.3)
 ROCKETS45 = Workload("rockets45_gauss", "rockets45", 45, 0.05, 2.0, 262144, 131072, 30, 0.3)
 FLOCK = Workload("flock_murmuration", "flock4", 4, 0.02, 1.0, 100000, 16384, 15, 0.2)
-WORKLOADS = {w.name: w for w in (DUBINS3, ROCKETS6, ROCKETS45, FLOCK)}
+# The two further games of the appendix: the relative two-rocket game on a 25^3 grid over
+# (x, z) in [-100, 100]^2, theta in [-pi/2, pi/2] (a = 64, g = 32 ft/s^2, capture radius 1.5,
+# delta = 0.08, N = 14,000, 12 sweeps), and the double integrator on a 64^2 grid over
+# [-2, 2]^2 (target disc of radius 0.25 about the origin, delta = 0.08, N = 8,000, 15 sweeps,
+# horizons 0.2, 0.5, 0.8).
+ROCKETS_REL3 = Workload("rockets_rel3_grid25", "rockets_rel3", 3, 0.04, 1.0, 15625, 14000, 12, 1.5,
+                        speed=(64.0, 32.0))
+DOUBLE_INT2 = Workload("double_int2_grid64", "double_int2", 2, 0.04, 0.8, 4096, 8000, 15, 0.25)
+DOUBLE_INT2_HORIZONS = (0.2, 0.5, 0.8)
+WORKLOADS = {w.name: w for w in (DUBINS3, ROCKETS6, ROCKETS45, FLOCK, ROCKETS_REL3, DOUBLE_INT2)}
 
 # The mixed batch that runs alongside the flock: (workload, states) per instance, all at
 # nu = 0.02, T = 1, N = 16,384, 15 sweeps.
@@ -107,11 +116,25 @@ def flock_states(M: int, seed: int = 0, clusters: int = 6, ring: float = 40.0,
     return np.concatenate([pos, psi[:, None]], axis=1).astype(np.float32)
 
 
+def box_grid(lo, hi, m_side: int) -> np.ndarray:
+    """m_side points per axis on the box [lo, hi] (numpy linspace, endpoints included),
+    row-major over the axes (last axis fastest)."""
+    axes = [np.linspace(a, b, m_side) for a, b in zip(lo, hi)]
+    g = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, len(axes))
+    return g.astype(np.float32)
+
+
 def points(w: Workload, M: int | None = None, seed: int | None = None) -> np.ndarray:
     """Evaluation states of workload ``w`` (first M of them when M is given)."""
     seed = w.seed if seed is None else seed
     if w.game == "dubins3":
         x = dubins_grid(16)
+        return x if M is None else x[:M].copy()
+    if w.game == "rockets_rel3":
+        x = box_grid((-100.0, -100.0, -0.5 * math.pi), (100.0, 100.0, 0.5 * math.pi), 25)
+        return x if M is None else x[:M].copy()
+    if w.game == "double_int2":
+        x = box_grid((-2.0, -2.0), (2.0, 2.0), 64)
         return x if M is None else x[:M].copy()
     M = w.M if M is None else M
     if w.game == "rockets6":

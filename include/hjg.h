@@ -70,6 +70,13 @@ typedef enum {
                            radius.  The loaded states are the agents themselves: hjg_set_points
                            finds each one's neighbours and their circular mean heading psibar
                            and holds them frozen for the solve.  n = 4, M >= 8. */
+    HJG_ROCKETS_REL3 = 5, /* Appendix D: two rockets in relative coordinates (x, z, theta),
+                           Eq. ham_def: f = (a cos th + u_e x, a sin th + a - g + u_p x,
+                           u_p - u_e), H = -max_{u_e} min_{u_p} <p, f>, a = speed[0], g =
+                           speed[1]; l = |(x, z)| - radius.  n = 3. */
+    HJG_DOUBLE_INT2 = 6,  /* Appendix D: double integrator x1' = x2, x2' = u, |u| <= 1, the
+                           control minimises (Eq. dint_ham): H = p1 x2 - |p2|;
+                           l = |(x1, x2)| - radius.  n = 2. */
     HJG_TEST_QUADRATIC = 100, /* H = h_sign |p|^2 / 2, l = (y-x0)^T A (y-x0)/2 + d; n <= 8 */
     HJG_TEST_ZERO_H = 101     /* H = 0 (pure heat equation), same quadratic l; n <= 8 */
 } hjg_game;

@@ -28,8 +28,8 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-GAMES = {"dubins3": 1, "rockets6": 2, "rockets45": 3, "flock4": 4,
-         "quadratic": 100, "zero_h": 101}
+GAMES = {"dubins3": 1, "rockets6": 2, "rockets45": 3, "flock4": 4, "rockets_rel3": 5,
+         "double_int2": 6, "quadratic": 100, "zero_h": 101}
 
 
 class Problem(C.Structure):

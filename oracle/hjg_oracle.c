@@ -44,6 +44,8 @@ enum {
     ORC_ROCKETS6 = 2,
     ORC_ROCKETS45 = 3,
     ORC_FLOCK4 = 4,
+    ORC_ROCKETS_REL3 = 5,
+    ORC_DOUBLE_INT2 = 6,
     ORC_TEST_QUADRATIC = 100,
     ORC_TEST_ZERO_H = 101
 };
@@ -186,6 +188,8 @@ double orc_ell(const orc_problem *P, const double *y, const double *nbr)
 {
     switch (P->game) {
     case ORC_DUBINS3:
+    case ORC_ROCKETS_REL3:   /* capture disc in the relative (x, z) plane */
+    case ORC_DOUBLE_INT2:    /* disc about the origin of the (position, velocity) plane */
         return sqrt(y[0] * y[0] + y[1] * y[1]) - P->radius;
     case ORC_ROCKETS6: {
         double dx = y[0] - y[2], dz = y[1] - y[3];
@@ -223,7 +227,9 @@ void orc_grad_ell(const orc_problem *P, const double *x, const double *nbr, doub
     int n = P->n;
     for (int a = 0; a < n; ++a) g[a] = 0.0;
     switch (P->game) {
-    case ORC_DUBINS3: {
+    case ORC_DUBINS3:
+    case ORC_ROCKETS_REL3:
+    case ORC_DOUBLE_INT2: {
         double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
         if (rho > 0) { g[0] = x[0] / rho; g[1] = x[1] / rho; }
         break;
@@ -304,6 +310,17 @@ double orc_hamiltonian(const orc_problem *P, const double *x, const double *p, d
            the bird controls u_z (max), the attack disturbance d (min) */
         return P->speed[0] * (p[0] * cos(x[3]) + p[1] * sin(x[3])) + fabs(p[2])
              + p[3] * wrap_angle(psibar - x[3]) - fabs(p[3]);
+    case ORC_ROCKETS_REL3: {
+        /* relative rockets (x, z, theta), Eq. ham_def: f = (a cos th + u_e x,
+           a sin th + a - g + u_p x, u_p - u_e), H = -max_{u_e} min_{u_p} <p, f> with
+           a = speed[0], g = speed[1], |u_e|, |u_p| <= 1 */
+        double a = P->speed[0], g = P->speed[1];
+        return -(a * p[0] * cos(x[2]) + p[1] * (a * sin(x[2]) + a - g)
+                 + fabs(p[0] * x[0] - p[2]) - fabs(p[1] * x[0] + p[2]));
+    }
+    case ORC_DOUBLE_INT2:
+        /* x1' = x2, x2' = u, |u| <= 1, the control minimises (Eq. dint_ham) */
+        return p[0] * x[1] - fabs(p[1]);
     case ORC_TEST_QUADRATIC: {
         double s = 0.0;
         for (int a = 0; a < P->n; ++a) s += p[a] * p[a];

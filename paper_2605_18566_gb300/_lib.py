@@ -12,9 +12,10 @@ LIB_PATH = os.path.join(HERE, "libhjg.so")
 HJG_OK, HJG_EINVAL, HJG_ENOMEM, HJG_ECUDA, HJG_ENONFINITE, HJG_ETIMEOUT, \
     HJG_ENOTCONVERGED, HJG_EUNSUPPORTED = range(8)
 
-GAMES = {"dubins3": 1, "rockets6": 2, "rockets45": 3, "flock4": 4,
-         "quadratic": 100, "zero_h": 101}
-GAME_DIMS = {"dubins3": 3, "rockets6": 6, "rockets45": 45, "flock4": 4}
+GAMES = {"dubins3": 1, "rockets6": 2, "rockets45": 3, "flock4": 4, "rockets_rel3": 5,
+         "double_int2": 6, "quadratic": 100, "zero_h": 101}
+GAME_DIMS = {"dubins3": 3, "rockets6": 6, "rockets45": 45, "flock4": 4, "rockets_rel3": 3,
+             "double_int2": 2}
 
 
 class Dynamics(C.Structure):

@@ -29,6 +29,8 @@ GameKernels kernels_dubins3();
 GameKernels kernels_rockets6();
 GameKernels kernels_rockets45();
 GameKernels kernels_flock4();
+GameKernels kernels_rockets_rel3();
+GameKernels kernels_double_int2();
 bool kernels_quadratic(int n, bool zero_h, GameKernels* out);
 
 // Flock neighbour structure (flock.cu): 7 nearest agents, their mean heading, and the

@@ -27,7 +27,7 @@ struct GameParams {
 };
 
 enum GameId : int32_t {
-    kDubins3 = 1, kRockets6 = 2, kRockets45 = 3, kFlock4 = 4,
+    kDubins3 = 1, kRockets6 = 2, kRockets45 = 3, kFlock4 = 4, kRocketsRel3 = 5, kDoubleInt2 = 6,
     kTestQuadratic = 100, kTestZeroH = 101
 };
 
@@ -67,6 +67,72 @@ struct Dubins3 {
     __device__ static double cache(const double* x, int j, const float* = nullptr) { return j == 0 ? cos(x[2]) : sin(x[2]); }
     __device__ static double ham_c(const double* x, const double* hc, const double* p, const GameParams&) {
         return p[0] * (hc[0] - 1.0) + p[1] * hc[1] + fabs(p[0] * x[1] - p[1] * x[0] - p[2]) - fabs(p[2]);
+    }
+};
+
+// ------------------------------------------------ relative rockets (App. D, Eq. ham_def)
+// (x, z, th): f = (a cos th + u_e x, a sin th + a - g + u_p x, u_p - u_e), H = -max min <p, f>
+// with a = speed[0], g = speed[1]; target: capture disc in the (x, z) plane.
+struct RocketsRel3 {
+    static constexpr int kN = 3;
+    static constexpr bool kRadius = true;
+    static constexpr int kAux = 0;
+    __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
+                                                 const GameParams&, const float* = nullptr) {
+        const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
+        return sqrtf_fast(fmaf(y0, y0, y1 * y1));
+    }
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
+        return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
+        const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        gr[0] = rho > 0 ? x[0] / rho : 0.0;
+        gr[1] = rho > 0 ? x[1] / rho : 0.0;
+        gr[2] = 0.0;
+    }
+    __device__ static double ham_h(const double* x, double c, double s, const double* p, const GameParams& g) {
+        const double a = g.speed_d[0], gr = g.speed_d[1];
+        return -(a * p[0] * c + p[1] * (a * s + a - gr) + fabs(p[0] * x[0] - p[2]) - fabs(p[1] * x[0] + p[2]));
+    }
+    __device__ static double ham_d(const double* x, const double* p, const GameParams& g, const float* = nullptr) {
+        double s, c;
+        sincos(x[2], &s, &c);
+        return ham_h(x, c, s, p, g);
+    }
+    static constexpr int kCache = 2;
+    __device__ static double cache(const double* x, int j, const float* = nullptr) { return j == 0 ? cos(x[2]) : sin(x[2]); }
+    __device__ static double ham_c(const double* x, const double* hc, const double* p, const GameParams& g) {
+        return ham_h(x, hc[0], hc[1], p, g);
+    }
+};
+
+// ------------------------------------------------ double integrator (App. D, Eq. dint_ham)
+// x1' = x2, x2' = u, |u| <= 1, u minimises: H = p1 x2 - |p2|; target: disc about the origin.
+struct DoubleInt2 {
+    static constexpr int kN = 2;
+    static constexpr bool kRadius = true;
+    static constexpr int kAux = 0;
+    __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
+                                                 const GameParams&, const float* = nullptr) {
+        const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
+        return sqrtf_fast(fmaf(y0, y0, y1 * y1));
+    }
+    __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
+        return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+    }
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
+        const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        gr[0] = rho > 0 ? x[0] / rho : 0.0;
+        gr[1] = rho > 0 ? x[1] / rho : 0.0;
+    }
+    __device__ static double ham_d(const double* x, const double* p, const GameParams&, const float* = nullptr) {
+        return p[0] * x[1] - fabs(p[1]);
+    }
+    static constexpr int kCache = 0;
+    __device__ static double cache(const double*, int, const float* = nullptr) { return 0.0; }
+    __device__ static double ham_c(const double* x, const double*, const double* p, const GameParams&) {
+        return p[0] * x[1] - fabs(p[1]);
     }
 };
 

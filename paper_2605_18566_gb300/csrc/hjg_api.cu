@@ -367,6 +367,8 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
         if (!kernels_quadratic(dyn->n, dyn->game == HJG_TEST_ZERO_H, &ctx->kern)) st = HJG_EUNSUPPORTED;
         break;
     case HJG_FLOCK4: ctx->kern = kernels_flock4(); break;
+    case HJG_ROCKETS_REL3: ctx->kern = kernels_rockets_rel3(); break;
+    case HJG_DOUBLE_INT2: ctx->kern = kernels_double_int2(); break;
     default: st = HJG_EINVAL;
     }
     if (st == HJG_OK && ctx->kern.n != dyn->n) st = HJG_EINVAL;

@@ -83,6 +83,8 @@ bool pick_kernels(const hjg_dynamics* dyn, GameKernels* k) {
     case HJG_DUBINS3: *k = kernels_dubins3(); break;
     case HJG_ROCKETS6: *k = kernels_rockets6(); break;
     case HJG_ROCKETS45: *k = kernels_rockets45(); break;
+    case HJG_ROCKETS_REL3: *k = kernels_rockets_rel3(); break;
+    case HJG_DOUBLE_INT2: *k = kernels_double_int2(); break;
     case HJG_TEST_QUADRATIC:
     case HJG_TEST_ZERO_H:
         if (!kernels_quadratic(dyn->n, dyn->game == HJG_TEST_ZERO_H, k)) return false;

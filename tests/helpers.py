@@ -26,11 +26,15 @@ def assert_parity(v_gpu, p_gpu, v_ref, p_ref, frac=1.0, what=""):
 
 
 def problem_for(w, **kw):
+    if w.speed:
+        kw.setdefault("speed", list(w.speed))
     return oracle.make_problem(w.game, w.n, w.delta, w.T, radius=w.radius, **kw)
 
 
 def solver_for(w, N=None, K=None, **kw):
     from paper_2605_18566_gb300 import Solver
+    if w.speed:
+        kw.setdefault("speed", list(w.speed))
     return Solver(w.game, w.nu, w.T, N or w.N, K if K is not None else w.K, radius=w.radius, **kw)
 
 

@@ -220,3 +220,40 @@ def test_flock_workload_shape():
     dnn = np.linalg.norm(x[:, :3] - x[idx[:, 0], :3], axis=1)
     assert 0.1 < np.median(dnn) < 0.6        # 20k of the 100k birds: sparser than full size
     assert np.all(np.abs(x[:, 3]) <= np.pi)
+
+
+def test_relative_rockets_hamiltonian_brute_force():
+    """Eq. ham_def with the vector field as printed there: H = -max_{u_e} min_{u_p} <p, f>."""
+    a, g = 64.0, 32.0
+    P = oracle.make_problem("rockets_rel3", 3, 0.08, 1.0, radius=1.5, speed=[a, g])
+
+    def f(x, ue, up):
+        return np.array([a * math.cos(x[2]) + ue * x[0], a * math.sin(x[2]) + a + up * x[0] - g, up - ue])
+
+    r = np.random.default_rng(7)
+    for _ in range(25):
+        x = r.normal(size=3) * np.array([5, 5, 1])
+        p = r.normal(size=3)
+        brute = -max(min(float(p @ f(x, ue, up)) for up in GRID) for ue in GRID)
+        assert abs(oracle.hamiltonian(P, x, p) - brute) < 1e-9 * (1 + abs(brute))
+
+
+def test_double_integrator_hamiltonian_brute_force():
+    """Eq. dint_ham with the minimising control: H = min_u (p1 x2 + p2 u)."""
+    P = oracle.make_problem("double_int2", 2, 0.08, 0.8, radius=0.25)
+    r = np.random.default_rng(8)
+    for _ in range(25):
+        x = r.normal(size=2) * 2
+        p = r.normal(size=2)
+        brute = min(p[0] * x[1] + p[1] * u for u in GRID)
+        assert abs(oracle.hamiltonian(P, x, p) - brute) < 1e-12
+
+
+@pytest.mark.parametrize("game,n", [("rockets_rel3", 3), ("double_int2", 2)])
+def test_extra_game_targets(game, n):
+    P = oracle.make_problem(game, n, 0.08, 1.0, radius=1.5)
+    r = np.random.default_rng(9)
+    for _ in range(10):
+        x = r.normal(size=n) * 3
+        assert abs(oracle.ell(P, x) - (math.hypot(x[0], x[1]) - 1.5)) < 1e-12
+        np.testing.assert_allclose(oracle.grad_ell(P, x), fd_grad(lambda y: oracle.ell(P, y), x), atol=1e-6)
