@@ -41,7 +41,7 @@ class Problem(C.Structure):
         ("speed", C.c_double * 16), ("h_sign", C.c_double),
         ("A", C.c_double * 64), ("x0", C.c_double * 8), ("d", C.c_double),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("tilt", C.c_int32),
-        ("flock_k", C.c_int32), ("tube", C.c_int32),
+        ("flock_k", C.c_int32), ("tube", C.c_int32), ("cv", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -78,7 +78,7 @@ def lib():
         L.orc_coef.argtypes = [P(Problem), pd, pd, d]; L.orc_coef.restype = d
         L.orc_coef_batch.argtypes = [P(Problem), i64, pd, pd, pd, pd]
         pi64 = P(C.c_int64)
-        L.orc_sweep.argtypes = [P(Problem), i64, pd, pd, pd, pd, pi64, i64, u32, pd, pd, pd]
+        L.orc_sweep.argtypes = [P(Problem), i64, pd, pd, pd, pd, pi64, i64, u32, pd, pd, pd, pd, pd]
         L.orc_sweep.restype = i32
         L.orc_init.argtypes = [P(Problem), i64, pd, pd, pd, pd, pd, pd]
         L.orc_residual.argtypes = [i64, pd, pd, pd, pd]
@@ -110,7 +110,7 @@ def _f64(a, shape=None):
 
 def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=None,
                  c_max=None, radius=0.5, speed=None, h_sign=1.0, A=None, x0=None,
-                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7, tube=False) -> Problem:
+                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7, tube=False, cv=False) -> Problem:
     """Build an oracle problem.  Defaults follow the readings used throughout:
     eta = 1e-6, c_min = 1e-2/delta, c_max = 1e2/delta.  tube=True selects the tube form
     (Eq. HJ-RCBRT-Visc): the coefficient map uses min{0, H}."""
@@ -140,6 +140,7 @@ def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=N
     P.tilt = 1 if tilt else 0
     P.flock_k = flock_k
     P.tube = 1 if tube else 0
+    P.cv = 1 if cv else 0
     return P
 
 
@@ -213,18 +214,21 @@ def init(P, x, nbr=None, psibar=None):
     return v0, p0, c0
 
 
-def sweep(P, x, c, N, sweep_index, theta=None, nbr=None, idx=None):
+def sweep(P, x, c, N, sweep_index, theta=None, nbr=None, idx=None, cv_v=None, cv_p=None):
     """One frozen-coefficient heat-kernel solve Phi(c) at states x: (v, p, ess).
-    idx: global state indices of the rows (default 0..M-1)."""
+    idx: global state indices of the rows (default 0..M-1).  With P.cv, (cv_v, cv_p) is the
+    control variate's guess of the value and gradient (the iterate entering the sweep)."""
     x = _f64(x).reshape(-1, P.n)
     M = x.shape[0]
     c = _f64(c).reshape(M)
     th = _f64(theta).reshape(M, P.n) if theta is not None else None
     nb = _f64(nbr) if nbr is not None else None
+    cvv = _f64(cv_v).reshape(M) if cv_v is not None else None
+    cvp = _f64(cv_p).reshape(M, P.n) if cv_p is not None else None
     v = np.zeros(M); p = np.zeros((M, P.n)); ess = np.zeros(M)
     ia, ip = _idx(idx)
     rc = lib().orc_sweep(C.byref(P), M, _dp(x), _dp(c), _dp(th), _dp(nb), ip, int(N),
-                         int(sweep_index), _dp(v), _dp(p), _dp(ess))
+                         int(sweep_index), _dp(cvv), _dp(cvp), _dp(v), _dp(p), _dp(ess))
     if rc:
         raise RuntimeError("orc_sweep failed (%d)" % rc)
     return v, p, ess

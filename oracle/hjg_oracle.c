@@ -71,6 +71,8 @@ typedef struct {
     int32_t tilt;       /* 1: tilted proposal theta = -sigma^2 c p (Eq. tilt_shift) */
     int32_t flock_k;    /* flock: neighbours per agent */
     int32_t tube;       /* 1: tube form, Gamma built from min{0, H} (Eq. HJ-RCBRT-Visc) */
+    int32_t cv;         /* 1: Stein control variate around the current iterate (see solve_point) */
+    int32_t pad_;
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -356,9 +358,22 @@ double orc_coef(const orc_problem *P, const double *x, const double *p, double p
  *   Dv = (x - sum_i y_i w_i / sum_i w_i) / (t delta c)     (Cor. B.5 / B.6)
  *   ESS = (sum w)^2 / sum w^2                              (Section 2.4)
  * Two passes: the first finds max lw (log-sum-exp shift), the second regenerates
- * the same samples and accumulates. */
+ * the same samples and accumulates.
+ *
+ * Control variate (cv_g != NULL): zero-mean Stein polynomials of the normals with
+ * coefficients from a guess (v_hat, g_hat) of the value and gradient at x (the current
+ * iterate, or a surrogate's prediction after a warm start).  To first order the weight is
+ * w ~ mu (1 + b.z) with mu = exp(-c v_hat) and b = -c sigma g_hat - theta / sigma; b is 0
+ * in the tilted frame (theta = -sigma^2 c g_hat removes the linear term), so there b = 0.
+ * The sums become
+ *   sum w        -> sum w - mu b.(sum z)
+ *   sum w z      -> sum w z - mu (sum z + sum z (z.b) - N b)
+ * (E z = 0, E (z z^T - I) = 0: both corrections have mean zero for any fixed mu, b).  If the
+ * corrected weight sum is not positive the uncorrected sums are kept.  ESS stays that of
+ * the raw weights. */
 static void solve_point(const orc_problem *P, const double *x, double c, const double *theta,
                         const double *nbr, int64_t N, uint32_t point, uint32_t sweep,
+                        const double *cv_g, double cv_v,
                         double *lw, double *v_out, double *p_out, double *ess_out)
 {
     int n = P->n;
@@ -379,27 +394,47 @@ static void solve_point(const orc_problem *P, const double *x, double c, const d
         lw[i] = -c * orc_ell(P, y, nbr) + (th2 - 2.0 * dot) / (2.0 * sigma2);
         if (lw[i] > mx) mx = lw[i];
     }
-    double sw = 0.0, sw2 = 0.0, swy[ORC_MAXN];
-    for (int a = 0; a < n; ++a) swy[a] = 0.0;
+    double b[ORC_MAXN];
+    for (int a = 0; a < n; ++a) b[a] = (cv_g && !P->tilt) ? -c * sigma * cv_g[a] : 0.0;
+    double sw = 0.0, sw2 = 0.0, swz[ORC_MAXN], z1[ORC_MAXN], z2[ORC_MAXN];
+    for (int a = 0; a < n; ++a) { swz[a] = 0.0; z1[a] = 0.0; z2[a] = 0.0; }
     for (int64_t i = 0; i < N; ++i) {
         orc_normals(n, P->seed, P->instance, (uint32_t)i, point, sweep, z);
         double w = exp(lw[i] - mx);
         sw += w;
         sw2 += w * w;
-        for (int a = 0; a < n; ++a) swy[a] += w * (x[a] + theta[a] + sigma * z[a]);
+        double zb = 0.0;
+        for (int a = 0; a < n; ++a) zb += z[a] * b[a];
+        for (int a = 0; a < n; ++a) {
+            swz[a] += w * z[a];
+            z1[a] += z[a];
+            z2[a] += z[a] * zb;
+        }
     }
-    *v_out = -(mx + log(sw / (double)N)) / c;
-    for (int a = 0; a < n; ++a) p_out[a] = (x[a] - swy[a] / sw) / (P->T * P->delta * c);
+    double s = sw, S[ORC_MAXN];
+    for (int a = 0; a < n; ++a) S[a] = swz[a];
+    if (cv_g) {
+        double mu = exp(-c * cv_v - mx);   /* in the units of the shifted weights */
+        double bz = 0.0;
+        for (int a = 0; a < n; ++a) bz += b[a] * z1[a];
+        double s_cv = sw - mu * bz;
+        if (s_cv > 0.0 && isfinite(s_cv)) {
+            s = s_cv;
+            for (int a = 0; a < n; ++a) S[a] = swz[a] - mu * (z1[a] + z2[a] - (double)N * b[a]);
+        }
+    }
+    *v_out = -(mx + log(s / (double)N)) / c;
+    for (int a = 0; a < n; ++a) {
+        double ysum = (x[a] + theta[a]) * s + sigma * S[a];   /* sum_i y_i w_i */
+        p_out[a] = (x[a] - ysum / s) / (P->T * P->delta * c);
+    }
     *ess_out = sw * sw / sw2;
 }
 
-/* One sweep of the heat-kernel map Phi at M states for given frozen c (and tilt theta,
- * NULL for none).  x, theta, p are [M][n] row-major; nbr/psibar only for the flock.
- * idx (NULL: 0..M-1) gives each row's global state index, which keys its samples, so a
- * subset of a large workload draws exactly the samples it draws in the full run. */
 int orc_sweep(const orc_problem *P, int64_t M, const double *x, const double *c,
               const double *theta, const double *nbr, const int64_t *idx, int64_t N,
-              uint32_t sweep, double *v, double *p, double *ess)
+              uint32_t sweep, const double *cv_v, const double *cv_p, double *v, double *p,
+              double *ess)
 {
     int n = P->n;
     if (n < 1 || n > ORC_MAXN || N < 1) return 1;
@@ -418,7 +453,9 @@ int orc_sweep(const orc_problem *P, int64_t M, const double *x, const double *c,
                 const double *th = theta ? theta + m * n : zero;
                 const double *nb = nbr ? nbr + m * 3 * P->flock_k : NULL;
                 uint32_t point = (uint32_t)(idx ? idx[m] : m);
-                solve_point(P, x + m * n, c[m], th, nb, N, point, sweep, lw,
+                const int use_cv = P->cv && cv_v && cv_p;
+                solve_point(P, x + m * n, c[m], th, nb, N, point, sweep,
+                            use_cv ? cv_p + m * n : NULL, use_cv ? cv_v[m] : 0.0, lw,
                             v + m, p + m * n, ess + m);
             }
         }
@@ -473,10 +510,14 @@ int orc_picard(const orc_problem *P, int64_t M, const double *x, const double *n
 {
     int n = P->n;
     double sigma2 = P->delta * P->T;
-    double *theta = NULL;
+    double *theta = NULL, *p_old = NULL;
     if (P->tilt) {
         theta = (double *)malloc(sizeof(double) * (size_t)(M * n));
         if (!theta) return 2;
+    }
+    if (P->cv) {   /* the control variate's gradient guess is the iterate entering the sweep */
+        p_old = (double *)malloc(sizeof(double) * (size_t)(M * n));
+        if (!p_old) { free(theta); return 2; }
     }
     for (int k = 0; k < K; ++k) {
         double *v_old = v_hist + (int64_t)k * M;
@@ -484,13 +525,15 @@ int orc_picard(const orc_problem *P, int64_t M, const double *x, const double *n
         if (theta)
             for (int64_t m = 0; m < M; ++m)
                 for (int a = 0; a < n; ++a) theta[m * n + a] = -sigma2 * c[m] * p[m * n + a];
-        int rc = orc_sweep(P, M, x, c, theta, nbr, idx, N, k0 + (uint32_t)k, v_new, p, ess);
-        if (rc) { free(theta); return rc; }
+        if (p_old) memcpy(p_old, p, sizeof(double) * (size_t)(M * n));
+        int rc = orc_sweep(P, M, x, c, theta, nbr, idx, N, k0 + (uint32_t)k, v_old, p_old, v_new, p, ess);
+        if (rc) { free(theta); free(p_old); return rc; }
         for (int64_t m = 0; m < M; ++m)
             c[m] = orc_coef(P, x + m * n, p + m * n, psibar ? psibar[m] : 0.0);
         orc_residual(M, v_old, v_new, resid + k, sup + k);
     }
     free(theta);
+    free(p_old);
     return 0;
 }
 
