@@ -116,7 +116,16 @@ typedef struct {
     int32_t tube;          /* 1: tube form v_t + min{0, H} = (delta/2) Lap v (Eq. HJ-RCBRT-Visc):
                               Gamma is built from min{0, H}, so a state that has entered the
                               target keeps a non-positive value */
-    int32_t reserved[4];
+    int32_t cv;            /* 1: Stein control variate in every sweep (surrogate-assisted sweep):
+                              zero-mean polynomials of the normals with coefficients from the
+                              iterate entering the sweep (a surrogate's prediction after
+                              hjg_warm_start): mu = exp(-c v), b = -c sigma Dv (b = 0 with
+                              tilt); sum w -= mu b.(sum z), sum w z -= mu (sum z + sum z (z.b)
+                              - N b), kept only if mu is within a factor 4 of the sample
+                              mean weight and the weight sum stays positive.  Runs its
+                              own launch configuration (256-thread CTA per state); games with
+                              n <= 8 only (EUNSUPPORTED otherwise) */
+    int32_t reserved[3];
 } hjg_options;
 
 typedef struct {

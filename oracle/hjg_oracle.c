@@ -368,9 +368,10 @@ double orc_coef(const orc_problem *P, const double *x, const double *p, double p
  * The sums become
  *   sum w        -> sum w - mu b.(sum z)
  *   sum w z      -> sum w z - mu (sum z + sum z (z.b) - N b)
- * (E z = 0, E (z z^T - I) = 0: both corrections have mean zero for any fixed mu, b).  If the
- * corrected weight sum is not positive the uncorrected sums are kept.  ESS stays that of
- * the raw weights. */
+ * (E z = 0, E (z z^T - I) = 0: both corrections have mean zero for any fixed mu, b).  The
+ * uncorrected sums are kept when the guess is poor -- mu more than a factor 4 away from the
+ * sample mean weight (sum w)/N -- or the corrected weight sum is not positive.  ESS stays
+ * that of the raw weights. */
 static void solve_point(const orc_problem *P, const double *x, double c, const double *theta,
                         const double *nbr, int64_t N, uint32_t point, uint32_t sweep,
                         const double *cv_g, double cv_v,
@@ -414,11 +415,12 @@ static void solve_point(const orc_problem *P, const double *x, double c, const d
     double s = sw, S[ORC_MAXN];
     for (int a = 0; a < n; ++a) S[a] = swz[a];
     if (cv_g) {
-        double mu = exp(-c * cv_v - mx);   /* in the units of the shifted weights */
+        double lmu = -c * cv_v - mx;       /* log mu in the units of the shifted weights */
+        double mu = exp(lmu);
         double bz = 0.0;
         for (int a = 0; a < n; ++a) bz += b[a] * z1[a];
         double s_cv = sw - mu * bz;
-        if (s_cv > 0.0 && isfinite(s_cv)) {
+        if (fabs(lmu - log(sw / (double)N)) <= log(4.0) && s_cv > 0.0 && isfinite(s_cv)) {
             s = s_cv;
             for (int a = 0; a < n; ++a) S[a] = swz[a] - mu * (z1[a] + z2[a] - (double)N * b[a]);
         }

@@ -13,6 +13,7 @@ struct GameKernels {
     int threads[16];   // CTA size of each variant
     int minb[16];      // minimum resident CTAs per SM each variant was compiled for
     int per_warp[16];  // 1: one warp per state (the grid is counted in CTAs of threads/32 warps)
+    bool has_cv;       // the control-variate kernel exists (launch slot kCvVariant)
     // Launch the fused sweep, variant v, on `grid` CTAs.
     cudaError_t (*sweep)(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st);
     // Resident CTAs per SM of variant v (0 if it cannot launch).
@@ -48,12 +49,14 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
     cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {   \
         switch (v) {                                                                       \
             HJG_SWEEP_VARIANTS(HJG_CASE_LAUNCH)                                            \
+            case kCvVariant: return launch_sweep_cv<HJG_GAME>(A, tilt, grid, st);          \
         }                                                                                  \
         return cudaErrorInvalidValue;                                                      \
     }                                                                                      \
     int occ(bool tilt, int v) {                                                            \
         switch (v) {                                                                       \
             HJG_SWEEP_VARIANTS(HJG_CASE_OCC)                                               \
+            case kCvVariant: return occupancy_cv<HJG_GAME>(tilt);                          \
         }                                                                                  \
         return 0;                                                                          \
     }                                                                                      \
@@ -63,6 +66,8 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
         k.n = GAME::kN;                                                                    \
         k.nvariants = kNumVariants;                                                        \
         HJG_SWEEP_VARIANTS(HJG_FILL)                                                       \
+        k.threads[kCvVariant] = 256; k.minb[kCvVariant] = 4; k.per_warp[kCvVariant] = 0;   \
+        k.has_cv = true;                                                                   \
         k.sweep = sweep;                                                                   \
         k.occupancy = occ;                                                                 \
         k.init = launch_init<GAME>;                                                        \

@@ -274,7 +274,10 @@ SweepArgs make_args(hjg_ctx* ctx, int K) {
 hjg_status choose_launch(hjg_ctx* ctx) {
     const bool tilt = ctx->opt.tilt != 0;
     int v = ctx->variant;
-    if (ctx->opt.variant > 0) {
+    if (ctx->opt.cv) {   // the control variate has one kernel of its own
+        if (!ctx->kern.has_cv) return fail(ctx, HJG_EUNSUPPORTED, "no control-variate kernel for this game");
+        v = kCvVariant;
+    } else if (ctx->opt.variant > 0) {
         v = ctx->opt.variant - 1;
         if (v >= ctx->kern.nvariants) return fail(ctx, HJG_EINVAL, "variant %d out of range", v);
     } else if (ctx->opt.block_threads > 0) {

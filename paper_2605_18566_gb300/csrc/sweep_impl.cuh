@@ -135,6 +135,12 @@ struct SweepShared {
     float c;
     float red_m[W], red_s[W], red_q[W];
     float red_S[W][NPAD];
+    // control variate: value guess, linear coefficient b (FP64, and times kBmScale in FP32
+    // for the raw normals), per-warp unweighted sums of z and z (z.b), combined sums
+    double v_cur, s_use, mu;
+    double bd[NPAD], Sd[NPAD], z1d[NPAD], z2d[NPAD];
+    float braw[NPAD];
+    float red_Z1[W][NPAD], red_Z2[W][NPAD];
 };
 
 // Load state pt into shared memory (threads < NPAD) and its trigonometric cache.
@@ -152,6 +158,7 @@ __device__ __forceinline__ void load_state(SweepShared<NPAD, W, NC>& sh, const S
     if (tid == 0) {
         if (A.vhist) A.vhist[pt] = A.v[pt];
         sh.sig = item_sig(A, pt);
+        sh.v_cur = A.v[pt];
         sh.c = A.c[pt];
         sh.cneg2 = -sh.c * kLog2e;
         sh.cr = G::kRadius ? -sh.cneg2 * A.g.radius : 0.0f;
@@ -171,13 +178,18 @@ __device__ __forceinline__ void prepare_sweep(SweepShared<NPAD, W, NC>& sh, cons
         sh.theta[tid] = th;
         sh.yoff[tid] = sh.xf[tid] + th;
         sh.tq[tid] = -th * kLog2e * kBmScale / sh.sig.sigma;
+        // control variate coefficient b = -c sigma Dv (0 in the tilted frame, where the
+        // tilt has removed the weight's linear term)
+        const double b = (!TILT && tid < n) ? -(double)sh.c * sh.sig.sigma_d * (double)sh.p_cur[tid] : 0.0;
+        sh.bd[tid] = b;
+        sh.braw[tid] = (float)(b * (double)kBmScale);
     }
 }
 
 // Block combine of the per-warp partials in FP64, recovery of v, Dv, ESS and the
 // coefficient update.  Must be entered by all threads right after the partials are
 // written; ends synchronised.
-template <class G, int NPAD, int W, int NC, bool TILT>
+template <class G, int NPAD, int W, int NC, bool TILT, bool CV = false>
 __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const SweepArgs& A,
                                              int64_t pt, int k, int tid) {
     constexpr int n = G::kN;
@@ -192,24 +204,77 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
     }
     __syncthreads();
     const double c = (double)sh.c;
-    if (tid < n) {
-        double s = 0.0, Sj = 0.0;
+    if constexpr (CV) {
+        // Stein control variate (see the oracle): with mu = exp(-c v_guess) in the units of
+        // the shifted weights, sum w -> sum w - mu b.(sum z) and sum w z -> sum w z - mu
+        // (sum z + sum z (z.b) - N b); the uncorrected sums are kept when mu is more than a
+        // factor 4 away from the sample mean weight or the corrected weight sum is not
+        // positive.
+        if (tid < n) {
+            double s = 0.0, Sj = 0.0, z1 = 0.0, z2 = 0.0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            s = fma(sh.fw[w], (double)sh.red_s[w], s);
-            Sj = fma(sh.fw[w], (double)sh.red_S[w][tid], Sj);
+            for (int w = 0; w < W; ++w) {
+                s = fma(sh.fw[w], (double)sh.red_s[w], s);
+                Sj = fma(sh.fw[w], (double)sh.red_S[w][tid], Sj);
+                z1 += (double)sh.red_Z1[w][tid];
+                z2 += (double)sh.red_Z2[w][tid];
+            }
+            sh.Sd[tid] = Sj * (double)kBmScale;
+            sh.z1d[tid] = z1 * (double)kBmScale;
+            sh.z2d[tid] = z2 * (double)kBmScale;
+            if (tid == 0) {
+                double q = 0.0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) q = fma(sh.fw[w] * sh.fw[w], (double)sh.red_q[w], q);
+                sh.s = s;
+                sh.q = q;
+            }
         }
-        Sj *= (double)kBmScale;   // the sample loop accumulates raw normals
-        const double pj = -((double)sh.theta[tid] + sh.sig.sigma_d * Sj / s) / (c * sh.sig.sigma2_d);
-        sh.pd[tid] = pj;
-        sh.p_cur[tid] = (float)pj;
-        if (last) A.p[pt * A.ldp + tid] = (float)pj;
+        __syncthreads();
         if (tid == 0) {
-            double q = 0.0;
+            double th2 = 0.0, bz = 0.0;
+            for (int j = 0; j < n; ++j) {
+                th2 += (double)sh.theta[j] * (double)sh.theta[j];
+                bz += sh.bd[j] * sh.z1d[j];
+            }
+            // the sampled log2-weights omit -|theta|^2 / (2 sigma^2) and are shifted by mx
+            const double l2mu = (-c * sh.v_cur + th2 / (2.0 * sh.sig.sigma2_d)) * 1.4426950408889634 - sh.mx;
+            const bool near = fabs(l2mu - log2(sh.s / (double)A.N)) <= 2.0;
+            const double mu = near ? exp2(l2mu) : 0.0;
+            const double s_cv = sh.s - mu * bz;
+            const bool use = near && s_cv > 0.0 && isfinite(s_cv);
+            sh.s_use = use ? s_cv : sh.s;
+            sh.mu = use ? mu : 0.0;
+        }
+        __syncthreads();
+        if (tid < n) {
+            const double Sj = sh.Sd[tid] - sh.mu * (sh.z1d[tid] + sh.z2d[tid] - (double)A.N * sh.bd[tid]);
+            const double pj = -((double)sh.theta[tid] + sh.sig.sigma_d * Sj / sh.s_use) / (c * sh.sig.sigma2_d);
+            sh.pd[tid] = pj;
+            sh.p_cur[tid] = (float)pj;
+            if (last) A.p[pt * A.ldp + tid] = (float)pj;
+        }
+    } else {
+        if (tid < n) {
+            double s = 0.0, Sj = 0.0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) q = fma(sh.fw[w] * sh.fw[w], (double)sh.red_q[w], q);
-            sh.s = s;
-            sh.q = q;
+            for (int w = 0; w < W; ++w) {
+                s = fma(sh.fw[w], (double)sh.red_s[w], s);
+                Sj = fma(sh.fw[w], (double)sh.red_S[w][tid], Sj);
+            }
+            Sj *= (double)kBmScale;   // the sample loop accumulates raw normals
+            const double pj = -((double)sh.theta[tid] + sh.sig.sigma_d * Sj / s) / (c * sh.sig.sigma2_d);
+            sh.pd[tid] = pj;
+            sh.p_cur[tid] = (float)pj;
+            if (last) A.p[pt * A.ldp + tid] = (float)pj;
+            if (tid == 0) {
+                double q = 0.0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) q = fma(sh.fw[w] * sh.fw[w], (double)sh.red_q[w], q);
+                sh.s = s;
+                sh.q = q;
+                sh.s_use = s;
+            }
         }
     }
     __syncthreads();
@@ -222,8 +287,9 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
             finite = finite && isfinite(sh.pd[j]);
         }
         const double s = sh.s;
-        const double logmean = sh.mx * kLn2 - th2 / (2.0 * sh.sig.sigma2_d) + log(s / (double)A.N);
+        const double logmean = sh.mx * kLn2 - th2 / (2.0 * sh.sig.sigma2_d) + log(sh.s_use / (double)A.N);
         const double v = -logmean / c;
+        sh.v_cur = v;
         finite = finite && isfinite(v);
         const double h = G::ham_c(sh.x, sh.hc, sh.pd, A.g);
         int clipped = 0;
@@ -285,7 +351,7 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
 // One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
 // g = group_samples(n) that end on a Philox block boundary (n = 3: 4 samples from 3 blocks;
 // n = 6: 2 samples from 3 blocks), so every normal drawn is used.
-template <class G, int THREADS, int MINB, bool TILT, bool PIPE>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool CV = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int NPAD = (n + 3) / 4 * 4;
@@ -318,6 +384,12 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
             float m = -INFINITY, s = 0.0f, q = 0.0f, S[n];
 #pragma unroll
             for (int j = 0; j < n; ++j) S[j] = 0.0f;
+            constexpr int NC1 = CV ? n : 1, NC2 = (CV && !TILT) ? n : 1;
+            float Z1[NC1], Z2[NC2], braw[NC2];
+#pragma unroll
+            for (int j = 0; j < NC1; ++j) Z1[j] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NC2; ++j) { Z2[j] = 0.0f; braw[j] = (CV && !TILT) ? sh.braw[j] : 0.0f; }
 
             auto sample = [&](const float* zt) {
                 float a = fmaf(cneg2, G::dist(zt, yoff, sk, A.g, auxr), cr);
@@ -326,6 +398,17 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                     for (int j = 0; j < n; ++j) a = fmaf(zt[j], tq[j], a);
                 }
                 lse_accumulate<n>(a, zt, m, s, q, S);
+                if constexpr (CV) {
+#pragma unroll
+                    for (int j = 0; j < n; ++j) Z1[j] += zt[j];
+                    if constexpr (!TILT) {
+                        float t = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < n; ++j) t = fmaf(zt[j], braw[j], t);
+#pragma unroll
+                        for (int j = 0; j < n; ++j) Z2[j] = fmaf(zt[j], t, Z2[j]);
+                    }
+                }
             };
             run_groups<GS, GB, THREADS, PIPE>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
                                               [&](const float* z) {
@@ -341,12 +424,30 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
             }
 
             warp_merge<n>(1, m, s, q, S);
+            if constexpr (CV) {   // plain sums of the unweighted polynomials
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+#pragma unroll
+                    for (int j = 0; j < NC1; ++j) Z1[j] += __shfl_xor_sync(0xffffffffu, Z1[j], off);
+                    if constexpr (!TILT) {
+#pragma unroll
+                        for (int j = 0; j < NC2; ++j) Z2[j] += __shfl_xor_sync(0xffffffffu, Z2[j], off);
+                    }
+                }
+            }
             if (lane == 0) {
                 sh.red_m[warp] = m; sh.red_s[warp] = s; sh.red_q[warp] = q;
 #pragma unroll
                 for (int j = 0; j < n; ++j) sh.red_S[warp][j] = S[j];
+                if constexpr (CV) {
+#pragma unroll
+                    for (int j = 0; j < n; ++j) {
+                        sh.red_Z1[warp][j] = Z1[j];
+                        sh.red_Z2[warp][j] = TILT ? 0.0f : Z2[j < NC2 ? j : 0];
+                    }
+                }
             }
-            finish_sweep<G, NPAD, W, G::kCache, TILT>(sh, A, pt, k, tid);
+            finish_sweep<G, NPAD, W, G::kCache, TILT, CV>(sh, A, pt, k, tid);
         }
     }
 }
@@ -644,6 +745,23 @@ cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaSt
         else sweep_kernel<G, THREADS, MINB, false, PIPE><<<grid, THREADS, 0, st>>>(A);
     }
     return cudaGetLastError();
+}
+
+// The control-variate kernel: one CTA per state, 256 threads, 4 CTAs per SM.  It is
+// launched in the slot after the ordinary variants.
+constexpr int kCvVariant = kNumVariants;
+template <class G>
+cudaError_t launch_sweep_cv(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
+    if (tilt) sweep_kernel<G, 256, 4, true, false, true><<<grid, 256, 0, st>>>(A);
+    else sweep_kernel<G, 256, 4, false, false, true><<<grid, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+template <class G>
+int occupancy_cv(bool tilt) {
+    int nb = 0;
+    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, 256, 4, true, false, true>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, 256, 4, false, false, true>, 256, 0);
+    return nb;
 }
 
 template <class G, int KIND, int THREADS, int MINB>

@@ -38,7 +38,7 @@ class Solver:
                  tilt: bool = False, eps: float = 0.0, eta: float = -1.0,
                  c_min: float = 0.0, c_max: float = 0.0, block_threads: int = 0,
                  grid_blocks: int = 0, variant: int = -1, point_offset: int = 0,
-                 tube: bool = False, stream: Optional[torch.cuda.Stream] = None):
+                 tube: bool = False, cv: bool = False, stream: Optional[torch.cuda.Stream] = None):
         self.lib = _lib.load()
         if n is None:
             n = _lib.GAME_DIMS[game]
@@ -66,6 +66,7 @@ class Solver:
         opt.variant = variant + 1 if variant >= 0 else 0
         opt.point_offset = point_offset
         opt.tube = 1 if tube else 0
+        opt.cv = 1 if cv else 0
         self.opt = opt
         ctx = C.c_void_p()
         torch.cuda.init()

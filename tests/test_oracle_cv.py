@@ -68,17 +68,22 @@ def test_zero_gradient_guess_keeps_the_value_and_fallback_is_exact():
     c = np.full(5, 1.2)
     P0, P1 = _problem(False), _problem(True)
     v0, p0, e0 = oracle.sweep(P0, x, c, 512, 0)
-    v1, p1, e1 = oracle.sweep(P1, x, c, 512, 0, cv_v=np.zeros(5), cv_p=np.zeros((5, n)))
+    # the plain value as the guess: mu equals the sample mean weight exactly
+    v1, p1, e1 = oracle.sweep(P1, x, c, 512, 0, cv_v=v0, cv_p=np.zeros((5, n)))
     np.testing.assert_array_equal(v1, v0)           # b = 0: the weight sum is unchanged
     np.testing.assert_array_equal(e1, e0)
-    assert np.any(p1 != p0)                          # the gradient sum is corrected
-    # with a huge mu the correction -mu b.(sum z) has the sign of -b.(sum z): of the guesses
+    assert np.all(np.any(p1 != p0, axis=1))         # the gradient sum is corrected
+    # a large gradient guess: -mu b.(sum z) has the sign of +-(u . sum z), so of the guesses
     # +g and -g exactly one makes the weight sum negative, and that one falls back to the
     # plain sums bit for bit
     for m in range(5):
         res = []
         for sgn in (1.0, -1.0):
-            g = np.zeros((5, n)); g[m] = sgn * np.array([3.0, -1.0, 2.0])
-            v2, p2, _ = oracle.sweep(P1, x, c, 512, 0, cv_v=np.full(5, -40.0), cv_p=g)
+            g = np.zeros((5, n)); g[m] = sgn * 500.0 * np.array([0.6, -0.64, 0.48])
+            v2, p2, _ = oracle.sweep(P1, x, c, 512, 0, cv_v=v0, cv_p=g)
             res.append(bool(v2[m] == v0[m] and np.all(p2[m] == p0[m])))
         assert res.count(True) == 1, (m, res)
+    # a value guess far from the sample mean weight (factor > 4) is not used at all
+    v3, p3, _ = oracle.sweep(P1, x, c, 512, 0, cv_v=v0 - 2.0, cv_p=np.ones((5, n)))
+    np.testing.assert_array_equal(v3, v0)
+    np.testing.assert_array_equal(p3, p0)
