@@ -58,9 +58,9 @@ IMUL_PER_SM_CLK = 32
 
 
 # DRAM bytes per state of one sweep-kernel launch, from an ncu capture of the 6-D sweep
-# over 1,824 states (dram__bytes_read.sum 190,720 B + dram__bytes_write.sum 0 B; the
+# over 1,824 states (dram__bytes_read.sum 200,704 B + dram__bytes_write.sum 0 B; the
 # launch's writes stayed in L2); reads grow in proportion to the states processed.
-DRAM_BYTES_PER_STATE = 190720.0 / 1824
+DRAM_BYTES_PER_STATE = 200704.0 / 1824
 
 
 def roofline(game, samples, kernel_s, states=None):
