@@ -43,14 +43,15 @@ W = hjg_inputs.ROCKETS6
 # round does not multiply, so 4 of the 20 multiplies of a block depend only on the state
 # and sweep and are not per-sample work):
 #   Philox blocks per sample: n / 4 for n <= 8 (packed slots), ceil(n/4) above
-#   IMAD.WIDE (32x32->64 multiplies, FMA-heavy pipe): 16 per block
+#   high halves of the 32x32 products (mul.hi.u32, 32 per SM and clock): 16 per block
+#   (the low halves issue at twice that rate and are not the binding part)
 #   MUFU (XU pipe): log2, sqrt, sin, cos per Box-Muller pair, one sqrt for the target
 #   distance, one exp2 weight (exp2 issues at twice the rate of the others on GB300)
 BLOCKS_PER_SAMPLE = {"dubins3": 0.75, "rockets6": 1.5, "rockets45": 12.0}
 MUFU_PER_SAMPLE = {"dubins3": 2 * 3 + 2, "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
 IMUL_PER_BLOCK = 16
 # GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations
-# and 32 IMAD.WIDE (half the 64 32-bit IMADs per clock).
+# and 32 high-half integer multiplies.
 SMS = 152
 SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16
@@ -68,7 +69,7 @@ def roofline(game, samples, kernel_s, states=None):
     second over the pipe's peak at the maximum SM clock."""
     clk = SMS * SM_MAX_MHZ * 1e6
     pipes = {
-        "imad_wide": (samples * BLOCKS_PER_SAMPLE[game] * IMUL_PER_BLOCK, IMUL_PER_SM_CLK * clk),
+        "int_mul_hi": (samples * BLOCKS_PER_SAMPLE[game] * IMUL_PER_BLOCK, IMUL_PER_SM_CLK * clk),
         "mufu": (samples * (MUFU_PER_SAMPLE[game] - 0.5), MUFU_PER_SM_CLK * clk),
     }
     fr = {k: (ops / kernel_s) / peak for k, (ops, peak) in pipes.items()}

@@ -378,10 +378,13 @@ const char *hjg_batch_last_error(const hjg_batch *b);
 
 /* Instruction classes timed by hjg_microbench: FP32 FMA, the MUFU transcendental
  * approximations (ex2, lg2, sin, cos, sqrt), whole Philox4x32-10 blocks, whole
- * Box-Muller normals as the sweep draws them, and 32x32->64-bit integer multiplies. */
+ * Box-Muller normals as the sweep draws them, 32x32->64-bit integer multiplies, their low
+ * and high halves alone, and Philox blocks whose products are formed as separate high and
+ * low multiplies. */
 enum {
     HJG_MB_FFMA = 1, HJG_MB_EX2 = 2, HJG_MB_LG2 = 3, HJG_MB_SIN = 4, HJG_MB_COS = 5,
-    HJG_MB_SQRT = 6, HJG_MB_PHILOX = 7, HJG_MB_NORMALS = 8, HJG_MB_IMAD_WIDE = 9
+    HJG_MB_SQRT = 6, HJG_MB_PHILOX = 7, HJG_MB_NORMALS = 8, HJG_MB_IMAD_WIDE = 9,
+    HJG_MB_IMUL_LO = 10, HJG_MB_IMUL_HI = 11, HJG_MB_PHILOX_SPLIT = 12
 };
 
 /* Run one saturating launch (8 CTAs of 256 threads per SM, 8 independent chains per

@@ -33,6 +33,53 @@ __global__ void __launch_bounds__(kThreads) imad_wide_pipe(int64_t iters, float*
     if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
 }
 
+// The low or the high 32 bits of a 32x32 product alone (mul.lo.u32 / mul.hi.u32).
+template <bool HI>
+__global__ void __launch_bounds__(kThreads) imul_half_pipe(int64_t iters, float* sink) {
+    uint32_t x[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) x[j] = threadIdx.x * 7919u + j + 1u;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            uint32_t y;
+            if (HI) asm("mul.hi.u32 %0, %1, %2;" : "=r"(y) : "r"(x[j]), "r"(0xD2511F53u));
+            else asm("mul.lo.u32 %0, %1, %2;" : "=r"(y) : "r"(x[j]), "r"(0xD2511F53u));
+            x[j] = y ^ (uint32_t)j;
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) acc ^= x[j];
+    if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
+}
+
+// Philox4x32-10 with each round's products formed by separate high and low multiplies.
+__device__ __forceinline__ uint4 philox_split(uint4 ctr, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t h0, l0, h1, l1;
+        asm("mul.hi.u32 %0, %1, %2;" : "=r"(h0) : "r"(ctr.x), "r"(hjg::kPhiloxM0));
+        asm("mul.lo.u32 %0, %1, %2;" : "=r"(l0) : "r"(ctr.x), "r"(hjg::kPhiloxM0));
+        asm("mul.hi.u32 %0, %1, %2;" : "=r"(h1) : "r"(ctr.z), "r"(hjg::kPhiloxM1));
+        asm("mul.lo.u32 %0, %1, %2;" : "=r"(l1) : "r"(ctr.z), "r"(hjg::kPhiloxM1));
+        ctr = make_uint4(h1 ^ ctr.y ^ k0, l1, h0 ^ ctr.w ^ k1, l0);
+        k0 += hjg::kPhiloxW0;
+        k1 += hjg::kPhiloxW1;
+    }
+    return ctr;
+}
+
+__global__ void __launch_bounds__(kThreads) philox_split_pipe(int64_t iters, float* sink) {
+    uint32_t acc = 0;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = 0; i < iters; ++i) {
+        const uint4 r = philox_split(make_uint4(blockIdx.x, (uint32_t)i * 65536u + t, 9u, 0u), 0x1234u, 0x5678u);
+        acc ^= r.x ^ r.y ^ r.z ^ r.w;
+    }
+    if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
+}
+
 template <int OP>
 __device__ __forceinline__ float step(float x) {
     if (OP == HJG_MB_FFMA) return fmaf(x, 0.9999f, 0.0001f);
@@ -107,11 +154,14 @@ extern "C" hjg_status hjg_microbench(int op, int64_t iters, double* ops_per_s, d
         case HJG_MB_PHILOX: philox_pipe<<<grid, kThreads>>>(iters, sink); break;
         case HJG_MB_NORMALS: normals_pipe<<<grid, kThreads>>>(iters, sink); break;
         case HJG_MB_IMAD_WIDE: imad_wide_pipe<<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_IMUL_LO: imul_half_pipe<false><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_IMUL_HI: imul_half_pipe<true><<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_PHILOX_SPLIT: philox_split_pipe<<<grid, kThreads>>>(iters, sink); break;
         }
     };
-    if (op == HJG_MB_PHILOX) per_thread_iter = 1.0;   // Philox blocks
+    if (op == HJG_MB_PHILOX || op == HJG_MB_PHILOX_SPLIT) per_thread_iter = 1.0;   // Philox blocks
     if (op == HJG_MB_NORMALS) per_thread_iter = 4.0;  // normals
-    if (op < HJG_MB_FFMA || op > HJG_MB_IMAD_WIDE) { cudaFree(sink); return HJG_EINVAL; }
+    if (op < HJG_MB_FFMA || op > HJG_MB_PHILOX_SPLIT) { cudaFree(sink); return HJG_EINVAL; }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
