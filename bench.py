@@ -364,7 +364,8 @@ def run_surrogate(args):
     262,144-state workload (sweeps 23-30 of 30 at N = 131,072: 2,097,152 tuples), GPU
     training of the 45 -> 256^3 -> 46 BF16 network on them, and, on 1,024 held-out states,
     the value error against a high-sample tilted reference for the plain form and the
-    surrogate-assisted form over N = 4,096 ... 131,072."""
+    surrogate-assisted form (warm start + tilt, with and without the control variate) over
+    N = 4,096 ... 131,072."""
     import torch
     from paper_2605_18566_gb300 import Solver, Surrogate
     w = hjg_inputs.ROCKETS45
@@ -399,8 +400,8 @@ def run_surrogate(args):
     tensor_peak = peaks.get("bf16_tflops", 1906.5)
     xte = torch.from_numpy(hjg_inputs.rockets45_points(1024, seed=1)).cuda()
 
-    def solve(N, K, tilt=False, warm=None, seed=11):
-        so = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, tilt=tilt, seed=seed)
+    def solve(N, K, tilt=False, warm=None, seed=11, cv=False):
+        so = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, tilt=tilt, seed=seed, cv=cv)
         so.set_points(xte)
         if warm is not None:
             so.warm_start(warm[1], warm[0])
@@ -414,9 +415,10 @@ def run_surrogate(args):
     vs, ps = pred[:, 0].double().contiguous(), pred[:, 1:].contiguous()
     rows = []
     for N in (4096, 16384, 65536, 131072):
-        for mode in ("plain", "surrogate+tilt"):
+        for mode in ("plain", "surrogate+tilt", "surrogate+tilt+cv"):
             K = 12
-            v, r = solve(N, K, tilt=mode != "plain", warm=(vs, ps) if mode != "plain" else None)
+            v, r = solve(N, K, tilt=mode != "plain", warm=(vs, ps) if mode != "plain" else None,
+                         cv=mode.endswith("+cv"))
             rows.append({"mode": mode, "N": N, "K": K, "point_samples_per_state": N * K,
                          "rms_value_error": float(np.sqrt(np.mean((v - vref) ** 2))),
                          "final_residual": r})

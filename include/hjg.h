@@ -123,8 +123,8 @@ typedef struct {
                               tilt); sum w -= mu b.(sum z), sum w z -= mu (sum z + sum z (z.b)
                               - N b), kept only if mu is within a factor 4 of the sample
                               mean weight and the weight sum stays positive.  Runs its
-                              own launch configuration (256-thread CTA per state); games with
-                              n <= 8 only (EUNSUPPORTED otherwise) */
+                              own launch configuration (256-thread CTA per state); the 45-D
+                              game supports it with tilt only (EUNSUPPORTED otherwise) */
     int32_t reserved[3];
 } hjg_options;
 

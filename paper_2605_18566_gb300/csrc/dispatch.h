@@ -14,6 +14,7 @@ struct GameKernels {
     int minb[16];      // minimum resident CTAs per SM each variant was compiled for
     int per_warp[16];  // 1: one warp per state (the grid is counted in CTAs of threads/32 warps)
     bool has_cv;       // the control-variate kernel exists (launch slot kCvVariant)
+    bool cv_tilt_only; //   and runs only in the tilted frame
     // Launch the fused sweep, variant v, on `grid` CTAs.
     cudaError_t (*sweep)(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st);
     // Resident CTAs per SM of variant v (0 if it cannot launch).

@@ -276,6 +276,8 @@ hjg_status choose_launch(hjg_ctx* ctx) {
     int v = ctx->variant;
     if (ctx->opt.cv) {   // the control variate has one kernel of its own
         if (!ctx->kern.has_cv) return fail(ctx, HJG_EUNSUPPORTED, "no control-variate kernel for this game");
+        if (ctx->kern.cv_tilt_only && !tilt)
+            return fail(ctx, HJG_EUNSUPPORTED, "this game's control variate runs with the tilt only");
         v = kCvVariant;
     } else if (ctx->opt.variant > 0) {
         v = ctx->opt.variant - 1;

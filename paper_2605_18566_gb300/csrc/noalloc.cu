@@ -162,7 +162,7 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     int variant = opt->variant > 0 ? opt->variant - 1 : 0;
     if (variant >= kern.nvariants) return HJG_EINVAL;
     if (opt->cv) {
-        if (!kern.has_cv) return HJG_EUNSUPPORTED;
+        if (!kern.has_cv || (kern.cv_tilt_only && !tilt)) return HJG_EUNSUPPORTED;
         variant = kCvVariant;
     }
     int dev = 0, sms = 0;

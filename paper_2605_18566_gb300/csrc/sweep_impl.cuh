@@ -592,8 +592,9 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
 // each lane takes the minimum squared distance over its own pursuers, and two shuffles
 // finish the group minimum.  All four lanes then hold the same log-weight and accumulate
 // their own twelve S_j.
-template <int THREADS, int MINB, bool TILT>
+template <int THREADS, int MINB, bool TILT, bool CV = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArgs A) {
+    static_assert(!CV || TILT, "the 45-D control variate runs in the tilted frame");
     using G = Rockets45;
     constexpr int n = 45;
     constexpr int NPAD = 48;
@@ -623,6 +624,9 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
             float m = -INFINITY, s = 0.0f, q = 0.0f, S[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) S[j] = 0.0f;
+            float Z1[CV ? 12 : 1];   // control variate: plain sums of this lane's 12 normals
+#pragma unroll
+            for (int j = 0; j < (CV ? 12 : 1); ++j) Z1[j] = 0.0f;
 
             for (uint32_t i = grp; i < N32; i += GROUPS) {
                 float z[12];
@@ -656,15 +660,33 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
                     a2 += part;
                 }
                 lse_accumulate<12>(a2, z, m, s, q, S);
+                if constexpr (CV) {
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) Z1[j] += z[j];
+                }
             }
 
             warp_merge<12>(4, m, s, q, S);
+            if constexpr (CV) {
+#pragma unroll
+                for (int off = 16; off >= 4; off >>= 1) {
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) Z1[j] += __shfl_xor_sync(0xffffffffu, Z1[j], off);
+                }
+            }
             if (lane < 4) {
                 if (lane == 0) { sh.red_m[warp] = m; sh.red_s[warp] = s; sh.red_q[warp] = q; }
 #pragma unroll
                 for (int j = 0; j < 12; ++j) sh.red_S[warp][12 * lane + j] = S[j];
+                if constexpr (CV) {
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) {
+                        sh.red_Z1[warp][12 * lane + j] = Z1[j];
+                        sh.red_Z2[warp][12 * lane + j] = 0.0f;
+                    }
+                }
             }
-            finish_sweep<G, NPAD, W, G::kCache, TILT>(sh, A, pt, k, tid);
+            finish_sweep<G, NPAD, W, G::kCache, TILT, CV>(sh, A, pt, k, tid);
         }
     }
 }

@@ -4,7 +4,7 @@
   on the GPU agrees with the oracle's CV sweep (plain and tilted frames).
 * Variance: in the exact Cole-Hopf case warm-started with the closed form, the spread of
   the gradient over seeds shrinks against the plain sweep.
-* Games without a CV kernel refuse the option."""
+* The 45-D game refuses the option without the tilt."""
 import numpy as np
 import pytest
 
@@ -22,8 +22,10 @@ def _state(s):
     return {k: t for k, t in s.get_state().items()}
 
 
-@pytest.mark.parametrize("w,M,N", [(W1, 1024, 4096), (W2, 211, 16384)], ids=["dubins3", "rockets6"])
-@pytest.mark.parametrize("tilt", [False, True])
+@pytest.mark.parametrize("w,M,N,tilt", [(W1, 1024, 4096, False), (W1, 1024, 4096, True),
+                                        (W2, 211, 16384, False), (W2, 211, 16384, True),
+                                        (hjg_inputs.ROCKETS45, 24, 8192, True)],
+                         ids=["dubins3", "dubins3-tilt", "rockets6", "rockets6-tilt", "rockets45-tilt"])
 def test_cv_one_sweep_parity(w, M, N, tilt):
     xn = hjg_inputs.points(w, M=M)
     x = torch.from_numpy(xn).cuda()
@@ -90,7 +92,8 @@ def test_cv_reduces_gradient_spread_in_the_exact_case(tilt):
         assert np.all(np.abs(G.mean(0) - g) < 5 * G.std(0) / np.sqrt(len(G)) + 1e-5)
 
 
-def test_cv_unsupported_game():
+def test_cv_unsupported_combination():
+    """The 45-D game's control variate runs in the tilted frame only."""
     from paper_2605_18566_gb300 import HJGError
     w = hjg_inputs.ROCKETS45
     s = solver_for(w, N=256, K=1, cv=True)
