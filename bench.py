@@ -199,8 +199,10 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         for i in range(max(3, min(args.steps, 5))):
             solver.set_points(x)
-            solver.picard_sweep(W.K, residuals=True)
+            resid, _ = solver.picard_sweep(W.K, residuals=True)
             kern_ms.append(solver.diagnostics()["last_ms"])
+        st = solver.get_state()
+        final_v, final_p = st["v"].cpu().numpy(), st["p"].cpu().numpy()
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -252,8 +254,20 @@ def run_ours(args, rank, world, local_rank):
                          kernel_ms_per_step=statistics.median(kern_ms)),
         "clocks": clocks,
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
+        "residuals": [float(r) for r in resid],
+        "sweeps_to_floor": sweeps_to_floor(resid),
     }
+    out["_final"] = (final_v, final_p)
     return out
+
+
+def sweeps_to_floor(resid):
+    """Residual floor = median of the last three sweeps' residuals; sweeps to the floor =
+    first sweep whose residual is within 10 % of it."""
+    r = np.asarray(resid, dtype=np.float64)
+    floor = float(np.median(r[-3:]))
+    k = int(np.nonzero(r <= 1.1 * floor)[0][0]) + 1
+    return {"floor": floor, "sweeps": k}
 
 
 def run_cpu_baseline(seconds_target=12.0, rank=0):
@@ -272,11 +286,25 @@ def run_cpu_baseline(seconds_target=12.0, rank=0):
     m = int(min(W.M, max(threads, m)))
     idx = hjg_inputs.subset_indices(W.M, m, seed=5)
     t0 = time.perf_counter()
-    oracle.picard(P, x[idx].astype(np.float64), W.N, W.K, idx=idx)
+    ref = oracle.picard(P, x[idx].astype(np.float64), W.N, W.K, idx=idx)
     el = time.perf_counter() - t0
     return {"value": m * W.N * W.K / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of %d states (seeded subset), full N=%d and K=%d, %.1f s"
-                      % (m, W.M, W.N, W.K, el)}
+                      % (m, W.M, W.N, W.K, el), "elapsed_s": el}, (idx, ref)
+
+
+def oracle_error(final, sample):
+    """The benchmark solve's error against the oracle's FP64 trajectory on the oracle's
+    sample of states (same global indices, same draws): per state |dv|/(1+|v|) and
+    ||dDv||/(1+||Dv||), and the fraction within the parity tolerance (1e-4, 1e-3)."""
+    (v, p), (idx, ref) = final, sample
+    dv = np.abs(v[idx] - ref["v"]) / (1.0 + np.abs(ref["v"]))
+    dp = np.linalg.norm(p[idx].astype(np.float64) - ref["p"], axis=1) / (1.0 + np.linalg.norm(ref["p"], axis=1))
+    ok = (dv <= 1e-4) & (dp <= 1e-3)
+    return {"states": int(len(idx)), "within_tolerance": float(ok.mean()),
+            "dv_median": float(np.median(dv)), "dv_max": float(dv.max()),
+            "dgrad_median": float(np.median(dp)), "dgrad_max": float(dp.max()),
+            "tolerance": "|dv| <= 1e-4 (1+|v|), ||dDv|| <= 1e-3 (1+||Dv||) after K sweeps (FP64 oracle trajectory)"}
 
 
 def ncu_case(w, variant):
@@ -469,12 +497,13 @@ def main():
         import oracle
         runs = []
         for i in range(args.warmup + args.steps):
-            r = run_cpu_baseline(seconds_target=6.0)
+            r = run_cpu_baseline(seconds_target=6.0)[0]
             if i >= args.warmup:
                 runs.append(r)
         val = statistics.median(r["value"] for r in runs)
         out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * statistics.median(r["elapsed_s"] for r in runs),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64", "data": "synthetic (seeded uniform states)",
                "config": {"workload": "rockets6_uniform (bounded CPU sample per step)",
@@ -491,9 +520,11 @@ def main():
             print(json.dumps(run_mixed(args) if args.workload == "mixed" else run_surrogate(args)))
         return
     out = run_ours(args, rank, world, local_rank)
+    final = out.pop("_final")
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = run_cpu_baseline()
+            out["cpu_baseline"], sample = run_cpu_baseline()
+            out["oracle_error"] = oracle_error(final, sample)
         print(json.dumps(out))
 
 
