@@ -3,7 +3,7 @@
 // master weights and Adam.  It is trained on the (x, v, Dv) tuples the Picard sweeps
 // produce (loss: mean squared error of v plus the mean squared error of Dv averaged over
 // its n components) and supplies a warm start (v, Dv, hence c = Gamma(Dv) and the tilt
-// theta = -sigma^2 c Dv) for the sweep, which stays the judge of its accuracy.
+// theta = -sigma^2 c Dv) for the sweep, whose own estimate stays the measure of its accuracy.
 //
 // Layout: parameters are one FP32 array [W1 | b1 | W2 | b2 | W3 | b3 | W4 | b4] with each
 // W_l stored [out][in] row-major; a BF16 copy of the W_l feeds the tensor cores.  Inputs

@@ -1,7 +1,7 @@
 """What the learned part gains over the method without it (3-D Dubins game).
 
 A surrogate network is trained on the GPU on (x, v, Dv) tuples produced by the sweeps
-themselves, then judged by the sweep: against a high-sample reference solve, compare
+themselves, then measured by the sweep: against a high-sample reference solve, compare
   * the plain form (Algorithm 1 as printed: untilted proposal, start at v = g),
   * the surrogate's own prediction (no samples at query time),
   * the surrogate-assisted form (warm start v, Dv, c = Gamma(Dv) from the network, tilted
