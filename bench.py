@@ -75,9 +75,10 @@ def roofline(game, samples, kernel_s, states=None):
     fr = {k: (ops / kernel_s) / peak for k, (ops, peak) in pipes.items()}
     bind = max(fr, key=fr.get)
     ops, peak = pipes[bind]
+    traffic = DRAM_BYTES_PER_STATE * states if states and game == "rockets6" else None
     return {"bound": "alu", "pipe": bind, "achieved": ops / kernel_s / 1e9, "peak": peak / 1e9,
-            "unit": "Gop/s", "frac": fr[bind],
-            "traffic": (DRAM_BYTES_PER_STATE * states if states and game == "rockets6" else None),
+            "unit": "Gop/s", "frac": fr[bind], "traffic": traffic,
+            "hbm_gbs": traffic / kernel_s / 1e9 if traffic else None,
             "ops_per_point_sample": ops / samples,
             "other_pipes": {k: round(v, 4) for k, v in fr.items() if k != bind},
             "peak_basis": "per-SM-per-clock pipe rate x 152 SMs x 2070 MHz"}
@@ -238,6 +239,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "step_ms": {"median": statistics.median(step_ms),
+                    "iqr": float(np.subtract(*np.percentile(step_ms, [75, 25])))},
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 combine/log/residual)",
         "data": "synthetic (seeded uniform states)",
         "config": {"workload": "rockets6_uniform: 6-D two-rocket game, M=65536 states in "
