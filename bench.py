@@ -177,7 +177,7 @@ def run_ours(args, rank, world, local_rank):
 
     with torch.cuda.stream(stream):
         solver.set_points(x)
-        tuned = solver.autotune(max_states=4 * SMS * 6)   # launch variant, outside timing
+        tuned = solver.autotune(max_states=16 * SMS * 6)   # launch variant, outside timing
         for _ in range(args.warmup):
             step()
     torch.cuda.synchronize()

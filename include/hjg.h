@@ -227,8 +227,9 @@ hjg_status hjg_value_grad(hjg_ctx *ctx, const float *pts, int64_t M, int64_t ld,
 
 hjg_status hjg_get_diagnostics(hjg_ctx *ctx, hjg_diag *out);
 
-/* Autotuner: time one sweep of every launch variant of the sweep kernel (CTA size x
- * register budget, with the persistent grid that fills the SMs) on the first
+/* Autotuner: time one sweep of every launch variant of the sweep kernel (kernel kind, CTA
+ * size x register budget, sampler pipelining, with the persistent grid that fills the SMs;
+ * one warm-up launch, then the faster of two timed launches) on the first
  * min(M, max_states) loaded states (max_states <= 0: all), keep the fastest for this
  * context and report its index, CTA size and time.  Works on scratch copies: the iterate
  * and the sweep counter are unchanged.  Allocates and frees device scratch; synchronises
