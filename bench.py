@@ -460,6 +460,7 @@ def run_surrogate(args):
            "config": {"workload": "rockets45_gauss sweeps 23-30 -> 2,097,152 tuples; MLP 45-256-256-256-46",
                       "epochs": epochs, "batch": batch},
            "tuple_generation_s": t_data, "train_s": t_train, "loss": [hist[0], hist[-1]],
+           "rockets45_point_samples_per_s": w.M * w.N * w.K / t_data,   # the 30-sweep solve that made the tuples
            "data_residuals": resid,
            "mlp_tflops": tuples * flops_per_tuple / t_train / 1e12,
            "roofline": {"bound": "tensor", "achieved": tuples * flops_per_tuple / t_train / 1e12,

@@ -375,6 +375,13 @@ hjg_status hjg_batch_run(hjg_batch *b, int n_sweeps, double *residual_out, void 
 void hjg_batch_destroy(hjg_batch *b);
 const char *hjg_batch_last_error(const hjg_batch *b);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): a one-thread kernel
+ * waits on an mbarrier with the same wait loop the tensor-core GEMM uses, limited to
+ * `limit` polls; with arrive = 0 nothing arrives, the wait gives up and the call returns
+ * HJG_ETIMEOUT with the device still usable; with arrive = 1 it returns HJG_OK.
+ * Synchronises the stream. */
+hjg_status hjg_selftest_bounded_wait(int arrive, int64_t limit, void *stream);
+
 /* ---- pipe micro-benchmarks (roofline denominators) ------------------------------ */
 
 /* Instruction classes timed by hjg_microbench: FP32 FMA, the MUFU transcendental

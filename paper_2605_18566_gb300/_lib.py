@@ -69,6 +69,7 @@ _SIGS = {
     "hjg_warm_start": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int]),
     "hjg_get_residual_parts": (C.c_int, [_vp, _vp]),
     "hjg_set_horizons": (C.c_int, [_vp, _vp, C.c_int]),
+    "hjg_selftest_bounded_wait": (C.c_int, [C.c_int, C.c_int64, _vp]),
     "hjg_topology": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, _vp, _vp]),
     "hjg_certify": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp,
                               C.c_int]),

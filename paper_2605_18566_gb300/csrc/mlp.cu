@@ -85,8 +85,8 @@ __device__ __forceinline__ uint32_t canon_off(int r, int k, int R) {
     return (uint32_t)((k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err) {
-    for (uint32_t it = 0; it < (1u << 24); ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, uint32_t limit = 1u << 24) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -500,6 +500,21 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
+// Self-test of the bounded wait: one thread initialises an mbarrier expecting one arrival,
+// arrives on it only if `arrive` is set, and waits with the given iteration limit.  With no
+// arrival the wait gives up, sets *err and the kernel returns normally.
+__global__ void bounded_wait_kernel(int arrive, uint32_t limit, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if (arrive) {
+        uint64_t state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(b) : "memory");
+    }
+    mbar_wait(b, 0, err, limit);
+}
+
 // ------------------------------------------------------------------------------------
 struct hjg_mlp {
     int n_in, n_out, width, in_pad, out_pad;
@@ -814,6 +829,24 @@ hjg_status hjg_gemm_bf16(const void* A, int64_t sam, int64_t sak, const void* B,
         if (e) return HJG_ETIMEOUT;
     }
     return HJG_OK;
+}
+
+hjg_status hjg_selftest_bounded_wait(int arrive, int64_t limit, void* stream) {
+    if (limit < 1 || limit > 0xFFFFFFFFll) return HJG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = nullptr;
+    if (cudaMallocAsync((void**)&err, sizeof(int), st) != cudaSuccess) return HJG_ENOMEM;
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        bounded_wait_kernel<<<1, 1, 0, st>>>(arrive, (uint32_t)limit, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(err, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return HJG_ECUDA;
+    return h ? HJG_ETIMEOUT : HJG_OK;
 }
 
 hjg_status hjg_mlp_train_step(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
