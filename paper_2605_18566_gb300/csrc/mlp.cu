@@ -31,7 +31,7 @@ __host__ __device__ inline int pad16(int n) { return (n + 15) / 16 * 16; }
 // B(k, n) = B[k*sbk + n*sbn] (BF16), FP32 accumulation, and an epilogue (bias, SiLU,
 // BF16 activation copy).  gridDim.z splits K (each split writes its own partial for a
 // later reduction).
-enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2 };
+enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiSiluBwd = 3 };
 
 struct GemmArgs {
     const __nv_bfloat16* A;
@@ -40,8 +40,12 @@ struct GemmArgs {
     int M, N, K;
     float* C;          // FP32 output (z or partial), [M][ldc] (+ split * M * ldc)
     int64_t ldc;
-    __nv_bfloat16* H;  // BF16 activation output (kEpiBiasSilu), [M][ldh]
+    __nv_bfloat16* H;  // BF16 activation output (kEpiBiasSilu, kEpiSiluBwd), [M][ldh]
     int64_t ldh;
+    __nv_bfloat16* Ht; // the same BF16 output transposed, [N][ldht] (or null)
+    int64_t ldht;
+    const float* Zin;  // kEpiSiluBwd: pre-activations [M][ldz]; H = C * silu'(Zin)
+    int64_t ldz;
     const float* bias; // [N]
     int kper;          // K values per split (a multiple of 64 when split)
 };
@@ -217,6 +221,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     float* C = g.C ? g.C + (int64_t)blockIdx.z * g.M * g.ldc : nullptr;
     const bool vecC = C && (g.ldc % 4) == 0 && ((uintptr_t)C & 15) == 0;
     const bool vecH = (g.ldh % 8) == 0 && ((uintptr_t)g.H & 15) == 0;
+    const bool vecZ = EPI == kEpiSiluBwd && (g.ldz % 4) == 0 && ((uintptr_t)g.Zin & 15) == 0;
+    constexpr bool kH = EPI == kEpiBiasSilu || EPI == kEpiSiluBwd;
     if (ok && nch > 0) {
 #pragma unroll 1
         for (int c0 = 0; c0 < kTcN; c0 += 8) {
@@ -228,13 +234,35 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (m >= g.M) continue;
             const int nb = n0 + c0;
+            const bool full = nb + 8 <= g.N;
             float x[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 x[j] = __uint_as_float(v[j]);
-                if (EPI != kEpiStore && nb + j < g.N) x[j] += g.bias[nb + j];
+                if ((EPI == kEpiBiasSilu || EPI == kEpiBias) && nb + j < g.N) x[j] += g.bias[nb + j];
             }
-            if (nb + 8 <= g.N) {
+            if (EPI == kEpiSiluBwd) {   // dZ = dH silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)
+                float z[8];
+                if (full && vecZ) {
+                    const float4* zp = reinterpret_cast<const float4*>(g.Zin + (int64_t)m * g.ldz + nb);
+                    const float4 a = zp[0], b = zp[1];
+                    z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w; z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) z[j] = nb + j < g.N ? g.Zin[(int64_t)m * g.ldz + nb + j] : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float sg = 1.0f / (1.0f + __expf(-z[j]));
+                    x[j] = x[j] * sg * (1.0f + z[j] * (1.0f - sg));
+                }
+            }
+            __align__(16) __nv_bfloat16 h[8];
+            if (kH) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(EPI == kEpiBiasSilu ? silu(x[j]) : x[j]);
+            }
+            if (full) {
                 if (C && vecC) {
                     float4* d = reinterpret_cast<float4*>(C + (int64_t)m * g.ldc + nb);
                     d[0] = make_float4(x[0], x[1], x[2], x[3]);
@@ -243,29 +271,37 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
 #pragma unroll
                     for (int j = 0; j < 8; ++j) C[(int64_t)m * g.ldc + nb + j] = x[j];
                 }
-                if (EPI == kEpiBiasSilu) {
-                    __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(silu(x[j]));
+                if (kH) {
                     if (vecH) {
                         *reinterpret_cast<uint4*>(g.H + (int64_t)m * g.ldh + nb) = *reinterpret_cast<const uint4*>(h);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
                     }
+                    if (g.Ht) {   // transposed copy: the lanes of a warp write consecutive m
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
+                    }
                 }
             } else {
                 for (int j = 0; j < 8 && nb + j < g.N; ++j) {
                     if (C) C[(int64_t)m * g.ldc + nb + j] = x[j];
-                    if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + nb + j] = __float2bfloat16(silu(x[j]));
+                    if (kH) {
+                        g.H[(int64_t)m * g.ldh + nb + j] = h[j];
+                        if (g.Ht) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
+                    }
                 }
             }
         }
-    } else if (m < g.M && C) {   // empty K range (or a timed-out wait): C = 0 (+ bias)
+    } else if (m < g.M) {   // empty K range (or a timed-out wait): C = 0 (+ bias)
         for (int n = n0; n < min(g.N, n0 + kTcN); ++n) {
-            const float x = (EPI != kEpiStore) ? g.bias[n] : 0.0f;
-            C[(int64_t)m * g.ldc + n] = x;
-            if (EPI == kEpiBiasSilu) g.H[(int64_t)m * g.ldh + n] = __float2bfloat16(silu(x));
+            const float x = (EPI == kEpiBiasSilu || EPI == kEpiBias) ? g.bias[n] : 0.0f;
+            if (C) C[(int64_t)m * g.ldc + n] = x;
+            if (kH) {
+                const __nv_bfloat16 hv = __float2bfloat16(EPI == kEpiBiasSilu ? silu(x) : 0.0f);
+                g.H[(int64_t)m * g.ldh + n] = hv;
+                if (g.Ht) g.Ht[(int64_t)n * g.ldht + m] = hv;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -355,6 +391,7 @@ cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st, __nv_b
     case kEpiStore: return launch_tc<kEpiStore>(k, splits, st);
     case kEpiBiasSilu: return launch_tc<kEpiBiasSilu>(k, splits, st);
     case kEpiBias: return launch_tc<kEpiBias>(k, splits, st);
+    case kEpiSiluBwd: return launch_tc<kEpiSiluBwd>(k, splits, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -477,6 +514,21 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __res
     if (e < n) wb[e] = __float2bfloat16(w[e]);
 }
 
+// Per-layer transposed BF16 copies of the weights, W_l^T [cols][rows] at the same offset
+// as W_l: the K-major operand of the backward data-gradient GEMM dH = dZ W.
+struct WeightMap {
+    int64_t w_off[kLayers];
+    int rows[kLayers], cols[kLayers];
+};
+__global__ void weights_t_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wt, WeightMap map) {
+    const int l = blockIdx.y;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = map.rows[l], cols = map.cols[l];
+    if (e >= (int64_t)rows * cols) return;
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    wt[map.w_off[l] + (int64_t)c * rows + r] = __float2bfloat16(w[map.w_off[l] + e]);
+}
+
 // Deterministic initialisation: W_l uniform in +-sqrt(6 / (fan_in + fan_out)) (rows beyond
 // n_out and columns beyond n_in zero), biases zero; uniforms from a 64-bit mix of
 // (seed, index).
@@ -508,10 +560,7 @@ __global__ void bounded_wait_kernel(int arrive, uint32_t limit, int* err) {
     const uint32_t b = smem_u32(&bar);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b));
     asm volatile("fence.mbarrier_init.release.cluster;");
-    if (arrive) {
-        uint64_t state;
-        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(b) : "memory");
-    }
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
     mbar_wait(b, 0, err, limit);
 }
 
@@ -525,11 +574,15 @@ struct hjg_mlp {
     float* m1 = nullptr;                  // Adam moments
     float* m2 = nullptr;
     __nv_bfloat16* pb = nullptr;          // BF16 copy (weights used by the GEMMs)
+    __nv_bfloat16* pbT = nullptr;         // BF16 transposed weights W_l^T (same offsets)
     int64_t cap = 0;                      // batch capacity of the work buffers
     __nv_bfloat16* X = nullptr;           // [cap][in_pad]
     float* Z[kLayers] = {};               // pre-activations [cap][width] (layer 4: outputs)
     __nv_bfloat16* H[kLayers] = {};       // activations [cap][width] BF16
     __nv_bfloat16* dZ = nullptr;          // [cap][width] BF16
+    __nv_bfloat16* dZ2 = nullptr;         // [cap][width] BF16 (the fused backward alternates)
+    __nv_bfloat16* Ht[kLayers] = {};      // transposed activations H_l^T [width][pad8(B)] (training)
+    __nv_bfloat16* dZt = nullptr;         // transposed dZ [D][pad8(B)]
     float* dH = nullptr;                  // [cap][width] FP32
     float* wpart = nullptr;               // split-K partial weight gradients
     __nv_bfloat16* packA = nullptr;       // K-major copies of transposed GEMM operands
@@ -548,9 +601,12 @@ constexpr int kSplits = 16;
 hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
     if (B <= m->cap) return HJG_OK;
     auto fre = [](void* p) { if (p) cudaFree(p); };
-    fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart); fre(m->packA); fre(m->packB);
-    m->packA = m->packB = nullptr;
-    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); m->Z[l] = nullptr; m->H[l] = nullptr; }
+    fre(m->X); fre(m->dZ); fre(m->dZ2); fre(m->dZt); fre(m->dH); fre(m->lpart); fre(m->packA); fre(m->packB);
+    m->packA = m->packB = m->dZ2 = m->dZt = nullptr;
+    for (int l = 0; l < kLayers; ++l) {
+        fre(m->Z[l]); fre(m->H[l]); fre(m->Ht[l]);
+        m->Z[l] = nullptr; m->H[l] = nullptr; m->Ht[l] = nullptr;
+    }
     const int W = m->width;
     const int64_t D = std::max<int64_t>(W, std::max(m->in_pad, m->out_pad));
     const int64_t pa = D * pad8(B), pbk = D * std::max(pad8(B), pad8(D));
@@ -558,7 +614,11 @@ hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
               cudaMalloc(&m->dZ, (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&m->dH, (size_t)B * W * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->packA, (size_t)pa * sizeof(__nv_bfloat16)) == cudaSuccess &&
-              cudaMalloc(&m->packB, (size_t)pbk * sizeof(__nv_bfloat16)) == cudaSuccess;
+              cudaMalloc(&m->packB, (size_t)pbk * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&m->dZ2, (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&m->dZt, (size_t)D * pad8(B) * sizeof(__nv_bfloat16)) == cudaSuccess;
+    for (int l = 0; l + 1 < kLayers && ok; ++l)
+        ok = cudaMalloc(&m->Ht[l], (size_t)W * pad8(B) * sizeof(__nv_bfloat16)) == cudaSuccess;
     for (int l = 0; l < kLayers && ok; ++l) {
         ok = cudaMalloc(&m->Z[l], (size_t)B * W * sizeof(float)) == cudaSuccess &&
              cudaMalloc(&m->H[l], (size_t)B * W * sizeof(__nv_bfloat16)) == cudaSuccess;
@@ -570,9 +630,24 @@ hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
     return HJG_OK;
 }
 
-// Forward pass on X (already packed); outputs FP32 in Z[3] [B][out_pad].
-cudaError_t mlp_forward(hjg_mlp* m, int64_t B) {
+// Refresh the transposed BF16 weights from the FP32 master copy.
+cudaError_t refresh_wt(hjg_mlp* m, cudaStream_t st) {
+    WeightMap map{};
+    int64_t mx = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        map.w_off[l] = m->w_off[l]; map.rows[l] = m->rows[l]; map.cols[l] = m->cols[l];
+        mx = std::max<int64_t>(mx, (int64_t)m->rows[l] * m->cols[l]);
+    }
+    weights_t_kernel<<<dim3(nblk(mx), kLayers), 256, 0, st>>>(m->p, m->pbT, map);
+    return cudaGetLastError();
+}
+
+// Forward pass on X (already packed); outputs FP32 in Z[3] [B][out_pad].  With `train` the
+// hidden layers also write their activations transposed (H_l^T, leading dimension
+// pad8(B)), the K-major operand of the weight-gradient GEMMs.
+cudaError_t mlp_forward(hjg_mlp* m, int64_t B, bool train = false) {
     cudaError_t e = cudaSuccess;
+    const int64_t ldT = pad8(B);
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
         GemmArgs g{};
         const __nv_bfloat16* in = l == 0 ? m->X : m->H[l - 1];
@@ -584,6 +659,14 @@ cudaError_t mlp_forward(hjg_mlp* m, int64_t B) {
         g.bias = m->p + m->b_off[l];
         if (l + 1 < kLayers) {
             g.H = m->H[l]; g.ldh = m->rows[l];
+            if (train) {
+                // the padding columns B..ldT-1 of H_l^T are read as K values: keep them zero
+                if (ldT > B &&
+                    (e = cudaMemset2DAsync(m->Ht[l] + B, ldT * sizeof(__nv_bfloat16), 0,
+                                           (ldT - B) * sizeof(__nv_bfloat16), m->rows[l], m->stream)) != cudaSuccess)
+                    break;
+                g.Ht = m->Ht[l]; g.ldht = ldT;
+            }
             e = gemm(g, kEpiBiasSilu, 1, m->stream);
         } else {
             e = gemm(g, kEpiBias, 1, m->stream);
@@ -592,38 +675,56 @@ cudaError_t mlp_forward(hjg_mlp* m, int64_t B) {
     return e;
 }
 
-// Backward pass from dO (BF16 in m->dZ, [B][out_pad]); gradients into m->g.
+// Backward pass from dO (BF16 in m->dZ, [B][out_pad]) after a training forward; gradients
+// into m->g.  Per layer l: dW_l = dZ_l^T H_{l-1} (split-K over the batch, both operands
+// K-major with K = pad8(B): dZ_l^T from the previous layer's fused epilogue, H_{l-1}^T from
+// the forward), the bias gradient, and dZ_{l-1} = (dZ_l W_l) silu'(Z_{l-1}) in one GEMM whose
+// epilogue writes dZ_{l-1} and its transpose.
 cudaError_t mlp_backward(hjg_mlp* m, int64_t B) {
     cudaError_t e = cudaSuccess;
+    const int64_t ldT = pad8(B);
+    __nv_bfloat16* dz = m->dZ;
+    __nv_bfloat16* dz_next = m->dZ2;
+    // the transposed operands of the output layer (dO^T) and the input layer (X^T)
+    {
+        const int r3 = m->rows[kLayers - 1];
+        dim3 ga((unsigned)((ldT + 31) / 32), (unsigned)((r3 + 31) / 32));
+        pack_kmajor_kernel<<<ga, dim3(32, 8), 0, m->stream>>>(m->dZ, 1, r3, r3, (int)B, m->dZt, ldT);
+        const int c0 = m->cols[0];
+        dim3 gb((unsigned)((ldT + 31) / 32), (unsigned)((c0 + 31) / 32));
+        pack_kmajor_kernel<<<gb, dim3(32, 8), 0, m->stream>>>(m->X, 1, c0, c0, (int)B, m->packB, ldT);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const int rows = m->rows[l], cols = m->cols[l];
-        // dW_l = dZ_l^T . H_{l-1}  ([rows][cols], reduction over the batch, split-K)
         GemmArgs gw{};
-        gw.A = m->dZ; gw.sam = 1; gw.sak = rows;
-        const __nv_bfloat16* hin = l == 0 ? m->X : m->H[l - 1];
-        gw.B = hin; gw.sbk = cols; gw.sbn = 1;
-        gw.M = rows; gw.N = cols; gw.K = (int)B;
+        gw.A = m->dZt; gw.sam = ldT; gw.sak = 1;
+        gw.B = l == 0 ? m->packB : m->Ht[l - 1]; gw.sbk = 1; gw.sbn = ldT;
+        gw.M = rows; gw.N = cols; gw.K = (int)ldT;
         gw.C = m->wpart; gw.ldc = cols;
-        e = gemm(gw, kEpiStore, kSplits, m->stream, m->packA, m->packB);
+        e = gemm(gw, kEpiStore, kSplits, m->stream);
         if (e != cudaSuccess) break;
         const int64_t nw = (int64_t)rows * cols;
         reduce_wgrad_kernel<<<nblk(nw), 256, 0, m->stream>>>(m->wpart, kSplits, nw, m->g + m->w_off[l]);
         // the split-K partials are consumed: the bias partials reuse their buffer
-        bias_partial_kernel<<<dim3((rows + 31) / 32, kBiasChunks), dim3(32, 8), 0, m->stream>>>(m->dZ, B, rows,
+        bias_partial_kernel<<<dim3((rows + 31) / 32, kBiasChunks), dim3(32, 8), 0, m->stream>>>(dz, B, rows,
                                                                                             m->wpart);
         reduce_wgrad_kernel<<<nblk(rows), 256, 0, m->stream>>>(m->wpart, kBiasChunks, rows, m->g + m->b_off[l]);
         if ((e = cudaGetLastError()) != cudaSuccess || l == 0) break;
-        // dH_{l-1} = dZ_l . W_l  ([B][cols])
+        if (ldT > B &&
+            (e = cudaMemset2DAsync(m->dZt + B, ldT * sizeof(__nv_bfloat16), 0, (ldT - B) * sizeof(__nv_bfloat16),
+                                   cols, m->stream)) != cudaSuccess)
+            break;
         GemmArgs gd{};
-        gd.A = m->dZ; gd.sam = rows; gd.sak = 1;
-        gd.B = m->pb + m->w_off[l]; gd.sbk = cols; gd.sbn = 1;
+        gd.A = dz; gd.sam = rows; gd.sak = 1;
+        gd.B = m->pbT + m->w_off[l]; gd.sbk = 1; gd.sbn = rows;   // W_l^T [cols][rows]
         gd.M = (int)B; gd.N = cols; gd.K = rows;
-        gd.C = m->dH; gd.ldc = cols;
-        e = gemm(gd, kEpiStore, 1, m->stream, m->packA, m->packB);
-        if (e != cudaSuccess) break;
-        const int64_t nh = B * (int64_t)cols;
-        silu_backward_kernel<<<nblk(nh), 256, 0, m->stream>>>(m->dH, m->Z[l - 1], nh, m->dZ);
-        e = cudaGetLastError();
+        gd.C = nullptr;
+        gd.Zin = m->Z[l - 1]; gd.ldz = cols;
+        gd.H = dz_next; gd.ldh = cols;
+        gd.Ht = m->dZt; gd.ldht = ldT;
+        e = gemm(gd, kEpiSiluBwd, 1, m->stream);
+        std::swap(dz, dz_next);
     }
     return e;
 }
@@ -634,7 +735,7 @@ hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const flo
     if (s) return s;
     cudaStream_t st = m->stream;
     pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
-    if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B) != cudaSuccess) return HJG_ECUDA;
+    if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B, true) != cudaSuccess) return HJG_ECUDA;
     const int64_t nb = (B * m->out_pad + 255) / 256;
     loss_grad_kernel<<<(unsigned)nb, 256, 0, st>>>(m->Z[kLayers - 1], m->out_pad, y, ldy, B, m->n_out,
                                                    m->out_pad, m->dZ, nullptr, m->lpart);
@@ -681,6 +782,7 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
     if (cudaMalloc(&m->p, nb) != cudaSuccess || cudaMalloc(&m->g, nb) != cudaSuccess ||
         cudaMalloc(&m->m1, nb) != cudaSuccess || cudaMalloc(&m->m2, nb) != cudaSuccess ||
         cudaMalloc(&m->pb, (size_t)off * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc(&m->pbT, (size_t)off * sizeof(__nv_bfloat16)) != cudaSuccess ||
         cudaMalloc(&m->wpart, (size_t)wpart * sizeof(float)) != cudaSuccess) {
         hjg_mlp_destroy(m);
         return HJG_ENOMEM;
@@ -698,7 +800,10 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
                                              used_in[l], scale, seed * 31 + l);
     }
     to_bf16_kernel<<<nblk(off), 256>>>(m->p, m->pb, off);
-    if (cudaDeviceSynchronize() != cudaSuccess) { hjg_mlp_destroy(m); return HJG_ECUDA; }
+    if (refresh_wt(m, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        hjg_mlp_destroy(m);
+        return HJG_ECUDA;
+    }
     *out = m;
     return HJG_OK;
 }
@@ -706,9 +811,9 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
 void hjg_mlp_destroy(hjg_mlp* m) {
     if (!m) return;
     auto fre = [](void* p) { if (p) cudaFree(p); };
-    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->wpart); fre(m->packA); fre(m->packB);
-    fre(m->X); fre(m->dZ); fre(m->dH); fre(m->lpart);
-    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); }
+    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->pbT); fre(m->wpart); fre(m->packA);
+    fre(m->packB); fre(m->X); fre(m->dZ); fre(m->dZ2); fre(m->dZt); fre(m->dH); fre(m->lpart);
+    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); fre(m->Ht[l]); }
     delete m;
 }
 
@@ -735,7 +840,9 @@ hjg_status hjg_mlp_set_params(hjg_mlp* m, const float* in, int on_device) {
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
         return HJG_ECUDA;
     to_bf16_kernel<<<nblk(m->n_params), 256, 0, m->stream>>>(m->p, m->pb, m->n_params);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess) return HJG_ECUDA;
+    if (cudaGetLastError() != cudaSuccess || refresh_wt(m, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return HJG_ECUDA;
     m->step = 0;
     cudaMemsetAsync(m->m1, 0, m->n_params * sizeof(float), m->stream);
     cudaMemsetAsync(m->m2, 0, m->n_params * sizeof(float), m->stream);
@@ -783,7 +890,7 @@ hjg_status hjg_mlp_input_grad(hjg_mlp* m, const float* x, int64_t ldx, int64_t B
         const int rows = m->rows[l], cols = m->cols[l];
         GemmArgs gd{};
         gd.A = m->dZ; gd.sam = rows; gd.sak = 1;
-        gd.B = m->pb + m->w_off[l]; gd.sbk = cols; gd.sbn = 1;
+        gd.B = m->pbT + m->w_off[l]; gd.sbk = 1; gd.sbn = rows;   // W_l^T [cols][rows]
         gd.M = (int)B; gd.N = cols; gd.K = rows;
         gd.C = m->dH; gd.ldc = cols;
         if (gemm(gd, kEpiStore, 1, st, m->packA, m->packB) != cudaSuccess) return HJG_ECUDA;
@@ -859,7 +966,8 @@ hjg_status hjg_mlp_train_step(hjg_mlp* m, const float* x, int64_t ldx, const flo
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     adam_kernel<<<nblk(m->n_params), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb, m->n_params, lr,
                                                            b1, b2, 1e-8f, c1, c2);
-    return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
+    if (cudaGetLastError() != cudaSuccess || refresh_wt(m, m->stream) != cudaSuccess) return HJG_ECUDA;
+    return HJG_OK;
 }
 
 }  // extern "C"
