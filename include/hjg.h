@@ -392,7 +392,7 @@ hjg_status hjg_selftest_bounded_wait(int arrive, int64_t limit, void *stream);
 enum {
     HJG_MB_FFMA = 1, HJG_MB_EX2 = 2, HJG_MB_LG2 = 3, HJG_MB_SIN = 4, HJG_MB_COS = 5,
     HJG_MB_SQRT = 6, HJG_MB_PHILOX = 7, HJG_MB_NORMALS = 8, HJG_MB_IMAD_WIDE = 9,
-    HJG_MB_IMUL_LO = 10, HJG_MB_IMUL_HI = 11, HJG_MB_PHILOX_SPLIT = 12
+    HJG_MB_IMUL_LO = 10, HJG_MB_IMUL_HI = 11, HJG_MB_PHILOX_SPLIT = 12, HJG_MB_PHILOX_MIXED = 13
 };
 
 /* Run one saturating launch (8 CTAs of 256 threads per SM, 8 independent chains per

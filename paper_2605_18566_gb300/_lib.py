@@ -100,7 +100,8 @@ _SIGS = {
 }
 
 MICROBENCH = {"ffma": 1, "ex2": 2, "lg2": 3, "sin": 4, "cos": 5, "sqrt": 6, "philox": 7,
-              "normals": 8, "imad_wide": 9, "imul_lo": 10, "imul_hi": 11, "philox_split": 12}
+              "normals": 8, "imad_wide": 9, "imul_lo": 10, "imul_hi": 11, "philox_split": 12,
+              "philox_mixed": 13}
 
 _lib = None
 

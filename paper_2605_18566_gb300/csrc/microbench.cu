@@ -70,6 +70,31 @@ __device__ __forceinline__ uint4 philox_split(uint4 ctr, uint32_t k0, uint32_t k
     return ctr;
 }
 
+// Philox4x32-10 with one product of each round widening and the other split.
+__device__ __forceinline__ uint4 philox_mixed(uint4 ctr, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)hjg::kPhiloxM0 * ctr.x;
+        uint32_t h1, l1;
+        asm("mul.hi.u32 %0, %1, %2;" : "=r"(h1) : "r"(ctr.z), "r"(hjg::kPhiloxM1));
+        asm("mul.lo.u32 %0, %1, %2;" : "=r"(l1) : "r"(ctr.z), "r"(hjg::kPhiloxM1));
+        ctr = make_uint4(h1 ^ ctr.y ^ k0, l1, (uint32_t)(p0 >> 32) ^ ctr.w ^ k1, (uint32_t)p0);
+        k0 += hjg::kPhiloxW0;
+        k1 += hjg::kPhiloxW1;
+    }
+    return ctr;
+}
+
+__global__ void __launch_bounds__(kThreads) philox_mixed_pipe(int64_t iters, float* sink) {
+    uint32_t acc = 0;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = 0; i < iters; ++i) {
+        const uint4 r = philox_mixed(make_uint4(blockIdx.x, (uint32_t)i * 65536u + t, 9u, 0u), 0x1234u, 0x5678u);
+        acc ^= r.x ^ r.y ^ r.z ^ r.w;
+    }
+    if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
+}
+
 __global__ void __launch_bounds__(kThreads) philox_split_pipe(int64_t iters, float* sink) {
     uint32_t acc = 0;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,11 +182,13 @@ extern "C" hjg_status hjg_microbench(int op, int64_t iters, double* ops_per_s, d
         case HJG_MB_IMUL_LO: imul_half_pipe<false><<<grid, kThreads>>>(iters, sink); break;
         case HJG_MB_IMUL_HI: imul_half_pipe<true><<<grid, kThreads>>>(iters, sink); break;
         case HJG_MB_PHILOX_SPLIT: philox_split_pipe<<<grid, kThreads>>>(iters, sink); break;
+        case HJG_MB_PHILOX_MIXED: philox_mixed_pipe<<<grid, kThreads>>>(iters, sink); break;
         }
     };
-    if (op == HJG_MB_PHILOX || op == HJG_MB_PHILOX_SPLIT) per_thread_iter = 1.0;   // Philox blocks
+    if (op == HJG_MB_PHILOX || op == HJG_MB_PHILOX_SPLIT || op == HJG_MB_PHILOX_MIXED)
+        per_thread_iter = 1.0;   // Philox blocks
     if (op == HJG_MB_NORMALS) per_thread_iter = 4.0;  // normals
-    if (op < HJG_MB_FFMA || op > HJG_MB_PHILOX_SPLIT) { cudaFree(sink); return HJG_EINVAL; }
+    if (op < HJG_MB_FFMA || op > HJG_MB_PHILOX_MIXED) { cudaFree(sink); return HJG_EINVAL; }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
