@@ -1,0 +1,76 @@
+"""Degenerate and edge cases of the sweep against the oracle: one sample per state (ESS = 1),
+a single state, states far from the target (weights spanning hundreds of orders of
+magnitude, handled by the running log-sum-exp shift), coefficients pinned at the clip
+bounds, and a non-finite state that is reported (HJG_ENONFINITE) without disturbing the
+others."""
+import numpy as np
+import pytest
+
+import hjg_inputs
+import oracle
+from helpers import assert_parity, problem_for, solver_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W1, W2 = hjg_inputs.DUBINS3, hjg_inputs.ROCKETS6
+
+
+def _run(w, x, N, K, **kw):
+    s = solver_for(w, N=N, K=K, **kw)
+    s.set_points(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    r, sup = s.picard_sweep(K)
+    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    d = s.diagnostics()
+    status = s.last_status
+    s.close()
+    return st, r, d, status
+
+
+@pytest.mark.parametrize("N", [1, 2, 5])
+def test_tiny_sample_counts(N):
+    x = hjg_inputs.points(W1, M=200)
+    st, r, d, _ = _run(W1, x, N, 3)
+    ref = oracle.picard(problem_for(W1), x.astype(np.float64), N, 3)
+    assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.97, what="N=%d" % N)
+    if N == 1:
+        np.testing.assert_allclose(st["ess"], 1.0, rtol=1e-6)
+
+
+def test_single_state_many_sweeps():
+    x = hjg_inputs.points(W2, M=1)
+    st, r, d, _ = _run(W2, x, 65536, 8)
+    ref = oracle.picard(problem_for(W2), x.astype(np.float64), 65536, 8)
+    assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="M=1")
+    np.testing.assert_allclose(r, ref["resid"], rtol=1e-3)
+
+
+def test_far_states_and_clipped_coefficients():
+    """States 50-5000 units from the capture disc: c is at its clip bound (|c| = 1e2/delta)
+    and c l(y) reaches ~1e5, so the weights span far beyond FP32 range before the shift."""
+    rng = np.random.default_rng(5)
+    M = 64
+    rad = np.exp(rng.uniform(np.log(50.0), np.log(5000.0), M))
+    ang = rng.uniform(-np.pi, np.pi, M)
+    x = np.stack([rad * np.cos(ang), rad * np.sin(ang), rng.uniform(-np.pi, np.pi, M)], 1).astype(np.float32)
+    st, r, d, _ = _run(W1, x, 4096, 3)
+    ref = oracle.picard(problem_for(W1), x.astype(np.float64), 4096, 3)
+    assert np.all(np.isfinite(st["v"])) and np.all(np.isfinite(st["p"]))
+    assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="far states")
+    c_max = 1e2 / W1.delta
+    assert d["clipped"] > 0 and np.any(np.isclose(np.abs(st["c"]), c_max, rtol=1e-6))
+
+
+def test_nonfinite_state_is_reported_and_isolated():
+    x = hjg_inputs.points(W1, M=300)
+    bad = x.copy()
+    bad[17, 0] = np.nan
+    st_bad, _, d, status = _run(W1, bad, 1024, 2)
+    st_ok, _, _, status_ok = _run(W1, x, 1024, 2)
+    from paper_2605_18566_gb300 import _lib
+    assert status == _lib.HJG_ENONFINITE and status_ok == _lib.HJG_OK
+    assert d["nonfinite"] >= 1
+    assert not np.isfinite(st_bad["v"][17])
+    keep = np.arange(300) != 17
+    np.testing.assert_array_equal(st_bad["v"][keep], st_ok["v"][keep])
+    np.testing.assert_array_equal(st_bad["p"][keep], st_ok["p"][keep])
