@@ -193,6 +193,8 @@ def run_ours(args, rank, world, local_rank):
                 step()
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     # sweep-kernel duration alone: the library brackets the sweep launch with its own CUDA
     # events on the launching stream and reports it when residuals are read back
@@ -530,6 +532,10 @@ def main():
             out["cpu_baseline"], sample = run_cpu_baseline()
             out["oracle_error"] = oracle_error(final, sample)
         print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
