@@ -392,18 +392,21 @@ def run_mixed(args):
     return out
 
 
-def run_surrogate(args):
-    """The learned part on the 45-D game: tuples (x, v, Dv) from the plain sweeps of the
-    262,144-state workload (sweeps 23-30 of 30 at N = 131,072: 2,097,152 tuples), GPU
-    training of the 45 -> 256^3 -> 46 BF16 network on them, and, on 1,024 held-out states,
-    the value error against a high-sample tilted reference for the plain form and the
-    surrogate-assisted form (warm start + tilt, with and without the control variate) over
-    N = 4,096 ... 131,072."""
+def surrogate_study(points_fn, label):
+    """One study of the learned part on the 45-D game: tuples (x, v, Dv) from the plain
+    sweeps of 262,144 states drawn by points_fn (sweeps 23-30 of 30 at N = 131,072:
+    2,097,152 tuples), GPU training of the 45 -> 256^3 -> 46 BF16 network on them, and, on
+    1,024 held-out states, the value error against a tilted N = 2^20 reference for the plain
+    form, the tilted form without the network, and the surrogate-assisted form (warm start +
+    tilt, with and without the control variate) over N = 4,096 ... 262,144, 12 sweeps each.  `four_x` compares each plain run
+    with the assisted run at a quarter of its point-samples: success when the assisted run
+    reaches the plain run's residual at no larger value error."""
     import torch
     from paper_2605_18566_gb300 import Solver, Surrogate
     w = hjg_inputs.ROCKETS45
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x = torch.from_numpy(hjg_inputs.points(w)).cuda()
+    x = torch.from_numpy(points_fn(w.M, 0)).cuda()
     s = Solver(w.game, w.nu, w.T, w.N, w.K, radius=w.radius)
     s.set_points(x)
     s.autotune(max_states=4 * SMS * 2)
@@ -427,11 +430,7 @@ def run_surrogate(args):
     torch.cuda.synchronize(); t1 = time.perf_counter()
     hist = sur.fit(X, Y, epochs=epochs, batch=batch, lr=2e-3, lr_final=1e-4)
     torch.cuda.synchronize(); t_train = time.perf_counter() - t1
-    tuples = X.shape[0] * epochs
-    flops_per_tuple = 6 * (48 * 256 + 256 * 256 * 2 + 256 * 48)   # forward + backward GEMMs
-    peaks = load_peaks()
-    tensor_peak = peaks.get("bf16_tflops", 1906.5)
-    xte = torch.from_numpy(hjg_inputs.rockets45_points(1024, seed=1)).cuda()
+    xte = torch.from_numpy(points_fn(1024, 1)).cuda()
 
     def solve(N, K, tilt=False, warm=None, seed=11, cv=False):
         so = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, tilt=tilt, seed=seed, cv=cv)
@@ -447,32 +446,56 @@ def run_surrogate(args):
     pred = sur.forward(xte)
     vs, ps = pred[:, 0].double().contiguous(), pred[:, 1:].contiguous()
     rows = []
-    for N in (4096, 16384, 65536, 131072):
-        for mode in ("plain", "surrogate+tilt", "surrogate+tilt+cv"):
-            K = 12
-            v, r = solve(N, K, tilt=mode != "plain", warm=(vs, ps) if mode != "plain" else None,
+    K = 12
+    for N in (4096, 16384, 65536, 262144):
+        for mode in ("plain", "tilt", "surrogate+tilt", "surrogate+tilt+cv"):
+            v, r = solve(N, K, tilt=mode != "plain", warm=(vs, ps) if mode.startswith("surrogate") else None,
                          cv=mode.endswith("+cv"))
             rows.append({"mode": mode, "N": N, "K": K, "point_samples_per_state": N * K,
                          "rms_value_error": float(np.sqrt(np.mean((v - vref) ** 2))),
                          "final_residual": r})
     sur.close()
-    out = {"metric": "surrogate training tuples/s and error vs point-samples (45-D game)",
-           "value": tuples / t_train, "unit": "tuples/s", "n_gpus": 1, "higher_is_better": True,
-           "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (tuples from the plain sweeps)",
-           "config": {"workload": "rockets45_gauss sweeps 23-30 -> 2,097,152 tuples; MLP 45-256-256-256-46",
-                      "epochs": epochs, "batch": batch},
-           "tuple_generation_s": t_data, "train_s": t_train, "loss": [hist[0], hist[-1]],
-           "rockets45_point_samples_per_s": w.M * w.N * w.K / t_data,   # the 30-sweep solve that made the tuples
-           "data_residuals": resid,
-           "mlp_tflops": tuples * flops_per_tuple / t_train / 1e12,
-           "roofline": {"bound": "tensor", "achieved": tuples * flops_per_tuple / t_train / 1e12,
-                        "peak": tensor_peak, "unit": "TFLOP/s",
-                        "frac": tuples * flops_per_tuple / t_train / 1e12 / tensor_peak,
-                        "note": "whole training step (GEMMs + element-wise + Adam) at batch 8192"},
-           "reference": {"N": 1 << 20, "K": 12, "tilt": True, "final_residual": rref},
-           "surrogate_alone_rms_value_error": float(np.sqrt(np.mean((vs.cpu().numpy() - vref) ** 2))),
-           "study": rows}
-    return out
+    four_x = []
+    for p in rows:
+        if p["mode"] != "plain":
+            continue
+        for a in rows:
+            if a["mode"].startswith("surrogate") and a["N"] * 4 == p["N"]:
+                four_x.append({"plain_N": p["N"], "assisted": a["mode"], "assisted_N": a["N"],
+                               "met": bool(a["final_residual"] <= p["final_residual"]
+                                           and a["rms_value_error"] <= p["rms_value_error"])})
+    return {"label": label, "tuple_generation_s": t_data, "train_s": t_train,
+            "tuples": int(X.shape[0]), "epochs": epochs, "batch": batch,
+            "loss": [hist[0], hist[-1]], "data_residuals": resid,
+            "reference": {"N": 1 << 20, "K": 12, "tilt": True, "final_residual": rref},
+            "surrogate_alone_rms_value_error": float(np.sqrt(np.mean((vs.cpu().numpy() - vref) ** 2))),
+            "study": rows, "four_x": four_x}
+
+
+def run_surrogate(args):
+    """The learned part on the 45-D game, on two state distributions: the workload's own
+    (positions N(0, 2^2): most states start near a capture) and the paper's wider one
+    (positions uniform in [-100, 100]); the line's value is the training throughput of the
+    first."""
+    w = hjg_inputs.ROCKETS45
+    main = surrogate_study(lambda M, seed: hjg_inputs.rockets45_points(M, seed), "positions N(0, 2^2)")
+    wide = surrogate_study(lambda M, seed: hjg_inputs.rockets45_wide_points(M, seed),
+                           "positions uniform in [-100, 100]")
+    flops_per_tuple = 6 * (48 * 256 + 256 * 256 * 2 + 256 * 48)   # forward + backward GEMMs
+    tuples = main["tuples"] * main["epochs"]
+    tflops = tuples * flops_per_tuple / main["train_s"] / 1e12
+    tensor_peak = load_peaks().get("bf16_tflops", 1906.5)
+    return {"metric": "surrogate training tuples/s and error vs point-samples (45-D game)",
+            "value": tuples / main["train_s"], "unit": "tuples/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (tuples from the plain sweeps)",
+            "config": {"workload": "rockets45_gauss sweeps 23-30 -> 2,097,152 tuples; MLP 45-256-256-256-46",
+                       "epochs": main["epochs"], "batch": main["batch"]},
+            "rockets45_point_samples_per_s": w.M * w.N * w.K / main["tuple_generation_s"],
+            "mlp_tflops": tflops,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": tensor_peak, "unit": "TFLOP/s",
+                         "frac": tflops / tensor_peak,
+                         "note": "whole training step (GEMMs + element-wise + Adam) at batch 8192"},
+            "studies": [main, wide]}
 
 
 def main():

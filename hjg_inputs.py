@@ -100,6 +100,15 @@ def rockets45_points(M: int, seed: int = 0) -> np.ndarray:
     return np.concatenate([pos, ang], axis=2).reshape(M, 45).astype(np.float32)
 
 
+def rockets45_wide_points(M: int, seed: int = 0, half_width: float = 100.0) -> np.ndarray:
+    """M states of the 15 planar agents spread as in the paper's 45-D evaluation: positions
+    uniform in [-half_width, half_width] per coordinate, headings uniform in [-pi, pi]."""
+    r = _rng(seed)
+    pos = r.uniform(-half_width, half_width, size=(M, 15, 2))
+    ang = r.uniform(-math.pi, math.pi, size=(M, 15, 1))
+    return np.concatenate([pos, ang], axis=2).reshape(M, 45).astype(np.float32)
+
+
 def flock_states(M: int, seed: int = 0, clusters: int = 6, ring: float = 40.0,
                  std: float = 2.4, heading_std: float = 0.3) -> np.ndarray:
     """M starlings (p_x, p_y, p_z, psi) in `clusters` Gaussian flocks spaced on a ring of

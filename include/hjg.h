@@ -338,6 +338,20 @@ hjg_status hjg_mlp_gradients(hjg_mlp *m, const float *x, int64_t ldx, const floa
  * gives the derivative of the predicted value, a gradient field consistent with it. */
 hjg_status hjg_mlp_input_grad(hjg_mlp *m, const float *x, int64_t ldx, int64_t B, int j, float *gx,
                               int64_t ldg);
+/* Feature standardisation of the network (a training convenience; the paper's network is
+ * not specified to this level): inputs enter as (x_i - shift_i) mul_i and the network's
+ * outputs o_j are reported as o_j mul_j + shift_j, so that features and targets of very
+ * different sizes (positions of +-100 next to headings) train alike.  The default is the
+ * identity.  hjg_mlp_fit_scaling sets shift = mean and mul = 1/std for the inputs x [B][ldx]
+ * and shift = mean, mul = std for the targets y [B][ldy] (device, FP64 sums; a constant
+ * column gets std 1); the loss of hjg_mlp_gradients / hjg_mlp_train_step is then measured on
+ * standardised targets.  get/set exchange the four arrays as one host buffer
+ * [in_shift n_in | in_mul n_in | out_shift n_out | out_mul n_out] (set: EINVAL unless every
+ * mul > 0 and every shift finite). */
+hjg_status hjg_mlp_fit_scaling(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t B);
+hjg_status hjg_mlp_get_scaling(hjg_mlp *m, float *out);
+hjg_status hjg_mlp_set_scaling(hjg_mlp *m, const float *in);
+
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on one batch;
  * loss_out (host) may be NULL (then the call does not synchronise). */
 hjg_status hjg_mlp_train_step(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,

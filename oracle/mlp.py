@@ -47,12 +47,17 @@ def silu(z):
     return z / (1.0 + np.exp(-z))
 
 
-def forward(params, x, n_in, n_out, width, bf16=False):
-    """Returns (outputs [B, n_out], cache for backward)."""
+def forward(params, x, n_in, n_out, width, bf16=False, scaling=None):
+    """Returns (outputs [B, n_out], cache for backward).  scaling = (in_shift, in_mul,
+    out_shift, out_mul): the network sees (x - in_shift) in_mul and reports o out_mul +
+    out_shift (default: identity)."""
     layers = unpack(params, n_in, n_out, width)
     B = x.shape[0]
     X = np.zeros((B, pad16(n_in)))
-    X[:, :n_in] = x[:, :n_in]
+    if scaling is not None:
+        X[:, :n_in] = (np.asarray(x[:, :n_in], dtype=np.float64) - scaling[0]) * scaling[1]
+    else:
+        X[:, :n_in] = x[:, :n_in]
     rnd = to_bf16 if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     h = rnd(X)
     hs, zs = [h], []
@@ -62,15 +67,24 @@ def forward(params, x, n_in, n_out, width, bf16=False):
         if l < 3:
             h = rnd(silu(z))
             hs.append(h)
-    return zs[-1][:, :n_out], (layers, hs, zs, rnd)
+    o = zs[-1][:, :n_out]
+    if scaling is not None:
+        o = o * scaling[3] + scaling[2]
+    return o, (layers, hs, zs, rnd)
 
 
-def loss_and_grads(params, x, y, n_in, n_out, width, bf16=False):
-    """Loss and the gradient of every parameter (flat array in the parameter layout)."""
-    out, (layers, hs, zs, rnd) = forward(params, x, n_in, n_out, width, bf16)
+def loss_and_grads(params, x, y, n_in, n_out, width, bf16=False, scaling=None):
+    """Loss and the gradient of every parameter (flat array in the parameter layout); with
+    scaling the loss compares the raw network outputs with standardised targets
+    (y - out_shift) / out_mul."""
+    _, (layers, hs, zs, rnd) = forward(params, x, n_in, n_out, width, bf16, scaling)
+    out = zs[-1][:, :n_out]
     B = x.shape[0]
     wts = np.full(n_out, 1.0 / (n_out - 1)); wts[0] = 1.0
-    d = out - y[:, :n_out]
+    yt = np.asarray(y[:, :n_out], dtype=np.float64)
+    if scaling is not None:
+        yt = (yt - scaling[2]) / scaling[3]
+    d = out - yt
     loss = float(np.sum(wts * d * d) / B)
     dO = np.zeros_like(zs[-1])
     dO[:, :n_out] = 2.0 * wts * d / B

@@ -85,6 +85,9 @@ _SIGS = {
     "hjg_gemm_bf16": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_int,
                                 C.c_int, C.c_int, _vp, C.c_int64, C.POINTER(C.c_int), _vp]),
     "hjg_mlp_input_grad": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, C.c_int, _vp, C.c_int64]),
+    "hjg_mlp_fit_scaling": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64]),
+    "hjg_mlp_get_scaling": (C.c_int, [_vp, _vp]),
+    "hjg_mlp_set_scaling": (C.c_int, [_vp, _vp]),
     "hjg_mlp_train_step": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_float,
                                      C.POINTER(C.c_double)]),
     "hjg_batch_create": (C.c_int, [C.POINTER(_vp)]),

@@ -400,20 +400,71 @@ cudaError_t gemm(const GemmArgs& g, int epi, int splits, cudaStream_t st, __nv_b
 // Element-wise kernels.
 
 // x [B][ldx] FP32 (n_in used) -> X [B][in_pad] BF16 (zero padding).
+// Network input: the standardised features (x_j - shift_j) mul_j in BF16, zero padded.
 __global__ void pack_input_kernel(const float* __restrict__ x, int64_t ldx, int64_t B, int n_in,
-                                  int in_pad, __nv_bfloat16* __restrict__ X) {
+                                  int in_pad, const float* __restrict__ scal, __nv_bfloat16* __restrict__ X) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= B * in_pad) return;
     const int64_t b = e / in_pad;
     const int j = (int)(e % in_pad);
-    X[e] = __float2bfloat16(j < n_in ? x[b * ldx + j] : 0.0f);
+    X[e] = __float2bfloat16(j < n_in ? (x[b * ldx + j] - scal[j]) * scal[in_pad + j] : 0.0f);
+}
+
+// Network output in the targets' units: out_j = o_j mul_j + shift_j.
+__global__ void unscale_output_kernel(const float* __restrict__ o, int out_pad, int64_t B, int n_out,
+                                      const float* __restrict__ oscal, float* __restrict__ out, int64_t ldout) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * n_out) return;
+    const int64_t b = e / n_out;
+    const int j = (int)(e % n_out);
+    out[b * ldout + j] = fmaf(o[b * out_pad + j], oscal[out_pad + j], oscal[j]);
+}
+
+// Input gradient in the inputs' units: d out_j / d x_i = (d o_j / d xs_i) mul_i^in mul_j^out.
+__global__ void scale_input_grad_kernel(const float* __restrict__ g, int in_pad, int64_t B, int n_in,
+                                        const float* __restrict__ iscal, const float* __restrict__ oscal,
+                                        int out_pad, int j, float* __restrict__ gx, int64_t ldg) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * n_in) return;
+    const int64_t b = e / n_in;
+    const int i = (int)(e % n_in);
+    gx[b * ldg + i] = g[b * in_pad + i] * iscal[in_pad + i] * oscal[out_pad + j];
+}
+
+// Per-feature mean and standard deviation of v [B][ld] (columns 0..n-1, FP64 sums, one
+// CTA per column, fixed reduction order): shift_j = mean, mul_j = 1/std (inputs) or std
+// (outputs); a column with std below 1e-12 (relative) gets std 1.
+__global__ void feature_stats_kernel(const float* __restrict__ v, int64_t ld, int64_t B, int pad, int inverse,
+                                     float* __restrict__ scal) {
+    __shared__ double s1[256], s2[256];
+    const int j = blockIdx.x;
+    double a = 0.0, q = 0.0;
+    for (int64_t b = threadIdx.x; b < B; b += 256) {
+        const double x = (double)v[b * ld + j];
+        a += x;
+        q = fma(x, x, q);
+    }
+    s1[threadIdx.x] = a; s2[threadIdx.x] = q;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) { s1[threadIdx.x] += s1[threadIdx.x + w]; s2[threadIdx.x] += s2[threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = s1[0] / (double)B;
+        const double var = fmax(s2[0] / (double)B - mean * mean, 0.0);
+        double sd = sqrt(var);
+        if (!(sd > 1e-12 * (1.0 + fabs(mean)))) sd = 1.0;
+        scal[j] = (float)mean;
+        scal[pad + j] = (float)(inverse ? 1.0 / sd : sd);
+    }
 }
 
 // Loss and its gradient w.r.t. the outputs: L = mean_b[(o_0 - y_0)^2 + mean_j (o_j - y_j)^2]
-// over j = 1..n_out-1.  dO (BF16) is written for the backward GEMMs; the per-block partial
+// over j = 1..n_out-1, with the targets standardised like the outputs (y - shift) / mul.  dO (BF16) is written for the backward GEMMs; the per-block partial
 // sums of L go to partial[blockIdx.x] (reduced in a fixed order on the host side).
 __global__ void loss_grad_kernel(const float* __restrict__ out, int64_t ldo, const float* __restrict__ y,
-                                 int64_t ldy, int64_t B, int n_out, int out_pad,
+                                 int64_t ldy, int64_t B, int n_out, int out_pad, const float* __restrict__ oscal,
                                  __nv_bfloat16* __restrict__ dO, float* __restrict__ dOf,
                                  double* __restrict__ partial) {
     __shared__ double red[256];
@@ -424,7 +475,7 @@ __global__ void loss_grad_kernel(const float* __restrict__ out, int64_t ldo, con
         const int j = (int)(e % out_pad);
         float g = 0.0f;
         if (j < n_out) {
-            const float d = out[b * ldo + j] - y[b * ldy + j];
+            const float d = out[b * ldo + j] - (y[b * ldy + j] - oscal[j]) / oscal[out_pad + j];
             const float w = j == 0 ? 1.0f : 1.0f / (float)(n_out - 1);
             l = (double)w * (double)d * (double)d / (double)B;
             g = 2.0f * w * d / (float)B;
@@ -575,6 +626,8 @@ struct hjg_mlp {
     float* m2 = nullptr;
     __nv_bfloat16* pb = nullptr;          // BF16 copy (weights used by the GEMMs)
     __nv_bfloat16* pbT = nullptr;         // BF16 transposed weights W_l^T (same offsets)
+    float* iscal = nullptr;               // input standardisation [shift in_pad | mul in_pad]
+    float* oscal = nullptr;               // output scaling [shift out_pad | mul out_pad]
     int64_t cap = 0;                      // batch capacity of the work buffers
     __nv_bfloat16* X = nullptr;           // [cap][in_pad]
     float* Z[kLayers] = {};               // pre-activations [cap][width] (layer 4: outputs)
@@ -734,11 +787,11 @@ hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const flo
     hjg_status s = mlp_ensure(m, B);
     if (s) return s;
     cudaStream_t st = m->stream;
-    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
+    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->iscal, m->X);
     if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B, true) != cudaSuccess) return HJG_ECUDA;
     const int64_t nb = (B * m->out_pad + 255) / 256;
     loss_grad_kernel<<<(unsigned)nb, 256, 0, st>>>(m->Z[kLayers - 1], m->out_pad, y, ldy, B, m->n_out,
-                                                   m->out_pad, m->dZ, nullptr, m->lpart);
+                                                   m->out_pad, m->oscal, m->dZ, nullptr, m->lpart);
     if (cudaGetLastError() != cudaSuccess || mlp_backward(m, B) != cudaSuccess) return HJG_ECUDA;
     if (loss_out) {
         std::vector<double> part((size_t)nb);
@@ -783,6 +836,8 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
         cudaMalloc(&m->m1, nb) != cudaSuccess || cudaMalloc(&m->m2, nb) != cudaSuccess ||
         cudaMalloc(&m->pb, (size_t)off * sizeof(__nv_bfloat16)) != cudaSuccess ||
         cudaMalloc(&m->pbT, (size_t)off * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc(&m->iscal, 2 * (size_t)m->in_pad * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&m->oscal, 2 * (size_t)m->out_pad * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&m->wpart, (size_t)wpart * sizeof(float)) != cudaSuccess) {
         hjg_mlp_destroy(m);
         return HJG_ENOMEM;
@@ -800,6 +855,13 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
                                              used_in[l], scale, seed * 31 + l);
     }
     to_bf16_kernel<<<nblk(off), 256>>>(m->p, m->pb, off);
+    {   // identity scaling until hjg_mlp_fit_scaling / hjg_mlp_set_scaling
+        std::vector<float> si(2 * (size_t)m->in_pad, 0.0f), so(2 * (size_t)m->out_pad, 0.0f);
+        std::fill(si.begin() + m->in_pad, si.end(), 1.0f);
+        std::fill(so.begin() + m->out_pad, so.end(), 1.0f);
+        cudaMemcpy(m->iscal, si.data(), si.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(m->oscal, so.data(), so.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (refresh_wt(m, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         hjg_mlp_destroy(m);
         return HJG_ECUDA;
@@ -811,7 +873,8 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
 void hjg_mlp_destroy(hjg_mlp* m) {
     if (!m) return;
     auto fre = [](void* p) { if (p) cudaFree(p); };
-    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->pbT); fre(m->wpart); fre(m->packA);
+    fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->pbT); fre(m->iscal); fre(m->oscal);
+    fre(m->wpart); fre(m->packA);
     fre(m->packB); fre(m->X); fre(m->dZ); fre(m->dZ2); fre(m->dZt); fre(m->dH); fre(m->lpart);
     for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); fre(m->Ht[l]); }
     delete m;
@@ -854,12 +917,12 @@ hjg_status hjg_mlp_forward(hjg_mlp* m, const float* x, int64_t ldx, int64_t B, f
     if (B == 0) return HJG_OK;
     hjg_status s = mlp_ensure(m, B);
     if (s) return s;
-    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, m->stream>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
+    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, m->stream>>>(x, ldx, B, m->n_in, m->in_pad, m->iscal,
+                                                                  m->X);
     if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B) != cudaSuccess) return HJG_ECUDA;
-    if (cudaMemcpy2DAsync(out, ldout * sizeof(float), m->Z[kLayers - 1], m->out_pad * sizeof(float),
-                          m->n_out * sizeof(float), (size_t)B, cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess)
-        return HJG_ECUDA;
-    return HJG_OK;
+    unscale_output_kernel<<<nblk(B * m->n_out), 256, 0, m->stream>>>(m->Z[kLayers - 1], m->out_pad, B, m->n_out,
+                                                                     m->oscal, out, ldout);
+    return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
 }
 
 hjg_status hjg_mlp_gradients(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
@@ -883,7 +946,7 @@ hjg_status hjg_mlp_input_grad(hjg_mlp* m, const float* x, int64_t ldx, int64_t B
     hjg_status s = mlp_ensure(m, B);
     if (s) return s;
     cudaStream_t st = m->stream;
-    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->X);
+    pack_input_kernel<<<nblk(B * m->in_pad), 256, 0, st>>>(x, ldx, B, m->n_in, m->in_pad, m->iscal, m->X);
     if (cudaGetLastError() != cudaSuccess || mlp_forward(m, B) != cudaSuccess) return HJG_ECUDA;
     unit_output_kernel<<<nblk(B * m->out_pad), 256, 0, st>>>(B, m->out_pad, j, m->dZ);
     for (int l = kLayers - 1; l >= 0; --l) {   // chain rule down to the inputs (no weight gradients)
@@ -899,8 +962,47 @@ hjg_status hjg_mlp_input_grad(hjg_mlp* m, const float* x, int64_t ldx, int64_t B
         silu_backward_kernel<<<nblk(nh), 256, 0, st>>>(m->dH, m->Z[l - 1], nh, m->dZ);
         if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
     }
-    if (cudaMemcpy2DAsync(gx, ldg * sizeof(float), m->dH, m->in_pad * sizeof(float), m->n_in * sizeof(float),
-                          (size_t)B, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    scale_input_grad_kernel<<<nblk(B * m->n_in), 256, 0, st>>>(m->dH, m->in_pad, B, m->n_in, m->iscal, m->oscal,
+                                                               m->out_pad, j, gx, ldg);
+    return cudaGetLastError() == cudaSuccess ? HJG_OK : HJG_ECUDA;
+}
+
+hjg_status hjg_mlp_fit_scaling(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t B) {
+    if (!m || B < 1 || !x || !y || ldx < m->n_in || ldy < m->n_out) return HJG_EINVAL;
+    feature_stats_kernel<<<m->n_in, 256, 0, m->stream>>>(x, ldx, B, m->in_pad, 1, m->iscal);
+    feature_stats_kernel<<<m->n_out, 256, 0, m->stream>>>(y, ldy, B, m->out_pad, 0, m->oscal);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess) return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_get_scaling(hjg_mlp* m, float* out) {
+    if (!m || !out) return HJG_EINVAL;
+    const size_t ni = (size_t)m->n_in, no = (size_t)m->n_out;
+    if (cudaMemcpyAsync(out, m->iscal, ni * sizeof(float), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(out + ni, m->iscal + m->in_pad, ni * sizeof(float), cudaMemcpyDeviceToHost, m->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(out + 2 * ni, m->oscal, no * sizeof(float), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(out + 2 * ni + no, m->oscal + m->out_pad, no * sizeof(float), cudaMemcpyDeviceToHost,
+                        m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_set_scaling(hjg_mlp* m, const float* in) {
+    if (!m || !in) return HJG_EINVAL;
+    const size_t ni = (size_t)m->n_in, no = (size_t)m->n_out;
+    for (size_t i = 0; i < ni; ++i)
+        if (!(in[ni + i] > 0.0f) || !std::isfinite(in[i])) return HJG_EINVAL;
+    for (size_t i = 0; i < no; ++i)
+        if (!(in[2 * ni + no + i] > 0.0f) || !std::isfinite(in[2 * ni + i])) return HJG_EINVAL;
+    if (cudaMemcpyAsync(m->iscal, in, ni * sizeof(float), cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(m->iscal + m->in_pad, in + ni, ni * sizeof(float), cudaMemcpyHostToDevice, m->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(m->oscal, in + 2 * ni, no * sizeof(float), cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(m->oscal + m->out_pad, in + 2 * ni + no, no * sizeof(float), cudaMemcpyHostToDevice,
+                        m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
         return HJG_ECUDA;
     return HJG_OK;
 }

@@ -296,11 +296,34 @@ class Surrogate:
             raise HJGError(st, "hjg_mlp_train_step")
         return loss.value if want_loss else None
 
+    def fit_scaling(self, x: torch.Tensor, y: torch.Tensor):
+        """Standardise inputs and targets by their per-feature mean and std (hjg_mlp_fit_scaling)."""
+        st = self.lib.hjg_mlp_fit_scaling(self.m, C.c_void_p(x.data_ptr()), x.stride(0),
+                                          C.c_void_p(y.data_ptr()), y.stride(0), x.shape[0])
+        if st:
+            raise HJGError(st, "hjg_mlp_fit_scaling")
+
+    def scaling(self) -> np.ndarray:
+        out = np.zeros(2 * (self.n_in + self.n_out), dtype=np.float32)
+        st = self.lib.hjg_mlp_get_scaling(self.m, out.ctypes.data_as(C.c_void_p))
+        if st:
+            raise HJGError(st, "hjg_mlp_get_scaling")
+        return out
+
+    def set_scaling(self, sc) -> None:
+        sc = np.ascontiguousarray(np.asarray(sc, dtype=np.float32).ravel())
+        st = self.lib.hjg_mlp_set_scaling(self.m, sc.ctypes.data_as(C.c_void_p))
+        if st:
+            raise HJGError(st, "hjg_mlp_set_scaling")
+
     def fit(self, x: torch.Tensor, y: torch.Tensor, epochs: int, batch: int = 4096,
-            lr: float = 1e-3, lr_final: float = 1e-5):
+            lr: float = 1e-3, lr_final: float = 1e-5, standardize: bool = True):
         """Adam over contiguous minibatches of (x, y) (shuffle the rows beforehand), with
-        the learning rate decayed geometrically from lr to lr_final; returns the mean loss
-        of each epoch."""
+        the learning rate decayed geometrically from lr to lr_final, after fitting the
+        feature standardisation to (x, y) when `standardize`; returns the mean loss (on
+        standardised targets) of each epoch."""
+        if standardize:
+            self.fit_scaling(x, y)
         n = x.shape[0]
         steps = epochs * max(1, n // batch)
         hist, t = [], 0

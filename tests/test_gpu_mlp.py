@@ -61,7 +61,7 @@ def test_training_lowers_loss():
     x = rng.uniform(-2, 2, size=(16384, N_IN)).astype(np.float32)
     y = np.concatenate([np.sin(x).sum(1, keepdims=True) / 10, np.cos(x) / 10], 1).astype(np.float32)
     xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    hist = s.fit(xt, yt, epochs=40, batch=2048, lr=2e-3, lr_final=1e-4)
+    hist = s.fit(xt, yt, epochs=40, batch=2048, lr=2e-3, lr_final=1e-4, standardize=False)
     assert hist[-1] < 0.35 * hist[0], hist
     assert all(b <= a * 1.05 for a, b in zip(hist, hist[1:])), hist   # steady descent
     out = s.forward(xt).cpu().numpy()
@@ -100,4 +100,46 @@ def test_input_gradient_matches_reference():
         dn, _ = omlp.forward(p, x - e, N_IN, N_OUT, WIDTH)
         fd[:, a] = (up[:, 0] - dn[:, 0]) / (2 * h)
     assert np.linalg.norm(gx - fd) <= 3e-2 * np.linalg.norm(fd)
+    s.close()
+
+
+def test_scaling_forward_gradients_and_input_grad():
+    """Standardisation fitted on the device equals numpy's mean / std; forward outputs,
+    parameter gradients and input gradients with it match the FP64 reference."""
+    s = _sur(seed=5)
+    rng = np.random.default_rng(8)
+    x = (rng.normal(size=(400, N_IN)) * rng.uniform(0.5, 80, N_IN) + rng.normal(size=N_IN) * 20).astype(np.float32)
+    y = (rng.normal(size=(400, N_OUT)) * rng.uniform(0.1, 50, N_OUT) + 5).astype(np.float32)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    s.fit_scaling(xt, yt)
+    sc = s.scaling().astype(np.float64)
+    a, m_in = sc[:N_IN], sc[N_IN:2 * N_IN]
+    b, m_out = sc[2 * N_IN:2 * N_IN + N_OUT], sc[2 * N_IN + N_OUT:]
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    np.testing.assert_allclose(a, xd.mean(0), rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(1.0 / m_in, xd.std(0), rtol=1e-4)
+    np.testing.assert_allclose(b, yd.mean(0), rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(m_out, yd.std(0), rtol=1e-4)
+    scaling = (a, m_in, b, m_out)
+    p = s.params()
+    out = s.forward(xt).cpu().numpy().astype(np.float64)
+    ref, _ = omlp.forward(p, xd, N_IN, N_OUT, WIDTH, bf16=True, scaling=scaling)
+    assert np.abs(out - ref).max() <= 1e-2 * np.abs(ref).max()
+    loss, g = s.gradients(xt, yt)
+    rloss, rg = omlp.loss_and_grads(p, xd, yd, N_IN, N_OUT, WIDTH, bf16=True, scaling=scaling)
+    assert abs(loss - rloss) <= 1e-3 * rloss
+    assert np.linalg.norm(g.astype(np.float64) - rg) <= 2e-2 * np.linalg.norm(rg)
+    gx = s.input_grad(xt[:50].contiguous(), 3).cpu().numpy().astype(np.float64)
+    h = 1e-4 * np.abs(xd[:50]).max()
+    fd = np.zeros((50, N_IN))
+    for i in range(N_IN):
+        e = np.zeros(N_IN); e[i] = h
+        up, _ = omlp.forward(p, xd[:50] + e, N_IN, N_OUT, WIDTH, scaling=scaling)
+        dn, _ = omlp.forward(p, xd[:50] - e, N_IN, N_OUT, WIDTH, scaling=scaling)
+        fd[:, i] = (up[:, 3] - dn[:, 3]) / (2 * h)
+    assert np.linalg.norm(gx - fd) <= 3e-2 * np.linalg.norm(fd)
+    s2 = _sur(seed=6)
+    s2.set_scaling(s.scaling())
+    np.testing.assert_array_equal(s2.scaling(), s.scaling())
+    s2.close()
     s.close()
