@@ -59,9 +59,9 @@ IMUL_PER_SM_CLK = 32
 
 
 # DRAM bytes per state of one sweep-kernel launch, from an ncu capture of the 6-D sweep
-# over 1,824 states (dram__bytes_read.sum 200,704 B + dram__bytes_write.sum 0 B; the
-# launch's writes stayed in L2); reads grow in proportion to the states processed.
-DRAM_BYTES_PER_STATE = 200704.0 / 1824
+# (warp-per-state variant) over 7,296 states (dram__bytes_read.sum 1,011,456 B +
+# dram__bytes_write.sum 370,944 B); both grow in proportion to the states processed.
+DRAM_BYTES_PER_STATE = (1011456.0 + 370944.0) / 7296
 
 
 def roofline(game, samples, kernel_s, states=None):
@@ -312,13 +312,14 @@ def oracle_error(final, sample):
             "tolerance": "|dv| <= 1e-4 (1+|v|), ||dDv|| <= 1e-3 (1+||Dv||) after K sweeps (FP64 oracle trajectory)"}
 
 
-def ncu_case(w, variant):
-    """A small case of one workload for ncu: M = 12 x 152 states (a few MB on the device),
-    the workload's N, two sweeps per launch, launch variant `variant`; one warm-up launch,
-    then one profiled launch."""
+def ncu_case(w, variant, M=None):
+    """A small case of one workload for ncu: M states (default 12 x 152: two waves of the
+    CTA-per-state kernels; the warp-per-state kernels need 48 x 152 for one full wave), a
+    few MB on the device, the workload's N, two sweeps per launch, launch variant
+    `variant`; one warm-up launch, then one profiled launch."""
     import torch
     from paper_2605_18566_gb300 import Solver
-    M = 12 * SMS
+    M = M or 12 * SMS
     x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
     s = Solver(w.game, w.nu, w.T, w.N, 2, radius=w.radius, variant=variant)
     for _ in range(2):
@@ -511,13 +512,14 @@ def main():
     ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS) + ["surrogate_mlp"],
                     help="run one small launch of the named workload's sweep (profiling)")
     ap.add_argument("--variant", type=int, default=2, help="sweep launch variant for --ncu-case")
+    ap.add_argument("--ncu-states", type=int, default=0, help="states of --ncu-case (default 12 x 152)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if args.ncu_case == "surrogate_mlp":
         ncu_case_surrogate()
         return
     if args.ncu_case:
-        ncu_case(hjg_inputs.WORKLOADS[args.ncu_case], args.variant)
+        ncu_case(hjg_inputs.WORKLOADS[args.ncu_case], args.variant, args.ncu_states or None)
         return
 
     if args.impl == "reference":
