@@ -58,10 +58,10 @@ MUFU_PER_SM_CLK = 16
 IMUL_PER_SM_CLK = 32
 
 
-# DRAM bytes per state of one sweep-kernel launch, from an ncu capture of the 6-D sweep
-# (warp-per-state variant) over 7,296 states (dram__bytes_read.sum 1,011,456 B +
-# dram__bytes_write.sum 370,944 B); both grow in proportion to the states processed.
-DRAM_BYTES_PER_STATE = (1011456.0 + 370944.0) / 7296
+# DRAM bytes of one benchmark sweep launch (65,536 states, K = 20, warp-per-state
+# variant), from a one-pass ncu capture of that launch inside the benchmark command:
+# dram__bytes_read.sum 6,353,152 B + dram__bytes_write.sum 4,574,208 B.
+DRAM_BYTES_BENCH_LAUNCH = 6353152.0 + 4574208.0
 
 
 def roofline(game, samples, kernel_s, states=None):
@@ -75,7 +75,7 @@ def roofline(game, samples, kernel_s, states=None):
     fr = {k: (ops / kernel_s) / peak for k, (ops, peak) in pipes.items()}
     bind = max(fr, key=fr.get)
     ops, peak = pipes[bind]
-    traffic = DRAM_BYTES_PER_STATE * states if states and game == "rockets6" else None
+    traffic = DRAM_BYTES_BENCH_LAUNCH if states == W.M and game == W.game else None
     return {"bound": "alu", "pipe": bind, "achieved": ops / kernel_s / 1e9, "peak": peak / 1e9,
             "unit": "Gop/s", "frac": fr[bind], "traffic": traffic,
             "hbm_gbs": traffic / kernel_s / 1e9 if traffic else None,
