@@ -752,9 +752,9 @@ cudaError_t launch_coef(const float* x, int64_t ldx, int64_t M, const float* p, 
     X(4, 0, 512, 1) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12) X(8, 2, 256, 4)      \
     X(9, 2, 128, 8) X(10, 3, 256, 4) X(11, 3, 128, 8)
 #define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 1) X(3, 0, 128, 4) \
-    X(4, 0, 512, 1)
+    X(4, 0, 512, 1) X(5, 0, 256, 3) X(6, 0, 256, 4) X(7, 0, 128, 6)
 constexpr int kNumVariants = 12;
-constexpr int kNumR45Variants = 5;
+constexpr int kNumR45Variants = 8;
 
 template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
