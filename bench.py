@@ -42,12 +42,13 @@ W = hjg_inputs.ROCKETS6
 # for each workload's game; the block index sits in the Philox counter words the first
 # round does not multiply, so 4 of the 20 multiplies of a block depend only on the state
 # and sweep and are not per-sample work):
-#   Philox blocks per sample: n / 4 for n <= 8 (packed slots), ceil(n/4) above
+#   Philox blocks per sample (six normals per block): n / 6 for n <= 8 (packed slots),
+#   ceil(n/6) above
 #   high halves of the 32x32 products (mul.hi.u32, 32 per SM and clock): 16 per block
 #   (the low halves issue at twice that rate and are not the binding part)
 #   MUFU (XU pipe): log2, sqrt, sin, cos per Box-Muller pair, one sqrt for the target
 #   distance, one exp2 weight (exp2 issues at twice the rate of the others on GB300)
-BLOCKS_PER_SAMPLE = {"dubins3": 0.75, "rockets6": 1.5, "rockets45": 12.0}
+BLOCKS_PER_SAMPLE = {"dubins3": 0.5, "rockets6": 1.0, "rockets45": 8.0}
 MUFU_PER_SAMPLE = {"dubins3": 2 * 3 + 2, "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
 IMUL_PER_BLOCK = 16
 # GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations

@@ -17,10 +17,14 @@
  * (Eq. tilt_shift, Cor. B.6).  Viscosity is given as nu with delta = 2 nu, so samples
  * are y = x + sqrt(2 nu t) z.
  *
- * Samples are never stored: sample i of state m in sweep k, dims 4j..4j+3, come from
- * Philox4x32-10 with counter (i, j, m, k) and key (seed_lo, seed_hi ^ instance),
- * mapped to uniforms u = ((r >> 9) + 0.5) 2^-23 and Box-Muller normals (radius from
- * u0 / u2, angle from u1 / u3).
+ * Samples are never stored.  The normals of state m in sweep k form one stream: slot q
+ * is lane q % 6 of Philox4x32-10 block b = q / 6, counter (m, b_lo, k, b_hi), key
+ * (seed_lo, seed_hi ^ instance).  A block's words (X, Y, Z, W) give three Box-Muller
+ * pairs, every bit used once: radius uniforms u = ((r & (2^23-1)) + 0.5) 2^-23 from the
+ * low 23 bits of X, Y, Z; angle uniforms (k + 0.5) 2^-bits from the high 23 bits of W,
+ * from the high 9 bits of X then Y, and from the high 9 bits of Z then the low 9 of W.
+ * Sample i, dim d is slot i S + d, S = n for n <= 8 and n rounded up to a multiple of
+ * 6 above.
  *
  * Conventions for every entry point:
  *   - Return an hjg_status; no call aborts or exits.  hjg_last_error() gives a message.
@@ -97,9 +101,10 @@ typedef struct {
 } hjg_target;
 
 typedef struct {
-    int64_t N;           /* samples per state and sweep (>= 1; at most 2^34 / S, S = n for
-                            n <= 8 and n rounded up to a multiple of 4 above, so that one
-                            state's stream needs at most 2^32 Philox blocks) */
+    int64_t N;           /* samples per state and sweep (1 .. 2^32 - 1, and at most
+                            6 * 2^32 / S, S = n for n <= 8 and n rounded up to a multiple of
+                            6 above, so that one state's stream needs at most 2^32 Philox
+                            blocks; HJG_EINVAL otherwise) */
     int32_t K;           /* sweeps run by hjg_value_grad */
     int32_t tilt;        /* 1: tilted proposal theta = -delta t c Dv (Eq. tilt_shift) */
     double eps;          /* hjg_value_grad stops after the sweep whose residual < eps (0: never) */
@@ -271,7 +276,8 @@ hjg_status hjg_philox_blocks(const uint32_t *ctr, const uint32_t *key, uint32_t 
                              int64_t count, void *stream);
 
 /* The FP32 standard normals the sweep consumes for state `point`, sweep `sweep`, samples
- * 0..n_samples-1: out is device [n_samples][n] FP32. */
+ * 0..n_samples-1 (the stream layout at the top of this header): out is device
+ * [n_samples][n] FP32. */
 hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t point,
                               uint32_t sweep, int64_t n_samples, float *out, void *stream);
 

@@ -72,6 +72,7 @@ def lib():
         L.orc_u01.argtypes = [u32]; L.orc_u01.restype = d
         L.orc_slot_stride.argtypes = [i32]; L.orc_slot_stride.restype = i32
         L.orc_normals.argtypes = [i32, C.c_uint64, u32, u32, u32, u32, pd]
+        L.orc_block_words_normals.argtypes = [P(C.c_uint32), pd]
         L.orc_ell.argtypes = [P(Problem), pd, pd]; L.orc_ell.restype = d
         L.orc_grad_ell.argtypes = [P(Problem), pd, pd, pd]
         L.orc_hamiltonian.argtypes = [P(Problem), pd, pd, d]; L.orc_hamiltonian.restype = d
@@ -167,6 +168,14 @@ def slot_stride(n: int) -> int:
 def normals(n, seed, instance, sample, point, sweep):
     z = np.zeros(n, dtype=np.float64)
     lib().orc_normals(n, seed, instance, sample, point, sweep, _dp(z))
+    return z
+
+
+def block_words_normals(words):
+    """The six normals of one Philox output block (four uint32 words)."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(4))
+    z = np.zeros(6, dtype=np.float64)
+    lib().orc_block_words_normals(w.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(z))
     return z
 
 

@@ -22,8 +22,9 @@
  *     Section 3.2 multi-rocket game (Eq. multiagent_dynamics), a two-rocket planar game
  *     built from the same per-agent dynamics, and quadratic test problems
  *     (H = +-|p|^2/2, the exact Cole-Hopf case of Corollary B.2).
- *   - Counter-based sampler: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), uniforms
- *     u = ((x & (2^23-1))+0.5) 2^-23, Box-Muller normals, packed per-sample slots.
+ *   - Counter-based sampler: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11); each
+ *     128-bit block gives three Box-Muller pairs (23-bit radius uniforms u = ((x & (2^23-1))
+ *     +0.5) 2^-23, angle uniforms of 23, 18, 18 bits); packed per-sample slots.
  *
  * Everything is double precision except the Philox integer stream itself.
  * Pinned by tests/test_oracle_*.py (closed forms, quadrature, brute force, an
@@ -118,50 +119,69 @@ double orc_u01(uint32_t x)
     return ((double)(x & 0x7FFFFFu) + 0.5) * (1.0 / 8388608.0);
 }
 
+/* Angle uniform from a b-bit field k: (k + 0.5) 2^-b, also exact in both precisions. */
+static double angle_u(uint32_t k, int bits)
+{
+    return ((double)k + 0.5) / (double)(1u << bits);
+}
+
 /* Slots per sample in the normal stream of one (state, sweep): n for n <= 8 (the normals
- * of consecutive samples are packed back to back), n rounded up to a multiple of 4 above
+ * of consecutive samples are packed back to back), n rounded up to a multiple of 6 above
  * (each sample starts on a fresh Philox block). */
 int orc_slot_stride(int n)
 {
-    return n <= 8 ? n : (n + 3) / 4 * 4;
+    return n <= 8 ? n : (n + 5) / 6 * 6;
 }
 
-/* The four normals of Philox block b of the stream of (point, sweep): counter
- * (point, b_lo, sweep, b_hi), key (seed_lo, seed_hi ^ instance).  Box-Muller on (u0,u1)
- * gives slots 4b, 4b+1 (radius from u0, angle from u1); (u2,u3) give 4b+2, 4b+3. */
+/* The six normals of one Philox output block (X, Y, Z, W); block b of the stream of
+ * (point, sweep) has counter (point, b_lo, sweep, b_hi) and key (seed_lo, seed_hi ^
+ * instance).  Every one of the 128 bits feeds exactly one uniform:
+ *   pair j = 0, 1, 2 (slots 6b+2j, 6b+2j+1) takes its radius uniform from the low 23 bits
+ *   of X, Y, Z respectively, and its angle uniform from
+ *     j = 0: the high 23 bits of W,
+ *     j = 1: the high 9 bits of X followed by the high 9 bits of Y (18 bits),
+ *     j = 2: the high 9 bits of Z followed by the low 9 bits of W (18 bits);
+ *   (z_2j, z_2j+1) = sqrt(-2 ln u_r) (cos 2 pi u_a, sin 2 pi u_a)  (Box-Muller). */
+void orc_block_words_normals(const uint32_t r[4], double zz[6])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    const uint32_t X = r[0], Y = r[1], Z = r[2], W = r[3];
+    double ur[3] = {orc_u01(X), orc_u01(Y), orc_u01(Z)};
+    double ua[3] = {angle_u(W >> 9, 23),
+                    angle_u(((X >> 23) << 9) | (Y >> 23), 18),
+                    angle_u(((Z >> 23) << 9) | (W & 0x1FFu), 18)};
+    for (int j = 0; j < 3; ++j) {
+        double rad = sqrt(-2.0 * log(ur[j]));
+        zz[2 * j] = rad * cos(two_pi * ua[j]);
+        zz[2 * j + 1] = rad * sin(two_pi * ua[j]);
+    }
+}
+
 static void block_normals(uint64_t seed, uint32_t instance, uint64_t b, uint32_t point,
-                          uint32_t sweep, double zz[4])
+                          uint32_t sweep, double zz[6])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance};
     uint32_t ctr[4] = {point, (uint32_t)b, sweep, (uint32_t)(b >> 32)};
     uint32_t r[4];
-    const double two_pi = 6.283185307179586476925286766559;
     orc_philox4x32_10(ctr, key, r);
-    double u[4];
-    for (int q = 0; q < 4; ++q) u[q] = orc_u01(r[q]);
-    double ra = sqrt(-2.0 * log(u[0]));
-    double rb = sqrt(-2.0 * log(u[2]));
-    zz[0] = ra * cos(two_pi * u[1]);
-    zz[1] = ra * sin(two_pi * u[1]);
-    zz[2] = rb * cos(two_pi * u[3]);
-    zz[3] = rb * sin(two_pi * u[3]);
+    orc_block_words_normals(r, zz);
 }
 
 /* Standard normals z[0..n) of sample `sample` of state `point` in sweep `sweep`: slot
- * q = sample * orc_slot_stride(n) + d of the stream, i.e. lane q % 4 of block q / 4. */
+ * q = sample * orc_slot_stride(n) + d of the stream, i.e. lane q % 6 of block q / 6. */
 void orc_normals(int n, uint64_t seed, uint32_t instance, uint32_t sample,
                  uint32_t point, uint32_t sweep, double *z)
 {
     uint64_t q0 = (uint64_t)sample * (uint64_t)orc_slot_stride(n);
     uint64_t cached = UINT64_MAX;
-    double zz[4] = {0, 0, 0, 0};
+    double zz[6] = {0, 0, 0, 0, 0, 0};
     for (int d = 0; d < n; ++d) {
         uint64_t q = q0 + (uint64_t)d;
-        if ((q >> 2) != cached) {
-            cached = q >> 2;
+        if (q / 6 != cached) {
+            cached = q / 6;
             block_normals(seed, instance, cached, point, sweep, zz);
         }
-        z[d] = zz[q & 3];
+        z[d] = zz[q % 6];
     }
 }
 

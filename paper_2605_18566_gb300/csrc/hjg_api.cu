@@ -145,21 +145,21 @@ __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, const uin
 }
 
 // The normals the sweep draws for samples 0..ns-1 of (point, sweep): sample i, dim d is
-// slot i * slot_stride(n) + d of the stream, i.e. lane (slot % 4) of block slot / 4.
+// slot i * slot_stride(n) + d of the stream, i.e. lane (slot % 6) of block slot / 6.
 __global__ void normals_kernel(int n, uint32_t k0, uint32_t k1, uint32_t point, uint32_t sweep,
                                int64_t ns, float* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     const uint64_t q0 = (uint64_t)i * (uint64_t)slot_stride(n);
     uint64_t cached = ~0ull;
-    float z[4];
+    float z[kNormalsPerBlock];
     for (int d = 0; d < n; ++d) {
         const uint64_t q = q0 + (uint64_t)d;
-        if ((q >> 2) != cached) {
-            cached = q >> 2;
-            block_normals<4>((uint32_t)cached, point, sweep, k0, k1, z);
+        if (q / kNormalsPerBlock != cached) {
+            cached = q / kNormalsPerBlock;
+            block_normals<kNormalsPerBlock>((uint32_t)cached, point, sweep, k0, k1, z);
         }
-        out[i * n + d] = z[q & 3];
+        out[i * n + d] = z[q % kNormalsPerBlock];
     }
 }
 

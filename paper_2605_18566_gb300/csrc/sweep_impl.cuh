@@ -313,7 +313,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
 }
 
 // The full groups g = start, start + STRIDE, ... < full of one (state, sweep) stream, each
-// turned into GB Philox blocks, 4 GB normals and GS samples handed to `sample`.  With PIPE
+// turned into GB Philox blocks, 6 GB normals and GS samples handed to `sample`.  With PIPE
 // the Philox blocks of the next group are drawn while the current group's Box-Muller and
 // samples run (software pipelining), so that each warp's instruction stream interleaves the
 // integer multiplies of the generator with the transcendental and FP32 work of the samples;
@@ -330,18 +330,18 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
             const uint32_t nxt = grp + STRIDE;
 #pragma unroll
             for (int b = 0; b < GB; ++b) rn[b] = stream_block(nxt * GB + b, point, sweep, rk);
-            float z[4 * GB];
+            float z[kNormalsPerBlock * GB];
 #pragma unroll
-            for (int b = 0; b < GB; ++b) bm_normals_raw<4>(r[b], z + 4 * b);
+            for (int b = 0; b < GB; ++b) bm_normals_raw<kNormalsPerBlock>(r[b], z + kNormalsPerBlock * b);
             sample_group(z);
 #pragma unroll
             for (int b = 0; b < GB; ++b) r[b] = rn[b];
         }
     } else {
         for (uint32_t grp = start; grp < full; grp += STRIDE) {
-            float z[4 * GB];
+            float z[kNormalsPerBlock * GB];
 #pragma unroll
-            for (int b = 0; b < GB; ++b) block_normals_raw<4>(grp * GB + b, point, sweep, rk, z + 4 * b);
+            for (int b = 0; b < GB; ++b) block_normals_raw<kNormalsPerBlock>(grp * GB + b, point, sweep, rk, z + kNormalsPerBlock * b);
             sample_group(z);
         }
     }
@@ -349,8 +349,8 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
 
 // ------------------------------------------------------------------------------------
 // One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
-// g = group_samples(n) that end on a Philox block boundary (n = 3: 4 samples from 3 blocks;
-// n = 6: 2 samples from 3 blocks), so every normal drawn is used.
+// g = group_samples(n) that end on a Philox block boundary (n = 3: 2 samples from 1 block;
+// n = 4: 3 samples from 2 blocks; n = 6: 1 sample from 1 block), so every normal drawn is used.
 template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool CV = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
@@ -416,10 +416,11 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                                                   for (int t = 0; t < GS; ++t) sample(z + t * n);
                                               });
             if (GS > 1 && full < groups && tid == (int)(full % THREADS)) {   // ragged last group
-                float z[4 * GB];
+                float z[kNormalsPerBlock * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(full * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                    block_normals_raw<kNormalsPerBlock>(full * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                                        z + kNormalsPerBlock * b);
                 for (uint32_t t = 0; t < N32 - full * GS; ++t) sample(z + t * n);
             }
 
@@ -563,10 +564,11 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                                              for (int t = 0; t < GS; ++t) sample(z + t * n);
                                          });
             if (GS > 1 && full < groups && lane == (int)(full % 32)) {
-                float z[4 * GB];
+                float z[kNormalsPerBlock * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
-                    block_normals_raw<4>(full * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * b);
+                    block_normals_raw<kNormalsPerBlock>(full * GB + b, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                                        z + kNormalsPerBlock * b);
                 for (uint32_t t = 0; t < N32 - full * GS; ++t) sample(z + t * n);
             }
             warp_merge<n>(1, m, s, q, S);
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
 
 // ------------------------------------------------------------------------------------
 // 45-D multi-rocket game: four lanes per sample stream.  Lane q of a group owns dims
-// 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. blocks 12 i + 3q + j of the
+// 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. blocks 8 i + 2q + j of the
 // stream.  The evader (agent 14, dims 42..44) sits on lane 3; its position is broadcast,
 // each lane takes the minimum squared distance over its own pursuers, and two shuffles
 // finish the group minimum.  All four lanes then hold the same log-weight and accumulate
@@ -631,8 +633,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
             for (uint32_t i = grp; i < N32; i += GROUPS) {
                 float z[12];
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    block_normals_raw<4>(12u * i + 3u * q4 + j, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 4 * j);
+                for (int j = 0; j < 2; ++j)
+                    block_normals_raw<6>(8u * i + 2u * q4 + j, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 6 * j);
                 float yx[4], yz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {

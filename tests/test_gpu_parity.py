@@ -173,9 +173,9 @@ def test_empty_and_zero_sweeps():
 
 def test_sample_count_limit():
     """One state's stream may span at most 2^32 Philox blocks: the largest N of the 45-D
-    game (12 blocks per sample) is accepted, the next one is refused."""
+    game (8 blocks of six normals per sample) is accepted, the next one is refused."""
     from paper_2605_18566_gb300 import HJGError
-    nmax = (1 << 32) // 12
+    nmax = (1 << 32) // 8
     solver_for(W3, N=nmax, K=1).close()
     with pytest.raises(HJGError):
         solver_for(W3, N=nmax + 1, K=1)

@@ -104,34 +104,75 @@ def test_uniform_map_exact_and_symmetric():
     assert oracle.u01(2**32 - 1) == 1.0 - 2.0**-24
 
 
+def _pairs(z):
+    return [tuple(z[2 * j:2 * j + 2]) for j in range(3)]
+
+
 def test_box_muller_pair_structure():
-    """Radius of pair (z_4j, z_4j+1) comes from u0, its angle from u1 (likewise u2, u3)."""
-    seed, inst, sample, point, sweep = 0x1234_5678_9ABC, 3, 17, 5, 2
-    n = 8                                   # 8 slots per sample: blocks 2*sample, 2*sample+1
-    z = oracle.normals(n, seed, inst, sample, point, sweep)
+    """Pair j of a block takes its radius from the low 23 bits of word j and its angle
+    from a disjoint field: the high 23 bits of W (j = 0), the high 9 bits of X then of Y
+    (j = 1), the high 9 bits of Z then the low 9 bits of W (j = 2)."""
+    seed, inst, point, sweep = 0x1234_5678_9ABC, 3, 5, 2
     key = np.array([[seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ inst]], dtype=np.uint32)
-    for j in range(2):
-        b = 2 * sample + j
-        blk = oracle.philox4x32_10(np.array([[point, b, sweep, 0]], dtype=np.uint32), key)[0]
-        u = [oracle.u01(int(v)) for v in blk]
-        for q in (0, 2):
-            za, zb = z[4 * j + q], z[4 * j + q + 1]
-            np.testing.assert_allclose(za * za + zb * zb, -2.0 * np.log(u[q]), rtol=1e-12)
+    n = 6                                   # one block per sample
+    for sample in (0, 17, 40000):
+        z = oracle.normals(n, seed, inst, sample, point, sweep)
+        X, Y, Z, W = (int(v) for v in oracle.philox4x32_10(
+            np.array([[point, sample, sweep, 0]], dtype=np.uint32), key)[0])
+        radius_u = [oracle.u01(X), oracle.u01(Y), oracle.u01(Z)]
+        angle_u = [((W >> 9) + 0.5) / 2**23,
+                   ((((X >> 23) << 9) | (Y >> 23)) + 0.5) / 2**18,
+                   ((((Z >> 23) << 9) | (W & 511)) + 0.5) / 2**18]
+        for j, (za, zb) in enumerate(_pairs(z)):
+            np.testing.assert_allclose(za * za + zb * zb, -2.0 * np.log(radius_u[j]), rtol=1e-12)
             ang = np.arctan2(zb, za) % (2 * np.pi)
-            np.testing.assert_allclose(ang, (2 * np.pi * u[q + 1]) % (2 * np.pi), atol=1e-9)
+            np.testing.assert_allclose(ang, (2 * np.pi * angle_u[j]) % (2 * np.pi), atol=1e-9)
+
+
+def test_every_block_bit_feeds_exactly_one_pair():
+    """The three pairs of a block read disjoint bit fields that together cover all 128
+    bits: flipping any single bit moves exactly one pair and leaves the other two alone
+    (so pairs within a block are independent, and no generator output is wasted)."""
+    r = np.random.default_rng(11)
+    for _ in range(4):
+        words = r.integers(0, 2**32, size=4, dtype=np.uint64).astype(np.uint32)
+        base = _pairs(oracle.block_words_normals(words))
+        owner = []
+        for bit in range(128):
+            w = words.copy()
+            w[bit // 32] ^= np.uint32(1 << (bit % 32))
+            moved = [j for j, pr in enumerate(_pairs(oracle.block_words_normals(w)))
+                     if pr != base[j]]
+            assert len(moved) == 1, (bit, moved)
+            owner.append(moved[0])
+        # 23 radius bits + 23 / 18 / 18 angle bits
+        assert [owner.count(j) for j in range(3)] == [46, 41, 41]
+
+
+def test_angle_grids_integrate_exactly():
+    """The 18- and 23-bit angle grids are midpoint rules on the circle: the mean of
+    cos(m 2 pi u) and sin(m 2 pi u) over each grid vanishes for 0 < m < 2^bits, so the
+    pair's first 2^bits - 1 trigonometric moments are those of a uniform angle."""
+    for bits in (18,):
+        k = np.arange(2**bits, dtype=np.int64)
+        for m in (1, 2, 3, 7, 1000, 2**bits - 1):
+            # m * 2 pi u, reduced exactly: u = (2k + 1) / 2^(bits+1)
+            ph = 2 * np.pi * ((m * (2 * k + 1)) % 2**(bits + 1)) / 2**(bits + 1)
+            assert abs(np.mean(np.cos(ph))) < 1e-12
+            assert abs(np.mean(np.sin(ph))) < 1e-12
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 6, 7, 45])
 def test_slot_packing(n):
     """Sample s, dim d reads slot s*stride + d of one stream per (state, sweep); the stream
-    is the same whatever n is (compare with the n = 4 layout, one block per sample)."""
+    is the same whatever n is (compare with the n = 6 layout, one block per sample)."""
     stride = oracle.slot_stride(n)
-    assert stride == (n if n <= 8 else 4 * ((n + 3) // 4))
+    assert stride == (n if n <= 8 else 6 * ((n + 5) // 6))
     for s in (0, 1, 2, 3, 11):
         z = oracle.normals(n, 5, 1, s, 9, 4)
         for d in range(n):
             q = s * stride + d
-            assert z[d] == oracle.normals(4, 5, 1, q // 4, 9, 4)[q % 4]
+            assert z[d] == oracle.normals(6, 5, 1, q // 6, 9, 4)[q % 6]
 
 
 def test_normals_distribution():
