@@ -116,6 +116,30 @@ def test_quadratic_exact_case_and_negative_c():
         np.testing.assert_allclose(st["c"], h_sign / 0.2, rtol=1e-6)
 
 
+@pytest.mark.parametrize("n", [1, 2, 4, 8])
+@pytest.mark.parametrize("tilt", [False, True])
+def test_sample_group_remainders(n, tilt):
+    """A thread draws its samples in groups that end on a Philox block boundary (six
+    normals per block: groups of 6, 3, 3, 3 samples for n = 1, 2, 4, 8); every remainder of
+    N modulo the group, and N below one group, matches the oracle's slot-by-slot stream."""
+    from paper_2605_18566_gb300 import Solver
+    gs = {1: 6, 2: 3, 4: 3, 8: 3}[n]
+    A = hjg_inputs.spd_matrix(n, 0.3, 0.9, seed=11)
+    x0 = np.linspace(-0.3, 0.3, n); d = 0.2
+    x = hjg_inputs.random_states(40, n, 1.0, seed=12)
+    for N in sorted({1, gs - 1, 2} | {gs * 97 + r for r in range(gs)}):
+        if N < 1:
+            continue
+        s = Solver("quadratic", 0.1, 1.0, N, 2, n=n, A=A, x0=x0, d=d, tilt=tilt)
+        s.set_points(torch.from_numpy(x).cuda())
+        s.picard_sweep(2)
+        st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+        s.close()
+        P = oracle.make_problem("quadratic", n, 0.2, 1.0, A=A, x0=x0, d=d, tilt=tilt)
+        ref = oracle.picard(P, x.astype(np.float64), N, 2)
+        assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="n=%d N=%d" % (n, N))
+
+
 def test_zero_hamiltonian_parity():
     n = 2
     A = np.array([[0.8, 0.1], [0.1, 0.5]])
