@@ -4,21 +4,24 @@
 
 namespace hjg {
 namespace {
-template <int T, int B>
+// KIND bit 1: the software-pipelined sampler.
+template <int KIND, int T, int B>
 cudaError_t launch(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
-    if (tilt) sweep_kernel_r45<T, B, true><<<grid, T, 0, st>>>(A);
-    else sweep_kernel_r45<T, B, false><<<grid, T, 0, st>>>(A);
+    constexpr bool P = (KIND & 2) != 0;
+    if (tilt) sweep_kernel_r45<T, B, true, false, P><<<grid, T, 0, st>>>(A);
+    else sweep_kernel_r45<T, B, false, false, P><<<grid, T, 0, st>>>(A);
     return cudaGetLastError();
 }
-template <int T, int B>
+template <int KIND, int T, int B>
 int occupancy(bool tilt) {
+    constexpr bool P = (KIND & 2) != 0;
     int nb = 0;
-    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, true>, T, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, false>, T, 0);
+    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, true, false, P>, T, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, false, false, P>, T, 0);
     return nb;
 }
-#define R45_LAUNCH(i, KIND, T, B) case i: return launch<T, B>(A, tilt, grid, st);
-#define R45_OCC(i, KIND, T, B) case i: return occupancy<T, B>(tilt);
+#define R45_LAUNCH(i, KIND, T, B) case i: return launch<KIND, T, B>(A, tilt, grid, st);
+#define R45_OCC(i, KIND, T, B) case i: return occupancy<KIND, T, B>(tilt);
 // The control-variate kernel (tilted frame only): 256 threads, 1 CTA per SM minimum.
 cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
     if (v == kCvVariant) {

@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
 // each lane takes the minimum squared distance over its own pursuers, and two shuffles
 // finish the group minimum.  All four lanes then hold the same log-weight and accumulate
 // their own twelve S_j.
-template <int THREADS, int MINB, bool TILT, bool CV = false>
+template <int THREADS, int MINB, bool TILT, bool CV = false, bool PIPE = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArgs A) {
     static_assert(!CV || TILT, "the 45-D control variate runs in the tilted frame");
     using G = Rockets45;
@@ -630,11 +630,36 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
 #pragma unroll
             for (int j = 0; j < (CV ? 12 : 1); ++j) Z1[j] = 0.0f;
 
-            for (uint32_t i = grp; i < N32; i += GROUPS) {
-                float z[12];
+            // The shuffles below take the whole warp, so every lane runs the trip count of
+            // the warp's first group; a group whose sample index is past N draws (an unused
+            // block) and joins the shuffles but accumulates nothing.
+            // With PIPE the two Philox blocks of the next sample are drawn while the current
+            // sample's Box-Muller, distances and accumulation run (identical draws).
+            const uint32_t g_first = (uint32_t)(grp & ~7);
+            const uint32_t trips = N32 > g_first ? (N32 - g_first + GROUPS - 1) / GROUPS : 0u;
+            const uint32_t point = A.pt0 + (uint32_t)pt;
+            uint4 rb[2];
+            if constexpr (PIPE) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    block_normals_raw<6>(8u * i + 2u * q4 + j, A.pt0 + (uint32_t)pt, sweep, A.rk, z + 6 * j);
+                for (int j = 0; j < 2; ++j) rb[j] = stream_block(8u * (uint32_t)grp + 2u * q4 + j, point, sweep, A.rk);
+            }
+            for (uint32_t t = 0; t < trips; ++t) {
+                const uint32_t i = (uint32_t)grp + t * (uint32_t)GROUPS;
+                const bool live = i < N32;
+                float z[12];
+                if constexpr (PIPE) {
+                    const uint32_t nx = i + (uint32_t)GROUPS;
+                    uint4 rn[2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) rn[j] = stream_block(8u * nx + 2u * q4 + j, point, sweep, A.rk);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) bm_normals_raw<6>(rb[j], z + 6 * j);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) rb[j] = rn[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) block_normals_raw<6>(8u * i + 2u * q4 + j, point, sweep, A.rk, z + 6 * j);
+                }
                 float yx[4], yz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -661,10 +686,12 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
                     part += __shfl_xor_sync(0xffffffffu, part, 2);
                     a2 += part;
                 }
-                lse_accumulate<12>(a2, z, m, s, q, S);
-                if constexpr (CV) {
+                if (live) {
+                    lse_accumulate<12>(a2, z, m, s, q, S);
+                    if constexpr (CV) {
 #pragma unroll
-                    for (int j = 0; j < 12; ++j) Z1[j] += z[j];
+                        for (int j = 0; j < 12; ++j) Z1[j] += z[j];
+                    }
                 }
             }
 
@@ -754,9 +781,10 @@ cudaError_t launch_coef(const float* x, int64_t ldx, int64_t M, const float* p, 
     X(4, 0, 512, 1) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12) X(8, 2, 256, 4)      \
     X(9, 2, 128, 8) X(10, 3, 256, 4) X(11, 3, 128, 8)
 #define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 1) X(3, 0, 128, 4) \
-    X(4, 0, 512, 1) X(5, 0, 256, 3) X(6, 0, 256, 4) X(7, 0, 128, 6)
+    X(4, 0, 512, 1) X(5, 0, 256, 3) X(6, 0, 256, 4) X(7, 0, 128, 6) X(8, 2, 256, 2)      \
+    X(9, 2, 256, 3) X(10, 2, 128, 6)
 constexpr int kNumVariants = 12;
-constexpr int kNumR45Variants = 8;
+constexpr int kNumR45Variants = 11;
 
 template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {

@@ -24,8 +24,10 @@ def _state(s):
 
 @pytest.mark.parametrize("w,M,N,tilt", [(W1, 1024, 4096, False), (W1, 1024, 4096, True),
                                         (W2, 211, 16384, False), (W2, 211, 16384, True),
-                                        (hjg_inputs.ROCKETS45, 24, 8192, True)],
-                         ids=["dubins3", "dubins3-tilt", "rockets6", "rockets6-tilt", "rockets45-tilt"])
+                                        (hjg_inputs.ROCKETS45, 24, 8192, True),
+                                        (hjg_inputs.ROCKETS45, 24, 1000, True)],
+                         ids=["dubins3", "dubins3-tilt", "rockets6", "rockets6-tilt", "rockets45-tilt",
+                              "rockets45-tilt-ragged-N"])
 def test_cv_one_sweep_parity(w, M, N, tilt):
     xn = hjg_inputs.points(w, M=M)
     x = torch.from_numpy(xn).cuda()

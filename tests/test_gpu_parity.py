@@ -140,6 +140,22 @@ def test_sample_group_remainders(n, tilt):
         assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="n=%d N=%d" % (n, N))
 
 
+@pytest.mark.parametrize("variant", [0, 2, 4], ids=["256thr", "128thr", "512thr"])
+@pytest.mark.parametrize("tilt", [False, True])
+def test_rockets45_sample_counts_off_the_group_grid(variant, tilt):
+    """The 45-D kernel runs four lanes per sample and THREADS / 4 samples per CTA pass, with
+    warp-wide shuffles inside the sample loop: N below, and not a multiple of, the number
+    of sample groups per CTA (32, 64, 128) must give the oracle's result on every state."""
+    x = hjg_inputs.points(W3, M=6)
+    for N in (1, 7, 100, 1000):
+        st0, st, r, sup, hist = run_gpu(W3, x, N, 1, variant=variant, tilt=tilt)
+        c0 = st0["c"].astype(np.float64)
+        theta = -W3.sigma2 * c0[:, None] * st0["p"].astype(np.float64) if tilt else None
+        v, p, ess = oracle.sweep(problem_for(W3), x.astype(np.float64), c0, N, 0, theta=theta)
+        assert_parity(st["v"], st["p"], v, p, what="45-D N=%d variant %d" % (N, variant))
+        np.testing.assert_allclose(st["ess"], ess, rtol=1e-3)
+
+
 def test_zero_hamiltonian_parity():
     n = 2
     A = np.array([[0.8, 0.1], [0.1, 0.5]])
