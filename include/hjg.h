@@ -285,7 +285,9 @@ hjg_status hjg_sample_normals(int n, uint64_t seed, uint32_t instance, uint32_t 
  * (ld >= 4; components 0..2 position, 3 heading), idx_out [M][k] int32 receives the k
  * nearest other agents (exact, squared FP32 distance, ties by index) and psibar_out [M]
  * FP32 (or NULL) the circular mean atan2(sum sin psi_j, sum cos psi_j) of their headings.
- * k must be 7; device pointers; asynchronous on stream. */
+ * A NaN distance (a non-finite position) never qualifies: where fewer than k other agents
+ * remain, the empty slots hold -1 and psibar is NaN (a solve then reports that agent as
+ * non-finite).  k must be 7; device pointers; asynchronous on stream. */
 hjg_status hjg_flock_neighbours(const float *states, int64_t M, int64_t ld, int k, int32_t *idx_out,
                                 float *psibar_out, void *stream);
 

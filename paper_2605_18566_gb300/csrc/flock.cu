@@ -17,7 +17,9 @@ constexpr int kKnnThreads = 256;
 constexpr int kKnnTile = 1024;
 
 // Exact k nearest neighbours (k = K) of each agent among all others, ordered by squared
-// distance (FP32) and then by index.  One thread per query agent.
+// distance (FP32) and then by index.  One thread per query agent.  A NaN distance (a
+// non-finite position on either side) never enters the list, so a slot can stay empty;
+// it is written as -1.
 template <int K>
 __global__ void __launch_bounds__(kKnnThreads) knn_kernel(const float* __restrict__ x, int64_t ldx,
                                                           int64_t M, int32_t* __restrict__ idx) {
@@ -64,11 +66,12 @@ __global__ void __launch_bounds__(kKnnThreads) knn_kernel(const float* __restric
     }
     if (active)
 #pragma unroll
-        for (int t = 0; t < K; ++t) idx[i * K + t] = bi[t];
+        for (int t = 0; t < K; ++t) idx[i * K + t] = bi[t] < M ? bi[t] : -1;
 }
 
 // psibar (FP64 circular mean of the neighbours' headings, state component 3) and the
-// per-agent game data: the K neighbour positions followed by psibar.
+// per-agent game data: the K neighbour positions followed by psibar.  An empty slot (-1)
+// gives NaN there and in psibar, so the agent's solve is reported as non-finite.
 template <int K>
 __global__ void flock_aux_kernel(const float* __restrict__ x, int64_t ldx, int64_t M,
                                  const int32_t* __restrict__ idx, float* __restrict__ psibar,
@@ -76,8 +79,15 @@ __global__ void flock_aux_kernel(const float* __restrict__ x, int64_t ldx, int64
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     double ss = 0.0, cs = 0.0;
+    bool empty = false;
     for (int t = 0; t < K; ++t) {
         const int64_t j = idx[i * K + t];
+        if (j < 0 || j >= M) {
+            empty = true;
+            if (aux)
+                for (int a = 0; a < 3; ++a) aux[i * ldaux + 3 * t + a] = NAN;
+            continue;
+        }
         double s, c;
         sincos((double)x[j * ldx + 3], &s, &c);
         ss += s;
@@ -85,7 +95,7 @@ __global__ void flock_aux_kernel(const float* __restrict__ x, int64_t ldx, int64
         if (aux)
             for (int a = 0; a < 3; ++a) aux[i * ldaux + 3 * t + a] = x[j * ldx + a];
     }
-    const float pb = (float)atan2(ss, cs);
+    const float pb = empty ? NAN : (float)atan2(ss, cs);
     if (psibar) psibar[i] = pb;
     if (aux) aux[i * ldaux + 3 * K] = pb;
 }

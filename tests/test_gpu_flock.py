@@ -47,3 +47,43 @@ def test_flock_full_size_sampled():
     x = hjg_inputs.points(W)
     idx = hjg_inputs.subset_indices(W.M, 24, seed=8)
     check_trajectory(W, x, W.N, 3, idx=idx, min_pass=0.9)
+
+
+def test_neighbours_and_solve_with_non_finite_agents():
+    """A NaN position never qualifies as a neighbour: other agents' lists skip it, its own
+    list is empty (-1, psibar NaN), and where fewer than 7 finite agents remain the empty
+    slots are -1.  A solve reports such agents as non-finite and leaves the rest finite."""
+    from paper_2605_18566_gb300 import _lib, flock_neighbours
+    from helpers import solver_for
+    x = hjg_inputs.flock_states(100, seed=4)
+    x[5, 0] = np.nan
+    idx, pb = flock_neighbours(torch.from_numpy(x).cuda())
+    idx = idx.cpu().numpy(); pb = pb.cpu().numpy()
+    assert np.all(idx[5] == -1) and np.isnan(pb[5])
+    pos = x[:, :3].astype(np.float64)
+    for i in range(100):
+        if i == 5:
+            continue
+        d = np.linalg.norm(pos - pos[i], axis=1)
+        d[i] = np.inf; d[5] = np.inf
+        assert 5 not in idx[i] and np.all(idx[i] >= 0)
+        np.testing.assert_allclose(np.sort(d[idx[i]]), np.sort(d)[:7], rtol=1e-5)
+        assert np.isfinite(pb[i])
+    y = hjg_inputs.flock_states(12, seed=6)
+    y[:6, 1] = np.nan
+    idx2, pb2 = flock_neighbours(torch.from_numpy(y).cuda())
+    idx2 = idx2.cpu().numpy(); pb2 = pb2.cpu().numpy()
+    assert np.all(idx2[:6] == -1)
+    for i in range(6, 12):   # five finite others, then two empty slots
+        assert sorted(idx2[i][:5]) == sorted(j for j in range(6, 12) if j != i)
+        assert np.all(idx2[i][5:] == -1) and np.isnan(pb2[i])
+    s = solver_for(W, N=1024, K=2)
+    s.set_points(torch.from_numpy(x).cuda())
+    s.picard_sweep(2)
+    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    status = s.last_status
+    s.close()
+    assert status == _lib.HJG_ENONFINITE
+    assert not np.isfinite(st["v"][5])
+    keep = np.arange(100) != 5
+    assert np.all(np.isfinite(st["v"][keep])) and np.all(np.isfinite(st["p"][keep]))
