@@ -318,7 +318,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
 // samples run (software pipelining), so that each warp's instruction stream interleaves the
 // integer multiplies of the generator with the transcendental and FP32 work of the samples;
 // the one group drawn past the end is discarded.  Both forms consume identical draws.
-template <int GS, int GB, int STRIDE, bool PIPE, class F>
+template <int GS, int GB, int STRIDE, bool PIPE, bool UNR2, class F>
 __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32_t point, uint32_t sweep,
                                            const PhiloxKeys& rk, F&& sample_group) {
     if constexpr (PIPE) {
@@ -338,7 +338,21 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
             for (int b = 0; b < GB; ++b) r[b] = rn[b];
         }
     } else {
-        for (uint32_t grp = start; grp < full; grp += STRIDE) {
+        uint32_t grp = start;
+        if constexpr (UNR2) {   // two independent groups per iteration (more work in flight)
+            for (; grp + STRIDE < full; grp += 2 * STRIDE) {
+                float z[kNormalsPerBlock * GB], y[kNormalsPerBlock * GB];
+#pragma unroll
+                for (int b = 0; b < GB; ++b) {
+                    block_normals_raw<kNormalsPerBlock>(grp * GB + b, point, sweep, rk, z + kNormalsPerBlock * b);
+                    block_normals_raw<kNormalsPerBlock>((grp + STRIDE) * GB + b, point, sweep, rk,
+                                                        y + kNormalsPerBlock * b);
+                }
+                sample_group(z);
+                sample_group(y);
+            }
+        }
+        for (; grp < full; grp += STRIDE) {
             float z[kNormalsPerBlock * GB];
 #pragma unroll
             for (int b = 0; b < GB; ++b) block_normals_raw<kNormalsPerBlock>(grp * GB + b, point, sweep, rk, z + kNormalsPerBlock * b);
@@ -351,7 +365,7 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
 // One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
 // g = group_samples(n) that end on a Philox block boundary (n = 3: 2 samples from 1 block;
 // n = 4: 3 samples from 2 blocks; n = 6: 1 sample from 1 block), so every normal drawn is used.
-template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool CV = false>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool CV = false, bool UNR2 = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int NPAD = (n + 3) / 4 * 4;
@@ -410,7 +424,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                     }
                 }
             };
-            run_groups<GS, GB, THREADS, PIPE>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+            run_groups<GS, GB, THREADS, PIPE, UNR2>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
                                               [&](const float* z) {
 #pragma unroll
                                                   for (int t = 0; t < GS; ++t) sample(z + t * n);
@@ -500,7 +514,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, const Sig& sig, i
 // FP64 recovery and coefficient update and broadcasts the new (c, Dv) with shuffles.
 // No CTA barrier is involved, so a warp never waits for another state's epilogue.
 // Chosen by the autotuner when there are many more states than warps in flight.
-template <class G, int THREADS, int MINB, bool TILT, bool PIPE>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool UNR2 = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int GS = group_samples(n);
@@ -558,7 +572,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 }
                 lse_accumulate<n>(a, zt, m, s, q, S);
             };
-            run_groups<GS, GB, 32, PIPE>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+            run_groups<GS, GB, 32, PIPE, UNR2>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
                                          [&](const float* z) {
 #pragma unroll
                                              for (int t = 0; t < GS; ++t) sample(z + t * n);
@@ -775,10 +789,11 @@ cudaError_t launch_coef(const float* x, int64_t ldx, int64_t M, const float* p, 
 }
 
 // Launch variants the autotuner chooses among: kind bit 0 = one warp per state (else one
-// CTA per state), kind bit 1 = software-pipelined sampler; CTA size; minimum resident CTAs
-// per SM (the register budget).  Every game's translation unit instantiates all of them.
-#define HJG_SWEEP_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 5) X(2, 0, 256, 6) X(3, 0, 128, 1) \
-    X(4, 0, 512, 1) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12) X(8, 2, 256, 4)      \
+// CTA per state), bit 1 = software-pipelined sampler, bit 2 = two sample groups per loop
+// iteration; CTA size; minimum resident CTAs per SM (the register budget).  Every game's
+// translation unit instantiates all of them.
+#define HJG_SWEEP_VARIANTS(X) X(0, 4, 128, 8) X(1, 0, 256, 5) X(2, 0, 256, 6) X(3, 0, 128, 1) \
+    X(4, 5, 128, 8) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12) X(8, 2, 256, 4)      \
     X(9, 2, 128, 8) X(10, 3, 256, 4) X(11, 3, 128, 8)
 #define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 1) X(3, 0, 128, 4) \
     X(4, 0, 512, 1) X(5, 0, 256, 3) X(6, 0, 256, 4) X(7, 0, 128, 6) X(8, 2, 256, 2)      \
@@ -788,13 +803,13 @@ constexpr int kNumR45Variants = 11;
 
 template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
-    constexpr bool PIPE = (KIND & 2) != 0;
+    constexpr bool PIPE = (KIND & 2) != 0, U2 = (KIND & 4) != 0;
     if constexpr ((KIND & 1) != 0) {
-        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true, PIPE><<<grid, THREADS, 0, st>>>(A);
-        else sweep_kernel_warp<G, THREADS, MINB, false, PIPE><<<grid, THREADS, 0, st>>>(A);
+        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true, PIPE, U2><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel_warp<G, THREADS, MINB, false, PIPE, U2><<<grid, THREADS, 0, st>>>(A);
     } else {
-        if (tilt) sweep_kernel<G, THREADS, MINB, true, PIPE><<<grid, THREADS, 0, st>>>(A);
-        else sweep_kernel<G, THREADS, MINB, false, PIPE><<<grid, THREADS, 0, st>>>(A);
+        if (tilt) sweep_kernel<G, THREADS, MINB, true, PIPE, false, U2><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel<G, THREADS, MINB, false, PIPE, false, U2><<<grid, THREADS, 0, st>>>(A);
     }
     return cudaGetLastError();
 }
@@ -819,13 +834,13 @@ int occupancy_cv(bool tilt) {
 template <class G, int KIND, int THREADS, int MINB>
 int occupancy_generic(bool tilt) {
     int nb = 0;
-    constexpr bool PIPE = (KIND & 2) != 0;
+    constexpr bool PIPE = (KIND & 2) != 0, U2 = (KIND & 4) != 0;
     if constexpr ((KIND & 1) != 0) {
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true, PIPE>, THREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false, PIPE>, THREADS, 0);
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true, PIPE, U2>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false, PIPE, U2>, THREADS, 0);
     } else {
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true, PIPE>, THREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false, PIPE>, THREADS, 0);
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true, PIPE, false, U2>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false, PIPE, false, U2>, THREADS, 0);
     }
     return nb;
 }

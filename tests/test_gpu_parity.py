@@ -174,7 +174,7 @@ def test_zero_hamiltonian_parity():
 
 # ------------------------------------------------------------------------------ edges
 @pytest.mark.parametrize("M,N,threads", [(1, 1, 0), (5, 31, 0), (17, 1000, 128),
-                                         (130, 777, 512), (3, 257, 256)])
+                                         (130, 777, 256), (3, 257, 256)])
 def test_ragged_sizes(M, N, threads):
     w = W1
     x = hjg_inputs.points(w)[7:7 + M].copy()
