@@ -462,15 +462,18 @@ __global__ void feature_stats_kernel(const float* __restrict__ v, int64_t ld, in
 }
 
 // Loss and its gradient w.r.t. the outputs: L = mean_b[(o_0 - y_0)^2 + mean_j (o_j - y_j)^2]
-// over j = 1..n_out-1, with the targets standardised like the outputs (y - shift) / mul.  dO (BF16) is written for the backward GEMMs; the per-block partial
-// sums of L go to partial[blockIdx.x] (reduced in a fixed order on the host side).
-__global__ void loss_grad_kernel(const float* __restrict__ out, int64_t ldo, const float* __restrict__ y,
-                                 int64_t ldy, int64_t B, int n_out, int out_pad, const float* __restrict__ oscal,
-                                 __nv_bfloat16* __restrict__ dO, float* __restrict__ dOf,
-                                 double* __restrict__ partial) {
-    __shared__ double red[256];
+// over j = 1..n_out-1, with the targets standardised like the outputs (y - shift) / mul.
+// dO (BF16) is written for the backward GEMMs; each block sums its elements' loss terms in
+// FP32 (warp shuffles, then the 8 warps) and writes the sum / B to partial[blockIdx.x]
+// (added in a fixed order on the host).  Launched with 256 threads.
+__global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict__ out, int64_t ldo,
+                                                         const float* __restrict__ y, int64_t ldy, int64_t B,
+                                                         int n_out, int out_pad, const float* __restrict__ oscal,
+                                                         __nv_bfloat16* __restrict__ dO, float* __restrict__ dOf,
+                                                         double* __restrict__ partial) {
+    __shared__ float red[8];
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double l = 0.0;
+    float l = 0.0f;   // w d^2 of this element; the block's sum is divided by B in FP64
     if (e < B * out_pad) {
         const int64_t b = e / out_pad;
         const int j = (int)(e % out_pad);
@@ -478,19 +481,22 @@ __global__ void loss_grad_kernel(const float* __restrict__ out, int64_t ldo, con
         if (j < n_out) {
             const float d = out[b * ldo + j] - (y[b * ldy + j] - oscal[j]) / oscal[out_pad + j];
             const float w = j == 0 ? 1.0f : 1.0f / (float)(n_out - 1);
-            l = (double)w * (double)d * (double)d / (double)B;
+            l = w * d * d;
             g = 2.0f * w * d / (float)B;
         }
         dO[e] = __float2bfloat16(g);
         if (dOf) dOf[e] = g;
     }
-    red[threadIdx.x] = l;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += red[w];
+        partial[blockIdx.x] = (double)t / (double)B;
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
 // dZ = dH * SiLU'(Z), SiLU'(z) = s (1 + z (1 - s)), s = sigmoid(z); BF16 out.
@@ -650,7 +656,7 @@ struct hjg_mlp {
 
 namespace {
 
-constexpr int kSplits = 16;
+constexpr int kSplits = 32;
 
 hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
     if (B <= m->cap) return HJG_OK;
