@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
         ok = __syncthreads_and(ok) != 0;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: row r = 32 warp + lane, 8 columns per tcgen05.ld
+    // epilogue: row r = 32 warp + lane; per pass of 32 columns the bias and (kEpiSiluBwd)
+    // pre-activation loads are issued first, then four tcgen05.ld of 8 columns and one
+    // wait, so the global-memory and TMEM latencies overlap instead of adding up per
+    // 8 columns.
     const int r = warp * 32 + lane;
     const int m = m0 + r;
     float* C = g.C ? g.C + (int64_t)blockIdx.z * g.M * g.ldc : nullptr;
@@ -224,72 +227,91 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     const bool vecH = (g.ldh % 8) == 0 && ((uintptr_t)g.H & 15) == 0;
     const bool vecZ = EPI == kEpiSiluBwd && (g.ldz % 4) == 0 && ((uintptr_t)g.Zin & 15) == 0;
     constexpr bool kH = EPI == kEpiBiasSilu || EPI == kEpiSiluBwd;
+    constexpr bool kBias = EPI == kEpiBiasSilu || EPI == kEpiBias;
+    constexpr int kPass = 32;
     if (ok && nch > 0) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTcN; c0 += 8) {
-            uint32_t v[8];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m >= g.M) continue;
-            const int nb = n0 + c0;
-            const bool full = nb + 8 <= g.N;
-            float x[8];
+        for (int p0 = 0; p0 < kTcN; p0 += kPass) {
+            const int np = n0 + p0;
+            float pre[kPass];   // bias (kBias) or pre-activation Z (kEpiSiluBwd) of the pass
+            if (kBias) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                x[j] = __uint_as_float(v[j]);
-                if ((EPI == kEpiBiasSilu || EPI == kEpiBias) && nb + j < g.N) x[j] += g.bias[nb + j];
-            }
-            if (EPI == kEpiSiluBwd) {   // dZ = dH silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)
-                float z[8];
-                if (full && vecZ) {
-                    const float4* zp = reinterpret_cast<const float4*>(g.Zin + (int64_t)m * g.ldz + nb);
-                    const float4 a = zp[0], b = zp[1];
-                    z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w; z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+                for (int j = 0; j < kPass; ++j) pre[j] = np + j < g.N ? g.bias[np + j] : 0.0f;
+            } else if (EPI == kEpiSiluBwd) {
+                if (m < g.M && np + kPass <= g.N && vecZ) {
+                    const float4* zp = reinterpret_cast<const float4*>(g.Zin + (int64_t)m * g.ldz + np);
+#pragma unroll
+                    for (int q = 0; q < kPass / 4; ++q) {
+                        const float4 t = zp[q];
+                        pre[4 * q] = t.x; pre[4 * q + 1] = t.y; pre[4 * q + 2] = t.z; pre[4 * q + 3] = t.w;
+                    }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) z[j] = nb + j < g.N ? g.Zin[(int64_t)m * g.ldz + nb + j] : 0.0f;
+                    for (int j = 0; j < kPass; ++j)
+                        pre[j] = (m < g.M && np + j < g.N) ? g.Zin[(int64_t)m * g.ldz + np + j] : 0.0f;
                 }
+            }
+            uint32_t v[kPass];
+#pragma unroll
+            for (int q = 0; q < kPass / 8; ++q)
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                    : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
+                      "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p0 + 8 * q)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int q = 0; q < kPass / 8; ++q) {
+                const int nb = np + 8 * q;
+                const bool full = nb + 8 <= g.N;
+                float x[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float sg = 1.0f / (1.0f + __expf(-z[j]));
-                    x[j] = x[j] * sg * (1.0f + z[j] * (1.0f - sg));
+                    x[j] = __uint_as_float(v[8 * q + j]);
+                    if (kBias) x[j] += pre[8 * q + j];
                 }
-            }
-            __align__(16) __nv_bfloat16 h[8];
-            if (kH) {
+                if (EPI == kEpiSiluBwd) {   // dZ = dH silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(EPI == kEpiBiasSilu ? silu(x[j]) : x[j]);
-            }
-            if (full) {
-                if (C && vecC) {
-                    float4* d = reinterpret_cast<float4*>(C + (int64_t)m * g.ldc + nb);
-                    d[0] = make_float4(x[0], x[1], x[2], x[3]);
-                    d[1] = make_float4(x[4], x[5], x[6], x[7]);
-                } else if (C) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) C[(int64_t)m * g.ldc + nb + j] = x[j];
+                    for (int j = 0; j < 8; ++j) {
+                        const float z = pre[8 * q + j];
+                        const float sg = 1.0f / (1.0f + __expf(-z));
+                        x[j] = x[j] * sg * (1.0f + z * (1.0f - sg));
+                    }
                 }
+                __align__(16) __nv_bfloat16 h[8];
                 if (kH) {
-                    if (vecH) {
-                        *reinterpret_cast<uint4*>(g.H + (int64_t)m * g.ldh + nb) = *reinterpret_cast<const uint4*>(h);
-                    } else {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
-                    }
-                    if (g.Ht) {   // transposed copy: the lanes of a warp write consecutive m
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
-                    }
+                    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(EPI == kEpiBiasSilu ? silu(x[j]) : x[j]);
                 }
-            } else {
-                for (int j = 0; j < 8 && nb + j < g.N; ++j) {
-                    if (C) C[(int64_t)m * g.ldc + nb + j] = x[j];
+                if (full) {
+                    if (C && vecC) {
+                        float4* d = reinterpret_cast<float4*>(C + (int64_t)m * g.ldc + nb);
+                        d[0] = make_float4(x[0], x[1], x[2], x[3]);
+                        d[1] = make_float4(x[4], x[5], x[6], x[7]);
+                    } else if (C) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) C[(int64_t)m * g.ldc + nb + j] = x[j];
+                    }
                     if (kH) {
-                        g.H[(int64_t)m * g.ldh + nb + j] = h[j];
-                        if (g.Ht) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
+                        if (vecH) {
+                            *reinterpret_cast<uint4*>(g.H + (int64_t)m * g.ldh + nb) = *reinterpret_cast<const uint4*>(h);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
+                        }
+                        if (g.Ht) {   // transposed copy: the lanes of a warp write consecutive m
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
+                        }
+                    }
+                } else {
+                    for (int j = 0; j < 8 && nb + j < g.N; ++j) {
+                        if (C) C[(int64_t)m * g.ldc + nb + j] = x[j];
+                        if (kH) {
+                            g.H[(int64_t)m * g.ldh + nb + j] = h[j];
+                            if (g.Ht) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
+                        }
                     }
                 }
             }
