@@ -104,14 +104,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err
     return false;
 }
 
-// Two-stage pipeline: while the tensor core multiplies chunk c from one shared-memory
-// stage, the CTA's threads copy chunk c + 1 into the other with 16-byte cp.async (global
-// -> shared, bypassing L1); a stage is overwritten only after the commit of the MMAs that
-// read it has arrived on that stage's mbarrier.  Both operands are K-major in global memory
-// (A(m, k) = A[m lda + k], B(k, n) = Bt[n ldb + k], lda and ldb multiples of 8, rows
-// 16-byte aligned); gemm() packs other layouts first.
+// S-stage pipeline: the copies of chunks c + 1 .. c + S - 1 (16-byte cp.async, global ->
+// shared, bypassing L1) are in flight while the tensor core multiplies chunk c; a stage is
+// overwritten only after the commit of the MMAs that read it has arrived on that stage's
+// mbarrier.  S = 4 when a CTA's K range has at most four chunks and the grid fits in one
+// wave at two CTAs per SM (every GEMM of the width-256 network at batch 8,192, which then
+// issues all its loads at once: measured 5 % faster), else S = 2 (four CTAs per SM for
+// long K ranges and multi-wave grids: measured 6 % faster at batch 32,768).  Both operands are K-major in global memory (A(m, k) = A[m lda + k], B(k, n) =
+// Bt[n ldb + k], lda and ldb multiples of 8, rows 16-byte aligned); gemm() packs other
+// layouts first.
 constexpr int kTcStage = (kTcM + kTcN) * kTcK * 2;   // bytes of one stage (A then B)
-constexpr int kTcSmem = 2 * kTcStage;
+constexpr int tc_smem(int stages) { return stages * kTcStage; }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
@@ -136,25 +139,24 @@ __device__ __forceinline__ void load_chunk(uint32_t dst, const __nv_bfloat16* sr
     }
 }
 
-template <int EPI>
+template <int EPI, int kTcStages>
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
     const int kbeg = blockIdx.z * g.kper, kend = min(g.K, kbeg + g.kper);
     const int nch = kend > kbeg ? (kend - kbeg + kTcK - 1) / kTcK : 0;
     const uint32_t s0 = smem_u32(smem);
-    const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&tmem_base)), "r"(kTcN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar1));
+#pragma unroll
+        for (int i = 0; i < kTcStages; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[i])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -162,31 +164,38 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = umma_idesc_bf16(kTcM, kTcN);
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase[kTcStages] = {};   // parity of the next completion to wait for, per stage
     bool ok = true;
-    if (nch > 0) {
-        load_chunk<kTcM>(s0, g.A, g.sam, m0, g.M, kbeg, kend, tid);
-        load_chunk<kTcN>(s0 + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, kbeg, kend, tid);
+    // cp.async group i holds chunk i: the prologue commits chunks 0 .. S-2 (empty groups past
+    // the last chunk keep the count uniform), iteration c commits chunk c + S - 1.
+#pragma unroll
+    for (int c = 0; c < kTcStages - 1; ++c) {
+        if (c < nch) {
+            const uint32_t st = s0 + (uint32_t)(c * kTcStage);
+            const int k0 = kbeg + c * kTcK;
+            load_chunk<kTcM>(st, g.A, g.sam, m0, g.M, k0, kend, tid);
+            load_chunk<kTcN>(st + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, k0, kend, tid);
+        }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     for (int c = 0; c < nch && ok; ++c) {
-        const int s = c & 1;
-        if (c + 1 < nch) {
-            if (c >= 1) {   // the MMAs of chunk c - 1 read stage s ^ 1: wait for them
-                ok = mbar_wait(s ? bar0 : bar1, phase[s ^ 1], err);
-                phase[s ^ 1] ^= 1u;
+        const int s = c % kTcStages;
+        const int cn = c + kTcStages - 1;
+        if (cn < nch) {
+            const int sn = cn % kTcStages;   // the stage chunk c - 1 used
+            if (c >= 1) {   // its MMAs must be done before the stage is overwritten
+                ok = mbar_wait(smem_u32(&mbar[sn]), phase[sn], err);
+                phase[sn] ^= 1u;
                 ok = __syncthreads_and(ok) != 0;
                 if (!ok) break;
             }
-            const uint32_t st = s0 + (uint32_t)((s ^ 1) * kTcStage);
-            const int k0 = kbeg + (c + 1) * kTcK;
+            const uint32_t st = s0 + (uint32_t)(sn * kTcStage);
+            const int k0 = kbeg + cn * kTcK;
             load_chunk<kTcM>(st, g.A, g.sam, m0, g.M, k0, kend, tid);
             load_chunk<kTcN>(st + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, k0, kend, tid);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" :: "n"(kTcStages - 1) : "memory");   // chunk c has landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -204,14 +213,14 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(s ? bar1 : bar0) : "memory");
+                         :: "r"(smem_u32(&mbar[s])) : "memory");
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // nothing left in flight on any path
     if (nch > 0) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");   // nothing left in flight on any path
         if (ok) {   // the last commit covers every earlier MMA of this thread
-            const int s = (nch - 1) & 1;
-            ok = mbar_wait(s ? bar1 : bar0, phase[s], err);
+            const int s = (nch - 1) % kTcStages;
+            ok = mbar_wait(smem_u32(&mbar[s]), phase[s], err);
         }
         ok = __syncthreads_and(ok) != 0;
     }
@@ -370,18 +379,31 @@ inline int64_t gemm_scratch_b(const GemmArgs& g) {
     return ok ? 0 : (int64_t)g.N * pad8(g.K);
 }
 
-template <int EPI>
-cudaError_t launch_tc(const GemmArgs& k, int splits, cudaStream_t st) {
-    static bool attr = false;   // opt in to 64 KB of dynamic shared memory once per process
+template <int EPI, int S>
+cudaError_t launch_tc_s(const GemmArgs& k, int splits, cudaStream_t st) {
+    static bool attr = false;   // opt in to the dynamic shared memory once per process
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kTcSmem);
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<EPI, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tc_smem(S));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((k.N + kTcN - 1) / kTcN, (k.M + kTcM - 1) / kTcM, splits);
-    gemm_tc_kernel<EPI><<<grid, 128, kTcSmem, st>>>(k, g_tc_err);
+    gemm_tc_kernel<EPI, S><<<grid, 128, tc_smem(S), st>>>(k, g_tc_err);
     return cudaGetLastError();
+}
+template <int EPI>
+cudaError_t launch_tc(const GemmArgs& k, int splits, cudaStream_t st) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    const int64_t ctas = (int64_t)((k.N + kTcN - 1) / kTcN) * ((k.M + kTcM - 1) / kTcM) * splits;
+    const bool deep = k.kper <= 4 * kTcK && ctas <= 2 * (int64_t)sms;   // one wave at 2 CTAs per SM
+    return deep ? launch_tc_s<EPI, 4>(k, splits, st) : launch_tc_s<EPI, 2>(k, splits, st);
 }
 
 // C = A B (+ epilogue) on the tensor cores.  Operands that are not K-major with aligned
