@@ -554,7 +554,9 @@ __global__ void silu_backward_kernel(const float* __restrict__ dH, const float* 
 }
 
 // Sum of `splits` partial weight gradients [splits][rows][cols] into grad (FP32), and the
-// bias gradient (column sums of dZ over the batch) for this layer.
+// bias gradient (column sums of dZ over the batch) for this layer; the splits are added in
+// order, one element per thread (a float4 form with a quarter of the threads measured 10 %
+// slower over a training step).
 __global__ void reduce_wgrad_kernel(const float* __restrict__ part, int splits, int64_t n,
                                     float* __restrict__ grad) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -562,6 +564,11 @@ __global__ void reduce_wgrad_kernel(const float* __restrict__ part, int splits, 
     float s = 0.0f;
     for (int k = 0; k < splits; ++k) s += part[(int64_t)k * n + e];
     grad[e] = s;
+}
+
+inline cudaError_t reduce_wgrad(const float* part, int splits, int64_t n, float* grad, cudaStream_t st) {
+    reduce_wgrad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, splits, n, grad);
+    return cudaGetLastError();
 }
 
 // Bias gradient = column sums of dZ [B][cols], first stage: CTA (x, y) sums 32 columns
@@ -809,12 +816,13 @@ cudaError_t mlp_backward(hjg_mlp* m, int64_t B) {
         e = gemm(gw, kEpiStore, kSplits, m->stream);
         if (e != cudaSuccess) break;
         const int64_t nw = (int64_t)rows * cols;
-        reduce_wgrad_kernel<<<nblk(nw), 256, 0, m->stream>>>(m->wpart, kSplits, nw, m->g + m->w_off[l]);
+        if ((e = reduce_wgrad(m->wpart, kSplits, nw, m->g + m->w_off[l], m->stream)) != cudaSuccess) break;
         // the split-K partials are consumed: the bias partials reuse their buffer
         bias_partial_kernel<<<dim3((rows + 31) / 32, kBiasChunks), dim3(32, 8), 0, m->stream>>>(dz, B, rows,
                                                                                             m->wpart);
-        reduce_wgrad_kernel<<<nblk(rows), 256, 0, m->stream>>>(m->wpart, kBiasChunks, rows, m->g + m->b_off[l]);
-        if ((e = cudaGetLastError()) != cudaSuccess || l == 0) break;
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = reduce_wgrad(m->wpart, kBiasChunks, rows, m->g + m->b_off[l], m->stream)) != cudaSuccess || l == 0)
+            break;
         if (ldT > B &&
             (e = cudaMemset2DAsync(m->dZt + B, ldT * sizeof(__nv_bfloat16), 0, (ldT - B) * sizeof(__nv_bfloat16),
                                    cols, m->stream)) != cudaSuccess)
