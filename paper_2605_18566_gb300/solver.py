@@ -310,6 +310,23 @@ class Surrogate:
             raise HJGError(st, "hjg_mlp_get_scaling")
         return out
 
+    def save(self, path: str) -> None:
+        """Write the network (FP32 master parameters, feature standardisation, shape) to an
+        .npz file; the optimiser state is not saved (a loaded network predicts, and training
+        it further starts Adam afresh)."""
+        np.savez(path, params=self.params(), scaling=self.scaling(),
+                 shape=np.array([self.n_in, self.n_out, self.width], dtype=np.int64))
+
+    @classmethod
+    def load(cls, path: str, stream: Optional[torch.cuda.Stream] = None) -> "Surrogate":
+        """A network written by save(); its predictions equal the saved network's."""
+        with np.load(path) as f:
+            n_in, n_out, width = (int(v) for v in f["shape"])
+            s = cls(n_in, n_out, width, stream=stream)
+            s.set_params(f["params"])
+            s.set_scaling(f["scaling"])
+        return s
+
     def set_scaling(self, sc) -> None:
         sc = np.ascontiguousarray(np.asarray(sc, dtype=np.float32).ravel())
         st = self.lib.hjg_mlp_set_scaling(self.m, sc.ctypes.data_as(C.c_void_p))

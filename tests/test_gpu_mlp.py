@@ -143,3 +143,23 @@ def test_scaling_forward_gradients_and_input_grad():
     np.testing.assert_array_equal(s2.scaling(), s.scaling())
     s2.close()
     s.close()
+
+
+def test_save_and_load_reproduce_predictions(tmp_path):
+    """A trained network with fitted standardisation, written by save() and read by load(),
+    predicts the same values bit for bit."""
+    from paper_2605_18566_gb300 import Surrogate
+    s = _sur(seed=4)
+    rng = np.random.default_rng(6)
+    x = rng.uniform(-50, 50, size=(4096, N_IN)).astype(np.float32)
+    y = rng.normal(size=(4096, N_OUT)).astype(np.float32) * 3 + 1
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    s.fit(xt, yt, epochs=2, batch=1024)
+    path = str(tmp_path / "net.npz")
+    s.save(path)
+    t = Surrogate.load(path)
+    assert (t.n_in, t.n_out, t.width) == (N_IN, N_OUT, WIDTH)
+    np.testing.assert_array_equal(t.params(), s.params())
+    np.testing.assert_array_equal(t.scaling(), s.scaling())
+    np.testing.assert_array_equal(t.forward(xt).cpu().numpy(), s.forward(xt).cpu().numpy())
+    s.close(); t.close()
