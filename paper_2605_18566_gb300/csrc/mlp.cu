@@ -238,6 +238,11 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     constexpr bool kH = EPI == kEpiBiasSilu || EPI == kEpiSiluBwd;
     constexpr bool kBias = EPI == kEpiBiasSilu || EPI == kEpiBias;
     constexpr int kPass = 32;
+    // Transposed BF16 tile of one pass ([kPass][kHtLd], column-major: the rows of a column
+    // contiguous), in the operand stages' shared memory, which the finished MMAs no longer read.
+    constexpr int kHtLd = kTcM + 8;
+    static_assert(kPass * kHtLd * 2 <= 2 * kTcStage, "transposed tile must fit the operand stages");
+    __nv_bfloat16* hs_t = reinterpret_cast<__nv_bfloat16*>(smem);
     if (ok && nch > 0) {
 #pragma unroll 1
         for (int p0 = 0; p0 < kTcN; p0 += kPass) {
@@ -269,7 +274,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                       "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p0 + 8 * q)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m >= g.M) continue;
+            const bool row_in = m < g.M;
 #pragma unroll
             for (int q = 0; q < kPass / 8; ++q) {
                 const int nb = np + 8 * q;
@@ -293,6 +298,11 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(EPI == kEpiBiasSilu ? silu(x[j]) : x[j]);
                 }
+                if (kH && g.Ht) {   // transposed copy staged in shared memory, column-major
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) hs_t[(8 * q + j) * kHtLd + r] = h[j];
+                }
+                if (!row_in) continue;
                 if (full) {
                     if (C && vecC) {
                         float4* d = reinterpret_cast<float4*>(C + (int64_t)m * g.ldc + nb);
@@ -309,20 +319,34 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
 #pragma unroll
                             for (int j = 0; j < 8; ++j) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
                         }
-                        if (g.Ht) {   // transposed copy: the lanes of a warp write consecutive m
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
-                        }
                     }
                 } else {
                     for (int j = 0; j < 8 && nb + j < g.N; ++j) {
                         if (C) C[(int64_t)m * g.ldc + nb + j] = x[j];
-                        if (kH) {
-                            g.H[(int64_t)m * g.ldh + nb + j] = h[j];
-                            if (g.Ht) g.Ht[(int64_t)(nb + j) * g.ldht + m] = h[j];
-                        }
+                        if (kH) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
                     }
                 }
+            }
+            if (kH && g.Ht) {
+                // write the pass's transposed tile: 32 columns x 128 rows, each column a
+                // contiguous run of Ht; 16-byte pieces of 8 rows, a warp covering two columns
+                __syncthreads();
+                const bool vecT = (g.ldht % 8) == 0 && ((uintptr_t)g.Ht & 15) == 0;
+#pragma unroll
+                for (int i = 0; i < kPass * kTcM / 8 / 128; ++i) {
+                    const int idx = tid + 128 * i;
+                    const int c = idx / (kTcM / 8), r8 = 8 * (idx % (kTcM / 8));
+                    const int n = np + c, mm = m0 + r8;
+                    if (n >= g.N || mm >= g.M) continue;
+                    const __nv_bfloat16* src = hs_t + c * kHtLd + r8;
+                    __nv_bfloat16* dst = g.Ht + (int64_t)n * g.ldht + mm;
+                    if (vecT && mm + 8 <= g.M) {
+                        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+                    } else {
+                        for (int t = 0; t < 8 && mm + t < g.M; ++t) dst[t] = src[t];
+                    }
+                }
+                __syncthreads();   // the next pass overwrites the tile
             }
         }
     } else if (m < g.M) {   // empty K range (or a timed-out wait): C = 0 (+ bias)
