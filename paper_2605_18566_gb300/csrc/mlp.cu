@@ -238,11 +238,17 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     constexpr bool kH = EPI == kEpiBiasSilu || EPI == kEpiSiluBwd;
     constexpr bool kBias = EPI == kEpiBiasSilu || EPI == kEpiBias;
     constexpr int kPass = 32;
-    // Transposed BF16 tile of one pass ([kPass][kHtLd], column-major: the rows of a column
-    // contiguous), in the operand stages' shared memory, which the finished MMAs no longer read.
-    constexpr int kHtLd = kTcM + 8;
-    static_assert(kPass * kHtLd * 2 <= 2 * kTcStage, "transposed tile must fit the operand stages");
-    __nv_bfloat16* hs_t = reinterpret_cast<__nv_bfloat16*>(smem);
+    // One pass's outputs are staged in the operand stages' shared memory (the finished MMAs
+    // no longer read it) and written out cooperatively, so that every global store is a
+    // 16-byte piece of a contiguous row run: the FP32 output [128][kCsLd], the BF16
+    // activation [128][kHsLd] and its transpose [kPass][kHtLd] (the rows of a column
+    // contiguous).  The paddings keep the shared-memory accesses free of bank conflicts.
+    constexpr int kCsLd = kPass + 4, kHsLd = kPass + 8, kHtLd = kTcM + 8;
+    constexpr int kCsBytes = kTcM * kCsLd * 4, kHsBytes = kTcM * kHsLd * 2;
+    static_assert(kCsBytes + kHsBytes + kPass * kHtLd * 2 <= 2 * kTcStage, "staging must fit the operand stages");
+    float* cs = reinterpret_cast<float*>(smem);
+    __nv_bfloat16* hs = reinterpret_cast<__nv_bfloat16*>(smem + kCsBytes);
+    __nv_bfloat16* hs_t = reinterpret_cast<__nv_bfloat16*>(smem + kCsBytes + kHsBytes);
     if (ok && nch > 0) {
 #pragma unroll 1
         for (int p0 = 0; p0 < kTcN; p0 += kPass) {
@@ -274,11 +280,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                       "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p0 + 8 * q)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const bool row_in = m < g.M;
 #pragma unroll
-            for (int q = 0; q < kPass / 8; ++q) {
-                const int nb = np + 8 * q;
-                const bool full = nb + 8 <= g.N;
+            for (int q = 0; q < kPass / 8; ++q) {   // stage row r of the pass
                 float x[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -293,61 +296,64 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                         x[j] = x[j] * sg * (1.0f + z * (1.0f - sg));
                     }
                 }
-                __align__(16) __nv_bfloat16 h[8];
+                if (C) {
+                    float4* d = reinterpret_cast<float4*>(cs + r * kCsLd + 8 * q);
+                    d[0] = make_float4(x[0], x[1], x[2], x[3]);
+                    d[1] = make_float4(x[4], x[5], x[6], x[7]);
+                }
                 if (kH) {
+                    __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(EPI == kEpiBiasSilu ? silu(x[j]) : x[j]);
-                }
-                if (kH && g.Ht) {   // transposed copy staged in shared memory, column-major
+                    *reinterpret_cast<uint4*>(hs + r * kHsLd + 8 * q) = *reinterpret_cast<const uint4*>(h);
+                    if (g.Ht) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) hs_t[(8 * q + j) * kHtLd + r] = h[j];
-                }
-                if (!row_in) continue;
-                if (full) {
-                    if (C && vecC) {
-                        float4* d = reinterpret_cast<float4*>(C + (int64_t)m * g.ldc + nb);
-                        d[0] = make_float4(x[0], x[1], x[2], x[3]);
-                        d[1] = make_float4(x[4], x[5], x[6], x[7]);
-                    } else if (C) {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) C[(int64_t)m * g.ldc + nb + j] = x[j];
-                    }
-                    if (kH) {
-                        if (vecH) {
-                            *reinterpret_cast<uint4*>(g.H + (int64_t)m * g.ldh + nb) = *reinterpret_cast<const uint4*>(h);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
-                        }
-                    }
-                } else {
-                    for (int j = 0; j < 8 && nb + j < g.N; ++j) {
-                        if (C) C[(int64_t)m * g.ldc + nb + j] = x[j];
-                        if (kH) g.H[(int64_t)m * g.ldh + nb + j] = h[j];
+                        for (int j = 0; j < 8; ++j) hs_t[(8 * q + j) * kHtLd + r] = h[j];
                     }
                 }
             }
-            if (kH && g.Ht) {
-                // write the pass's transposed tile: 32 columns x 128 rows, each column a
-                // contiguous run of Ht; 16-byte pieces of 8 rows, a warp covering two columns
-                __syncthreads();
-                const bool vecT = (g.ldht % 8) == 0 && ((uintptr_t)g.Ht & 15) == 0;
+            __syncthreads();
+            if (C) {   // 128 rows x kPass FP32: 16-byte pieces, a warp covering four rows
 #pragma unroll
-                for (int i = 0; i < kPass * kTcM / 8 / 128; ++i) {
+                for (int i = 0; i < kTcM * kPass / 4 / 128; ++i) {
                     const int idx = tid + 128 * i;
-                    const int c = idx / (kTcM / 8), r8 = 8 * (idx % (kTcM / 8));
-                    const int n = np + c, mm = m0 + r8;
-                    if (n >= g.N || mm >= g.M) continue;
-                    const __nv_bfloat16* src = hs_t + c * kHtLd + r8;
-                    __nv_bfloat16* dst = g.Ht + (int64_t)n * g.ldht + mm;
-                    if (vecT && mm + 8 <= g.M) {
-                        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
-                    } else {
-                        for (int t = 0; t < 8 && mm + t < g.M; ++t) dst[t] = src[t];
+                    const int rr = idx / (kPass / 4), c4 = 4 * (idx % (kPass / 4));
+                    const int mm = m0 + rr, n = np + c4;
+                    if (mm >= g.M || n >= g.N) continue;
+                    const float* src = cs + rr * kCsLd + c4;
+                    float* dst = C + (int64_t)mm * g.ldc + n;
+                    if (vecC && n + 4 <= g.N) *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+                    else for (int t = 0; t < 4 && n + t < g.N; ++t) dst[t] = src[t];
+                }
+            }
+            if (kH) {   // 128 rows x kPass BF16, and the transpose: kPass columns x 128 rows
+#pragma unroll
+                for (int i = 0; i < kTcM * kPass / 8 / 128; ++i) {
+                    const int idx = tid + 128 * i;
+                    const int rr = idx / (kPass / 8), c8 = 8 * (idx % (kPass / 8));
+                    const int mm = m0 + rr, n = np + c8;
+                    if (mm >= g.M || n >= g.N) continue;
+                    const __nv_bfloat16* src = hs + rr * kHsLd + c8;
+                    __nv_bfloat16* dst = g.H + (int64_t)mm * g.ldh + n;
+                    if (vecH && n + 8 <= g.N) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+                    else for (int t = 0; t < 8 && n + t < g.N; ++t) dst[t] = src[t];
+                }
+                if (g.Ht) {
+                    const bool vecT = (g.ldht % 8) == 0 && ((uintptr_t)g.Ht & 15) == 0;
+#pragma unroll
+                    for (int i = 0; i < kPass * kTcM / 8 / 128; ++i) {
+                        const int idx = tid + 128 * i;
+                        const int c = idx / (kTcM / 8), r8 = 8 * (idx % (kTcM / 8));
+                        const int n = np + c, mm = m0 + r8;
+                        if (n >= g.N || mm >= g.M) continue;
+                        const __nv_bfloat16* src = hs_t + c * kHtLd + r8;
+                        __nv_bfloat16* dst = g.Ht + (int64_t)n * g.ldht + mm;
+                        if (vecT && mm + 8 <= g.M) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+                        else for (int t = 0; t < 8 && mm + t < g.M; ++t) dst[t] = src[t];
                     }
                 }
-                __syncthreads();   // the next pass overwrites the tile
             }
+            __syncthreads();   // the next pass overwrites the staging
         }
     } else if (m < g.M) {   // empty K range (or a timed-out wait): C = 0 (+ bias)
         for (int n = n0; n < min(g.N, n0 + kTcN); ++n) {
