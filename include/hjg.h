@@ -112,12 +112,14 @@ typedef struct {
     double c_min, c_max; /* |c| clip; <= 0 selects 1e-2/delta and 1e2/delta */
     uint64_t seed;       /* Philox key (low word, high word ^ instance) */
     uint32_t instance;
-    int32_t block_threads; /* 0: tuned default; else 128, 256 or 512 */
+    int32_t block_threads; /* 0: tuned default; else the CTA size of one of the game's launch
+                              variants (128 or 256; also 512 for the 45-D game) */
     int32_t grid_blocks;   /* 0: tuned default (persistent grid over the SMs) */
     int32_t variant;       /* 0: default / autotuned; v > 0 forces sweep launch variant v - 1 */
     uint32_t point_offset; /* global index of the first loaded state (Philox counter word 0):
                               a shard of a larger state set draws the samples it would draw
-                              in the whole set */
+                              in the whole set; point_offset + loaded items must not exceed
+                              2^32 (HJG_EINVAL) */
     int32_t tube;          /* 1: tube form v_t + min{0, H} = (delta/2) Lap v (Eq. HJ-RCBRT-Visc):
                               Gamma is built from min{0, H}, so a state that has entered the
                               target keeps a non-positive value */

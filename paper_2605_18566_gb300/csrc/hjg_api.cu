@@ -422,6 +422,8 @@ hjg_status hjg_set_points(hjg_ctx* ctx, const float* pts, int64_t M, int64_t ld,
     if (M < 0 || M * H > 0xFFFFFFFFll || (M > 0 && !pts) || ld < ctx->n)
         return fail(ctx, HJG_EINVAL, "set_points: bad M=%lld or ld=%lld (n=%d)", (long long)M,
                     (long long)ld, ctx->n);
+    if ((uint64_t)ctx->opt.point_offset + (uint64_t)(M * H) > 0x100000000ull)   // 32-bit counter word
+        return fail(ctx, HJG_EINVAL, "set_points: point_offset + items exceeds 2^32");
     cudaStream_t st = pick_stream(ctx, stream);
     hjg_status s;
     const int64_t items = M * H;   // item j M + m: state m at horizon j

@@ -126,6 +126,7 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     if (!dyn || !target || !opt) return HJG_EINVAL;
     if (!(nu > 0) || !(T > 0) || !std::isfinite(nu) || !std::isfinite(T)) return HJG_EINVAL;
     if (opt->N < 1 || opt->N > 0xFFFFFFFFll || opt->K < 1 || M < 0 || M > 0xFFFFFFFFll) return HJG_EINVAL;
+    if ((uint64_t)opt->point_offset + (uint64_t)M > 0x100000000ull) return HJG_EINVAL;   // 32-bit counter word
     if (!stream_blocks_fit(dyn->n, opt->N)) return HJG_EINVAL;
     GameKernels kern{};
     if (!pick_kernels(dyn, &kern)) return HJG_EINVAL;

@@ -74,3 +74,17 @@ def test_nonfinite_state_is_reported_and_isolated():
     keep = np.arange(300) != 17
     np.testing.assert_array_equal(st_bad["v"][keep], st_ok["v"][keep])
     np.testing.assert_array_equal(st_bad["p"][keep], st_ok["p"][keep])
+
+
+def test_point_offset_range():
+    """The state's global index is one 32-bit Philox counter word: a shard whose offset plus
+    its states would pass 2^32 is refused, the largest one that fits is accepted."""
+    from paper_2605_18566_gb300 import HJGError
+    x = torch.from_numpy(hjg_inputs.points(W1, M=11)).cuda()
+    s = solver_for(W1, N=64, K=1, point_offset=2**32 - 10)
+    s.set_points(x[:10])
+    s.picard_sweep(1)
+    assert np.all(np.isfinite(s.get_state()["v"].cpu().numpy()))
+    with pytest.raises(HJGError):
+        s.set_points(x)
+    s.close()
