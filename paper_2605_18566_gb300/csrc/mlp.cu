@@ -8,6 +8,7 @@
 // Layout: parameters are one FP32 array [W1 | b1 | W2 | b2 | W3 | b3 | W4 | b4] with each
 // W_l stored [out][in] row-major; a BF16 copy of the W_l feeds the tensor cores.  Inputs
 // and outputs are padded to multiples of 16 (45 -> 48, 46 -> 48).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -56,10 +57,10 @@ __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z));
 // The GEMM runs on the 5th-generation tensor cores (tcgen05, sm_100 family):
 // a CTA of 4 warps owns a 128 x 64 tile of C, accumulated in tensor memory (TMEM, 128
 // lanes x 64 FP32 columns; the narrow tile doubles the CTAs of the width-256 layers, which
-// measured 11-13 % faster than 128 x 128 tiles).  Per K chunk of 64 the operands are staged
-// in shared memory in the canonical K-major no-swizzle layout (8-row x 16-byte core
-// matrices, 128 B apart along K, 256 B apart along rows), made visible to the tensor core's
-// async proxy, and thread 0 issues four tcgen05.mma (M = 128, N = 64, K = 16) and commits them to an
+// measured 11-13 % faster than 128 x 128 tiles).  Per K chunk of 64 the operands are copied
+// by the tensor memory accelerator into shared memory in the canonical K-major no-swizzle
+// layout (8-row x 16-byte core matrices), and thread 0 issues four tcgen05.mma (M = 128,
+// N = 64, K = 16) and commits them to an
 // mbarrier; every wait on a barrier is bounded and records a time-out in *err.  The
 // epilogue reads TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31 = rows).
 constexpr int kTcM = 128, kTcN = 64, kTcK = 64;
@@ -85,11 +86,6 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Byte offset of element (r, k) of a [R][64] operand chunk in the canonical layout.
-__device__ __forceinline__ uint32_t canon_off(int r, int k, int R) {
-    return (uint32_t)((k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, uint32_t limit = 1u << 24) {
     for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
@@ -104,45 +100,49 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err
     return false;
 }
 
-// S-stage pipeline: the copies of chunks c + 1 .. c + S - 1 (16-byte cp.async, global ->
-// shared, bypassing L1) are in flight while the tensor core multiplies chunk c; a stage is
-// overwritten only after the commit of the MMAs that read it has arrived on that stage's
-// mbarrier.  S = 4 when a CTA's K range has at most four chunks and the grid fits in one
-// wave at two CTAs per SM (every GEMM of the width-256 network at batch 8,192, which then
-// issues all its loads at once: measured 5 % faster), else S = 2 (four CTAs per SM for
-// long K ranges and multi-wave grids: measured 6 % faster at batch 32,768).  Both operands are K-major in global memory (A(m, k) = A[m lda + k], B(k, n) =
-// Bt[n ldb + k], lda and ldb multiples of 8, rows 16-byte aligned); gemm() packs other
-// layouts first.
+// S-stage TMA pipeline: one thread issues, per K chunk of 64, the tensor-memory-accelerator
+// copies of both operand tiles (cp.async.bulk.tensor, completion counted in bytes on the
+// stage's "full" mbarrier) and, once a stage is full, the four tcgen05.mma of that chunk,
+// whose commit arrives on the stage's "empty" mbarrier; a stage is refilled only after that
+// arrival.  Up to S chunks are in flight.  The operands are K-major in global memory (A(m, k)
+// = A[m lda + k], B(k, n) = Bt[n ldb + k], lda and ldb multiples of 8, 16-byte aligned
+// bases; gemm() packs other layouts first) and are described by 2-D tensor maps (K
+// innermost); each copy moves one 8-element K slice of 128 (A) or 64 (B) rows, so a chunk
+// lands in shared memory as [8 K slices][rows][16 B]: the canonical K-major no-swizzle
+// layout with core matrices 128 B apart along the rows and rows x 16 B apart along K.  Rows
+// and K beyond the tensor read as zero.  S = 4 when a CTA's K range has at most four chunks
+// and the grid fits in one wave at two CTAs per SM (every GEMM of the width-256 network at
+// batch 8,192 then issues all its copies at once), else S = 2 (four CTAs per SM for long K
+// ranges and multi-wave grids).
 constexpr int kTcStage = (kTcM + kTcN) * kTcK * 2;   // bytes of one stage (A then B)
 constexpr int tc_smem(int stages) { return stages * kTcStage; }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
 }
 
-// Copy the 64-wide K chunk starting at k0 of rows [r0, r0 + R) of a K-major operand into
-// the canonical layout at `dst`; rows >= rmax and columns >= kend read as zero.  Lanes pair
-// up on 32 contiguous bytes of one row (one sector); eight rows fill 256 contiguous bytes of
-// shared memory, so the 16-byte writes are conflict-free.
-template <int R>
-__device__ __forceinline__ void load_chunk(uint32_t dst, const __nv_bfloat16* src, int64_t ld, int r0, int rmax,
-                                           int k0, int kend, int tid) {
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+// The copies of one K chunk (k0 = its first K index, a multiple of 64) into stage `st`.
+__device__ __forceinline__ void tma_chunk(uint32_t st, const CUtensorMap* tmA, const CUtensorMap* tmB, int m0,
+                                          int n0, int k0, uint32_t bar) {
+    mbar_expect_tx(bar, (uint32_t)kTcStage);
 #pragma unroll
-    for (int i = 0; i < R * 8 / 128; ++i) {
-        const int e = tid + 128 * i;
-        const int lo = e & 1, r = (e >> 1) % R, kq = (e >> 1) / R;
-        const int k8 = 2 * kq + lo;
-        const int row = r0 + r, kk = k0 + 8 * k8;
-        const bool in = row < rmax && kk < kend;
-        const __nv_bfloat16* p = in ? src + (int64_t)row * ld + kk : src;
-        cp_async16(dst + canon_off(r, 8 * k8, R), p, in ? 16u : 0u);
+    for (int o = 0; o < kTcK / 8; ++o) {
+        tma_load_2d(st + (uint32_t)(o * kTcM * 16), tmA, k0 + 8 * o, m0, bar);
+        tma_load_2d(st + (uint32_t)(kTcM * kTcK * 2 + o * kTcN * 16), tmB, k0 + 8 * o, n0, bar);
     }
 }
 
 template <int EPI, int kTcStages>
-__global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err) {
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, int* err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[kTcStages];
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
@@ -156,7 +156,10 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     }
     if (tid == 0) {
 #pragma unroll
-        for (int i = 0; i < kTcStages; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[i])));
+        for (int i = 0; i < kTcStages; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -164,47 +167,25 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = umma_idesc_bf16(kTcM, kTcN);
-    uint32_t phase[kTcStages] = {};   // parity of the next completion to wait for, per stage
     bool ok = true;
-    // cp.async group i holds chunk i: the prologue commits chunks 0 .. S-2 (empty groups past
-    // the last chunk keep the count uniform), iteration c commits chunk c + S - 1.
-#pragma unroll
-    for (int c = 0; c < kTcStages - 1; ++c) {
-        if (c < nch) {
-            const uint32_t st = s0 + (uint32_t)(c * kTcStage);
-            const int k0 = kbeg + c * kTcK;
-            load_chunk<kTcM>(st, g.A, g.sam, m0, g.M, k0, kend, tid);
-            load_chunk<kTcN>(st + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, k0, kend, tid);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    for (int c = 0; c < nch && ok; ++c) {
-        const int s = c % kTcStages;
-        const int cn = c + kTcStages - 1;
-        if (cn < nch) {
-            const int sn = cn % kTcStages;   // the stage chunk c - 1 used
-            if (c >= 1) {   // its MMAs must be done before the stage is overwritten
-                ok = mbar_wait(smem_u32(&mbar[sn]), phase[sn], err);
-                phase[sn] ^= 1u;
-                ok = __syncthreads_and(ok) != 0;
-                if (!ok) break;
-            }
-            const uint32_t st = s0 + (uint32_t)(sn * kTcStage);
-            const int k0 = kbeg + cn * kTcK;
-            load_chunk<kTcM>(st, g.A, g.sam, m0, g.M, k0, kend, tid);
-            load_chunk<kTcN>(st + kTcM * kTcK * 2, g.B, g.sbn, n0, g.N, k0, kend, tid);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" :: "n"(kTcStages - 1) : "memory");   // chunk c has landed
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    if (tid == 0 && nch > 0) {
+        // parities of the next completion to wait for on each stage's barriers
+        uint32_t ph_full[kTcStages] = {}, ph_empty[kTcStages] = {};
+        int issued = 0, landed = 0;
+        for (; issued < nch && issued < kTcStages; ++issued)
+            tma_chunk(s0 + (uint32_t)(issued * kTcStage), &tmA, &tmB, m0, n0, kbeg + issued * kTcK,
+                      smem_u32(&full[issued]));
+        for (int c = 0; c < nch; ++c) {
+            const int s = c % kTcStages;
+            if (!mbar_wait(smem_u32(&full[s]), ph_full[s], err)) { ok = false; break; }
+            ph_full[s] ^= 1u;
+            landed = c + 1;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = s0 + (uint32_t)(s * kTcStage), sb = sa + kTcM * kTcK * 2;
 #pragma unroll
             for (int ks = 0; ks < kTcK / 16; ++ks) {
-                const uint64_t da = umma_desc(sa + ks * (kTcM * 32), 128, 256);
-                const uint64_t db = umma_desc(sb + ks * (kTcN * 32), 128, 256);
+                const uint64_t da = umma_desc(sa + ks * (kTcM * 32), kTcM * 16, 128);
+                const uint64_t db = umma_desc(sb + ks * (kTcN * 32), kTcN * 16, 128);
                 const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -213,17 +194,26 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int* err
                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&mbar[s])) : "memory");
+                         :: "r"(smem_u32(&empty[s])) : "memory");
+            if (issued < nch) {   // refill this stage once its MMAs are done
+                if (!mbar_wait(smem_u32(&empty[s]), ph_empty[s], err)) { ok = false; break; }
+                ph_empty[s] ^= 1u;
+                tma_chunk(sa, &tmA, &tmB, m0, n0, kbeg + issued * kTcK, smem_u32(&full[s]));
+                ++issued;
+            }
         }
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");   // nothing left in flight on any path
-    if (nch > 0) {
         if (ok) {   // the last commit covers every earlier MMA of this thread
             const int s = (nch - 1) % kTcStages;
-            ok = mbar_wait(smem_u32(&mbar[s]), phase[s], err);
+            ok = mbar_wait(smem_u32(&empty[s]), ph_empty[s], err);
+        } else {    // a wait ran out: let the copies still in flight land (bounded) before leaving
+            for (int c = landed; c < issued; ++c) {
+                const int s = c % kTcStages;
+                mbar_wait(smem_u32(&full[s]), ph_full[s], err);
+                ph_full[s] ^= 1u;
+            }
         }
-        ok = __syncthreads_and(ok) != 0;
     }
+    ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: row r = 32 warp + lane; per pass of 32 columns the bias and (kEpiSiluBwd)
     // pre-activation loads are issued first, then four tcgen05.ld of 8 columns and one
@@ -409,6 +399,42 @@ inline int64_t gemm_scratch_b(const GemmArgs& g) {
     return ok ? 0 : (int64_t)g.N * pad8(g.K);
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link
+// against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2-D tensor map of a K-major BF16 operand [rows][ld] (K = the first k_extent columns of a
+// row), box = one 8-element K slice of box_rows rows; out-of-range elements read as zero.
+bool operand_map(CUtensorMap* tm, const __nv_bfloat16* base, int64_t rows, int64_t k_extent, int64_t ld,
+                 int box_rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || ((uintptr_t)base & 15) != 0 || (ld % 8) != 0 || rows < 1 || k_extent < 1) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)k_extent, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int EPI, int S>
 cudaError_t launch_tc_s(const GemmArgs& k, int splits, cudaStream_t st) {
     static bool attr = false;   // opt in to the dynamic shared memory once per process
@@ -418,10 +444,17 @@ cudaError_t launch_tc_s(const GemmArgs& k, int splits, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap tmA, tmB;   // unused (zero) when K is empty: the kernel then writes C = 0 (+ bias)
+    memset(&tmA, 0, sizeof tmA);
+    memset(&tmB, 0, sizeof tmB);
+    if (k.K > 0 &&
+        (!operand_map(&tmA, k.A, k.M, k.K, k.sam, kTcM) || !operand_map(&tmB, k.B, k.N, k.K, k.sbn, kTcN)))
+        return cudaErrorInvalidValue;
     dim3 grid((k.N + kTcN - 1) / kTcN, (k.M + kTcM - 1) / kTcM, splits);
-    gemm_tc_kernel<EPI, S><<<grid, 128, tc_smem(S), st>>>(k, g_tc_err);
+    gemm_tc_kernel<EPI, S><<<grid, 128, tc_smem(S), st>>>(k, tmA, tmB, g_tc_err);
     return cudaGetLastError();
 }
+
 template <int EPI>
 cudaError_t launch_tc(const GemmArgs& k, int splits, cudaStream_t st) {
     static int sms = 0;
