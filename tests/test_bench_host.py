@@ -1,0 +1,76 @@
+"""Host logic of the benchmark (no GPU): the per-point-sample work constants agree with the
+sampler's stream layout as the oracle defines it, the residual-floor and oracle-error
+summaries behave on synthetic inputs, and the reference arm prints the contract's line."""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import bench
+import hjg_inputs
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("game,n", [("dubins3", 3), ("rockets6", 6), ("rockets45", 45)])
+def test_work_constants_follow_the_stream_layout(game, n):
+    # Philox blocks per sample: slots per sample over the six normals a block yields
+    assert bench.BLOCKS_PER_SAMPLE[game] == pytest.approx(oracle.slot_stride(n) / 6.0)
+    # MUFU: lg2, sqrt, sin, cos per Box-Muller pair of the n normals used, one square root
+    # for the target distance and one exp2 weight
+    assert bench.MUFU_PER_SAMPLE[game] == 4 * n / 2 + 2
+
+
+def test_roofline_picks_the_binding_pipe():
+    clk = bench.SMS * bench.SM_MAX_MHZ * 1e6
+    samples = 1e12
+    # a time at which the MUFU pipe runs exactly at its peak
+    t = samples * (bench.MUFU_PER_SAMPLE["rockets6"] - 0.5) / (bench.MUFU_PER_SM_CLK * clk)
+    r = bench.roofline("rockets6", samples, t)
+    assert r["pipe"] == "mufu" and r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(1.0)
+    assert r["other_pipes"]["int_mul_hi"] < 1.0
+    assert r["traffic"] is None                      # not the benchmark launch
+    r2 = bench.roofline("rockets6", hjg_inputs.ROCKETS6.M * 10, 1.0, states=hjg_inputs.ROCKETS6.M)
+    assert r2["traffic"] == bench.DRAM_BYTES_BENCH_LAUNCH
+
+
+def test_sweeps_to_floor():
+    r = [0.5, 0.2, 0.11, 0.1, 0.1, 0.1]
+    out = bench.sweeps_to_floor(r)
+    assert out["floor"] == pytest.approx(0.1)
+    assert out["sweeps"] == 3                        # 0.11 <= 1.1 * 0.1
+    assert bench.sweeps_to_floor([0.3, 0.3, 0.3])["sweeps"] == 1
+
+
+def test_oracle_error_summary():
+    rng = np.random.default_rng(0)
+    v_ref = rng.normal(size=20); p_ref = rng.normal(size=(20, 3))
+    v = v_ref.copy(); p = p_ref.astype(np.float32).copy()
+    v[3] += 1.0                                      # one state far outside the tolerance
+    idx = np.arange(20)
+    out = bench.oracle_error((v, p), (idx, {"v": v_ref, "p": p_ref}))
+    assert out["states"] == 20
+    assert out["within_tolerance"] == pytest.approx(19 / 20)
+    assert out["dv_max"] == pytest.approx(1.0 / (1.0 + abs(v_ref[3])))
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_prints_the_contract_line():
+    proc = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                           "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                          timeout=600, cwd=ROOT)
+    assert proc.returncode == 0, proc.stderr[-2000:]
+    line = json.loads(proc.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and math.isfinite(line["value"])
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
