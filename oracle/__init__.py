@@ -41,7 +41,8 @@ class Problem(C.Structure):
         ("speed", C.c_double * 16), ("h_sign", C.c_double),
         ("A", C.c_double * 64), ("x0", C.c_double * 8), ("d", C.c_double),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("tilt", C.c_int32),
-        ("flock_k", C.c_int32), ("tube", C.c_int32), ("cv", C.c_int32), ("pad_", C.c_int32),
+        ("flock_k", C.c_int32), ("tube", C.c_int32), ("cv", C.c_int32), ("obstacle", C.c_int32),
+        ("obs_c", C.c_double * 2), ("obs_r", C.c_double),
     ]
 
 
@@ -109,12 +110,18 @@ def _f64(a, shape=None):
     return a
 
 
+OBSTACLE_GAMES = ("dubins3", "rockets_rel3", "double_int2")
+
+
 def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=None,
                  c_max=None, radius=0.5, speed=None, h_sign=1.0, A=None, x0=None,
-                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7, tube=False, cv=False) -> Problem:
+                 d=0.0, seed=0, instance=0, tilt=False, flock_k=7, tube=False, cv=False,
+                 obstacle=None) -> Problem:
     """Build an oracle problem.  Defaults follow the readings used throughout:
     eta = 1e-6, c_min = 1e-2/delta, c_max = 1e2/delta.  tube=True selects the tube form
-    (Eq. HJ-RCBRT-Visc): the coefficient map uses min{0, H}."""
+    (Eq. HJ-RCBRT-Visc): the coefficient map uses min{0, H}.  obstacle = (cx, cy, r) adds the
+    reach-avoid obstacle (a disc in the plane of state dims 0, 1; games dubins3, rockets_rel3,
+    double_int2)."""
     P = Problem()
     P.game = GAMES[game]
     P.n = n
@@ -142,6 +149,12 @@ def make_problem(game: str, n: int, delta: float, T: float, *, eta=1e-6, c_min=N
     P.flock_k = flock_k
     P.tube = 1 if tube else 0
     P.cv = 1 if cv else 0
+    if obstacle is not None:
+        if game not in OBSTACLE_GAMES:
+            raise ValueError("the reach-avoid obstacle is defined for %s only" % (OBSTACLE_GAMES,))
+        cx, cy, r = (float(v) for v in obstacle)
+        P.obstacle = 1
+        P.obs_c[0], P.obs_c[1], P.obs_r = cx, cy, r
     return P
 
 

@@ -22,6 +22,9 @@
  *     Section 3.2 multi-rocket game (Eq. multiagent_dynamics), a two-rocket planar game
  *     built from the same per-agent dynamics, and quadratic test problems
  *     (H = +-|p|^2/2, the exact Cole-Hopf case of Corollary B.2).
+ *   - Reach-avoid tube (reading of Eq. HJI-RCBRAT-Visc): an avoid disc whose constraint
+ *     function o enters the datum as max{l, o} and bounds the value from below after every
+ *     sweep (see obstacle_fn).
  *   - Counter-based sampler: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11); each
  *     128-bit block gives three Box-Muller pairs (23-bit radius uniforms u = ((x & (2^23-1))
  *     +0.5) 2^-23, angle uniforms of 23, 18, 18 bits); packed per-sample slots.
@@ -73,7 +76,9 @@ typedef struct {
     int32_t flock_k;    /* flock: neighbours per agent */
     int32_t tube;       /* 1: tube form, Gamma built from min{0, H} (Eq. HJ-RCBRT-Visc) */
     int32_t cv;         /* 1: Stein control variate around the current iterate (see solve_point) */
-    int32_t pad_;
+    int32_t obstacle;   /* 1: reach-avoid obstacle, a disc in the plane of state dims 0, 1 */
+    double obs_c[2];    /* obstacle centre */
+    double obs_r;       /* obstacle radius */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -206,7 +211,7 @@ static double quad_form(const orc_problem *P, const double *y)
     return r;
 }
 
-double orc_ell(const orc_problem *P, const double *y, const double *nbr)
+static double ell_base(const orc_problem *P, const double *y, const double *nbr)
 {
     switch (P->game) {
     case ORC_DUBINS3:
@@ -243,8 +248,52 @@ double orc_ell(const orc_problem *P, const double *y, const double *nbr)
     return NAN;
 }
 
-/* Analytic gradient of l, 0 where it is undefined (the ridge of a distance). */
+/* Reach-avoid obstacle (reading of Eq. HJI-RCBRAT-Visc): the avoid set is a disc of radius
+ * obs_r about obs_c in the plane of state dims 0 and 1 (the position, or relative position,
+ * of the games that support it), with constraint function o(y) = obs_r - |y_{0,1} - obs_c|,
+ * positive inside the obstacle.  The value is held above o: the datum of every sweep is
+ * max{l, o} (a sample inside the obstacle counts as outside the target), and after every
+ * sweep v <- max{v, o(x)} with Dv <- Do(x) where the obstacle binds -- the projection form of
+ * the reach-avoid variational inequality max{min{v_t + H - (delta/2) Lap v, l - v}, o - v} = 0. */
+static double obstacle_fn(const orc_problem *P, const double *y)
+{
+    double dx = y[0] - P->obs_c[0], dy = y[1] - P->obs_c[1];
+    return P->obs_r - sqrt(dx * dx + dy * dy);
+}
+
+static void obstacle_grad(const orc_problem *P, const double *x, double *g)
+{
+    double dx = x[0] - P->obs_c[0], dy = x[1] - P->obs_c[1];
+    double rho = sqrt(dx * dx + dy * dy);
+    for (int a = 0; a < P->n; ++a) g[a] = 0.0;
+    if (rho > 0) { g[0] = -dx / rho; g[1] = -dy / rho; }
+}
+
+/* The datum l of the sweep: the target's signed distance, or max{l, o} with an obstacle. */
+double orc_ell(const orc_problem *P, const double *y, const double *nbr)
+{
+    double l = ell_base(P, y, nbr);
+    if (P->obstacle) {
+        double o = obstacle_fn(P, y);
+        if (o > l) l = o;
+    }
+    return l;
+}
+
+static void grad_ell_base(const orc_problem *P, const double *x, const double *nbr, double *g);
+
+/* Analytic gradient of the datum, 0 where it is undefined (the ridge of a distance); with
+ * an obstacle, the gradient of whichever of l and o is larger. */
 void orc_grad_ell(const orc_problem *P, const double *x, const double *nbr, double *g)
+{
+    if (P->obstacle && obstacle_fn(P, x) > ell_base(P, x, nbr)) {
+        obstacle_grad(P, x, g);
+        return;
+    }
+    grad_ell_base(P, x, nbr, g);
+}
+
+static void grad_ell_base(const orc_problem *P, const double *x, const double *nbr, double *g)
 {
     int n = P->n;
     for (int a = 0; a < n; ++a) g[a] = 0.0;
@@ -451,6 +500,13 @@ static void solve_point(const orc_problem *P, const double *x, double c, const d
         p_out[a] = (x[a] - ysum / s) / (P->T * P->delta * c);
     }
     *ess_out = sw * sw / sw2;
+    if (P->obstacle) {   /* the value is held above the obstacle's constraint function */
+        double o = obstacle_fn(P, x);
+        if (o > *v_out) {
+            *v_out = o;
+            obstacle_grad(P, x, p_out);
+        }
+    }
 }
 
 int orc_sweep(const orc_problem *P, int64_t M, const double *x, const double *c,
