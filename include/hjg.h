@@ -98,6 +98,14 @@ typedef struct {
     double A[64];        /* quadratic test target, row-major n x n, symmetric */
     double x0[8];
     double d;
+    double obstacle_radius;     /* > 0: reach-avoid tube (reading of Eq. HJI-RCBRAT-Visc) with an
+                                   avoid disc of this radius about obstacle_center in the plane of
+                                   state dims 0 and 1, o(y) = radius - |y_{0,1} - center| (> 0
+                                   inside); the datum of every sweep is max{l, o} and after every
+                                   sweep v <- max{v, o(x)}, Dv <- Do(x) where the obstacle binds.
+                                   HJG_DUBINS3, HJG_ROCKETS_REL3 and HJG_DOUBLE_INT2 only
+                                   (HJG_EUNSUPPORTED otherwise); 0: no obstacle */
+    double obstacle_center[2];
 } hjg_target;
 
 typedef struct {

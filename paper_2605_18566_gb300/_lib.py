@@ -25,7 +25,7 @@ class Dynamics(C.Structure):
 
 class Target(C.Structure):
     _fields_ = [("radius", C.c_double), ("A", C.c_double * 64), ("x0", C.c_double * 8),
-                ("d", C.c_double)]
+                ("d", C.c_double), ("obstacle_radius", C.c_double), ("obstacle_center", C.c_double * 2)]
 
 
 class Options(C.Structure):

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/hjg.h"
 #include "sweep_impl.cuh"
 
 namespace hjg {
@@ -34,6 +35,9 @@ GameKernels kernels_flock4();
 GameKernels kernels_rockets_rel3();
 GameKernels kernels_double_int2();
 bool kernels_quadratic(int n, bool zero_h, GameKernels* out);
+
+// Whether the target's reach-avoid obstacle (if any) is valid for the game (hjg_api.cu).
+bool obstacle_ok(const hjg_dynamics* dyn, const hjg_target* t);
 
 // Flock neighbour structure (flock.cu): 7 nearest agents, their mean heading, and the
 // per-agent game data [M][kFlockAux] (neighbour positions, then the mean heading).

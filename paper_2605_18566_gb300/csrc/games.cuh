@@ -24,7 +24,44 @@ struct GameParams {
     double A_d[64];
     double x0_d[8];
     double d_d;
+    int32_t obstacle;   // 1: reach-avoid avoid disc in the plane of state dims 0, 1
+    float obs_c[2];     // its centre
+    float obs_off;      // radius + obstacle radius: the sample datum max{l, o} in "dist" units
+    double obs_c_d[2];
+    double obs_r_d;     // obstacle radius
 };
+
+// ------------------------------------------------------------- reach-avoid obstacle
+// Reading of Eq. HJI-RCBRAT-Visc: an avoid disc with constraint function o(y) = r_O -
+// |y_{0,1} - c_O| (> 0 inside).  The sweep's datum is max{l, o}; after every sweep the value
+// is held above o: v <- max{v, o(x)}, Dv <- Do(x) where the obstacle binds.
+// Sample level (FP32): the games' "dist" returns d with l = d - radius, so max{l, o} is
+// max{d, radius + r_O - |y - c_O|}.
+__device__ __forceinline__ float obstacle_dist(float d, float y0, float y1, const GameParams& g) {
+    const float ox = y0 - g.obs_c[0], oy = y1 - g.obs_c[1];
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaf(ox, ox, oy * oy)));
+    return fmaxf(d, g.obs_off - r);
+}
+__device__ inline double obstacle_d(const double* x, const GameParams& g) {
+    const double dx = x[0] - g.obs_c_d[0], dy = x[1] - g.obs_c_d[1];
+    return g.obs_r_d - sqrt(dx * dx + dy * dy);
+}
+__device__ inline void obstacle_grad_d(const double* x, const GameParams& g, int n, double* gr) {
+    const double dx = x[0] - g.obs_c_d[0], dy = x[1] - g.obs_c_d[1];
+    const double rho = sqrt(dx * dx + dy * dy);
+    for (int j = 0; j < n; ++j) gr[j] = 0.0;
+    if (rho > 0) { gr[0] = -dx / rho; gr[1] = -dy / rho; }
+}
+// The projection after a sweep: true (and v, Dv replaced) where the obstacle binds.
+__device__ inline bool obstacle_project(const double* x, const GameParams& g, int n, double& v, double* pd) {
+    if (!g.obstacle) return false;
+    const double o = obstacle_d(x, g);
+    if (!(o > v)) return false;
+    v = o;
+    obstacle_grad_d(x, g, n, pd);
+    return true;
+}
 
 enum GameId : int32_t {
     kDubins3 = 1, kRockets6 = 2, kRockets45 = 3, kFlock4 = 4, kRocketsRel3 = 5, kDoubleInt2 = 6,
@@ -44,15 +81,18 @@ struct Dubins3 {
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
-                                                 const GameParams&, const float* = nullptr) {
+                                                 const GameParams& g, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
-        return sqrtf_fast(fmaf(y0, y0, y1 * y1));
+        const float d = sqrtf_fast(fmaf(y0, y0, y1 * y1));
+        return g.obstacle ? obstacle_dist(d, y0, y1, g) : d;
     }
     __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
-        return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+        const double l = sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+        return g.obstacle ? fmax(l, obstacle_d(x, g)) : l;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams& g, const float* = nullptr) {
         const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        if (g.obstacle && obstacle_d(x, g) > rho - g.radius_d) { obstacle_grad_d(x, g, kN, gr); return; }
         gr[0] = rho > 0 ? x[0] / rho : 0.0;
         gr[1] = rho > 0 ? x[1] / rho : 0.0;
         gr[2] = 0.0;
@@ -78,15 +118,18 @@ struct RocketsRel3 {
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
-                                                 const GameParams&, const float* = nullptr) {
+                                                 const GameParams& g, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
-        return sqrtf_fast(fmaf(y0, y0, y1 * y1));
+        const float d = sqrtf_fast(fmaf(y0, y0, y1 * y1));
+        return g.obstacle ? obstacle_dist(d, y0, y1, g) : d;
     }
     __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
-        return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+        const double l = sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+        return g.obstacle ? fmax(l, obstacle_d(x, g)) : l;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams& g, const float* = nullptr) {
         const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        if (g.obstacle && obstacle_d(x, g) > rho - g.radius_d) { obstacle_grad_d(x, g, kN, gr); return; }
         gr[0] = rho > 0 ? x[0] / rho : 0.0;
         gr[1] = rho > 0 ? x[1] / rho : 0.0;
         gr[2] = 0.0;
@@ -114,15 +157,18 @@ struct DoubleInt2 {
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
-                                                 const GameParams&, const float* = nullptr) {
+                                                 const GameParams& g, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
-        return sqrtf_fast(fmaf(y0, y0, y1 * y1));
+        const float d = sqrtf_fast(fmaf(y0, y0, y1 * y1));
+        return g.obstacle ? obstacle_dist(d, y0, y1, g) : d;
     }
     __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
-        return sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+        const double l = sqrt(x[0] * x[0] + x[1] * x[1]) - g.radius_d;
+        return g.obstacle ? fmax(l, obstacle_d(x, g)) : l;
     }
-    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams&, const float* = nullptr) {
+    __device__ static void grad_ell_d(const double* x, double* gr, const GameParams& g, const float* = nullptr) {
         const double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        if (g.obstacle && obstacle_d(x, g) > rho - g.radius_d) { obstacle_grad_d(x, g, kN, gr); return; }
         gr[0] = rho > 0 ? x[0] / rho : 0.0;
         gr[1] = rho > 0 ? x[1] / rho : 0.0;
     }

@@ -182,6 +182,15 @@ void fill_game_params(hjg_ctx* ctx) {
     for (int i = 0; i < 8; ++i) { g.x0[i] = (float)ctx->target.x0[i]; g.x0_d[i] = ctx->target.x0[i]; }
     g.d = (float)ctx->target.d;
     g.d_d = ctx->target.d;
+    if (ctx->target.obstacle_radius > 0.0) {
+        g.obstacle = 1;
+        for (int i = 0; i < 2; ++i) {
+            g.obs_c[i] = (float)ctx->target.obstacle_center[i];
+            g.obs_c_d[i] = ctx->target.obstacle_center[i];
+        }
+        g.obs_r_d = ctx->target.obstacle_radius;
+        g.obs_off = (float)(ctx->target.radius + ctx->target.obstacle_radius);
+    }
 }
 
 hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
@@ -302,6 +311,18 @@ hjg_status choose_launch(hjg_ctx* ctx) {
 
 }  // namespace
 
+namespace hjg {
+// The reach-avoid obstacle is defined for the games whose state dims 0, 1 are a position.
+bool obstacle_ok(const hjg_dynamics* dyn, const hjg_target* t) {
+    if (!(t->obstacle_radius > 0.0)) return t->obstacle_radius == 0.0;   // NaN or negative: refused
+    if (!std::isfinite(t->obstacle_radius) || !std::isfinite(t->obstacle_center[0]) ||
+        !std::isfinite(t->obstacle_center[1]))
+        return false;
+    return dyn->game == HJG_DUBINS3 || dyn->game == HJG_ROCKETS_REL3 || dyn->game == HJG_DOUBLE_INT2;
+}
+
+}  // namespace hjg
+
 // Conservative certificate of Cor. 2.9 per state: band E_m = e0 + q/(1-q) ||v^(K) - v^(K-1)||_inf
 // + z se_m (the a-posteriori iteration bound of Theorem 2.8 from the last sweep's sup-norm
 // change, and the Monte-Carlo term from the state's standard error); label +1 (SAFE) if
@@ -377,6 +398,7 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
     default: st = HJG_EINVAL;
     }
     if (st == HJG_OK && ctx->kern.n != dyn->n) st = HJG_EINVAL;
+    if (st == HJG_OK && !obstacle_ok(dyn, target)) st = HJG_EUNSUPPORTED;
     if (st == HJG_OK && !(ctx->c_min <= ctx->c_max)) st = HJG_EINVAL;
     if (st != HJG_OK) { delete ctx; return st; }
     ctx->ldx = (ctx->n + 3) / 4 * 4;

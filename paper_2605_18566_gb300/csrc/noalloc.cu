@@ -113,6 +113,15 @@ GameParams game_params(const hjg_dynamics* dyn, const hjg_target* t, int tube) {
     for (int i = 0; i < 8; ++i) { g.x0[i] = (float)t->x0[i]; g.x0_d[i] = t->x0[i]; }
     g.d = (float)t->d;
     g.d_d = t->d;
+    if (t->obstacle_radius > 0.0) {
+        g.obstacle = 1;
+        for (int i = 0; i < 2; ++i) {
+            g.obs_c[i] = (float)t->obstacle_center[i];
+            g.obs_c_d[i] = t->obstacle_center[i];
+        }
+        g.obs_r_d = t->obstacle_radius;
+        g.obs_off = (float)(t->radius + t->obstacle_radius);
+    }
     return g;
 }
 
@@ -130,6 +139,7 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     if (!stream_blocks_fit(dyn->n, opt->N)) return HJG_EINVAL;
     GameKernels kern{};
     if (!pick_kernels(dyn, &kern)) return HJG_EINVAL;
+    if (!obstacle_ok(dyn, target)) return HJG_EUNSUPPORTED;
     const int n = dyn->n;
     if (ld < n || ldg < n) return HJG_EINVAL;
     if (M > 0 && (!pts || !v_out || !grad_out)) return HJG_EINVAL;

@@ -288,7 +288,17 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
         }
         const double s = sh.s;
         const double logmean = sh.mx * kLn2 - th2 / (2.0 * sh.sig.sigma2_d) + log(sh.s_use / (double)A.N);
-        const double v = -logmean / c;
+        double v = -logmean / c;
+        if (obstacle_project(sh.x, A.g, n, v, sh.pd)) {   // reach-avoid: v >= o(x)
+            pp = 0.0;
+            finite = true;
+            for (int j = 0; j < n; ++j) {
+                pp += sh.pd[j] * sh.pd[j];
+                finite = finite && isfinite(sh.pd[j]);
+                sh.p_cur[j] = (float)sh.pd[j];
+                if (last) A.p[pt * A.ldp + j] = (float)sh.pd[j];
+            }
+        }
         sh.v_cur = v;
         finite = finite && isfinite(v);
         const double h = G::ham_c(sh.x, sh.hc, sh.pd, A.g);
@@ -489,7 +499,15 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, const Sig& sig, i
         pp += pj * pj;
         finite = finite && isfinite(pj);
     }
-    const double v = -((double)m * kLn2 - th2 / (2.0 * sig.sigma2_d) + log(sd / (double)A.N)) / cd;
+    double v = -((double)m * kLn2 - th2 / (2.0 * sig.sigma2_d) + log(sd / (double)A.N)) / cd;
+    if (obstacle_project(xd, A.g, n, v, pd)) {   // reach-avoid: v >= o(x)
+        pp = 0.0;
+        finite = true;
+        for (int j = 0; j < n; ++j) {
+            pp += pd[j] * pd[j];
+            finite = finite && isfinite(pd[j]);
+        }
+    }
     finite = finite && isfinite(v);
     int clipped = 0;
     const float c_new = (float)coef_update(G::ham_d(xd, pd, A.g, aux), pp, A.delta, A.eta, A.c_min,

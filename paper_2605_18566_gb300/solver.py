@@ -38,7 +38,8 @@ class Solver:
                  tilt: bool = False, eps: float = 0.0, eta: float = -1.0,
                  c_min: float = 0.0, c_max: float = 0.0, block_threads: int = 0,
                  grid_blocks: int = 0, variant: int = -1, point_offset: int = 0,
-                 tube: bool = False, cv: bool = False, stream: Optional[torch.cuda.Stream] = None):
+                 tube: bool = False, cv: bool = False, obstacle: Optional[Sequence[float]] = None,
+                 stream: Optional[torch.cuda.Stream] = None):
         self.lib = _lib.load()
         if n is None:
             n = _lib.GAME_DIMS[game]
@@ -59,6 +60,10 @@ class Solver:
             for i, a in enumerate(np.asarray(x0, dtype=np.float64).ravel()):
                 tgt.x0[i] = a
         tgt.d = d
+        if obstacle is not None:   # reach-avoid avoid disc (cx, cy, r) in the plane of dims 0, 1
+            cx, cy, r = (float(a) for a in obstacle)
+            tgt.obstacle_center[0], tgt.obstacle_center[1] = cx, cy
+            tgt.obstacle_radius = r
         opt = _lib.Options()
         opt.N = N; opt.K = K; opt.tilt = 1 if tilt else 0; opt.eps = eps; opt.eta = eta
         opt.c_min = c_min; opt.c_max = c_max; opt.seed = seed; opt.instance = instance

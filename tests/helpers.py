@@ -57,7 +57,7 @@ def gpu_trajectory(w, x, N, K, **kw):
     return states, np.array(resid), one, r_all
 
 
-def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False):
+def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False, obstacle=None):
     """Verify a GPU Picard trajectory step by step, then compare it with the FP64 one.
 
     Per sweep k (on every state, or on the subset idx of global state indices):
@@ -72,7 +72,8 @@ def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False
     the tolerance when its coefficient is perturbed, each sweep, by twice the GPU's
     largest local coefficient error at that state (three random perturbations).  At least
     ``min_pass`` of the states must pass P2 outright."""
-    states, resid, one, r_all = gpu_trajectory(w, x, N, K, tilt=tilt, tube=tube)
+    extra = {} if obstacle is None else {"obstacle": obstacle}
+    states, resid, one, r_all = gpu_trajectory(w, x, N, K, tilt=tilt, tube=tube, **extra)
     nb_all = pb_all = None
     if w.game == "flock4":   # neighbours among all loaded agents, as the GPU found them
         _, nb_all, pb_all = oracle.flock_neighbours(x)
@@ -84,8 +85,8 @@ def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False
     xs = x[sel].astype(np.float64)
     nb = nb_all[sel] if nb_all is not None else None
     pb = pb_all[sel] if pb_all is not None else None
-    P = problem_for(w, tilt=tilt, tube=tube)
-    P1 = problem_for(w, tube=tube)
+    P = problem_for(w, tilt=tilt, tube=tube, **extra)
+    P1 = problem_for(w, tube=tube, **extra)
     local_c = np.zeros(len(sel))
     for k in range(K):
         c_k = states[k]["c"][sel].astype(np.float64)
