@@ -140,7 +140,12 @@ typedef struct {
                               mean weight and the weight sum stays positive.  Runs its
                               own launch configuration (256-thread CTA per state); the 45-D
                               game supports it with tilt only (EUNSUPPORTED otherwise) */
-    int32_t reserved[3];
+    int32_t precision;     /* 0: FP32 per-sample path with FP64 combine, log, coefficient and
+                              residual (default); 1: FP64 throughout -- normals, samples, target,
+                              log-weights and sums in double precision (one 128-thread CTA per
+                              state; games with n <= 8; not with cv: EUNSUPPORTED).  The
+                              iterate is stored alike in both (v FP64, Dv and c FP32) */
+    int32_t reserved[2];
 } hjg_options;
 
 typedef struct {

@@ -33,7 +33,8 @@ class Options(C.Structure):
                 ("eta", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double),
                 ("seed", C.c_uint64), ("instance", C.c_uint32), ("block_threads", C.c_int32),
                 ("grid_blocks", C.c_int32), ("variant", C.c_int32), ("point_offset", C.c_uint32),
-                ("tube", C.c_int32), ("cv", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("tube", C.c_int32), ("cv", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class Diag(C.Structure):

@@ -5,6 +5,7 @@
 
 #include "../../include/hjg.h"
 #include "sweep_impl.cuh"
+#include "sweep_f64.cuh"
 
 namespace hjg {
 
@@ -16,6 +17,7 @@ struct GameKernels {
     int per_warp[16];  // 1: one warp per state (the grid is counted in CTAs of threads/32 warps)
     bool has_cv;       // the control-variate kernel exists (launch slot kCvVariant)
     bool cv_tilt_only; //   and runs only in the tilted frame
+    bool has_f64;      // the FP64-throughout kernel exists (launch slot kF64Variant)
     // Launch the fused sweep, variant v, on `grid` CTAs.
     cudaError_t (*sweep)(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st);
     // Resident CTAs per SM of variant v (0 if it cannot launch).
@@ -55,6 +57,7 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
         switch (v) {                                                                       \
             HJG_SWEEP_VARIANTS(HJG_CASE_LAUNCH)                                            \
             case kCvVariant: return launch_sweep_cv<HJG_GAME>(A, tilt, grid, st);          \
+            case kF64Variant: return launch_sweep_f64<HJG_GAME>(A, tilt, grid, st);        \
         }                                                                                  \
         return cudaErrorInvalidValue;                                                      \
     }                                                                                      \
@@ -62,6 +65,7 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
         switch (v) {                                                                       \
             HJG_SWEEP_VARIANTS(HJG_CASE_OCC)                                               \
             case kCvVariant: return occupancy_cv<HJG_GAME>(tilt);                          \
+            case kF64Variant: return occupancy_f64<HJG_GAME>(tilt);                        \
         }                                                                                  \
         return 0;                                                                          \
     }                                                                                      \
@@ -73,6 +77,8 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
         HJG_SWEEP_VARIANTS(HJG_FILL)                                                       \
         k.threads[kCvVariant] = 256; k.minb[kCvVariant] = 4; k.per_warp[kCvVariant] = 0;   \
         k.has_cv = true;                                                                   \
+        k.threads[kF64Variant] = kF64Threads; k.minb[kF64Variant] = 1;                     \
+        k.per_warp[kF64Variant] = 0; k.has_f64 = true;                                     \
         k.sweep = sweep;                                                                   \
         k.occupancy = occ;                                                                 \
         k.init = launch_init<GAME>;                                                        \

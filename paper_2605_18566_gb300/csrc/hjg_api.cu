@@ -287,7 +287,12 @@ hjg_status choose_launch(hjg_ctx* ctx) {
         if (!ctx->kern.has_cv) return fail(ctx, HJG_EUNSUPPORTED, "no control-variate kernel for this game");
         if (ctx->kern.cv_tilt_only && !tilt)
             return fail(ctx, HJG_EUNSUPPORTED, "this game's control variate runs with the tilt only");
+        if (ctx->opt.precision != 0)
+            return fail(ctx, HJG_EUNSUPPORTED, "the control variate runs on the FP32 path only");
         v = kCvVariant;
+    } else if (ctx->opt.precision == 1) {   // FP64 throughout: one kernel of its own
+        if (!ctx->kern.has_f64) return fail(ctx, HJG_EUNSUPPORTED, "no FP64 sweep for this game");
+        v = kF64Variant;
     } else if (ctx->opt.variant > 0) {
         v = ctx->opt.variant - 1;
         if (v >= ctx->kern.nvariants) return fail(ctx, HJG_EINVAL, "variant %d out of range", v);
@@ -399,6 +404,8 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
     }
     if (st == HJG_OK && ctx->kern.n != dyn->n) st = HJG_EINVAL;
     if (st == HJG_OK && !obstacle_ok(dyn, target)) st = HJG_EUNSUPPORTED;
+    if (st == HJG_OK && (opt->precision < 0 || opt->precision > 1)) st = HJG_EINVAL;
+    if (st == HJG_OK && opt->precision == 1 && !ctx->kern.has_f64) st = HJG_EUNSUPPORTED;
     if (st == HJG_OK && !(ctx->c_min <= ctx->c_max)) st = HJG_EINVAL;
     if (st != HJG_OK) { delete ctx; return st; }
     ctx->ldx = (ctx->n + 3) / 4 * 4;
@@ -718,6 +725,13 @@ hjg_status hjg_autotune(hjg_ctx* ctx, int64_t max_states, int32_t* variant_out, 
                         double* best_ms_out) {
     if (!ctx) return HJG_EINVAL;
     if (ctx->M == 0) return fail(ctx, HJG_EINVAL, "autotune needs loaded states");
+    if (ctx->opt.cv || ctx->opt.precision) {   // these run one kernel of their own: nothing to tune
+        const int fixed = ctx->opt.cv ? kCvVariant : kF64Variant;
+        if (variant_out) *variant_out = fixed;
+        if (threads_out) *threads_out = ctx->kern.threads[fixed];
+        if (best_ms_out) *best_ms_out = 0.0;
+        return HJG_OK;
+    }
     const bool tilt = ctx->opt.tilt != 0;
     const int64_t Mt = std::min<int64_t>(ctx->M, max_states > 0 ? max_states : ctx->M);
     cudaStream_t st = ctx->stream;

@@ -9,12 +9,14 @@ namespace {
 template <class G>
 cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
     if (v == kCvVariant) return launch_sweep_cv<G>(A, tilt, grid, st);
+    if (v == kF64Variant) return launch_sweep_f64<G>(A, tilt, grid, st);
     if (v != 0) return cudaErrorInvalidValue;
     return launch_sweep_generic<G, 0, 128, 1>(A, tilt, grid, st);
 }
 template <class G>
 int occ(bool tilt, int v) {
     if (v == kCvVariant) return occupancy_cv<G>(tilt);
+    if (v == kF64Variant) return occupancy_f64<G>(tilt);
     return v == 0 ? occupancy_generic<G, 0, 128, 1>(tilt) : 0;
 }
 template <int N, bool Z>
@@ -28,6 +30,9 @@ GameKernels make() {
     k.threads[kCvVariant] = 256;   // the control-variate kernel
     k.minb[kCvVariant] = 4;
     k.has_cv = true;
+    k.threads[kF64Variant] = kF64Threads;   // the FP64-throughout kernel
+    k.minb[kF64Variant] = 1;
+    k.has_f64 = true;
     k.sweep = sweep<G>;
     k.occupancy = occ<G>;
     k.init = launch_init<G>;

@@ -172,9 +172,13 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     const bool tilt = opt->tilt != 0;
     int variant = opt->variant > 0 ? opt->variant - 1 : 0;
     if (variant >= kern.nvariants) return HJG_EINVAL;
+    if (opt->precision < 0 || opt->precision > 1) return HJG_EINVAL;
     if (opt->cv) {
-        if (!kern.has_cv || (kern.cv_tilt_only && !tilt)) return HJG_EUNSUPPORTED;
+        if (!kern.has_cv || (kern.cv_tilt_only && !tilt) || opt->precision) return HJG_EUNSUPPORTED;
         variant = kCvVariant;
+    } else if (opt->precision == 1) {
+        if (!kern.has_f64) return HJG_EUNSUPPORTED;
+        variant = kF64Variant;
     }
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||

@@ -835,6 +835,7 @@ cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaSt
 // The control-variate kernel: one CTA per state, 256 threads, 4 CTAs per SM.  It is
 // launched in the slot after the ordinary variants.
 constexpr int kCvVariant = kNumVariants;
+constexpr int kF64Variant = kNumVariants + 1;   // the FP64-throughout sweep (sweep_f64.cuh)
 template <class G>
 cudaError_t launch_sweep_cv(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
     if (tilt) sweep_kernel<G, 256, 4, true, false, true><<<grid, 256, 0, st>>>(A);

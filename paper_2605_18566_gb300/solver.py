@@ -39,7 +39,7 @@ class Solver:
                  c_min: float = 0.0, c_max: float = 0.0, block_threads: int = 0,
                  grid_blocks: int = 0, variant: int = -1, point_offset: int = 0,
                  tube: bool = False, cv: bool = False, obstacle: Optional[Sequence[float]] = None,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 precision: str = "fp32", stream: Optional[torch.cuda.Stream] = None):
         self.lib = _lib.load()
         if n is None:
             n = _lib.GAME_DIMS[game]
@@ -72,6 +72,9 @@ class Solver:
         opt.point_offset = point_offset
         opt.tube = 1 if tube else 0
         opt.cv = 1 if cv else 0
+        if precision not in ("fp32", "fp64"):
+            raise ValueError("precision must be 'fp32' or 'fp64'")
+        opt.precision = 1 if precision == "fp64" else 0
         self.opt = opt
         ctx = C.c_void_p()
         torch.cuda.init()

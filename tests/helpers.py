@@ -57,7 +57,8 @@ def gpu_trajectory(w, x, N, K, **kw):
     return states, np.array(resid), one, r_all
 
 
-def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False, obstacle=None):
+def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False, obstacle=None,
+                     precision="fp32"):
     """Verify a GPU Picard trajectory step by step, then compare it with the FP64 one.
 
     Per sweep k (on every state, or on the subset idx of global state indices):
@@ -73,7 +74,7 @@ def check_trajectory(w, x, N, K, idx=None, tilt=False, min_pass=0.97, tube=False
     largest local coefficient error at that state (three random perturbations).  At least
     ``min_pass`` of the states must pass P2 outright."""
     extra = {} if obstacle is None else {"obstacle": obstacle}
-    states, resid, one, r_all = gpu_trajectory(w, x, N, K, tilt=tilt, tube=tube, **extra)
+    states, resid, one, r_all = gpu_trajectory(w, x, N, K, tilt=tilt, tube=tube, precision=precision, **extra)
     nb_all = pb_all = None
     if w.game == "flock4":   # neighbours among all loaded agents, as the GPU found them
         _, nb_all, pb_all = oracle.flock_neighbours(x)
