@@ -75,3 +75,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     r = torch.empty(2 * K, dtype=torch.float64, device="cuda")
     st = _noalloc(lib, dyn, tgt, w.nu, w.T, opt, x, v, g, r, None)
     assert st == _lib.HJG_EINVAL
+
+
+def test_noalloc_fp64_and_obstacle_match_value_grad():
+    """The FP64 sweep and the reach-avoid obstacle through the allocation-free entry point:
+    the same kernel as the context path, so the results agree bit for bit."""
+    from paper_2605_18566_gb300 import Solver, _lib
+    lib = _lib.load()
+    w = hjg_inputs.DUBINS3
+    N, K, M = 2048, 4, 1000
+    obst = (0.8, 0.3, 0.6)
+    x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
+    s = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, seed=0, precision="fp64", obstacle=obst)
+    v_ref, g_ref, r_ref = s.value_grad(x)
+    s.close()
+    dyn, tgt, opt = _structs(w, N, K)
+    opt.precision = 1
+    tgt.obstacle_radius = obst[2]
+    tgt.obstacle_center[0], tgt.obstacle_center[1] = obst[0], obst[1]
+    v = torch.full((M,), float("nan"), dtype=torch.float64, device="cuda")
+    g = torch.full((M, w.n), float("nan"), dtype=torch.float32, device="cuda")
+    r = torch.full((2 * K,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = _noalloc(lib, dyn, tgt, w.nu, w.T, opt, x, v, g, r, stream)
+    assert st == 0, _lib.status_string(st)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(v.cpu().numpy(), v_ref.cpu().numpy())
+    np.testing.assert_array_equal(g.cpu().numpy(), g_ref.cpu().numpy())
