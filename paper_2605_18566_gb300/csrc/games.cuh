@@ -80,6 +80,7 @@ struct Dubins3 {
     static constexpr int kN = 3;
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
+    static constexpr bool kObstacle = true;   // supports the reach-avoid obstacle (dims 0, 1 a position)
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
                                                  const GameParams& g, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
@@ -117,6 +118,7 @@ struct RocketsRel3 {
     static constexpr int kN = 3;
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
+    static constexpr bool kObstacle = true;   // supports the reach-avoid obstacle (dims 0, 1 a position)
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
                                                  const GameParams& g, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
@@ -156,6 +158,7 @@ struct DoubleInt2 {
     static constexpr int kN = 2;
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
+    static constexpr bool kObstacle = true;   // supports the reach-avoid obstacle (dims 0, 1 a position)
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
                                                  const GameParams& g, const float* = nullptr) {
         const float y0 = fmaf(sk, z[0], yoff[0]), y1 = fmaf(sk, z[1], yoff[1]);
@@ -189,6 +192,7 @@ struct Rockets6 {
     static constexpr int kN = 6;
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
+    static constexpr bool kObstacle = false;   // supports the reach-avoid obstacle (dims 0, 1 a position)
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
                                                  const GameParams&, const float* = nullptr) {
         const float dx = fmaf(sk, z[0] - z[2], yoff[0] - yoff[2]);
@@ -231,6 +235,7 @@ struct Rockets45 {
     static constexpr int kN = 45;
     static constexpr bool kRadius = true;
     static constexpr int kAux = 0;
+    static constexpr bool kObstacle = false;   // supports the reach-avoid obstacle (dims 0, 1 a position)
     __device__ static double ell_d(const double* x, const GameParams& g, const float* = nullptr) {
         double best = INFINITY;
         for (int i = 0; i < 14; ++i) {
@@ -298,6 +303,7 @@ struct Flock4 {
     static constexpr int kN = 4;
     static constexpr bool kRadius = true;
     static constexpr int kAux = 22;
+    static constexpr bool kObstacle = false;   // supports the reach-avoid obstacle (dims 0, 1 a position)
     static constexpr int kNbr = 7;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
                                                  const GameParams&, const float* aux) {
@@ -352,6 +358,7 @@ struct Quadratic {
     static constexpr int kN = NDIM;
     static constexpr bool kRadius = false;
     static constexpr int kAux = 0;
+    static constexpr bool kObstacle = false;
     __device__ static __forceinline__ float dist(const float* z, const float* yoff, float sk,
                                                  const GameParams& g, const float* = nullptr) {
         float e[NDIM];

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kF64Threads) sweep_kernel_f64(const SweepArgs 
                 for (int d = 0; d < n; ++d) {   // Cor. B.5 / B.6, centred form
                     pd[d] = -(th[d] + sig.sigma_d * St[d] / st) / (c * sig.sigma2_d);
                 }
-                obstacle_project(x, A.g, n, v, pd);   // reach-avoid: v >= o(x)
+                if (G::kObstacle) obstacle_project(x, A.g, n, v, pd);   // reach-avoid: v >= o(x)
                 for (int d = 0; d < n; ++d) {
                     pp += pd[d] * pd[d];
                     finite = finite && isfinite(pd[d]);

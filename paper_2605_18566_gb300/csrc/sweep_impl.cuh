@@ -289,7 +289,7 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
         const double s = sh.s;
         const double logmean = sh.mx * kLn2 - th2 / (2.0 * sh.sig.sigma2_d) + log(sh.s_use / (double)A.N);
         double v = -logmean / c;
-        if (obstacle_project(sh.x, A.g, n, v, sh.pd)) {   // reach-avoid: v >= o(x)
+        if (G::kObstacle && obstacle_project(sh.x, A.g, n, v, sh.pd)) {   // reach-avoid: v >= o(x)
             pp = 0.0;
             finite = true;
             for (int j = 0; j < n; ++j) {
@@ -500,7 +500,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, const Sig& sig, i
         finite = finite && isfinite(pj);
     }
     double v = -((double)m * kLn2 - th2 / (2.0 * sig.sigma2_d) + log(sd / (double)A.N)) / cd;
-    if (obstacle_project(xd, A.g, n, v, pd)) {   // reach-avoid: v >= o(x)
+    if (G::kObstacle && obstacle_project(xd, A.g, n, v, pd)) {   // reach-avoid: v >= o(x)
         pp = 0.0;
         finite = true;
         for (int j = 0; j < n; ++j) {
