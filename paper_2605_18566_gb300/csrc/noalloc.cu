@@ -140,6 +140,24 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     GameKernels kern{};
     if (!pick_kernels(dyn, &kern)) return HJG_EINVAL;
     if (!obstacle_ok(dyn, target)) return HJG_EUNSUPPORTED;
+    // every option is checked before any device work
+    const double delta = 2.0 * nu;
+    const double sigma2 = delta * T;
+    const double eta = opt->eta < 0 ? 1e-6 : opt->eta;
+    const double c_min = opt->c_min > 0 ? opt->c_min : 1e-2 / delta;
+    const double c_max = opt->c_max > 0 ? opt->c_max : 1e2 / delta;
+    if (!(c_min <= c_max)) return HJG_EINVAL;
+    const bool tilt = opt->tilt != 0;
+    int variant = opt->variant > 0 ? opt->variant - 1 : 0;
+    if (variant >= kern.nvariants) return HJG_EINVAL;
+    if (opt->precision < 0 || opt->precision > 1) return HJG_EINVAL;
+    if (opt->cv) {
+        if (!kern.has_cv || (kern.cv_tilt_only && !tilt) || opt->precision) return HJG_EUNSUPPORTED;
+        variant = kCvVariant;
+    } else if (opt->precision == 1) {
+        if (!kern.has_f64) return HJG_EUNSUPPORTED;
+        variant = kF64Variant;
+    }
     const int n = dyn->n;
     if (ld < n || ldg < n) return HJG_EINVAL;
     if (M > 0 && (!pts || !v_out || !grad_out)) return HJG_EINVAL;
@@ -163,23 +181,6 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     unsigned long long* cnt = (unsigned long long*)(b + off_cnt);
     double* resid = (double*)(b + off_res);
 
-    const double delta = 2.0 * nu;
-    const double sigma2 = delta * T;
-    const double eta = opt->eta < 0 ? 1e-6 : opt->eta;
-    const double c_min = opt->c_min > 0 ? opt->c_min : 1e-2 / delta;
-    const double c_max = opt->c_max > 0 ? opt->c_max : 1e2 / delta;
-    if (!(c_min <= c_max)) return HJG_EINVAL;
-    const bool tilt = opt->tilt != 0;
-    int variant = opt->variant > 0 ? opt->variant - 1 : 0;
-    if (variant >= kern.nvariants) return HJG_EINVAL;
-    if (opt->precision < 0 || opt->precision > 1) return HJG_EINVAL;
-    if (opt->cv) {
-        if (!kern.has_cv || (kern.cv_tilt_only && !tilt) || opt->precision) return HJG_EUNSUPPORTED;
-        variant = kCvVariant;
-    } else if (opt->precision == 1) {
-        if (!kern.has_f64) return HJG_EUNSUPPORTED;
-        variant = kF64Variant;
-    }
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
