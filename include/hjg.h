@@ -180,7 +180,9 @@ hjg_status hjg_set_points(hjg_ctx *ctx, const float *pts, int64_t M, int64_t ld,
 /* Run n_sweeps Picard sweeps (Algorithm 1 loop body) on the loaded states, continuing the
  * global sweep counter.  residual_out / supnorm_out: host arrays of n_sweeps doubles
  * (relative L2 change and sup-norm change per sweep) or NULL (then the call does not
- * synchronise).  ENONFINITE if any state produced a non-finite v or Dv. */
+ * synchronise); the relative change divides by ||v^(k)||_2 as IEEE arithmetic does (+inf,
+ * or NaN when v^(k+1) = v^(k) = 0, if every loaded value is 0).  ENONFINITE if any state
+ * produced a non-finite v or Dv. */
 hjg_status hjg_picard_sweep(hjg_ctx *ctx, int n_sweeps, double *residual_out, double *supnorm_out);
 
 /* Copy the current iterate out: v [M] FP64, p = Dv [M][ldp] FP32, c [M] FP32 (the frozen
