@@ -195,6 +195,16 @@ void fill_game_params(hjg_ctx* ctx) {
 
 hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
     if (M <= ctx->cap) return HJG_OK;
+    // Drop the loaded states and the recorded sizes first: if an allocation below fails,
+    // the context holds no states (every later call sees M = 0) and the next load grows
+    // every buffer again, instead of trusting a capacity some buffers no longer have.
+    ctx->M = 0;
+    ctx->m_base = 0;
+    ctx->last_sweeps = 0;
+    ctx->se_valid = false;
+    ctx->cap = 0;
+    if (ctx->d_vhist) { cudaFree(ctx->d_vhist); ctx->d_vhist = nullptr; }
+    ctx->vhist_rows = 0;
     hjg_status st;
     if ((st = grow(ctx, &ctx->d_x, (size_t)M * ctx->ldx))) return st;
     if ((st = grow(ctx, &ctx->d_v, (size_t)M))) return st;
@@ -208,7 +218,6 @@ hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
         if ((st = grow(ctx, &ctx->d_aux, (size_t)M * kFlockAux))) return st;
         if ((st = grow(ctx, &ctx->d_idx, (size_t)M * 7))) return st;
     }
-    if (ctx->d_vhist) { cudaFree(ctx->d_vhist); ctx->d_vhist = nullptr; ctx->vhist_rows = 0; }
     ctx->cap = M;
     return HJG_OK;
 }
@@ -216,10 +225,12 @@ hjg_status ensure_capacity(hjg_ctx* ctx, int64_t M) {
 hjg_status ensure_history(hjg_ctx* ctx, int K) {
     hjg_status st;
     if (K + 1 > ctx->vhist_rows) {
+        ctx->vhist_rows = 0;   // a failed growth leaves no rows to trust
         if ((st = grow(ctx, &ctx->d_vhist, (size_t)(K + 1) * ctx->cap))) return st;
         ctx->vhist_rows = K + 1;
     }
     if (K > ctx->resid_cap) {
+        ctx->resid_cap = 0;
         if ((st = grow(ctx, &ctx->d_resid, (size_t)2 * K))) return st;
         if ((st = grow(ctx, &ctx->d_parts, (size_t)3 * K))) return st;
         ctx->resid_cap = K;
@@ -518,7 +529,8 @@ hjg_status hjg_picard_sweep(hjg_ctx* ctx, int n_sweeps, double* residual_out, do
     if (n_sweeps < 0) return fail(ctx, HJG_EINVAL, "n_sweeps < 0");
     if ((uint64_t)ctx->next_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull)
         return fail(ctx, HJG_EINVAL, "sweep counter would overflow");
-    if (n_sweeps == 0 || ctx->M == 0) { ctx->last_sweeps = 0; return HJG_OK; }
+    ctx->last_sweeps = 0;   // until this call's sweeps have been launched
+    if (n_sweeps == 0 || ctx->M == 0) return HJG_OK;
     hjg_status s;
     if ((s = ensure_history(ctx, n_sweeps))) return s;
     if ((s = choose_launch(ctx))) return s;
@@ -872,6 +884,7 @@ hjg_status hjg_batch_run(hjg_batch* b, int n_sweeps, double* residual_out, void*
         if (c->M == 0) { b->err = "a batch instance has no states loaded"; return HJG_EINVAL; }
         if ((uint64_t)c->next_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull) return HJG_EINVAL;
         hjg_status s;
+        c->last_sweeps = 0;   // until this call's sweeps have been launched
         if ((s = ensure_history(c, n_sweeps)) || (s = choose_launch(c))) {
             b->err = c->err;
             return s;
