@@ -279,7 +279,10 @@ const char *hjg_status_string(hjg_status s);
  * routine.  The first call on each device looks up that array's device address (with
  * the device current), so make it before any stream capture.  Asynchronous on `stream`;
  * calls share the array, so calls that overlap on the GPU race and must be serialised by
- * the caller.  Default launch variant 0 (opt->variant > 0 selects another). */
+ * the caller.  Default launch variant 0 (opt->variant > 0 selects another).  Every game
+ * but the flock (HJG_FLOCK4 returns EINVAL: its neighbour data is per-agent storage), with
+ * the options of hjg_create (tilt, tube, obstacle, cv, precision, point_offset); every
+ * argument is checked, and a refusal returned, before any device work. */
 hjg_status hjg_value_grad_noalloc(const hjg_dynamics *dyn, const hjg_target *target, double nu,
                                   double T, const hjg_options *opt, const float *pts, int64_t M,
                                   int64_t ld, double *v_out, float *grad_out, int64_t ldg,

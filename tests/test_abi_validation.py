@@ -83,3 +83,9 @@ def test_noalloc_refusals_before_any_device_work(lib):
     dyn, tgt, opt = _args(_lib, "rockets45", 45)
     opt.precision = 1
     assert call(dyn, tgt, opt) == _lib.HJG_EUNSUPPORTED
+    # the flock's neighbour data needs per-agent storage: not on the allocation-free path
+    dyn, tgt, opt = _args(_lib, "flock4", 4)
+    assert call(dyn, tgt, opt) == _lib.HJG_EINVAL
+    # no sweeps requested
+    dyn, tgt, opt = _args(_lib, K=0)
+    assert call(dyn, tgt, opt) == _lib.HJG_EINVAL
