@@ -26,9 +26,12 @@ def _stream_handle(stream: Optional[torch.cuda.Stream]):
 class Solver:
     """One game instance of the frozen-coefficient Picard sweep (Algorithm 1).
 
-    game: 'dubins3' | 'rockets6' | 'rockets45' | 'quadratic' | 'zero_h';
+    game: 'dubins3' | 'rockets6' | 'rockets45' | 'flock4' | 'rockets_rel3' | 'double_int2'
+    | 'quadratic' | 'zero_h' (the last two need n, A, x0, d: the closed-form test games);
     nu: viscosity with delta = 2 nu; T: horizon; N: samples per state and sweep;
-    K: sweeps run by value_grad.
+    K: sweeps run by value_grad.  The keyword options map one to one onto hjg_options and
+    hjg_target (tilt, tube, cv, obstacle=(cx, cy, r), precision 'fp32' | 'fp64', variant,
+    point_offset, seed, instance, eps, eta, c_min, c_max).
     """
 
     def __init__(self, game: str, nu: float, T: float, N: int, K: int = 10, *,
@@ -118,9 +121,10 @@ class Solver:
         """x: [M, ld] float32 (ld >= n), on the GPU or in host memory."""
         assert x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1
         on_dev = 1 if x.is_cuda else 0
-        self.M = x.shape[0] * getattr(self, "n_horizons", 1)
+        self.M = 0   # a refused load leaves no states to read back
         _check(self.lib, self.ctx, self.lib.hjg_set_points(
             self.ctx, self._ptr(x), x.shape[0], x.stride(0), on_dev, None))
+        self.M = x.shape[0] * getattr(self, "n_horizons", 1)
 
     def picard_sweep(self, n_sweeps: int, residuals: bool = True):
         """Run n_sweeps sweeps; returns (relative L2 residual, sup-norm) per sweep as numpy,
@@ -195,12 +199,13 @@ class Solver:
             grad_out = torch.empty(M, self.n, dtype=torch.float32, **kw)
         K = self.opt.K
         r = np.full(max(K, 1), np.nan)
-        self.M = M
+        self.M = 0
         st = self.lib.hjg_value_grad(self.ctx, self._ptr(x), x.shape[0], x.stride(0), 1 if dev else 0,
                                      self._ptr(v_out), self._ptr(grad_out), grad_out.stride(0),
                                      r.ctypes.data_as(C.c_void_p), None)
         if st not in (_lib.HJG_OK, _lib.HJG_ENONFINITE):
             _check(self.lib, self.ctx, st)
+        self.M = M
         self.last_status = st
         return v_out, grad_out, r[:K]
 
