@@ -20,7 +20,10 @@
  *   - Games: Appendix D.2 Dubins relative game (Hamiltonian of Eq. dubins_ham_unit
  *     with the sign of the p2 term taken from the dynamics of Eq. dubins_dyna),
  *     Section 3.2 multi-rocket game (Eq. multiagent_dynamics), a two-rocket planar game
- *     built from the same per-agent dynamics, and quadratic test problems
+ *     built from the same per-agent dynamics, the relative two-rocket game (Eq. ham_def),
+ *     the double integrator (Eq. dint_ham), the flock of Appendix D.5 (aerial Dubins
+ *     agents steered toward the circular mean heading of their 7 nearest neighbours,
+ *     target = nearness to those neighbours), and quadratic test problems
  *     (H = +-|p|^2/2, the exact Cole-Hopf case of Corollary B.2).
  *   - Reach-avoid tube (reading of Eq. HJI-RCBRAT-Visc): an avoid disc whose constraint
  *     function o enters the datum as max{l, o} and bounds the value from below after every
