@@ -430,8 +430,10 @@ hjg_status hjg_create(const hjg_dynamics* dyn, const hjg_target* target, double 
         delete ctx;
         return HJG_ENOMEM;
     }
-    cudaEventCreate(&ctx->ev0);
-    cudaEventCreate(&ctx->ev1);
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        hjg_destroy(ctx);
+        return HJG_ECUDA;
+    }
     *out = ctx;
     return HJG_OK;
 }
@@ -838,7 +840,7 @@ hjg_status hjg_batch_create(hjg_batch** out) {
     if (!b) return HJG_ENOMEM;
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
-        delete b;
+        hjg_batch_destroy(b);   // releases whichever events were created
         return HJG_ECUDA;
     }
     *out = b;
