@@ -164,6 +164,40 @@ def test_laplace_tilt_reduces_variance():
     assert ess1[0] > 3 * ess0[0]
 
 
+@pytest.mark.parametrize("c", [0.7, 3.0])
+def test_ess_closed_form(c):
+    """Effective sample size (Section 2.4), ESS = (sum w)^2 / sum w^2: ESS / N converges to
+    (E w)^2 / E w^2, and for a quadratic target both moments are Gaussian integrals,
+    E exp(-c l) = exp(-c v_c) and E exp(-2c l) = exp(-2c v_2c) with v_c of the closed form
+    above, so ESS / N -> exp(2c (v_2c - v_c)).  A constant target (A = 0) gives equal
+    weights and ESS = N exactly.  The replica means land within ~1e-4 to 7e-4 of the
+    closed form, so a wrong power or shift in either sum fails."""
+    n = 3
+    A = hjg_inputs.spd_matrix(n, 0.4, 1.1, seed=21); x0 = np.array([0.3, -0.2, 0.1]); d = 0.4
+    delta, T = 0.2, 1.0
+    sigma2 = delta * T
+    P = oracle.make_problem("quadratic", n, delta, T, A=A, x0=x0, d=d)
+    x = hjg_inputs.random_states(3, n, 1.0, seed=22).astype(np.float64)
+    cc = np.full(len(x), c)
+    N, R = 1 << 15, 6
+    ratios = []
+    for r in range(R):
+        P.seed = 2000 + r
+        _, _, ess = oracle.sweep(P, x, cc, N, 0)
+        ratios.append(ess / N)
+    ratios = np.array(ratios)
+    for m in range(len(x)):
+        v_c, _ = quad_closed_form(A, x0, d, x[m], c, sigma2)
+        v_2c, _ = quad_closed_form(A, x0, d, x[m], 2.0 * c, sigma2)
+        ref = math.exp(2.0 * c * (v_2c - v_c))
+        assert 0.0 < ref < 1.0
+        se = ratios[:, m].std(ddof=1) / math.sqrt(R) + 1e-4
+        assert abs(ratios[:, m].mean() - ref) < 5 * se, (m, ratios[:, m].mean(), ref)
+    P0 = oracle.make_problem("quadratic", n, delta, T, A=np.zeros((n, n)), x0=x0, d=d)
+    _, _, ess0 = oracle.sweep(P0, x, cc, 4096, 0)
+    np.testing.assert_allclose(ess0, 4096.0, rtol=1e-12)
+
+
 def test_mc_error_law():
     """RMS error of the value estimator falls as N^-1/2 (Theorem 2.4)."""
     n = 2
