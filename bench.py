@@ -91,6 +91,16 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(value, device):
+    """The largest value over the ranks of the default process group: the slowest rank's
+    time, which the whole job's throughput is divided by."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -210,9 +220,7 @@ def run_ours(args, rank, world, local_rank):
         final_v, final_p = st["v"].cpu().numpy(), st["p"].cpu().numpy()
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
 
     # ---- end to end through the public API with pinned host buffers
     x_host = torch.from_numpy(x_np).pin_memory()
@@ -228,9 +236,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dev)
     solver.close()
 
     samples_per_step = W.M * W.N * W.K
