@@ -62,6 +62,18 @@ def test_struct_layout_matches_header(tmp_path):
             assert int(got["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
 
 
+def test_header_is_plain_c_and_cxx(tmp_path):
+    """The boundary header compiles warning-free as strict C99 and as C++11, so C callers
+    and C++ callers see the same declarations."""
+    prog = tmp_path / "hdr.c"
+    prog.write_text('#include "hjg.h"\nint main(void) { return sizeof(hjg_options) > 0 ? 0 : 1; }\n')
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                    str(prog), "-o", str(tmp_path / "c99")], check=True)
+    subprocess.run(["g++", "-std=c++11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                    "-x", "c++", str(prog), "-o", str(tmp_path / "cxx11")], check=True)
+
+
 def test_missing_library_fails_loudly():
     from paper_2605_18566_gb300 import _lib
     saved = _lib._lib
