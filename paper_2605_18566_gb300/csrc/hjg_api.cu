@@ -93,6 +93,7 @@ hjg_status grow(hjg_ctx* ctx, T** ptr, size_t count) {
     cudaError_t e = cudaMalloc((void**)ptr, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) {
         *ptr = nullptr;
+        cudaGetLastError();   // reported here as ENOMEM: not left for a later launch check to find
         return fail(ctx, HJG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
                     cudaGetErrorString(e));
     }

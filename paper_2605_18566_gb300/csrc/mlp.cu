@@ -776,7 +776,9 @@ hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
     if (B <= m->cap) return HJG_OK;
     auto fre = [](void* p) { if (p) cudaFree(p); };
     fre(m->X); fre(m->dZ); fre(m->dZ2); fre(m->dZt); fre(m->dH); fre(m->lpart); fre(m->packA); fre(m->packB);
-    m->packA = m->packB = m->dZ2 = m->dZt = nullptr;
+    m->X = m->dZ = m->dZ2 = m->dZt = m->packA = m->packB = nullptr;   // none survives a failed growth
+    m->dH = nullptr;
+    m->lpart = nullptr;
     for (int l = 0; l < kLayers; ++l) {
         fre(m->Z[l]); fre(m->H[l]); fre(m->Ht[l]);
         m->Z[l] = nullptr; m->H[l] = nullptr; m->Ht[l] = nullptr;
@@ -799,7 +801,12 @@ hjg_status mlp_ensure(hjg_mlp* m, int64_t B) {
     }
     m->lpart_cap = (B * m->out_pad + 255) / 256;
     ok = ok && cudaMalloc(&m->lpart, (size_t)m->lpart_cap * sizeof(double)) == cudaSuccess;
-    if (!ok) { m->cap = 0; m->err = "MLP work buffers: out of memory"; return HJG_ENOMEM; }
+    if (!ok) {
+        cudaGetLastError();   // reported here as ENOMEM: not left for a later launch check to find
+        m->cap = 0;
+        m->err = "MLP work buffers: out of memory";
+        return HJG_ENOMEM;
+    }
     m->cap = B;
     return HJG_OK;
 }

@@ -88,3 +88,36 @@ def test_point_offset_range():
     with pytest.raises(HJGError):
         s.set_points(x)
     s.close()
+
+
+def test_failed_growth_leaves_the_context_usable():
+    """A load the device cannot hold (2^31 states of the 45-D game: 412 GB of padded state
+    rows, refused by the first allocation, before any state is read) returns HJG_ENOMEM and
+    leaves the context with no states; the failed allocation is not reported again by the
+    next sweep, and a later load solves exactly as a fresh context does."""
+    import ctypes as C
+    from paper_2605_18566_gb300 import _lib
+    w = hjg_inputs.ROCKETS45
+    x = torch.from_numpy(hjg_inputs.points(w, M=64)).cuda()
+    s = solver_for(w, N=256, K=2)
+    s.set_points(x)
+    s.picard_sweep(2)
+    huge = 1 << 31
+    assert huge * 48 * 4 > 300e9   # more than the device holds: the first cudaMalloc fails
+    st = s.lib.hjg_set_points(s.ctx, C.c_void_p(x.data_ptr()), huge, x.stride(0), 1, None)
+    assert st == _lib.HJG_ENOMEM
+    r = np.full(2, -1.0)
+    assert s.lib.hjg_picard_sweep(s.ctx, 1, r.ctypes.data_as(C.c_void_p), None) == _lib.HJG_OK
+    assert r[0] == -1.0            # no states loaded: nothing ran
+    s.set_points(x)
+    r1, _ = s.picard_sweep(2)
+    got = {k: t.cpu().numpy() for k, t in s.get_state().items()}
+    s.close()
+    f = solver_for(w, N=256, K=2)
+    f.set_points(x)
+    r2, _ = f.picard_sweep(2)
+    ref = {k: t.cpu().numpy() for k, t in f.get_state().items()}
+    f.close()
+    for key in ("v", "p", "c"):
+        np.testing.assert_array_equal(got[key], ref[key])
+    np.testing.assert_array_equal(r1, r2)
