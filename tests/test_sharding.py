@@ -65,6 +65,42 @@ def test_two_rank_sharded_solve_equals_unsharded(tmp_path):
     np.testing.assert_array_equal(v, full["v"])
 
 
+def _combine_main(rank, world, port, parts_all, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    rel, sup = sharding.combine_residual_parts(parts_all[rank])
+    np.savez(os.path.join(out_dir, "c%d.npz" % rank), rel=rel, sup=sup)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_three_ranks_one_empty_shard():
+    """More ranks than a shard has states: an empty rank contributes zero sums and a zero
+    maximum (what hjg_get_residual_parts leaves after a sweep over no states), and every
+    rank ends with the residual of the states that exist."""
+    import tempfile
+    import torch.multiprocessing as mp
+    M, world = 2, 3
+    assert [sharding.shard_bounds(M, world, r) for r in range(world)] == [(0, 1), (1, 2), (2, 2)]
+    rng = np.random.default_rng(3)
+    K = 4
+    v_hist = rng.normal(size=(K + 1, M)) + 2.0
+    parts_all = [_parts(v_hist[:, r:r + 1]) for r in range(2)] + [np.zeros((K, 3))]
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_combine_main, args=(world, port, parts_all, d), nprocs=world,
+                           start_method="spawn", join=True)
+        want = _parts(v_hist)
+        for r in range(world):
+            got = np.load(os.path.join(d, "c%d.npz" % r))
+            np.testing.assert_allclose(got["rel"], np.sqrt(want[:, 0] / want[:, 1]), rtol=1e-14)
+            np.testing.assert_array_equal(got["sup"], want[:, 2])
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("world", [2, 3])
 def test_gpu_shards_reproduce_unsharded_solve(world):
