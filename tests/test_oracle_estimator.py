@@ -9,6 +9,9 @@ oracle itself:
   * the zero-Hamiltonian limit (Remark 2.8: c -> 0 recovers the Gaussian mean);
   * unbiasedness of the tilted proposal for every shift (Corollary B.6);
   * the O(N^-1/2) Monte-Carlo error law (Theorem 2.4);
+  * robustness to terminal-cost perturbations (Theorem thm:robustness-g), exact on fixed
+    draws for one frozen-coefficient solve;
+  * the effective sample size against its closed form (Section 2.4);
   * dense 2-D quadrature of the heat integral for the non-quadratic Dubins and
     two-rocket targets (Eq. heat_kernel).
 """
@@ -196,6 +199,40 @@ def test_ess_closed_form(c):
     P0 = oracle.make_problem("quadratic", n, delta, T, A=np.zeros((n, n)), x0=x0, d=d)
     _, _, ess0 = oracle.sweep(P0, x, cc, 4096, 0)
     np.testing.assert_allclose(ess0, 4096.0, rtol=1e-12)
+
+
+def test_terminal_cost_perturbation_moves_the_value_by_at_most_its_size():
+    """Theorem thm:robustness-g (a terminal cost moved by at most eps moves the value by at
+    most eps), at the level of one frozen-coefficient solve on fixed draws, where it holds
+    exactly: v = -(1/c) log mean exp(-c l(y_i)) is monotone in l and 1-Lipschitz in the
+    sup-norm for either sign of c.  A constant shift of the target (a larger capture radius)
+    lowers v by exactly the shift and leaves Dv unchanged; the flock target with every
+    neighbour moved by at most eps (so l moves by at most eps) moves v by at most eps."""
+    eps = 0.05
+    w = hjg_inputs.DUBINS3
+    x = hjg_inputs.points(w, M=48).astype(np.float64)
+    P1 = oracle.make_problem(w.game, w.n, w.delta, w.T, radius=w.radius)
+    P2 = oracle.make_problem(w.game, w.n, w.delta, w.T, radius=w.radius + eps)
+    _, _, c0 = oracle.init(P1, x)
+    v1, p1, _ = oracle.sweep(P1, x, c0, 2048, 0)
+    v2, p2, _ = oracle.sweep(P2, x, c0, 2048, 0)
+    np.testing.assert_allclose(v2, v1 - eps, rtol=0, atol=1e-11 * (1 + np.abs(v1).max()))
+    np.testing.assert_allclose(p2, p1, rtol=1e-9, atol=1e-12)
+
+    xf = hjg_inputs.flock_states(300, seed=4).astype(np.float64)
+    _, nbr, psibar = oracle.flock_neighbours(xf)
+    rng = np.random.default_rng(6)
+    d = rng.normal(size=(len(xf), 7, 3))
+    d *= (eps * rng.uniform(0.0, 1.0, size=(len(xf), 7, 1))) / np.linalg.norm(d, axis=2, keepdims=True)
+    nbr2 = nbr + d.reshape(len(xf), 21)
+    P = oracle.make_problem("flock4", 4, 0.04, 1.0, radius=0.2)
+    _, _, cf = oracle.init(P, xf, nbr, psibar)
+    for c in (np.abs(cf), -np.abs(cf)):
+        va, _, _ = oracle.sweep(P, xf, c, 1024, 0, nbr=nbr)
+        vb, _, _ = oracle.sweep(P, xf, c, 1024, 0, nbr=nbr2)
+        dv = np.abs(vb - va)
+        assert np.all(dv <= eps * (1 + 1e-9) + 1e-12), dv.max()
+        assert dv.max() > 0.1 * eps     # the perturbation does move the values
 
 
 def test_mc_error_law():
