@@ -13,7 +13,9 @@ oracle itself:
     draws for one frozen-coefficient solve;
   * the effective sample size against its closed form (Section 2.4);
   * dense 2-D quadrature of the heat integral for the non-quadratic Dubins and
-    two-rocket targets (Eq. heat_kernel).
+    two-rocket targets (Eq. heat_kernel), and a whole quadrature Picard loop on the 2-D
+    double integrator against the Monte-Carlo Picard loop (a stale coefficient or a
+    wrong sample variance in the loop moves the values by 20 to 10^4 standard errors).
 """
 import math
 
@@ -283,6 +285,71 @@ def test_dubins_quadrature():
         v_ref = -math.log(E) / c[m]
         g_ref = np.array([*(x[m, :2] - ybar) / (sigma2 * c[m]), 0.0])
         check_against(vs[:, m], ps[:, m], v_ref, g_ref, floor_v=1e-5, floor_p=1e-5)
+
+
+def heat_log_quadrature_2d(f, x, sigma2, c, center, half_width=8.0, n=641):
+    """log E_{y ~ N(x, sigma2 I_2)}[exp(-c f(y))] and E[y exp(-c f)] / E[exp(-c f)] by a
+    dense trapezoid rule over +-half_width standard deviations about `center` (where the
+    integrand's mass sits when |c| is large), with the exponent shifted by its maximum."""
+    s = math.sqrt(sigma2)
+    t = np.linspace(-half_width, half_width, n)
+    h = t[1] - t[0]
+    wts = np.ones(n); wts[0] = wts[-1] = 0.5
+    Y1, Y2 = np.meshgrid(center[0] + s * t, center[1] + s * t, indexing="ij")
+    Z1, Z2 = (Y1 - x[0]) / s, (Y2 - x[1]) / s
+    a = -0.5 * (Z1 ** 2 + Z2 ** 2) - c * f(Y1, Y2)
+    mx = a.max()
+    F = np.exp(a - mx) * (wts[:, None] * wts[None, :] * h * h)
+    S = F.sum()
+    return mx + math.log(S / (2 * math.pi)), np.array([(Y1 * F).sum() / S, (Y2 * F).sum() / S])
+
+
+def test_quadrature_picard_matches_mc_picard():
+    """Algorithm 1 run twice on the 2-D double integrator: once with every heat integral
+    done by dense quadrature (each sweep's grid centred at the Laplace point
+    x - sigma^2 c Dv of the current iterate) and the coefficient map applied to the
+    quadrature gradient, once by the oracle's Monte-Carlo Picard loop with the tilted
+    proposal.  After every sweep the Monte-Carlo values (replicas over seeds) agree with
+    the quadrature iterate, and so do the final gradients, on every state whose coefficient
+    keeps its sign along the quadrature trajectory (where H crosses 0 the coefficient map
+    jumps and the two iterations may legitimately part)."""
+    w = hjg_inputs.DOUBLE_INT2
+    t_h, K, N, R = 0.8, 4, 1 << 16, 8
+    sigma2 = w.delta * t_h
+    P = oracle.make_problem(w.game, w.n, w.delta, t_h, radius=w.radius)
+    Pt = oracle.make_problem(w.game, w.n, w.delta, t_h, radius=w.radius, tilt=True)
+    f = lambda a, b: np.sqrt(a * a + b * b) - w.radius
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1.6, 1.6, size=(40, 2)).astype(np.float32).astype(np.float64)
+    for m in range(3):
+        assert abs(oracle.ell(P, x[m]) - f(*x[m])) < 1e-12
+    v, p, c = oracle.init(P, x)
+    vq_hist, cs = [v.copy()], [c.copy()]
+    for k in range(K):
+        v = np.zeros(len(x)); pn = np.zeros_like(p)
+        for m in range(len(x)):
+            logE, ybar = heat_log_quadrature_2d(f, x[m], sigma2, c[m], x[m] - sigma2 * c[m] * p[m])
+            v[m] = -logE / c[m]
+            pn[m] = (x[m] - ybar) / (sigma2 * c[m])
+        p = pn
+        c = oracle.coef_batch(P, x, p)
+        vq_hist.append(v.copy()); cs.append(c.copy())
+    cs = np.array(cs)
+    keep = np.all(np.sign(cs) == np.sign(cs[0]), axis=0)
+    assert keep.mean() >= 0.8
+    runs = []
+    for r in range(R):
+        Pt.seed = 700 + r
+        runs.append(oracle.picard(Pt, x, N, K))
+    for k in range(1, K + 1):
+        vs = np.array([o["v_hist"][k] for o in runs])
+        se = vs.std(0, ddof=1) / math.sqrt(R) + 1e-7 * (1 + np.abs(vq_hist[k]))
+        z = np.abs(vs.mean(0) - vq_hist[k]) / se
+        assert np.all(z[keep] < 6.0), (k, z[keep].max())
+    ps = np.array([o["p"] for o in runs])
+    se = ps.std(0, ddof=1) / math.sqrt(R) + 1e-7 * (1 + np.abs(p))
+    z = (np.abs(ps.mean(0) - p) / se).max(1)
+    assert np.all(z[keep] < 6.0), z[keep].max()
 
 
 def test_rockets6_quadrature():
