@@ -134,7 +134,9 @@ def box_grid(lo, hi, m_side: int) -> np.ndarray:
 
 
 def points(w: Workload, M: int | None = None, seed: int | None = None) -> np.ndarray:
-    """Evaluation states of workload ``w`` (first M of them when M is given)."""
+    """Evaluation states of workload ``w``.  With M given: the first M states of a grid
+    workload, or M states drawn by a scattered workload's recipe (a draw of its own, not a
+    prefix of the full set: the recipe draws each coordinate block for all states at once)."""
     seed = w.seed if seed is None else seed
     if w.game == "dubins3":
         x = dubins_grid(16)
