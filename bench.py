@@ -37,6 +37,12 @@ import hjg_inputs  # noqa: E402
 METRIC = "point-samples/s per Picard sweep (v+grad v)"
 UNIT = "point-samples/s"
 W = hjg_inputs.ROCKETS6
+# The paper's own throughput on this path, for context only (its timings are CPU-only): its
+# 3-D slice runs (1,600 states, N = 14,000, 12 sweeps in 13.5 s; N = 20,000, 15 sweeps in
+# 23.6 s) give about 2.0e7 point-samples/s.
+PAPER_CONTEXT = {"value": 2.0e7, "unit": UNIT,
+                 "hardware": "one core of an Intel Core i7-14700K, JAX on the CPU backend",
+                 "derived_from": "3-D slice timings (states x N x sweeps / time)"}
 
 # Algorithmic per-point-sample work of the sweep on the two pipes that bind it (counts
 # for each workload's game; the block index sits in the Philox counter words the first
@@ -269,6 +275,7 @@ def run_ours(args, rank, world, local_rank):
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
         "residuals": [float(r) for r in resid],
         "sweeps_to_floor": sweeps_to_floor(resid),
+        "paper_context": PAPER_CONTEXT,
     }
     out["_final"] = (final_v, final_p)
     return out

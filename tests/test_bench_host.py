@@ -119,3 +119,11 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1, proc.stdout[-2000:]
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_paper_context_is_the_derived_rate():
+    # rockets slices: 1,600 states x N = 14,000 x 12 sweeps in 13.5 s; Dubins: N = 20,000,
+    # 15 sweeps in 23.6 s
+    for rate in (1600 * 14000 * 12 / 13.5, 1600 * 20000 * 15 / 23.6):
+        assert bench.PAPER_CONTEXT["value"] == pytest.approx(rate, rel=0.02)
+    json.dumps(bench.PAPER_CONTEXT)
