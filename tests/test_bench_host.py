@@ -127,3 +127,17 @@ def test_paper_context_is_the_derived_rate():
     for rate in (1600 * 14000 * 12 / 13.5, 1600 * 20000 * 15 / 23.6):
         assert bench.PAPER_CONTEXT["value"] == pytest.approx(rate, rel=0.02)
     json.dumps(bench.PAPER_CONTEXT)
+
+
+def test_clock_summary_parses_the_sampled_lines():
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["unsampled"]
+    cs.lines = ["0, 2070, 2070, 910.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+                "0, 1995, 2070, 1395.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+                "0, 2070, 2070, 1390.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+                "garbage", "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.lines.append("0, 1500, 2070, 1400, 0x8, Active, Not Active, Active, Not Active")
+    assert bench.ClockSampler.summary(cs)["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
