@@ -279,7 +279,11 @@ const char *hjg_status_string(hjg_status s);
  * routine.  The first call on each device looks up that array's device address (with
  * the device current), so make it before any stream capture.  Asynchronous on `stream`;
  * calls share the array, so calls that overlap on the GPU race and must be serialised by
- * the caller.  Default launch variant 0 (opt->variant > 0 selects another).  Every game
+ * the caller.  Default launch variant 0 (opt->variant > 0 selects another; otherwise
+ * opt->block_threads > 0 selects the first variant of that CTA size, as in hjg_create, and
+ * EINVAL if the game has none).  The call never synchronises, so it cannot see the
+ * sweep's non-finite counter and never returns HJG_ENONFINITE: a state whose v or Dv is
+ * not finite shows up as NaN or inf in v_out / grad_out, which the caller checks.  Every game
  * but the flock (HJG_FLOCK4 returns EINVAL: its neighbour data is per-agent storage), with
  * the options of hjg_create (tilt, tube, obstacle, cv, precision, point_offset); every
  * argument is checked, and a refusal returned, before any device work. */

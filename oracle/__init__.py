@@ -280,6 +280,36 @@ def picard(P, x, N, K, k0=0, state=None, nbr=None, psibar=None, idx=None):
             "resid": resid, "sup": sup, "ess": ess}
 
 
+def ill_conditioned(P, x, N, K, amp, ref, idx=None, nbr=None, psibar=None, tol_v=1e-4, tol_p=1e-3,
+                    reps=3):
+    """Which states of a K-sweep trajectory are too sensitive to be compared to FP32
+    rounding: the oracle's own run is repeated with its coefficient perturbed in every
+    sweep by relative Gaussian noise of size ``amp`` (per state, or one scalar), ``reps``
+    times; a state is ill-conditioned where any repeat ends more than a tenth of the
+    tolerance (|dv| / (1 + |v|) > tol_v / 10 or ||dDv|| / (1 + ||Dv||) > tol_p / 10) away
+    from the unperturbed run ``ref`` (a dict with v and p, as picard returns).  Where the
+    Picard map of Algorithm 1 is not contractive (c changing sign between sweeps, ESS near
+    1: outside Assumption 2.6) such a perturbation grows from sweep to sweep, and so does
+    an FP32 sweep's local rounding error."""
+    x = _f64(x).reshape(-1, P.n)
+    M = x.shape[0]
+    amp = np.broadcast_to(np.asarray(amp, dtype=np.float64), (M,))
+    v0, p0, c0 = init(P, x, nbr, psibar)
+    v_ref = np.asarray(ref["v"], np.float64); p_ref = np.asarray(ref["p"], np.float64)
+    ill = np.zeros(M, bool)
+    for rep in range(reps):
+        rng = np.random.default_rng(100 + rep)
+        st = (v0, p0, c0)
+        for k in range(K):
+            c_pert = st[2] * (1.0 + amp * rng.standard_normal(M))
+            out = picard(P, x, N, 1, k0=k, state=(st[0], st[1], c_pert), idx=idx, nbr=nbr, psibar=psibar)
+            st = (out["v"], out["p"], out["c"])
+        sv = np.abs(st[0] - v_ref) / (1.0 + np.abs(v_ref))
+        sp = np.linalg.norm(st[1] - p_ref, axis=1) / (1.0 + np.linalg.norm(p_ref, axis=1))
+        ill |= (sv > 0.1 * tol_v) | (sp > 0.1 * tol_p)
+    return ill
+
+
 def picard_horizons(P, x, N, K, times, nbr=None, psibar=None):
     """The value at several horizons t_h: for each h an independent run of Algorithm 1 at
     T = t_h (kernel width sqrt(delta t_h), Lemma 2.2) whose state m carries the global

@@ -150,6 +150,12 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     const bool tilt = opt->tilt != 0;
     int variant = opt->variant > 0 ? opt->variant - 1 : 0;
     if (variant >= kern.nvariants) return HJG_EINVAL;
+    if (opt->variant <= 0 && opt->block_threads > 0) {   // the first variant of that CTA size
+        variant = -1;
+        for (int i = 0; i < kern.nvariants && variant < 0; ++i)
+            if (kern.threads[i] == opt->block_threads) variant = i;
+        if (variant < 0) return HJG_EINVAL;
+    }
     if (opt->precision < 0 || opt->precision > 1) return HJG_EINVAL;
     if (opt->cv) {
         if (!kern.has_cv || (kern.cv_tilt_only && !tilt) || opt->precision) return HJG_EUNSUPPORTED;
@@ -201,7 +207,7 @@ extern "C" hjg_status hjg_value_grad_noalloc(const hjg_dynamics* dyn, const hjg_
     A.x = pts; A.p = grad_out; A.c = c; A.v = v_out; A.vhist = vhist; A.ess = ess; A.counters = cnt;
     A.ldx = ld; A.ldp = ldg; A.M = M; A.N = opt->N;
     A.rk = philox_round_keys((uint32_t)opt->seed, (uint32_t)(opt->seed >> 32) ^ opt->instance);
-    A.k0 = 0; A.K = K;
+    A.k0 = 0; A.pt0 = opt->point_offset; A.K = K;
     A.sigma_d = std::sqrt(sigma2);
     A.sigma = (float)A.sigma_d;
     A.sk = (float)(A.sigma_d * (double)kBmScale);

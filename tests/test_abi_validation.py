@@ -89,3 +89,7 @@ def test_noalloc_refusals_before_any_device_work(lib):
     # no sweeps requested
     dyn, tgt, opt = _args(_lib, K=0)
     assert call(dyn, tgt, opt) == _lib.HJG_EINVAL
+    # a CTA size the game has no launch variant for (the 6-D game has 128 and 256)
+    dyn, tgt, opt = _args(_lib, "rockets6", 6)
+    opt.block_threads = 96
+    assert call(dyn, tgt, opt) == _lib.HJG_EINVAL

@@ -35,29 +35,45 @@ def test_roofline_picks_the_binding_pipe():
     assert r["pipe"] == "mufu" and r["bound"] == "alu"
     assert r["frac"] == pytest.approx(1.0)
     assert r["other_pipes"]["int_mul_hi"] < 1.0
-    assert r["traffic"] is None                      # not the benchmark launch
-    r2 = bench.roofline("rockets6", hjg_inputs.ROCKETS6.M * 10, 1.0, states=hjg_inputs.ROCKETS6.M)
-    assert r2["traffic"] == bench.DRAM_BYTES_BENCH_LAUNCH
+    assert r["traffic"] is None                      # not a full-size launch
+    r2 = bench.roofline("rockets6", hjg_inputs.ROCKETS6.M * 10, 1.0, full_size=True)
+    assert r2["traffic"] == bench.DRAM_BYTES_LAUNCH["rockets6"]
 
 
 def test_sweeps_to_floor():
     r = [0.5, 0.2, 0.11, 0.1, 0.1, 0.1]
     out = bench.sweeps_to_floor(r)
     assert out["floor"] == pytest.approx(0.1)
-    assert out["sweeps"] == 3                        # 0.11 <= 1.1 * 0.1
+    assert out["sweeps"] == 3                        # |0.11 - 0.1| <= 0.1 * 0.1
     assert bench.sweeps_to_floor([0.3, 0.3, 0.3])["sweeps"] == 1
+    # a residual that dips and then rises back settles only where it enters the band for good
+    rise = [0.418, 0.097, 0.103, 0.118, 0.135, 0.150, 0.159, 0.163, 0.170, 0.178, 0.176, 0.178]
+    out = bench.sweeps_to_floor(rise)
+    assert out["floor"] == pytest.approx(0.178)
+    assert out["sweeps"] == 8                        # band [0.160, 0.196]: 0.163 onward
+    assert out["min"] == pytest.approx(0.097) and out["min_sweep"] == 2
+    # the last residual is outside the band: not settled (K + 1)
+    out = bench.sweeps_to_floor([1.0, 0.5, 0.25, 0.125, 0.3, 0.05])
+    assert out["sweeps"] == 7 and not out["settled"]
 
 
 def test_oracle_error_summary():
-    rng = np.random.default_rng(0)
-    v_ref = rng.normal(size=20); p_ref = rng.normal(size=(20, 3))
-    v = v_ref.copy(); p = p_ref.astype(np.float32).copy()
-    v[3] += 1.0                                      # one state far outside the tolerance
-    idx = np.arange(20)
-    out = bench.oracle_error((v, p), (idx, {"v": v_ref, "p": p_ref}))
+    """One state moved far off the oracle's trajectory: counted outside the tolerance and
+    classified (explained or not) by the oracle's own sensitivity there."""
+    import dataclasses
+    w = dataclasses.replace(hjg_inputs.DUBINS3, N=256, K=2)
+    x = hjg_inputs.points(w)
+    idx = hjg_inputs.subset_indices(w.M, 20, seed=3)
+    P = oracle.make_problem(w.game, w.n, w.delta, w.T, radius=w.radius)
+    ref = oracle.picard(P, x[idx].astype(np.float64), w.N, w.K, idx=idx)
+    v = np.zeros(w.M); p = np.zeros((w.M, w.n), np.float32)
+    v[idx] = ref["v"]; p[idx] = ref["p"]
+    v[idx[3]] += 1.0                                 # one state far outside the tolerance
+    out = bench.oracle_error((v, p), (idx, ref, P, x), w)
     assert out["states"] == 20
     assert out["within_tolerance"] == pytest.approx(19 / 20)
-    assert out["dv_max"] == pytest.approx(1.0 / (1.0 + abs(v_ref[3])))
+    assert out["dv_max"] == pytest.approx(1.0 / (1.0 + abs(ref["v"][3])))
+    assert out["outside_tolerance"] == 1 and out["explained"] + out["unexplained"] == 1
 
 
 @pytest.mark.timeout(600)
@@ -141,3 +157,53 @@ def test_clock_summary_parses_the_sampled_lines():
     assert s["reasons"] == ["sw_power_cap"]
     cs.lines.append("0, 1500, 2070, 1400, 0x8, Active, Not Active, Active, Not Active")
     assert bench.ClockSampler.summary(cs)["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+
+
+def _shard_rank_main(rank, world, port, out_dir):
+    """One gloo rank of the benchmark's sharded solve, its block computed by the oracle."""
+    import dataclasses
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = dataclasses.replace(hjg_inputs.ROCKETS6, M=203, N=512, K=3)
+    x = hjg_inputs.points(w, M=w.M).astype(np.float64)
+    P = oracle.make_problem(w.game, w.n, w.delta, w.T, radius=w.radius)
+
+    def solve_parts(lo, hi):
+        out = oracle.picard(P, x[lo:hi], w.N, w.K, idx=np.arange(lo, hi))
+        vh = out["v_hist"]
+        dv = np.diff(vh, axis=0)
+        parts = np.stack([(dv ** 2).sum(1), (vh[:-1] ** 2).sum(1), np.abs(dv).max(1)], 1)
+        return parts, out["v"]
+    lo, hi, rel, sup, v = bench.shard_solve(solve_parts, w.M, world, rank)
+    np.savez(os.path.join(out_dir, "rank%d.npz" % rank), rel=rel, sup=sup, v=v, lo=lo, hi=hi)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_bench_solve_equals_unsharded(tmp_path, world):
+    """The benchmark's multi-GPU path (contiguous blocks, Philox point offset, one
+    all-reduce of the residual parts) on gloo ranks whose blocks the oracle solves: every
+    rank holds the unsharded solve's residuals and its block's values bit for bit."""
+    import dataclasses
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_shard_rank_main, args=(world, port, str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    w = dataclasses.replace(hjg_inputs.ROCKETS6, M=203, N=512, K=3)
+    x = hjg_inputs.points(w, M=w.M).astype(np.float64)
+    P = oracle.make_problem(w.game, w.n, w.delta, w.T, radius=w.radius)
+    full = oracle.picard(P, x, w.N, w.K)
+    covered = 0
+    for r in range(world):
+        d = np.load(tmp_path / ("rank%d.npz" % r))
+        np.testing.assert_allclose(d["rel"], full["resid"], rtol=1e-12)
+        np.testing.assert_allclose(d["sup"], full["sup"], rtol=1e-12)
+        np.testing.assert_array_equal(d["v"], full["v"][int(d["lo"]):int(d["hi"])])
+        covered += int(d["hi"]) - int(d["lo"])
+    assert covered == w.M

@@ -5,8 +5,7 @@ import numpy as np
 import pytest
 
 import hjg_inputs
-import oracle
-from helpers import assert_parity, problem_for, solver_for
+from helpers import check_trajectory, solver_for
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,20 +45,27 @@ def test_batch_matches_individual_runs():
 
 
 def test_batch_instances_against_oracle():
+    """Each instance of a mixed batch, advanced 5 sweeps by the graph launch, equals its own
+    one-sweep-at-a-time trajectory bit for bit, and that trajectory passes the oracle
+    protocol (P1 and Gamma every sweep, P2 with every failure explained)."""
     from paper_2605_18566_gb300 import Batch
+    K = 5
+    cases = [(hjg_inputs.DUBINS3, 512, 4096), (hjg_inputs.ROCKETS6, 256, 8192),
+             (hjg_inputs.ROCKETS45, 24, 4096)]
     solvers, xs = [], []
-    for w, M, N in CASES:
-        x = hjg_inputs.points(w, M=min(M, 64))
-        s = solver_for(w, N=N, K=2)
+    for w, M, N in cases:
+        x = hjg_inputs.points(w, M=M)
+        s = solver_for(w, N=N, K=K)
         s.set_points(torch.from_numpy(x).cuda())
         solvers.append(s); xs.append(x)
     b = Batch(solvers)
-    r, _ = b.run(2)
-    for (w, M, N), s, x, ri in zip(CASES, solvers, xs, r):
-        st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
-        ref = oracle.picard(problem_for(w), x.astype(np.float64), N, 2)
-        assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.95, what="batch %s" % w.game)
-        np.testing.assert_allclose(ri, ref["resid"], rtol=1e-2)
+    r, _ = b.run(K)
+    batch_states = [{k: t.cpu().numpy() for k, t in s.get_state().items()} for s in solvers]
     b.close()
     for s in solvers:
         s.close()
+    for (w, M, N), x, st, ri in zip(cases, xs, batch_states, r):
+        out = check_trajectory(w, x, N, K, min_pass=0.97 if M > 200 else 0.9)
+        for key in ("v", "p", "c"):
+            np.testing.assert_array_equal(st[key], out["states"][-1][key])
+        np.testing.assert_array_equal(ri, out["resid"])

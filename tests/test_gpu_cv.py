@@ -10,7 +10,7 @@ import pytest
 
 import hjg_inputs
 import oracle
-from helpers import assert_parity, problem_for, solver_for
+from helpers import TOL_P, TOL_V, problem_for, rel_errors, solver_for
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,16 +46,30 @@ def test_cv_one_sweep_parity(w, M, N, tilt):
     c0 = st["c"].cpu().numpy().astype(np.float64)
     theta = -w.sigma2 * c0[:, None] * p0 if tilt else None
     P = problem_for(w, tilt=tilt, cv=True)
-    v, p, ess = oracle.sweep(P, xn.astype(np.float64), c0, N, 2, theta=theta, cv_v=v0, cv_p=p0)
-    # states whose incoming iterate is already non-finite stay so on both sides
-    fin = np.isfinite(v0) & np.all(np.isfinite(p0), axis=1)
-    out_fin = np.isfinite(out["v"]) & np.all(np.isfinite(out["p"]), axis=1)
-    ref_fin = np.isfinite(v) & np.all(np.isfinite(p), axis=1)
-    np.testing.assert_array_equal(out_fin, ref_fin)
-    assert fin.mean() > 0.9 and np.all(out_fin[fin])
-    assert_parity(out["v"][fin], out["p"][fin], v[fin], p[fin], frac=0.99,
-                  what="CV P1 %s tilt=%s" % (w.game, tilt))
-    np.testing.assert_allclose(out["ess"][fin], ess[fin], rtol=1e-3)
+    xd = xn.astype(np.float64)
+    v, p, ess = oracle.sweep(P, xd, c0, N, 2, theta=theta, cv_v=v0, cv_p=p0)
+    # two plain sweeps leave every state finite, and so does the CV sweep on both sides
+    assert np.all(np.isfinite(v0)) and np.all(np.isfinite(p0))
+    assert np.all(np.isfinite(out["v"])) and np.all(np.isfinite(out["p"]))
+    assert np.all(np.isfinite(v)) and np.all(np.isfinite(p))
+    dv, dp = rel_errors(out["v"], out["p"], v, p)
+    fail = (dv > TOL_V) | (dp > TOL_P)
+    if fail.any():
+        # The corrected sums are used only where mu = exp(-c v_guess) lies within a factor
+        # 4 of the sample mean weight, i.e. |c (v_plain - v_guess)| <= ln 4 with v_plain the
+        # uncorrected estimate of the same samples: a decision taken in FP32 sums on the GPU
+        # and in FP64 in the oracle.  A state may differ only where that decision sits at the
+        # threshold (FP32 rounding of the sums can flip it) and the GPU then agrees with the
+        # oracle's other branch, the uncorrected sweep.
+        vp, pp, _ = oracle.sweep(problem_for(w, tilt=tilt), xd, c0, N, 2, theta=theta)
+        margin = np.abs(np.abs(c0 * (vp - v0)) - np.log(4.0))
+        at_edge = margin <= 1e-4 * (1.0 + np.abs(c0 * vp))
+        dv2, dp2 = rel_errors(out["v"], out["p"], vp, pp)
+        other = (dv2 <= TOL_V) & (dp2 <= TOL_P)
+        bad = fail & ~(at_edge & other)
+        assert not bad.any(), "CV P1 %s tilt=%s: states %s outside tolerance (max dv %.3e, dp %.3e)" % (
+            w.game, tilt, np.nonzero(bad)[0][:10], dv.max(), dp.max())
+    np.testing.assert_allclose(out["ess"], ess, rtol=1e-3)
 
 
 @pytest.mark.parametrize("tilt", [False, True])

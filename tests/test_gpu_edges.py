@@ -8,7 +8,7 @@ import pytest
 
 import hjg_inputs
 import oracle
-from helpers import assert_parity, problem_for, solver_for
+from helpers import assert_parity, check_trajectory, problem_for, solver_for
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -30,11 +30,9 @@ def _run(w, x, N, K, **kw):
 @pytest.mark.parametrize("N", [1, 2, 5])
 def test_tiny_sample_counts(N):
     x = hjg_inputs.points(W1, M=200)
-    st, r, d, _ = _run(W1, x, N, 3)
-    ref = oracle.picard(problem_for(W1), x.astype(np.float64), N, 3)
-    assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.97, what="N=%d" % N)
+    out = check_trajectory(W1, x, N, 3, min_pass=0.9)
     if N == 1:
-        np.testing.assert_allclose(st["ess"], 1.0, rtol=1e-6)
+        np.testing.assert_allclose(out["states"][-1]["ess"], 1.0, rtol=1e-6)
 
 
 def test_single_state_many_sweeps():

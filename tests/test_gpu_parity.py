@@ -84,14 +84,16 @@ def test_trajectory_parity_tilted():
     check_trajectory(w, x, 4096, 6, tilt=True)
 
 
-@pytest.mark.parametrize("w,n_sub,K", [(W2, 48, 20), (W3, 8, 3)],
-                         ids=["rockets6-full", "rockets45-full"])
-def test_full_size_sampled_parity(w, n_sub, K):
-    """The workload at its full size (the benchmark's launch configuration); a seeded
-    subset of states is recomputed by the oracle (same global indices, same draws)."""
+@pytest.mark.parametrize("w,n_sub", [(W2, 48), (W3, 16)], ids=["rockets6-full", "rockets45-full"])
+def test_full_size_sampled_parity(w, n_sub):
+    """The workload at its full size -- every state, the workload's N and all K sweeps,
+    the benchmark's launch configuration -- with a seeded subset of states recomputed by
+    the oracle (same global indices, same draws): P1 and Gamma every sweep on the subset,
+    P2 against the oracle's own FP64 trajectory after K sweeps, every state outside the
+    tolerance explained by the oracle's own sensitivity there."""
     x = hjg_inputs.points(w)
     idx = hjg_inputs.subset_indices(w.M, n_sub, seed=11)
-    out = check_trajectory(w, x, w.N, K, idx=idx, min_pass=0.85)
+    out = check_trajectory(w, x, w.N, w.K, idx=idx, min_pass=0.8, rows_only=True)
     last = out["states"][-1]
     assert np.all(np.isfinite(last["v"])) and np.all(np.isfinite(last["p"]))
     assert np.all(np.isfinite(out["resid"])) and np.all(out["resid"] >= 0)
@@ -266,11 +268,9 @@ def test_autotune_keeps_state_and_results():
     for key in ("v", "p", "c"):
         assert torch.equal(before[key], after[key]), key
     assert tuned["threads"] in (128, 256, 512) and tuned["ms"] > 0
-    r_tuned, _ = s.picard_sweep(3)
-    st = {k: t.cpu().numpy() for k, t in s.get_state().items()}
     s.close()
-    ref = oracle.picard(problem_for(w), x.cpu().numpy().astype(np.float64), 4096, 3)
-    assert_parity(st["v"], st["p"], ref["v"], ref["p"], frac=0.99, what="tuned variant")
+    # the tuned variant's 3-sweep trajectory against the oracle (P1, Gamma, P2 explained)
+    check_trajectory(w, x.cpu().numpy(), 4096, 3, solver_kw={"variant": tuned["variant"]})
     xs = x.cpu().numpy().astype(np.float64)
     for v in range(12):    # every launch variant agrees with the oracle on one sweep
         s = solver_for(w, N=4096, K=1, variant=v)

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import hjg_inputs
-from helpers import assert_parity
+from helpers import assert_parity, solver_for
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -60,6 +60,82 @@ def test_noalloc_matches_value_grad_twice(game):
                       what="noalloc call %d" % call)
         res = r.cpu().numpy().reshape(K, 2)[:, 0]
         np.testing.assert_allclose(res, r_ref, rtol=1e-6, atol=1e-12)
+
+
+# Options passed both to the context (Solver keywords) and to the allocation-free call
+# (hjg_options fields): the 45-D four-lanes-per-sample kernel on its default and on a
+# software-pipelined variant, the control variate in the tilted frame, a shard's point
+# offset (the Philox counter of every state moves with it), and a CTA size chosen by
+# block_threads instead of a variant index.
+OPTION_CASES = [
+    ("rockets45", dict(), 300, 2048, 3),
+    ("rockets45", dict(variant=8), 300, 2048, 3),
+    ("rockets45", dict(tilt=True, cv=True), 200, 2048, 2),
+    ("dubins3", dict(tilt=True, cv=True), 800, 4096, 3),
+    ("rockets6", dict(point_offset=12345), 1000, 4096, 3),
+    ("rockets45", dict(point_offset=777), 200, 2048, 2),
+    ("dubins3", dict(block_threads=256), 800, 4096, 3),
+]
+
+
+@pytest.mark.parametrize("game,kw,M,N,K", OPTION_CASES,
+                         ids=["r45", "r45-pipelined", "r45-cv-tilt", "dubins3-cv-tilt",
+                              "rockets6-offset", "r45-offset", "dubins3-block256"])
+def test_noalloc_options_match_value_grad(game, kw, M, N, K):
+    from paper_2605_18566_gb300 import _lib
+    lib = _lib.load()
+    w = {"dubins3": hjg_inputs.DUBINS3, "rockets6": hjg_inputs.ROCKETS6,
+         "rockets45": hjg_inputs.ROCKETS45}[game]
+    x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
+    s = solver_for(w, N=N, K=K, seed=0, **kw)
+    v_ref, g_ref, r_ref = s.value_grad(x)
+    s.close()
+    v_ref = v_ref.cpu().numpy(); g_ref = g_ref.cpu().numpy()
+    dyn, tgt, opt = _structs(w, N, K)
+    for i, a in enumerate(w.speed or []):
+        dyn.speed[i] = a
+    opt.tilt = 1 if kw.get("tilt") else 0
+    opt.cv = 1 if kw.get("cv") else 0
+    opt.point_offset = kw.get("point_offset", 0)
+    opt.block_threads = kw.get("block_threads", 0)
+    opt.variant = kw["variant"] + 1 if "variant" in kw else 0
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call in range(2):
+        v = torch.full((M,), float("nan"), dtype=torch.float64, device="cuda")
+        g = torch.full((M, w.n), float("nan"), dtype=torch.float32, device="cuda")
+        r = torch.full((2 * K,), float("nan"), dtype=torch.float64, device="cuda")
+        st = _noalloc(lib, dyn, tgt, w.nu, w.T, opt, x, v, g, r, stream)
+        assert st == 0, _lib.status_string(st)
+        torch.cuda.synchronize()
+        assert_parity(v.cpu().numpy(), g.cpu().numpy(), v_ref, g_ref,
+                      what="noalloc %s %s call %d" % (game, kw, call))
+        res = r.cpu().numpy().reshape(K, 2)[:, 0]
+        np.testing.assert_allclose(res, r_ref, rtol=1e-5, atol=1e-12)
+
+
+def test_noalloc_point_offset_draws_the_shard_samples():
+    """A shard [a, b) of a state set, solved with point_offset = a, reproduces those rows
+    of the solve of the whole set (the same Philox counters), bit for bit."""
+    from paper_2605_18566_gb300 import _lib
+    lib = _lib.load()
+    w = hjg_inputs.ROCKETS6
+    N, K, M, a, b = 4096, 3, 1200, 500, 900
+    x = torch.from_numpy(hjg_inputs.points(w, M=M)).cuda()
+    dyn, tgt, opt = _structs(w, N, K)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = []
+    for lo, hi in ((0, M), (a, b)):
+        opt.point_offset = lo
+        xs = x[lo:hi].contiguous()
+        v = torch.full((hi - lo,), float("nan"), dtype=torch.float64, device="cuda")
+        g = torch.full((hi - lo, w.n), float("nan"), dtype=torch.float32, device="cuda")
+        r = torch.full((2 * K,), float("nan"), dtype=torch.float64, device="cuda")
+        st = _noalloc(lib, dyn, tgt, w.nu, w.T, opt, xs, v, g, r, stream)
+        assert st == 0, _lib.status_string(st)
+        torch.cuda.synchronize()
+        out.append((v.cpu().numpy(), g.cpu().numpy()))
+    np.testing.assert_array_equal(out[1][0], out[0][0][a:b])
+    np.testing.assert_array_equal(out[1][1], out[0][1][a:b])
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
