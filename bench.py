@@ -55,13 +55,13 @@ PAPER_CONTEXT = {"value": 2.0e7, "unit": UNIT,
 # for each workload's game; the block index sits in the Philox counter words the first
 # round does not multiply, so 4 of the 20 multiplies of a block depend only on the state
 # and sweep and are not per-sample work):
-#   Philox blocks per sample (six normals per block): n / 6 for n <= 8 (packed slots),
-#   ceil(n/6) above
+#   Philox blocks per sample (eight normals per block): n / 8 for n <= 8 (packed slots),
+#   ceil(n/8) above
 #   high halves of the 32x32 products (mul.hi.u32, 32 per SM and clock): 16 per block
 #   (the low halves issue at twice that rate and are not the binding part)
 #   MUFU (XU pipe): log2, sqrt, sin, cos per Box-Muller pair, one sqrt for the target
 #   distance, one exp2 weight (exp2 issues at twice the rate of the others on GB300)
-BLOCKS_PER_SAMPLE = {"dubins3": 0.5, "rockets6": 1.0, "rockets45": 8.0}
+BLOCKS_PER_SAMPLE = {"dubins3": 3 / 8, "rockets6": 6 / 8, "rockets45": 6.0}
 MUFU_PER_SAMPLE = {"dubins3": 2 * 3 + 2, "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
 IMUL_PER_BLOCK = 16
 # GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations
@@ -75,7 +75,7 @@ IMUL_PER_SM_CLK = 32
 # workload at its full M and K, from one-pass ncu captures of the sweep kernel.  The
 # traffic does not depend on N (samples never touch memory; each state's rows are read and
 # written once per launch).  A workload without a capture of the current kernel has none.
-DRAM_BYTES_LAUNCH = {"rockets6": 5168896.0 + 0.0}
+DRAM_BYTES_LAUNCH = {}
 
 
 def roofline(game, samples, kernel_s, full_size=False):
@@ -545,14 +545,17 @@ def run_mixed(args):
 
 
 def surrogate_study(points_fn, label):
-    """One study of the learned part on the 45-D game: tuples (x, v, Dv) from the plain
-    sweeps of 262,144 states drawn by points_fn (sweeps 23-30 of 30 at N = 131,072:
-    2,097,152 tuples), GPU training of the 45 -> 256^3 -> 46 BF16 network on them, and, on
-    1,024 held-out states, the value error against a tilted N = 2^20 reference for the plain
-    form, the tilted form without the network, and the surrogate-assisted form (warm start +
-    tilt, with and without the control variate) over N = 4,096 ... 262,144, 12 sweeps each.  `four_x` compares each plain run
-    with the assisted run at a quarter of its point-samples: success when the assisted run
-    reaches the plain run's residual at no larger value error."""
+    """One study of the learned part on the 45-D game: tuples (x, v - l(x), Dv - Dl(x)) from
+    the plain sweeps of 262,144 states drawn by points_fn (sweeps 23-30 of 30 at N = 131,072:
+    2,097,152 tuples), GPU training of the 45 -> 256^3 -> 46 BF16 network on them (it learns
+    the correction the Picard iteration makes to its initial iterate l, Dl), and, on 1,024
+    held-out states, the value error against a tilted N = 2^20 reference for the plain form,
+    the tilted form without the network, and the surrogate-assisted form (warm start
+    l + correction, then tilt, with and without the control variate) over N = 4,096 ...
+    262,144, 12 sweeps each.  `four_x` compares each plain run with the assisted run at a
+    quarter of its point-samples (success: the assisted run reaches the plain run's residual
+    at no larger value error), and `vs_tilt` each assisted run with the tilted run without
+    the network at the same N."""
     import torch
     from paper_2605_18566_gb300 import Solver, Surrogate
     w = hjg_inputs.ROCKETS45
@@ -568,9 +571,8 @@ def surrogate_study(points_fn, label):
     for _ in range(8):
         r, _ = s.picard_sweep(1)
         resid.append(float(r[0]))
-        st = s.get_state()
         X.append(x)
-        Y.append(torch.cat([st["v"][:, None].float(), st["p"]], 1))
+        Y.append(s.state_delta())
     s.close()
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
@@ -583,45 +585,49 @@ def surrogate_study(points_fn, label):
     hist = sur.fit(X, Y, epochs=epochs, batch=batch, lr=2e-3, lr_final=1e-4)
     torch.cuda.synchronize(); t_train = time.perf_counter() - t1
     xte = torch.from_numpy(points_fn(1024, 1)).cuda()
+    pred = sur.forward(xte)
 
-    def solve(N, K, tilt=False, warm=None, seed=11, cv=False):
-        so = Solver(w.game, w.nu, w.T, N, K, radius=w.radius, tilt=tilt, seed=seed, cv=cv)
+    def solve(N, K, tilt=False, warm=False, seed=11, cv=False):
+        so = Solver(w.game, w.nu, w.T, N, max(K, 1), radius=w.radius, tilt=tilt, seed=seed, cv=cv)
         so.set_points(xte)
-        if warm is not None:
-            so.warm_start(warm[1], warm[0])
-        r, _ = so.picard_sweep(K)
+        if warm:
+            so.warm_start_delta(pred)
+        r = so.picard_sweep(K)[0] if K > 0 else [float("nan")]
         st = so.get_state()
         so.close()
         return st["v"].cpu().numpy(), float(r[-1])
 
     vref, rref = solve(1 << 20, 12, tilt=True, seed=7)
-    pred = sur.forward(xte)
-    vs, ps = pred[:, 0].double().contiguous(), pred[:, 1:].contiguous()
+    rms = lambda v: float(np.sqrt(np.mean((v - vref) ** 2)))
     rows = []
     K = 12
     for N in (4096, 16384, 65536, 262144):
         for mode in ("plain", "tilt", "surrogate+tilt", "surrogate+tilt+cv"):
-            v, r = solve(N, K, tilt=mode != "plain", warm=(vs, ps) if mode.startswith("surrogate") else None,
-                         cv=mode.endswith("+cv"))
+            v, r = solve(N, K, tilt=mode != "plain", warm=mode.startswith("surrogate"), cv=mode.endswith("+cv"))
             rows.append({"mode": mode, "N": N, "K": K, "point_samples_per_state": N * K,
-                         "rms_value_error": float(np.sqrt(np.mean((v - vref) ** 2))),
-                         "final_residual": r})
+                         "rms_value_error": rms(v), "final_residual": r})
     sur.close()
-    four_x = []
+    four_x, vs_tilt = [], []
     for p in rows:
-        if p["mode"] != "plain":
-            continue
-        for a in rows:
-            if a["mode"].startswith("surrogate") and a["N"] * 4 == p["N"]:
-                four_x.append({"plain_N": p["N"], "assisted": a["mode"], "assisted_N": a["N"],
-                               "met": bool(a["final_residual"] <= p["final_residual"]
-                                           and a["rms_value_error"] <= p["rms_value_error"])})
+        if p["mode"] == "plain":
+            for a in rows:
+                if a["mode"].startswith("surrogate") and a["N"] * 4 == p["N"]:
+                    four_x.append({"plain_N": p["N"], "assisted": a["mode"], "assisted_N": a["N"],
+                                   "met": bool(a["final_residual"] <= p["final_residual"]
+                                               and a["rms_value_error"] <= p["rms_value_error"])})
+        if p["mode"] == "tilt":
+            for a in rows:
+                if a["mode"].startswith("surrogate") and a["N"] == p["N"]:
+                    vs_tilt.append({"N": p["N"], "assisted": a["mode"], "tilt_error": p["rms_value_error"],
+                                    "assisted_error": a["rms_value_error"],
+                                    "better": bool(a["rms_value_error"] <= p["rms_value_error"])})
     return {"label": label, "tuple_generation_s": t_data, "train_s": t_train,
             "tuples": int(X.shape[0]), "epochs": epochs, "batch": batch,
             "loss": [hist[0], hist[-1]], "data_residuals": resid,
             "reference": {"N": 1 << 20, "K": 12, "tilt": True, "final_residual": rref},
-            "surrogate_alone_rms_value_error": float(np.sqrt(np.mean((vs.cpu().numpy() - vref) ** 2))),
-            "study": rows, "four_x": four_x}
+            "initial_iterate_rms_value_error": rms(solve(4096, 0)[0]),
+            "surrogate_alone_rms_value_error": rms(solve(4096, 0, warm=True)[0]),
+            "study": rows, "four_x": four_x, "vs_tilt": vs_tilt}
 
 
 def run_surrogate(args):

@@ -18,13 +18,11 @@
  * are y = x + sqrt(2 nu t) z.
  *
  * Samples are never stored.  The normals of state m in sweep k form one stream: slot q
- * is lane q % 6 of Philox4x32-10 block b = q / 6, counter (m, b_lo, k, b_hi), key
- * (seed_lo, seed_hi ^ instance).  A block's words (X, Y, Z, W) give three Box-Muller
- * pairs, every bit used once: radius uniforms u = ((r & (2^23-1)) + 0.5) 2^-23 from the
- * low 23 bits of X, Y, Z; angle uniforms (k + 0.5) 2^-bits from the high 23 bits of W,
- * from the high 9 bits of X then Y, and from the high 9 bits of Z then the low 9 of W.
- * Sample i, dim d is slot i S + d, S = n for n <= 8 and n rounded up to a multiple of
- * 6 above.
+ * is lane q % 8 of Philox4x32-10 block b = q / 8, counter (m, b_lo, k, b_hi), key
+ * (seed_lo, seed_hi ^ instance).  Each word w of a block (X, Y, Z, W) gives one Box-Muller
+ * pair, every bit used once: radius uniform ((w & (2^20-1)) + 0.5) 2^-20 from its low 20
+ * bits, angle uniform ((w >> 20) + 0.5) 2^-12 from its high 12 bits.  Sample i, dim d is
+ * slot i S + d, S = n for n <= 8 and n rounded up to a multiple of 8 above.
  *
  * Conventions for every entry point:
  *   - Return an hjg_status; no call aborts or exits.  hjg_last_error() gives a message.
@@ -110,8 +108,8 @@ typedef struct {
 
 typedef struct {
     int64_t N;           /* samples per state and sweep (1 .. 2^32 - 1, and at most
-                            6 * 2^32 / S, S = n for n <= 8 and n rounded up to a multiple of
-                            6 above, so that one state's stream needs at most 2^32 Philox
+                            8 * 2^32 / S, S = n for n <= 8 and n rounded up to a multiple of
+                            8 above, so that one state's stream needs at most 2^32 Philox
                             blocks; HJG_EINVAL otherwise) */
     int32_t K;           /* sweeps run by hjg_value_grad */
     int32_t tilt;        /* 1: tilted proposal theta = -delta t c Dv (Eq. tilt_shift) */
@@ -211,6 +209,20 @@ hjg_status hjg_set_horizons(hjg_ctx *ctx, const double *t, int n_horizons);
  * the device.  With opt.tilt the first sweep is then drawn from the tilted proposal around
  * theta = -delta t c^(0) p0 (Eq. tilt_shift).  Synchronises the context's stream. */
 hjg_status hjg_warm_start(hjg_ctx *ctx, const double *v0, const float *p0, int64_t ldp, int on_device);
+
+/* Warm start from a learned correction to Algorithm 1's initial iterate ("Fix" step:
+ * v^(0) = l, p^(0) = Dl): v = l(x_m) + d[m][0], Dv_j = D_j l(x_m) + d[m][1 + j], then
+ * c = Gamma(Dv) (Eq. coeff_frozen, Lemma 2.7, Remark 2.8), l and Dl evaluated in FP64 per
+ * state.  d is a DEVICE array [M][ldd] FP32 (ldd >= n + 1; the layout of a surrogate's
+ * output rows (v, Dv) trained on hjg_get_state_delta targets).  Synchronises the context's
+ * stream.  EINVAL for ldd < n + 1 or a NULL d. */
+hjg_status hjg_warm_start_delta(hjg_ctx *ctx, const float *d, int64_t ldd);
+
+/* The current iterate minus the initial one, per loaded state: out[m][0] = v - l(x_m),
+ * out[m][1 + j] = Dv_j - D_j l(x_m) (FP64 difference rounded to FP32), out a DEVICE array
+ * [M][ldo], ldo >= n + 1: the targets of a surrogate that learns the correction the Picard
+ * iteration makes to its initial iterate.  Synchronises the context's stream. */
+hjg_status hjg_get_state_delta(hjg_ctx *ctx, float *out, int64_t ldo);
 
 /* Per-sweep parts of the residual of the last hjg_picard_sweep call over the loaded
  * states: out [n_sweeps][3] = (sum (v^(k+1)-v^(k))^2, sum (v^(k))^2, max |v^(k+1)-v^(k)|),

@@ -185,9 +185,9 @@ def normals(n, seed, instance, sample, point, sweep):
 
 
 def block_words_normals(words):
-    """The six normals of one Philox output block (four uint32 words)."""
+    """The eight normals of one Philox output block (four uint32 words)."""
     w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(4))
-    z = np.zeros(6, dtype=np.float64)
+    z = np.zeros(8, dtype=np.float64)
     lib().orc_block_words_normals(w.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(z))
     return z
 

@@ -29,8 +29,9 @@
  *     function o enters the datum as max{l, o} and bounds the value from below after every
  *     sweep (see obstacle_fn).
  *   - Counter-based sampler: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11); each
- *     128-bit block gives three Box-Muller pairs (23-bit radius uniforms u = ((x & (2^23-1))
- *     +0.5) 2^-23, angle uniforms of 23, 18, 18 bits); packed per-sample slots.
+ *     32-bit word of a block gives one Box-Muller pair (radius uniform ((x & (2^20-1)) + 0.5)
+ *     2^-20 from its low 20 bits, angle uniform ((x >> 20) + 0.5) 2^-12 from its high 12),
+ *     eight normals per block; packed per-sample slots.
  *
  * Everything is double precision except the Philox integer stream itself.
  * Pinned by tests/test_oracle_*.py (closed forms, quadrature, brute force, an
@@ -120,53 +121,50 @@ void orc_philox_batch(int64_t count, const uint32_t *ctr, const uint32_t *key, u
         orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
 }
 
-/* 23-bit uniform strictly inside (0,1) from the low 23 bits of a Philox word:
- * u = ((x & (2^23-1)) + 0.5) 2^-23; every value is exact in FP32 and FP64. */
+/* Radius uniform of one Philox word, strictly inside (0,1): the low 20 bits k give
+ * u = (k + 0.5) 2^-20; every value is exact in FP32 and FP64. */
 double orc_u01(uint32_t x)
 {
-    return ((double)(x & 0x7FFFFFu) + 0.5) * (1.0 / 8388608.0);
+    return ((double)(x & 0xFFFFFu) + 0.5) * (1.0 / 1048576.0);
 }
 
-/* Angle uniform from a b-bit field k: (k + 0.5) 2^-b, also exact in both precisions. */
-static double angle_u(uint32_t k, int bits)
+/* Angle uniform of one Philox word: the high 12 bits k give (k + 0.5) 2^-12, also exact in
+ * both precisions. */
+static double angle_u(uint32_t x)
 {
-    return ((double)k + 0.5) / (double)(1u << bits);
+    return ((double)(x >> 20) + 0.5) / 4096.0;
 }
+
+/* Normals per Philox block: one Box-Muller pair per 32-bit word. */
+#define ORC_NPB 8
 
 /* Slots per sample in the normal stream of one (state, sweep): n for n <= 8 (the normals
- * of consecutive samples are packed back to back), n rounded up to a multiple of 6 above
+ * of consecutive samples are packed back to back), n rounded up to a multiple of 8 above
  * (each sample starts on a fresh Philox block). */
 int orc_slot_stride(int n)
 {
-    return n <= 8 ? n : (n + 5) / 6 * 6;
+    return n <= 8 ? n : (n + 7) / 8 * 8;
 }
 
-/* The six normals of one Philox output block (X, Y, Z, W); block b of the stream of
+/* The eight normals of one Philox output block (X, Y, Z, W); block b of the stream of
  * (point, sweep) has counter (point, b_lo, sweep, b_hi) and key (seed_lo, seed_hi ^
- * instance).  Every one of the 128 bits feeds exactly one uniform:
- *   pair j = 0, 1, 2 (slots 6b+2j, 6b+2j+1) takes its radius uniform from the low 23 bits
- *   of X, Y, Z respectively, and its angle uniform from
- *     j = 0: the high 23 bits of W,
- *     j = 1: the high 9 bits of X followed by the high 9 bits of Y (18 bits),
- *     j = 2: the high 9 bits of Z followed by the low 9 bits of W (18 bits);
+ * instance).  Word j = 0..3 makes pair j (slots 8b+2j, 8b+2j+1) and every one of its 32
+ * bits feeds exactly one uniform: the radius uniform u_r from its low 20 bits, the angle
+ * uniform u_a from its high 12 bits;
  *   (z_2j, z_2j+1) = sqrt(-2 ln u_r) (cos 2 pi u_a, sin 2 pi u_a)  (Box-Muller). */
-void orc_block_words_normals(const uint32_t r[4], double zz[6])
+void orc_block_words_normals(const uint32_t r[4], double zz[ORC_NPB])
 {
     const double two_pi = 6.283185307179586476925286766559;
-    const uint32_t X = r[0], Y = r[1], Z = r[2], W = r[3];
-    double ur[3] = {orc_u01(X), orc_u01(Y), orc_u01(Z)};
-    double ua[3] = {angle_u(W >> 9, 23),
-                    angle_u(((X >> 23) << 9) | (Y >> 23), 18),
-                    angle_u(((Z >> 23) << 9) | (W & 0x1FFu), 18)};
-    for (int j = 0; j < 3; ++j) {
-        double rad = sqrt(-2.0 * log(ur[j]));
-        zz[2 * j] = rad * cos(two_pi * ua[j]);
-        zz[2 * j + 1] = rad * sin(two_pi * ua[j]);
+    for (int j = 0; j < 4; ++j) {
+        double rad = sqrt(-2.0 * log(orc_u01(r[j])));
+        double ua = angle_u(r[j]);
+        zz[2 * j] = rad * cos(two_pi * ua);
+        zz[2 * j + 1] = rad * sin(two_pi * ua);
     }
 }
 
 static void block_normals(uint64_t seed, uint32_t instance, uint64_t b, uint32_t point,
-                          uint32_t sweep, double zz[6])
+                          uint32_t sweep, double zz[ORC_NPB])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance};
     uint32_t ctr[4] = {point, (uint32_t)b, sweep, (uint32_t)(b >> 32)};
@@ -176,20 +174,20 @@ static void block_normals(uint64_t seed, uint32_t instance, uint64_t b, uint32_t
 }
 
 /* Standard normals z[0..n) of sample `sample` of state `point` in sweep `sweep`: slot
- * q = sample * orc_slot_stride(n) + d of the stream, i.e. lane q % 6 of block q / 6. */
+ * q = sample * orc_slot_stride(n) + d of the stream, i.e. lane q % 8 of block q / 8. */
 void orc_normals(int n, uint64_t seed, uint32_t instance, uint32_t sample,
                  uint32_t point, uint32_t sweep, double *z)
 {
     uint64_t q0 = (uint64_t)sample * (uint64_t)orc_slot_stride(n);
     uint64_t cached = UINT64_MAX;
-    double zz[6] = {0, 0, 0, 0, 0, 0};
+    double zz[ORC_NPB] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int d = 0; d < n; ++d) {
         uint64_t q = q0 + (uint64_t)d;
-        if (q / 6 != cached) {
-            cached = q / 6;
+        if (q / ORC_NPB != cached) {
+            cached = q / ORC_NPB;
             block_normals(seed, instance, cached, point, sweep, zz);
         }
-        z[d] = zz[q % 6];
+        z[d] = zz[q % ORC_NPB];
     }
 }
 

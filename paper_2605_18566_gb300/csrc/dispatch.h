@@ -28,6 +28,10 @@ struct GameKernels {
     cudaError_t (*coef)(const float* x, int64_t ldx, int64_t M, const float* p, int64_t ldp,
                         const GameParams& g, double delta, double eta, double c_min, double c_max, float* c,
                         const float* aux, int64_t ldaux, cudaStream_t st);
+    // The iterate relative to the initial one (delta_kernel): read it out, or warm start.
+    cudaError_t (*delta)(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta, double eta,
+                         double c_min, double c_max, double* v, float* p, int64_t ldp, float* c, float* d,
+                         int64_t ldd, bool warm, const float* aux, int64_t ldaux, cudaStream_t st);
 };
 
 GameKernels kernels_dubins3();
@@ -83,6 +87,7 @@ cudaError_t flock_neighbours(const float* x, int64_t ldx, int64_t M, int32_t* id
         k.occupancy = occ;                                                                 \
         k.init = launch_init<GAME>;                                                        \
         k.coef = launch_coef<GAME>;                                                        \
+        k.delta = launch_delta<GAME>;                                                      \
         return k;                                                                          \
     }                                                                                      \
     }

@@ -146,7 +146,7 @@ __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, const uin
 }
 
 // The normals the sweep draws for samples 0..ns-1 of (point, sweep): sample i, dim d is
-// slot i * slot_stride(n) + d of the stream, i.e. lane (slot % 6) of block slot / 6.
+// slot i * slot_stride(n) + d of the stream, i.e. lane (slot % 8) of block slot / 8.
 __global__ void normals_kernel(int n, uint32_t k0, uint32_t k1, uint32_t point, uint32_t sweep,
                                int64_t ns, float* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -618,6 +618,33 @@ hjg_status hjg_warm_start(hjg_ctx* ctx, const double* v0, const float* p0, int64
                                     ctx->n * sizeof(float), (size_t)M, kind, st));
     HJG_CUDA(ctx, ctx->kern.coef(ctx->d_x, ctx->ldx, M, ctx->d_p, ctx->ldx, ctx->gp, ctx->delta, ctx->eta,
                                  ctx->c_min, ctx->c_max, ctx->d_c, ctx->d_aux, kFlockAux, st));
+    HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
+hjg_status hjg_warm_start_delta(hjg_ctx* ctx, const float* d, int64_t ldd) {
+    if (!ctx || !d) return HJG_EINVAL;
+    if (ldd < ctx->n + 1) return fail(ctx, HJG_EINVAL, "ldd < n + 1");
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    cudaStream_t st = ctx->stream;
+    ctx->se_valid = false;
+    HJG_CUDA(ctx, ctx->kern.delta(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min, ctx->c_max,
+                                  ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, const_cast<float*>(d), ldd, true,
+                                  ctx->d_aux, kFlockAux, st));
+    HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
+hjg_status hjg_get_state_delta(hjg_ctx* ctx, float* out, int64_t ldo) {
+    if (!ctx || !out) return HJG_EINVAL;
+    if (ldo < ctx->n + 1) return fail(ctx, HJG_EINVAL, "ldo < n + 1");
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    cudaStream_t st = ctx->stream;
+    HJG_CUDA(ctx, ctx->kern.delta(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min, ctx->c_max,
+                                  ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, out, ldo, false, ctx->d_aux, kFlockAux,
+                                  st));
     HJG_CUDA(ctx, cudaStreamSynchronize(st));
     return HJG_OK;
 }

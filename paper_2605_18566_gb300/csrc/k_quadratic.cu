@@ -37,6 +37,7 @@ GameKernels make() {
     k.occupancy = occ<G>;
     k.init = launch_init<G>;
     k.coef = launch_coef<G>;
+    k.delta = launch_delta<G>;
     return k;
 }
 }  // namespace

@@ -54,6 +54,7 @@ GameKernels kernels_rockets45() {
     k.occupancy = occ;
     k.init = launch_init<Rockets45>;
     k.coef = launch_coef<Rockets45>;
+    k.delta = launch_delta<Rockets45>;
     return k;
 }
 }  // namespace hjg

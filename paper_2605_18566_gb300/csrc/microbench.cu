@@ -144,14 +144,15 @@ __global__ void __launch_bounds__(kThreads) philox_pipe(int64_t iters, float* si
     if (acc == 0x9E3779B9u) sink[threadIdx.x] = (float)acc;
 }
 
-// Full Box-Muller normals from Philox blocks, as the sweep draws them (6 per block).
+// Full Box-Muller normals from Philox blocks, as the sweep draws them (8 per block).
 __global__ void __launch_bounds__(kThreads) normals_pipe(int64_t iters, float* sink) {
     float acc = 0.0f;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = 0; i < iters; ++i) {
-        float z[6];
-        hjg::block_normals<6>((uint32_t)i * 65536u + t, blockIdx.x, 3u, 0x1234u, 0x5678u, z);
-        acc += z[0] + z[1] + z[2] + z[3] + z[4] + z[5];
+        float z[hjg::kNormalsPerBlock];
+        hjg::block_normals<hjg::kNormalsPerBlock>((uint32_t)i * 65536u + t, blockIdx.x, 3u, 0x1234u, 0x5678u, z);
+#pragma unroll
+        for (int q = 0; q < hjg::kNormalsPerBlock; ++q) acc += z[q];
     }
     if (acc == 1234.5f) sink[threadIdx.x] = acc;
 }
@@ -187,7 +188,7 @@ extern "C" hjg_status hjg_microbench(int op, int64_t iters, double* ops_per_s, d
     };
     if (op == HJG_MB_PHILOX || op == HJG_MB_PHILOX_SPLIT || op == HJG_MB_PHILOX_MIXED)
         per_thread_iter = 1.0;   // Philox blocks
-    if (op == HJG_MB_NORMALS) per_thread_iter = 6.0;  // normals
+    if (op == HJG_MB_NORMALS) per_thread_iter = hjg::kNormalsPerBlock;  // normals
     if (op < HJG_MB_FFMA || op > HJG_MB_PHILOX_MIXED) { cudaFree(sink); return HJG_EINVAL; }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -763,6 +763,17 @@ struct hjg_mlp {
     __nv_bfloat16* packB = nullptr;       //   (dZ^T, H^T, W^T) for the backward GEMMs
     double* lpart = nullptr;              // loss partial sums
     int64_t lpart_cap = 0;
+    // fused training step (width 256, in_pad and out_pad <= 64): canonical copies of the BF16
+    // weights, W_l and W_l^T in the tensor cores' K-major core-matrix layout, one contiguous
+    // block per layer (offsets wp_off, n_w weights in all), and its work buffers
+    int64_t wp_off[kLayers] = {}, n_w = 0;
+    __nv_bfloat16* wc = nullptr;          // W_l [rows][cols] as B operands (N = rows, K = cols)
+    __nv_bfloat16* wct = nullptr;         // W_l^T [cols][rows] as B operands (N = cols, K = rows)
+    int64_t fcap = 0;                     // batch capacity of the fused buffers
+    __nv_bfloat16* Xt = nullptr;          // X^T [in_pad][pad8(B)]
+    __nv_bfloat16* dZt4[kLayers] = {};    // dZ_l^T [rows_l][pad8(B)] (layer 4: dO^T)
+    float* fpart = nullptr;               // split-K weight-gradient partials [splits][n_w]
+    double* flpart = nullptr;             // loss partial sums, one per batch tile
     int64_t step = 0;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -935,6 +946,616 @@ hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const flo
     return HJG_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Fused training step of the width-256 network (in_pad, out_pad <= 64), three launches:
+//   A  one CTA per 128 batch rows runs the whole forward pass, the loss and the backward
+//      data-gradient pass through all four layers on the tensor cores: each layer's input
+//      sits in shared memory in the canonical K-major layout, the layer's weights arrive
+//      by one bulk copy (issued while the previous layer's epilogue runs), the 128 x 256
+//      FP32 accumulator lives in TMEM, and the epilogue writes the next layer's input back
+//      to shared memory, so activations never leave the SM between layers; it also writes
+//      what the weight gradients need (H_l^T, dZ_l^T, X^T) and the pre-activations Z_l;
+//   B  the weight gradients dW_l = dZ_l^T H_{l-1} as 128 x N tiles (N = the layer's input
+//      width, up to 256) over a split of the batch (split-K), TMA-fed four-stage pipeline;
+//   C  the fixed-order sum of the splits, the bias gradients (column sums of dZ_l), Adam and
+//      the BF16 weight copies (row-major, transposed, canonical) for the next step.
+constexpr int kFW = 256;                         // width of the fused network
+constexpr int kFRows = 128;                      // batch rows per phase-A CTA (one M = 128 tile)
+constexpr int kFThreads = 256;                   // 8 warps: TMEM lane quarter w % 4, column half w / 4
+constexpr int kFBufA = kFRows * kFW * 2;         // 64 KB: a layer input, canonical K-major
+constexpr int kFBufB = kFW * kFW * 2;            // 128 KB: a layer's weights, canonical K-major
+constexpr int kFSmemA = kFBufA + kFBufB;
+constexpr int kWgSplits = 16;                    // phase B split of the batch
+constexpr int kWgStages = 4;
+constexpr int kWgStage = (kTcM + kFW) * kTcK * 2;   // A 128 rows + B up to 256 rows, one 64-wide K chunk
+constexpr int kWgSmem = kWgStages * kWgStage;
+
+// Offset (elements) of element (r, k) of an [R][K] operand in the canonical K-major
+// no-swizzle layout: core matrices of 8 rows x 8 K values (16 bytes a row), ordered
+// [K / 8][R][8] -- core matrices 128 B apart along the rows and R x 16 B apart along K.
+__host__ __device__ inline int64_t canon_idx(int64_t r, int64_t k, int64_t R) {
+    return ((k >> 3) * R + r) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    mbar_expect_tx(bar, bytes);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// D (TMEM) = A (128 x K, canonical at a) * B^T (rowsB x K, canonical at b), K a multiple of 16.
+__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, int rowsB, int K, uint32_t idesc) {
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t da = umma_desc(a + (uint32_t)(ks * kFRows * 32), kFRows * 16, 128);
+        const uint64_t db = umma_desc(b + (uint32_t)(ks * rowsB * 32), (uint32_t)rowsB * 16, 128);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+            :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float* x) {
+    uint32_t v[32];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
+              "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+            : "r"(addr + (uint32_t)(8 * q)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
+}
+
+// Eight BF16 values of one row into the canonical layout of a 128-row operand (k0 % 8 == 0).
+__device__ __forceinline__ void st_canon8(__nv_bfloat16* buf, int row, int k0, const float* v) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(v[j]);
+    *reinterpret_cast<uint4*>(buf + canon_idx(row, k0, kFRows)) = *reinterpret_cast<const uint4*>(h);
+}
+
+struct FusedArgs {
+    const float* x; int64_t ldx; const float* y; int64_t ldy; int64_t B; int64_t ldT;
+    int n_in, n_out, in_pad, out_pad;
+    const float* iscal; const float* oscal;          // [shift | mul] of inputs and targets
+    const float* p;                                  // FP32 parameters (biases read from here)
+    int64_t b_off[kLayers], wp_off[kLayers];
+    const __nv_bfloat16* wc; const __nv_bfloat16* wct;
+    float* Z[kLayers - 1];                           // hidden pre-activations [B][256]
+    __nv_bfloat16* Xt; __nv_bfloat16* Ht[kLayers - 1]; __nv_bfloat16* dZt[kLayers];
+    double* lpart;                                   // loss / B per CTA
+    int* err;
+};
+
+__global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const FusedArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar_w, bar_m;
+    __shared__ uint32_t tmem_base;
+    __shared__ float s_loss[kFThreads / 32];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = 32 * quarter + lane;                       // this thread's TMEM lane = tile row
+    const int64_t rg = (int64_t)blockIdx.x * kFRows + row;     // batch row
+    const bool valid = rg < a.B;
+    const bool in_t = rg < a.ldT;                              // a column of the transposed outputs
+    const uint32_t sA = smem_u32(smem), sB = sA + kFBufA;
+    __nv_bfloat16* bufA = reinterpret_cast<__nv_bfloat16*>(smem);
+    const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_m);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(kFW));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bw));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bm));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_ok = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's TMEM lanes
+    uint32_t ph_w = 0, ph_m = 0;
+    bool w_pending = false;   // thread 0: a weight copy in flight that no wait has consumed
+    const int ip = a.in_pad, op = a.out_pad;
+    // weight copies in the order the seven products use them
+    const __nv_bfloat16* wsrc[7] = {a.wc + a.wp_off[0], a.wc + a.wp_off[1], a.wc + a.wp_off[2], a.wc + a.wp_off[3],
+                                    a.wct + a.wp_off[3], a.wct + a.wp_off[2], a.wct + a.wp_off[1]};
+    const uint32_t wbytes[7] = {(uint32_t)(kFW * ip * 2), (uint32_t)(kFW * kFW * 2), (uint32_t)(kFW * kFW * 2),
+                                (uint32_t)(op * kFW * 2), (uint32_t)(kFW * op * 2), (uint32_t)(kFW * kFW * 2),
+                                (uint32_t)(kFW * kFW * 2)};
+    const int wrows[7] = {kFW, kFW, kFW, op, kFW, kFW, kFW};         // N of each product
+    const int kdim[7] = {ip, kFW, kFW, kFW, op, kFW, kFW};           // K of each product
+    if (tid == 0) { bulk_g2s(sB, wsrc[0], wbytes[0], bw); w_pending = true; }
+
+    // input tile: standardised features in BF16 (zero beyond n_in and beyond the batch)
+    for (int e = tid; e < kFRows * ip; e += kFThreads) {
+        const int r = e / ip, j = e % ip;
+        const int64_t b = (int64_t)blockIdx.x * kFRows + r;
+        float xv = 0.0f;
+        if (b < a.B && j < a.n_in) xv = (a.x[b * a.ldx + j] - a.iscal[j]) * a.iscal[ip + j];
+        bufA[canon_idx(r, j, kFRows)] = __float2bfloat16(xv);
+    }
+    __syncthreads();
+    for (int e = tid; e < kFRows * ip; e += kFThreads) {   // X^T, the K-major operand of dW_1
+        const int j = e / kFRows, r = e % kFRows;
+        const int64_t b = (int64_t)blockIdx.x * kFRows + r;
+        if (b < a.ldT) a.Xt[(int64_t)j * a.ldT + b] = bufA[canon_idx(r, j, kFRows)];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+
+    float loss = 0.0f;
+    for (int t = 0; t < 7; ++t) {
+        // thread 0: the product of step t once its weights have landed
+        if (tid == 0 && s_ok) {
+            if (!mbar_wait(bw, ph_w, a.err)) {
+                s_ok = 0;
+            } else {
+                w_pending = false;
+                ph_w ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                mma_layer(tmem, sA, sB, wrows[t], kdim[t], umma_idesc_bf16(kFRows, wrows[t]));
+                mma_commit(bm);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        if (!mbar_wait(bm, ph_m, a.err)) s_ok = 0;
+        ph_m ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();   // every thread past the wait: operands free, accumulator complete
+        if (!s_ok) break;
+        if (tid == 0 && t + 1 < 7) { bulk_g2s(sB, wsrc[t + 1], wbytes[t + 1], bw); w_pending = true; }
+        if (t < 3) {
+            // hidden layer t: z = acc + b, Z_t, h = silu(z) -> next input, H_t^T
+#pragma unroll 1
+            for (int pass = 0; pass < 4; ++pass) {
+                const int c0 = half * 128 + 32 * pass;
+                float v[32];
+                tmem_ld32(tl + (uint32_t)c0, v);
+                const float* bias = a.p + a.b_off[t] + c0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] += bias[j];
+                if (valid) {
+                    float4* zr = reinterpret_cast<float4*>(a.Z[t] + rg * kFW + c0);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) zr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = valid ? silu(v[j]) : 0.0f;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
+                if (in_t) {
+                    __nv_bfloat16* ht = a.Ht[t] + (int64_t)c0 * a.ldT + rg;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) ht[(int64_t)j * a.ldT] = __float2bfloat16(v[j]);
+                }
+            }
+        } else if (t == 3) {
+            // output layer: o = acc + b, loss against the standardised targets, dO -> next input, dO^T
+            const int c0 = half * 32;
+            if (c0 < op) {
+                float v[32];
+                tmem_ld32(tl + (uint32_t)c0, v);
+                const float winv = a.n_out > 1 ? 1.0f / (float)(a.n_out - 1) : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c0 + j;
+                    float g = 0.0f;
+                    if (valid && col < a.n_out) {
+                        const float o = v[j] + a.p[a.b_off[3] + col];
+                        const float d = o - (a.y[rg * a.ldy + col] - a.oscal[col]) / a.oscal[op + col];
+                        const float w = col == 0 ? 1.0f : winv;
+                        loss += w * d * d;
+                        g = 2.0f * w * d / (float)a.B;
+                    }
+                    v[j] = g;
+                }
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    if (c0 + 8 * g < op) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
+                if (in_t) {
+                    __nv_bfloat16* dt = a.dZt[3] + (int64_t)c0 * a.ldT + rg;
+                    for (int j = 0; j < 32 && c0 + j < op; ++j) dt[(int64_t)j * a.ldT] = __float2bfloat16(v[j]);
+                }
+            }
+        } else {
+            // backward: dZ_l = (dZ_{l+1} W_{l+1}) silu'(Z_l), l = 5 - t -> next input (l > 0), dZ_l^T
+            const int l = 5 - t;
+#pragma unroll 1
+            for (int pass = 0; pass < 4; ++pass) {
+                const int c0 = half * 128 + 32 * pass;
+                float v[32];
+                tmem_ld32(tl + (uint32_t)c0, v);
+                if (valid) {
+                    const float4* zr = reinterpret_cast<const float4*>(a.Z[l] + rg * kFW + c0);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float4 zz = zr[g];
+                        const float z4[4] = {zz.x, zz.y, zz.z, zz.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float z = z4[i];
+                            const float sg = 1.0f / (1.0f + __expf(-z));
+                            v[4 * g + i] *= sg * (1.0f + z * (1.0f - sg));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+                }
+                if (l > 0) {
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
+                }
+                if (in_t) {
+                    __nv_bfloat16* dt = a.dZt[l] + (int64_t)c0 * a.ldT + rg;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) dt[(int64_t)j * a.ldT] = __float2bfloat16(v[j]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    // the loss of this tile (FP32 per thread, then the warps in a fixed order)
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, off);
+    if (lane == 0) s_loss[warp] = loss;
+    if (tid == 0 && w_pending) mbar_wait(bw, ph_w, a.err);   // no copy may land after the exit
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < kFThreads / 32; ++w) t += s_loss[w];
+        a.lpart[blockIdx.x] = (double)t / (double)a.B;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFW));
+}
+
+// Phase B: split-K weight gradients.  Item i = (layer, 128-row tile of dW_l), split s of the
+// batch: part[s][wp_off[l] + r cols_l + c] = sum over its batch rows of dZ_l^T[r][b] X_l^T[c][b]
+// (X_l = the layer's input: X, H_1, H_2, H_3).  Both operands are K-major in global memory
+// (K = the batch) and arrive by TMA, 8-element K slices of 128 (A) and cols_l (B) rows.
+struct WgradArgs {
+    CUtensorMap ta[kLayers], tb[kLayers];
+    int rows[kLayers], cols[kLayers];
+    int64_t wp_off[kLayers], n_w, K;
+    int item_l[8], item_m[8];
+    int splits, kper;
+    float* part;
+    int* err;
+};
+
+__global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant__ WgradArgs g) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[kWgStages], empty[kWgStages];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int item = blockIdx.x / g.splits, split = blockIdx.x % g.splits;
+    const int l = g.item_l[item], m0 = g.item_m[item] * kTcM;
+    const int N = g.cols[l];
+    const int64_t kbeg = (int64_t)split * g.kper, kend = min(g.K, kbeg + g.kper);
+    const int nch = kend > kbeg ? (int)((kend - kbeg + kTcK - 1) / kTcK) : 0;
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t stage_bytes = (uint32_t)((kTcM + N) * kTcK * 2);
+    const CUtensorMap* tmA = &g.ta[l];
+    const CUtensorMap* tmB = &g.tb[l];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(kFW));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < kWgStages; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = umma_idesc_bf16(kTcM, N);
+    auto chunk = [&](uint32_t st, int64_t k0, uint32_t bar) {
+        mbar_expect_tx(bar, stage_bytes);
+#pragma unroll
+        for (int o = 0; o < kTcK / 8; ++o) {
+            tma_load_2d(st + (uint32_t)(o * kTcM * 16), tmA, (int)(k0 + 8 * o), m0, bar);
+            tma_load_2d(st + (uint32_t)(kTcM * kTcK * 2 + o * N * 16), tmB, (int)(k0 + 8 * o), 0, bar);
+        }
+    };
+    bool ok = true;
+    if (tid == 0 && nch > 0) {
+        uint32_t ph_full[kWgStages] = {}, ph_empty[kWgStages] = {};
+        int issued = 0, landed = 0;
+        for (; issued < nch && issued < kWgStages; ++issued)
+            chunk(s0 + (uint32_t)(issued * kWgStage), kbeg + (int64_t)issued * kTcK, smem_u32(&full[issued]));
+        for (int c = 0; c < nch; ++c) {
+            const int s = c % kWgStages;
+            if (!mbar_wait(smem_u32(&full[s]), ph_full[s], g.err)) { ok = false; break; }
+            ph_full[s] ^= 1u;
+            landed = c + 1;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = s0 + (uint32_t)(s * kWgStage), sb = sa + kTcM * kTcK * 2;
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 16; ++ks) {
+                const uint64_t da = umma_desc(sa + ks * (kTcM * 32), kTcM * 16, 128);
+                const uint64_t db = umma_desc(sb + (uint32_t)(ks * N * 32), (uint32_t)N * 16, 128);
+                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                    :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            mma_commit(smem_u32(&empty[s]));
+            if (issued < nch) {
+                if (!mbar_wait(smem_u32(&empty[s]), ph_empty[s], g.err)) { ok = false; break; }
+                ph_empty[s] ^= 1u;
+                chunk(sa, kbeg + (int64_t)issued * kTcK, smem_u32(&full[s]));
+                ++issued;
+            }
+        }
+        if (ok) {
+            const int s = (nch - 1) % kWgStages;
+            ok = mbar_wait(smem_u32(&empty[s]), ph_empty[s], g.err);
+        } else {
+            for (int c = landed; c < issued; ++c) {
+                const int s = c % kWgStages;
+                mbar_wait(smem_u32(&full[s]), ph_full[s], g.err);
+                ph_full[s] ^= 1u;
+            }
+        }
+    }
+    ok = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int rr = m0 + warp * 32 + lane;
+    const bool have = ok && nch > 0;   // uniform over the CTA: the TMEM loads are warp-collective
+    float* dst = g.part + (int64_t)split * g.n_w + g.wp_off[l] + (int64_t)rr * N;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+        if (have) {
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+        }
+        if (rr < g.rows[l]) {
+            const int nv = min(32, N - c0);   // N is a multiple of 16
+            for (int q = 0; q < nv / 4; ++q)
+                reinterpret_cast<float4*>(dst + c0)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFW));
+}
+
+// Phase C: gradients and (with lr > 0) the Adam step and the BF16 weight copies.  Blocks
+// [0, nwb): one thread per weight, the splits added in order; blocks [nwb, ...): one warp per
+// bias, the column sum of dZ_l over the batch (lanes over the rows, then a fixed butterfly).
+struct ApplyArgs {
+    int64_t w_off[kLayers], b_off[kLayers], wp_off[kLayers], n_w;
+    int rows[kLayers], cols[kLayers];
+    const float* part; int splits;
+    const __nv_bfloat16* dZt[kLayers]; int64_t ldT, B;
+    float* p; float* g; float* m1; float* m2;
+    __nv_bfloat16* pb; __nv_bfloat16* pbT; __nv_bfloat16* wc; __nv_bfloat16* wct;
+    float lr, b1, b2, eps, c1, c2;
+    int nwb, n_bias;
+};
+
+__device__ __forceinline__ float adam_update(const ApplyArgs& a, int64_t pi, float gg) {
+    const float m = a.b1 * a.m1[pi] + (1.0f - a.b1) * gg;
+    const float v = a.b2 * a.m2[pi] + (1.0f - a.b2) * gg * gg;
+    a.m1[pi] = m;
+    a.m2[pi] = v;
+    const float nw = a.p[pi] - a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+    a.p[pi] = nw;
+    a.pb[pi] = __float2bfloat16(nw);
+    return nw;
+}
+
+__global__ void __launch_bounds__(256) mlp_apply_kernel(const ApplyArgs a) {
+    if ((int)blockIdx.x < a.nwb) {
+        const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+        if (e >= a.n_w) return;
+        int l = 0;
+        while (l + 1 < kLayers && e >= a.wp_off[l + 1]) ++l;
+        const int64_t k = e - a.wp_off[l];
+        const int R = a.rows[l], Cc = a.cols[l];
+        const int r = (int)(k / Cc), c = (int)(k % Cc);
+        float s = 0.0f;
+        for (int t = 0; t < a.splits; ++t) s += a.part[(int64_t)t * a.n_w + e];
+        const int64_t pi = a.w_off[l] + k;
+        a.g[pi] = s;
+        if (a.lr > 0.0f) {
+            const __nv_bfloat16 hb = __float2bfloat16(adam_update(a, pi, s));
+            a.pbT[a.w_off[l] + (int64_t)c * R + r] = hb;
+            a.wc[a.wp_off[l] + canon_idx(r, c, R)] = hb;
+            a.wct[a.wp_off[l] + canon_idx(c, r, Cc)] = hb;
+        }
+        return;
+    }
+    const int gw = ((int)blockIdx.x - a.nwb) * 8 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (gw >= a.n_bias) return;
+    int l = 0, i = gw;
+    while (l + 1 < kLayers && i >= a.rows[l]) { i -= a.rows[l]; ++l; }
+    const __nv_bfloat16* row = a.dZt[l] + (int64_t)i * a.ldT;
+    float s = 0.0f;
+    for (int64_t b = lane; b < a.B; b += 32) s += __bfloat162float(row[b]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        const int64_t pi = a.b_off[l] + i;
+        a.g[pi] = s;
+        if (a.lr > 0.0f) adam_update(a, pi, s);
+    }
+}
+
+// Canonical BF16 copies of the weights from the FP32 parameters (creation, set_params).
+__global__ void canon_weights_kernel(const float* __restrict__ p, ApplyArgs a) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.n_w) return;
+    int l = 0;
+    while (l + 1 < kLayers && e >= a.wp_off[l + 1]) ++l;
+    const int64_t k = e - a.wp_off[l];
+    const int R = a.rows[l], Cc = a.cols[l];
+    const int r = (int)(k / Cc), c = (int)(k % Cc);
+    const __nv_bfloat16 hb = __float2bfloat16(p[a.w_off[l] + k]);
+    a.wc[a.wp_off[l] + canon_idx(r, c, R)] = hb;
+    a.wct[a.wp_off[l] + canon_idx(c, r, Cc)] = hb;
+}
+
+bool fused_ok(const hjg_mlp* m) {
+    return m->width == kFW && m->in_pad <= 64 && m->out_pad <= 64 && m->wc && m->wct;
+}
+
+ApplyArgs apply_args(const hjg_mlp* m) {
+    ApplyArgs a;
+    memset(&a, 0, sizeof a);
+    for (int l = 0; l < kLayers; ++l) {
+        a.w_off[l] = m->w_off[l]; a.b_off[l] = m->b_off[l]; a.wp_off[l] = m->wp_off[l];
+        a.rows[l] = m->rows[l]; a.cols[l] = m->cols[l];
+        a.dZt[l] = m->dZt4[l];
+    }
+    a.n_w = m->n_w;
+    a.part = m->fpart; a.splits = kWgSplits;
+    a.p = m->p; a.g = m->g; a.m1 = m->m1; a.m2 = m->m2;
+    a.pb = m->pb; a.pbT = m->pbT; a.wc = m->wc; a.wct = m->wct;
+    a.nwb = (int)((m->n_w + 255) / 256);
+    int nb = 0;
+    for (int l = 0; l < kLayers; ++l) nb += m->rows[l];
+    a.n_bias = nb;
+    return a;
+}
+
+cudaError_t refresh_canon(hjg_mlp* m, cudaStream_t st) {
+    if (!m->wc) return cudaSuccess;
+    const ApplyArgs a = apply_args(m);
+    canon_weights_kernel<<<nblk(m->n_w), 256, 0, st>>>(m->p, a);
+    return cudaGetLastError();
+}
+
+hjg_status fused_ensure(hjg_mlp* m, int64_t B) {
+    if (B <= m->fcap) return HJG_OK;
+    auto fre = [](void* p) { if (p) cudaFree(p); };
+    fre(m->Xt); fre(m->fpart); fre(m->flpart);
+    m->Xt = nullptr; m->fpart = nullptr; m->flpart = nullptr;
+    for (int l = 0; l < kLayers; ++l) { fre(m->dZt4[l]); m->dZt4[l] = nullptr; }
+    m->fcap = 0;
+    const int64_t ldT = pad8(B);
+    bool ok = cudaMalloc(&m->Xt, (size_t)m->in_pad * ldT * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&m->fpart, (size_t)kWgSplits * m->n_w * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->flpart, (size_t)((B + kFRows - 1) / kFRows) * sizeof(double)) == cudaSuccess;
+    for (int l = 0; l < kLayers && ok; ++l)
+        ok = cudaMalloc(&m->dZt4[l], (size_t)m->rows[l] * ldT * sizeof(__nv_bfloat16)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        m->err = "fused training buffers: out of memory";
+        return HJG_ENOMEM;
+    }
+    m->fcap = B;
+    return HJG_OK;
+}
+
+// One fused training step (lr > 0: gradients and Adam) or the gradients alone (lr = 0).
+hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t B,
+                          float lr, double* loss_out) {
+    hjg_status s = mlp_ensure(m, B);
+    if (s || (s = fused_ensure(m, B))) return s;
+    if (!g_tc_err) {
+        if (cudaMalloc(&g_tc_err, sizeof(int)) != cudaSuccess || cudaMemset(g_tc_err, 0, sizeof(int)) != cudaSuccess)
+            return HJG_ENOMEM;
+    }
+    cudaStream_t st = m->stream;
+    const int64_t ldT = pad8(B);
+    static bool attrA = false, attrB = false;
+    if (!attrA) {
+        if (cudaFuncSetAttribute(mlp_fused_fwdbwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemA) !=
+            cudaSuccess)
+            return HJG_ECUDA;
+        attrA = true;
+    }
+    if (!attrB) {
+        if (cudaFuncSetAttribute(mlp_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) !=
+            cudaSuccess)
+            return HJG_ECUDA;
+        attrB = true;
+    }
+    FusedArgs fa;
+    memset(&fa, 0, sizeof fa);
+    fa.x = x; fa.ldx = ldx; fa.y = y; fa.ldy = ldy; fa.B = B; fa.ldT = ldT;
+    fa.n_in = m->n_in; fa.n_out = m->n_out; fa.in_pad = m->in_pad; fa.out_pad = m->out_pad;
+    fa.iscal = m->iscal; fa.oscal = m->oscal; fa.p = m->p;
+    for (int l = 0; l < kLayers; ++l) { fa.b_off[l] = m->b_off[l]; fa.wp_off[l] = m->wp_off[l]; fa.dZt[l] = m->dZt4[l]; }
+    fa.wc = m->wc; fa.wct = m->wct;
+    for (int l = 0; l + 1 < kLayers; ++l) { fa.Z[l] = m->Z[l]; fa.Ht[l] = m->Ht[l]; }
+    fa.Xt = m->Xt; fa.lpart = m->flpart; fa.err = g_tc_err;
+    const int ntile = (int)((B + kFRows - 1) / kFRows);
+    mlp_fused_fwdbwd_kernel<<<ntile, kFThreads, kFSmemA, st>>>(fa);
+    if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+
+    WgradArgs wa;
+    memset(&wa, 0, sizeof wa);
+    int items = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        wa.rows[l] = m->rows[l]; wa.cols[l] = m->cols[l]; wa.wp_off[l] = m->wp_off[l];
+        const __nv_bfloat16* opB = l == 0 ? m->Xt : m->Ht[l - 1];
+        if (!operand_map(&wa.ta[l], m->dZt4[l], m->rows[l], B, ldT, kTcM) ||
+            !operand_map(&wa.tb[l], opB, m->cols[l], B, ldT, m->cols[l]))
+            return HJG_ECUDA;
+        for (int t = 0; t < (m->rows[l] + kTcM - 1) / kTcM; ++t) { wa.item_l[items] = l; wa.item_m[items] = t; ++items; }
+    }
+    wa.n_w = m->n_w; wa.K = B; wa.splits = kWgSplits;
+    wa.kper = (int)(((B + kWgSplits - 1) / kWgSplits + kTcK - 1) / kTcK * kTcK);
+    wa.part = m->fpart; wa.err = g_tc_err;
+    mlp_wgrad_kernel<<<items * kWgSplits, 128, kWgSmem, st>>>(wa);
+    if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+
+    ApplyArgs aa = apply_args(m);
+    aa.ldT = ldT; aa.B = B;
+    aa.lr = lr;
+    if (lr > 0.0f) {
+        m->step += 1;
+        aa.b1 = 0.9f; aa.b2 = 0.999f; aa.eps = 1e-8f;
+        aa.c1 = 1.0f - powf(aa.b1, (float)m->step);
+        aa.c2 = 1.0f - powf(aa.b2, (float)m->step);
+    }
+    mlp_apply_kernel<<<aa.nwb + (aa.n_bias + 7) / 8, 256, 0, st>>>(aa);
+    if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+    if (loss_out) {
+        std::vector<double> part((size_t)ntile);
+        if (cudaMemcpyAsync(part.data(), m->flpart, ntile * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return HJG_ECUDA;
+        double l = 0.0;
+        for (double v : part) l += v;
+        *loss_out = l;
+    }
+    return HJG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -956,6 +1577,9 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
         m->b_off[l] = off; off += outs[l];
     }
     m->n_params = off;
+    int64_t woff = 0;
+    for (int l = 0; l < kLayers; ++l) { m->wp_off[l] = woff; woff += (int64_t)m->rows[l] * m->cols[l]; }
+    m->n_w = woff;
     const size_t nb = (size_t)off * sizeof(float);
     int64_t wpart = 0;
     for (int l = 0; l < kLayers; ++l) wpart = std::max<int64_t>(wpart, (int64_t)m->rows[l] * m->cols[l]);
@@ -968,6 +1592,12 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
         cudaMalloc(&m->iscal, 2 * (size_t)m->in_pad * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&m->oscal, 2 * (size_t)m->out_pad * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&m->wpart, (size_t)wpart * sizeof(float)) != cudaSuccess) {
+        hjg_mlp_destroy(m);
+        return HJG_ENOMEM;
+    }
+    if (width == kFW && m->in_pad <= 64 && m->out_pad <= 64 &&
+        (cudaMalloc(&m->wc, (size_t)m->n_w * sizeof(__nv_bfloat16)) != cudaSuccess ||
+         cudaMalloc(&m->wct, (size_t)m->n_w * sizeof(__nv_bfloat16)) != cudaSuccess)) {
         hjg_mlp_destroy(m);
         return HJG_ENOMEM;
     }
@@ -991,7 +1621,8 @@ hjg_status hjg_mlp_create(int n_in, int n_out, int width, uint64_t seed, hjg_mlp
         cudaMemcpy(m->iscal, si.data(), si.size() * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(m->oscal, so.data(), so.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
-    if (refresh_wt(m, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    if (refresh_wt(m, nullptr) != cudaSuccess || refresh_canon(m, nullptr) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
         hjg_mlp_destroy(m);
         return HJG_ECUDA;
     }
@@ -1005,7 +1636,8 @@ void hjg_mlp_destroy(hjg_mlp* m) {
     fre(m->p); fre(m->g); fre(m->m1); fre(m->m2); fre(m->pb); fre(m->pbT); fre(m->iscal); fre(m->oscal);
     fre(m->wpart); fre(m->packA);
     fre(m->packB); fre(m->X); fre(m->dZ); fre(m->dZ2); fre(m->dZt); fre(m->dH); fre(m->lpart);
-    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); fre(m->Ht[l]); }
+    for (int l = 0; l < kLayers; ++l) { fre(m->Z[l]); fre(m->H[l]); fre(m->Ht[l]); fre(m->dZt4[l]); }
+    fre(m->wc); fre(m->wct); fre(m->Xt); fre(m->fpart); fre(m->flpart);
     delete m;
 }
 
@@ -1033,7 +1665,7 @@ hjg_status hjg_mlp_set_params(hjg_mlp* m, const float* in, int on_device) {
         return HJG_ECUDA;
     to_bf16_kernel<<<nblk(m->n_params), 256, 0, m->stream>>>(m->p, m->pb, m->n_params);
     if (cudaGetLastError() != cudaSuccess || refresh_wt(m, m->stream) != cudaSuccess ||
-        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        refresh_canon(m, m->stream) != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess)
         return HJG_ECUDA;
     m->step = 0;
     cudaMemsetAsync(m->m1, 0, m->n_params * sizeof(float), m->stream);
@@ -1057,7 +1689,8 @@ hjg_status hjg_mlp_forward(hjg_mlp* m, const float* x, int64_t ldx, int64_t B, f
 hjg_status hjg_mlp_gradients(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
                              int64_t B, double* loss_out, float* grad_out) {
     if (!m || B < 1 || !x || !y || ldx < m->n_in || ldy < m->n_out) return HJG_EINVAL;
-    hjg_status s = mlp_loss_and_grads(m, x, ldx, y, ldy, B, loss_out);
+    hjg_status s = fused_ok(m) ? mlp_fused_step(m, x, ldx, y, ldy, B, 0.0f, loss_out)
+                               : mlp_loss_and_grads(m, x, ldx, y, ldy, B, loss_out);
     if (s) return s;
     if (grad_out &&
         (cudaMemcpyAsync(grad_out, m->g, m->n_params * sizeof(float), cudaMemcpyDeviceToHost, m->stream) !=
@@ -1190,6 +1823,7 @@ hjg_status hjg_selftest_bounded_wait(int arrive, int64_t limit, void* stream) {
 hjg_status hjg_mlp_train_step(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy,
                               int64_t B, float lr, double* loss_out) {
     if (!m || B < 1 || !x || !y || ldx < m->n_in || ldy < m->n_out || !(lr > 0)) return HJG_EINVAL;
+    if (fused_ok(m)) return mlp_fused_step(m, x, ldx, y, ldy, B, lr, loss_out);
     hjg_status s = mlp_loss_and_grads(m, x, ldx, y, ldy, B, loss_out);
     if (s) return s;
     m->step += 1;

@@ -1,19 +1,19 @@
 // sampler.cuh -- in-register counter-based Gaussian sampler for the Picard sweep.
 //
 // For each (state m, sweep k) the sampler defines one stream of standard normals: slot q
-// is lane q % 6 of Philox4x32-10 block b = q / 6, drawn with counter (m, b_lo, k, b_hi)
+// is lane q % 8 of Philox4x32-10 block b = q / 8, drawn with counter (m, b_lo, k, b_hi)
 // and key (seed_lo, seed_hi ^ instance) (Philox: Salmon et al., SC'11).  The block index
 // sits in the words the first round does not multiply, so the products of the first
 // rounds that depend only on (m, k) are the same for every sample of a state and sweep.
-// Each block (words X, Y, Z, W) gives three Box-Muller pairs and every one of its 128 bits
-// feeds exactly one uniform: pair j (slots 6b+2j, 6b+2j+1) takes its radius from the low
-// 23 bits of X, Y, Z (u = ((r & (2^23-1)) + 0.5) 2^-23) and its angle from the high 23 bits
-// of W (j = 0), the high 9 bits of X then of Y (j = 1, 18 bits), the high 9 bits of Z then
-// the low 9 of W (j = 2, 18 bits), with u = (k + 0.5) 2^-bits.  Sample i of a game with n
-// state dimensions reads slots i*S .. i*S + n - 1, S = n for n <= 8 (consecutive samples
-// packed back to back, so every Philox output is used) and S = n rounded up to a multiple
-// of 6 above.  Nothing is written to memory: the heat-kernel expectation of Prop. 2.1 /
-// Cor. B.4 consumes each draw where it is made.
+// Each 32-bit word of a block (X, Y, Z, W) gives one Box-Muller pair, so a block gives
+// eight normals and every one of its 128 bits feeds exactly one uniform: word j makes the
+// pair in slots 8b+2j, 8b+2j+1 with its radius uniform from the low 20 bits,
+// u = ((w & (2^20-1)) + 0.5) 2^-20, and its angle uniform from the high 12 bits,
+// u = ((w >> 20) + 0.5) 2^-12.  Sample i of a game with n state dimensions reads slots
+// i*S .. i*S + n - 1, S = n for n <= 8 (consecutive samples packed back to back, so every
+// Philox output is used) and S = n rounded up to a multiple of 8 above.  Nothing is written
+// to memory: the heat-kernel expectation of Prop. 2.1 / Cor. B.4 consumes each draw where
+// it is made.
 #pragma once
 #include <cstdint>
 
@@ -56,40 +56,28 @@ __device__ __forceinline__ float cos_approx(float x) {
     float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y;
 }
 
-// The low 23 bits of r as a float in [1, 2): 1 + (r & (2^23-1)) 2^-23 (exact): a single
-// three-input logic operation (r & 0x7FFFFF) | one, with `one` held in a register.
-__device__ __forceinline__ float mant_one_two(uint32_t r) {
+// Radius uniform of one word: u = ((w & (2^20-1)) + 0.5) 2^-20, exactly.  One three-input
+// logic operation builds f = 1 + (w & (2^20-1)) 2^-23 (the field in the low mantissa bits,
+// `one` held in a register), and one FMA gives 8 f - 8 + 2^-21 = u (exact in binary32).
+__device__ __forceinline__ float mant_low20(uint32_t w) {
     uint32_t one = 0x3F800000u, y;
-    asm("lop3.b32 %0, %1, 0x007FFFFF, %2, 0xEA;" : "=r"(y) : "r"(r), "r"(one));
+    asm("lop3.b32 %0, %1, 0x000FFFFF, %2, 0xEA;" : "=r"(y) : "r"(w), "r"(one));
     return __uint_as_float(y);
 }
-
-// u = ((r & (2^23-1)) + 0.5) 2^-23, exactly (the sum below is exact in binary32).
-__device__ __forceinline__ float u01(uint32_t r) {
-    return mant_one_two(r) + (-1.0f + 0x1.0p-24f);
+constexpr float kRadOff = -0x1.fffffep+2f;   // -8 + 2^-21
+__device__ __forceinline__ float u_radius(uint32_t w) {
+    return fmaf(mant_low20(w), 8.0f, kRadOff);
 }
 
-// Box-Muller phase phi = 2 pi u - pi in (-pi, pi) for the angle uniform u = (k + 0.5) 2^-b,
-// one FMA from the mantissa float f = 1 + k 2^-b (the b-bit field k in the top bits of the
-// mantissa): phi = 2 pi f - 3 pi + pi 2^-b.  The pair is (r cos 2 pi u, r sin 2 pi u) =
-// (-r cos phi, -r sin phi).
+// Box-Muller phase phi = 2 pi u - pi in (-pi, pi) for the angle uniform u = (k + 0.5) 2^-12
+// of the high 12 bits k of w: with f = 1 + k 2^-12 (the field placed in the top mantissa
+// bits), phi = 2 pi f - 3 pi + pi 2^-12, one FMA.  The pair is (r cos 2 pi u, r sin 2 pi u)
+// = (-r cos phi, -r sin phi).
 constexpr float kTwoPi = 6.283185307179586f;
-constexpr float kPhase23 = -9.42477798461914f;    // -3 pi + pi 2^-23 in binary32
-constexpr float kPhase18 = -9.424765586853027f;   // -3 pi + pi 2^-18 in binary32
-
-// Pair 0: the high 23 bits of W.
-__device__ __forceinline__ float bm_phase0(const uint4& r) {
-    return fmaf(mant_one_two(r.w >> 9), kTwoPi, kPhase23);
-}
-// Pair 1: k = (X >> 23) << 9 | (Y >> 23), placed in mantissa bits 22..5.
-__device__ __forceinline__ float bm_phase1(const uint4& r) {
-    const uint32_t f = ((r.x >> 9) & 0x007FC000u) | ((r.y >> 18) & 0x00003FE0u) | 0x3F800000u;
-    return fmaf(__uint_as_float(f), kTwoPi, kPhase18);
-}
-// Pair 2: k = (Z >> 23) << 9 | (W & 511), placed in mantissa bits 22..5.
-__device__ __forceinline__ float bm_phase2(const uint4& r) {
-    const uint32_t f = ((r.z >> 9) & 0x007FC000u) | ((r.w << 5) & 0x00003FE0u) | 0x3F800000u;
-    return fmaf(__uint_as_float(f), kTwoPi, kPhase18);
+constexpr float kPhase12 = -0x1.2d918p+3f;   // -3 pi + pi 2^-12 in binary32
+__device__ __forceinline__ float bm_phase(uint32_t w) {
+    const uint32_t f = ((w >> 9) & 0x007FF800u) | 0x3F800000u;
+    return fmaf(__uint_as_float(f), kTwoPi, kPhase12);
 }
 
 // Per-round Philox keys (k + r W for rounds r = 0..9), computed once on the host so that
@@ -136,28 +124,20 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 ctr, const PhiloxKeys& r
 // slope and the final gradient).
 constexpr float kBmScale = -1.1774100225154747f;
 
-// Box-Muller on the four words of one Philox block: up to six normals (constant factors
-// left out, see above).
+// Box-Muller on the four words of one Philox block: up to eight normals, pair j from word
+// j (constant factors left out, see above).
+__device__ __forceinline__ void bm_pair_raw(uint32_t w, float* z, bool both) {
+    const float ra = sqrt_approx(fabsf(lg2_approx(u_radius(w))));
+    const float ph = bm_phase(w);
+    z[0] = ra * cos_approx(ph);
+    if (both) z[1] = ra * sin_approx(ph);
+}
 template <int NUSE>
 __device__ __forceinline__ void bm_normals_raw(const uint4& r, float* z) {
-    {
-        const float ra = sqrt_approx(fabsf(lg2_approx(u01(r.x))));
-        const float ph = bm_phase0(r);
-        z[0] = ra * cos_approx(ph);
-        if (NUSE > 1) z[1] = ra * sin_approx(ph);
-    }
-    if (NUSE > 2) {
-        const float rb = sqrt_approx(fabsf(lg2_approx(u01(r.y))));
-        const float ph = bm_phase1(r);
-        z[2] = rb * cos_approx(ph);
-        if (NUSE > 3) z[3] = rb * sin_approx(ph);
-    }
-    if (NUSE > 4) {
-        const float rc = sqrt_approx(fabsf(lg2_approx(u01(r.z))));
-        const float ph = bm_phase2(r);
-        z[4] = rc * cos_approx(ph);
-        if (NUSE > 5) z[5] = rc * sin_approx(ph);
-    }
+    bm_pair_raw(r.x, z, NUSE > 1);
+    if (NUSE > 2) bm_pair_raw(r.y, z + 2, NUSE > 3);
+    if (NUSE > 4) bm_pair_raw(r.z, z + 4, NUSE > 5);
+    if (NUSE > 6) bm_pair_raw(r.w, z + 6, NUSE > 7);
 }
 
 // Philox block b of the stream of (point, sweep).
@@ -182,15 +162,15 @@ __device__ __forceinline__ void block_normals(uint32_t b, uint32_t point, uint32
 
 // Normals per Philox block, slots per sample and the sample grouping that makes a group
 // end on a block boundary.
-constexpr int kNormalsPerBlock = 6;
-__host__ __device__ constexpr int slot_stride(int n) { return n <= 8 ? n : (n + 5) / 6 * 6; }
-__host__ __device__ constexpr int gcd6(int a) {
-    return (a % 6 == 0) ? 6 : (a % 3 == 0) ? 3 : (a % 2 == 0) ? 2 : 1;
+constexpr int kNormalsPerBlock = 8;
+__host__ __device__ constexpr int slot_stride(int n) { return n <= 8 ? n : (n + 7) / 8 * 8; }
+__host__ __device__ constexpr int gcd8(int a) {
+    return (a % 8 == 0) ? 8 : (a % 4 == 0) ? 4 : (a % 2 == 0) ? 2 : 1;
 }
-__host__ __device__ constexpr int group_samples(int n) { return 6 / gcd6(slot_stride(n)); }
+__host__ __device__ constexpr int group_samples(int n) { return 8 / gcd8(slot_stride(n)); }
 
 __host__ __device__ constexpr int group_blocks(int n) {
-    return group_samples(n) * slot_stride(n) / 6;
+    return group_samples(n) * slot_stride(n) / 8;
 }
 
 // The kernels carry a stream's block index in one 32-bit counter word (the high word is

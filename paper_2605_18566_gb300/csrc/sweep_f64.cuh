@@ -11,20 +11,17 @@ namespace hjg {
 
 constexpr int kF64Threads = 128;
 
-// Six FP64 normals of one Philox block, with the uniforms of bm_normals_raw: radius
-// uniforms ((r & (2^23-1)) + 0.5) 2^-23 from X, Y, Z; angle uniforms (k + 0.5) 2^-b from the
-// high 23 bits of W, the high 9 bits of X then Y, the high 9 bits of Z then the low 9 of W.
+// Eight FP64 normals of one Philox block, with the uniforms of bm_normals_raw: word j gives
+// pair j, radius uniform ((w & (2^20-1)) + 0.5) 2^-20 and angle uniform ((w >> 20) + 0.5) 2^-12.
 __device__ __forceinline__ void bm_normals_f64(const uint4& r, double* z) {
-    const double ur[3] = {((double)(r.x & 0x7FFFFFu) + 0.5) * 0x1p-23, ((double)(r.y & 0x7FFFFFu) + 0.5) * 0x1p-23,
-                          ((double)(r.z & 0x7FFFFFu) + 0.5) * 0x1p-23};
-    const double ua[3] = {((double)(r.w >> 9) + 0.5) * 0x1p-23,
-                          ((double)(((r.x >> 23) << 9) | (r.y >> 23)) + 0.5) * 0x1p-18,
-                          ((double)(((r.z >> 23) << 9) | (r.w & 511u)) + 0.5) * 0x1p-18};
+    const uint32_t wd[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const double rad = sqrt(-2.0 * log(ur[j]));
+    for (int j = 0; j < 4; ++j) {
+        const double ur = ((double)(wd[j] & 0xFFFFFu) + 0.5) * 0x1p-20;
+        const double ua = ((double)(wd[j] >> 20) + 0.5) * 0x1p-12;
+        const double rad = sqrt(-2.0 * log(ur));
         double s, c;
-        sincospi(2.0 * ua[j], &s, &c);
+        sincospi(2.0 * ua, &s, &c);
         z[2 * j] = rad * c;
         z[2 * j + 1] = rad * s;
     }
@@ -73,17 +70,17 @@ __global__ void __launch_bounds__(kF64Threads) sweep_kernel_f64(const SweepArgs 
 #pragma unroll
             for (int j = 0; j < n; ++j) Sz[j] = 0.0;
             for (uint32_t i = (uint32_t)tid; i < N32; i += T) {
-                double z[n], zz[6];
+                double z[n], zz[kNormalsPerBlock];
                 const uint64_t q0 = (uint64_t)i * (uint64_t)S;
                 uint64_t cur = ~0ull;
 #pragma unroll
                 for (int d = 0; d < n; ++d) {
                     const uint64_t qq = q0 + (uint64_t)d;
-                    if (qq / 6 != cur) {
-                        cur = qq / 6;
+                    if (qq / kNormalsPerBlock != cur) {
+                        cur = qq / kNormalsPerBlock;
                         bm_normals_f64(stream_block((uint32_t)cur, point, sweep, A.rk), zz);
                     }
-                    z[d] = zz[qq % 6];
+                    z[d] = zz[qq % kNormalsPerBlock];
                 }
                 double y[n], dot = 0.0;
 #pragma unroll

@@ -322,30 +322,44 @@ __device__ __forceinline__ void finish_sweep(SweepShared<NPAD, W, NC>& sh, const
     __syncthreads();
 }
 
+// Last block of a group that sample t of the group reads (S slots per sample, eight
+// normals per block): the sample can be consumed as soon as that block is drawn.
+__host__ __device__ constexpr int last_block_of(int t, int S) { return (t * S + S - 1) / kNormalsPerBlock; }
+
+// Box-Muller on block b of a group and every sample that block completes (compile-time
+// selection once the loops are unrolled), so that the normals of a consumed sample need no
+// register afterwards.
+template <int GS, int S, class F>
+__device__ __forceinline__ void consume_block(int b, const uint4& r, float* z, F&& sample) {
+    bm_normals_raw<kNormalsPerBlock>(r, z + kNormalsPerBlock * b);
+#pragma unroll
+    for (int t = 0; t < GS; ++t)
+        if (last_block_of(t, S) == b) sample(z + t * S);
+}
+
 // The full groups g = start, start + STRIDE, ... < full of one (state, sweep) stream, each
-// turned into GB Philox blocks, 6 GB normals and GS samples handed to `sample`.  With PIPE
-// the Philox blocks of the next group are drawn while the current group's Box-Muller and
-// samples run (software pipelining), so that each warp's instruction stream interleaves the
-// integer multiplies of the generator with the transcendental and FP32 work of the samples;
-// the one group drawn past the end is discarded.  Both forms consume identical draws.
-template <int GS, int GB, int STRIDE, bool PIPE, bool UNR2, class F>
+// turned into GB Philox blocks, 8 GB normals and GS samples of S slots handed to `sample`
+// one by one as their blocks are drawn.  With PIPE the Philox block after the current one
+// (the next block of this group, or the first block of the thread's next group) is drawn
+// while the current block's Box-Muller and samples run (software pipelining one block
+// ahead), so that each warp's instruction stream interleaves the integer multiplies of the
+// generator with the transcendental and FP32 work of the samples; the one block drawn past
+// the end is discarded.  With UNR2 two independent groups are drawn per iteration.  All
+// forms consume identical draws.
+template <int GS, int GB, int S, int STRIDE, bool PIPE, bool UNR2, class F>
 __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32_t point, uint32_t sweep,
-                                           const PhiloxKeys& rk, F&& sample_group) {
+                                           const PhiloxKeys& rk, F&& sample) {
     if constexpr (PIPE) {
-        uint4 r[GB];
-#pragma unroll
-        for (int b = 0; b < GB; ++b) r[b] = stream_block(start * GB + b, point, sweep, rk);
+        uint4 r = stream_block(start * GB, point, sweep, rk);
         for (uint32_t grp = start; grp < full; grp += STRIDE) {
-            uint4 rn[GB];
-            const uint32_t nxt = grp + STRIDE;
-#pragma unroll
-            for (int b = 0; b < GB; ++b) rn[b] = stream_block(nxt * GB + b, point, sweep, rk);
             float z[kNormalsPerBlock * GB];
 #pragma unroll
-            for (int b = 0; b < GB; ++b) bm_normals_raw<kNormalsPerBlock>(r[b], z + kNormalsPerBlock * b);
-            sample_group(z);
-#pragma unroll
-            for (int b = 0; b < GB; ++b) r[b] = rn[b];
+            for (int b = 0; b < GB; ++b) {
+                const uint32_t nb = (b + 1 < GB) ? grp * GB + b + 1 : (grp + STRIDE) * GB;
+                const uint4 rn = stream_block(nb, point, sweep, rk);
+                consume_block<GS, S>(b, r, z, sample);
+                r = rn;
+            }
         }
     } else {
         uint32_t grp = start;
@@ -354,19 +368,17 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
                 float z[kNormalsPerBlock * GB], y[kNormalsPerBlock * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b) {
-                    block_normals_raw<kNormalsPerBlock>(grp * GB + b, point, sweep, rk, z + kNormalsPerBlock * b);
-                    block_normals_raw<kNormalsPerBlock>((grp + STRIDE) * GB + b, point, sweep, rk,
-                                                        y + kNormalsPerBlock * b);
+                    const uint4 ra = stream_block(grp * GB + b, point, sweep, rk);
+                    const uint4 rb = stream_block((grp + STRIDE) * GB + b, point, sweep, rk);
+                    consume_block<GS, S>(b, ra, z, sample);
+                    consume_block<GS, S>(b, rb, y, sample);
                 }
-                sample_group(z);
-                sample_group(y);
             }
         }
         for (; grp < full; grp += STRIDE) {
             float z[kNormalsPerBlock * GB];
 #pragma unroll
-            for (int b = 0; b < GB; ++b) block_normals_raw<kNormalsPerBlock>(grp * GB + b, point, sweep, rk, z + kNormalsPerBlock * b);
-            sample_group(z);
+            for (int b = 0; b < GB; ++b) consume_block<GS, S>(b, stream_block(grp * GB + b, point, sweep, rk), z, sample);
         }
     }
 }
@@ -434,11 +446,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                     }
                 }
             };
-            run_groups<GS, GB, THREADS, PIPE, UNR2>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
-                                              [&](const float* z) {
-#pragma unroll
-                                                  for (int t = 0; t < GS; ++t) sample(z + t * n);
-                                              });
+            run_groups<GS, GB, n, THREADS, PIPE, UNR2>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                                      sample);
             if (GS > 1 && full < groups && tid == (int)(full % THREADS)) {   // ragged last group
                 float z[kNormalsPerBlock * GB];
 #pragma unroll
@@ -590,11 +599,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 }
                 lse_accumulate<n>(a, zt, m, s, q, S);
             };
-            run_groups<GS, GB, 32, PIPE, UNR2>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
-                                         [&](const float* z) {
-#pragma unroll
-                                             for (int t = 0; t < GS; ++t) sample(z + t * n);
-                                         });
+            run_groups<GS, GB, n, 32, PIPE, UNR2>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                                 sample);
             if (GS > 1 && full < groups && lane == (int)(full % 32)) {
                 float z[kNormalsPerBlock * GB];
 #pragma unroll
@@ -620,12 +626,13 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
 }
 
 // ------------------------------------------------------------------------------------
-// 45-D multi-rocket game: four lanes per sample stream.  Lane q of a group owns dims
-// 12q..12q+11 (agents 4q..4q+3; dims 45..47 are padding), i.e. blocks 8 i + 2q + j of the
-// stream.  The evader (agent 14, dims 42..44) sits on lane 3; its position is broadcast,
-// each lane takes the minimum squared distance over its own pursuers, and two shuffles
-// finish the group minimum.  All four lanes then hold the same log-weight and accumulate
-// their own twelve S_j.
+// 45-D multi-rocket game: two lanes per sample stream.  Lane h of a pair owns dims
+// 24h..24h+23 (agents 8h..8h+7; dims 45..47 are padding), i.e. blocks 6 i + 3h + j of the
+// stream (three blocks of eight normals).  The evader (agent 14, dims 42..44) sits on lane
+// h = 1 as its local agent 6; its position goes to the other lane with two shuffles, each
+// lane takes the minimum squared distance over its own pursuers (eight on h = 0, six on
+// h = 1), and one shuffle finishes the pair's minimum.  Both lanes then hold the same
+// log-weight and accumulate their own 24 S_j.
 template <int THREADS, int MINB, bool TILT, bool CV = false, bool PIPE = false>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArgs A) {
     static_assert(!CV || TILT, "the 45-D control variate runs in the tilted frame");
@@ -633,14 +640,14 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
     constexpr int n = 45;
     constexpr int NPAD = 48;
     constexpr int W = THREADS / 32;
-    constexpr int GROUPS = THREADS / 4;
+    constexpr int GROUPS = THREADS / 2;   // samples in flight per CTA
+    constexpr int L = 24;                 // dims per lane
     __shared__ SweepShared<NPAD, W, G::kCache> sh;
     __shared__ float s_aux[1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int q4 = lane & 3;
-    const int grp = tid >> 2;
-    const int src3 = (lane & ~3) | 3;
-    const int nag = (q4 == 3) ? 2 : 4;   // pursuers owned by this lane
+    const int h = lane & 1;
+    const int grp = tid >> 1;
+    const int src_e = lane | 1;
     const uint32_t N32 = (uint32_t)A.N;
 
     for (int64_t pt = blockIdx.x; pt < A.M; pt += gridDim.x) {
@@ -652,98 +659,103 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
         for (int k = 0; k < A.K; ++k) {
             const uint32_t sweep = A.k0 + (uint32_t)k;
             const float cneg2 = sh.cneg2, cr = sh.cr, sk = sh.sig.sk;
-            float yoff[12], tq[12];
+            float yx0[8], yz0[8], tq[TILT ? L : 1];
 #pragma unroll
-            for (int j = 0; j < 12; ++j) { yoff[j] = sh.yoff[12 * q4 + j]; tq[j] = sh.tq[12 * q4 + j]; }
-            float m = -INFINITY, s = 0.0f, q = 0.0f, S[12];
+            for (int a = 0; a < 8; ++a) {
+                yx0[a] = sh.yoff[L * h + 3 * a];
+                yz0[a] = sh.yoff[L * h + 3 * a + 1];
+            }
 #pragma unroll
-            for (int j = 0; j < 12; ++j) S[j] = 0.0f;
-            float Z1[CV ? 12 : 1];   // control variate: plain sums of this lane's 12 normals
+            for (int j = 0; j < (TILT ? L : 1); ++j) tq[j] = TILT ? sh.tq[L * h + j] : 0.0f;
+            float m = -INFINITY, s = 0.0f, q = 0.0f, S[L];
 #pragma unroll
-            for (int j = 0; j < (CV ? 12 : 1); ++j) Z1[j] = 0.0f;
+            for (int j = 0; j < L; ++j) S[j] = 0.0f;
+            float Z1[CV ? L : 1];   // control variate: plain sums of this lane's 24 normals
+#pragma unroll
+            for (int j = 0; j < (CV ? L : 1); ++j) Z1[j] = 0.0f;
 
             // The shuffles below take the whole warp, so every lane runs the trip count of
-            // the warp's first group; a group whose sample index is past N draws (an unused
-            // block) and joins the shuffles but accumulates nothing.
-            // With PIPE the two Philox blocks of the next sample are drawn while the current
-            // sample's Box-Muller, distances and accumulation run (identical draws).
-            const uint32_t g_first = (uint32_t)(grp & ~7);
+            // the warp's first group; a group whose sample index is past N draws (unused
+            // blocks) and joins the shuffles but accumulates nothing.
+            // With PIPE the three Philox blocks of the next sample are drawn while the
+            // current sample's Box-Muller, distances and accumulation run (identical draws).
+            const uint32_t g_first = (uint32_t)(grp & ~15);
             const uint32_t trips = N32 > g_first ? (N32 - g_first + GROUPS - 1) / GROUPS : 0u;
             const uint32_t point = A.pt0 + (uint32_t)pt;
-            uint4 rb[2];
+            uint4 rb[3];
             if constexpr (PIPE) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j) rb[j] = stream_block(8u * (uint32_t)grp + 2u * q4 + j, point, sweep, A.rk);
+                for (int j = 0; j < 3; ++j) rb[j] = stream_block(6u * (uint32_t)grp + 3u * h + j, point, sweep, A.rk);
             }
             for (uint32_t t = 0; t < trips; ++t) {
                 const uint32_t i = (uint32_t)grp + t * (uint32_t)GROUPS;
                 const bool live = i < N32;
-                float z[12];
+                float z[L];
                 if constexpr (PIPE) {
                     const uint32_t nx = i + (uint32_t)GROUPS;
-                    uint4 rn[2];
+                    uint4 rn[3];
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) rn[j] = stream_block(8u * nx + 2u * q4 + j, point, sweep, A.rk);
+                    for (int j = 0; j < 3; ++j) rn[j] = stream_block(6u * nx + 3u * h + j, point, sweep, A.rk);
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) bm_normals_raw<6>(rb[j], z + 6 * j);
+                    for (int j = 0; j < 3; ++j) bm_normals_raw<8>(rb[j], z + 8 * j);
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) rb[j] = rn[j];
+                    for (int j = 0; j < 3; ++j) rb[j] = rn[j];
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) block_normals_raw<6>(8u * i + 2u * q4 + j, point, sweep, A.rk, z + 6 * j);
+                    for (int j = 0; j < 3; ++j) block_normals_raw<8>(6u * i + 3u * h + j, point, sweep, A.rk, z + 8 * j);
                 }
-                float yx[4], yz[4];
+                float yx[8], yz[8];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    yx[a] = fmaf(sk, z[3 * a], yoff[3 * a]);
-                    yz[a] = fmaf(sk, z[3 * a + 1], yoff[3 * a + 1]);
+                for (int a = 0; a < 8; ++a) {
+                    yx[a] = fmaf(sk, z[3 * a], yx0[a]);
+                    yz[a] = fmaf(sk, z[3 * a + 1], yz0[a]);
                 }
-                const float ex = __shfl_sync(0xffffffffu, yx[2], src3);
-                const float ez = __shfl_sync(0xffffffffu, yz[2], src3);
-                float d2 = INFINITY;
+                const float ex = __shfl_sync(0xffffffffu, yx[6], src_e);
+                const float ez = __shfl_sync(0xffffffffu, yz[6], src_e);
+                float dd[8];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < 8; ++a) {
                     const float dx = yx[a] - ex, dz = yz[a] - ez;
-                    const float dd = fmaf(dx, dx, dz * dz);
-                    d2 = (a < nag) ? fminf(d2, dd) : d2;
+                    dd[a] = fmaf(dx, dx, dz * dz);
                 }
+                float d2 = fminf(fminf(fminf(dd[0], dd[1]), fminf(dd[2], dd[3])), fminf(dd[4], dd[5]));
+                const float d67 = fminf(dd[6], dd[7]);   // pursuers 6, 7 on h = 0; evader, padding on h = 1
+                d2 = h ? d2 : fminf(d2, d67);
                 d2 = fminf(d2, __shfl_xor_sync(0xffffffffu, d2, 1));
-                d2 = fminf(d2, __shfl_xor_sync(0xffffffffu, d2, 2));
                 float a2 = fmaf(cneg2, sqrt_approx(d2), cr);
                 if (TILT) {
                     float part = 0.0f;
 #pragma unroll
-                    for (int j = 0; j < 12; ++j) part = fmaf(z[j], tq[j], part);
+                    for (int j = 0; j < L; ++j) part = fmaf(z[j], tq[j], part);
                     part += __shfl_xor_sync(0xffffffffu, part, 1);
-                    part += __shfl_xor_sync(0xffffffffu, part, 2);
                     a2 += part;
                 }
                 if (live) {
-                    lse_accumulate<12>(a2, z, m, s, q, S);
+                    lse_accumulate<L>(a2, z, m, s, q, S);
                     if constexpr (CV) {
 #pragma unroll
-                        for (int j = 0; j < 12; ++j) Z1[j] += z[j];
+                        for (int j = 0; j < L; ++j) Z1[j] += z[j];
                     }
                 }
             }
 
-            warp_merge<12>(4, m, s, q, S);
+            warp_merge<L>(2, m, s, q, S);
             if constexpr (CV) {
 #pragma unroll
-                for (int off = 16; off >= 4; off >>= 1) {
+                for (int off = 16; off >= 2; off >>= 1) {
 #pragma unroll
-                    for (int j = 0; j < 12; ++j) Z1[j] += __shfl_xor_sync(0xffffffffu, Z1[j], off);
+                    for (int j = 0; j < L; ++j) Z1[j] += __shfl_xor_sync(0xffffffffu, Z1[j], off);
                 }
             }
-            if (lane < 4) {
+            if (lane < 2) {
                 if (lane == 0) { sh.red_m[warp] = m; sh.red_s[warp] = s; sh.red_q[warp] = q; }
 #pragma unroll
-                for (int j = 0; j < 12; ++j) sh.red_S[warp][12 * lane + j] = S[j];
+                for (int j = 0; j < L; ++j) sh.red_S[warp][L * lane + j] = S[j];
                 if constexpr (CV) {
 #pragma unroll
-                    for (int j = 0; j < 12; ++j) {
-                        sh.red_Z1[warp][12 * lane + j] = Z1[j];
-                        sh.red_Z2[warp][12 * lane + j] = 0.0f;
+                    for (int j = 0; j < L; ++j) {
+                        sh.red_Z1[warp][L * lane + j] = Z1[j];
+                        sh.red_Z2[warp][L * lane + j] = 0.0f;
                     }
                 }
             }
@@ -806,18 +818,62 @@ cudaError_t launch_coef(const float* x, int64_t ldx, int64_t M, const float* p, 
     return cudaGetLastError();
 }
 
+// The iterate relative to Algorithm 1's initial one, for a surrogate that learns the
+// correction to it (FP64 per state).  warm = false: d[m] = (v - l(x), Dv - Dl(x)) of the
+// current iterate; warm = true: the iterate becomes v = l(x) + d_v, Dv = Dl(x) + d_p with
+// c = Gamma(Dv).  Row m of d holds the value part in column 0 and Dv in columns 1..n.
+template <class G>
+__global__ void delta_kernel(const float* __restrict__ x, int64_t ldx, int64_t M, GameParams g, double delta,
+                             double eta, double c_min, double c_max, double* __restrict__ v,
+                             float* __restrict__ p, int64_t ldp, float* __restrict__ c, float* __restrict__ d,
+                             int64_t ldd, bool warm, const float* __restrict__ aux, int64_t ldaux) {
+    constexpr int n = G::kN;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double xd[n], gr[n];
+    for (int j = 0; j < n; ++j) xd[j] = (double)x[m * ldx + j];
+    const float* am = G::kAux > 0 ? aux + m * ldaux : nullptr;
+    const double l = G::ell_d(xd, g, am);
+    G::grad_ell_d(xd, gr, g, am);
+    float* dm = d + m * ldd;
+    if (!warm) {
+        dm[0] = (float)(v[m] - l);
+        for (int j = 0; j < n; ++j) dm[1 + j] = (float)((double)p[m * ldp + j] - gr[j]);
+        return;
+    }
+    v[m] = l + (double)dm[0];
+    double pp = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double pj = gr[j] + (double)dm[1 + j];
+        p[m * ldp + j] = (float)pj;
+        gr[j] = (double)(float)pj;   // Gamma of the stored FP32 Dv, as after any sweep
+        pp += gr[j] * gr[j];
+    }
+    int clipped;
+    c[m] = (float)coef_update(G::ham_d(xd, gr, g, am), pp, delta, eta, c_min, c_max, g.tube, &clipped);
+}
+
+template <class G>
+cudaError_t launch_delta(const float* x, int64_t ldx, int64_t M, const GameParams& g, double delta, double eta,
+                         double c_min, double c_max, double* v, float* p, int64_t ldp, float* c, float* d,
+                         int64_t ldd, bool warm, const float* aux, int64_t ldaux, cudaStream_t st) {
+    const int T = 128;
+    delta_kernel<G><<<(unsigned)((M + T - 1) / T), T, 0, st>>>(x, ldx, M, g, delta, eta, c_min, c_max, v, p, ldp,
+                                                               c, d, ldd, warm, aux, ldaux);
+    return cudaGetLastError();
+}
+
 // Launch variants the autotuner chooses among: kind bit 0 = one warp per state (else one
 // CTA per state), bit 1 = software-pipelined sampler, bit 2 = two sample groups per loop
 // iteration; CTA size; minimum resident CTAs per SM (the register budget).  Every game's
 // translation unit instantiates all of them.
-#define HJG_SWEEP_VARIANTS(X) X(0, 4, 128, 8) X(1, 0, 256, 5) X(2, 0, 256, 6) X(3, 0, 128, 1) \
-    X(4, 5, 128, 8) X(5, 1, 256, 6) X(6, 1, 256, 5) X(7, 1, 128, 12) X(8, 2, 256, 4)      \
-    X(9, 2, 128, 8) X(10, 3, 256, 4) X(11, 3, 128, 8)
-#define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 1) X(3, 0, 128, 4) \
-    X(4, 0, 512, 1) X(5, 0, 256, 3) X(6, 0, 256, 4) X(7, 0, 128, 6) X(8, 2, 256, 2)      \
-    X(9, 2, 256, 3) X(10, 2, 128, 6)
+#define HJG_SWEEP_VARIANTS(X) X(0, 4, 128, 8) X(1, 0, 128, 6) X(2, 2, 128, 6) X(3, 0, 128, 4) \
+    X(4, 4, 128, 6) X(5, 1, 256, 3) X(6, 3, 256, 3) X(7, 5, 256, 3) X(8, 2, 256, 4)      \
+    X(9, 2, 128, 8) X(10, 0, 256, 3) X(11, 4, 256, 4)
+#define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 3) X(3, 0, 128, 4) \
+    X(4, 0, 512, 1) X(5, 2, 256, 1) X(6, 2, 128, 3) X(7, 2, 512, 1) X(8, 2, 256, 2)
 constexpr int kNumVariants = 12;
-constexpr int kNumR45Variants = 11;
+constexpr int kNumR45Variants = 9;
 
 template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {

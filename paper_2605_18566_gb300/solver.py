@@ -217,6 +217,18 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.hjg_warm_start(
             self.ctx, self._ptr(v0), self._ptr(p0), p0.stride(0), 1))
 
+    def warm_start_delta(self, d: torch.Tensor):
+        """Initial iterate (l, Dl) plus a learned correction d [M, >= n + 1] (column 0 the
+        value, 1..n the gradient), c = Gamma(Dv) (hjg_warm_start_delta)."""
+        assert d.is_cuda and d.dtype == torch.float32 and d.stride(1) == 1 and d.shape[1] >= self.n + 1
+        _check(self.lib, self.ctx, self.lib.hjg_warm_start_delta(self.ctx, self._ptr(d), d.stride(0)))
+
+    def state_delta(self) -> torch.Tensor:
+        """[M, n + 1] FP32: (v - l(x), Dv - Dl(x)) of the current iterate (hjg_get_state_delta)."""
+        out = torch.empty(self.M, self.n + 1, dtype=torch.float32, device="cuda")
+        _check(self.lib, self.ctx, self.lib.hjg_get_state_delta(self.ctx, self._ptr(out), out.stride(0)))
+        return out
+
     def autotune(self, max_states: int = 0) -> dict:
         """Pick the fastest sweep launch variant on the loaded states (see hjg_autotune)."""
         v = C.c_int32(); t = C.c_int32(); ms = C.c_double()

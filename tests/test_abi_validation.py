@@ -51,7 +51,7 @@ def test_refusals_before_any_device_work(lib):
     for N in (0, 1 << 32):
         dyn, tgt, opt = _args(_lib, N=N)
         assert _create(L, dyn, tgt, opt) == _lib.HJG_EINVAL
-    dyn, tgt, opt = _args(_lib, "rockets45", 45, N=(1 << 32) // 8 + 1)
+    dyn, tgt, opt = _args(_lib, "rockets45", 45, N=(1 << 32) // 6 + 1)   # 6 blocks per sample
     assert _create(L, dyn, tgt, opt) == _lib.HJG_EINVAL
     # viscosity and horizon must be positive and finite
     dyn, tgt, opt = _args(_lib)

@@ -19,8 +19,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.mark.parametrize("game,n", [("dubins3", 3), ("rockets6", 6), ("rockets45", 45)])
 def test_work_constants_follow_the_stream_layout(game, n):
-    # Philox blocks per sample: slots per sample over the six normals a block yields
-    assert bench.BLOCKS_PER_SAMPLE[game] == pytest.approx(oracle.slot_stride(n) / 6.0)
+    # Philox blocks per sample: slots per sample over the eight normals a block yields
+    assert bench.BLOCKS_PER_SAMPLE[game] == pytest.approx(oracle.slot_stride(n) / 8.0)
     # MUFU: lg2, sqrt, sin, cos per Box-Muller pair of the n normals used, one square root
     # for the target distance and one exp2 weight
     assert bench.MUFU_PER_SAMPLE[game] == 4 * n / 2 + 2
@@ -37,7 +37,7 @@ def test_roofline_picks_the_binding_pipe():
     assert r["other_pipes"]["int_mul_hi"] < 1.0
     assert r["traffic"] is None                      # not a full-size launch
     r2 = bench.roofline("rockets6", hjg_inputs.ROCKETS6.M * 10, 1.0, full_size=True)
-    assert r2["traffic"] == bench.DRAM_BYTES_LAUNCH["rockets6"]
+    assert r2["traffic"] == bench.DRAM_BYTES_LAUNCH.get("rockets6")
 
 
 def test_sweeps_to_floor():

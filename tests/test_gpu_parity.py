@@ -118,14 +118,15 @@ def test_quadratic_exact_case_and_negative_c():
         np.testing.assert_allclose(st["c"], h_sign / 0.2, rtol=1e-6)
 
 
-@pytest.mark.parametrize("n", [1, 2, 4, 8])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 8])
 @pytest.mark.parametrize("tilt", [False, True])
 def test_sample_group_remainders(n, tilt):
-    """A thread draws its samples in groups that end on a Philox block boundary (six
-    normals per block: groups of 6, 3, 3, 3 samples for n = 1, 2, 4, 8); every remainder of
-    N modulo the group, and N below one group, matches the oracle's slot-by-slot stream."""
+    """A thread draws its samples in groups that end on a Philox block boundary (eight
+    normals per block: groups of 8, 4, 8, 2, 4, 1 samples from 1, 1, 3, 1, 3, 1 blocks for
+    n = 1, 2, 3, 4, 6, 8); every remainder of N modulo the group, and N below one group,
+    matches the oracle's slot-by-slot stream."""
     from paper_2605_18566_gb300 import Solver
-    gs = {1: 6, 2: 3, 4: 3, 8: 3}[n]
+    gs = {1: 8, 2: 4, 3: 8, 4: 2, 6: 4, 8: 1}[n]
     A = hjg_inputs.spd_matrix(n, 0.3, 0.9, seed=11)
     x0 = np.linspace(-0.3, 0.3, n); d = 0.2
     x = hjg_inputs.random_states(40, n, 1.0, seed=12)
@@ -142,12 +143,12 @@ def test_sample_group_remainders(n, tilt):
         assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="n=%d N=%d" % (n, N))
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4], ids=["256thr", "128thr", "512thr"])
+@pytest.mark.parametrize("variant", [0, 2, 4, 8], ids=["256thr", "128thr", "512thr", "256thr-pipelined"])
 @pytest.mark.parametrize("tilt", [False, True])
 def test_rockets45_sample_counts_off_the_group_grid(variant, tilt):
-    """The 45-D kernel runs four lanes per sample and THREADS / 4 samples per CTA pass, with
+    """The 45-D kernel runs two lanes per sample and THREADS / 2 samples per CTA pass, with
     warp-wide shuffles inside the sample loop: N below, and not a multiple of, the number
-    of sample groups per CTA (32, 64, 128) must give the oracle's result on every state."""
+    of sample groups per CTA (64, 128, 256) must give the oracle's result on every state."""
     x = hjg_inputs.points(W3, M=6)
     for N in (1, 7, 100, 1000):
         st0, st, r, sup, hist = run_gpu(W3, x, N, 1, variant=variant, tilt=tilt)
@@ -215,9 +216,9 @@ def test_empty_and_zero_sweeps():
 
 def test_sample_count_limit():
     """One state's stream may span at most 2^32 Philox blocks: the largest N of the 45-D
-    game (8 blocks of six normals per sample) is accepted, the next one is refused."""
+    game (6 blocks of eight normals per sample) is accepted, the next one is refused."""
     from paper_2605_18566_gb300 import HJGError
-    nmax = (1 << 32) // 8
+    nmax = (1 << 32) // 6
     solver_for(W3, N=nmax, K=1).close()
     with pytest.raises(HJGError):
         solver_for(W3, N=nmax + 1, K=1)

@@ -74,12 +74,14 @@ def test_zero_gradient_guess_keeps_the_value_and_fallback_is_exact():
     np.testing.assert_array_equal(e1, e0)
     assert np.all(np.any(p1 != p0, axis=1))         # the gradient sum is corrected
     # a large gradient guess: -mu b.(sum z) has the sign of +-(u . sum z), so of the guesses
-    # +g and -g exactly one makes the weight sum negative, and that one falls back to the
-    # plain sums bit for bit
+    # +g and -g exactly one makes the weight sum negative (mu = mean weight, so that needs
+    # c sigma |g| |u . sum z| > N: with |g| = 1e4 every stream but one whose |u . sum z| is
+    # below 0.1, against a typical sqrt(N) = 23), and that one falls back to the plain sums
+    # bit for bit
     for m in range(5):
         res = []
         for sgn in (1.0, -1.0):
-            g = np.zeros((5, n)); g[m] = sgn * 500.0 * np.array([0.6, -0.64, 0.48])
+            g = np.zeros((5, n)); g[m] = sgn * 1e4 * np.array([0.6, -0.64, 0.48])
             v2, p2, _ = oracle.sweep(P1, x, c, 512, 0, cv_v=v0, cv_p=g)
             res.append(bool(v2[m] == v0[m] and np.all(p2[m] == p0[m])))
         assert res.count(True) == 1, (m, res)

@@ -91,47 +91,44 @@ def test_philox_counter_sensitivity():
 
 
 def test_uniform_map_exact_and_symmetric():
-    xs = [0, 1, 511, 512, 2**31, 2**32 - 1, 0x12345678]
+    xs = [0, 1, 511, 512, 2**20 - 1, 2**20, 2**31, 2**32 - 1, 0x12345678]
     for x in xs:
         u = oracle.u01(x)
         assert 0.0 < u < 1.0
-        # 23-bit level plus half a step, exact in binary32
+        # 20-bit level plus half a step, exact in binary32
         assert np.float32(u) == u
-        assert u * 2**23 == (x & 0x7FFFFF) + 0.5
+        assert u * 2**20 == (x & 0xFFFFF) + 0.5
         # reflection x -> ~x maps u -> 1 - u exactly
         assert oracle.u01(x) + oracle.u01((~x) & 0xFFFFFFFF) == 1.0
-    assert oracle.u01(0) == 2.0**-24
-    assert oracle.u01(2**32 - 1) == 1.0 - 2.0**-24
+    assert oracle.u01(0) == 2.0**-21
+    assert oracle.u01(2**32 - 1) == 1.0 - 2.0**-21
 
 
 def _pairs(z):
-    return [tuple(z[2 * j:2 * j + 2]) for j in range(3)]
+    return [tuple(z[2 * j:2 * j + 2]) for j in range(4)]
 
 
 def test_box_muller_pair_structure():
-    """Pair j of a block takes its radius from the low 23 bits of word j and its angle
-    from a disjoint field: the high 23 bits of W (j = 0), the high 9 bits of X then of Y
-    (j = 1), the high 9 bits of Z then the low 9 bits of W (j = 2)."""
+    """Pair j of a block is made from word j alone: its radius from the low 20 bits, its
+    angle from the high 12 bits."""
     seed, inst, point, sweep = 0x1234_5678_9ABC, 3, 5, 2
     key = np.array([[seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ inst]], dtype=np.uint32)
-    n = 6                                   # one block per sample
+    n = 8                                   # one block per sample
     for sample in (0, 17, 40000):
         z = oracle.normals(n, seed, inst, sample, point, sweep)
-        X, Y, Z, W = (int(v) for v in oracle.philox4x32_10(
-            np.array([[point, sample, sweep, 0]], dtype=np.uint32), key)[0])
-        radius_u = [oracle.u01(X), oracle.u01(Y), oracle.u01(Z)]
-        angle_u = [((W >> 9) + 0.5) / 2**23,
-                   ((((X >> 23) << 9) | (Y >> 23)) + 0.5) / 2**18,
-                   ((((Z >> 23) << 9) | (W & 511)) + 0.5) / 2**18]
+        words = [int(v) for v in oracle.philox4x32_10(
+            np.array([[point, sample, sweep, 0]], dtype=np.uint32), key)[0]]
         for j, (za, zb) in enumerate(_pairs(z)):
-            np.testing.assert_allclose(za * za + zb * zb, -2.0 * np.log(radius_u[j]), rtol=1e-12)
+            u_r = ((words[j] & 0xFFFFF) + 0.5) / 2**20
+            u_a = ((words[j] >> 20) + 0.5) / 2**12
+            np.testing.assert_allclose(za * za + zb * zb, -2.0 * np.log(u_r), rtol=1e-12)
             ang = np.arctan2(zb, za) % (2 * np.pi)
-            np.testing.assert_allclose(ang, (2 * np.pi * angle_u[j]) % (2 * np.pi), atol=1e-9)
+            np.testing.assert_allclose(ang, (2 * np.pi * u_a) % (2 * np.pi), atol=1e-9)
 
 
 def test_every_block_bit_feeds_exactly_one_pair():
-    """The three pairs of a block read disjoint bit fields that together cover all 128
-    bits: flipping any single bit moves exactly one pair and leaves the other two alone
+    """The four pairs of a block read disjoint bit fields that together cover all 128
+    bits: flipping any single bit moves exactly one pair and leaves the other three alone
     (so pairs within a block are independent, and no generator output is wasted)."""
     r = np.random.default_rng(11)
     for _ in range(4):
@@ -145,52 +142,76 @@ def test_every_block_bit_feeds_exactly_one_pair():
                      if pr != base[j]]
             assert len(moved) == 1, (bit, moved)
             owner.append(moved[0])
-        # 23 radius bits + 23 / 18 / 18 angle bits
-        assert [owner.count(j) for j in range(3)] == [46, 41, 41]
+        # word j feeds pair j: 20 radius + 12 angle bits each
+        assert owner == [b // 32 for b in range(128)]
 
 
-def test_angle_grids_integrate_exactly():
-    """The 18- and 23-bit angle grids are midpoint rules on the circle: the mean of
-    cos(m 2 pi u) and sin(m 2 pi u) over each grid vanishes for 0 < m < 2^bits, so the
-    pair's first 2^bits - 1 trigonometric moments are those of a uniform angle."""
-    for bits in (18,):
-        k = np.arange(2**bits, dtype=np.int64)
-        for m in (1, 2, 3, 7, 1000, 2**bits - 1):
-            # m * 2 pi u, reduced exactly: u = (2k + 1) / 2^(bits+1)
-            ph = 2 * np.pi * ((m * (2 * k + 1)) % 2**(bits + 1)) / 2**(bits + 1)
-            assert abs(np.mean(np.cos(ph))) < 1e-12
-            assert abs(np.mean(np.sin(ph))) < 1e-12
+def test_angle_grid_integrates_exactly():
+    """The 12-bit angle grid is a midpoint rule on the circle: the mean of cos(m 2 pi u) and
+    sin(m 2 pi u) over it vanishes for 0 < m < 2^12, so the pair's first 4,095
+    trigonometric moments are those of a uniform angle."""
+    bits = 12
+    k = np.arange(2**bits, dtype=np.int64)
+    for m in (1, 2, 3, 7, 1000, 2**bits - 1):
+        # m * 2 pi u, reduced exactly: u = (2k + 1) / 2^(bits+1)
+        ph = 2 * np.pi * ((m * (2 * k + 1)) % 2**(bits + 1)) / 2**(bits + 1)
+        assert abs(np.mean(np.cos(ph))) < 1e-12
+        assert abs(np.mean(np.sin(ph))) < 1e-12
+
+
+def test_angle_grid_bias_below_tolerance_for_steep_weights():
+    """The 12-bit angle grid against a continuous angle, for the weights the sweep forms:
+    v = -(1/c) log E exp(-c l(x + sigma z)) with l the distance to a disc, sigma^2 = 0.2 and
+    c up to 1e3 (the clip bound of delta = 0.1).  A finer grid stands in for the continuous
+    angle (the radius integrated on one fine grid for both); the discretisation moves v by
+    less than a fifth of the parity tolerance 1e-4 (1 + |v|): about 1e-7 at c = 10, 1e-6 at
+    c = 100 and at most 1.3e-5 at the clip bound c = 1e3."""
+    sigma, r0 = np.sqrt(0.2), 0.3
+    U = (np.arange(4000) + 0.5) / 4000
+    rho = np.sqrt(-2 * np.log(U))
+
+    def v_est(d, c, nang):
+        ph = 2 * np.pi * (np.arange(nang) + 0.5) / nang + 0.123
+        y0 = d + sigma * rho[:, None] * np.cos(ph)[None]
+        y1 = sigma * rho[:, None] * np.sin(ph)[None]
+        a = -c * (np.sqrt(y0 * y0 + y1 * y1) - r0)
+        m = a.max()
+        return -(m + np.log(np.mean(np.exp(a - m)))) / c
+    for d in (0.5, 1.0, 2.0):
+        for c in (10.0, 100.0, 1000.0):
+            fine = v_est(d, c, 1 << 15)
+            assert abs(v_est(d, c, 1 << 12) - fine) < 2e-5 * (1 + abs(fine)), (d, c)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 6, 7, 45])
 def test_slot_packing(n):
     """Sample s, dim d reads slot s*stride + d of one stream per (state, sweep); the stream
-    is the same whatever n is (compare with the n = 6 layout, one block per sample)."""
+    is the same whatever n is (compare with the n = 8 layout, one block per sample)."""
     stride = oracle.slot_stride(n)
-    assert stride == (n if n <= 8 else 6 * ((n + 5) // 6))
+    assert stride == (n if n <= 8 else 8 * ((n + 7) // 8))
     for s in (0, 1, 2, 3, 11):
         z = oracle.normals(n, 5, 1, s, 9, 4)
         for d in range(n):
             q = s * stride + d
-            assert z[d] == oracle.normals(6, 5, 1, q // 6, 9, 4)[q % 6]
+            assert z[d] == oracle.normals(8, 5, 1, q // 8, 9, 4)[q % 8]
 
 
 def test_normals_distribution():
-    n = 6
+    n = 8
     Z = np.array([oracle.normals(n, 0, 0, i, 3, 1) for i in range(100000)])
     # mean, variance, no cross-correlation, Gaussian shape
     assert np.all(np.abs(Z.mean(0)) < 5 / np.sqrt(len(Z)))
     np.testing.assert_allclose(Z.var(0), 1.0, atol=0.03)
     C = np.corrcoef(Z.T)
     assert np.max(np.abs(C - np.eye(n))) < 0.03
-    for d in range(n):      # six tests: a 1e-4 level each keeps false alarms below 1e-3
+    for d in range(n):      # eight tests: a 1e-4 level each keeps false alarms below 1e-3
         assert stats.kstest(Z[:, d], "norm").pvalue > 1e-4
     # different points / sweeps draw different samples
     a = oracle.normals(n, 0, 0, 0, 0, 0)
     assert not np.allclose(a, oracle.normals(n, 0, 0, 0, 1, 0))
     assert not np.allclose(a, oracle.normals(n, 0, 0, 0, 0, 1))
     assert not np.allclose(a, oracle.normals(n, 0, 1, 0, 0, 0))
-    # truncation: |z| <= sqrt(-2 ln 2^-24)
-    assert np.abs(Z).max() <= np.sqrt(-2 * np.log(2.0**-24)) + 1e-12
+    # truncation: |z| <= sqrt(-2 ln 2^-21)
+    assert np.abs(Z).max() <= np.sqrt(-2 * np.log(2.0**-21)) + 1e-12
 
 
