@@ -550,12 +550,12 @@ def surrogate_study(points_fn, label):
     2,097,152 tuples), GPU training of the 45 -> 256^3 -> 46 BF16 network on them (it learns
     the correction the Picard iteration makes to its initial iterate l, Dl), and, on 1,024
     held-out states, the value error against a tilted N = 2^20 reference for the plain form,
-    the tilted form without the network, and the surrogate-assisted form (warm start
-    l + correction, then tilt, with and without the control variate) over N = 4,096 ...
-    262,144, 12 sweeps each.  `four_x` compares each plain run with the assisted run at a
-    quarter of its point-samples (success: the assisted run reaches the plain run's residual
-    at no larger value error), and `vs_tilt` each assisted run with the tilted run without
-    the network at the same N."""
+    the tilted form without the network (with and without the control variate), and the
+    surrogate-assisted form (warm start l + correction, then tilt, with and without the
+    control variate) over N = 4,096 ... 262,144, 12 sweeps each.  `four_x` compares each
+    plain run with the assisted run at a quarter of its point-samples (success: the assisted
+    run reaches the plain run's residual at no larger value error), and `vs_tilt` each
+    assisted run with the same sweep without the network at the same N."""
     import torch
     from paper_2605_18566_gb300 import Solver, Surrogate
     w = hjg_inputs.ROCKETS45
@@ -602,7 +602,7 @@ def surrogate_study(points_fn, label):
     rows = []
     K = 12
     for N in (4096, 16384, 65536, 262144):
-        for mode in ("plain", "tilt", "surrogate+tilt", "surrogate+tilt+cv"):
+        for mode in ("plain", "tilt", "tilt+cv", "surrogate+tilt", "surrogate+tilt+cv"):
             v, r = solve(N, K, tilt=mode != "plain", warm=mode.startswith("surrogate"), cv=mode.endswith("+cv"))
             rows.append({"mode": mode, "N": N, "K": K, "point_samples_per_state": N * K,
                          "rms_value_error": rms(v), "final_residual": r})
@@ -615,10 +615,12 @@ def surrogate_study(points_fn, label):
                     four_x.append({"plain_N": p["N"], "assisted": a["mode"], "assisted_N": a["N"],
                                    "met": bool(a["final_residual"] <= p["final_residual"]
                                                and a["rms_value_error"] <= p["rms_value_error"])})
-        if p["mode"] == "tilt":
+        if p["mode"] in ("tilt", "tilt+cv"):   # the same sweep without the network
             for a in rows:
-                if a["mode"].startswith("surrogate") and a["N"] == p["N"]:
-                    vs_tilt.append({"N": p["N"], "assisted": a["mode"], "tilt_error": p["rms_value_error"],
+                if (a["mode"].startswith("surrogate") and a["N"] == p["N"]
+                        and a["mode"].endswith("+cv") == p["mode"].endswith("+cv")):
+                    vs_tilt.append({"N": p["N"], "assisted": a["mode"], "without_network": p["mode"],
+                                    "tilt_error": p["rms_value_error"],
                                     "assisted_error": a["rms_value_error"],
                                     "better": bool(a["rms_value_error"] <= p["rms_value_error"])})
     return {"label": label, "tuple_generation_s": t_data, "train_s": t_train,

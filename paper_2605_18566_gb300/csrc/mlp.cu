@@ -961,12 +961,15 @@ hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const flo
 //      the BF16 weight copies (row-major, transposed, canonical) for the next step.
 constexpr int kFW = 256;                         // width of the fused network
 constexpr int kFRows = 128;                      // batch rows per phase-A CTA (one M = 128 tile)
-constexpr int kFThreads = 256;                   // 8 warps: TMEM lane quarter w % 4, column half w / 4
+constexpr int kFThreads = 512;                   // 16 warps: TMEM lane quarter w % 4, column quarter w / 4
 constexpr int kFBufA = kFRows * kFW * 2;         // 64 KB: a layer input, canonical K-major
 constexpr int kFBufB = kFW * kFW * 2;            // 128 KB: a layer's weights, canonical K-major
-constexpr int kFSmemA = kFBufA + kFBufB;
+constexpr int kFPass = 16;                       // columns per epilogue pass of one column group
+constexpr int kFStage = 4 * kFPass * kFRows * 2;  // 16 KB: one pass of the four column groups, transposed
+constexpr int kFBias = kLayers * kFW * 4;         // 4 KB: the biases of the four layers
+constexpr int kFSmemA = kFBufA + kFBufB + kFStage + kFBias;
 constexpr int kWgSplits = 16;                    // phase B split of the batch
-constexpr int kWgStages = 4;
+constexpr int kWgStages = 4;                     // (32 splits at 2 stages, two CTAs per SM: 30 % slower)
 constexpr int kWgStage = (kTcM + kFW) * kTcK * 2;   // A 128 rows + B up to 256 rows, one 64-wide K chunk
 constexpr int kWgSmem = kWgStages * kWgStage;
 
@@ -1037,6 +1040,42 @@ struct FusedArgs {
     int* err;
 };
 
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* x) {
+    uint32_t v[16];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
+              "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+            : "r"(addr + (uint32_t)(8 * q)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(v[j]);
+}
+
+// One pass of a tile, transposed: every thread has put its row's kFPass values into the
+// staging tile [group][kFPass columns][128 rows] (BF16, one group per column quarter of
+// the layer); the CTA writes them as 16-byte pieces of the destination's rows
+// dst[c0g[group] + column][r0 + row] (rows below ldT), so that each store covers eight
+// consecutive batch rows of one column.  ncols[g] limits the columns of group g.
+__device__ __forceinline__ void store_transposed(const __nv_bfloat16* stg, __nv_bfloat16* dst, int64_t ldT,
+                                                 int64_t r0, const int* c0g, const int* ncols, int tid) {
+    constexpr int kPieces = 4 * kFPass * (kFRows / 8);
+#pragma unroll
+    for (int i = 0; i < kPieces / kFThreads; ++i) {
+        const int q = tid + kFThreads * i;
+        const int grp = q / (kFPass * 16), col = (q / 16) % kFPass, rc = q % 16;
+        const int64_t b = r0 + 8 * rc;
+        if (col < ncols[grp] && b < ldT)
+            *reinterpret_cast<uint4*>(dst + (int64_t)(c0g[grp] + col) * ldT + b) =
+                *reinterpret_cast<const uint4*>(stg + ((grp * kFPass + col) * kFRows + 8 * rc));
+    }
+}
+
 __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const FusedArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar_w, bar_m;
@@ -1044,13 +1083,15 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
     __shared__ float s_loss[kFThreads / 32];
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, cg = warp >> 2;             // TMEM lane quarter, column group (of 4)
     const int row = 32 * quarter + lane;                       // this thread's TMEM lane = tile row
-    const int64_t rg = (int64_t)blockIdx.x * kFRows + row;     // batch row
+    const int64_t r0 = (int64_t)blockIdx.x * kFRows;
+    const int64_t rg = r0 + row;                               // batch row
     const bool valid = rg < a.B;
-    const bool in_t = rg < a.ldT;                              // a column of the transposed outputs
     const uint32_t sA = smem_u32(smem), sB = sA + kFBufA;
     __nv_bfloat16* bufA = reinterpret_cast<__nv_bfloat16*>(smem);
+    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + kFBufA + kFBufB);
+    float* s_bias = reinterpret_cast<float*>(smem + kFBufA + kFBufB + kFStage);   // [4][256]
     const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_m);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -1081,10 +1122,15 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
     const int kdim[7] = {ip, kFW, kFW, kFW, op, kFW, kFW};           // K of each product
     if (tid == 0) { bulk_g2s(sB, wsrc[0], wbytes[0], bw); w_pending = true; }
 
-    // input tile: standardised features in BF16 (zero beyond n_in and beyond the batch)
+    // biases of the four layers, and the input tile: standardised features in BF16 (zero
+    // beyond n_in and beyond the batch)
+    for (int e = tid; e < kLayers * kFW; e += kFThreads) {
+        const int l = e / kFW, i = e % kFW;
+        s_bias[e] = i < (l == kLayers - 1 ? op : kFW) ? a.p[a.b_off[l] + i] : 0.0f;
+    }
     for (int e = tid; e < kFRows * ip; e += kFThreads) {
         const int r = e / ip, j = e % ip;
-        const int64_t b = (int64_t)blockIdx.x * kFRows + r;
+        const int64_t b = r0 + r;
         float xv = 0.0f;
         if (b < a.B && j < a.n_in) xv = (a.x[b * a.ldx + j] - a.iscal[j]) * a.iscal[ip + j];
         bufA[canon_idx(r, j, kFRows)] = __float2bfloat16(xv);
@@ -1092,15 +1138,15 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
     __syncthreads();
     for (int e = tid; e < kFRows * ip; e += kFThreads) {   // X^T, the K-major operand of dW_1
         const int j = e / kFRows, r = e % kFRows;
-        const int64_t b = (int64_t)blockIdx.x * kFRows + r;
-        if (b < a.ldT) a.Xt[(int64_t)j * a.ldT + b] = bufA[canon_idx(r, j, kFRows)];
+        if (r0 + r < a.ldT) a.Xt[(int64_t)j * a.ldT + r0 + r] = bufA[canon_idx(r, j, kFRows)];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
 
     float loss = 0.0f;
     for (int t = 0; t < 7; ++t) {
-        // thread 0: the product of step t once its weights have landed
+        // thread 0: the product of step t once its weights have landed, and its completion;
+        // the other threads wait at the barrier (no polling)
         if (tid == 0 && s_ok) {
             if (!mbar_wait(bw, ph_w, a.err)) {
                 s_ok = 0;
@@ -1110,54 +1156,88 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 mma_layer(tmem, sA, sB, wrows[t], kdim[t], umma_idesc_bf16(kFRows, wrows[t]));
                 mma_commit(bm);
+                if (!mbar_wait(bm, ph_m, a.err)) s_ok = 0;
+                ph_m ^= 1u;
             }
         }
-        __syncthreads();
-        if (!s_ok) break;
-        if (!mbar_wait(bm, ph_m, a.err)) s_ok = 0;
-        ph_m ^= 1u;
+        __syncthreads();   // operands free, accumulator complete (or a wait gave up)
         asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();   // every thread past the wait: operands free, accumulator complete
         if (!s_ok) break;
         if (tid == 0 && t + 1 < 7) { bulk_g2s(sB, wsrc[t + 1], wbytes[t + 1], bw); w_pending = true; }
-        if (t < 3) {
-            // hidden layer t: z = acc + b, Z_t, h = silu(z) -> next input, H_t^T
+        // staging tile of this thread: column j of its group, its row
+        __nv_bfloat16* my_stg = stg + cg * kFPass * kFRows + row;
+        if (t < 3 || t > 3) {
+            // hidden layer t (t < 3): z = acc + b, Z_t, h = silu(z) -> next input, H_t^T;
+            // backward (t = 4, 5, 6): dZ_l = (dZ_{l+1} W_{l+1}) silu'(Z_l) for the hidden layer
+            // l = 6 - t (2, 1, 0) -> next input (l > 0), dZ_l^T
+            const bool fwd = t < 3;
+            const int l = fwd ? t : 6 - t;
+            __nv_bfloat16* tdst = fwd ? a.Ht[l] : a.dZt[l];
 #pragma unroll 1
-            for (int pass = 0; pass < 4; ++pass) {
-                const int c0 = half * 128 + 32 * pass;
-                float v[32];
-                tmem_ld32(tl + (uint32_t)c0, v);
-                const float* bias = a.p + a.b_off[t] + c0;
+            for (int pass = 0; pass < 64 / kFPass; ++pass) {
+                const int c0 = cg * 64 + kFPass * pass;
+                float zin[kFPass];
+                if (!fwd) {   // the pre-activations, loaded ahead of the TMEM read
+                    if (valid) {
+                        const float4* zr = reinterpret_cast<const float4*>(a.Z[l] + rg * kFW + c0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] += bias[j];
-                if (valid) {
-                    float4* zr = reinterpret_cast<float4*>(a.Z[t] + rg * kFW + c0);
+                        for (int g = 0; g < kFPass / 4; ++g) {
+                            const float4 zz = zr[g];
+                            zin[4 * g] = zz.x; zin[4 * g + 1] = zz.y; zin[4 * g + 2] = zz.z; zin[4 * g + 3] = zz.w;
+                        }
+                    } else {
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) zr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                        for (int j = 0; j < kFPass; ++j) zin[j] = 0.0f;
+                    }
+                }
+                float v[kFPass];
+                tmem_ld16(tl + (uint32_t)c0, v);
+                if (fwd) {
+                    const float* bias = s_bias + t * kFW + c0;
+#pragma unroll
+                    for (int j = 0; j < kFPass; ++j) v[j] += bias[j];
+                    if (valid) {
+                        float4* zr = reinterpret_cast<float4*>(a.Z[t] + rg * kFW + c0);
+#pragma unroll
+                        for (int g = 0; g < kFPass / 4; ++g)
+                            zr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < kFPass; ++j) v[j] = valid ? silu_fast(v[j]) : 0.0f;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kFPass; ++j) {
+                        const float z = zin[j];
+                        const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
+                        v[j] = valid ? v[j] * sg * (1.0f + z * (1.0f - sg)) : 0.0f;
+                    }
+                }
+                if (fwd || l > 0) {
+#pragma unroll
+                    for (int g = 0; g < kFPass / 8; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
                 }
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = valid ? silu(v[j]) : 0.0f;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
-                if (in_t) {
-                    __nv_bfloat16* ht = a.Ht[t] + (int64_t)c0 * a.ldT + rg;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) ht[(int64_t)j * a.ldT] = __float2bfloat16(v[j]);
-                }
+                for (int j = 0; j < kFPass; ++j) my_stg[j * kFRows] = __float2bfloat16(v[j]);
+                __syncthreads();
+                const int c0g[4] = {kFPass * pass, 64 + kFPass * pass, 128 + kFPass * pass, 192 + kFPass * pass};
+                const int nc[4] = {kFPass, kFPass, kFPass, kFPass};
+                store_transposed(stg, tdst, a.ldT, r0, c0g, nc, tid);
+                __syncthreads();
             }
-        } else if (t == 3) {
-            // output layer: o = acc + b, loss against the standardised targets, dO -> next input, dO^T
-            const int c0 = half * 32;
+        } else {
+            // output layer: o = acc + b, loss against the standardised targets, dO -> next input,
+            // dO^T; each column group covers kFPass of the (at most 64) outputs
+            const int c0 = cg * kFPass;
+            float v[kFPass];
             if (c0 < op) {
-                float v[32];
-                tmem_ld32(tl + (uint32_t)c0, v);
+                tmem_ld16(tl + (uint32_t)c0, v);
                 const float winv = a.n_out > 1 ? 1.0f / (float)(a.n_out - 1) : 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                for (int j = 0; j < kFPass; ++j) {
                     const int col = c0 + j;
                     float g = 0.0f;
                     if (valid && col < a.n_out) {
-                        const float o = v[j] + a.p[a.b_off[3] + col];
+                        const float o = v[j] + s_bias[3 * kFW + col];
                         const float d = o - (a.y[rg * a.ldy + col] - a.oscal[col]) / a.oscal[op + col];
                         const float w = col == 0 ? 1.0f : winv;
                         loss += w * d * d;
@@ -1166,48 +1246,20 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
                     v[j] = g;
                 }
 #pragma unroll
-                for (int g = 0; g < 4; ++g)
-                    if (c0 + 8 * g < op) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
-                if (in_t) {
-                    __nv_bfloat16* dt = a.dZt[3] + (int64_t)c0 * a.ldT + rg;
-                    for (int j = 0; j < 32 && c0 + j < op; ++j) dt[(int64_t)j * a.ldT] = __float2bfloat16(v[j]);
-                }
+                for (int g = 0; g < kFPass / 8; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kFPass; ++j) v[j] = 0.0f;
             }
-        } else {
-            // backward: dZ_l = (dZ_{l+1} W_{l+1}) silu'(Z_l), l = 5 - t -> next input (l > 0), dZ_l^T
-            const int l = 5 - t;
-#pragma unroll 1
-            for (int pass = 0; pass < 4; ++pass) {
-                const int c0 = half * 128 + 32 * pass;
-                float v[32];
-                tmem_ld32(tl + (uint32_t)c0, v);
-                if (valid) {
-                    const float4* zr = reinterpret_cast<const float4*>(a.Z[l] + rg * kFW + c0);
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) {
-                        const float4 zz = zr[g];
-                        const float z4[4] = {zz.x, zz.y, zz.z, zz.w};
+            for (int j = 0; j < kFPass; ++j) my_stg[j * kFRows] = __float2bfloat16(v[j]);
+            __syncthreads();
+            const int c0g[4] = {0, kFPass, 2 * kFPass, 3 * kFPass};
+            int nc[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float z = z4[i];
-                            const float sg = 1.0f / (1.0f + __expf(-z));
-                            v[4 * g + i] *= sg * (1.0f + z * (1.0f - sg));
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0.0f;
-                }
-                if (l > 0) {
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
-                }
-                if (in_t) {
-                    __nv_bfloat16* dt = a.dZt[l] + (int64_t)c0 * a.ldT + rg;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) dt[(int64_t)j * a.ldT] = __float2bfloat16(v[j]);
-                }
-            }
+            for (int g = 0; g < 4; ++g) nc[g] = max(0, min(kFPass, op - g * kFPass));
+            store_transposed(stg, a.dZt[3], a.ldT, r0, c0g, nc, tid);
+            __syncthreads();
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1400,9 +1452,16 @@ __global__ void __launch_bounds__(256) mlp_apply_kernel(const ApplyArgs a) {
     if (gw >= a.n_bias) return;
     int l = 0, i = gw;
     while (l + 1 < kLayers && i >= a.rows[l]) { i -= a.rows[l]; ++l; }
-    const __nv_bfloat16* row = a.dZt[l] + (int64_t)i * a.ldT;
+    const __nv_bfloat16* row = a.dZt[l] + (int64_t)i * a.ldT;   // 16-byte aligned (ldT % 8 == 0)
     float s = 0.0f;
-    for (int64_t b = lane; b < a.B; b += 32) s += __bfloat162float(row[b]);
+    const int64_t nfull = a.B / 8;
+    for (int64_t q = lane; q < nfull; q += 32) {
+        const uint4 u = *reinterpret_cast<const uint4*>(row + 8 * q);
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += __bfloat162float(h[j]);
+    }
+    for (int64_t b = 8 * nfull + lane; b < a.B; b += 32) s += __bfloat162float(row[b]);
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) {

@@ -11,20 +11,20 @@ namespace hjg {
 
 constexpr int kF64Threads = 128;
 
-// Eight FP64 normals of one Philox block, with the uniforms of bm_normals_raw: word j gives
-// pair j, radius uniform ((w & (2^20-1)) + 0.5) 2^-20 and angle uniform ((w >> 20) + 0.5) 2^-12.
-__device__ __forceinline__ void bm_normals_f64(const uint4& r, double* z) {
-    const uint32_t wd[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const double ur = ((double)(wd[j] & 0xFFFFFu) + 0.5) * 0x1p-20;
-        const double ua = ((double)(wd[j] >> 20) + 0.5) * 0x1p-12;
-        const double rad = sqrt(-2.0 * log(ur));
-        double s, c;
-        sincospi(2.0 * ua, &s, &c);
-        z[2 * j] = rad * c;
-        z[2 * j + 1] = rad * s;
-    }
+// The FP64 Box-Muller pair of one Philox word, with the uniforms of bm_normals_raw: radius
+// uniform ((w & (2^20-1)) + 0.5) 2^-20, angle uniform ((w >> 20) + 0.5) 2^-12.
+__device__ __forceinline__ void bm_pair_f64(uint32_t w, double* z) {
+    const double ur = ((double)(w & 0xFFFFFu) + 0.5) * 0x1p-20;
+    const double ua = ((double)(w >> 20) + 0.5) * 0x1p-12;
+    const double rad = sqrt(-2.0 * log(ur));
+    double s, c;
+    sincospi(2.0 * ua, &s, &c);
+    z[0] = rad * c;
+    z[1] = rad * s;
+}
+
+__device__ __forceinline__ uint32_t block_word(const uint4& r, int j) {
+    return j == 0 ? r.x : j == 1 ? r.y : j == 2 ? r.z : r.w;
 }
 
 template <class G, bool TILT>
@@ -70,17 +70,23 @@ __global__ void __launch_bounds__(kF64Threads) sweep_kernel_f64(const SweepArgs 
 #pragma unroll
             for (int j = 0; j < n; ++j) Sz[j] = 0.0;
             for (uint32_t i = (uint32_t)tid; i < N32; i += T) {
-                double z[n], zz[kNormalsPerBlock];
+                // only the pairs the sample reads: the FP64 transcendentals dominate this kernel
+                double z[n], zp[2];
                 const uint64_t q0 = (uint64_t)i * (uint64_t)S;
-                uint64_t cur = ~0ull;
+                uint64_t cur = ~0ull, curp = ~0ull;
+                uint4 rb = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                 for (int d = 0; d < n; ++d) {
                     const uint64_t qq = q0 + (uint64_t)d;
                     if (qq / kNormalsPerBlock != cur) {
                         cur = qq / kNormalsPerBlock;
-                        bm_normals_f64(stream_block((uint32_t)cur, point, sweep, A.rk), zz);
+                        rb = stream_block((uint32_t)cur, point, sweep, A.rk);
                     }
-                    z[d] = zz[qq % kNormalsPerBlock];
+                    if (qq / 2 != curp) {
+                        curp = qq / 2;
+                        bm_pair_f64(block_word(rb, (int)((qq % kNormalsPerBlock) / 2)), zp);
+                    }
+                    z[d] = zp[qq % 2];
                 }
                 double y[n], dot = 0.0;
 #pragma unroll
