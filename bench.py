@@ -75,7 +75,11 @@ IMUL_PER_SM_CLK = 32
 # workload at its full M and K, from one-pass ncu captures of the sweep kernel.  The
 # traffic does not depend on N (samples never touch memory; each state's rows are read and
 # written once per launch).  A workload without a capture of the current kernel has none.
-DRAM_BYTES_LAUNCH = {}
+# rockets45: 110,771,456 B read + 71,333,376 B written, captured at the full 262,144 states and
+# K = 30 with N = 1,024 (launch variant 2, the autotuner's pick); see profiles/.
+DRAM_BYTES_LAUNCH = {"rockets45": 110771456.0 + 71333376.0,
+                     # rockets6: 5,245,440 B read + 0 B written at M = 65,536, K = 20, N = 1,024
+                     "rockets6": 5245440.0 + 0.0}
 
 
 def roofline(game, samples, kernel_s, full_size=False):
@@ -247,7 +251,8 @@ def time_workload(w, steps, warmup, e2e_steps, dev, stream, rank, world, group=N
     buffers."""
     import torch
     from paper_2605_18566_gb300 import Solver, sharding
-    x_np = hjg_inputs.points(w)
+    x_np = hjg_inputs.points(w) if w.M == BENCH_WORKLOADS[w.game].M else \
+        hjg_inputs.points(BENCH_WORKLOADS[w.game])[:w.M]
     lo, hi = sharding.shard_bounds(w.M, world, rank) if sharded else (0, w.M)
     x = torch.from_numpy(x_np[lo:hi]).to(dev)
     Ms = hi - lo
@@ -335,7 +340,8 @@ def workload_line(w, m, world, dev, sharded):
                     "iqr": float(np.subtract(*np.percentile(m["step_ms"], [75, 25])))},
         "e2e": {"value": samples_per_step / e2e_s, "unit": UNIT, "steps": m["e2e_steps"],
                 "h2d_bytes_per_step": m["h2d"] * scale, "d2h_bytes_per_step": m["d2h"] * scale},
-        "roofline": dict(roofline(w.game, rank_samples, kern_s, full_size=not sharded),
+        "roofline": dict(roofline(w.game, rank_samples, kern_s,
+                                  full_size=not sharded and w.M == BENCH_WORKLOADS[w.game].M),
                          kernel_ms_per_step=kern_s * 1e3),
         "launch": {"variant": m["tuned"]["variant"], "threads": m["tuned"]["threads"]},
         "residuals": [float(r) for r in m["resid"]],
@@ -361,6 +367,9 @@ def run_ours(args, rank, world, local_rank):
     sharded = world > 1
     stream = torch.cuda.Stream(device=dev)
     w = BENCH_WORKLOADS[args.workload]
+    if args.states:   # a prefix of the state set (profiling): same states, same draws
+        import dataclasses
+        w = dataclasses.replace(w, M=min(args.states, w.M))
     m = time_workload(w, args.steps, args.warmup, args.e2e_steps, dev, stream, rank, world, sharded=sharded)
     line = workload_line(w, m, world, dev, sharded)
     out = {
@@ -667,6 +676,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
+    ap.add_argument("--states", type=int, default=0,
+                    help="profiling: time only the first STATES states of the workload (same draws)")
     ap.add_argument("--workload", default="rockets45", choices=list(BENCH_WORKLOADS) + ["mixed", "surrogate"],
                     help="rockets45 (default, the benchmark line), rockets6, the mixed batch + flock, "
                          "or the learned part on the 45-D game")

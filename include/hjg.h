@@ -224,6 +224,27 @@ hjg_status hjg_warm_start_delta(hjg_ctx *ctx, const float *d, int64_t ldd);
  * iteration makes to its initial iterate.  Synchronises the context's stream. */
 hjg_status hjg_get_state_delta(hjg_ctx *ctx, float *out, int64_t ldo);
 
+/* The invariant frame of the 45-D game for a surrogate network (Section 3.2's game is
+ * invariant under a common translation, under a common rotation of positions and headings,
+ * and -- with equal pursuer speeds -- under permutations of the pursuers; the paper has no
+ * network).  Per loaded state the pursuers are ordered by distance to the evader (ties by
+ * index) and described in the evader's frame: r_k = R(-theta_e)(p_i - p_e), phi_k =
+ * theta_i - theta_e.
+ *   hjg_frame_features: out [M][ldo] (ldo >= 56) = (r_k, cos phi_k, sin phi_k) for k = 0..13.
+ *   hjg_frame_targets:  out [M][ldo] (ldo >= 43) = (v - l, then per ordered pursuer
+ *                       R(-theta_e) (Dv - Dl)_{p_i} and (Dv - Dl)_{theta_i}) of the current
+ *                       iterate: the training targets.
+ *   hjg_warm_start_frame: from a prediction pred [M][ldp] (ldp >= 43) in that layout, the
+ *                       iterate v = l + dv, Dv = Dl + the correction mapped back by the chain
+ *                       rule (the evader's position part from translation invariance, its
+ *                       heading part from the frame's rotation), c = Gamma(Dv) (Eq.
+ *                       coeff_frozen).
+ * All arrays are DEVICE memory; each call synchronises the context's stream.
+ * EUNSUPPORTED for another game, unequal pursuer speeds or several horizons. */
+hjg_status hjg_frame_features(hjg_ctx *ctx, float *out, int64_t ldo);
+hjg_status hjg_frame_targets(hjg_ctx *ctx, float *out, int64_t ldo);
+hjg_status hjg_warm_start_frame(hjg_ctx *ctx, const float *pred, int64_t ldp);
+
 /* Per-sweep parts of the residual of the last hjg_picard_sweep call over the loaded
  * states: out [n_sweeps][3] = (sum (v^(k+1)-v^(k))^2, sum (v^(k))^2, max |v^(k+1)-v^(k)|),
  * FP64, host.  Shards of one state set combine these (sum, sum, max) to the global

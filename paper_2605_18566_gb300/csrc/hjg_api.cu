@@ -13,6 +13,7 @@
 
 #include "../../include/hjg.h"
 #include "dispatch.h"
+#include "frame45.cuh"
 
 using namespace hjg;
 
@@ -646,6 +647,66 @@ hjg_status hjg_get_state_delta(hjg_ctx* ctx, float* out, int64_t ldo) {
                                   ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c, out, ldo, false, ctx->d_aux, kFlockAux,
                                   st));
     HJG_CUDA(ctx, cudaStreamSynchronize(st));
+    return HJG_OK;
+}
+
+namespace {
+// The invariant frame needs the 45-D game with one speed shared by the pursuers.
+hjg_status frame45_ok(hjg_ctx* ctx) {
+    if (ctx->dyn.game != HJG_ROCKETS45)
+        return fail(ctx, HJG_EUNSUPPORTED, "the invariant surrogate frame is defined for the 45-D game only");
+    for (int i = 1; i < kF45P; ++i)
+        if (ctx->gp.speed_d[i] != ctx->gp.speed_d[0])
+            return fail(ctx, HJG_EUNSUPPORTED, "the invariant surrogate frame needs equal pursuer speeds");
+    if (!ctx->horizons.empty()) return fail(ctx, HJG_EUNSUPPORTED, "the invariant frame takes one horizon");
+    return HJG_OK;
+}
+}  // namespace
+
+hjg_status hjg_frame_features(hjg_ctx* ctx, float* out, int64_t ldo) {
+    if (!ctx || !out) return HJG_EINVAL;
+    hjg_status s;
+    if ((s = frame45_ok(ctx))) return s;
+    if (ldo < kF45In) return fail(ctx, HJG_EINVAL, "ldo < 56");
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    const int T = 128;
+    frame45_out_kernel<<<(unsigned)((M + T - 1) / T), T, 0, ctx->stream>>>(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->d_v,
+                                                                          ctx->d_p, ctx->ldx, out, ldo, 0);
+    HJG_CUDA(ctx, cudaGetLastError());
+    HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HJG_OK;
+}
+
+hjg_status hjg_frame_targets(hjg_ctx* ctx, float* out, int64_t ldo) {
+    if (!ctx || !out) return HJG_EINVAL;
+    hjg_status s;
+    if ((s = frame45_ok(ctx))) return s;
+    if (ldo < kF45Out) return fail(ctx, HJG_EINVAL, "ldo < 43");
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    const int T = 128;
+    frame45_out_kernel<<<(unsigned)((M + T - 1) / T), T, 0, ctx->stream>>>(ctx->d_x, ctx->ldx, M, ctx->gp, ctx->d_v,
+                                                                          ctx->d_p, ctx->ldx, out, ldo, 1);
+    HJG_CUDA(ctx, cudaGetLastError());
+    HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HJG_OK;
+}
+
+hjg_status hjg_warm_start_frame(hjg_ctx* ctx, const float* pred, int64_t ldp) {
+    if (!ctx || !pred) return HJG_EINVAL;
+    hjg_status s;
+    if ((s = frame45_ok(ctx))) return s;
+    if (ldp < kF45Out) return fail(ctx, HJG_EINVAL, "ldp < 43");
+    const int64_t M = ctx->M;
+    if (M == 0) return HJG_OK;
+    ctx->se_valid = false;
+    const int T = 128;
+    frame45_warm_kernel<<<(unsigned)((M + T - 1) / T), T, 0, ctx->stream>>>(
+        ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min, ctx->c_max, pred, ldp, ctx->d_v, ctx->d_p,
+        ctx->ldx, ctx->d_c);
+    HJG_CUDA(ctx, cudaGetLastError());
+    HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HJG_OK;
 }
 

@@ -4,20 +4,23 @@
 
 namespace hjg {
 namespace {
-// KIND bit 1: the software-pipelined sampler.
+// KIND bit 1: the software-pipelined sampler; bits 2-3: the Philox multiply form (0 separate
+// high and low multiplies, 1 widening, 2 one of each per round).
 template <int KIND, int T, int B>
 cudaError_t launch(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
     constexpr bool P = (KIND & 2) != 0;
-    if (tilt) sweep_kernel_r45<T, B, true, false, P><<<grid, T, 0, st>>>(A);
-    else sweep_kernel_r45<T, B, false, false, P><<<grid, T, 0, st>>>(A);
+    constexpr int F = (KIND >> 2) & 3;
+    if (tilt) sweep_kernel_r45<T, B, true, false, P, F><<<grid, T, 0, st>>>(A);
+    else sweep_kernel_r45<T, B, false, false, P, F><<<grid, T, 0, st>>>(A);
     return cudaGetLastError();
 }
 template <int KIND, int T, int B>
 int occupancy(bool tilt) {
     constexpr bool P = (KIND & 2) != 0;
+    constexpr int F = (KIND >> 2) & 3;
     int nb = 0;
-    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, true, false, P>, T, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, false, false, P>, T, 0);
+    if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, true, false, P, F>, T, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<T, B, false, false, P, F>, T, 0);
     return nb;
 }
 #define R45_LAUNCH(i, KIND, T, B) case i: return launch<KIND, T, B>(A, tilt, grid, st);
@@ -42,6 +45,7 @@ int occ(bool tilt, int v) {
     return 0;
 }
 }  // namespace
+static_assert(kNumR45Variants <= kCvVariant, "the 45-D launch variants must not reach the control-variate slot");
 GameKernels kernels_rockets45() {
     GameKernels k{};
     k.n = 45;

@@ -1060,23 +1060,62 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* x) {
 // One pass of a tile, transposed: every thread has put its row's kFPass values into the
 // staging tile [group][kFPass columns][128 rows] (BF16, one group per column quarter of
 // the layer); the CTA writes them as 16-byte pieces of the destination's rows
-// dst[c0g[group] + column][r0 + row] (rows below ldT), so that each store covers eight
-// consecutive batch rows of one column.  ncols[g] limits the columns of group g.
+// dst[c + column][r0 + row] with c = cbase + group * gstride (columns below cmax, rows below
+// ldT), so that each store covers eight consecutive batch rows of one column.
 __device__ __forceinline__ void store_transposed(const __nv_bfloat16* stg, __nv_bfloat16* dst, int64_t ldT,
-                                                 int64_t r0, const int* c0g, const int* ncols, int tid) {
+                                                 int64_t r0, int gstride, int cbase, int cmax, int tid) {
     constexpr int kPieces = 4 * kFPass * (kFRows / 8);
 #pragma unroll
     for (int i = 0; i < kPieces / kFThreads; ++i) {
         const int q = tid + kFThreads * i;
         const int grp = q / (kFPass * 16), col = (q / 16) % kFPass, rc = q % 16;
+        const int c = cbase + grp * gstride + col;
         const int64_t b = r0 + 8 * rc;
-        if (col < ncols[grp] && b < ldT)
-            *reinterpret_cast<uint4*>(dst + (int64_t)(c0g[grp] + col) * ldT + b) =
+        if (c < cmax && b < ldT)
+            *reinterpret_cast<uint4*>(dst + (int64_t)c * ldT + b) =
                 *reinterpret_cast<const uint4*>(stg + ((grp * kFPass + col) * kFRows + 8 * rc));
     }
 }
 
-__global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const FusedArgs a) {
+// Product t of the fused step (0-2 hidden layers, 3 output layer, 4-6 backward data
+// gradients): its weights (canonical copy), their bytes, N (rows of the B operand) and K.
+__device__ __forceinline__ const __nv_bfloat16* fused_w(const FusedArgs& a, int t) {
+    switch (t) {
+    case 0: return a.wc + a.wp_off[0];
+    case 1: return a.wc + a.wp_off[1];
+    case 2: return a.wc + a.wp_off[2];
+    case 3: return a.wc + a.wp_off[3];
+    case 4: return a.wct + a.wp_off[3];
+    case 5: return a.wct + a.wp_off[2];
+    default: return a.wct + a.wp_off[1];
+    }
+}
+__device__ __forceinline__ int fused_n(const FusedArgs& a, int t) { return t == 3 ? a.out_pad : kFW; }
+__device__ __forceinline__ int fused_k(const FusedArgs& a, int t) {
+    return t == 0 ? a.in_pad : t == 4 ? a.out_pad : kFW;
+}
+__device__ __forceinline__ float* fused_z(const FusedArgs& a, int l) { return l == 0 ? a.Z[0] : l == 1 ? a.Z[1] : a.Z[2]; }
+__device__ __forceinline__ __nv_bfloat16* fused_t(const FusedArgs& a, bool fwd, int l) {
+    if (fwd) return l == 0 ? a.Ht[0] : l == 1 ? a.Ht[1] : a.Ht[2];
+    return l == 0 ? a.dZt[0] : l == 1 ? a.dZt[1] : a.dZt[2];
+}
+
+// 64 consecutive FP32 columns of this thread's TMEM lane (one wait for all eight loads).
+__device__ __forceinline__ void tmem_ld64(uint32_t addr, float* x) {
+    uint32_t v[64];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
+              "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+            : "r"(addr + (uint32_t)(8 * q)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(v[j]);
+}
+
+__global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __grid_constant__ FusedArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar_w, bar_m;
     __shared__ uint32_t tmem_base;
@@ -1112,15 +1151,11 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
     uint32_t ph_w = 0, ph_m = 0;
     bool w_pending = false;   // thread 0: a weight copy in flight that no wait has consumed
     const int ip = a.in_pad, op = a.out_pad;
-    // weight copies in the order the seven products use them
-    const __nv_bfloat16* wsrc[7] = {a.wc + a.wp_off[0], a.wc + a.wp_off[1], a.wc + a.wp_off[2], a.wc + a.wp_off[3],
-                                    a.wct + a.wp_off[3], a.wct + a.wp_off[2], a.wct + a.wp_off[1]};
-    const uint32_t wbytes[7] = {(uint32_t)(kFW * ip * 2), (uint32_t)(kFW * kFW * 2), (uint32_t)(kFW * kFW * 2),
-                                (uint32_t)(op * kFW * 2), (uint32_t)(kFW * op * 2), (uint32_t)(kFW * kFW * 2),
-                                (uint32_t)(kFW * kFW * 2)};
-    const int wrows[7] = {kFW, kFW, kFW, op, kFW, kFW, kFW};         // N of each product
-    const int kdim[7] = {ip, kFW, kFW, kFW, op, kFW, kFW};           // K of each product
-    if (tid == 0) { bulk_g2s(sB, wsrc[0], wbytes[0], bw); w_pending = true; }
+    // weight copies in the order the seven products use them (N x K BF16 each)
+    if (tid == 0) {
+        bulk_g2s(sB, fused_w(a, 0), (uint32_t)(fused_n(a, 0) * fused_k(a, 0) * 2), bw);
+        w_pending = true;
+    }
 
     // biases of the four layers, and the input tile: standardised features in BF16 (zero
     // beyond n_in and beyond the batch)
@@ -1154,7 +1189,7 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
                 w_pending = false;
                 ph_w ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                mma_layer(tmem, sA, sB, wrows[t], kdim[t], umma_idesc_bf16(kFRows, wrows[t]));
+                mma_layer(tmem, sA, sB, fused_n(a, t), fused_k(a, t), umma_idesc_bf16(kFRows, fused_n(a, t)));
                 mma_commit(bm);
                 if (!mbar_wait(bm, ph_m, a.err)) s_ok = 0;
                 ph_m ^= 1u;
@@ -1163,7 +1198,10 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
         __syncthreads();   // operands free, accumulator complete (or a wait gave up)
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!s_ok) break;
-        if (tid == 0 && t + 1 < 7) { bulk_g2s(sB, wsrc[t + 1], wbytes[t + 1], bw); w_pending = true; }
+        if (tid == 0 && t + 1 < 7) {
+            bulk_g2s(sB, fused_w(a, t + 1), (uint32_t)(fused_n(a, t + 1) * fused_k(a, t + 1) * 2), bw);
+            w_pending = true;
+        }
         // staging tile of this thread: column j of its group, its row
         __nv_bfloat16* my_stg = stg + cg * kFPass * kFRows + row;
         if (t < 3 || t > 3) {
@@ -1172,32 +1210,37 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
             // l = 6 - t (2, 1, 0) -> next input (l > 0), dZ_l^T
             const bool fwd = t < 3;
             const int l = fwd ? t : 6 - t;
-            __nv_bfloat16* tdst = fwd ? a.Ht[l] : a.dZt[l];
-#pragma unroll 1
+            __nv_bfloat16* tdst = fused_t(a, fwd, l);
+            float* zl = fused_z(a, l) + rg * kFW + cg * 64;   // this thread's 64 pre-activations
+            float acc[64];
+            float zin[kFPass];
+            if (!fwd) {   // pass 0's pre-activations, loaded ahead of the TMEM read
+#pragma unroll
+                for (int g = 0; g < kFPass / 4; ++g) {
+                    const float4 zz = valid ? reinterpret_cast<const float4*>(zl)[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    zin[4 * g] = zz.x; zin[4 * g + 1] = zz.y; zin[4 * g + 2] = zz.z; zin[4 * g + 3] = zz.w;
+                }
+            }
+            tmem_ld64(tl + (uint32_t)(cg * 64), acc);
+#pragma unroll
             for (int pass = 0; pass < 64 / kFPass; ++pass) {
                 const int c0 = cg * 64 + kFPass * pass;
-                float zin[kFPass];
-                if (!fwd) {   // the pre-activations, loaded ahead of the TMEM read
-                    if (valid) {
-                        const float4* zr = reinterpret_cast<const float4*>(a.Z[l] + rg * kFW + c0);
+                float* v = acc + kFPass * pass;
+                float znext[kFPass];
+                if (!fwd && pass + 1 < 64 / kFPass) {   // the next pass's pre-activations
 #pragma unroll
-                        for (int g = 0; g < kFPass / 4; ++g) {
-                            const float4 zz = zr[g];
-                            zin[4 * g] = zz.x; zin[4 * g + 1] = zz.y; zin[4 * g + 2] = zz.z; zin[4 * g + 3] = zz.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < kFPass; ++j) zin[j] = 0.0f;
+                    for (int g = 0; g < kFPass / 4; ++g) {
+                        const float4 zz = valid ? reinterpret_cast<const float4*>(zl + kFPass * (pass + 1))[g]
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                        znext[4 * g] = zz.x; znext[4 * g + 1] = zz.y; znext[4 * g + 2] = zz.z; znext[4 * g + 3] = zz.w;
                     }
                 }
-                float v[kFPass];
-                tmem_ld16(tl + (uint32_t)c0, v);
                 if (fwd) {
                     const float* bias = s_bias + t * kFW + c0;
 #pragma unroll
                     for (int j = 0; j < kFPass; ++j) v[j] += bias[j];
                     if (valid) {
-                        float4* zr = reinterpret_cast<float4*>(a.Z[t] + rg * kFW + c0);
+                        float4* zr = reinterpret_cast<float4*>(zl + kFPass * pass);
 #pragma unroll
                         for (int g = 0; g < kFPass / 4; ++g)
                             zr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
@@ -1211,6 +1254,8 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
                         const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
                         v[j] = valid ? v[j] * sg * (1.0f + z * (1.0f - sg)) : 0.0f;
                     }
+#pragma unroll
+                    for (int j = 0; j < kFPass; ++j) zin[j] = znext[j];
                 }
                 if (fwd || l > 0) {
 #pragma unroll
@@ -1219,9 +1264,7 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
 #pragma unroll
                 for (int j = 0; j < kFPass; ++j) my_stg[j * kFRows] = __float2bfloat16(v[j]);
                 __syncthreads();
-                const int c0g[4] = {kFPass * pass, 64 + kFPass * pass, 128 + kFPass * pass, 192 + kFPass * pass};
-                const int nc[4] = {kFPass, kFPass, kFPass, kFPass};
-                store_transposed(stg, tdst, a.ldT, r0, c0g, nc, tid);
+                store_transposed(stg, tdst, a.ldT, r0, 64, kFPass * pass, kFW, tid);
                 __syncthreads();
             }
         } else {
@@ -1254,11 +1297,7 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const Fu
 #pragma unroll
             for (int j = 0; j < kFPass; ++j) my_stg[j * kFRows] = __float2bfloat16(v[j]);
             __syncthreads();
-            const int c0g[4] = {0, kFPass, 2 * kFPass, 3 * kFPass};
-            int nc[4];
-#pragma unroll
-            for (int g = 0; g < 4; ++g) nc[g] = max(0, min(kFPass, op - g * kFPass));
-            store_transposed(stg, a.dZt[3], a.ldT, r0, c0g, nc, tid);
+            store_transposed(stg, a.dZt[3], a.ldT, r0, kFPass, 0, op, tid);
             __syncthreads();
         }
         asm volatile("tcgen05.fence::before_thread_sync;");

@@ -108,11 +108,26 @@ __device__ __forceinline__ uint32_t mullo_u32(uint32_t a, uint32_t b) {
     uint32_t r; asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
 }
 
+// The rounds with the products in one of three instruction forms (identical results):
+// MULF = 0 separate high and low multiplies, 1 one widening multiply per product, 2 one of
+// each per round.  Which is fastest depends on the kernel's mix of pipes (the launch
+// variants carry the choice and the autotuner measures it).
+template <int MULF = 0>
 __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 ctr, const PhiloxKeys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t h0 = mulhi_u32(kPhiloxM0, ctr.x), l0 = mullo_u32(kPhiloxM0, ctr.x);
-        const uint32_t h1 = mulhi_u32(kPhiloxM1, ctr.z), l1 = mullo_u32(kPhiloxM1, ctr.z);
+        uint32_t h0, l0, h1, l1;
+        if (MULF == 1) {
+            const uint64_t p0 = (uint64_t)kPhiloxM0 * ctr.x, p1 = (uint64_t)kPhiloxM1 * ctr.z;
+            h0 = (uint32_t)(p0 >> 32); l0 = (uint32_t)p0; h1 = (uint32_t)(p1 >> 32); l1 = (uint32_t)p1;
+        } else if (MULF == 2) {
+            const uint64_t p0 = (uint64_t)kPhiloxM0 * ctr.x;
+            h0 = (uint32_t)(p0 >> 32); l0 = (uint32_t)p0;
+            h1 = mulhi_u32(kPhiloxM1, ctr.z); l1 = mullo_u32(kPhiloxM1, ctr.z);
+        } else {
+            h0 = mulhi_u32(kPhiloxM0, ctr.x); l0 = mullo_u32(kPhiloxM0, ctr.x);
+            h1 = mulhi_u32(kPhiloxM1, ctr.z); l1 = mullo_u32(kPhiloxM1, ctr.z);
+        }
         ctr = make_uint4(h1 ^ ctr.y ^ rk.k0[r], l1, h0 ^ ctr.w ^ rk.k1[r], l0);
     }
     return ctr;
@@ -141,15 +156,16 @@ __device__ __forceinline__ void bm_normals_raw(const uint4& r, float* z) {
 }
 
 // Philox block b of the stream of (point, sweep).
+template <int MULF = 0>
 __device__ __forceinline__ uint4 stream_block(uint32_t b, uint32_t point, uint32_t sweep,
                                               const PhiloxKeys& rk) {
-    return philox4x32_10_rk(make_uint4(point, b, sweep, 0u), rk);
+    return philox4x32_10_rk<MULF>(make_uint4(point, b, sweep, 0u), rk);
 }
 
-template <int NUSE>
+template <int NUSE, int MULF = 0>
 __device__ __forceinline__ void block_normals_raw(uint32_t b, uint32_t point, uint32_t sweep,
                                                   const PhiloxKeys& rk, float* z) {
-    bm_normals_raw<NUSE>(stream_block(b, point, sweep, rk), z);
+    bm_normals_raw<NUSE>(stream_block<MULF>(b, point, sweep, rk), z);
 }
 template <int NUSE>
 __device__ __forceinline__ void block_normals(uint32_t b, uint32_t point, uint32_t sweep,

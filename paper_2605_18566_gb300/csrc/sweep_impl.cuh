@@ -346,17 +346,17 @@ __device__ __forceinline__ void consume_block(int b, const uint4& r, float* z, F
 // generator with the transcendental and FP32 work of the samples; the one block drawn past
 // the end is discarded.  With UNR2 two independent groups are drawn per iteration.  All
 // forms consume identical draws.
-template <int GS, int GB, int S, int STRIDE, bool PIPE, bool UNR2, class F>
+template <int GS, int GB, int S, int STRIDE, bool PIPE, bool UNR2, int MULF, class F>
 __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32_t point, uint32_t sweep,
                                            const PhiloxKeys& rk, F&& sample) {
     if constexpr (PIPE) {
-        uint4 r = stream_block(start * GB, point, sweep, rk);
+        uint4 r = stream_block<MULF>(start * GB, point, sweep, rk);
         for (uint32_t grp = start; grp < full; grp += STRIDE) {
             float z[kNormalsPerBlock * GB];
 #pragma unroll
             for (int b = 0; b < GB; ++b) {
                 const uint32_t nb = (b + 1 < GB) ? grp * GB + b + 1 : (grp + STRIDE) * GB;
-                const uint4 rn = stream_block(nb, point, sweep, rk);
+                const uint4 rn = stream_block<MULF>(nb, point, sweep, rk);
                 consume_block<GS, S>(b, r, z, sample);
                 r = rn;
             }
@@ -368,8 +368,8 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
                 float z[kNormalsPerBlock * GB], y[kNormalsPerBlock * GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b) {
-                    const uint4 ra = stream_block(grp * GB + b, point, sweep, rk);
-                    const uint4 rb = stream_block((grp + STRIDE) * GB + b, point, sweep, rk);
+                    const uint4 ra = stream_block<MULF>(grp * GB + b, point, sweep, rk);
+                    const uint4 rb = stream_block<MULF>((grp + STRIDE) * GB + b, point, sweep, rk);
                     consume_block<GS, S>(b, ra, z, sample);
                     consume_block<GS, S>(b, rb, y, sample);
                 }
@@ -378,7 +378,7 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
         for (; grp < full; grp += STRIDE) {
             float z[kNormalsPerBlock * GB];
 #pragma unroll
-            for (int b = 0; b < GB; ++b) consume_block<GS, S>(b, stream_block(grp * GB + b, point, sweep, rk), z, sample);
+            for (int b = 0; b < GB; ++b) consume_block<GS, S>(b, stream_block<MULF>(grp * GB + b, point, sweep, rk), z, sample);
         }
     }
 }
@@ -387,7 +387,7 @@ __device__ __forceinline__ void run_groups(uint32_t start, uint32_t full, uint32
 // One lane per sample stream (games with n <= 8).  A thread draws samples in groups of
 // g = group_samples(n) that end on a Philox block boundary (n = 3: 2 samples from 1 block;
 // n = 4: 3 samples from 2 blocks; n = 6: 1 sample from 1 block), so every normal drawn is used.
-template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool CV = false, bool UNR2 = false>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool CV = false, bool UNR2 = false, int MULF = 0>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int NPAD = (n + 3) / 4 * 4;
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
                     }
                 }
             };
-            run_groups<GS, GB, n, THREADS, PIPE, UNR2>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
-                                                      sample);
+            run_groups<GS, GB, n, THREADS, PIPE, UNR2, MULF>((uint32_t)tid, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                                            sample);
             if (GS > 1 && full < groups && tid == (int)(full % THREADS)) {   // ragged last group
                 float z[kNormalsPerBlock * GB];
 #pragma unroll
@@ -541,7 +541,7 @@ __device__ __noinline__ float warp_recover(const SweepArgs& A, const Sig& sig, i
 // FP64 recovery and coefficient update and broadcasts the new (c, Dv) with shuffles.
 // No CTA barrier is involved, so a warp never waits for another state's epilogue.
 // Chosen by the autotuner when there are many more states than warps in flight.
-template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool UNR2 = false>
+template <class G, int THREADS, int MINB, bool TILT, bool PIPE, bool UNR2 = false, int MULF = 0>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepArgs A) {
     constexpr int n = G::kN;
     constexpr int GS = group_samples(n);
@@ -599,8 +599,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
                 }
                 lse_accumulate<n>(a, zt, m, s, q, S);
             };
-            run_groups<GS, GB, n, 32, PIPE, UNR2>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
-                                                 sample);
+            run_groups<GS, GB, n, 32, PIPE, UNR2, MULF>((uint32_t)lane, full, A.pt0 + (uint32_t)pt, sweep, A.rk,
+                                                       sample);
             if (GS > 1 && full < groups && lane == (int)(full % 32)) {
                 float z[kNormalsPerBlock * GB];
 #pragma unroll
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
 // lane takes the minimum squared distance over its own pursuers (eight on h = 0, six on
 // h = 1), and one shuffle finishes the pair's minimum.  Both lanes then hold the same
 // log-weight and accumulate their own 24 S_j.
-template <int THREADS, int MINB, bool TILT, bool CV = false, bool PIPE = false>
+template <int THREADS, int MINB, bool TILT, bool CV = false, bool PIPE = false, int MULF = 0>
 __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArgs A) {
     static_assert(!CV || TILT, "the 45-D control variate runs in the tilted frame");
     using G = Rockets45;
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
             uint4 rb[3];
             if constexpr (PIPE) {
 #pragma unroll
-                for (int j = 0; j < 3; ++j) rb[j] = stream_block(6u * (uint32_t)grp + 3u * h + j, point, sweep, A.rk);
+                for (int j = 0; j < 3; ++j) rb[j] = stream_block<MULF>(6u * (uint32_t)grp + 3u * h + j, point, sweep, A.rk);
             }
             for (uint32_t t = 0; t < trips; ++t) {
                 const uint32_t i = (uint32_t)grp + t * (uint32_t)GROUPS;
@@ -695,14 +695,14 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
                     const uint32_t nx = i + (uint32_t)GROUPS;
                     uint4 rn[3];
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) rn[j] = stream_block(6u * nx + 3u * h + j, point, sweep, A.rk);
+                    for (int j = 0; j < 3; ++j) rn[j] = stream_block<MULF>(6u * nx + 3u * h + j, point, sweep, A.rk);
 #pragma unroll
                     for (int j = 0; j < 3; ++j) bm_normals_raw<8>(rb[j], z + 8 * j);
 #pragma unroll
                     for (int j = 0; j < 3; ++j) rb[j] = rn[j];
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) block_normals_raw<8>(6u * i + 3u * h + j, point, sweep, A.rk, z + 8 * j);
+                    for (int j = 0; j < 3; ++j) block_normals_raw<8, MULF>(6u * i + 3u * h + j, point, sweep, A.rk, z + 8 * j);
                 }
                 float yx[8], yz[8];
 #pragma unroll
@@ -865,25 +865,28 @@ cudaError_t launch_delta(const float* x, int64_t ldx, int64_t M, const GameParam
 
 // Launch variants the autotuner chooses among: kind bit 0 = one warp per state (else one
 // CTA per state), bit 1 = software-pipelined sampler, bit 2 = two sample groups per loop
-// iteration; CTA size; minimum resident CTAs per SM (the register budget).  Every game's
-// translation unit instantiates all of them.
+// iteration, bits 3-4 = the Philox multiply form (philox4x32_10_rk); CTA size; minimum
+// resident CTAs per SM (the register budget).  Every game's translation unit instantiates
+// all of them.
 #define HJG_SWEEP_VARIANTS(X) X(0, 4, 128, 8) X(1, 0, 128, 6) X(2, 2, 128, 6) X(3, 0, 128, 4) \
     X(4, 4, 128, 6) X(5, 1, 256, 3) X(6, 3, 256, 3) X(7, 5, 256, 3) X(8, 2, 256, 4)      \
-    X(9, 2, 128, 8) X(10, 0, 256, 3) X(11, 4, 256, 4)
+    X(9, 2, 128, 8) X(10, 13, 256, 3) X(11, 10, 128, 8)
 #define HJG_R45_VARIANTS(X) X(0, 0, 256, 1) X(1, 0, 256, 2) X(2, 0, 128, 3) X(3, 0, 128, 4) \
-    X(4, 0, 512, 1) X(5, 2, 256, 1) X(6, 2, 128, 3) X(7, 2, 512, 1) X(8, 2, 256, 2)
+    X(4, 0, 512, 1) X(5, 2, 256, 1) X(6, 2, 128, 3) X(7, 2, 512, 1) X(8, 2, 256, 2)       \
+    X(9, 4, 128, 3) X(10, 8, 128, 3) X(11, 6, 128, 3)
 constexpr int kNumVariants = 12;
-constexpr int kNumR45Variants = 9;
+constexpr int kNumR45Variants = 12;   // below kCvVariant: the slots after the variants are taken
 
 template <class G, int KIND, int THREADS, int MINB>
 cudaError_t launch_sweep_generic(const SweepArgs& A, bool tilt, int grid, cudaStream_t st) {
     constexpr bool PIPE = (KIND & 2) != 0, U2 = (KIND & 4) != 0;
+    constexpr int F = (KIND >> 3) & 3;
     if constexpr ((KIND & 1) != 0) {
-        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true, PIPE, U2><<<grid, THREADS, 0, st>>>(A);
-        else sweep_kernel_warp<G, THREADS, MINB, false, PIPE, U2><<<grid, THREADS, 0, st>>>(A);
+        if (tilt) sweep_kernel_warp<G, THREADS, MINB, true, PIPE, U2, F><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel_warp<G, THREADS, MINB, false, PIPE, U2, F><<<grid, THREADS, 0, st>>>(A);
     } else {
-        if (tilt) sweep_kernel<G, THREADS, MINB, true, PIPE, false, U2><<<grid, THREADS, 0, st>>>(A);
-        else sweep_kernel<G, THREADS, MINB, false, PIPE, false, U2><<<grid, THREADS, 0, st>>>(A);
+        if (tilt) sweep_kernel<G, THREADS, MINB, true, PIPE, false, U2, F><<<grid, THREADS, 0, st>>>(A);
+        else sweep_kernel<G, THREADS, MINB, false, PIPE, false, U2, F><<<grid, THREADS, 0, st>>>(A);
     }
     return cudaGetLastError();
 }
@@ -910,12 +913,13 @@ template <class G, int KIND, int THREADS, int MINB>
 int occupancy_generic(bool tilt) {
     int nb = 0;
     constexpr bool PIPE = (KIND & 2) != 0, U2 = (KIND & 4) != 0;
+    constexpr int F = (KIND >> 3) & 3;
     if constexpr ((KIND & 1) != 0) {
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true, PIPE, U2>, THREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false, PIPE, U2>, THREADS, 0);
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, true, PIPE, U2, F>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_warp<G, THREADS, MINB, false, PIPE, U2, F>, THREADS, 0);
     } else {
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true, PIPE, false, U2>, THREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false, PIPE, false, U2>, THREADS, 0);
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, true, PIPE, false, U2, F>, THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, THREADS, MINB, false, PIPE, false, U2, F>, THREADS, 0);
     }
     return nb;
 }

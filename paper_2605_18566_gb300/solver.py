@@ -229,6 +229,23 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.hjg_get_state_delta(self.ctx, self._ptr(out), out.stride(0)))
         return out
 
+    def frame_features(self) -> torch.Tensor:
+        """45-D game: [M, 56] invariant-frame inputs of the loaded states (hjg_frame_features)."""
+        out = torch.empty(self.M, 56, dtype=torch.float32, device="cuda")
+        _check(self.lib, self.ctx, self.lib.hjg_frame_features(self.ctx, self._ptr(out), out.stride(0)))
+        return out
+
+    def frame_targets(self) -> torch.Tensor:
+        """45-D game: [M, 43] invariant-frame correction of the current iterate (hjg_frame_targets)."""
+        out = torch.empty(self.M, 43, dtype=torch.float32, device="cuda")
+        _check(self.lib, self.ctx, self.lib.hjg_frame_targets(self.ctx, self._ptr(out), out.stride(0)))
+        return out
+
+    def warm_start_frame(self, pred: torch.Tensor):
+        """45-D game: warm start from an invariant-frame prediction [M, >= 43] (hjg_warm_start_frame)."""
+        assert pred.is_cuda and pred.dtype == torch.float32 and pred.stride(1) == 1 and pred.shape[1] >= 43
+        _check(self.lib, self.ctx, self.lib.hjg_warm_start_frame(self.ctx, self._ptr(pred), pred.stride(0)))
+
     def autotune(self, max_states: int = 0) -> dict:
         """Pick the fastest sweep launch variant on the loaded states (see hjg_autotune)."""
         v = C.c_int32(); t = C.c_int32(); ms = C.c_double()

@@ -15,9 +15,9 @@ pytestmark = pytest.mark.gpu
 N_IN, N_OUT, WIDTH = 45, 46, 256
 
 
-def _sur(seed=1):
+def _sur(seed=1, n_in=N_IN, n_out=N_OUT):
     from paper_2605_18566_gb300 import Surrogate
-    return Surrogate(N_IN, N_OUT, WIDTH, seed=seed)
+    return Surrogate(n_in, n_out, WIDTH, seed=seed)
 
 
 def test_forward_matches_reference():
@@ -34,24 +34,29 @@ def test_forward_matches_reference():
     s.close()
 
 
-def test_gradients_match_reference():
-    s = _sur(seed=2)
+# (45, 46): the state-coordinate network of the 45-D game (input pad 48); (56, 43): its
+# invariant-frame network (input pad 64, the largest the fused step takes; output pad 48)
+@pytest.mark.parametrize("n_in,n_out", [(N_IN, N_OUT), (56, 43)])
+def test_gradients_match_reference(n_in, n_out):
+    s = _sur(seed=2, n_in=n_in, n_out=n_out)
     rng = np.random.default_rng(4)
-    x = hjg_inputs.random_states(300, N_IN, 1.5, seed=5)
-    y = rng.normal(size=(300, N_OUT)).astype(np.float32)
+    x = hjg_inputs.random_states(300, n_in, 1.5, seed=5)
+    y = rng.normal(size=(300, n_out)).astype(np.float32)
     loss, g = s.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     p = s.params()
-    rloss, rg = omlp.loss_and_grads(p, x.astype(np.float64), y.astype(np.float64), N_IN, N_OUT,
+    rloss, rg = omlp.loss_and_grads(p, x.astype(np.float64), y.astype(np.float64), n_in, n_out,
                                     WIDTH, bf16=True)
     assert abs(loss - rloss) <= 1e-3 * rloss
-    lay, _ = omlp.layout(N_IN, N_OUT, WIDTH)
+    lay, _ = omlp.layout(n_in, n_out, WIDTH)
     for (w, o, i, b) in lay:
         for a, z in ((w, w + o * i), (b, b + o)):
             gg, rr = g[a:z].astype(np.float64), rg[a:z]
             assert np.linalg.norm(gg - rr) <= 2e-2 * np.linalg.norm(rr) + 1e-12, (a, z)
     # padded outputs/inputs receive no gradient
     w4, o4, i4, b4 = lay[3]
-    assert np.all(g[w4:w4 + o4 * i4].reshape(o4, i4)[N_OUT:] == 0)
+    assert np.all(g[w4:w4 + o4 * i4].reshape(o4, i4)[n_out:] == 0)
+    w1, o1, i1, b1 = lay[0]
+    assert np.all(g[w1:w1 + o1 * i1].reshape(o1, i1)[:, n_in:] == 0)
     s.close()
 
 

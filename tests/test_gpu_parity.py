@@ -143,7 +143,8 @@ def test_sample_group_remainders(n, tilt):
         assert_parity(st["v"], st["p"], ref["v"], ref["p"], what="n=%d N=%d" % (n, N))
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4, 8], ids=["256thr", "128thr", "512thr", "256thr-pipelined"])
+@pytest.mark.parametrize("variant", [0, 2, 4, 8, 9, 10],
+                         ids=["256thr", "128thr", "512thr", "256thr-pipelined", "wide-mul", "mixed-mul"])
 @pytest.mark.parametrize("tilt", [False, True])
 def test_rockets45_sample_counts_off_the_group_grid(variant, tilt):
     """The 45-D kernel runs two lanes per sample and THREADS / 2 samples per CTA pass, with
