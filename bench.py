@@ -61,8 +61,10 @@ PAPER_CONTEXT = {"value": 2.0e7, "unit": UNIT,
 #   (the low halves issue at twice that rate and are not the binding part)
 #   MUFU (XU pipe): log2, sqrt, sin, cos per Box-Muller pair, one sqrt for the target
 #   distance, one exp2 weight (exp2 issues at twice the rate of the others on GB300)
-BLOCKS_PER_SAMPLE = {"dubins3": 3 / 8, "rockets6": 6 / 8, "rockets45": 6.0}
-MUFU_PER_SAMPLE = {"dubins3": 2 * 3 + 2, "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
+BLOCKS_PER_SAMPLE = {"double_int2": 2 / 8, "dubins3": 3 / 8, "rockets_rel3": 3 / 8, "rockets6": 6 / 8,
+                     "rockets45": 6.0}
+MUFU_PER_SAMPLE = {"double_int2": 2 * 2 + 2, "dubins3": 2 * 3 + 2, "rockets_rel3": 2 * 3 + 2,
+                   "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
 IMUL_PER_BLOCK = 16
 # GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations
 # and 32 high-half integer multiplies.
@@ -553,6 +555,55 @@ def run_mixed(args):
     return out
 
 
+def run_games(args):
+    """Every game's sweep kernel on its own workload's states: the autotuner's launch variant,
+    the best of three timed launches of 2 sweeps at the workload's N (the Dubins game at
+    N = 65,536), with the binding-pipe roofline where the game's per-sample work is counted
+    (the flock's target reads its neighbour lists: no count, no roofline); and the 3-D Dubins
+    workload as specified (4,096 states, N = 4,096, 10 sweeps) solved in FP32 and in FP64."""
+    import torch
+    from paper_2605_18566_gb300 import Solver
+    games = {}
+    with ClockSampler(0) as clk:
+        for w in (hjg_inputs.DOUBLE_INT2, hjg_inputs.DUBINS3, hjg_inputs.ROCKETS_REL3, hjg_inputs.FLOCK,
+                  hjg_inputs.ROCKETS6, hjg_inputs.ROCKETS45):
+            x = torch.from_numpy(hjg_inputs.points(w)).cuda()
+            N = 65536 if w.game == "dubins3" else w.N
+            s = Solver(w.game, w.nu, w.T, N, 2, radius=w.radius, speed=list(w.speed) or None)
+            s.set_points(x)
+            t = s.autotune(max_states=4 * SMS * 6)
+            best = float("inf")
+            for _ in range(max(3, args.steps)):
+                s.set_points(x)
+                s.picard_sweep(2)
+                best = min(best, s.diagnostics()["last_ms"])
+            samples = x.shape[0] * N * 2
+            games[w.name] = {"game": w.game, "M": int(x.shape[0]), "N": N, "sweeps": 2,
+                             "variant": t["variant"], "threads": t["threads"], "kernel_ms": best,
+                             "value": samples / (best / 1e3),
+                             "roofline": roofline(w.game, samples, best / 1e3)
+                             if w.game in BLOCKS_PER_SAMPLE else None}
+            s.close()
+        w = hjg_inputs.DUBINS3
+        x = torch.from_numpy(hjg_inputs.points(w)).cuda()
+        solves = {}
+        for prec in ("fp32", "fp64"):
+            s = Solver(w.game, w.nu, w.T, w.N, w.K, radius=w.radius, precision=prec)
+            s.set_points(x)
+            if prec == "fp32":
+                s.autotune()
+            best = float("inf")
+            for _ in range(3):
+                s.set_points(x)
+                s.picard_sweep(w.K)
+                best = min(best, s.diagnostics()["last_ms"])
+            solves[prec] = {"kernel_ms": best, "value": w.M * w.N * w.K / (best / 1e3)}
+            s.close()
+    return {"metric": METRIC + ", per game", "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32 (FP64 combine/log/residual)", "data": "synthetic (seeded states)",
+            "games": games, "dubins3_workload_solve": solves, "clocks": clk.summary()}
+
+
 def surrogate_study(points_fn, label):
     """One study of the learned part on the 45-D game: tuples (x, v - l(x), Dv - Dl(x)) from
     the plain sweeps of 262,144 states drawn by points_fn (sweeps 23-30 of 30 at N = 131,072:
@@ -678,9 +729,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
     ap.add_argument("--states", type=int, default=0,
                     help="profiling: time only the first STATES states of the workload (same draws)")
-    ap.add_argument("--workload", default="rockets45", choices=list(BENCH_WORKLOADS) + ["mixed", "surrogate"],
+    ap.add_argument("--workload", default="rockets45", choices=list(BENCH_WORKLOADS) + ["mixed", "surrogate", "games"],
                     help="rockets45 (default, the benchmark line), rockets6, the mixed batch + flock, "
-                         "or the learned part on the 45-D game")
+                         "the learned part on the 45-D game, or every game's sweep kernel")
     ap.add_argument("--ncu-case", default=None, choices=list(hjg_inputs.WORKLOADS) + ["surrogate_mlp"],
                     help="run one small launch of the named workload's sweep (profiling)")
     ap.add_argument("--variant", type=int, default=2, help="sweep launch variant for --ncu-case")
@@ -721,9 +772,10 @@ def main():
         print(json.dumps(out))
         return
 
-    if args.workload in ("mixed", "surrogate"):
+    if args.workload in ("mixed", "surrogate", "games"):
         if rank == 0:
-            print(json.dumps(run_mixed(args) if args.workload == "mixed" else run_surrogate(args)))
+            run = {"mixed": run_mixed, "surrogate": run_surrogate, "games": run_games}[args.workload]
+            print(json.dumps(run(args)))
         return
     out = run_ours(args, rank, world, local_rank)
     final, w = out.pop("_final")

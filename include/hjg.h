@@ -422,6 +422,18 @@ hjg_status hjg_mlp_set_scaling(hjg_mlp *m, const float *in);
 hjg_status hjg_mlp_train_step(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy,
                               int64_t B, float lr, double *loss_out);
 
+/* Training loop in the library: Adam steps over the contiguous minibatches [b0, b0 + batch)
+ * of the n rows of x [n][ldx] and y [n][ldy] (device; shuffle the rows beforehand), b0 =
+ * 0, batch, 2 batch, ... while b0 + batch <= n (one minibatch of all n rows when n <
+ * batch), for `epochs` passes, the learning rate decaying geometrically from lr at the first
+ * step to lr_final at the last.  With standardize != 0 the feature standardisation is first
+ * fitted to (x, y) (hjg_mlp_fit_scaling).  hist (host, `epochs` doubles, may be NULL)
+ * receives each epoch's loss on its last minibatch; the call synchronises once per epoch
+ * when hist is given, else not at all.  EINVAL for epochs < 1, batch < 1, lr <= 0 or
+ * lr_final <= 0. */
+hjg_status hjg_mlp_fit(hjg_mlp *m, const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t n,
+                       int epochs, int64_t batch, float lr, float lr_final, int standardize, double *hist);
+
 /* The surrogate's GEMM on its own (the tensor-core kernel behind hjg_mlp_*):
  * C(m, n) = sum_k A(m, k) B(k, n) with A(m, k) = A[m*sam + k*sak] and B(k, n) =
  * B[k*sbk + n*sbn] in BF16, C [M][ldc] FP32, device pointers.  timed_out (host, may be

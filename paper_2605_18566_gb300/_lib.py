@@ -94,6 +94,8 @@ _SIGS = {
     "hjg_mlp_fit_scaling": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64]),
     "hjg_mlp_get_scaling": (C.c_int, [_vp, _vp]),
     "hjg_mlp_set_scaling": (C.c_int, [_vp, _vp]),
+    "hjg_mlp_fit": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_int, C.c_int64,
+                              C.c_float, C.c_float, C.c_int, _vp]),
     "hjg_mlp_train_step": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int64, C.c_float,
                                      C.POINTER(C.c_double)]),
     "hjg_batch_create": (C.c_int, [C.POINTER(_vp)]),

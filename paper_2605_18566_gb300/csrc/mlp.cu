@@ -948,26 +948,32 @@ hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const flo
 
 // ------------------------------------------------------------------------------------
 // Fused training step of the width-256 network (in_pad, out_pad <= 64), three launches:
-//   A  one CTA per 128 batch rows runs the whole forward pass, the loss and the backward
-//      data-gradient pass through all four layers on the tensor cores: each layer's input
-//      sits in shared memory in the canonical K-major layout, the layer's weights arrive
-//      by one bulk copy (issued while the previous layer's epilogue runs), the 128 x 256
-//      FP32 accumulator lives in TMEM, and the epilogue writes the next layer's input back
-//      to shared memory, so activations never leave the SM between layers; it also writes
-//      what the weight gradients need (H_l^T, dZ_l^T, X^T) and the pre-activations Z_l;
+//   A  a pair of CTAs (a thread-block cluster of two) per 128 batch rows runs the whole
+//      forward pass, the loss and the backward data-gradient pass through all four layers on
+//      the tensor cores.  Each CTA computes half of every 256-wide layer (128 output columns):
+//      the layer's input sits in shared memory in the canonical K-major layout, the CTA's half
+//      of the weights arrives by one bulk copy (issued while the previous layer's epilogue
+//      runs), the 128 x 128 FP32 accumulator lives in TMEM, and the epilogue writes the CTA's
+//      half of the next layer's input to shared memory, from where one bulk copy
+//      (shared::cta -> the partner's shared::cluster, completion counted on the partner's
+//      mbarrier) hands it to the partner: activations never leave the pair between layers.
+//      The narrow output layer (N = out_pad) is computed by both CTAs.  The epilogue also
+//      writes what the weight gradients need (H_l^T, dZ_l^T, X^T) and the pre-activations Z_l;
 //   B  the weight gradients dW_l = dZ_l^T H_{l-1} as 128 x N tiles (N = the layer's input
 //      width, up to 256) over a split of the batch (split-K), TMA-fed four-stage pipeline;
 //   C  the fixed-order sum of the splits, the bias gradients (column sums of dZ_l), Adam and
 //      the BF16 weight copies (row-major, transposed, canonical) for the next step.
 constexpr int kFW = 256;                         // width of the fused network
-constexpr int kFRows = 128;                      // batch rows per phase-A CTA (one M = 128 tile)
-constexpr int kFThreads = 512;                   // 16 warps: TMEM lane quarter w % 4, column quarter w / 4
-constexpr int kFBufA = kFRows * kFW * 2;         // 64 KB: a layer input, canonical K-major
-constexpr int kFBufB = kFW * kFW * 2;            // 128 KB: a layer's weights, canonical K-major
+constexpr int kFHalf = 128;                      // output columns per CTA of a pair
+constexpr int kFRows = 128;                      // batch rows per CTA pair (one M = 128 tile)
+constexpr int kFThreads = 512;                   // 16 warps: TMEM lane quarter w % 4, column group w / 4
+constexpr int kFBuf = kFRows * kFW * 2;          // 64 KB: a layer input (K <= 256), canonical K-major; two of them
+constexpr int kFBufW = kFHalf * kFW * 2;         // 64 KB: this CTA's half of a layer's weights, canonical K-major
 constexpr int kFPass = 16;                       // columns per epilogue pass of one column group
 constexpr int kFStage = 4 * kFPass * kFRows * 2;  // 16 KB: one pass of the four column groups, transposed
 constexpr int kFBias = kLayers * kFW * 4;         // 4 KB: the biases of the four layers
-constexpr int kFSmemA = kFBufA + kFBufB + kFStage + kFBias;
+constexpr int kFSmemA = 2 * kFBuf + kFBufW + kFStage + kFBias;
+constexpr uint32_t kFHalfBytes = kFRows * kFHalf * 2;   // 32 KB: one CTA's half of a 256-wide layer input
 constexpr int kWgSplits = 16;                    // phase B split of the batch
 constexpr int kWgStages = 4;                     // (32 splits at 2 stages, two CTAs per SM: 30 % slower)
 constexpr int kWgStage = (kTcM + kFW) * kTcK * 2;   // A 128 rows + B up to 256 rows, one 64-wide K chunk
@@ -978,6 +984,30 @@ constexpr int kWgSmem = kWgStages * kWgStage;
 // [K / 8][R][8] -- core matrices 128 B apart along the rows and R x 16 B apart along K.
 __host__ __device__ inline int64_t canon_idx(int64_t r, int64_t k, int64_t R) {
     return ((k >> 3) * R + r) * 8 + (k & 7);
+}
+
+// Offset of W(r, k) of an R x K weight operand in the canonical BF16 copies: a 256-row
+// operand is stored as two 128-row halves [half][K / 8][128][8], so that each CTA of a
+// pair loads its half with one contiguous copy; narrower operands are one block.
+__host__ __device__ inline int64_t canon_w_idx(int64_t r, int64_t k, int64_t R, int64_t K) {
+    if (R == kFW) return (r / kFHalf) * kFHalf * K + canon_idx(r % kFHalf, k, kFHalf);
+    return canon_idx(r, k, R);
+}
+
+// Bulk copy of `bytes` from this CTA's shared memory to the same offset in the partner
+// CTA's (rank `peer` of the cluster), completion counted on the partner's mbarrier at the
+// same offset as `bar` here.
+__device__ __forceinline__ void bulk_s2peer(uint32_t src, uint32_t bytes, uint32_t bar, uint32_t peer) {
+    uint32_t dst, rbar;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst) : "r"(src), "r"(peer));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(bar), "r"(peer));
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "r"(src), "r"(bytes), "r"(rbar) : "memory");
+}
+
+// Every thread of both CTAs of the pair (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -1078,21 +1108,23 @@ __device__ __forceinline__ void store_transposed(const __nv_bfloat16* stg, __nv_
 }
 
 // Product t of the fused step (0-2 hidden layers, 3 output layer, 4-6 backward data
-// gradients): its weights (canonical copy), their bytes, N (rows of the B operand) and K.
-__device__ __forceinline__ const __nv_bfloat16* fused_w(const FusedArgs& a, int t) {
-    switch (t) {
-    case 0: return a.wc + a.wp_off[0];
-    case 1: return a.wc + a.wp_off[1];
-    case 2: return a.wc + a.wp_off[2];
-    case 3: return a.wc + a.wp_off[3];
-    case 4: return a.wct + a.wp_off[3];
-    case 5: return a.wct + a.wp_off[2];
-    default: return a.wct + a.wp_off[1];
-    }
-}
-__device__ __forceinline__ int fused_n(const FusedArgs& a, int t) { return t == 3 ? a.out_pad : kFW; }
+// gradients): this CTA's weights (canonical copy; the half of rank `rank` for the 256-row
+// operands, all of the output layer's), N (rows of the B operand) and K.
 __device__ __forceinline__ int fused_k(const FusedArgs& a, int t) {
     return t == 0 ? a.in_pad : t == 4 ? a.out_pad : kFW;
+}
+__device__ __forceinline__ int fused_n(const FusedArgs& a, int t) { return t == 3 ? a.out_pad : kFHalf; }
+__device__ __forceinline__ const __nv_bfloat16* fused_w(const FusedArgs& a, int t, uint32_t rank) {
+    const int64_t half = t == 3 ? 0 : (int64_t)rank * kFHalf * fused_k(a, t);
+    switch (t) {
+    case 0: return a.wc + a.wp_off[0] + half;
+    case 1: return a.wc + a.wp_off[1] + half;
+    case 2: return a.wc + a.wp_off[2] + half;
+    case 3: return a.wc + a.wp_off[3];
+    case 4: return a.wct + a.wp_off[3] + half;
+    case 5: return a.wct + a.wp_off[2] + half;
+    default: return a.wct + a.wp_off[1] + half;
+    }
 }
 __device__ __forceinline__ float* fused_z(const FusedArgs& a, int l) { return l == 0 ? a.Z[0] : l == 1 ? a.Z[1] : a.Z[2]; }
 __device__ __forceinline__ __nv_bfloat16* fused_t(const FusedArgs& a, bool fwd, int l) {
@@ -1100,46 +1132,36 @@ __device__ __forceinline__ __nv_bfloat16* fused_t(const FusedArgs& a, bool fwd, 
     return l == 0 ? a.dZt[0] : l == 1 ? a.dZt[1] : a.dZt[2];
 }
 
-// 64 consecutive FP32 columns of this thread's TMEM lane (one wait for all eight loads).
-__device__ __forceinline__ void tmem_ld64(uint32_t addr, float* x) {
-    uint32_t v[64];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
-              "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
-            : "r"(addr + (uint32_t)(8 * q)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(v[j]);
-}
-
-__global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __grid_constant__ FusedArgs a) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
+    mlp_fused_fwdbwd_kernel(const __grid_constant__ FusedArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bar_w, bar_m;
+    __shared__ __align__(8) uint64_t bar_w, bar_m, bar_x;
     __shared__ uint32_t tmem_base;
     __shared__ float s_loss[kFThreads / 32];
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, cg = warp >> 2;             // TMEM lane quarter, column group (of 4)
     const int row = 32 * quarter + lane;                       // this thread's TMEM lane = tile row
-    const int64_t r0 = (int64_t)blockIdx.x * kFRows;
+    uint32_t rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const uint32_t peer = rank ^ 1u;
+    const int hcol = (int)rank * kFHalf;                       // first layer column of this CTA's half
+    const int64_t r0 = (int64_t)(blockIdx.x >> 1) * kFRows;
     const int64_t rg = r0 + row;                               // batch row
     const bool valid = rg < a.B;
-    const uint32_t sA = smem_u32(smem), sB = sA + kFBufA;
-    __nv_bfloat16* bufA = reinterpret_cast<__nv_bfloat16*>(smem);
-    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + kFBufA + kFBufB);
-    float* s_bias = reinterpret_cast<float*>(smem + kFBufA + kFBufB + kFStage);   // [4][256]
-    const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_m);
+    const uint32_t sbuf = smem_u32(smem), sW = sbuf + 2 * kFBuf;
+    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + 2 * kFBuf + kFBufW);
+    float* s_bias = reinterpret_cast<float*>(smem + 2 * kFBuf + kFBufW + kFStage);   // [4][256]
+    const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_m), bx = smem_u32(&bar_x);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(kFW));
+                     :: "r"(smem_u32(&tmem_base)), "r"(kFHalf));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bw));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bm));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bx));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_ok = 1;
     }
@@ -1148,71 +1170,94 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's TMEM lanes
-    uint32_t ph_w = 0, ph_m = 0;
+    uint32_t ph_w = 0, ph_m = 0, ph_x = 0;
     bool w_pending = false;   // thread 0: a weight copy in flight that no wait has consumed
     const int ip = a.in_pad, op = a.out_pad;
-    // weight copies in the order the seven products use them (N x K BF16 each)
     if (tid == 0) {
-        bulk_g2s(sB, fused_w(a, 0), (uint32_t)(fused_n(a, 0) * fused_k(a, 0) * 2), bw);
+        bulk_g2s(sW, fused_w(a, 0, rank), (uint32_t)(fused_n(a, 0) * fused_k(a, 0) * 2), bw);
         w_pending = true;
+        mbar_expect_tx(bx, kFHalfBytes);   // the partner's half of the first hidden layer
     }
 
-    // biases of the four layers, and the input tile: standardised features in BF16 (zero
-    // beyond n_in and beyond the batch)
+    // biases of the four layers, and the input tile in buffer 0: standardised features in
+    // BF16 (zero beyond n_in and beyond the batch)
     for (int e = tid; e < kLayers * kFW; e += kFThreads) {
         const int l = e / kFW, i = e % kFW;
         s_bias[e] = i < (l == kLayers - 1 ? op : kFW) ? a.p[a.b_off[l] + i] : 0.0f;
     }
+    __nv_bfloat16* buf0 = reinterpret_cast<__nv_bfloat16*>(smem);
     for (int e = tid; e < kFRows * ip; e += kFThreads) {
         const int r = e / ip, j = e % ip;
         const int64_t b = r0 + r;
         float xv = 0.0f;
         if (b < a.B && j < a.n_in) xv = (a.x[b * a.ldx + j] - a.iscal[j]) * a.iscal[ip + j];
-        bufA[canon_idx(r, j, kFRows)] = __float2bfloat16(xv);
+        buf0[canon_idx(r, j, kFRows)] = __float2bfloat16(xv);
     }
     __syncthreads();
-    for (int e = tid; e < kFRows * ip; e += kFThreads) {   // X^T, the K-major operand of dW_1
-        const int j = e / kFRows, r = e % kFRows;
-        if (r0 + r < a.ldT) a.Xt[(int64_t)j * a.ldT + r0 + r] = bufA[canon_idx(r, j, kFRows)];
+    if (rank == 0) {
+        for (int e = tid; e < kFRows * ip; e += kFThreads) {   // X^T, the K-major operand of dW_1
+            const int j = e / kFRows, r = e % kFRows;
+            if (r0 + r < a.ldT) a.Xt[(int64_t)j * a.ldT + r0 + r] = buf0[canon_idx(r, j, kFRows)];
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    cluster_sync();   // both CTAs' barriers are initialised before any copy reaches them
 
+    // Step t reads buffer t % 2 and writes the next input into buffer (t + 1) % 2.  The
+    // partner's half arrives (on bar_x) for the inputs of steps 1, 2, 3, 5 and 6; this CTA
+    // sends its half after steps 0, 1, 2, 4 and 5.  A copy into the partner's buffer
+    // (t + 1) % 2 cannot overtake the partner's product t - 1 that reads it: this CTA's
+    // product t needed the partner's output of step t - 1, written after that product --
+    // except after step 3, whose inputs are local, hence the cluster barrier there.  The
+    // sequence of cluster barriers is the same on every path (a failed wait skips work, not
+    // barriers), so neither CTA can wait on one the other never reaches.
     float loss = 0.0f;
     for (int t = 0; t < 7; ++t) {
-        // thread 0: the product of step t once its weights have landed, and its completion;
-        // the other threads wait at the barrier (no polling)
+        const bool recv = t == 1 || t == 2 || t == 3 || t == 5 || t == 6;
+        const bool send = t == 0 || t == 1 || t == 2 || t == 4 || t == 5;
+        const uint32_t s_in = sbuf + (uint32_t)((t & 1) * kFBuf);
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(smem + ((t + 1) & 1) * kFBuf);
+        // thread 0: the product of step t once its weights (and the partner's half of its
+        // input) have landed, and its completion; the other threads wait at the barrier
         if (tid == 0 && s_ok) {
-            if (!mbar_wait(bw, ph_w, a.err)) {
-                s_ok = 0;
-            } else {
-                w_pending = false;
-                ph_w ^= 1u;
+            bool ok = mbar_wait(bw, ph_w, a.err);
+            if (ok) { w_pending = false; ph_w ^= 1u; }
+            if (ok && recv) {
+                ok = mbar_wait(bx, ph_x, a.err);
+                if (ok) {
+                    ph_x ^= 1u;
+                    if (t != 6) mbar_expect_tx(bx, kFHalfBytes);   // the next reception
+                }
+            }
+            if (ok) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                mma_layer(tmem, sA, sB, fused_n(a, t), fused_k(a, t), umma_idesc_bf16(kFRows, fused_n(a, t)));
+                mma_layer(tmem, s_in, sW, fused_n(a, t), fused_k(a, t), umma_idesc_bf16(kFRows, fused_n(a, t)));
                 mma_commit(bm);
-                if (!mbar_wait(bm, ph_m, a.err)) s_ok = 0;
+                ok = mbar_wait(bm, ph_m, a.err);
                 ph_m ^= 1u;
             }
+            if (!ok) s_ok = 0;
         }
         __syncthreads();   // operands free, accumulator complete (or a wait gave up)
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!s_ok) break;
-        if (tid == 0 && t + 1 < 7) {
-            bulk_g2s(sB, fused_w(a, t + 1), (uint32_t)(fused_n(a, t + 1) * fused_k(a, t + 1) * 2), bw);
+        const bool ok = s_ok != 0;   // uniform over the CTA
+        if (t == 3) cluster_sync();  // both products of step 3 are done with buffer 1
+        if (ok && tid == 0 && t + 1 < 7) {
+            bulk_g2s(sW, fused_w(a, t + 1, rank), (uint32_t)(fused_n(a, t + 1) * fused_k(a, t + 1) * 2), bw);
             w_pending = true;
         }
         // staging tile of this thread: column j of its group, its row
         __nv_bfloat16* my_stg = stg + cg * kFPass * kFRows + row;
-        if (t < 3 || t > 3) {
+        if (ok && t != 3) {
             // hidden layer t (t < 3): z = acc + b, Z_t, h = silu(z) -> next input, H_t^T;
             // backward (t = 4, 5, 6): dZ_l = (dZ_{l+1} W_{l+1}) silu'(Z_l) for the hidden layer
-            // l = 6 - t (2, 1, 0) -> next input (l > 0), dZ_l^T
+            // l = 6 - t (2, 1, 0) -> next input (l > 0), dZ_l^T; 32 columns per thread
             const bool fwd = t < 3;
             const int l = fwd ? t : 6 - t;
             __nv_bfloat16* tdst = fused_t(a, fwd, l);
-            float* zl = fused_z(a, l) + rg * kFW + cg * 64;   // this thread's 64 pre-activations
-            float acc[64];
+            float* zl = fused_z(a, l) + rg * kFW + hcol + cg * 32;   // this thread's 32 pre-activations
+            float acc[32];
             float zin[kFPass];
             if (!fwd) {   // pass 0's pre-activations, loaded ahead of the TMEM read
 #pragma unroll
@@ -1221,13 +1266,13 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __
                     zin[4 * g] = zz.x; zin[4 * g + 1] = zz.y; zin[4 * g + 2] = zz.z; zin[4 * g + 3] = zz.w;
                 }
             }
-            tmem_ld64(tl + (uint32_t)(cg * 64), acc);
+            tmem_ld32(tl + (uint32_t)(cg * 32), acc);
 #pragma unroll
-            for (int pass = 0; pass < 64 / kFPass; ++pass) {
-                const int c0 = cg * 64 + kFPass * pass;
+            for (int pass = 0; pass < 32 / kFPass; ++pass) {
+                const int c0 = hcol + cg * 32 + kFPass * pass;   // layer column
                 float* v = acc + kFPass * pass;
                 float znext[kFPass];
-                if (!fwd && pass + 1 < 64 / kFPass) {   // the next pass's pre-activations
+                if (!fwd && pass + 1 < 32 / kFPass) {   // the next pass's pre-activations
 #pragma unroll
                     for (int g = 0; g < kFPass / 4; ++g) {
                         const float4 zz = valid ? reinterpret_cast<const float4*>(zl + kFPass * (pass + 1))[g]
@@ -1259,17 +1304,18 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __
                 }
                 if (fwd || l > 0) {
 #pragma unroll
-                    for (int g = 0; g < kFPass / 8; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
+                    for (int g = 0; g < kFPass / 8; ++g) st_canon8(out, row, c0 + 8 * g, v + 8 * g);
                 }
 #pragma unroll
                 for (int j = 0; j < kFPass; ++j) my_stg[j * kFRows] = __float2bfloat16(v[j]);
                 __syncthreads();
-                store_transposed(stg, tdst, a.ldT, r0, 64, kFPass * pass, kFW, tid);
+                store_transposed(stg, tdst, a.ldT, r0, 32, hcol + kFPass * pass, kFW, tid);
                 __syncthreads();
             }
-        } else {
-            // output layer: o = acc + b, loss against the standardised targets, dO -> next input,
-            // dO^T; each column group covers kFPass of the (at most 64) outputs
+        } else if (ok) {
+            // output layer (both CTAs): o = acc + b, dO against the standardised targets ->
+            // next input; the loss and dO^T from rank 0; each column group covers kFPass of
+            // the (at most 64) outputs
             const int c0 = cg * kFPass;
             float v[kFPass];
             if (c0 < op) {
@@ -1283,13 +1329,13 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __
                         const float o = v[j] + s_bias[3 * kFW + col];
                         const float d = o - (a.y[rg * a.ldy + col] - a.oscal[col]) / a.oscal[op + col];
                         const float w = col == 0 ? 1.0f : winv;
-                        loss += w * d * d;
+                        if (rank == 0) loss += w * d * d;
                         g = 2.0f * w * d / (float)a.B;
                     }
                     v[j] = g;
                 }
 #pragma unroll
-                for (int g = 0; g < kFPass / 8; ++g) st_canon8(bufA, row, c0 + 8 * g, v + 8 * g);
+                for (int g = 0; g < kFPass / 8; ++g) st_canon8(out, row, c0 + 8 * g, v + 8 * g);
             } else {
 #pragma unroll
                 for (int j = 0; j < kFPass; ++j) v[j] = 0.0f;
@@ -1297,12 +1343,14 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __
 #pragma unroll
             for (int j = 0; j < kFPass; ++j) my_stg[j * kFRows] = __float2bfloat16(v[j]);
             __syncthreads();
-            store_transposed(stg, a.dZt[3], a.ldT, r0, kFPass, 0, op, tid);
+            if (rank == 0) store_transposed(stg, a.dZt[3], a.ldT, r0, kFPass, 0, op, tid);
             __syncthreads();
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (ok && send && tid == 0)   // this CTA's half of the next input to the partner
+            bulk_s2peer(smem_u32(out) + (uint32_t)rank * kFHalfBytes, kFHalfBytes, bx, peer);
     }
     // the loss of this tile (FP32 per thread, then the warps in a fixed order)
 #pragma unroll
@@ -1310,14 +1358,17 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_fwdbwd_kernel(const __
     if (lane == 0) s_loss[warp] = loss;
     if (tid == 0 && w_pending) mbar_wait(bw, ph_w, a.err);   // no copy may land after the exit
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && rank == 0) {
         float t = 0.0f;
         for (int w = 0; w < kFThreads / 32; ++w) t += s_loss[w];
-        a.lpart[blockIdx.x] = (double)t / (double)a.B;
+        a.lpart[blockIdx.x >> 1] = (double)t / (double)a.B;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFW));
+    // neither CTA leaves while the partner may still copy into its shared memory: every copy
+    // was consumed by the receiver's wait before the receiver reached this barrier
+    cluster_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFHalf));
 }
 
 // Phase B: split-K weight gradients.  Item i = (layer, 128-row tile of dW_l), split s of the
@@ -1442,8 +1493,9 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
 }
 
 // Phase C: gradients and (with lr > 0) the Adam step and the BF16 weight copies.  Blocks
-// [0, nwb): one thread per weight, the splits added in order; blocks [nwb, ...): one warp per
-// bias, the column sum of dZ_l over the batch (lanes over the rows, then a fixed butterfly).
+// [0, nwb): one thread per weight, the splits added in order; blocks [nwb, ...): one block per
+// bias, the column sum of dZ_l over the batch (eight warps over the rows, lanes within a
+// warp, then fixed-order combines).
 struct ApplyArgs {
     int64_t w_off[kLayers], b_off[kLayers], wp_off[kLayers], n_w;
     int rows[kLayers], cols[kLayers];
@@ -1482,31 +1534,41 @@ __global__ void __launch_bounds__(256) mlp_apply_kernel(const ApplyArgs a) {
         if (a.lr > 0.0f) {
             const __nv_bfloat16 hb = __float2bfloat16(adam_update(a, pi, s));
             a.pbT[a.w_off[l] + (int64_t)c * R + r] = hb;
-            a.wc[a.wp_off[l] + canon_idx(r, c, R)] = hb;
-            a.wct[a.wp_off[l] + canon_idx(c, r, Cc)] = hb;
+            a.wc[a.wp_off[l] + canon_w_idx(r, c, R, Cc)] = hb;
+            a.wct[a.wp_off[l] + canon_w_idx(c, r, Cc, R)] = hb;
         }
         return;
     }
-    const int gw = ((int)blockIdx.x - a.nwb) * 8 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (gw >= a.n_bias) return;
-    int l = 0, i = gw;
+    // one block per bias: warp w sums the batch rows [w B / 8, (w + 1) B / 8) of its dZ_l^T row,
+    // then thread 0 adds the eight warp sums in order
+    __shared__ float s_part[8];
+    const int gb = (int)blockIdx.x - a.nwb, warp = (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (gb >= a.n_bias) return;
+    int l = 0, i = gb;
     while (l + 1 < kLayers && i >= a.rows[l]) { i -= a.rows[l]; ++l; }
     const __nv_bfloat16* row = a.dZt[l] + (int64_t)i * a.ldT;   // 16-byte aligned (ldT % 8 == 0)
+    const int64_t nfull = a.B / 8;                                // 8-row pieces
+    const int64_t q0 = nfull * warp / 8, q1 = nfull * (warp + 1) / 8;
     float s = 0.0f;
-    const int64_t nfull = a.B / 8;
-    for (int64_t q = lane; q < nfull; q += 32) {
+#pragma unroll 4
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
         const uint4 u = *reinterpret_cast<const uint4*>(row + 8 * q);
         const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
 #pragma unroll
         for (int j = 0; j < 8; ++j) s += __bfloat162float(h[j]);
     }
-    for (int64_t b = 8 * nfull + lane; b < a.B; b += 32) s += __bfloat162float(row[b]);
+    if (warp == 7)
+        for (int64_t b = 8 * nfull + lane; b < a.B; b += 32) s += __bfloat162float(row[b]);
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
+    if (lane == 0) s_part[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < 8; ++w) t += s_part[w];
         const int64_t pi = a.b_off[l] + i;
-        a.g[pi] = s;
-        if (a.lr > 0.0f) adam_update(a, pi, s);
+        a.g[pi] = t;
+        if (a.lr > 0.0f) adam_update(a, pi, t);
     }
 }
 
@@ -1520,8 +1582,8 @@ __global__ void canon_weights_kernel(const float* __restrict__ p, ApplyArgs a) {
     const int R = a.rows[l], Cc = a.cols[l];
     const int r = (int)(k / Cc), c = (int)(k % Cc);
     const __nv_bfloat16 hb = __float2bfloat16(p[a.w_off[l] + k]);
-    a.wc[a.wp_off[l] + canon_idx(r, c, R)] = hb;
-    a.wct[a.wp_off[l] + canon_idx(c, r, Cc)] = hb;
+    a.wc[a.wp_off[l] + canon_w_idx(r, c, R, Cc)] = hb;
+    a.wct[a.wp_off[l] + canon_w_idx(c, r, Cc, R)] = hb;
 }
 
 bool fused_ok(const hjg_mlp* m) {
@@ -1610,7 +1672,7 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
     for (int l = 0; l + 1 < kLayers; ++l) { fa.Z[l] = m->Z[l]; fa.Ht[l] = m->Ht[l]; }
     fa.Xt = m->Xt; fa.lpart = m->flpart; fa.err = g_tc_err;
     const int ntile = (int)((B + kFRows - 1) / kFRows);
-    mlp_fused_fwdbwd_kernel<<<ntile, kFThreads, kFSmemA, st>>>(fa);
+    mlp_fused_fwdbwd_kernel<<<2 * ntile, kFThreads, kFSmemA, st>>>(fa);   // clusters of two
     if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
 
     WgradArgs wa;
@@ -1639,7 +1701,7 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
         aa.c1 = 1.0f - powf(aa.b1, (float)m->step);
         aa.c2 = 1.0f - powf(aa.b2, (float)m->step);
     }
-    mlp_apply_kernel<<<aa.nwb + (aa.n_bias + 7) / 8, 256, 0, st>>>(aa);
+    mlp_apply_kernel<<<aa.nwb + aa.n_bias, 256, 0, st>>>(aa);
     if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
     if (loss_out) {
         std::vector<double> part((size_t)ntile);
@@ -1930,6 +1992,30 @@ hjg_status hjg_mlp_train_step(hjg_mlp* m, const float* x, int64_t ldx, const flo
     adam_kernel<<<nblk(m->n_params), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb, m->n_params, lr,
                                                            b1, b2, 1e-8f, c1, c2);
     if (cudaGetLastError() != cudaSuccess || refresh_wt(m, m->stream) != cudaSuccess) return HJG_ECUDA;
+    return HJG_OK;
+}
+
+hjg_status hjg_mlp_fit(hjg_mlp* m, const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t n,
+                       int epochs, int64_t batch, float lr, float lr_final, int standardize, double* hist) {
+    if (!m || !x || !y || n < 1 || epochs < 1 || batch < 1 || !(lr > 0) || !(lr_final > 0)) return HJG_EINVAL;
+    hjg_status s;
+    if (standardize && (s = hjg_mlp_fit_scaling(m, x, ldx, y, ldy, n))) return s;
+    const int64_t per = n >= batch ? n / batch : 1;   // minibatches per epoch
+    const int64_t steps = (int64_t)epochs * per;
+    const double ratio = (double)lr_final / (double)lr;
+    int64_t t = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t q = 0; q < per; ++q, ++t) {
+            const int64_t b0 = q * batch, b1 = std::min(n, b0 + batch);
+            const float rate = (float)((double)lr * std::pow(ratio, (double)t / (double)std::max<int64_t>(1, steps - 1)));
+            double loss = 0.0;
+            const bool last = q + 1 == per;
+            if ((s = hjg_mlp_train_step(m, x + b0 * ldx, ldx, y + b0 * ldy, ldy, b1 - b0, rate,
+                                        last && hist ? &loss : nullptr)))
+                return s;
+            if (last && hist) hist[ep] = loss;
+        }
+    }
     return HJG_OK;
 }
 

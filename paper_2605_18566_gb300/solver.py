@@ -379,25 +379,16 @@ class Surrogate:
             lr: float = 1e-3, lr_final: float = 1e-5, standardize: bool = True):
         """Adam over contiguous minibatches of (x, y) (shuffle the rows beforehand), with
         the learning rate decayed geometrically from lr to lr_final, after fitting the
-        feature standardisation to (x, y) when `standardize`; returns the mean loss (on
-        standardised targets) of each epoch."""
-        if standardize:
-            self.fit_scaling(x, y)
-        n = x.shape[0]
-        steps = epochs * max(1, n // batch)
-        hist, t = [], 0
-        for ep in range(epochs):
-            tot, cnt = 0.0, 0
-            for b0 in range(0, n - batch + 1 if n >= batch else 1, batch):
-                b1 = min(n, b0 + batch)
-                rate = lr * (lr_final / lr) ** (t / max(1, steps - 1))
-                last = b0 + batch > n - batch
-                l = self.train_step(x[b0:b1], y[b0:b1], rate, want_loss=last)
-                t += 1
-                if last:
-                    tot += l; cnt += 1
-            hist.append(tot / max(cnt, 1))
-        return hist
+        feature standardisation to (x, y) when `standardize` (hjg_mlp_fit: the loop runs in
+        the library); returns the loss (on standardised targets) of each epoch's last
+        minibatch."""
+        hist = np.zeros(epochs, dtype=np.float64)
+        st = self.lib.hjg_mlp_fit(self.m, C.c_void_p(x.data_ptr()), x.stride(0),
+                                  C.c_void_p(y.data_ptr()), y.stride(0), x.shape[0], epochs, batch,
+                                  lr, lr_final, 1 if standardize else 0, hist.ctypes.data_as(C.c_void_p))
+        if st:
+            raise HJGError(st, "hjg_mlp_fit")
+        return [float(h) for h in hist]
 
 
 class Batch:

@@ -93,3 +93,16 @@ def test_noalloc_refusals_before_any_device_work(lib):
     dyn, tgt, opt = _args(_lib, "rockets6", 6)
     opt.block_threads = 96
     assert call(dyn, tgt, opt) == _lib.HJG_EINVAL
+
+
+def test_mlp_refusals_before_any_device_work(lib):
+    """hjg_mlp_create rejects shapes outside its documented range, and hjg_mlp_fit refuses a
+    missing network or a non-positive epoch count, batch or learning rate before it launches
+    anything."""
+    L, _lib = lib
+    m = C.c_void_p()
+    assert L.hjg_mlp_create(0, 4, 256, 0, C.byref(m)) == _lib.HJG_EINVAL and not m.value
+    assert L.hjg_mlp_create(3, 4, 250, 0, C.byref(m)) == _lib.HJG_EINVAL and not m.value
+    hist = (C.c_double * 2)()
+    buf = C.c_void_p(8)   # never dereferenced: every call below fails its argument check
+    assert L.hjg_mlp_fit(None, buf, 3, buf, 4, 16, 2, 8, 1e-3, 1e-4, 0, hist) == _lib.HJG_EINVAL
