@@ -80,6 +80,22 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout that a SWIZZLE_128B
+// tensor-map copy of a 64-wide BF16 K chunk produces: one 128-byte row per M/N index (its
+// eight 16-byte pieces permuted by the row index mod 8), 8-row groups 1,024 bytes apart
+// (SBO), the leading offset unused; swizzle mode 2 in bits 61-63.  The tile must start on a
+// 1,024-byte boundary; the K steps of 16 within the chunk advance the start address by 32
+// bytes (base offset 0: the start stays within the first 128 bytes of the pattern).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
@@ -432,6 +448,22 @@ bool operand_map(CUtensorMap* tm, const __nv_bfloat16* base, int64_t rows, int64
     const cuuint32_t estr[2] = {1u, 1u};
     return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The same operand as 64-wide K boxes of box_rows rows in the 128-byte swizzled layout (one
+// copy per operand and K chunk; umma_desc_sw128 reads it).
+bool operand_map_sw128(CUtensorMap* tm, const __nv_bfloat16* base, int64_t rows, int64_t k_extent, int64_t ld,
+                       int box_rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || ((uintptr_t)base & 15) != 0 || (ld % 8) != 0 || rows < 1 || k_extent < 1 || box_rows > 256)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)k_extent, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -977,7 +1009,7 @@ constexpr uint32_t kFHalfBytes = kFRows * kFHalf * 2;   // 32 KB: one CTA's half
 constexpr int kWgSplits = 16;                    // phase B split of the batch
 constexpr int kWgStages = 4;                     // (32 splits at 2 stages, two CTAs per SM: 30 % slower)
 constexpr int kWgStage = (kTcM + kFW) * kTcK * 2;   // A 128 rows + B up to 256 rows, one 64-wide K chunk
-constexpr int kWgSmem = kWgStages * kWgStage;
+constexpr int kWgSmem = kWgStages * kWgStage + 1024;   // + slack to start the stages on 1,024 bytes
 
 // Offset (elements) of element (r, k) of an [R][K] operand in the canonical K-major
 // no-swizzle layout: core matrices of 8 rows x 8 K values (16 bytes a row), ordered
@@ -1395,7 +1427,7 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
     const int N = g.cols[l];
     const int64_t kbeg = (int64_t)split * g.kper, kend = min(g.K, kbeg + g.kper);
     const int nch = kend > kbeg ? (int)((kend - kbeg + kTcK - 1) / kTcK) : 0;
-    const uint32_t s0 = smem_u32(smem);
+    const uint32_t s0 = (smem_u32(smem) + 1023u) & ~1023u;   // the swizzle pattern repeats every 1,024 B
     const uint32_t stage_bytes = (uint32_t)((kTcM + N) * kTcK * 2);
     const CUtensorMap* tmA = &g.ta[l];
     const CUtensorMap* tmB = &g.tb[l];
@@ -1417,13 +1449,10 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = umma_idesc_bf16(kTcM, N);
-    auto chunk = [&](uint32_t st, int64_t k0, uint32_t bar) {
+    auto chunk = [&](uint32_t st, int64_t k0, uint32_t bar) {   // A rows then B rows, 128 B each
         mbar_expect_tx(bar, stage_bytes);
-#pragma unroll
-        for (int o = 0; o < kTcK / 8; ++o) {
-            tma_load_2d(st + (uint32_t)(o * kTcM * 16), tmA, (int)(k0 + 8 * o), m0, bar);
-            tma_load_2d(st + (uint32_t)(kTcM * kTcK * 2 + o * N * 16), tmB, (int)(k0 + 8 * o), 0, bar);
-        }
+        tma_load_2d(st, tmA, (int)k0, m0, bar);
+        tma_load_2d(st + (uint32_t)(kTcM * kTcK * 2), tmB, (int)k0, 0, bar);
     };
     bool ok = true;
     if (tid == 0 && nch > 0) {
@@ -1440,8 +1469,8 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
             const uint32_t sa = s0 + (uint32_t)(s * kWgStage), sb = sa + kTcM * kTcK * 2;
 #pragma unroll
             for (int ks = 0; ks < kTcK / 16; ++ks) {
-                const uint64_t da = umma_desc(sa + ks * (kTcM * 32), kTcM * 16, 128);
-                const uint64_t db = umma_desc(sb + (uint32_t)(ks * N * 32), (uint32_t)N * 16, 128);
+                const uint64_t da = umma_desc_sw128(sa + (uint32_t)(ks * 32));
+                const uint64_t db = umma_desc_sw128(sb + (uint32_t)(ks * 32));
                 const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -1470,9 +1499,12 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
     }
     ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const int rr = m0 + warp * 32 + lane;
+    // the 128 x N tile through shared memory (the stages are free: every product has
+    // completed), then out as consecutive 16-byte pieces of its contiguous rows
+    const int row = warp * 32 + lane;
     const bool have = ok && nch > 0;   // uniform over the CTA: the TMEM loads are warp-collective
-    float* dst = g.part + (int64_t)split * g.n_w + g.wp_off[l] + (int64_t)rr * N;
+    const int ldt = N + 4;             // padded row of the staging tile (floats)
+    float* stile = reinterpret_cast<float*>(smem + (s0 - smem_u32(smem)));
     for (int c0 = 0; c0 < N; c0 += 32) {
         float v[32];
         if (have) {
@@ -1481,14 +1513,19 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = 0.0f;
         }
-        if (rr < g.rows[l]) {
-            const int nv = min(32, N - c0);   // N is a multiple of 16
-            for (int q = 0; q < nv / 4; ++q)
-                reinterpret_cast<float4*>(dst + c0)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
+        const int nv = min(32, N - c0);   // N is a multiple of 16
+        for (int q = 0; q < nv / 4; ++q)
+            *reinterpret_cast<float4*>(stile + row * ldt + c0 + 4 * q) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    const int nrow = min(kTcM, g.rows[l] - m0);
+    float* dst = g.part + (int64_t)split * g.n_w + g.wp_off[l] + (int64_t)m0 * N;
+    for (int i = tid; i < nrow * N / 4; i += 128) {
+        const int r = (4 * i) / N, c = (4 * i) % N;
+        reinterpret_cast<float4*>(dst)[i] = *reinterpret_cast<const float4*>(stile + r * ldt + c);
+    }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFW));
 }
 
@@ -1681,8 +1718,8 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
     for (int l = 0; l < kLayers; ++l) {
         wa.rows[l] = m->rows[l]; wa.cols[l] = m->cols[l]; wa.wp_off[l] = m->wp_off[l];
         const __nv_bfloat16* opB = l == 0 ? m->Xt : m->Ht[l - 1];
-        if (!operand_map(&wa.ta[l], m->dZt4[l], m->rows[l], B, ldT, kTcM) ||
-            !operand_map(&wa.tb[l], opB, m->cols[l], B, ldT, m->cols[l]))
+        if (!operand_map_sw128(&wa.ta[l], m->dZt4[l], m->rows[l], B, ldT, kTcM) ||
+            !operand_map_sw128(&wa.tb[l], opB, m->cols[l], B, ldT, m->cols[l]))
             return HJG_ECUDA;
         for (int t = 0; t < (m->rows[l] + kTcM - 1) / kTcM; ++t) { wa.item_l[items] = l; wa.item_m[items] = t; ++items; }
     }
