@@ -51,7 +51,18 @@ struct GemmArgs {
     int kper;          // K values per split (a multiple of 64 when split)
 };
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// Logistic sigmoid and SiLU through one hardware tanh (sigma(z) = (1 + tanh(z / 2)) / 2):
+// one MUFU operation per element instead of an exponential and a reciprocal; its relative
+// error (about 2^-11) is below the BF16 rounding of the activations it produces.
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigmoid_t(float z) { return fmaf(0.5f, tanh_hw(0.5f * z), 0.5f); }
+__device__ __forceinline__ float silu_t(float z) { return z * sigmoid_t(z); }
+__device__ __forceinline__ float silu(float z) { return silu_t(z); }
+
 
 // ------------------------------------------------------------------------------------
 // The GEMM runs on the 5th-generation tensor cores (tcgen05, sm_100 family):
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, const __
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const float z = pre[8 * q + j];
-                        const float sg = 1.0f / (1.0f + __expf(-z));
+                        const float sg = sigmoid_t(z);
                         x[j] = x[j] * sg * (1.0f + z * (1.0f - sg));
                     }
                 }
@@ -644,7 +655,7 @@ __global__ void silu_backward_kernel(const float* __restrict__ dH, const float* 
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const float z = Z[e];
-    const float s = 1.0f / (1.0f + __expf(-z));
+    const float s = sigmoid_t(z);
     dZ[e] = __float2bfloat16(dH[e] * s * (1.0f + z * (1.0f - s)));
 }
 
@@ -990,7 +1001,8 @@ hjg_status mlp_loss_and_grads(hjg_mlp* m, const float* x, int64_t ldx, const flo
 //      (shared::cta -> the partner's shared::cluster, completion counted on the partner's
 //      mbarrier) hands it to the partner: activations never leave the pair between layers.
 //      The narrow output layer (N = out_pad) is computed by both CTAs.  The epilogue also
-//      writes what the weight gradients need (H_l^T, dZ_l^T, X^T) and the pre-activations Z_l;
+//      writes what the weight gradients need (H_l^T, dZ_l^T, X^T); the pre-activations Z_l
+//      stay in TMEM (the accumulator and Z_0..Z_2 fill its 512 columns) for the backward pass;
 //   B  the weight gradients dW_l = dZ_l^T H_{l-1} as 128 x N tiles (N = the layer's input
 //      width, up to 256) over a split of the batch (split-K), TMA-fed four-stage pipeline;
 //   C  the fixed-order sum of the splits, the bias gradients (column sums of dZ_l), Adam and
@@ -1006,6 +1018,7 @@ constexpr int kFStage = 4 * kFPass * kFRows * 2;  // 16 KB: one pass of the four
 constexpr int kFBias = kLayers * kFW * 4;         // 4 KB: the biases of the four layers
 constexpr int kFSmemA = 2 * kFBuf + kFBufW + kFStage + kFBias;
 constexpr uint32_t kFHalfBytes = kFRows * kFHalf * 2;   // 32 KB: one CTA's half of a 256-wide layer input
+constexpr int kFTmemCols = 4 * kFHalf;   // TMEM: the accumulator, then Z_0, Z_1, Z_2 (128 columns each)
 constexpr int kWgSplits = 16;                    // phase B split of the batch
 constexpr int kWgStages = 4;                     // (32 splits at 2 stages, two CTAs per SM: 30 % slower)
 constexpr int kWgStage = (kTcM + kFW) * kTcK * 2;   // A 128 rows + B up to 256 rows, one 64-wide K chunk
@@ -1096,13 +1109,23 @@ struct FusedArgs {
     const float* p;                                  // FP32 parameters (biases read from here)
     int64_t b_off[kLayers], wp_off[kLayers];
     const __nv_bfloat16* wc; const __nv_bfloat16* wct;
-    float* Z[kLayers - 1];                           // hidden pre-activations [B][256]
     __nv_bfloat16* Xt; __nv_bfloat16* Ht[kLayers - 1]; __nv_bfloat16* dZt[kLayers];
     double* lpart;                                   // loss / B per CTA
     int* err;
 };
 
-__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// 16 consecutive FP32 columns into this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const float* x) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+            :: "r"(addr + (uint32_t)(8 * q)), "r"(__float_as_uint(x[8 * q])), "r"(__float_as_uint(x[8 * q + 1])),
+               "r"(__float_as_uint(x[8 * q + 2])), "r"(__float_as_uint(x[8 * q + 3])),
+               "r"(__float_as_uint(x[8 * q + 4])), "r"(__float_as_uint(x[8 * q + 5])),
+               "r"(__float_as_uint(x[8 * q + 6])), "r"(__float_as_uint(x[8 * q + 7]))
+            : "memory");
+}
 
 // 16 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* x) {
@@ -1158,7 +1181,6 @@ __device__ __forceinline__ const __nv_bfloat16* fused_w(const FusedArgs& a, int 
     default: return a.wct + a.wp_off[1] + half;
     }
 }
-__device__ __forceinline__ float* fused_z(const FusedArgs& a, int l) { return l == 0 ? a.Z[0] : l == 1 ? a.Z[1] : a.Z[2]; }
 __device__ __forceinline__ __nv_bfloat16* fused_t(const FusedArgs& a, bool fwd, int l) {
     if (fwd) return l == 0 ? a.Ht[0] : l == 1 ? a.Ht[1] : a.Ht[2];
     return l == 0 ? a.dZt[0] : l == 1 ? a.dZt[1] : a.dZt[2];
@@ -1187,7 +1209,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
     const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_m), bx = smem_u32(&bar_x);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(kFHalf));
+                     :: "r"(smem_u32(&tmem_base)), "r"(kFTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -1250,6 +1272,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         const bool send = t == 0 || t == 1 || t == 2 || t == 4 || t == 5;
         const uint32_t s_in = sbuf + (uint32_t)((t & 1) * kFBuf);
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(smem + ((t + 1) & 1) * kFBuf);
+        // the output layer's standardised targets of this thread's row and kFPass columns,
+        // loaded while thread 0 waits for the product
+        float ystd[kFPass];
+        if (t == 3) {
+#pragma unroll
+            for (int j = 0; j < kFPass; ++j) {
+                const int col = cg * kFPass + j;
+                ystd[j] = valid && col < a.n_out ? (a.y[rg * a.ldy + col] - a.oscal[col]) / a.oscal[op + col] : 0.0f;
+            }
+        }
         // thread 0: the product of step t once its weights (and the partner's half of its
         // input) have landed, and its completion; the other threads wait at the barrier
         if (tid == 0 && s_ok) {
@@ -1282,57 +1314,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         // staging tile of this thread: column j of its group, its row
         __nv_bfloat16* my_stg = stg + cg * kFPass * kFRows + row;
         if (ok && t != 3) {
-            // hidden layer t (t < 3): z = acc + b, Z_t, h = silu(z) -> next input, H_t^T;
+            // hidden layer t (t < 3): z = acc + b -> Z_t (TMEM), h = silu(z) -> next input, H_t^T;
             // backward (t = 4, 5, 6): dZ_l = (dZ_{l+1} W_{l+1}) silu'(Z_l) for the hidden layer
             // l = 6 - t (2, 1, 0) -> next input (l > 0), dZ_l^T; 32 columns per thread
             const bool fwd = t < 3;
             const int l = fwd ? t : 6 - t;
             __nv_bfloat16* tdst = fused_t(a, fwd, l);
-            float* zl = fused_z(a, l) + rg * kFW + hcol + cg * 32;   // this thread's 32 pre-activations
+            const uint32_t tz = tl + (uint32_t)(kFHalf * (l + 1) + cg * 32);   // Z_l, this thread's 32 columns
             float acc[32];
-            float zin[kFPass];
-            if (!fwd) {   // pass 0's pre-activations, loaded ahead of the TMEM read
-#pragma unroll
-                for (int g = 0; g < kFPass / 4; ++g) {
-                    const float4 zz = valid ? reinterpret_cast<const float4*>(zl)[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    zin[4 * g] = zz.x; zin[4 * g + 1] = zz.y; zin[4 * g + 2] = zz.z; zin[4 * g + 3] = zz.w;
-                }
-            }
+            float zin[32];
             tmem_ld32(tl + (uint32_t)(cg * 32), acc);
+            if (!fwd) tmem_ld32(tz, zin);
 #pragma unroll
             for (int pass = 0; pass < 32 / kFPass; ++pass) {
                 const int c0 = hcol + cg * 32 + kFPass * pass;   // layer column
                 float* v = acc + kFPass * pass;
-                float znext[kFPass];
-                if (!fwd && pass + 1 < 32 / kFPass) {   // the next pass's pre-activations
-#pragma unroll
-                    for (int g = 0; g < kFPass / 4; ++g) {
-                        const float4 zz = valid ? reinterpret_cast<const float4*>(zl + kFPass * (pass + 1))[g]
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                        znext[4 * g] = zz.x; znext[4 * g + 1] = zz.y; znext[4 * g + 2] = zz.z; znext[4 * g + 3] = zz.w;
-                    }
-                }
                 if (fwd) {
                     const float* bias = s_bias + t * kFW + c0;
 #pragma unroll
                     for (int j = 0; j < kFPass; ++j) v[j] += bias[j];
-                    if (valid) {
-                        float4* zr = reinterpret_cast<float4*>(zl + kFPass * pass);
+                    tmem_st16(tz + (uint32_t)(kFPass * pass), v);   // Z_t stays on the SM for the backward pass
 #pragma unroll
-                        for (int g = 0; g < kFPass / 4; ++g)
-                            zr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < kFPass; ++j) v[j] = valid ? silu_fast(v[j]) : 0.0f;
+                    for (int j = 0; j < kFPass; ++j) v[j] = valid ? silu_t(v[j]) : 0.0f;
                 } else {
 #pragma unroll
                     for (int j = 0; j < kFPass; ++j) {
-                        const float z = zin[j];
-                        const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
+                        const float z = zin[kFPass * pass + j];
+                        const float sg = sigmoid_t(z);
                         v[j] = valid ? v[j] * sg * (1.0f + z * (1.0f - sg)) : 0.0f;
                     }
-#pragma unroll
-                    for (int j = 0; j < kFPass; ++j) zin[j] = znext[j];
                 }
                 if (fwd || l > 0) {
 #pragma unroll
@@ -1344,6 +1354,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
                 store_transposed(stg, tdst, a.ldT, r0, 32, hcol + kFPass * pass, kFW, tid);
                 __syncthreads();
             }
+            if (fwd) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         } else if (ok) {
             // output layer (both CTAs): o = acc + b, dO against the standardised targets ->
             // next input; the loss and dO^T from rank 0; each column group covers kFPass of
@@ -1359,7 +1370,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
                     float g = 0.0f;
                     if (valid && col < a.n_out) {
                         const float o = v[j] + s_bias[3 * kFW + col];
-                        const float d = o - (a.y[rg * a.ldy + col] - a.oscal[col]) / a.oscal[op + col];
+                        const float d = o - ystd[j];
                         const float w = col == 0 ? 1.0f : winv;
                         if (rank == 0) loss += w * d * d;
                         g = 2.0f * w * d / (float)a.B;
@@ -1400,7 +1411,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
     // neither CTA leaves while the partner may still copy into its shared memory: every copy
     // was consumed by the receiver's wait before the receiver reached this barrier
     cluster_sync();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFHalf));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFTmemCols));
 }
 
 // Phase B: split-K weight gradients.  Item i = (layer, 128-row tile of dW_l), split s of the
@@ -1530,9 +1541,9 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
 }
 
 // Phase C: gradients and (with lr > 0) the Adam step and the BF16 weight copies.  Blocks
-// [0, nwb): one thread per weight, the splits added in order; blocks [nwb, ...): one block per
-// bias, the column sum of dZ_l over the batch (eight warps over the rows, lanes within a
-// warp, then fixed-order combines).
+// [0, nwb): one 8 x 32 weight tile each, the splits added in order; blocks [nwb, ...): one
+// block per bias, the column sum of dZ_l over the batch (eight warps over the rows, lanes
+// within a warp, then fixed-order combines).
 struct ApplyArgs {
     int64_t w_off[kLayers], b_off[kLayers], wp_off[kLayers], n_w;
     int rows[kLayers], cols[kLayers];
@@ -1542,6 +1553,7 @@ struct ApplyArgs {
     __nv_bfloat16* pb; __nv_bfloat16* pbT; __nv_bfloat16* wc; __nv_bfloat16* wct;
     float lr, b1, b2, eps, c1, c2;
     int nwb, n_bias;
+    int tile_off[kLayers + 1];   // first block of each layer's 8 x 32 weight tiles
 };
 
 __device__ __forceinline__ float adam_update(const ApplyArgs& a, int64_t pi, float gg) {
@@ -1557,22 +1569,46 @@ __device__ __forceinline__ float adam_update(const ApplyArgs& a, int64_t pi, flo
 
 __global__ void __launch_bounds__(256) mlp_apply_kernel(const ApplyArgs a) {
     if ((int)blockIdx.x < a.nwb) {
-        const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
-        if (e >= a.n_w) return;
+        // one block per 8 x 32 tile of one layer's weights, one weight per thread: the split
+        // sums, the gradient and Adam (row-major, coalesced), then the BF16 copies through a
+        // shared tile so that the transposed and canonical copies go out as 16-byte or longer
+        // runs
+        __shared__ __nv_bfloat16 sh[8][34];
         int l = 0;
-        while (l + 1 < kLayers && e >= a.wp_off[l + 1]) ++l;
-        const int64_t k = e - a.wp_off[l];
+        while (l + 1 < kLayers && (int)blockIdx.x >= a.tile_off[l + 1]) ++l;
         const int R = a.rows[l], Cc = a.cols[l];
-        const int r = (int)(k / Cc), c = (int)(k % Cc);
-        float s = 0.0f;
-        for (int t = 0; t < a.splits; ++t) s += a.part[(int64_t)t * a.n_w + e];
-        const int64_t pi = a.w_off[l] + k;
-        a.g[pi] = s;
-        if (a.lr > 0.0f) {
-            const __nv_bfloat16 hb = __float2bfloat16(adam_update(a, pi, s));
-            a.pbT[a.w_off[l] + (int64_t)c * R + r] = hb;
-            a.wc[a.wp_off[l] + canon_w_idx(r, c, R, Cc)] = hb;
-            a.wct[a.wp_off[l] + canon_w_idx(c, r, Cc, R)] = hb;
+        const int tcn = (Cc + 31) / 32, t = (int)blockIdx.x - a.tile_off[l];
+        const int r0 = (t / tcn) * 8, c0 = (t % tcn) * 32;
+        const int tid = threadIdx.x;
+        {
+            const int r = tid >> 5, c = tid & 31;
+            if (r0 + r < R && c0 + c < Cc) {
+                const int64_t k = (int64_t)(r0 + r) * Cc + c0 + c;
+                const int64_t e = a.wp_off[l] + k;
+                float part[kWgSplits];
+#pragma unroll
+                for (int q = 0; q < kWgSplits; ++q) part[q] = a.part[(int64_t)q * a.n_w + e];
+                float sum = 0.0f;
+#pragma unroll
+                for (int q = 0; q < kWgSplits; ++q) sum += part[q];
+                const int64_t pi = a.w_off[l] + k;
+                a.g[pi] = sum;
+                if (a.lr > 0.0f) sh[r][c] = __float2bfloat16(adam_update(a, pi, sum));
+            }
+        }
+        if (!(a.lr > 0.0f)) return;   // uniform over the block
+        __syncthreads();
+        {   // W^T row-major: 8 consecutive rows of W per column
+            const int c = tid >> 3, r = tid & 7;
+            if (r0 + r < R && c0 + c < Cc) a.pbT[a.w_off[l] + (int64_t)(c0 + c) * R + r0 + r] = sh[r][c];
+        }
+        {   // canonical W: 8 columns of the 8 rows
+            const int c = 8 * (tid >> 6) + (tid & 7), r = (tid >> 3) & 7;
+            if (r0 + r < R && c0 + c < Cc) a.wc[a.wp_off[l] + canon_w_idx(r0 + r, c0 + c, R, Cc)] = sh[r][c];
+        }
+        {   // canonical W^T: the 8 rows of W for consecutive columns
+            const int c = tid >> 3, r = tid & 7;
+            if (r0 + r < R && c0 + c < Cc) a.wct[a.wp_off[l] + canon_w_idx(c0 + c, r0 + r, Cc, R)] = sh[r][c];
         }
         return;
     }
@@ -1639,7 +1675,10 @@ ApplyArgs apply_args(const hjg_mlp* m) {
     a.part = m->fpart; a.splits = kWgSplits;
     a.p = m->p; a.g = m->g; a.m1 = m->m1; a.m2 = m->m2;
     a.pb = m->pb; a.pbT = m->pbT; a.wc = m->wc; a.wct = m->wct;
-    a.nwb = (int)((m->n_w + 255) / 256);
+    a.tile_off[0] = 0;
+    for (int l = 0; l < kLayers; ++l)
+        a.tile_off[l + 1] = a.tile_off[l] + ((m->rows[l] + 7) / 8) * ((m->cols[l] + 31) / 32);
+    a.nwb = a.tile_off[kLayers];
     int nb = 0;
     for (int l = 0; l < kLayers; ++l) nb += m->rows[l];
     a.n_bias = nb;
@@ -1706,7 +1745,7 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
     fa.iscal = m->iscal; fa.oscal = m->oscal; fa.p = m->p;
     for (int l = 0; l < kLayers; ++l) { fa.b_off[l] = m->b_off[l]; fa.wp_off[l] = m->wp_off[l]; fa.dZt[l] = m->dZt4[l]; }
     fa.wc = m->wc; fa.wct = m->wct;
-    for (int l = 0; l + 1 < kLayers; ++l) { fa.Z[l] = m->Z[l]; fa.Ht[l] = m->Ht[l]; }
+    for (int l = 0; l + 1 < kLayers; ++l) fa.Ht[l] = m->Ht[l];
     fa.Xt = m->Xt; fa.lpart = m->flpart; fa.err = g_tc_err;
     const int ntile = (int)((B + kFRows - 1) / kFRows);
     mlp_fused_fwdbwd_kernel<<<2 * ntile, kFThreads, kFSmemA, st>>>(fa);   // clusters of two
