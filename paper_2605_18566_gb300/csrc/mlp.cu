@@ -1061,12 +1061,14 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// D (TMEM) = A (128 x K, canonical at a) * B^T (rowsB x K, canonical at b), K a multiple of 16.
-__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, int rowsB, int K, uint32_t idesc) {
-    for (int ks = 0; ks < K / 16; ++ks) {
+// D (TMEM) += A (128 x K, canonical at a) * B^T (rowsB x K, canonical at b) over the K steps
+// [ks0, ks0 + nks) of 16 K values; the first step overwrites the accumulator when `first`.
+__device__ __forceinline__ void mma_steps(uint32_t tmem, uint32_t a, uint32_t b, int rowsB, int ks0, int nks,
+                                          bool first, uint32_t idesc) {
+    for (int ks = ks0; ks < ks0 + nks; ++ks) {
         const uint64_t da = umma_desc(a + (uint32_t)(ks * kFRows * 32), kFRows * 16, 128);
         const uint64_t db = umma_desc(b + (uint32_t)(ks * rowsB * 32), (uint32_t)rowsB * 16, 128);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
+        const uint32_t acc = first && ks == ks0 ? 0u : 1u;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
@@ -1240,12 +1242,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         s_bias[e] = i < (l == kLayers - 1 ? op : kFW) ? a.p[a.b_off[l] + i] : 0.0f;
     }
     __nv_bfloat16* buf0 = reinterpret_cast<__nv_bfloat16*>(smem);
-    for (int e = tid; e < kFRows * ip; e += kFThreads) {
-        const int r = e / ip, j = e % ip;
-        const int64_t b = r0 + r;
-        float xv = 0.0f;
-        if (b < a.B && j < a.n_in) xv = (a.x[b * a.ldx + j] - a.iscal[j]) * a.iscal[ip + j];
-        buf0[canon_idx(r, j, kFRows)] = __float2bfloat16(xv);
+    {   // all of a thread's loads issued before any store
+        constexpr int kPer = kFRows * 64 / kFThreads;
+        float xv[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int e = tid + k * kFThreads, r = e / ip, j = e % ip;
+            const int64_t b = r0 + r;
+            xv[k] = e < kFRows * ip && b < a.B && j < a.n_in ? a.x[b * a.ldx + j] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int e = tid + k * kFThreads, r = e / ip, j = e % ip;
+            if (e < kFRows * ip)
+                buf0[canon_idx(r, j, kFRows)] =
+                    __float2bfloat16(j < a.n_in && r0 + r < a.B ? (xv[k] - a.iscal[j]) * a.iscal[ip + j] : 0.0f);
+        }
     }
     __syncthreads();
     if (rank == 0) {
@@ -1272,14 +1284,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         const bool send = t == 0 || t == 1 || t == 2 || t == 4 || t == 5;
         const uint32_t s_in = sbuf + (uint32_t)((t & 1) * kFBuf);
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(smem + ((t + 1) & 1) * kFBuf);
-        // the output layer's standardised targets of this thread's row and kFPass columns,
-        // loaded while thread 0 waits for the product
-        float ystd[kFPass];
-        if (t == 3) {
+        // the output layer's standardised targets of the tile, loaded row by row (coalesced)
+        // by warps 1-15 while thread 0 waits for the product, into the upper half of buffer 0:
+        // nothing reads or writes it during step 3 (its inputs were consumed by product 2, dO
+        // goes to the lower half, and the partner's next copy into it comes after step 3)
+        float* ys = reinterpret_cast<float*>(smem + kFBuf / 2);
+        if (t == 3 && warp > 0) {   // all of a thread's loads issued before any store
+            constexpr int kPer = (kFRows * 64 + kFThreads - 33) / (kFThreads - 32);
+            float yv[kPer];
 #pragma unroll
-            for (int j = 0; j < kFPass; ++j) {
-                const int col = cg * kFPass + j;
-                ystd[j] = valid && col < a.n_out ? (a.y[rg * a.ldy + col] - a.oscal[col]) / a.oscal[op + col] : 0.0f;
+            for (int k = 0; k < kPer; ++k) {
+                const int e = tid - 32 + k * (kFThreads - 32);
+                const int r = e / op, col = e % op;
+                const int64_t b = r0 + r;
+                yv[k] = e < kFRows * op && b < a.B && col < a.n_out ? a.y[b * a.ldy + col] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int e = tid - 32 + k * (kFThreads - 32);
+                const int col = e % op;
+                if (e < kFRows * op) ys[e] = col < a.n_out ? (yv[k] - a.oscal[col]) / a.oscal[op + col] : 0.0f;
             }
         }
         // thread 0: the product of step t once its weights (and the partner's half of its
@@ -1287,19 +1311,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         if (tid == 0 && s_ok) {
             bool ok = mbar_wait(bw, ph_w, a.err);
             if (ok) { w_pending = false; ph_w ^= 1u; }
-            if (ok && recv) {
-                ok = mbar_wait(bx, ph_x, a.err);
-                if (ok) {
-                    ph_x ^= 1u;
-                    if (t != 6) mbar_expect_tx(bx, kFHalfBytes);   // the next reception
-                }
-            }
             if (ok) {
+                const int n = fused_n(a, t), kst = fused_k(a, t) / 16;
+                const uint32_t idesc = umma_idesc_bf16(kFRows, n);
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                mma_layer(tmem, s_in, sW, fused_n(a, t), fused_k(a, t), umma_idesc_bf16(kFRows, fused_n(a, t)));
-                mma_commit(bm);
-                ok = mbar_wait(bm, ph_m, a.err);
+                if (recv) {
+                    // this CTA's half of the input (its own epilogue wrote it) while the
+                    // partner's half is still on its way, then the partner's half
+                    const int kh = kFHalf / 16;
+                    mma_steps(tmem, s_in, sW, n, (int)rank * kh, kh, true, idesc);
+                    ok = mbar_wait(bx, ph_x, a.err);
+                    if (ok) {
+                        ph_x ^= 1u;
+                        if (t != 6) mbar_expect_tx(bx, kFHalfBytes);   // the next reception
+                        mma_steps(tmem, s_in, sW, n, (int)peer * kh, kh, false, idesc);
+                    }
+                } else {
+                    mma_steps(tmem, s_in, sW, n, 0, kst, true, idesc);
+                }
+                mma_commit(bm);   // also after a failed wait: the issued products must finish
+                const bool done = mbar_wait(bm, ph_m, a.err);
                 ph_m ^= 1u;
+                ok = ok && done;
             }
             if (!ok) s_ok = 0;
         }
@@ -1370,7 +1403,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
                     float g = 0.0f;
                     if (valid && col < a.n_out) {
                         const float o = v[j] + s_bias[3 * kFW + col];
-                        const float d = o - ystd[j];
+                        const float d = o - ys[row * op + col];
                         const float w = col == 0 ? 1.0f : winv;
                         if (rank == 0) loss += w * d * d;
                         g = 2.0f * w * d / (float)a.B;
