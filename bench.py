@@ -605,117 +605,114 @@ def run_games(args):
 
 
 def surrogate_study(points_fn, label):
-    """One study of the learned part on the 45-D game: tuples (x, v - l(x), Dv - Dl(x)) from
-    the plain sweeps of 262,144 states drawn by points_fn (sweeps 23-30 of 30 at N = 131,072:
-    2,097,152 tuples), GPU training of the 45 -> 256^3 -> 46 BF16 network on them (it learns
-    the correction the Picard iteration makes to its initial iterate l, Dl), and, on 1,024
-    held-out states, the value error against a tilted N = 2^20 reference for the plain form,
-    the tilted form without the network (with and without the control variate), and the
-    surrogate-assisted form (warm start l + correction, then tilt, with and without the
-    control variate) over N = 4,096 ... 262,144, 12 sweeps each.  `four_x` compares each
-    plain run with the assisted run at a quarter of its point-samples (success: the assisted
-    run reaches the plain run's residual at no larger value error), and `vs_tilt` each
-    assisted run with the same sweep without the network at the same N."""
+    """One study of the learned part on the 45-D game.  Tuples: the invariant-frame features
+    (hjg_frame_features, 56 inputs) of 1,048,576 states drawn by points_fn and the correction
+    (v - l, Dv - Dl) that 12 tilted control-variate sweeps at N = 16,384 make to the initial
+    iterate, in the frame and averaged over the last four sweeps (hjg_frame_targets, 43
+    outputs).  GPU training of the 56 -> 256^3 -> 43 BF16 network on them.  Then, on 1,024
+    held-out states, the value error against a tilted N = 2^20, 12-sweep reference of: the
+    plain form (Algorithm 1 as printed, 12 sweeps), the tilted control-variate sweep started
+    from l, and the same sweep warm-started from the network (hjg_warm_start_frame, position
+    rows only), for K = 1, 2, 3, 6, 12 sweeps and N = 4,096, 16,384, 65,536.
+    `sweeps_to_match`: per N, the fewest sweeps after which the assisted form is at least as
+    close as the sweep from l after 12."""
     import torch
     from paper_2605_18566_gb300 import Solver, Surrogate
     w = hjg_inputs.ROCKETS45
+    k_data, n_data, chunk, m_train = 12, 16384, 262144, 1 << 20
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x = torch.from_numpy(points_fn(w.M, 0)).cuda()
-    s = Solver(w.game, w.nu, w.T, w.N, w.K, radius=w.radius)
-    s.set_points(x)
-    s.autotune(max_states=4 * SMS * 2)
-    s.picard_sweep(w.K - 8, residuals=False)
     X, Y = [], []
-    resid = []
-    for _ in range(8):
-        r, _ = s.picard_sweep(1)
-        resid.append(float(r[0]))
-        X.append(x)
-        Y.append(s.state_delta())
-    s.close()
+    for c in range(m_train // chunk):
+        x = torch.from_numpy(points_fn(chunk, 100 + c)).cuda()
+        s = Solver(w.game, w.nu, w.T, n_data, k_data, radius=w.radius, tilt=True, cv=True)
+        s.set_points(x)
+        X.append(s.frame_features())
+        s.picard_sweep(k_data - 4, residuals=False)
+        acc = None
+        for _ in range(4):
+            s.picard_sweep(1, residuals=False)
+            t = s.frame_targets()
+            acc = t if acc is None else acc + t
+        Y.append(acc / 4)
+        s.close()
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     X = torch.cat(X); Y = torch.cat(Y)
     perm = torch.from_numpy(np.random.default_rng(0).permutation(X.shape[0])).cuda()
     X = X[perm].contiguous(); Y = Y[perm].contiguous()
-    sur = Surrogate(45, 46, 256, seed=0)
-    epochs, batch = 8, 8192
+    sur = Surrogate(56, 43, 256, seed=0)
+    epochs, batch = 30, 8192
     torch.cuda.synchronize(); t1 = time.perf_counter()
     hist = sur.fit(X, Y, epochs=epochs, batch=batch, lr=2e-3, lr_final=1e-4)
     torch.cuda.synchronize(); t_train = time.perf_counter() - t1
     xte = torch.from_numpy(points_fn(1024, 1)).cuda()
-    pred = sur.forward(xte)
+    probe = Solver(w.game, w.nu, w.T, 1024, 1, radius=w.radius)
+    probe.set_points(xte)
+    pred = sur.forward(probe.frame_features())
+    probe.close()
+    sur.close()
 
-    def solve(N, K, tilt=False, warm=False, seed=11, cv=False):
+    def solve(N, K, tilt=True, cv=True, warm=False, seed=11):
         so = Solver(w.game, w.nu, w.T, N, max(K, 1), radius=w.radius, tilt=tilt, seed=seed, cv=cv)
         so.set_points(xte)
         if warm:
-            so.warm_start_delta(pred)
+            so.warm_start_frame(pred, positions_only=True)
         r = so.picard_sweep(K)[0] if K > 0 else [float("nan")]
         st = so.get_state()
         so.close()
         return st["v"].cpu().numpy(), float(r[-1])
 
-    vref, rref = solve(1 << 20, 12, tilt=True, seed=7)
+    vref, rref = solve(1 << 20, 12, cv=False, seed=7)
     rms = lambda v: float(np.sqrt(np.mean((v - vref) ** 2)))
-    rows = []
-    K = 12
-    for N in (4096, 16384, 65536, 262144):
-        for mode in ("plain", "tilt", "tilt+cv", "surrogate+tilt", "surrogate+tilt+cv"):
-            v, r = solve(N, K, tilt=mode != "plain", warm=mode.startswith("surrogate"), cv=mode.endswith("+cv"))
-            rows.append({"mode": mode, "N": N, "K": K, "point_samples_per_state": N * K,
-                         "rms_value_error": rms(v), "final_residual": r})
-    sur.close()
-    four_x, vs_tilt = [], []
-    for p in rows:
-        if p["mode"] == "plain":
-            for a in rows:
-                if a["mode"].startswith("surrogate") and a["N"] * 4 == p["N"]:
-                    four_x.append({"plain_N": p["N"], "assisted": a["mode"], "assisted_N": a["N"],
-                                   "met": bool(a["final_residual"] <= p["final_residual"]
-                                               and a["rms_value_error"] <= p["rms_value_error"])})
-        if p["mode"] in ("tilt", "tilt+cv"):   # the same sweep without the network
-            for a in rows:
-                if (a["mode"].startswith("surrogate") and a["N"] == p["N"]
-                        and a["mode"].endswith("+cv") == p["mode"].endswith("+cv")):
-                    vs_tilt.append({"N": p["N"], "assisted": a["mode"], "without_network": p["mode"],
-                                    "tilt_error": p["rms_value_error"],
-                                    "assisted_error": a["rms_value_error"],
-                                    "better": bool(a["rms_value_error"] <= p["rms_value_error"])})
+    rows, match = [], []
+    for N in (4096, 16384, 65536):
+        v, r = solve(N, 12, tilt=False, cv=False)
+        rows.append({"mode": "plain", "N": N, "K": 12, "rms_value_error": rms(v), "final_residual": r})
+        for K in (1, 2, 3, 6, 12):
+            for mode in ("tilt+cv", "surrogate+tilt+cv"):
+                v, r = solve(N, K, warm=mode.startswith("surrogate"))
+                rows.append({"mode": mode, "N": N, "K": K, "rms_value_error": rms(v), "final_residual": r})
+        e12 = next(q["rms_value_error"] for q in rows if q["mode"] == "tilt+cv" and q["N"] == N and q["K"] == 12)
+        ks = [q["K"] for q in rows if q["mode"] == "surrogate+tilt+cv" and q["N"] == N
+              and q["rms_value_error"] <= e12]
+        match.append({"N": N, "from_l_12_sweeps_error": e12, "assisted_sweeps": min(ks) if ks else None})
     return {"label": label, "tuple_generation_s": t_data, "train_s": t_train,
             "tuples": int(X.shape[0]), "epochs": epochs, "batch": batch,
-            "loss": [hist[0], hist[-1]], "data_residuals": resid,
+            "loss": [hist[0], hist[-1]],
             "reference": {"N": 1 << 20, "K": 12, "tilt": True, "final_residual": rref},
             "initial_iterate_rms_value_error": rms(solve(4096, 0)[0]),
             "surrogate_alone_rms_value_error": rms(solve(4096, 0, warm=True)[0]),
-            "study": rows, "four_x": four_x, "vs_tilt": vs_tilt}
+            "study": rows, "sweeps_to_match": match}
 
 
 def run_surrogate(args):
-    """The learned part on the 45-D game, on two state distributions: the workload's own
-    (positions N(0, 2^2): most states start near a capture) and the paper's wider one
-    (positions uniform in [-100, 100]); the line's value is the training throughput of the
-    first."""
-    w = hjg_inputs.ROCKETS45
-    main = surrogate_study(lambda M, seed: hjg_inputs.rockets45_points(M, seed), "positions N(0, 2^2)")
-    wide = surrogate_study(lambda M, seed: hjg_inputs.rockets45_wide_points(M, seed),
+    """The learned part on the 45-D game, on two state distributions: the paper's wide one
+    (positions uniform in [-100, 100]) and the workload's own (positions N(0, 2^2): most
+    states start near a capture and no form converges there); the line's value is the
+    training throughput of the first."""
+    main = surrogate_study(lambda M, seed: hjg_inputs.rockets45_wide_points(M, seed),
                            "positions uniform in [-100, 100]")
-    flops_per_tuple = 6 * (48 * 256 + 256 * 256 * 2 + 256 * 48)   # forward + backward GEMMs
+    narrow = surrogate_study(lambda M, seed: hjg_inputs.rockets45_points(M, seed), "positions N(0, 2^2)")
+    # per tuple: forward (4 layers), backward data gradients (3 products) and weight
+    # gradients (4 layers) of the 56 -> 256^3 -> 43 network at its padded widths 64 and 48
+    fwd = 64 * 256 + 2 * 256 * 256 + 256 * 48
+    flops_per_tuple = 2 * (fwd + (48 * 256 + 2 * 256 * 256) + fwd)
     tuples = main["tuples"] * main["epochs"]
     tflops = tuples * flops_per_tuple / main["train_s"] / 1e12
     tensor_peak = load_peaks().get("bf16_tflops", 1906.5)
-    return {"metric": "surrogate training tuples/s and error vs point-samples (45-D game)",
+    return {"metric": "surrogate training tuples/s and error vs sweeps (45-D game)",
             "value": tuples / main["train_s"], "unit": "tuples/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (tuples from the plain sweeps)",
-            "config": {"workload": "rockets45_gauss sweeps 23-30 -> 2,097,152 tuples; MLP 45-256-256-256-46",
+            "dtype": "bf16 (FP32 accumulate)",
+            "data": "synthetic (tuples from tilted control-variate sweeps)",
+            "config": {"workload": "45-D game, 1,048,576 states uniform in [-100, 100], 12 sweeps at "
+                                   "N = 16,384 -> 1,048,576 frame tuples; MLP 56-256-256-256-43",
                        "epochs": main["epochs"], "batch": main["batch"]},
-            "rockets45_point_samples_per_s": w.M * w.N * w.K / main["tuple_generation_s"],
             "mlp_tflops": tflops,
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": tensor_peak, "unit": "TFLOP/s",
                          "frac": tflops / tensor_peak,
-                         "note": "whole training step (GEMMs + element-wise + Adam) at batch 8192"},
-            "studies": [main, wide]}
+                         "note": "whole training step (products + element-wise + Adam) at batch 8192"},
+            "studies": [main, narrow]}
 
 
 def main():

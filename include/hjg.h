@@ -238,12 +238,18 @@ hjg_status hjg_get_state_delta(hjg_ctx *ctx, float *out, int64_t ldo);
  *                       iterate v = l + dv, Dv = Dl + the correction mapped back by the chain
  *                       rule (the evader's position part from translation invariance, its
  *                       heading part from the frame's rotation), c = Gamma(Dv) (Eq.
- *                       coeff_frozen).
+ *                       coeff_frozen).  With positions_only != 0 only the position rows of
+ *                       Dv take the correction and the 15 heading rows keep Dl's (zero:
+ *                       l does not depend on the headings).  The sweep sees the iterate only
+ *                       through c, and the game's Hamiltonian subtracts |p_theta| for every
+ *                       pursuer heading, so small errors of a network in those rows lower H
+ *                       and can flip the sign of c where Dl gets it right; measured on the
+ *                       paper's wide 45-D domain, positions_only is the form that helps.
  * All arrays are DEVICE memory; each call synchronises the context's stream.
  * EUNSUPPORTED for another game, unequal pursuer speeds or several horizons. */
 hjg_status hjg_frame_features(hjg_ctx *ctx, float *out, int64_t ldo);
 hjg_status hjg_frame_targets(hjg_ctx *ctx, float *out, int64_t ldo);
-hjg_status hjg_warm_start_frame(hjg_ctx *ctx, const float *pred, int64_t ldp);
+hjg_status hjg_warm_start_frame(hjg_ctx *ctx, const float *pred, int64_t ldp, int positions_only);
 
 /* Per-sweep parts of the residual of the last hjg_picard_sweep call over the loaded
  * states: out [n_sweeps][3] = (sum (v^(k+1)-v^(k))^2, sum (v^(k))^2, max |v^(k+1)-v^(k)|),

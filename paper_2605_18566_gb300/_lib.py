@@ -72,7 +72,7 @@ _SIGS = {
     "hjg_get_state_delta": (C.c_int, [_vp, _vp, C.c_int64]),
     "hjg_frame_features": (C.c_int, [_vp, _vp, C.c_int64]),
     "hjg_frame_targets": (C.c_int, [_vp, _vp, C.c_int64]),
-    "hjg_warm_start_frame": (C.c_int, [_vp, _vp, C.c_int64]),
+    "hjg_warm_start_frame": (C.c_int, [_vp, _vp, C.c_int64, C.c_int]),
     "hjg_get_residual_parts": (C.c_int, [_vp, _vp]),
     "hjg_set_horizons": (C.c_int, [_vp, _vp, C.c_int]),
     "hjg_selftest_bounded_wait": (C.c_int, [C.c_int, C.c_int64, _vp]),

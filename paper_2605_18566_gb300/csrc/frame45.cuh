@@ -88,11 +88,14 @@ __global__ void frame45_out_kernel(const float* __restrict__ x, int64_t ldx, int
 }
 
 // Warm start from the network's frame outputs pred [M][ldpr]: v = l + dv, Dv = Dl + the
-// correction mapped back to state coordinates, c = Gamma(Dv) on the stored FP32 Dv.
+// correction mapped back to state coordinates, c = Gamma(Dv) on the stored FP32 Dv.  With
+// positions_only the heading rows of Dv keep Dl's (zero: l does not depend on the headings)
+// and only the position rows take the correction.
 __global__ void frame45_warm_kernel(const float* __restrict__ x, int64_t ldx, int64_t M, GameParams g,
                                     double delta, double eta, double c_min, double c_max,
-                                    const float* __restrict__ pred, int64_t ldpr, double* __restrict__ v,
-                                    float* __restrict__ p, int64_t ldp, float* __restrict__ c) {
+                                    const float* __restrict__ pred, int64_t ldpr, bool positions_only,
+                                    double* __restrict__ v, float* __restrict__ p, int64_t ldp,
+                                    float* __restrict__ c) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     double xd[45], gr[45];
@@ -112,14 +115,14 @@ __global__ void frame45_warm_kernel(const float* __restrict__ x, int64_t ldx, in
         const double gx = ux * ce - uz * se, gz = ux * se + uz * ce;   // R(-theta_e)^T u
         gr[3 * i] += gx;
         gr[3 * i + 1] += gz;
-        gr[3 * i + 2] += w;
+        if (!positions_only) gr[3 * i + 2] += w;
         ex -= gx;
         ez -= gz;
         th += ux * rz - uz * rx - w;
     }
     gr[42] += ex;
     gr[43] += ez;
-    gr[44] += th;
+    if (!positions_only) gr[44] += th;
     v[m] = Rockets45::ell_d(xd, g) + (double)q[0];
     double pp = 0.0;
     for (int j = 0; j < 45; ++j) {

@@ -693,7 +693,7 @@ hjg_status hjg_frame_targets(hjg_ctx* ctx, float* out, int64_t ldo) {
     return HJG_OK;
 }
 
-hjg_status hjg_warm_start_frame(hjg_ctx* ctx, const float* pred, int64_t ldp) {
+hjg_status hjg_warm_start_frame(hjg_ctx* ctx, const float* pred, int64_t ldp, int positions_only) {
     if (!ctx || !pred) return HJG_EINVAL;
     hjg_status s;
     if ((s = frame45_ok(ctx))) return s;
@@ -703,8 +703,8 @@ hjg_status hjg_warm_start_frame(hjg_ctx* ctx, const float* pred, int64_t ldp) {
     ctx->se_valid = false;
     const int T = 128;
     frame45_warm_kernel<<<(unsigned)((M + T - 1) / T), T, 0, ctx->stream>>>(
-        ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min, ctx->c_max, pred, ldp, ctx->d_v, ctx->d_p,
-        ctx->ldx, ctx->d_c);
+        ctx->d_x, ctx->ldx, M, ctx->gp, ctx->delta, ctx->eta, ctx->c_min, ctx->c_max, pred, ldp, positions_only != 0,
+        ctx->d_v, ctx->d_p, ctx->ldx, ctx->d_c);
     HJG_CUDA(ctx, cudaGetLastError());
     HJG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HJG_OK;

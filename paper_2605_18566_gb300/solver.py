@@ -241,10 +241,12 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.hjg_frame_targets(self.ctx, self._ptr(out), out.stride(0)))
         return out
 
-    def warm_start_frame(self, pred: torch.Tensor):
-        """45-D game: warm start from an invariant-frame prediction [M, >= 43] (hjg_warm_start_frame)."""
+    def warm_start_frame(self, pred: torch.Tensor, positions_only: bool = True):
+        """45-D game: warm start from an invariant-frame prediction [M, >= 43]
+        (hjg_warm_start_frame); by default only the position rows of Dv take the correction."""
         assert pred.is_cuda and pred.dtype == torch.float32 and pred.stride(1) == 1 and pred.shape[1] >= 43
-        _check(self.lib, self.ctx, self.lib.hjg_warm_start_frame(self.ctx, self._ptr(pred), pred.stride(0)))
+        _check(self.lib, self.ctx, self.lib.hjg_warm_start_frame(self.ctx, self._ptr(pred), pred.stride(0),
+                                                                 1 if positions_only else 0))
 
     def autotune(self, max_states: int = 0) -> dict:
         """Pick the fastest sweep launch variant on the loaded states (see hjg_autotune)."""

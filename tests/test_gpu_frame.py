@@ -146,7 +146,7 @@ def test_targets_and_warm_start_round_trip():
     _close(tn, ref, 2e-6, "targets")
 
     s2 = _solver(x)
-    s2.warm_start_frame(t)
+    s2.warm_start_frame(t, positions_only=False)
     st2 = {k: v.cpu().numpy() for k, v in s2.get_state().items()}
     s2.close()
     _close(st2["v"][:, None], st1["v"][:, None], 1e-6, "v")
@@ -165,3 +165,33 @@ def test_frame_rejects_other_games():
     with pytest.raises(RuntimeError):
         s.frame_features()
     s.close()
+
+
+def test_positions_only_warm_start_keeps_heading_rows_of_l():
+    """positions_only: the position rows of Dv are those of the full mapping, the 15 heading
+    rows keep Dl's (zero), the value is the same, and c is Gamma of that Dv (recomputed here
+    through hjg_warm_start_delta with the same state-coordinate correction)."""
+    x = hjg_inputs.rockets45_wide_points(512, 7).astype(np.float32)
+    xd = x.astype(np.float64)
+    h, g = _h(xd), _grad_fd(xd)
+    d = torch.from_numpy(np.concatenate([h[:, None], g], 1).astype(np.float32)).cuda()
+    s1 = _solver(x)
+    s1.warm_start_delta(d)
+    t = s1.frame_targets()
+    s1.close()
+    s2 = _solver(x)
+    s2.warm_start_frame(t, positions_only=True)
+    st2 = {k: v.cpu().numpy() for k, v in s2.get_state().items()}
+    d2 = s2.state_delta().cpu().numpy()
+    s2.close()
+    heading = np.arange(2, 45, 3)
+    position = np.setdiff1d(np.arange(45), heading)
+    assert np.all(d2[:, 1 + heading] == 0.0)
+    np.testing.assert_allclose(d2[:, 1 + position], g[:, position], rtol=0, atol=1e-5)
+    gp = g.copy(); gp[:, heading] = 0.0
+    s3 = _solver(x)
+    s3.warm_start_delta(torch.from_numpy(np.concatenate([h[:, None], gp], 1).astype(np.float32)).cuda())
+    st3 = {k: v.cpu().numpy() for k, v in s3.get_state().items()}
+    s3.close()
+    _close(st2["v"][:, None], st3["v"][:, None], 1e-6, "v")
+    np.testing.assert_allclose(st2["c"], st3["c"], rtol=1e-3, atol=0)
