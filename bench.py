@@ -77,9 +77,9 @@ IMUL_PER_SM_CLK = 32
 # workload at its full M and K, from one-pass ncu captures of the sweep kernel.  The
 # traffic does not depend on N (samples never touch memory; each state's rows are read and
 # written once per launch).  A workload without a capture of the current kernel has none.
-# rockets45: 110,771,456 B read + 71,333,376 B written, captured at the full 262,144 states and
-# K = 30 with N = 1,024 (launch variant 2, the autotuner's pick); see profiles/.
-DRAM_BYTES_LAUNCH = {"rockets45": 110771456.0 + 71333376.0,
+# rockets45: 110,425,088 B read + 70,873,088 B written, captured at the full 262,144 states and
+# K = 30 with N = 1,024 (launch variant 9, the autotuner's pick); see profiles/.
+DRAM_BYTES_LAUNCH = {"rockets45": 110425088.0 + 70873088.0,
                      # rockets6: 5,245,440 B read + 0 B written at M = 65,536, K = 20, N = 1,024
                      "rockets6": 5245440.0 + 0.0}
 
