@@ -150,6 +150,8 @@ __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, const uin
 // slot i * slot_stride(n) + d of the stream, i.e. lane (slot % 8) of block slot / 8.
 __global__ void normals_kernel(int n, uint32_t k0, uint32_t k1, uint32_t point, uint32_t sweep,
                                int64_t ns, float* __restrict__ out) {
+    bm_table_fill();
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     const uint64_t q0 = (uint64_t)i * (uint64_t)slot_stride(n);

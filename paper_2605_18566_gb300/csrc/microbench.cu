@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(kThreads) philox_pipe(int64_t iters, float* si
 
 // Full Box-Muller normals from Philox blocks, as the sweep draws them (8 per block).
 __global__ void __launch_bounds__(kThreads) normals_pipe(int64_t iters, float* sink) {
+    hjg::bm_table_fill();
+    __syncthreads();
     float acc = 0.0f;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = 0; i < iters; ++i) {

@@ -140,12 +140,33 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 ctr, const PhiloxKeys& r
 constexpr float kBmScale = -1.1774100225154747f;
 
 // Box-Muller on the four words of one Philox block: up to eight normals, pair j from word
-// j (constant factors left out, see above).
+// j (constant factors left out, see above).  The calling kernel must have filled the
+// angle table.
+// The angle field takes one of 4,096 values, so (cos phi, sin phi) of every phase sits in a
+// 32 KB shared-memory table that each CTA of a sampling kernel fills once at its start
+// (bm_table_fill, then a CTA barrier): one shared load per pair instead of two MUFU
+// operations, and the entries are the FP32 roundings of sincospi of the exact phase.
+constexpr int kBmTableSize = 4096;
+__device__ __forceinline__ float2* bm_table() {
+    __shared__ float2 tab[kBmTableSize];
+    return tab;
+}
+// Every thread of the CTA (one-dimensional CTAs) takes part; phi_k = pi ((k + 0.5) 2^-11 - 1),
+// an exact FP32 multiple of pi, is the phase bm_phase builds for angle field k.
+__device__ __forceinline__ void bm_table_fill() {
+    float2* t = bm_table();
+    for (int k = threadIdx.x; k < kBmTableSize; k += blockDim.x) {
+        float s, c;
+        sincospif(fmaf((float)k + 0.5f, 1.0f / 2048.0f, -1.0f), &s, &c);
+        t[k] = make_float2(c, s);
+    }
+}
+
 __device__ __forceinline__ void bm_pair_raw(uint32_t w, float* z, bool both) {
     const float ra = sqrt_approx(fabsf(lg2_approx(u_radius(w))));
-    const float ph = bm_phase(w);
-    z[0] = ra * cos_approx(ph);
-    if (both) z[1] = ra * sin_approx(ph);
+    const float2 cs = bm_table()[w >> 20];
+    z[0] = ra * cs.x;
+    if (both) z[1] = ra * cs.y;
 }
 template <int NUSE>
 __device__ __forceinline__ void bm_normals_raw(const uint4& r, float* z) {

@@ -398,6 +398,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel(const SweepArgs A)
     __shared__ SweepShared<NPAD, W, G::kCache> sh;
     __shared__ float s_aux[KA];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    bm_table_fill();
+    __syncthreads();
     const uint32_t N32 = (uint32_t)A.N;
     const uint32_t full = N32 / GS;            // groups whose GS samples all lie inside N
     const uint32_t groups = (N32 + GS - 1) / GS;
@@ -554,6 +556,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_warp(const SweepAr
     __shared__ float s_S[WPC][n];
     constexpr int KA = G::kAux > 0 ? G::kAux : 1;
     __shared__ float s_aux[WPC][KA];
+    bm_table_fill();
+    __syncthreads();
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * WPC;
     const uint32_t N32 = (uint32_t)A.N;
@@ -645,6 +649,8 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
     __shared__ SweepShared<NPAD, W, G::kCache> sh;
     __shared__ float s_aux[1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    bm_table_fill();
+    __syncthreads();
     const int h = lane & 1;
     const int grp = tid >> 1;
     const int src_e = lane | 1;
