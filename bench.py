@@ -51,47 +51,68 @@ PAPER_CONTEXT = {"value": 2.0e7, "unit": UNIT,
                  "hardware": "one core of an Intel Core i7-14700K, JAX on the CPU backend",
                  "derived_from": "3-D slice timings (states x N x sweeps / time)"}
 
-# Algorithmic per-point-sample work of the sweep on the two pipes that bind it (counts
-# for each workload's game; the block index sits in the Philox counter words the first
-# round does not multiply, so 4 of the 20 multiplies of a block depend only on the state
-# and sweep and are not per-sample work):
+# Per-point-sample work of the sweep on the pipes that share its time (counts for each
+# workload's game; the block index sits in the Philox counter words the first round does
+# not multiply, so 4 of the 20 multiplies of a block depend only on the state and sweep and
+# are not per-sample work):
 #   Philox blocks per sample (eight normals per block): n / 8 for n <= 8 (packed slots),
 #   ceil(n/8) above
 #   high halves of the 32x32 products (mul.hi.u32, 32 per SM and clock): 16 per block
-#   (the low halves issue at twice that rate and are not the binding part)
-#   MUFU (XU pipe): log2, sqrt, sin, cos per Box-Muller pair, one sqrt for the target
-#   distance, one exp2 weight (exp2 issues at twice the rate of the others on GB300)
+#   MUFU (XU pipe, 16 per SM and clock): log2 and sqrt per Box-Muller pair -- the pair's
+#   cos and sin come from the 4,096-entry shared-memory table of the 12-bit angle field --,
+#   one sqrt for the target distance and one exp2 weight at half cost: n + 1.5
+#   issue (4 warp instructions = 128 thread instructions per SM and clock): the kernel's
+#   own thread instructions per point-sample, per launch variant, from ncu
+#   (smsp__inst_executed.sum x 32 / point-samples on each workload's small ncu case, one
+#   capture per variant) -- measured, not algorithmic
+#   mufu_equivalent: the 2n + 1.5 transcendental evaluations of the Box-Muller transform
+#   with cos and sin on the MUFU pipe, the accounting before the table, over the MUFU peak;
+#   kept for comparison only, it is no pipe's load
 BLOCKS_PER_SAMPLE = {"double_int2": 2 / 8, "dubins3": 3 / 8, "rockets_rel3": 3 / 8, "rockets6": 6 / 8,
                      "rockets45": 6.0}
-MUFU_PER_SAMPLE = {"double_int2": 2 * 2 + 2, "dubins3": 2 * 3 + 2, "rockets_rel3": 2 * 3 + 2,
-                   "rockets6": 2 * 6 + 2, "rockets45": 2 * 45 + 2}
+GAME_N = {"double_int2": 2, "dubins3": 3, "rockets_rel3": 3, "rockets6": 6, "rockets45": 45}
+MUFU_PER_SAMPLE = {g: n + 1.5 for g, n in GAME_N.items()}
+MUFU_EQUIV_PER_SAMPLE = {g: 2 * n + 1.5 for g, n in GAME_N.items()}
+INSTR_PER_SAMPLE = {
+    "rockets45": {0: 658.5, 1: 658.7, 2: 657.9, 3: 657.9, 4: 660.5, 5: 678.8, 6: 680.0, 7: 685.1,
+                  8: 683.0, 9: 647.9, 10: 647.9, 11: 679.9},
+    "rockets6": {0: 84.0, 1: 83.6, 2: 87.0, 3: 81.3, 4: 82.4, 5: 83.0, 6: 88.3, 7: 81.8, 8: 89.6,
+                 9: 88.5, 10: 82.6, 11: 91.8},
+}
 IMUL_PER_BLOCK = 16
-# GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations
-# and 32 high-half integer multiplies.
+# GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations,
+# 32 high-half integer multiplies and 4 issued warp instructions.
 SMS = 152
 SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16
 IMUL_PER_SM_CLK = 32
+ISSUE_PER_SM_CLK = 4 * 32
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep launch of each
 # workload at its full M and K, from one-pass ncu captures of the sweep kernel.  The
 # traffic does not depend on N (samples never touch memory; each state's rows are read and
 # written once per launch).  A workload without a capture of the current kernel has none.
-# rockets45: 110,425,088 B read + 70,873,088 B written, captured at the full 262,144 states and
-# K = 30 with N = 1,024 (launch variant 9, the autotuner's pick); see profiles/.
-DRAM_BYTES_LAUNCH = {"rockets45": 110425088.0 + 70873088.0,
-                     # rockets6: 5,245,440 B read + 0 B written at M = 65,536, K = 20, N = 1,024
-                     "rockets6": 5245440.0 + 0.0}
+# rockets45: 110,972,672 B read + 72,240,384 B written, captured at the full 262,144 states and
+# K = 30 with N = 1,024 (launch variant 3); see profiles/.
+DRAM_BYTES_LAUNCH = {"rockets45": 110972672.0 + 72240384.0,
+                     # rockets6: 5,066,496 B read + 0 B written at M = 65,536, K = 20, N = 1,024
+                     # (launch variant 7)
+                     "rockets6": 5066496.0 + 0.0}
 
 
-def roofline(game, samples, kernel_s, full_size=False):
-    """Binding-pipe roofline of the sweep kernel: achieved algorithmic operations per
-    second over the pipe's peak at the maximum SM clock."""
+def roofline(game, samples, kernel_s, full_size=False, variant=None):
+    """Binding-pipe roofline of the sweep kernel: operations per second over the pipe's peak
+    at the maximum SM clock, for the MUFU and high-half-multiply pipes (algorithmic counts)
+    and, where the launch variant's instruction count was measured, the issue port; the
+    bound is the pipe closest to its peak."""
     clk = SMS * SM_MAX_MHZ * 1e6
     pipes = {
         "int_mul_hi": (samples * BLOCKS_PER_SAMPLE[game] * IMUL_PER_BLOCK, IMUL_PER_SM_CLK * clk),
-        "mufu": (samples * (MUFU_PER_SAMPLE[game] - 0.5), MUFU_PER_SM_CLK * clk),
+        "mufu": (samples * MUFU_PER_SAMPLE[game], MUFU_PER_SM_CLK * clk),
     }
+    ips = INSTR_PER_SAMPLE.get(game, {}).get(variant)
+    if ips:
+        pipes["issue"] = (samples * ips, ISSUE_PER_SM_CLK * clk)
     fr = {k: (ops / kernel_s) / peak for k, (ops, peak) in pipes.items()}
     bind = max(fr, key=fr.get)
     ops, peak = pipes[bind]
@@ -100,7 +121,10 @@ def roofline(game, samples, kernel_s, full_size=False):
             "unit": "Gop/s", "frac": fr[bind], "traffic": traffic,
             "hbm_gbs": traffic / kernel_s / 1e9 if traffic else None,
             "ops_per_point_sample": ops / samples,
+            "ops_kind": "thread instructions (measured by ncu for this launch variant)" if bind == "issue"
+            else "algorithmic operations",
             "other_pipes": {k: round(v, 4) for k, v in fr.items() if k != bind},
+            "mufu_equivalent_frac": round(samples * MUFU_EQUIV_PER_SAMPLE[game] / kernel_s / (MUFU_PER_SM_CLK * clk), 4),
             "peak_basis": "per-SM-per-clock pipe rate x 152 SMs x 2070 MHz"}
 
 
@@ -343,7 +367,8 @@ def workload_line(w, m, world, dev, sharded):
         "e2e": {"value": samples_per_step / e2e_s, "unit": UNIT, "steps": m["e2e_steps"],
                 "h2d_bytes_per_step": m["h2d"] * scale, "d2h_bytes_per_step": m["d2h"] * scale},
         "roofline": dict(roofline(w.game, rank_samples, kern_s,
-                                  full_size=not sharded and w.M == BENCH_WORKLOADS[w.game].M),
+                                  full_size=not sharded and w.M == BENCH_WORKLOADS[w.game].M,
+                                  variant=m["tuned"]["variant"]),
                          kernel_ms_per_step=kern_s * 1e3),
         "launch": {"variant": m["tuned"]["variant"], "threads": m["tuned"]["threads"]},
         "residuals": [float(r) for r in m["resid"]],
@@ -581,7 +606,7 @@ def run_games(args):
             games[w.name] = {"game": w.game, "M": int(x.shape[0]), "N": N, "sweeps": 2,
                              "variant": t["variant"], "threads": t["threads"], "kernel_ms": best,
                              "value": samples / (best / 1e3),
-                             "roofline": roofline(w.game, samples, best / 1e3)
+                             "roofline": roofline(w.game, samples, best / 1e3, variant=t["variant"])
                              if w.game in BLOCKS_PER_SAMPLE else None}
             s.close()
         w = hjg_inputs.DUBINS3

@@ -21,23 +21,33 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_work_constants_follow_the_stream_layout(game, n):
     # Philox blocks per sample: slots per sample over the eight normals a block yields
     assert bench.BLOCKS_PER_SAMPLE[game] == pytest.approx(oracle.slot_stride(n) / 8.0)
-    # MUFU: lg2, sqrt, sin, cos per Box-Muller pair of the n normals used, one square root
-    # for the target distance and one exp2 weight
-    assert bench.MUFU_PER_SAMPLE[game] == 4 * n / 2 + 2
+    # MUFU: lg2 and sqrt per Box-Muller pair of the n normals used (cos and sin from the
+    # angle table), one square root for the target distance, one exp2 weight at half cost
+    assert bench.MUFU_PER_SAMPLE[game] == n + 1.5
+    # the transcendental evaluations with cos and sin on the MUFU pipe
+    assert bench.MUFU_EQUIV_PER_SAMPLE[game] == 4 * n / 2 + 1.5
 
 
 def test_roofline_picks_the_binding_pipe():
     clk = bench.SMS * bench.SM_MAX_MHZ * 1e6
     samples = 1e12
     # a time at which the MUFU pipe runs exactly at its peak
-    t = samples * (bench.MUFU_PER_SAMPLE["rockets6"] - 0.5) / (bench.MUFU_PER_SM_CLK * clk)
+    t = samples * bench.MUFU_PER_SAMPLE["rockets6"] / (bench.MUFU_PER_SM_CLK * clk)
     r = bench.roofline("rockets6", samples, t)
     assert r["pipe"] == "mufu" and r["bound"] == "alu"
     assert r["frac"] == pytest.approx(1.0)
-    assert r["other_pipes"]["int_mul_hi"] < 1.0
+    assert r["other_pipes"]["int_mul_hi"] < 1.0 and "issue" not in r["other_pipes"]
+    assert r["mufu_equivalent_frac"] == pytest.approx(13.5 / 7.5, rel=1e-3)
     assert r["traffic"] is None                      # not a full-size launch
     r2 = bench.roofline("rockets6", hjg_inputs.ROCKETS6.M * 10, 1.0, full_size=True)
     assert r2["traffic"] == bench.DRAM_BYTES_LAUNCH.get("rockets6")
+    # with a measured instruction count the issue port joins, and binds where it is closest
+    v = 7
+    t_issue = samples * bench.INSTR_PER_SAMPLE["rockets6"][v] / (bench.ISSUE_PER_SM_CLK * clk)
+    r3 = bench.roofline("rockets6", samples, t_issue, variant=v)
+    assert r3["pipe"] == "issue" and r3["frac"] == pytest.approx(1.0)
+    assert r3["ops_per_point_sample"] == pytest.approx(bench.INSTR_PER_SAMPLE["rockets6"][v])
+    assert set(bench.INSTR_PER_SAMPLE["rockets45"]) == set(range(12))
 
 
 def test_sweeps_to_floor():
