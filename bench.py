@@ -78,6 +78,13 @@ INSTR_PER_SAMPLE = {
                   8: 683.0, 9: 647.9, 10: 647.9, 11: 679.9},
     "rockets6": {0: 84.0, 1: 83.6, 2: 87.0, 3: 81.3, 4: 82.4, 5: 83.0, 6: 88.3, 7: 81.8, 8: 89.6,
                  9: 88.5, 10: 82.6, 11: 91.8},
+    # the other games at their workloads' N (the per-state work is part of the count)
+    "dubins3": {0: 56.1, 1: 54.0, 2: 56.6, 3: 54.0, 4: 54.3, 5: 54.6, 6: 57.2, 7: 54.7, 8: 58.2,
+                9: 57.5, 10: 54.8, 11: 58.9},
+    "rockets_rel3": {0: 63.4, 1: 60.3, 2: 63.2, 3: 60.3, 4: 61.6, 5: 58.5, 6: 61.2, 7: 58.6, 8: 67.4,
+                     9: 64.1, 10: 58.7, 11: 65.7},
+    "double_int2": {0: 55.3, 1: 53.4, 2: 58.5, 3: 53.4, 4: 55.4, 5: 49.0, 6: 54.1, 7: 49.5, 8: 64.2,
+                    9: 58.9, 10: 49.3, 11: 58.9},
 }
 IMUL_PER_BLOCK = 16
 # GB300 unit counts and clock: 152 SMs at 2070 MHz; per SM and clock 16 MUFU operations,
