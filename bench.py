@@ -647,7 +647,8 @@ def surrogate_study(points_fn, label):
     from l, and the same sweep warm-started from the network (hjg_warm_start_frame, position
     rows only), for K = 1, 2, 3, 6, 12 sweeps and N = 4,096, 16,384, 65,536.
     `sweeps_to_match`: per N, the fewest sweeps after which the assisted form is at least as
-    close as the sweep from l after 12."""
+    close as the sweep from l after 12, with the device time of both (sweep kernel, plus the
+    network's features, forward pass and warm start for the assisted one)."""
     import torch
     from paper_2605_18566_gb300 import Solver, Surrogate
     w = hjg_inputs.ROCKETS45
@@ -685,15 +686,32 @@ def surrogate_study(points_fn, label):
     probe.close()
     sur.close()
 
-    def solve(N, K, tilt=True, cv=True, warm=False, seed=11):
+    def solve(N, K, tilt=True, cv=True, warm=False, seed=11, timed=False):
         so = Solver(w.game, w.nu, w.T, N, max(K, 1), radius=w.radius, tilt=tilt, seed=seed, cv=cv)
         so.set_points(xte)
         if warm:
             so.warm_start_frame(pred, positions_only=True)
         r = so.picard_sweep(K)[0] if K > 0 else [float("nan")]
+        ms = so.diagnostics()["last_ms"] if K > 0 else 0.0
         st = so.get_state()
         so.close()
-        return st["v"].cpu().numpy(), float(r[-1])
+        out = (st["v"].cpu().numpy(), float(r[-1]))
+        return out + (ms,) if timed else out
+
+    # device time of the network's part of an assisted solve: frame features, forward pass,
+    # warm start (CUDA events on the current stream, best of three)
+    tsol = Solver(w.game, w.nu, w.T, 4096, 1, radius=w.radius, tilt=True, cv=True)
+    tsol.set_points(xte)
+    tnet = Surrogate(56, 43, 256, seed=0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    net_ms = float("inf")
+    for _ in range(3):
+        ev[0].record()
+        tsol.warm_start_frame(tnet.forward(tsol.frame_features()), positions_only=True)
+        ev[1].record()
+        torch.cuda.synchronize()
+        net_ms = min(net_ms, ev[0].elapsed_time(ev[1]))
+    tsol.close(); tnet.close()
 
     vref, rref = solve(1 << 20, 12, cv=False, seed=7)
     rms = lambda v: float(np.sqrt(np.mean((v - vref) ** 2)))
@@ -703,19 +721,26 @@ def surrogate_study(points_fn, label):
         rows.append({"mode": "plain", "N": N, "K": 12, "rms_value_error": rms(v), "final_residual": r})
         for K in (1, 2, 3, 6, 12):
             for mode in ("tilt+cv", "surrogate+tilt+cv"):
-                v, r = solve(N, K, warm=mode.startswith("surrogate"))
-                rows.append({"mode": mode, "N": N, "K": K, "rms_value_error": rms(v), "final_residual": r})
+                v, r, ms = solve(N, K, warm=mode.startswith("surrogate"), timed=True)
+                rows.append({"mode": mode, "N": N, "K": K, "rms_value_error": rms(v), "final_residual": r,
+                             "sweep_ms": ms})
         e12 = next(q["rms_value_error"] for q in rows if q["mode"] == "tilt+cv" and q["N"] == N and q["K"] == 12)
         ks = [q["K"] for q in rows if q["mode"] == "surrogate+tilt+cv" and q["N"] == N
               and q["rms_value_error"] <= e12]
-        match.append({"N": N, "from_l_12_sweeps_error": e12, "assisted_sweeps": min(ks) if ks else None})
+        k_a = min(ks) if ks else None
+        t12 = next(q["sweep_ms"] for q in rows if q["mode"] == "tilt+cv" and q["N"] == N and q["K"] == 12)
+        ta = next((q["sweep_ms"] for q in rows if q["mode"] == "surrogate+tilt+cv" and q["N"] == N
+                   and q["K"] == k_a), None)
+        match.append({"N": N, "from_l_12_sweeps_error": e12, "assisted_sweeps": k_a,
+                      "from_l_12_sweeps_ms": t12,
+                      "assisted_ms_incl_network": ta + net_ms if ta is not None else None})
     return {"label": label, "tuple_generation_s": t_data, "train_s": t_train,
             "tuples": int(X.shape[0]), "epochs": epochs, "batch": batch,
             "loss": [hist[0], hist[-1]],
             "reference": {"N": 1 << 20, "K": 12, "tilt": True, "final_residual": rref},
             "initial_iterate_rms_value_error": rms(solve(4096, 0)[0]),
             "surrogate_alone_rms_value_error": rms(solve(4096, 0, warm=True)[0]),
-            "study": rows, "sweeps_to_match": match}
+            "network_ms_per_1024_states": net_ms, "study": rows, "sweeps_to_match": match}
 
 
 def run_surrogate(args):
