@@ -70,15 +70,8 @@ __device__ __forceinline__ float u_radius(uint32_t w) {
 }
 
 // Box-Muller phase phi = 2 pi u - pi in (-pi, pi) for the angle uniform u = (k + 0.5) 2^-12
-// of the high 12 bits k of w: with f = 1 + k 2^-12 (the field placed in the top mantissa
-// bits), phi = 2 pi f - 3 pi + pi 2^-12, one FMA.  The pair is (r cos 2 pi u, r sin 2 pi u)
-// = (-r cos phi, -r sin phi).
-constexpr float kTwoPi = 6.283185307179586f;
-constexpr float kPhase12 = -0x1.2d918p+3f;   // -3 pi + pi 2^-12 in binary32
-__device__ __forceinline__ float bm_phase(uint32_t w) {
-    const uint32_t f = ((w >> 9) & 0x007FF800u) | 0x3F800000u;
-    return fmaf(__uint_as_float(f), kTwoPi, kPhase12);
-}
+// of the high 12 bits k of w: phi = pi ((k + 0.5) 2^-11 - 1).  The pair is
+// (r cos 2 pi u, r sin 2 pi u) = (-r cos phi, -r sin phi).
 
 // Per-round Philox keys (k + r W for rounds r = 0..9), computed once on the host so that
 // the rounds take them straight from the constant bank.
@@ -151,8 +144,8 @@ __device__ __forceinline__ float2* bm_table() {
     __shared__ float2 tab[kBmTableSize];
     return tab;
 }
-// Every thread of the CTA (one-dimensional CTAs) takes part; phi_k = pi ((k + 0.5) 2^-11 - 1),
-// an exact FP32 multiple of pi, is the phase bm_phase builds for angle field k.
+// Every thread of the CTA (one-dimensional CTAs) takes part; entry k holds the phase of angle
+// field k, phi_k = pi ((k + 0.5) 2^-11 - 1) (the argument of sincospi is exact in FP32).
 __device__ __forceinline__ void bm_table_fill() {
     float2* t = bm_table();
     for (int k = threadIdx.x; k < kBmTableSize; k += blockDim.x) {
