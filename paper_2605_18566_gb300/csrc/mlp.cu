@@ -1500,14 +1500,16 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
     };
     bool ok = true;
     if (tid == 0 && nch > 0) {
-        uint32_t ph_full[kWgStages] = {}, ph_empty[kWgStages] = {};
-        int issued = 0, landed = 0;
+        // chunk c uses stage c % S; its copies complete phase c / S of full[c % S] and its
+        // products' commit phase c / S of empty[c % S], so every wait takes its parity from
+        // the chunk index.  The stage of chunk c - 1 is refilled right after chunk c's
+        // products are issued: the tensor core works on chunk c while chunk c - 1 retires.
+        int issued = 0, landed = 0, last = -1;
         for (; issued < nch && issued < kWgStages; ++issued)
             chunk(s0 + (uint32_t)(issued * kWgStage), kbeg + (int64_t)issued * kTcK, smem_u32(&full[issued]));
         for (int c = 0; c < nch; ++c) {
             const int s = c % kWgStages;
-            if (!mbar_wait(smem_u32(&full[s]), ph_full[s], g.err)) { ok = false; break; }
-            ph_full[s] ^= 1u;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(c / kWgStages) & 1u, g.err)) { ok = false; break; }
             landed = c + 1;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = s0 + (uint32_t)(s * kWgStage), sb = sa + kTcM * kTcK * 2;
@@ -1523,23 +1525,24 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
             mma_commit(smem_u32(&empty[s]));
-            if (issued < nch) {
-                if (!mbar_wait(smem_u32(&empty[s]), ph_empty[s], g.err)) { ok = false; break; }
-                ph_empty[s] ^= 1u;
-                chunk(sa, kbeg + (int64_t)issued * kTcK, smem_u32(&full[s]));
+            last = c;
+            if (c >= 1 && issued < nch) {   // issued == c - 1 + S: the stage of chunk c - 1
+                const int sp = (c - 1) % kWgStages;
+                if (!mbar_wait(smem_u32(&empty[sp]), (uint32_t)((c - 1) / kWgStages) & 1u, g.err)) {
+                    ok = false;
+                    break;
+                }
+                chunk(s0 + (uint32_t)(sp * kWgStage), kbeg + (int64_t)issued * kTcK, smem_u32(&full[sp]));
                 ++issued;
             }
         }
-        if (ok) {
-            const int s = (nch - 1) % kWgStages;
-            ok = mbar_wait(smem_u32(&empty[s]), ph_empty[s], g.err);
-        } else {
-            for (int c = landed; c < issued; ++c) {
-                const int s = c % kWgStages;
-                mbar_wait(smem_u32(&full[s]), ph_full[s], g.err);
-                ph_full[s] ^= 1u;
-            }
-        }
+        // the last chunk's commit arrives once every product issued so far has completed
+        if (last >= 0 &&
+            !mbar_wait(smem_u32(&empty[last % kWgStages]), (uint32_t)(last / kWgStages) & 1u, g.err))
+            ok = false;
+        if (!ok)   // no copy may land after the exit
+            for (int c = landed; c < issued; ++c)
+                mbar_wait(smem_u32(&full[c % kWgStages]), (uint32_t)(c / kWgStages) & 1u, g.err);
     }
     ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
