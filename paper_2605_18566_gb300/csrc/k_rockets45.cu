@@ -1,5 +1,5 @@
 // Sweep kernels for the 15-agent multi-rocket game (Section 3.2), n = 45,
-// four lanes per sample stream, and its control-variate kernel (tilted frame).
+// two lanes per sample stream, and its control-variate kernel (tilted frame).
 #include "dispatch.h"
 
 namespace hjg {
@@ -25,11 +25,13 @@ int occupancy(bool tilt) {
 }
 #define R45_LAUNCH(i, KIND, T, B) case i: return launch<KIND, T, B>(A, tilt, grid, st);
 #define R45_OCC(i, KIND, T, B) case i: return occupancy<KIND, T, B>(tilt);
-// The control-variate kernel (tilted frame only): 256 threads, 1 CTA per SM minimum.
+// The control-variate kernel (tilted frame only): 128 threads, 3 CTAs per SM (its ~166
+// registers fit the 170 that bound allows; at 256 threads and one CTA per SM only 8 warps
+// were resident).
 cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t st) {
     if (v == kCvVariant) {
         if (!tilt) return cudaErrorInvalidValue;
-        sweep_kernel_r45<256, 1, true, true><<<grid, 256, 0, st>>>(A);
+        sweep_kernel_r45<128, 3, true, true><<<grid, 128, 0, st>>>(A);
         return cudaGetLastError();
     }
     switch (v) { HJG_R45_VARIANTS(R45_LAUNCH) }
@@ -38,7 +40,7 @@ cudaError_t sweep(const SweepArgs& A, bool tilt, int v, int grid, cudaStream_t s
 int occ(bool tilt, int v) {
     if (v == kCvVariant) {
         int nb = 0;
-        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<256, 1, true, true>, 256, 0);
+        if (tilt) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel_r45<128, 3, true, true>, 128, 0);
         return nb;
     }
     switch (v) { HJG_R45_VARIANTS(R45_OCC) }
@@ -51,7 +53,7 @@ GameKernels kernels_rockets45() {
     k.n = 45;
     k.nvariants = kNumR45Variants;
     HJG_R45_VARIANTS(HJG_FILL)
-    k.threads[kCvVariant] = 256; k.minb[kCvVariant] = 1; k.per_warp[kCvVariant] = 0;
+    k.threads[kCvVariant] = 128; k.minb[kCvVariant] = 3; k.per_warp[kCvVariant] = 0;
     k.has_cv = true;
     k.cv_tilt_only = true;
     k.sweep = sweep;

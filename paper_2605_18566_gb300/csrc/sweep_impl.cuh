@@ -665,14 +665,15 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
         for (int k = 0; k < A.K; ++k) {
             const uint32_t sweep = A.k0 + (uint32_t)k;
             const float cneg2 = sh.cneg2, cr = sh.cr, sk = sh.sig.sk;
-            float yx0[8], yz0[8], tq[TILT ? L : 1];
+            float yx0[8], yz0[8];
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
                 yx0[a] = sh.yoff[L * h + 3 * a];
                 yz0[a] = sh.yoff[L * h + 3 * a + 1];
             }
-#pragma unroll
-            for (int j = 0; j < (TILT ? L : 1); ++j) tq[j] = TILT ? sh.tq[L * h + j] : 0.0f;
+            // the tilt's 24 coefficients of this lane stay in shared memory (the two lanes of
+            // a pair read two addresses, broadcast to the warp): registers for the normals
+            const float* tql = sh.tq + L * h;
             float m = -INFINITY, s = 0.0f, q = 0.0f, S[L];
 #pragma unroll
             for (int j = 0; j < L; ++j) S[j] = 0.0f;
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(THREADS, MINB) sweep_kernel_r45(const SweepArg
                 if (TILT) {
                     float part = 0.0f;
 #pragma unroll
-                    for (int j = 0; j < L; ++j) part = fmaf(z[j], tq[j], part);
+                    for (int j = 0; j < L; ++j) part = fmaf(z[j], tql[j], part);
                     part += __shfl_xor_sync(0xffffffffu, part, 1);
                     a2 += part;
                 }
