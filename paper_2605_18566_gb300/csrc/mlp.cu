@@ -1226,6 +1226,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's TMEM lanes
+    // launched as a programmatic dependent of the previous kernel in the stream: the set-up
+    // above overlaps its tail, and nothing global is read before it has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     uint32_t ph_w = 0, ph_m = 0, ph_x = 0;
     bool w_pending = false;   // thread 0: a weight copy in flight that no wait has consumed
     const int ip = a.in_pad, op = a.out_pad;
@@ -1441,6 +1444,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // every global write is done
     // neither CTA leaves while the partner may still copy into its shared memory: every copy
     // was consumed by the receiver's wait before the receiver reached this barrier
     cluster_sync();
@@ -1493,6 +1497,7 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = umma_idesc_bf16(kTcM, N);
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // phase A's operands are complete
     auto chunk = [&](uint32_t st, int64_t k0, uint32_t bar) {   // A rows then B rows, 128 B each
         mbar_expect_tx(bar, stage_bytes);
         tma_load_2d(st, tmA, (int)k0, m0, bar);
@@ -1573,6 +1578,7 @@ __global__ void __launch_bounds__(128, 1) mlp_wgrad_kernel(const __grid_constant
         const int r = (4 * i) / N, c = (4 * i) % N;
         reinterpret_cast<float4*>(dst)[i] = *reinterpret_cast<const float4*>(stile + r * ldt + c);
     }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kFW));
 }
 
@@ -1604,6 +1610,7 @@ __device__ __forceinline__ float adam_update(const ApplyArgs& a, int64_t pi, flo
 }
 
 __global__ void __launch_bounds__(256) mlp_apply_kernel(const ApplyArgs a) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the weight-gradient partials are complete
     if ((int)blockIdx.x < a.nwb) {
         // one block per 8 x 32 tile of one layer's weights, one weight per thread: the split
         // sums, the gradient and Adam (row-major, coalesced), then the BF16 copies through a
@@ -1695,6 +1702,26 @@ __global__ void canon_weights_kernel(const float* __restrict__ p, ApplyArgs a) {
     a.wct[a.wp_off[l] + canon_w_idx(c, r, Cc, R)] = hb;
 }
 
+// Launch as a programmatic dependent of the previous kernel in the stream: its blocks may be
+// scheduled while that kernel's last blocks finish; the kernel itself waits
+// (griddepcontrol.wait) before its first global read.
+template <typename Kern, typename Arg>
+cudaError_t launch_dependent(Kern kern, unsigned grid, unsigned block, size_t smem, cudaStream_t st, const Arg& arg) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    memset(at, 0, sizeof at);
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 bool fused_ok(const hjg_mlp* m) {
     return m->width == kFW && m->in_pad <= 64 && m->out_pad <= 64 && m->wc && m->wct;
 }
@@ -1784,8 +1811,9 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
     for (int l = 0; l + 1 < kLayers; ++l) fa.Ht[l] = m->Ht[l];
     fa.Xt = m->Xt; fa.lpart = m->flpart; fa.err = g_tc_err;
     const int ntile = (int)((B + kFRows - 1) / kFRows);
-    mlp_fused_fwdbwd_kernel<<<2 * ntile, kFThreads, kFSmemA, st>>>(fa);   // clusters of two
-    if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+    if (launch_dependent(mlp_fused_fwdbwd_kernel, 2u * (unsigned)ntile, kFThreads, kFSmemA, st, fa) !=
+        cudaSuccess)   // clusters of two
+        return HJG_ECUDA;
 
     WgradArgs wa;
     memset(&wa, 0, sizeof wa);
@@ -1801,8 +1829,8 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
     wa.n_w = m->n_w; wa.K = B; wa.splits = kWgSplits;
     wa.kper = (int)(((B + kWgSplits - 1) / kWgSplits + kTcK - 1) / kTcK * kTcK);
     wa.part = m->fpart; wa.err = g_tc_err;
-    mlp_wgrad_kernel<<<items * kWgSplits, 128, kWgSmem, st>>>(wa);
-    if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+    if (launch_dependent(mlp_wgrad_kernel, (unsigned)(items * kWgSplits), 128, kWgSmem, st, wa) != cudaSuccess)
+        return HJG_ECUDA;
 
     ApplyArgs aa = apply_args(m);
     aa.ldT = ldT; aa.B = B;
@@ -1813,8 +1841,8 @@ hjg_status mlp_fused_step(hjg_mlp* m, const float* x, int64_t ldx, const float* 
         aa.c1 = 1.0f - powf(aa.b1, (float)m->step);
         aa.c2 = 1.0f - powf(aa.b2, (float)m->step);
     }
-    mlp_apply_kernel<<<aa.nwb + aa.n_bias, 256, 0, st>>>(aa);
-    if (cudaGetLastError() != cudaSuccess) return HJG_ECUDA;
+    if (launch_dependent(mlp_apply_kernel, (unsigned)(aa.nwb + aa.n_bias), 256, 0, st, aa) != cudaSuccess)
+        return HJG_ECUDA;
     if (loss_out) {
         std::vector<double> part((size_t)ntile);
         if (cudaMemcpyAsync(part.data(), m->flpart, ntile * sizeof(double), cudaMemcpyDeviceToHost, st) !=
