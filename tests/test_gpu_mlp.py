@@ -168,3 +168,23 @@ def test_save_and_load_reproduce_predictions(tmp_path):
     np.testing.assert_array_equal(t.scaling(), s.scaling())
     np.testing.assert_array_equal(t.forward(xt).cpu().numpy(), s.forward(xt).cpu().numpy())
     s.close(); t.close()
+
+
+def test_gradients_after_an_in_stream_producer():
+    """The training kernels are launched as programmatic dependents of the kernel before
+    them and wait before their first global read: inputs written by a kernel queued on the
+    same stream just before the step give the same gradients, bit for bit, as inputs that
+    were complete (synchronised) beforehand."""
+    s = _sur(seed=6)
+    rng = np.random.default_rng(8)
+    x0 = torch.from_numpy(hjg_inputs.random_states(1000, N_IN, 1.5, seed=9)).cuda()
+    y0 = torch.from_numpy(rng.normal(size=(1000, N_OUT)).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    loss_ref, g_ref = s.gradients(x0, y0)
+    for _ in range(3):
+        x = x0 * 1.0 + 0.0        # kernels on the current stream, not waited for on the host
+        y = (y0 * 2.0) * 0.5
+        loss, g = s.gradients(x, y)
+        assert loss == loss_ref
+        np.testing.assert_array_equal(g, g_ref)
+    s.close()
