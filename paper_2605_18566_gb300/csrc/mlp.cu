@@ -1050,6 +1050,16 @@ __device__ __forceinline__ void bulk_s2peer(uint32_t src, uint32_t bytes, uint32
                  :: "r"(dst), "r"(src), "r"(bytes), "r"(rbar) : "memory");
 }
 
+// Four bytes from global to shared memory without a register round trip (zero-filled when
+// `valid` is false, reading nothing); completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(dst), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Every thread of both CTAs of the pair (release / acquire at cluster scope).
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -1194,6 +1204,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
     __shared__ __align__(8) uint64_t bar_w, bar_m, bar_x;
     __shared__ uint32_t tmem_base;
     __shared__ float s_loss[kFThreads / 32];
+    __shared__ float s_isc[128], s_osc[128];   // inputs [shift | mul], targets [shift | 1 / mul]
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, cg = warp >> 2;             // TMEM lane quarter, column group (of 4)
@@ -1244,27 +1255,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         const int l = e / kFW, i = e % kFW;
         s_bias[e] = i < (l == kLayers - 1 ? op : kFW) ? a.p[a.b_off[l] + i] : 0.0f;
     }
+    if (tid < 2 * ip) s_isc[tid] = a.iscal[tid];
+    else if (tid >= 128 && tid < 128 + op) s_osc[tid - 128] = a.oscal[tid - 128];
+    else if (tid >= 256 && tid < 256 + op) s_osc[op + tid - 256] = 1.0f / a.oscal[op + tid - 256];
     __nv_bfloat16* buf0 = reinterpret_cast<__nv_bfloat16*>(smem);
-    {   // all of a thread's loads issued before any store
-        constexpr int kPer = kFRows * 64 / kFThreads;
-        float xv[kPer];
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int e = tid + k * kFThreads, r = e / ip, j = e % ip;
+    {   // the raw input tile [128][ip] FP32 into buffer 1 (free until the partner's first copy,
+        // which comes after the cluster barrier below) by asynchronous copies, then
+        // standardised into buffer 0 in the canonical layout
+        float* xr = reinterpret_cast<float*>(smem + kFBuf);
+        const uint32_t sxr = smem_u32(xr);
+        for (int e = tid; e < kFRows * ip; e += kFThreads) {
+            const int r = e / ip, j = e % ip;
             const int64_t b = r0 + r;
-            xv[k] = e < kFRows * ip && b < a.B && j < a.n_in ? a.x[b * a.ldx + j] : 0.0f;
+            const bool ok = b < a.B && j < a.n_in;
+            cp_async4(sxr + 4u * (uint32_t)e, ok ? (const void*)(a.x + b * a.ldx + j) : (const void*)a.x, ok);
         }
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int e = tid + k * kFThreads, r = e / ip, j = e % ip;
-            if (e < kFRows * ip)
-                buf0[canon_idx(r, j, kFRows)] =
-                    __float2bfloat16(j < a.n_in && r0 + r < a.B ? (xv[k] - a.iscal[j]) * a.iscal[ip + j] : 0.0f);
+        cp_async_wait_all();
+        __syncthreads();
+        for (int e = tid; e < kFRows * ip; e += kFThreads) {
+            const int r = e / ip, j = e % ip;
+            buf0[canon_idx(r, j, kFRows)] =
+                __float2bfloat16(j < a.n_in ? (xr[e] - s_isc[j]) * s_isc[ip + j] : 0.0f);
         }
     }
     __syncthreads();
-    if (rank == 0) {
-        for (int e = tid; e < kFRows * ip; e += kFThreads) {   // X^T, the K-major operand of dW_1
+    {   // X^T, the K-major operand of dW_1: each CTA of the pair writes half of its columns
+        const int half = kFRows * ip / 2;
+        for (int e = (int)rank * half + tid; e < ((int)rank + 1) * half; e += kFThreads) {
             const int j = e / kFRows, r = e % kFRows;
             if (r0 + r < a.ldT) a.Xt[(int64_t)j * a.ldT + r0 + r] = buf0[canon_idx(r, j, kFRows)];
         }
@@ -1287,27 +1304,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
         const bool send = t == 0 || t == 1 || t == 2 || t == 4 || t == 5;
         const uint32_t s_in = sbuf + (uint32_t)((t & 1) * kFBuf);
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(smem + ((t + 1) & 1) * kFBuf);
-        // the output layer's standardised targets of the tile, loaded row by row (coalesced)
-        // by warps 1-15 while thread 0 waits for the product, into the upper half of buffer 0:
+        // the output layer's targets of the tile, copied row by row (coalesced) by warps 1-15
+        // while thread 0 waits for the product, into the upper half of buffer 0:
         // nothing reads or writes it during step 3 (its inputs were consumed by product 2, dO
         // goes to the lower half, and the partner's next copy into it comes after step 3)
         float* ys = reinterpret_cast<float*>(smem + kFBuf / 2);
-        if (t == 3 && warp > 0) {   // all of a thread's loads issued before any store
-            constexpr int kPer = (kFRows * 64 + kFThreads - 33) / (kFThreads - 32);
-            float yv[kPer];
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const int e = tid - 32 + k * (kFThreads - 32);
+        if (t == 3 && warp > 0) {   // raw, by asynchronous copies; standardised at use
+            const uint32_t sys = smem_u32(ys);
+            for (int e = tid - 32; e < kFRows * op; e += kFThreads - 32) {
                 const int r = e / op, col = e % op;
                 const int64_t b = r0 + r;
-                yv[k] = e < kFRows * op && b < a.B && col < a.n_out ? a.y[b * a.ldy + col] : 0.0f;
+                const bool ok = b < a.B && col < a.n_out;
+                cp_async4(sys + 4u * (uint32_t)e, ok ? (const void*)(a.y + b * a.ldy + col) : (const void*)a.y, ok);
             }
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const int e = tid - 32 + k * (kFThreads - 32);
-                const int col = e % op;
-                if (e < kFRows * op) ys[e] = col < a.n_out ? (yv[k] - a.oscal[col]) / a.oscal[op + col] : 0.0f;
-            }
+            cp_async_wait_all();
         }
         // thread 0: the product of step t once its weights (and the partner's half of its
         // input) have landed, and its completion; the other threads wait at the barrier
@@ -1406,7 +1416,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFThreads, 1)
                     float g = 0.0f;
                     if (valid && col < a.n_out) {
                         const float o = v[j] + s_bias[3 * kFW + col];
-                        const float d = o - ys[row * op + col];
+                        const float d = o - (ys[row * op + col] - s_osc[col]) * s_osc[op + col];
                         const float w = col == 0 ? 1.0f : winv;
                         if (rank == 0) loss += w * d * d;
                         g = 2.0f * w * d / (float)a.B;
