@@ -230,7 +230,7 @@ struct Rockets6 {
 // ---------------------------------------------------------------- 15 rockets (Sec. 3.2)
 // agents i = 0..14 with (x_i, z_i, th_i) at dims 3i..3i+2; agent 14 evades.
 // l = min_{i < 14} |pos_i - pos_14| - r.  The per-sample target is evaluated cooperatively
-// by 4 lanes (see sweep.cu); only the per-state FP64 parts live here.
+// by the two lanes of a sample (sweep_kernel_r45); only the per-state FP64 parts live here.
 struct Rockets45 {
     static constexpr int kN = 45;
     static constexpr bool kRadius = true;
