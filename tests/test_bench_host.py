@@ -47,7 +47,11 @@ def test_roofline_picks_the_binding_pipe():
     r3 = bench.roofline("rockets6", samples, t_issue, variant=v)
     assert r3["pipe"] == "issue" and r3["frac"] == pytest.approx(1.0)
     assert r3["ops_per_point_sample"] == pytest.approx(bench.INSTR_PER_SAMPLE["rockets6"][v])
-    assert set(bench.INSTR_PER_SAMPLE["rockets45"]) == set(range(12))
+    # every launch variant of every counted game has its measured instruction count
+    for game, counts in bench.INSTR_PER_SAMPLE.items():
+        assert game in bench.BLOCKS_PER_SAMPLE and set(counts) == set(range(12)), game
+        # the sampler alone is at least n normals of work per sample
+        assert all(c > bench.GAME_N[game] for c in counts.values()), game
 
 
 def test_sweeps_to_floor():
